@@ -1,0 +1,245 @@
+"""Plain FP64 CPU oracle for the FM-CFUST EM algorithm (arXiv:1606.02054).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import this package.  The CUDA
+library never links, loads or calls it, and it shares no code with the CUDA
+path: the only common ground is the seeded synthetic inputs and published
+definitions (SplitMix64, Korobov lattices) that each side implements itself.
+
+The C source ``cfust_oracle.c`` follows the paper equation by equation:
+eqs (3)-(4) density, (12)-(17) E-step, (18)-(22) M-step, (24)-(26) Aitken,
+(27) log-likelihood.  This module only compiles it and marshals numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cfust_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+DEFAULT_NTHREADS = max(1, os.cpu_count() or 1)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (gcc, OpenMP)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "cfust_oracle.h"))
+    ):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Qmc(C.Structure):
+    _fields_ = [("npoints", C.c_int), ("nshifts", C.c_int), ("korobov_a", C.c_int),
+                ("seed", C.c_uint64)]
+
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = C.CDLL(path)
+            d, i = C.c_double, C.c_int
+            L.ora_digamma.argtypes = [d]; L.ora_digamma.restype = d
+            L.ora_phi.argtypes = [d]; L.ora_phi.restype = d
+            L.ora_phi_inv.argtypes = [d]; L.ora_phi_inv.restype = d
+            L.ora_incbeta.argtypes = [d, d, d]; L.ora_incbeta.restype = d
+            L.ora_incgamma_p.argtypes = [d, d]; L.ora_incgamma_p.restype = d
+            L.ora_chi2_quantile.argtypes = [d, d, d]; L.ora_chi2_quantile.restype = d
+            L.ora_t1pdf.argtypes = [d, d]; L.ora_t1pdf.restype = d
+            L.ora_t1cdf.argtypes = [d, d]; L.ora_t1cdf.restype = d
+            L.ora_t2cdf.argtypes = [d, d, d, d]; L.ora_t2cdf.restype = d
+            L.ora_splitmix64_u01.argtypes = [C.c_uint64]; L.ora_splitmix64_u01.restype = d
+            L.ora_qmc_shift.argtypes = [C.POINTER(Qmc), i, i]; L.ora_qmc_shift.restype = d
+            L.ora_tkcdf.argtypes = [i, _dp, _dp, d, C.POINTER(Qmc), _dp]
+            L.ora_tkcdf.restype = d
+            L.ora_pair.argtypes = [i, i, _dp, _dp, _dp, _dp, d, C.POINTER(Qmc), _dp, _dp, _dp,
+                                   _dp, _dp, _dp]
+            L.ora_pair.restype = i
+            L.ora_estep.argtypes = [i, i, i, i, _dp, _dp, _dp, _dp, _dp, _dp, C.POINTER(Qmc),
+                                    i, _dp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+            L.ora_estep.restype = i
+            L.ora_loglik.argtypes = [i, i, i, i, _dp, _dp, _dp, _dp, _dp, _dp, C.POINTER(Qmc),
+                                     i, _dp]
+            L.ora_loglik.restype = i
+            L.ora_mstep.argtypes = [i, i, i, i, _dp, _dp, _dp, _dp, _dp, _dp, d, d, _dp, _dp,
+                                    _dp, _dp, _dp, _ip]
+            L.ora_mstep.restype = i
+            L.ora_nu_root.argtypes = [d, d, d, d, _ip]; L.ora_nu_root.restype = d
+            L.ora_fit.argtypes = [i, i, i, i, _dp, _dp, _dp, _dp, _dp, _dp, C.POINTER(Qmc), i, d,
+                                  d, d, i, _ip, _dp]
+            L.ora_fit.restype = i
+            L.ora_aitken_converged.argtypes = [d, d, d, d, _dp]
+            L.ora_aitken_converged.restype = i
+            _lib = L
+    return _lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def qmc(npoints=1024, nshifts=8, korobov_a=119, seed=0):
+    """Lattice settings (both sides receive the same values as inputs)."""
+    return Qmc(int(npoints), int(nshifts), int(korobov_a), int(seed))
+
+
+# ---- scalar special functions -------------------------------------------------
+def digamma(x): return lib().ora_digamma(float(x))
+def phi(x): return lib().ora_phi(float(x))
+def phi_inv(p): return lib().ora_phi_inv(float(p))
+def incbeta(a, b, x): return lib().ora_incbeta(float(a), float(b), float(x))
+def incgamma_p(a, x): return lib().ora_incgamma_p(float(a), float(x))
+def chi2_quantile(w, nu, wc=None):
+    return lib().ora_chi2_quantile(float(w), float(1.0 - w if wc is None else wc), float(nu))
+def t1pdf(x, nu): return lib().ora_t1pdf(float(x), float(nu))
+def t1cdf(x, nu): return lib().ora_t1cdf(float(x), float(nu))
+def t2cdf(h, k, rho, nu): return lib().ora_t2cdf(float(h), float(k), float(rho), float(nu))
+def splitmix64_u01(key): return lib().ora_splitmix64_u01(int(key) & 0xFFFFFFFFFFFFFFFF)
+def qmc_shift(spec: Qmc, m, d): return lib().ora_qmc_shift(C.byref(spec), int(m), int(d))
+
+
+def tkcdf(b, V, nu, spec: Qmc | None = None):
+    """T_k(b; 0, V, nu) -> (value, standard error)."""
+    b = _f64(b).ravel()
+    k = b.size
+    V = _f64(V).reshape(k, k)
+    spec = spec or qmc()
+    se = C.c_double(0.0)
+    v = lib().ora_tkcdf(k, _ptr(b), _ptr(V), float(nu), C.byref(spec), C.byref(se))
+    return v, se.value
+
+
+def pair(y, mu, Sigma, Delta, nu, spec: Qmc | None = None):
+    """One (observation, component) pair: dict(logf, u, elogu, eu, euu, se)."""
+    y, mu, Sigma, Delta = _f64(y).ravel(), _f64(mu).ravel(), _f64(Sigma), _f64(Delta)
+    p = y.size
+    q = Delta.size // p
+    spec = spec or qmc()
+    logf, u, el, se = (C.c_double() for _ in range(4))
+    eu = np.zeros(q)
+    euu = np.zeros((q, q))
+    rc = lib().ora_pair(p, q, _ptr(y), _ptr(mu), _ptr(Sigma), _ptr(Delta), float(nu),
+                        C.byref(spec), C.byref(logf), C.byref(u), C.byref(el), _ptr(eu),
+                        _ptr(euu), C.byref(se))
+    if rc:
+        raise RuntimeError(f"ora_pair failed ({rc})")
+    return dict(logf=logf.value, u=u.value, elogu=el.value, eu=eu, euu=euu, se=se.value)
+
+
+def _params(params):
+    pi = _f64(params["pi"])
+    mu = _f64(params["mu"])
+    Sigma = _f64(params["Sigma"])
+    Delta = _f64(params["Delta"])
+    nu = _f64(params["nu"])
+    return pi, mu, Sigma, Delta, nu
+
+
+def estep(y, params, spec: Qmc | None = None, nthreads=None):
+    """Full E-step: dict(logf, tau, u, elogu, eu, euu, se, loglik), arrays [h, j, ...]."""
+    y = _f64(y)
+    n, p = y.shape
+    pi, mu, Sigma, Delta, nu = _params(params)
+    g = pi.size
+    q = Delta.shape[-1]
+    spec = spec or qmc()
+    out = dict(logf=np.zeros((g, n)), tau=np.zeros((g, n)), u=np.zeros((g, n)),
+               elogu=np.zeros((g, n)), eu=np.zeros((g, n, q)), euu=np.zeros((g, n, q, q)),
+               se=np.zeros((g, n)))
+    L = C.c_double()
+    rc = lib().ora_estep(n, p, q, g, _ptr(y), _ptr(pi), _ptr(mu), _ptr(Sigma), _ptr(Delta),
+                         _ptr(nu), C.byref(spec), int(nthreads or DEFAULT_NTHREADS),
+                         _ptr(out["logf"]), _ptr(out["tau"]), _ptr(out["u"]),
+                         _ptr(out["elogu"]), _ptr(out["eu"]), _ptr(out["euu"]),
+                         _ptr(out["se"]), C.byref(L))
+    if rc:
+        raise RuntimeError(f"ora_estep failed ({rc})")
+    out["loglik"] = L.value
+    return out
+
+
+def loglik(y, params, spec: Qmc | None = None, nthreads=None):
+    y = _f64(y)
+    n, p = y.shape
+    pi, mu, Sigma, Delta, nu = _params(params)
+    g, q = pi.size, Delta.shape[-1]
+    spec = spec or qmc()
+    L = C.c_double()
+    rc = lib().ora_loglik(n, p, q, g, _ptr(y), _ptr(pi), _ptr(mu), _ptr(Sigma), _ptr(Delta),
+                          _ptr(nu), C.byref(spec), int(nthreads or DEFAULT_NTHREADS), C.byref(L))
+    if rc:
+        raise RuntimeError(f"ora_loglik failed ({rc})")
+    return L.value
+
+
+def mstep(y, e, params, nu_min=1.0, nu_max=200.0):
+    """M-step from E-step arrays; returns (new params dict, nu_flag)."""
+    y = _f64(y)
+    n, p = y.shape
+    pi, mu, Sigma, Delta, nu = (a.copy() for a in _params(params))
+    g, q = pi.size, Delta.shape[-1]
+    flag = np.zeros(g, dtype=np.int32)
+    rc = lib().ora_mstep(n, p, q, g, _ptr(y), _ptr(_f64(e["tau"])), _ptr(_f64(e["u"])),
+                         _ptr(_f64(e["elogu"])), _ptr(_f64(e["eu"])), _ptr(_f64(e["euu"])),
+                         float(nu_min), float(nu_max), _ptr(pi), _ptr(mu), _ptr(Sigma),
+                         _ptr(Delta), _ptr(nu), flag.ctypes.data_as(_ip))
+    if rc:
+        raise RuntimeError(f"ora_mstep failed ({rc})")
+    return dict(pi=pi, mu=mu, Sigma=Sigma, Delta=Delta, nu=nu), flag
+
+
+def nu_root(n_h, s_h, nu_min=1.0, nu_max=200.0):
+    fl = C.c_int(0)
+    v = lib().ora_nu_root(float(n_h), float(s_h), float(nu_min), float(nu_max), C.byref(fl))
+    return v, fl.value
+
+
+def aitken_converged(l_km1, l_k, l_kp1, eps):
+    li = C.c_double()
+    c = lib().ora_aitken_converged(float(l_km1), float(l_k), float(l_kp1), float(eps),
+                                   C.byref(li))
+    return bool(c), li.value
+
+
+def fit(y, params, iters, spec: Qmc | None = None, tol=0.0, nu_min=1.0, nu_max=200.0,
+        nthreads=None):
+    """EM fit; returns (params, loglik history [iters_done+1], iters_done)."""
+    y = _f64(y)
+    n, p = y.shape
+    pi, mu, Sigma, Delta, nu = (a.copy() for a in _params(params))
+    g, q = pi.size, Delta.shape[-1]
+    spec = spec or qmc()
+    hist = np.full(iters + 1, np.nan)
+    done = C.c_int(0)
+    rc = lib().ora_fit(n, p, q, g, _ptr(y), _ptr(pi), _ptr(mu), _ptr(Sigma), _ptr(Delta),
+                       _ptr(nu), C.byref(spec), int(iters), float(tol), float(nu_min),
+                       float(nu_max), int(nthreads or DEFAULT_NTHREADS), C.byref(done),
+                       _ptr(hist))
+    if rc:
+        raise RuntimeError(f"ora_fit failed ({rc})")
+    k = done.value
+    return dict(pi=pi, mu=mu, Sigma=Sigma, Delta=Delta, nu=nu), hist[: k + 1], k

@@ -1,0 +1,119 @@
+/*
+ * cfust_oracle.h -- plain FP64 CPU oracle for the FM-CFUST EM algorithm.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This oracle exists to check the CUDA library.
+ * Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+ * load it.  It shares no code, header, table or constant with the CUDA path:
+ * the only things both sides see are the seeded synthetic inputs and the
+ * published definitions (SplitMix64, rank-1 Korobov lattices) that each
+ * side implements on its own.
+ *
+ * Paper: Lee, Leemaqz & McLachlan, "A simple multithreaded implementation
+ * of the EM algorithm for mixture models" (arXiv:1606.02054).
+ *   Sec. 2, eqs (1)-(4): mixture and CFUST component density.
+ *   Sec. 3.1, eqs (12)-(17): E-step conditional expectations.
+ *   Sec. 3.2, eqs (18)-(22): M-step updates.
+ *   Sec. 3.4, eqs (24)-(26): Aitken stopping rule.
+ *   Sec. 4.3, eq (27): log-likelihood.
+ *
+ * Layouts (all row-major, FP64):
+ *   y      n x p            observations
+ *   pi     g                mixing proportions
+ *   mu     g x p            locations
+ *   Sigma  g x p x p        scale matrices
+ *   Delta  g x p x q        skewness matrices
+ *   nu     g                degrees of freedom
+ *   per-pair outputs are component-major: X[h*n + j] (eu: [h][j][q],
+ *   euu: [h][j][q][q]).
+ */
+#ifndef CFUST_ORACLE_H
+#define CFUST_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Randomised rank-1 lattice rule used for every T_k with k >= 3.
+ * Points: x_{i,m,d} = frac(((i * z_d) mod N)/N + shift_{m,d}), z_d = a^d mod N,
+ * then the baker's (tent) transform w = 1 - |2x - 1|. */
+typedef struct {
+    int npoints;        /* N (power of two not required) */
+    int nshifts;        /* M */
+    int korobov_a;      /* Korobov generator a */
+    uint64_t seed;      /* SplitMix64 key for the random shifts */
+} ora_qmc;
+
+/* ---- special functions (exposed for the pin tests) ---- */
+double ora_digamma(double x);
+double ora_phi(double x);                 /* standard normal CDF */
+double ora_phi_inv(double p);             /* its inverse */
+double ora_incbeta(double a, double b, double x);   /* regularised I_x(a,b) */
+double ora_incgamma_p(double a, double x);          /* regularised P(a,x) */
+double ora_chi2_quantile(double w, double wc, double nu);  /* P(nu/2,x/2)=w; wc = 1-w */
+double ora_t1pdf(double x, double nu);    /* univariate standard t density */
+double ora_t1cdf(double x, double nu);    /* T_1(x; nu) */
+double ora_t2cdf(double h, double k, double rho, double nu);  /* standard bivariate T_2 */
+double ora_splitmix64_u01(uint64_t key);  /* one SplitMix64 output as a double in [0,1) */
+double ora_qmc_shift(const ora_qmc* qmc, int m, int d);
+/* T_k(b; 0, V, nu) for any k (k<=2 deterministic, k>=3 lattice QMC).
+ * V is k x k row-major.  *se receives the QMC standard error (0 for k<=2). */
+double ora_tkcdf(int k, const double* b, const double* V, double nu,
+                 const ora_qmc* qmc, double* se);
+
+/* ---- E-step for one (observation, component) pair ----
+ * Inputs are one component's parameters.  Outputs: log f_h(y) (eq 4),
+ * u (eq 13), elogu (eq 15), eu (eq 16, q), euu (eq 17, q x q),
+ * se_alpha_s = QMC standard error of the T_q factor of eq 4. */
+int ora_pair(int p, int q, const double* y, const double* mu,
+             const double* Sigma, const double* Delta, double nu,
+             const ora_qmc* qmc, double* logf, double* u, double* elogu,
+             double* eu, double* euu, double* se_alpha_s);
+
+/* ---- full E-step over all pairs (eqs 12-17, 27) ----
+ * Any of the per-pair output pointers may be NULL.  Returns 0 on success. */
+int ora_estep(int n, int p, int q, int g, const double* y,
+              const double* pi, const double* mu, const double* Sigma,
+              const double* Delta, const double* nu, const ora_qmc* qmc,
+              int nthreads, double* logf, double* tau, double* u,
+              double* elogu, double* eu, double* euu, double* se,
+              double* loglik);
+
+/* Density-only pass: log-likelihood (eq 27) at the given parameters. */
+int ora_loglik(int n, int p, int q, int g, const double* y,
+               const double* pi, const double* mu, const double* Sigma,
+               const double* Delta, const double* nu, const ora_qmc* qmc,
+               int nthreads, double* loglik);
+
+/* ---- M-step (eqs 18-22) from per-pair E-step arrays ----
+ * Parameters are updated in place.  nu is found in [nu_min, nu_max];
+ * nu_flag[h] = -1/+1 if clamped at the lower/upper bound, else 0.
+ * Returns 0, or 1 + h for the first component whose update failed. */
+int ora_mstep(int n, int p, int q, int g, const double* y,
+              const double* tau, const double* u, const double* elogu,
+              const double* eu, const double* euu, double nu_min,
+              double nu_max, double* pi, double* mu, double* Sigma,
+              double* Delta, double* nu, int* nu_flag);
+
+/* Root of eq (22) (sign read as + and sum over j) for one component:
+ * n_h [log(nu/2) - psi(nu/2) + 1] + s_h = 0 on [nu_min, nu_max]. */
+double ora_nu_root(double n_h, double s_h, double nu_min, double nu_max,
+                   int* flag);
+
+/* ---- EM fit: iters iterations (tol > 0 enables the Aitken rule) ----
+ * loglik_hist[k] = l(Psi^(k)) for k = 0..iters_done (iters_done+1 values).
+ * Returns 0 on success. */
+int ora_fit(int n, int p, int q, int g, const double* y, double* pi,
+            double* mu, double* Sigma, double* Delta, double* nu,
+            const ora_qmc* qmc, int max_iter, double tol, double nu_min,
+            double nu_max, int nthreads, int* iters_done,
+            double* loglik_hist);
+
+/* Aitken rule (eqs 24-26) on three consecutive log-likelihoods. */
+int ora_aitken_converged(double l_km1, double l_k, double l_kp1, double eps,
+                         double* l_inf);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,196 @@
+"""Pins for the oracle's density and E-step (eqs 4, 12-17), CPU only."""
+import math
+
+import numpy as np
+import pytest
+import scipy.integrate as si
+import scipy.special as sp
+import scipy.stats as st
+
+
+def _spec(oracle, seed=5):
+    return oracle.qmc(1024, 8, 119, seed)
+
+
+def _rand_spd(rng, p, jitter=0.5):
+    A = rng.standard_normal((p, p))
+    return A @ A.T / p + jitter * np.eye(p)
+
+
+@pytest.mark.parametrize("q", [1, 2, 3, 4])
+def test_delta_zero_is_multivariate_t(oracle, q):
+    # Sec. 2: Delta = 0 reduces eq (4) to the multivariate t density (3)
+    rng = np.random.default_rng(10 + q)
+    p = 4
+    S = _rand_spd(rng, p)
+    mu = rng.normal(0, 1, p)
+    nu = 5.7
+    for _ in range(3):
+        y = mu + rng.normal(0, 2, p)
+        r = oracle.pair(y, mu, S, np.zeros((p, q)), nu, _spec(oracle))
+        ref = st.multivariate_t(loc=mu, shape=S, df=nu).logpdf(y)
+        assert abs(r["logf"] - ref) < 1e-12 * max(1.0, abs(ref))
+        # E-step quantities with Delta = 0 have closed forms: u = (nu+p)/(nu+d),
+        # elogu = psi((nu+p)/2) - log((nu+d)/2) (the one-step-late term cancels),
+        # U is the positive part of a spherical t, so with m = nu+p+2 and
+        # s^2 = (nu+d)/m: E[W U_r] = u s 2 sqrt(m) G((m+1)/2) / (sqrt(pi) (m-1) G(m/2))
+        # and E[W U U^T] = I + (2/pi)(1 1^T - I).
+        d = float((y - mu) @ np.linalg.solve(S, y - mu))
+        u = (nu + p) / (nu + d)
+        assert abs(r["u"] - u) < 1e-12 * u
+        el = sp.digamma((nu + p) / 2) - math.log((nu + d) / 2)
+        assert abs(r["elogu"] - el) < 1e-12 * max(1.0, abs(el))
+        m = nu + p + 2
+        s = math.sqrt((nu + d) / m)
+        e1 = u * s * 2 * math.sqrt(m) * math.exp(sp.gammaln((m + 1) / 2) - sp.gammaln(m / 2)) \
+            / (math.sqrt(math.pi) * (m - 1))
+        assert np.allclose(r["eu"], e1, rtol=1e-10, atol=0)
+        E2 = np.eye(q) + (2 / math.pi) * (np.ones((q, q)) - np.eye(q))
+        assert np.allclose(r["euu"], E2, rtol=1e-10, atol=1e-12)
+
+
+def test_univariate_matches_hierarchy_integral(oracle):
+    # p = q = 1: f(y) = int int N(y; mu + delta u, sigma^2/w) 2 N(u; 0, 1/w) 1(u>0)
+    #                     gamma(w; nu/2, nu/2) du dw   (eq 6), by 2-D quadrature
+    mu, sig2, delta, nu = 0.3, 1.7, 1.4, 6.5
+    for y in [-2.0, 0.9, 4.0]:
+        def integrand(u, w):
+            return (st.norm.pdf(y, mu + delta * u, math.sqrt(sig2 / w))
+                    * 2 * st.norm.pdf(u, 0, math.sqrt(1 / w))
+                    * st.gamma.pdf(w, nu / 2, scale=2 / nu))
+        ref, _ = si.dblquad(integrand, 0, np.inf, 0, np.inf, epsabs=1e-12, epsrel=1e-10)
+        r = oracle.pair([y], [mu], [[sig2]], [[delta]], nu, _spec(oracle))
+        assert abs(r["logf"] - math.log(ref)) < 1e-7
+
+
+@pytest.mark.parametrize("q", [1, 2])
+def test_density_integrates_to_one(oracle, q):
+    # int f(y) dy = 1 by tensor Gauss-Legendre after y = mu + s tan(theta)
+    p = 2
+    if q == 2:
+        Sigma = np.array([[1.0, 0.5], [0.5, 1.0]])
+        Delta = np.array([[1.0, 0.5], [0.0, 1.5]])
+    else:
+        Sigma = np.array([[1.0, 0.3], [0.3, 0.8]])
+        Delta = np.array([[1.2], [-0.7]])
+    mu = np.array([0.5, -0.2])
+    nu = 6.0
+    nq = 64
+    x, wts = np.polynomial.legendre.leggauss(nq)
+    th = x * math.pi / 2
+    wt = wts * math.pi / 2
+    sc = 3.0
+    Y = []
+    W = []
+    for i in range(nq):
+        for j in range(nq):
+            Y.append(mu + sc * np.array([math.tan(th[i]), math.tan(th[j])]))
+            W.append(wt[i] * wt[j] * sc * sc / (math.cos(th[i]) ** 2 * math.cos(th[j]) ** 2))
+    Y = np.array(Y)
+    params = dict(pi=[1.0], mu=[mu], Sigma=[Sigma], Delta=[Delta], nu=[nu])
+    e = oracle.estep(Y, params, _spec(oracle))
+    total = float(np.sum(np.exp(e["logf"][0]) * np.array(W)))
+    assert abs(total - 1.0) < 2e-5
+
+
+def test_skew_normal_limit(oracle):
+    # nu -> infinity: 2^q phi_p(y; mu, Omega) Phi_q(c; 0, Lambda), eq (5); gap ~ 1/nu
+    p, q = 2, 2
+    mu = np.array([0.2, -0.4])
+    Sigma = np.array([[1.0, 0.3], [0.3, 1.5]])
+    Delta = np.array([[0.8, -0.3], [0.2, 1.1]])
+    Om = Sigma + Delta @ Delta.T
+    Oi = np.linalg.inv(Om)
+    Lam = np.eye(q) - Delta.T @ Oi @ Delta
+    for y in [np.array([0.5, 0.5]), np.array([-1.0, 1.3])]:
+        c = Delta.T @ Oi @ (y - mu)
+        ref = (q * math.log(2) + st.multivariate_normal(mu, Om).logpdf(y)
+               + math.log(st.multivariate_normal(np.zeros(q), Lam).cdf(c)))
+        g3 = oracle.pair(y, mu, Sigma, Delta, 1e3, _spec(oracle))["logf"] - ref
+        g4 = oracle.pair(y, mu, Sigma, Delta, 1e4, _spec(oracle))["logf"] - ref
+        assert abs(g4) < 1e-3
+        assert abs(g3 / g4 - 10.0) < 0.6, (g3, g4)
+
+
+def _mc_moments(y, mu, Sigma, Delta, nu, n, seed):
+    """Importance sampling from the prior of eq (6): draw (W, U), weight by
+    N(y; mu + Delta U, Sigma/W); return estimates and batch standard errors."""
+    rng = np.random.default_rng(seed)
+    p, q = Delta.shape
+    Lc = np.linalg.cholesky(Sigma)
+    Li = np.linalg.inv(Lc)
+    ld = np.log(np.diag(Lc)).sum()
+    nb = 16
+    m = n // nb
+    rows = []
+    for _ in range(nb):
+        Wd = rng.gamma(nu / 2, 2 / nu, m)
+        U = np.abs(rng.standard_normal((m, q))) / np.sqrt(Wd)[:, None]
+        z = (y - mu - U @ Delta.T) @ Li.T
+        wt = np.exp(-0.5 * Wd * (z * z).sum(1) + 0.5 * p * np.log(Wd)
+                    - 0.5 * p * math.log(2 * math.pi) - ld)
+        f = wt.mean()
+        rows.append(np.concatenate([[f, (wt * Wd).mean() / f],
+                                    (wt * Wd) @ U / m / f,
+                                    (np.einsum("i,ij,ik->jk", wt * Wd, U, U) / m / f).ravel()]))
+    R = np.array(rows)
+    est = R.mean(0)
+    se = R.std(0, ddof=1) / math.sqrt(nb)
+    return est, se
+
+
+@pytest.mark.parametrize("case", ["p2q2", "p3q3", "p4q1"])
+def test_moments_brute_force(oracle, case):
+    rng = np.random.default_rng(20)
+    if case == "p2q2":
+        y, mu = np.array([5.5, 6.0]), np.array([4.0, 4.0])
+        Sigma = np.array([[1.0, 0.5], [0.5, 1.0]])
+        Delta = np.array([[1.0, 0.5], [0.0, 1.5]])
+        nu = 10.0
+    elif case == "p3q3":
+        y, mu = np.array([0.8, -0.3, 1.5]), np.zeros(3)
+        Sigma = _rand_spd(rng, 3)
+        Delta = rng.normal(0, 1, (3, 3))
+        nu = 6.3
+    else:
+        y, mu = np.array([1.0, 0.5, -0.2, 2.0]), np.zeros(4)
+        Sigma = _rand_spd(rng, 4)
+        Delta = rng.normal(0, 1.2, (4, 1))
+        nu = 5.0
+    q = Delta.shape[1]
+    r = oracle.pair(y, mu, Sigma, Delta, nu, _spec(oracle))
+    est, se = _mc_moments(y, mu, Sigma, Delta, nu, 3_200_000, 7)
+    got = np.concatenate([[math.exp(r["logf"]), r["u"]], r["eu"], r["euu"].ravel()])
+    z = np.abs(got - est) / np.maximum(se, 1e-12)
+    assert np.all(z < 5.0), (case, got, est, se)
+
+
+def test_estep_invariants(oracle):
+    from paper_1606_02054_gb300 import synth
+
+    w = synth.make_workload("flow_p4", n=60, with_init=False)
+    e = oracle.estep(w["y"], w["truth"], oracle.qmc(**w["qmc"]))
+    assert np.allclose(e["tau"].sum(0), 1.0, atol=1e-13)
+    assert np.all(e["tau"] >= 0) and np.all(e["u"] > 0)
+    g, n, q = e["eu"].shape
+    t = w["truth"]
+    checked = 0
+    for h in range(g):
+        Om = t["Sigma"][h] + t["Delta"][h] @ t["Delta"][h].T
+        ltp = st.multivariate_t(loc=t["mu"][h], shape=Om, df=t["nu"][h]).logpdf(w["y"])
+        alpha_s = np.exp(e["logf"][h] - q * math.log(2) - ltp)
+        for j in range(n):
+            E3 = e["euu"][h, j]
+            assert np.allclose(E3, E3.T, atol=1e-15)
+            # E[W] E[W U U^T] - E[W U] E[W U]^T is positive semidefinite.  The
+            # lattice estimate of T_q loses relative accuracy far in its tail,
+            # where the moment formulas cancel; check where it is accurate.
+            if e["se"][h, j] > 1e-3 * alpha_s[j]:
+                continue
+            checked += 1
+            C = e["u"][h, j] * E3 - np.outer(e["eu"][h, j], e["eu"][h, j])
+            assert np.linalg.eigvalsh(C).min() > -1e-6 * np.abs(C).max(), (h, j)
+    assert checked >= n // 2
+    # log-likelihood = sum_j log sum_h pi_h f_h (eq 27)
+    lse = sp.logsumexp(np.log(w["truth"]["pi"])[:, None] + e["logf"], axis=0).sum()
+    assert abs(e["loglik"] - lse) < 1e-9 * abs(lse)
