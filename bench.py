@@ -1,0 +1,331 @@
+"""Benchmark of the FM-CFUST EM hot path on GB300 (one JSON line on stdout).
+
+A step is one EM iteration (E-step over every observation-component pair with
+the tau-weighted sufficient statistics, then the M-step) over the whole
+synthetic workload `flow_p4`: p = q = g = 4 (the HSCT flow-cytometry shape),
+n = 200,000 observations drawn from the latent hierarchy of eq (6), T_4 and
+T_3 by the randomised lattice (1024 points x 8 shifts).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+  python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
+
+value: observation-component pairs per second of whole EM iterations, summed
+over ranks (each rank runs its own replica: weak scaling).  Inputs are
+resident in HBM; L2 (129 MB) is flushed before every timed step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "E-step obs·comp/s and EM iter/s: chosen form vs plain GPU at stated loglik err"
+UNIT = "obs·comp/s"
+# Executed warp instructions per lattice point of the FP32 integrator, per
+# dimension k, from the ncu capture in profiles/lattice_fp32_flow_p4.md
+# (smsp__inst_executed.sum / points).  None until measured.
+INSTR_PER_POINT = {3: None, 4: None}
+SM_COUNT = 152
+SCHEDULERS_PER_SM = 4
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], parts[5:9]):
+                if v.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _opts(cf, w, precision, profile=0, stream=None):
+    q = w["qmc"]
+    return cf.cfust_default_opts(precision=precision, qmc_points=q["npoints"],
+                                 qmc_shifts=q["nshifts"], qmc_korobov_a=q["korobov_a"],
+                                 seed=q["seed"], profile=profile,
+                                 cuda_stream=stream)
+
+
+def cpu_baseline(w, nsample, steps=1):
+    """The FP64 oracle, as it stands, on `nsample` observations of the workload."""
+    import oracle
+
+    sub = w["y"][:nsample]
+    spec = oracle.qmc(**w["qmc"])
+    cores = os.cpu_count() or 1
+    params = {k: np.array(v, dtype=float) for k, v in w["init"].items()}
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        e = oracle.estep(sub, params, spec, nthreads=cores)
+        params, _ = oracle.mstep(sub, e, params)
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": nsample * w["g"] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {nsample} of {w['n']} observations of {w['name']}, "
+                      f"E-step + M-step in FP64 on {cores} host threads, {steps} step(s)",
+            "ms_per_step": dt * 1e3}
+
+
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    nsample = args.ref_sample
+    per = []
+    for i in range(args.warmup + args.steps):
+        b = cpu_baseline(w, nsample, 1)
+        if i >= args.warmup:
+            per.append(b["ms_per_step"])
+    ms = float(np.mean(per))
+    value = nsample * w["g"] / (ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": w["name"], "n": w["n"], "p": w["p"], "q": w["q"], "g": w["g"],
+                       "qmc": f"{w['qmc']['npoints']}x{w['qmc']['nshifts']}",
+                       "sample_n": nsample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"first {nsample} observations per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--workload", default="flow_p4")
+    ap.add_argument("--n", type=int, default=None, help="override the workload size")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--ref-sample", type=int, default=160)
+    ap.add_argument("--cpu-sample", type=int, default=240)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_1606_02054_gb300 import synth
+
+    w = synth.make_workload(args.workload, n=args.n)
+    w["name"] = args.workload
+
+    if args.impl == "reference":
+        run_reference(args, w, rank, world)
+        return
+
+    import torch
+
+    # CPU baseline first (in-process OpenMP threads; no fork after CUDA init)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_sample, 1)
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1606_02054_gb300 import build
+
+    build.build()
+    import paper_1606_02054_gb300 as cf
+
+    prec = cf.CFUST_PREC_FP32 if args.precision == "fp32" else cf.CFUST_PREC_FP64
+    stream = torch.cuda.current_stream()
+    ctx = cf.cfust_create(w["p"], w["q"], w["g"], w["n"],
+                          _opts(cf, w, prec, profile=1, stream=stream.cuda_stream))
+    y_dev = torch.tensor(w["y"], dtype=torch.float64, device="cuda")
+    cf.cfust_set_data(ctx, y_dev)
+    cf.cfust_set_params(ctx, w["init"])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        L = cf.cfust_estep(ctx)
+        cf.cfust_mstep(ctx)
+        return L
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    cf.cfust_profile(ctx, reset=True)
+    n_launch0 = cf.cfust_launch_count(ctx)
+    clocks = Clocks(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    lls = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # evict L2 before each timed step
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lls.append(step())
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = cf.cfust_launch_count(ctx) - n_launch0
+    prof = cf.cfust_profile(ctx)
+    ms = total_ms / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    pairs = w["n"] * w["g"]
+    value = pairs * world / (ms / 1e3)
+
+    # dominant kernel class and its roofline
+    lat_classes = [k for k in ("level0_Tq", "level1_Tq-1", "level2_Tq-2") if prof[k][1] > 0]
+    dom = max(lat_classes, key=lambda k: prof[k][0])
+    dom_ms_per_launch = prof[dom][0] / prof[dom][1]
+    kdim = {"level0_Tq": w["q"], "level1_Tq-1": w["q"] - 1, "level2_Tq-2": w["q"] - 2}[dom]
+    mult = {"level0_Tq": 2, "level1_Tq-1": w["q"], "level2_Tq-2": w["q"] * (w["q"] - 1)}[dom]
+    points = pairs * mult * w["qmc"]["npoints"] * w["qmc"]["nshifts"]
+    f_sm = (clk.get("sm_mhz") or _peaks().get("sm_max_mhz", 2070.0)) * 1e6
+    ipp = INSTR_PER_POINT.get(kdim) if kdim >= 3 and args.precision == "fp32" else None
+    if ipp:
+        achieved = ipp * points / (dom_ms_per_launch / 1e3) / 1e9
+        peak = SM_COUNT * SCHEDULERS_PER_SM * f_sm / 1e9
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "Gwarp-inst/s", "frac": achieved / peak, "traffic": None,
+                "kernel": dom, "k": kdim, "points_per_launch": points,
+                "ms_per_launch": dom_ms_per_launch,
+                "peak_basis": "152 SMs x 4 schedulers x 1 warp-instruction/clock at the sampled SM clock"}
+    else:
+        roof = {"bound": "alu", "achieved": points / (dom_ms_per_launch / 1e3) / 1e9,
+                "peak": None, "unit": "Gpoints/s", "frac": None, "traffic": None, "kernel": dom,
+                "k": kdim, "points_per_launch": points, "ms_per_launch": dom_ms_per_launch}
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        p, q, g = w["p"], w["q"], w["g"]
+        ctx2 = cf.cfust_create(p, q, g, w["n"], _opts(cf, w, prec, stream=stream.cuda_stream))
+        y_host = np.ascontiguousarray(w["y"])
+        params = {k: np.array(v, dtype=float) for k, v in w["init"].items()}
+        pbytes = 8 * (g + g * p + g * p * p + g * p * q + g)
+
+        def e2e_step(params):
+            cf.cfust_set_data(ctx2, y_host)
+            cf.cfust_set_params(ctx2, params)
+            cf.cfust_estep(ctx2)
+            cf.cfust_mstep(ctx2)
+            return cf.cfust_get_params(ctx2)
+
+        for _ in range(max(1, args.warmup)):
+            params = e2e_step(params)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            params = e2e_step(params)
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        if dist:
+            t = torch.tensor([e2e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": pairs * world / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(y_host.nbytes + pbytes),
+               "d2h_bytes_per_step": int(pbytes + 8 + 4 + 4 * g), "ms_per_step": e2e_ms}
+
+    if rank == 0:
+        estep_ms = sum(prof[k][0] for k in prof if k != "mstep") / args.steps
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+                "config": {"workload": w["name"], "n": w["n"], "p": w["p"], "q": w["q"],
+                           "g": w["g"], "qmc": f"{w['qmc']['npoints']}x{w['qmc']['nshifts']}",
+                           "precision": f"{args.precision} lattice/quadrature integrals, "
+                                        "fp64 whitening, densities, tau, loglik, statistics, M-step",
+                           "l2": "flushed (256 MB write) before every timed step",
+                           "parallelism": f"replicas x{world}"},
+                "em_iter_per_s": 1e3 / ms,
+                "estep_obs_comp_per_s": pairs * world / (estep_ms / 1e3),
+                "loglik_last": lls[-1],
+                "gpu_launches": int(launches),
+                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+                "roofline": roof, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

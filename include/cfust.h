@@ -1,0 +1,196 @@
+/*
+ * cfust.h -- C ABI of the GB300 (sm_103a) FM-CFUST EM library.
+ *
+ * The library runs the data-parallel hot path of the EM algorithm for finite
+ * mixtures of canonical fundamental skew t (CFUST) distributions of
+ * Lee, Leemaqz & McLachlan, "A simple multithreaded implementation of the EM
+ * algorithm for mixture models" (arXiv:1606.02054), on one GPU:
+ *
+ *   E-step over every (observation j, component h) pair     Sec. 3.1, eqs (12)-(17)
+ *     CFUST density                                         Sec. 2, eq (4)
+ *     weighted sufficient statistics of the M-step          Sec. 3.2, eqs (18)-(22)
+ *   M-step solve                                            Sec. 3.2, eqs (18)-(22)
+ *   log-likelihood, fused into the E-step pass              Sec. 4.3, eq (27)
+ *   Aitken stopping rule                                    Sec. 3.4, eqs (24)-(26)
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns a cfust_status and never aborts.  On failure,
+ *     cfust_last_error() gives a one-line reason (naming the component for
+ *     CFUST_ENOTPD / CFUST_EEMPTY / CFUST_ENUROOT).
+ *   - Parameters follow the paper's parameterisation exactly: pi (g),
+ *     mu (g x p), Sigma (g x p x p), Delta (g x p x q), nu (g), all FP64,
+ *     row-major, caller-owned.  They are copied in and out; the library keeps
+ *     its own device copy.
+ *   - A context is used from one host thread at a time.  All device work is
+ *     issued on opts.cuda_stream (NULL = the legacy default stream).
+ *   - There is no CPU fallback: without a usable CUDA device every call that
+ *     needs one returns CFUST_ECUDA.
+ */
+#ifndef CFUST_H
+#define CFUST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cfust_ctx cfust_ctx; /* opaque; owned by the library */
+
+typedef enum {
+    CFUST_OK = 0,
+    CFUST_EINVAL = 1,   /* bad argument (sizes, NULL pointer, option range) */
+    CFUST_ENOTPD = 2,   /* Sigma, Omega = Sigma + Delta Delta^T, Lambda or sum tau e3 not positive definite */
+    CFUST_EEMPTY = 3,   /* a component's sum of tau is not positive (eq 18) */
+    CFUST_ENUROOT = 4,  /* eq (22) has no root in [nu_min, nu_max]; nu clamped to the bound */
+    CFUST_ENAN = 5,     /* a non-finite log-likelihood or statistic */
+    CFUST_ETIMEOUT = 6, /* a bounded device wait gave up */
+    CFUST_ECUDA = 7,    /* CUDA runtime error (message in cfust_last_error) */
+    CFUST_ENOMEM = 8,   /* device or host allocation failed */
+    CFUST_ESTATE = 9    /* call out of order (e.g. estep before set_data/set_params) */
+} cfust_status;
+
+/* Arithmetic of the E-step integrals (the T_q terms of eqs (4), (13) and the
+ * truncated-t moments of eqs (16)-(17)).  Whitening, log t_p, the
+ * log-sum-exp of eq (12), the log-likelihood of eq (27), every sufficient
+ * statistic and the M-step stay FP64 in both modes. */
+enum { CFUST_PREC_FP64 = 0, CFUST_PREC_FP32 = 1 };
+
+/* Element type of the observation matrix passed to cfust_set_data. */
+enum { CFUST_F32 = 0, CFUST_F64 = 1 };
+
+typedef struct {
+    int precision;       /* CFUST_PREC_FP64 (default) or CFUST_PREC_FP32 */
+    int qmc_points;      /* N: points of the rank-1 Korobov lattice for T_k, k >= 3 (default 1024) */
+    int qmc_shifts;      /* M: random shifts of the lattice, 2..64 (default 8) */
+    int qmc_korobov_a;   /* Korobov generator a: z_d = a^d mod N (default 119) */
+    uint64_t seed;       /* key of the SplitMix64 shifts: shift(m,d) = u01(seed ^ (m+1)<<32 ^ (d+1)) */
+    double nu_min;       /* bracket of the eq (22) root (default 1) */
+    double nu_max;       /* (default 200) */
+    int device;          /* CUDA device ordinal (default 0) */
+    void* cuda_stream;   /* cudaStream_t to issue work on (default NULL) */
+    int t2_nodes;        /* Gauss-Legendre nodes per piece of the T_2 quadrature, 8..64
+                            (0: 64 in FP64 mode, 32 in FP32 mode) */
+    int profile;         /* 1: time every kernel class with CUDA events on the context
+                            stream (read with cfust_profile); 0 (default): off */
+} cfust_opts;
+
+/* Kernel classes reported by cfust_profile. */
+enum {
+    CFUST_PROF_SETUP = 0,   /* per-component factors (defs under eq 4) */
+    CFUST_PROF_CHI,         /* chi table of the lattice integrator */
+    CFUST_PROF_PLAN,        /* whitening, log t_p, integral limits */
+    CFUST_PROF_LEVEL0,      /* T_q of eqs (4) and (13) */
+    CFUST_PROF_LEVEL1,      /* T_{q-1} of the truncated-t first moments */
+    CFUST_PROF_LEVEL2,      /* T_{q-2} of the truncated-t second moments */
+    CFUST_PROF_COMBINE,     /* eqs (4), (13), (15)-(17) from the integrals */
+    CFUST_PROF_FIXUP,       /* FP64 re-evaluation of far-tail pairs (FP32 mode) */
+    CFUST_PROF_REDUCE,      /* eqs (12), (27) and the tau-weighted statistics */
+    CFUST_PROF_MSTEP,       /* eqs (18)-(22) */
+    CFUST_NPROF
+};
+
+/* Caller-owned parameter buffers (host memory), sizes as above. */
+typedef struct {
+    double* pi;     /* g */
+    double* mu;     /* g * p */
+    double* Sigma;  /* g * p * p */
+    double* Delta;  /* g * p * q */
+    double* nu;     /* g */
+} cfust_params;
+
+/* Fill *opts with the defaults listed above. */
+void cfust_default_opts(cfust_opts* opts);
+
+/* Create a context for n observations of dimension p, q latent skewing
+ * variables and g components (Sec. 2: p-variate CFUST with p x q Delta).
+ * Limits: 1 <= p <= 32, 1 <= q <= 8, 1 <= g <= 16, 1 <= n < 2^31.
+ * opts may be NULL (defaults).  Allocates every device buffer the E- and
+ * M-steps need; *out receives the context or NULL on failure. */
+cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64_t n, const cfust_opts* opts);
+
+/* Release a context and all its device memory.  NULL is accepted. */
+cfust_status cfust_destroy(cfust_ctx* ctx);
+
+/* Observations y_j (Sec. 2), row j at y + j*ld elements, p used per row.
+ * dtype CFUST_F64 or CFUST_F32 (FP32 rows are widened to FP64 on the device).
+ * on_device = 1: y is a device pointer on ctx's device (e.g. a torch
+ * tensor's data_ptr), read on the context stream; 0: host memory, copied.
+ * The data are copied; the caller keeps ownership of y. */
+cfust_status cfust_set_data(cfust_ctx* ctx, const void* y, int dtype, int64_t ld, int on_device);
+
+/* Copy Psi = (pi, mu, Sigma, Delta, nu) in (Sec. 2, eq (1)).  Returns
+ * CFUST_EINVAL if a pi is not in (0, 1], a nu not in [nu_min, nu_max], or a
+ * non-finite value is present. */
+cfust_status cfust_set_params(cfust_ctx* ctx, const cfust_params* params);
+
+/* Copy the current Psi out into caller buffers. */
+cfust_status cfust_get_params(cfust_ctx* ctx, cfust_params* out);
+
+/* One E-step at the current Psi^(k): eqs (4), (12)-(17) for every pair and
+ * the tau-weighted sufficient statistics of eqs (18)-(22).  *loglik_out
+ * (may be NULL) receives l(Psi^(k)) of eq (27), computed from the same
+ * density pass (Sec. 4.3).  The statistics stay on the device for
+ * cfust_mstep. */
+cfust_status cfust_estep(cfust_ctx* ctx, double* loglik_out);
+
+/* Copy the per-pair E-step arrays of the last cfust_estep to host buffers
+ * (any pointer may be NULL).  Layout component-major, index h*n + j:
+ * logf = log f_h(y_j) (eq 4); tau (eq 12); u (eq 13); elogu (eq 15);
+ * eu (q per pair, eq 16); euu (q x q per pair, eq 17); se = standard error
+ * of the lattice estimate of the T_q factor of eq (4) (0 when q <= 2). */
+cfust_status cfust_get_pairs(cfust_ctx* ctx, double* logf, double* tau, double* u,
+                             double* elogu, double* eu, double* euu, double* se);
+
+/* Copy the reduced sufficient statistics of the last E-step, per component h
+ * (stride 3 + p + q + p*q + q*q + p*p doubles): N = sum tau, U = sum tau u,
+ * Snu = sum tau (elogu - u), Sr = sum tau u r (p), Se = sum tau eu (q),
+ * Sre = sum tau r eu^T (p x q), See = sum tau euu (q x q),
+ * Srr = sum tau u r r^T (p x p), with r = y_j - mu_h^(k). */
+cfust_status cfust_get_stats(cfust_ctx* ctx, double* stats);
+
+/* M-step (eqs 18-22, in the order pi, mu, Delta, Sigma, nu) from the
+ * statistics of the last E-step; Psi^(k+1) replaces Psi^(k) on the device.
+ * On CFUST_EEMPTY / CFUST_ENOTPD the parameters are left unchanged.
+ * CFUST_ENUROOT is reported after the update, with nu clamped. */
+cfust_status cfust_mstep(cfust_ctx* ctx);
+
+/* Log-likelihood (eq 27) at the current Psi: a density-only pass (one T_q
+ * per pair, no moments). */
+cfust_status cfust_loglik(cfust_ctx* ctx, double* out);
+
+/* EM fit from the current Psi (Sec. 3): iteration k runs the E-step at
+ * Psi^(k) (giving l(Psi^(k)), Sec. 4.3) then the M-step.  With tol > 0 the
+ * Aitken rule (eqs 24-26) stops after the E-step whose l satisfies it;
+ * otherwise exactly max_iter M-steps run and one density pass gives
+ * l(Psi^(max_iter)).  loglik_hist (may be NULL) receives iters+1 values
+ * l(Psi^(0..iters)); *iters_out the number of M-steps run. */
+cfust_status cfust_fit(cfust_ctx* ctx, int max_iter, double tol, int* iters_out,
+                       double* loglik_hist);
+
+/* Evaluate T_k(b; 0, V, nu) for `count` independent cases with the
+ * library's device integrators (k <= 2 deterministic, k >= 3 lattice), host
+ * buffers: b (count x k), V (count x k x k scale matrices), nu (count);
+ * out (count), se (count, may be NULL).  Uses opts of ctx (precision,
+ * lattice, seed); ctx may be created with any n >= 1. */
+cfust_status cfust_tk_eval(cfust_ctx* ctx, int k, int count, const double* b, const double* V,
+                           const double* nu, double* out, double* se);
+
+/* Last error message of ctx (or of the last failed cfust_create when ctx is
+ * NULL).  Valid until the next call on the same context. */
+const char* cfust_last_error(const cfust_ctx* ctx);
+
+/* Number of kernels the library has launched on ctx since creation (for
+ * launch accounting in benchmarks). */
+int64_t cfust_launch_count(const cfust_ctx* ctx);
+
+/* Accumulated device time (ms, CUDA events) and launch count of each kernel
+ * class since creation or the last reset; arrays of CFUST_NPROF entries (either
+ * may be NULL).  Requires opts.profile = 1 (else CFUST_ESTATE).  reset = 1
+ * zeroes the totals after reading. */
+cfust_status cfust_profile(cfust_ctx* ctx, double* ms, int64_t* launches, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

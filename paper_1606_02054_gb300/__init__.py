@@ -1,0 +1,270 @@
+"""GB300 (sm_103a) FM-CFUST EM hot path: Python binding of include/cfust.h.
+
+The functions below carry the C names and only marshal arguments (numpy
+arrays or torch tensors in, numpy arrays out); every step of the E- and
+M-steps runs in the CUDA library ``libcfust.so`` built by ``build.py``.
+There is no CPU fallback: if the library is missing or no GPU is usable the
+calls raise ``CfustError``.
+
+Paper: Lee, Leemaqz & McLachlan, "A simple multithreaded implementation of
+the EM algorithm for mixture models" (arXiv:1606.02054), Secs. 2-4.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcfust.so")
+
+# cfust_status
+CFUST_OK, CFUST_EINVAL, CFUST_ENOTPD, CFUST_EEMPTY, CFUST_ENUROOT = 0, 1, 2, 3, 4
+CFUST_ENAN, CFUST_ETIMEOUT, CFUST_ECUDA, CFUST_ENOMEM, CFUST_ESTATE = 5, 6, 7, 8, 9
+STATUS_NAMES = {0: "CFUST_OK", 1: "CFUST_EINVAL", 2: "CFUST_ENOTPD", 3: "CFUST_EEMPTY",
+                4: "CFUST_ENUROOT", 5: "CFUST_ENAN", 6: "CFUST_ETIMEOUT", 7: "CFUST_ECUDA",
+                8: "CFUST_ENOMEM", 9: "CFUST_ESTATE"}
+CFUST_PREC_FP64, CFUST_PREC_FP32 = 0, 1
+CFUST_F32, CFUST_F64 = 0, 1
+# kernel classes of cfust_profile
+PROF_NAMES = ("setup", "chi_table", "plan", "level0_Tq", "level1_Tq-1", "level2_Tq-2",
+              "combine", "fixup_fp64", "reduce", "mstep")
+CFUST_NPROF = len(PROF_NAMES)
+
+
+class CfustError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class cfust_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("qmc_points", C.c_int), ("qmc_shifts", C.c_int),
+                ("qmc_korobov_a", C.c_int), ("seed", C.c_uint64), ("nu_min", C.c_double),
+                ("nu_max", C.c_double), ("device", C.c_int), ("cuda_stream", C.c_void_p),
+                ("t2_nodes", C.c_int), ("profile", C.c_int)]
+
+
+class cfust_params(C.Structure):
+    _fields_ = [("pi", C.POINTER(C.c_double)), ("mu", C.POINTER(C.c_double)),
+                ("Sigma", C.POINTER(C.c_double)), ("Delta", C.POINTER(C.c_double)),
+                ("nu", C.POINTER(C.c_double))]
+
+
+_lock = threading.Lock()
+_lib = None
+_dp = C.POINTER(C.c_double)
+
+
+def lib():
+    """Load libcfust.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise CfustError(CFUST_ECUDA, f"{LIB_PATH} is missing; build it with "
+                                 "`python -m paper_1606_02054_gb300.build`")
+            L = C.CDLL(LIB_PATH)
+            vp, i, d, i64 = C.c_void_p, C.c_int, C.c_double, C.c_int64
+            L.cfust_default_opts.argtypes = [C.POINTER(cfust_opts)]
+            L.cfust_default_opts.restype = None
+            L.cfust_create.argtypes = [C.POINTER(vp), i, i, i, i64, C.POINTER(cfust_opts)]
+            L.cfust_destroy.argtypes = [vp]
+            L.cfust_set_data.argtypes = [vp, vp, i, i64, i]
+            L.cfust_set_params.argtypes = [vp, C.POINTER(cfust_params)]
+            L.cfust_get_params.argtypes = [vp, C.POINTER(cfust_params)]
+            L.cfust_estep.argtypes = [vp, _dp]
+            L.cfust_get_pairs.argtypes = [vp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+            L.cfust_get_stats.argtypes = [vp, _dp]
+            L.cfust_mstep.argtypes = [vp]
+            L.cfust_loglik.argtypes = [vp, _dp]
+            L.cfust_fit.argtypes = [vp, i, d, C.POINTER(i), _dp]
+            L.cfust_tk_eval.argtypes = [vp, i, i, _dp, _dp, _dp, _dp, _dp]
+            L.cfust_last_error.argtypes = [vp]
+            L.cfust_last_error.restype = C.c_char_p
+            L.cfust_launch_count.argtypes = [vp]
+            L.cfust_launch_count.restype = i64
+            L.cfust_profile.argtypes = [vp, _dp, C.POINTER(C.c_int64), i]
+            L.cfust_profile.restype = i
+            for name in ("cfust_create", "cfust_destroy", "cfust_set_data", "cfust_set_params",
+                         "cfust_get_params", "cfust_estep", "cfust_get_pairs", "cfust_get_stats",
+                         "cfust_mstep", "cfust_loglik", "cfust_fit", "cfust_tk_eval"):
+                getattr(L, name).restype = i
+            _lib = L
+    return _lib
+
+
+def _check(status, ctx=None, allow=()):
+    if status != CFUST_OK and status not in allow:
+        raise CfustError(status, cfust_last_error(ctx))
+    return status
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Context:
+    """Owns one cfust_ctx (destroyed with the object)."""
+
+    def __init__(self, handle, p, q, g, n):
+        self.handle, self.p, self.q, self.g, self.n = handle, p, q, g, n
+
+    @property
+    def _as_parameter_(self):
+        return self.handle
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.cfust_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# the ABI, one function per C entry point
+# ---------------------------------------------------------------------------
+def cfust_default_opts(**overrides) -> cfust_opts:
+    o = cfust_opts()
+    lib().cfust_default_opts(C.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def cfust_create(p, q, g, n, opts: cfust_opts | None = None) -> Context:
+    h = C.c_void_p()
+    st = lib().cfust_create(C.byref(h), int(p), int(q), int(g), int(n),
+                            None if opts is None else C.byref(opts))
+    _check(st, None)
+    return Context(h.value, int(p), int(q), int(g), int(n))
+
+
+def cfust_destroy(ctx: Context):
+    h, ctx.handle = ctx.handle, None
+    return _check(lib().cfust_destroy(h))
+
+
+def cfust_set_data(ctx: Context, y):
+    """y: (n, p) numpy array (host) or torch tensor (host or device), f32 or f64."""
+    try:
+        import torch
+        is_t = isinstance(y, torch.Tensor)
+    except ImportError:  # pragma: no cover
+        is_t = False
+    if is_t:
+        if y.dim() != 2 or y.shape[0] != ctx.n or y.shape[1] != ctx.p or y.stride(1) != 1:
+            raise CfustError(CFUST_EINVAL, "y must be (n, p) with unit column stride")
+        dt = {torch.float32: CFUST_F32, torch.float64: CFUST_F64}.get(y.dtype)
+        if dt is None:
+            raise CfustError(CFUST_EINVAL, "y must be float32 or float64")
+        st = lib().cfust_set_data(ctx.handle, C.c_void_p(y.data_ptr()), dt, int(y.stride(0)),
+                                  int(y.is_cuda))
+        return _check(st, ctx)
+    y = np.asarray(y)
+    if y.dtype == np.float32:
+        yy, dt = np.ascontiguousarray(y), CFUST_F32
+    else:
+        yy, dt = _f64(y), CFUST_F64
+    if yy.shape != (ctx.n, ctx.p):
+        raise CfustError(CFUST_EINVAL, f"y must have shape {(ctx.n, ctx.p)}")
+    return _check(lib().cfust_set_data(ctx.handle, yy.ctypes.data_as(C.c_void_p), dt, ctx.p, 0), ctx)
+
+
+def cfust_set_params(ctx: Context, params):
+    arrs = [_f64(params[k]).ravel() for k in ("pi", "mu", "Sigma", "Delta", "nu")]
+    P = cfust_params(*[_ptr(a) for a in arrs])
+    return _check(lib().cfust_set_params(ctx.handle, C.byref(P)), ctx)
+
+
+def cfust_get_params(ctx: Context):
+    p, q, g = ctx.p, ctx.q, ctx.g
+    out = dict(pi=np.zeros(g), mu=np.zeros((g, p)), Sigma=np.zeros((g, p, p)),
+               Delta=np.zeros((g, p, q)), nu=np.zeros(g))
+    P = cfust_params(*[_ptr(out[k]) for k in ("pi", "mu", "Sigma", "Delta", "nu")])
+    _check(lib().cfust_get_params(ctx.handle, C.byref(P)), ctx)
+    return out
+
+
+def cfust_estep(ctx: Context) -> float:
+    L = C.c_double()
+    _check(lib().cfust_estep(ctx.handle, C.byref(L)), ctx)
+    return L.value
+
+
+def cfust_get_pairs(ctx: Context):
+    g, n, q = ctx.g, ctx.n, ctx.q
+    out = dict(logf=np.zeros((g, n)), tau=np.zeros((g, n)), u=np.zeros((g, n)),
+               elogu=np.zeros((g, n)), eu=np.zeros((g, n, q)), euu=np.zeros((g, n, q, q)),
+               se=np.zeros((g, n)))
+    _check(lib().cfust_get_pairs(ctx.handle, *[_ptr(out[k]) for k in
+                                               ("logf", "tau", "u", "elogu", "eu", "euu", "se")]), ctx)
+    return out
+
+
+def cfust_get_stats(ctx: Context):
+    p, q = ctx.p, ctx.q
+    S = 3 + p + q + p * q + q * q + p * p
+    out = np.zeros(ctx.g * S)
+    _check(lib().cfust_get_stats(ctx.handle, _ptr(out)), ctx)
+    return out.reshape(ctx.g, S)
+
+
+def cfust_mstep(ctx: Context) -> int:
+    """Returns CFUST_OK or CFUST_ENUROOT (nu clamped); raises on other errors."""
+    return _check(lib().cfust_mstep(ctx.handle), ctx, allow=(CFUST_ENUROOT,))
+
+
+def cfust_loglik(ctx: Context) -> float:
+    L = C.c_double()
+    _check(lib().cfust_loglik(ctx.handle, C.byref(L)), ctx)
+    return L.value
+
+
+def cfust_fit(ctx: Context, max_iter, tol=0.0):
+    """Returns (iterations, log-likelihood history l(Psi^(0..iterations)))."""
+    hist = np.full(int(max_iter) + 1, np.nan)
+    it = C.c_int(0)
+    _check(lib().cfust_fit(ctx.handle, int(max_iter), float(tol), C.byref(it), _ptr(hist)), ctx)
+    return it.value, hist[: it.value + 1]
+
+
+def cfust_tk_eval(ctx: Context, b, V, nu):
+    """T_k(b; 0, V, nu) per case: b (count, k), V (count, k, k), nu (count)."""
+    b = _f64(b)
+    count, k = b.shape
+    V = _f64(V).reshape(count, k, k)
+    nu = _f64(nu).reshape(count)
+    out, se = np.zeros(count), np.zeros(count)
+    _check(lib().cfust_tk_eval(ctx.handle, k, count, _ptr(b), _ptr(V), _ptr(nu), _ptr(out),
+                               _ptr(se)), ctx)
+    return out, se
+
+
+def cfust_last_error(ctx: Context | None = None) -> str:
+    h = None if ctx is None else (ctx.handle if isinstance(ctx, Context) else ctx)
+    msg = lib().cfust_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def cfust_launch_count(ctx: Context) -> int:
+    return int(lib().cfust_launch_count(ctx.handle))
+
+
+def cfust_profile(ctx: Context, reset=False):
+    """{class name: (ms, launches)} accumulated since creation or the last reset."""
+    ms = np.zeros(CFUST_NPROF)
+    n = np.zeros(CFUST_NPROF, dtype=np.int64)
+    _check(lib().cfust_profile(ctx.handle, _ptr(ms), n.ctypes.data_as(C.POINTER(C.c_int64)),
+                               int(bool(reset))), ctx)
+    return {PROF_NAMES[k]: (float(ms[k]), int(n[k])) for k in range(CFUST_NPROF)}
+
+
+def params_from_workload(params):
+    """Copy of a parameter dict as contiguous float64 arrays."""
+    return {k: _f64(params[k]).copy() for k in ("pi", "mu", "Sigma", "Delta", "nu")}

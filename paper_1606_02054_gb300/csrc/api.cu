@@ -1,0 +1,836 @@
+// api.cu -- the C ABI of include/cfust.h: context, device buffers, kernel
+// launches and the EM loop (Sec. 3; Aitken rule of Sec. 3.4, eqs (24)-(26)).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cfust.h"
+#include "internal.cuh"
+
+// kernels (defined in the other translation units)
+__global__ void setup_components_kernel(Dims, Layout, const double*, const double*, const double*,
+                                        const double*, double*, int*);
+__global__ void chi_table_kernel(int, const double*, Lattice, const double*, double*, float*);
+__global__ void estep_dofs_kernel(Dims, Layout, const double*, double*);
+__global__ void widen_kernel(const float*, long long, Dims, double*);
+
+
+__global__ void estep_reduce_kernel(ReduceArgs);
+__global__ void reduce_partials_kernel(const double*, int, int, double*, int*);
+__global__ void loglik_partial_kernel(Dims, const double*, const double*, double*);
+__global__ void mstep_kernel(Dims, const double*, double, double, const double*, const double*,
+                             const double*, double*, double*, double*, double*, double*, int*, int*);
+
+struct cfust_ctx {
+    int p = 0, q = 0, g = 0;
+    long long n = 0;
+    cfust_opts opts{};
+    cudaStream_t st = nullptr;
+    Dims D{};
+    Layout Ly{};
+    Lattice lat{};
+    int t2n = 0;
+    int nsm = 0;
+    int chunk = 0, row = 0, nblocks_red = 0, nblocks_ll = 0;
+    // device buffers
+    double* y = nullptr;
+    double *pi = nullptr, *mu = nullptr, *Sigma = nullptr, *Delta = nullptr, *nu = nullptr;
+    double *pi_n = nullptr, *mu_n = nullptr, *Sigma_n = nullptr, *Delta_n = nullptr, *nu_n = nullptr;
+    double* F = nullptr;
+    double* dofs = nullptr;
+    double* chi64 = nullptr;
+    float* chi32 = nullptr;
+    double* shf64 = nullptr;
+    float* shf32 = nullptr;
+    double *glx64 = nullptr, *glw64 = nullptr;
+    float *glx32 = nullptr, *glw32 = nullptr;
+    double *logf = nullptr, *u = nullptr, *elogu = nullptr, *eu = nullptr, *euu = nullptr,
+           *se = nullptr, *tau = nullptr;
+    double *partial = nullptr, *stats = nullptr;
+    int *flags = nullptr, *comp_status = nullptr;
+    float* stage32 = nullptr;
+    // E-step pipeline: per-pair (d, log t_p) and c, integral records per level
+    double *pd = nullptr, *pc = nullptr;
+    RecSet rec[3]{};
+    int *fix_count = nullptr, *fix_list = nullptr;
+    // optional per-kernel-class timing (opts.profile)
+    cudaEvent_t ev[CFUST_NPROF][2]{};
+    bool pending[CFUST_NPROF]{};
+    double prof_ms[CFUST_NPROF]{};
+    long long prof_n[CFUST_NPROF]{};
+    // pinned host scratch
+    double* h_ll = nullptr;
+    int* h_flags = nullptr;
+    int* h_comp = nullptr;
+    bool have_data = false, have_params = false, have_stats = false;
+    long long launches = 0;
+    std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static cfust_status fail(cfust_ctx* c, cfust_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    else g_create_err = msg;
+    return s;
+}
+
+#define CU(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(c, CFUST_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define LAUNCHED()                                                                          \
+    do {                                                                                    \
+        c->launches++;                                                                      \
+        cudaError_t e_ = cudaGetLastError();                                                \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(c, CFUST_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+static cudaError_t dalloc(T** p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): one output from state = key, as a
+// double in [0, 1).
+static double splitmix_u01(uint64_t key)
+{
+    uint64_t z = key + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z = z ^ (z >> 31);
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// n-point Gauss-Legendre rule mapped to [0, 1] (Newton iteration on P_n).
+static void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w)
+{
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double t = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (t * p1 - p0) / (t * t - 1.0);
+            const double step = p1 / dp;
+            t -= step;
+            if (std::fabs(step) < 1e-16) {
+                // derivative at the converged node
+                p0 = 1.0; p1 = t;
+                for (int k = 2; k <= n; ++k) {
+                    const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+                    p0 = p1;
+                    p1 = p2;
+                }
+                dp = n * (t * p1 - p0) / (t * t - 1.0);
+                break;
+            }
+        }
+        x[i] = 0.5 * (t + 1.0);
+        w[i] = 1.0 / ((1.0 - t * t) * dp * dp);  // (2/((1-t^2) P'^2)) / 2
+    }
+}
+
+static cfust_status check_flags(cfust_ctx* c, int f, const char* where)
+{
+    if (f & (KF_NOTPD_OMEGA | KF_NOTPD_LAMBDA))
+        return fail(c, CFUST_ENOTPD, std::string(where) + ": Sigma, Omega or Lambda not positive definite");
+    if (f & KF_NAN) return fail(c, CFUST_ENAN, std::string(where) + ": non-finite density or statistic");
+    return CFUST_OK;
+}
+
+// kernel-class timing: events bracket each class on the context stream and
+// are read after the next stream synchronisation
+static void prof_begin(cfust_ctx* c, int k)
+{
+    if (c->opts.profile) cudaEventRecord(c->ev[k][0], c->st);
+}
+static void prof_end(cfust_ctx* c, int k, long long launches)
+{
+    c->prof_n[k] += launches;
+    if (!c->opts.profile) return;
+    cudaEventRecord(c->ev[k][1], c->st);
+    c->pending[k] = true;
+}
+static void prof_collect(cfust_ctx* c)
+{
+    if (!c->opts.profile) return;
+    for (int k = 0; k < CFUST_NPROF; ++k)
+        if (c->pending[k]) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c->ev[k][0], c->ev[k][1]) == cudaSuccess) c->prof_ms[k] += ms;
+            c->pending[k] = false;
+        }
+}
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" void cfust_default_opts(cfust_opts* o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = CFUST_PREC_FP64;
+    o->qmc_points = 1024;
+    o->qmc_shifts = 8;
+    o->qmc_korobov_a = 119;
+    o->seed = 0;
+    o->nu_min = 1.0;
+    o->nu_max = 200.0;
+    o->device = 0;
+    o->cuda_stream = nullptr;
+    o->t2_nodes = 0;
+}
+
+extern "C" const char* cfust_last_error(const cfust_ctx* c)
+{
+    return c ? c->err.c_str() : g_create_err.c_str();
+}
+
+extern "C" int64_t cfust_launch_count(const cfust_ctx* c) { return c ? c->launches : 0; }
+
+extern "C" cfust_status cfust_profile(cfust_ctx* c, double* ms, int64_t* launches, int reset)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_profile: ctx is NULL");
+    if (!c->opts.profile) return fail(c, CFUST_ESTATE, "cfust_profile: context created without opts.profile");
+    for (int k = 0; k < CFUST_NPROF; ++k) {
+        if (ms) ms[k] = c->prof_ms[k];
+        if (launches) launches[k] = c->prof_n[k];
+        if (reset) { c->prof_ms[k] = 0.0; c->prof_n[k] = 0; }
+    }
+    return CFUST_OK;
+}
+
+static void free_all(cfust_ctx* c)
+{
+    void* bufs[] = {c->y, c->pi, c->mu, c->Sigma, c->Delta, c->nu, c->pi_n, c->mu_n, c->Sigma_n,
+                    c->Delta_n, c->nu_n, c->F, c->dofs, c->chi64, c->chi32, c->shf64, c->shf32,
+                    c->glx64, c->glw64, c->glx32, c->glw32, c->logf, c->u, c->elogu, c->eu,
+                    c->euu, c->se, c->tau, c->partial, c->stats, c->flags, c->comp_status,
+                    c->stage32, c->pd, c->pc, c->fix_count, c->fix_list};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    for (RecSet& r : c->rec) {
+        void* rb[] = {r.bt, r.fac, r.tab, r.dof, r.res, r.se};
+        for (void* b : rb)
+            if (b) cudaFree(b);
+    }
+    for (int k = 0; k < CFUST_NPROF; ++k)
+        for (int i = 0; i < 2; ++i)
+            if (c->ev[k][i]) cudaEventDestroy(c->ev[k][i]);
+    if (c->h_ll) cudaFreeHost(c->h_ll);
+    if (c->h_flags) cudaFreeHost(c->h_flags);
+    if (c->h_comp) cudaFreeHost(c->h_comp);
+}
+
+extern "C" cfust_status cfust_destroy(cfust_ctx* c)
+{
+    if (!c) return CFUST_OK;
+    cudaSetDevice(c->opts.device);
+    if (c->st) cudaStreamSynchronize(c->st);
+    free_all(c);
+    delete c;
+    return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64_t n,
+                                     const cfust_opts* opts)
+{
+    cfust_ctx* c = nullptr;
+    if (!out) return fail(nullptr, CFUST_EINVAL, "cfust_create: out is NULL");
+    *out = nullptr;
+    if (p < 1 || p > CF_MAXP || q < 1 || q > CF_MAXQ || g < 1 || g > CF_MAXG || n < 1 ||
+        n >= (int64_t(1) << 31))
+        return fail(nullptr, CFUST_EINVAL, "cfust_create: sizes out of range (1<=p<=32, 1<=q<=8, 1<=g<=16, 1<=n<2^31)");
+    cfust_opts o;
+    cfust_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision != CFUST_PREC_FP64 && o.precision != CFUST_PREC_FP32)
+        return fail(nullptr, CFUST_EINVAL, "cfust_create: precision must be CFUST_PREC_FP64 or CFUST_PREC_FP32");
+    if (o.qmc_points < 32 || o.qmc_points > (1 << 20) || o.qmc_shifts < 2 ||
+        o.qmc_shifts > CF_MAXSHIFT || o.qmc_korobov_a < 1)
+        return fail(nullptr, CFUST_EINVAL, "cfust_create: lattice needs 32 <= N <= 2^20, 2 <= M <= 64, a >= 1");
+    if (!(o.nu_min > 0.0) || !(o.nu_max >= o.nu_min))
+        return fail(nullptr, CFUST_EINVAL, "cfust_create: need 0 < nu_min <= nu_max");
+    if (o.t2_nodes != 0 && (o.t2_nodes < 8 || o.t2_nodes > 64))
+        return fail(nullptr, CFUST_EINVAL, "cfust_create: t2_nodes must be 0 or in [8, 64]");
+    cudaError_t e = cudaSetDevice(o.device);
+    if (e != cudaSuccess)
+        return fail(nullptr, CFUST_ECUDA, std::string("cfust_create: cudaSetDevice: ") + cudaGetErrorString(e));
+
+    c = new cfust_ctx();
+    c->p = p; c->q = q; c->g = g; c->n = n;
+    c->opts = o;
+    c->st = (cudaStream_t)o.cuda_stream;
+    c->D = Dims{p, q, g, (long long)n};
+    c->Ly = make_layout(p, q);
+    c->lat.N = o.qmc_points;
+    c->lat.M = o.qmc_shifts;
+    {
+        long long z = 1;
+        for (int d = 0; d < CF_MAXDIM; ++d) {
+            c->lat.z[d] = (int)(z % o.qmc_points);
+            z = (z * o.qmc_korobov_a) % o.qmc_points;
+        }
+    }
+    c->t2n = o.t2_nodes ? o.t2_nodes : (o.precision == CFUST_PREC_FP64 ? 64 : 32);
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, o.device)) != cudaSuccess) {
+        cfust_status s = fail(nullptr, CFUST_ECUDA, std::string("cfust_create: ") + cudaGetErrorString(e));
+        delete c;
+        return s;
+    }
+    c->nsm = prop.multiProcessorCount;
+    const size_t ng = (size_t)n * g;
+    const int S = stats_per_comp(p, q);
+    // reduction staging: rows of 4 + p + q + q^2 doubles, chunk <= 256 observations,
+    // at most ~64 KB of shared memory
+    c->row = 4 + p + q + q * q;
+    int chunk = 256;
+    while (chunk > 32 && (size_t)chunk * (c->row + g + 1) * sizeof(double) > 64 * 1024) chunk -= 32;
+    c->chunk = chunk;
+    c->nblocks_red = (int)((n + chunk - 1) / chunk);
+    c->nblocks_ll = (int)((n + 255) / 256);
+    const size_t NM = (size_t)o.qmc_points * o.qmc_shifts;
+    const int ntab = q >= 3 ? 3 * g : 0;
+    const size_t part = (size_t)std::max(c->nblocks_red * (g * S + 1), c->nblocks_ll);
+
+#define ALLOC(ptr, cnt)                                                                      \
+    if ((e = dalloc(&c->ptr, (cnt))) != cudaSuccess) {                                       \
+        free_all(c);                                                                         \
+        delete c;                                                                            \
+        return fail(nullptr, CFUST_ENOMEM, std::string("cfust_create: cudaMalloc " #ptr ": ") + \
+                                               cudaGetErrorString(e));                       \
+    }
+    ALLOC(y, (size_t)n * p);
+    ALLOC(pi, g); ALLOC(mu, (size_t)g * p); ALLOC(Sigma, (size_t)g * p * p);
+    ALLOC(Delta, (size_t)g * p * q); ALLOC(nu, g);
+    ALLOC(pi_n, g); ALLOC(mu_n, (size_t)g * p); ALLOC(Sigma_n, (size_t)g * p * p);
+    ALLOC(Delta_n, (size_t)g * p * q); ALLOC(nu_n, g);
+    ALLOC(F, (size_t)g * c->Ly.stride);
+    ALLOC(dofs, 3 * g);
+    ALLOC(chi64, ntab * NM);
+    ALLOC(chi32, ntab * NM);
+    ALLOC(shf64, (size_t)o.qmc_shifts * CF_MAXDIM);
+    ALLOC(shf32, (size_t)o.qmc_shifts * CF_MAXDIM);
+    ALLOC(glx64, c->t2n); ALLOC(glw64, c->t2n); ALLOC(glx32, c->t2n); ALLOC(glw32, c->t2n);
+    ALLOC(logf, ng); ALLOC(u, ng); ALLOC(elogu, ng); ALLOC(se, ng); ALLOC(tau, ng);
+    ALLOC(eu, ng * q); ALLOC(euu, ng * q * q);
+    ALLOC(partial, part);
+    ALLOC(stats, (size_t)g * S + 1);
+    ALLOC(flags, 1); ALLOC(comp_status, g);
+    ALLOC(pd, 2 * ng); ALLOC(pc, ng * q);
+    ALLOC(fix_count, 1); ALLOC(fix_list, ng);
+    {
+        const int kdim[3] = {q, q - 1, q - 2};
+        const long long mult[3] = {2, q >= 2 ? q : 0, q >= 3 ? (long long)q * (q - 1) : 0};
+        for (int l = 0; l < 3; ++l) {
+            RecSet& r = c->rec[l];
+            r.k = kdim[l] > 0 ? kdim[l] : 0;
+            r.nrec = r.k > 0 ? (long long)ng * mult[l] : 0;
+            const size_t nr = (size_t)r.nrec;
+            ALLOC(rec[l].bt, nr * (r.k > 0 ? r.k : 1));
+            ALLOC(rec[l].fac, nr); ALLOC(rec[l].tab, nr);
+            ALLOC(rec[l].dof, nr); ALLOC(rec[l].res, nr);
+            if (l == 0) { ALLOC(rec[l].se, nr); }
+        }
+    }
+#undef ALLOC
+    if (cudaMallocHost((void**)&c->h_ll, sizeof(double) * 4) != cudaSuccess ||
+        cudaMallocHost((void**)&c->h_flags, sizeof(int) * 4) != cudaSuccess ||
+        cudaMallocHost((void**)&c->h_comp, sizeof(int) * CF_MAXG) != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return fail(nullptr, CFUST_ENOMEM, "cfust_create: cudaMallocHost failed");
+    }
+    // lattice shifts and Gauss-Legendre nodes
+    std::vector<double> s64((size_t)o.qmc_shifts * CF_MAXDIM);
+    std::vector<float> s32(s64.size());
+    for (int m = 0; m < o.qmc_shifts; ++m)
+        for (int d = 0; d < CF_MAXDIM; ++d) {
+            const uint64_t key = o.seed ^ ((uint64_t)(m + 1) << 32) ^ (uint64_t)(d + 1);
+            s64[m * CF_MAXDIM + d] = splitmix_u01(key);
+            s32[m * CF_MAXDIM + d] = (float)s64[m * CF_MAXDIM + d];
+            if (s32[m * CF_MAXDIM + d] >= 1.0f) s32[m * CF_MAXDIM + d] = 0.0f;
+        }
+    std::vector<double> gx, gw;
+    gauss_legendre01(c->t2n, gx, gw);
+    std::vector<float> gx32(gx.begin(), gx.end()), gw32(gw.begin(), gw.end());
+    cfust_status s = CFUST_OK;
+    auto cp = [&](void* dst, const void* src, size_t bytes) {
+        cudaError_t ee = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+        if (ee != cudaSuccess && s == CFUST_OK)
+            s = fail(nullptr, CFUST_ECUDA, std::string("cfust_create: cudaMemcpy: ") + cudaGetErrorString(ee));
+    };
+    cp(c->shf64, s64.data(), sizeof(double) * s64.size());
+    cp(c->shf32, s32.data(), sizeof(float) * s32.size());
+    cp(c->glx64, gx.data(), sizeof(double) * gx.size());
+    cp(c->glw64, gw.data(), sizeof(double) * gw.size());
+    cp(c->glx32, gx32.data(), sizeof(float) * gx32.size());
+    cp(c->glw32, gw32.data(), sizeof(float) * gw32.size());
+    if (s != CFUST_OK) {
+        free_all(c);
+        delete c;
+        return s;
+    }
+    cudaFuncSetAttribute(estep_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    if (o.profile)
+        for (int k = 0; k < CFUST_NPROF; ++k)
+            for (int i = 0; i < 2; ++i)
+                if (cudaEventCreate(&c->ev[k][i]) != cudaSuccess) {
+                    free_all(c);
+                    delete c;
+                    return fail(nullptr, CFUST_ECUDA, "cfust_create: cudaEventCreate failed");
+                }
+    *out = c;
+    return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_set_data(cfust_ctx* c, const void* y, int dtype, int64_t ld, int on_device)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_set_data: ctx is NULL");
+    if (!y || ld < c->p || (dtype != CFUST_F32 && dtype != CFUST_F64))
+        return fail(c, CFUST_EINVAL, "cfust_set_data: need y != NULL, ld >= p, dtype F32 or F64");
+    CU(cudaSetDevice(c->opts.device));
+    const size_t rows = (size_t)c->n, pitch = (size_t)c->p;
+    if (dtype == CFUST_F64) {
+        CU(cudaMemcpy2DAsync(c->y, pitch * sizeof(double), y, (size_t)ld * sizeof(double),
+                             pitch * sizeof(double), rows,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+    } else {
+        const float* src = (const float*)y;
+        if (!on_device) {
+            if (!c->stage32) CU(dalloc(&c->stage32, rows * pitch));
+            CU(cudaMemcpy2DAsync(c->stage32, pitch * sizeof(float), y, (size_t)ld * sizeof(float),
+                                 pitch * sizeof(float), rows, cudaMemcpyHostToDevice, c->st));
+            src = c->stage32;
+            ld = c->p;
+        }
+        const long long total = (long long)rows * pitch;
+        const int blocks = (int)std::min<long long>((total + 255) / 256, 4LL * c->nsm * 8);
+        widen_kernel<<<blocks, 256, 0, c->st>>>(src, ld, c->D, c->y);
+        LAUNCHED();
+    }
+    c->have_data = true;
+    c->have_stats = false;
+    return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_set_params(cfust_ctx* c, const cfust_params* P)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_set_params: ctx is NULL");
+    if (!P || !P->pi || !P->mu || !P->Sigma || !P->Delta || !P->nu)
+        return fail(c, CFUST_EINVAL, "cfust_set_params: NULL parameter buffer");
+    const int p = c->p, q = c->q, g = c->g;
+    for (int h = 0; h < g; ++h) {
+        if (!(P->pi[h] > 0.0 && P->pi[h] <= 1.0))
+            return fail(c, CFUST_EINVAL, "cfust_set_params: pi[" + std::to_string(h) + "] not in (0, 1]");
+        if (!(P->nu[h] >= c->opts.nu_min && P->nu[h] <= c->opts.nu_max))
+            return fail(c, CFUST_EINVAL, "cfust_set_params: nu[" + std::to_string(h) + "] outside [nu_min, nu_max]");
+    }
+    for (size_t i = 0; i < (size_t)g * p; ++i)
+        if (!std::isfinite(P->mu[i])) return fail(c, CFUST_EINVAL, "cfust_set_params: non-finite mu");
+    for (size_t i = 0; i < (size_t)g * p * p; ++i)
+        if (!std::isfinite(P->Sigma[i])) return fail(c, CFUST_EINVAL, "cfust_set_params: non-finite Sigma");
+    for (size_t i = 0; i < (size_t)g * p * q; ++i)
+        if (!std::isfinite(P->Delta[i])) return fail(c, CFUST_EINVAL, "cfust_set_params: non-finite Delta");
+    CU(cudaSetDevice(c->opts.device));
+    CU(cudaMemcpyAsync(c->pi, P->pi, sizeof(double) * g, cudaMemcpyHostToDevice, c->st));
+    CU(cudaMemcpyAsync(c->mu, P->mu, sizeof(double) * g * p, cudaMemcpyHostToDevice, c->st));
+    CU(cudaMemcpyAsync(c->Sigma, P->Sigma, sizeof(double) * g * p * p, cudaMemcpyHostToDevice, c->st));
+    CU(cudaMemcpyAsync(c->Delta, P->Delta, sizeof(double) * g * p * q, cudaMemcpyHostToDevice, c->st));
+    CU(cudaMemcpyAsync(c->nu, P->nu, sizeof(double) * g, cudaMemcpyHostToDevice, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    c->have_params = true;
+    c->have_stats = false;
+    return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_get_params(cfust_ctx* c, cfust_params* P)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_get_params: ctx is NULL");
+    if (!P || !P->pi || !P->mu || !P->Sigma || !P->Delta || !P->nu)
+        return fail(c, CFUST_EINVAL, "cfust_get_params: NULL parameter buffer");
+    if (!c->have_params) return fail(c, CFUST_ESTATE, "cfust_get_params: no parameters set");
+    const int p = c->p, q = c->q, g = c->g;
+    CU(cudaSetDevice(c->opts.device));
+    CU(cudaMemcpyAsync(P->pi, c->pi, sizeof(double) * g, cudaMemcpyDeviceToHost, c->st));
+    CU(cudaMemcpyAsync(P->mu, c->mu, sizeof(double) * g * p, cudaMemcpyDeviceToHost, c->st));
+    CU(cudaMemcpyAsync(P->Sigma, c->Sigma, sizeof(double) * g * p * p, cudaMemcpyDeviceToHost, c->st));
+    CU(cudaMemcpyAsync(P->Delta, c->Delta, sizeof(double) * g * p * q, cudaMemcpyDeviceToHost, c->st));
+    CU(cudaMemcpyAsync(P->nu, c->nu, sizeof(double) * g, cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    return CFUST_OK;
+}
+
+// S0 + S1: per-component factors and (q >= 3) the chi tables.
+static cfust_status launch_setup(cfust_ctx* c)
+{
+    prof_begin(c, CFUST_PROF_SETUP);
+    setup_components_kernel<<<1, 32, 0, c->st>>>(c->D, c->Ly, c->mu, c->Sigma, c->Delta, c->nu,
+                                                 c->F, c->flags);
+    LAUNCHED();
+    prof_end(c, CFUST_PROF_SETUP, 1);
+    if (c->q >= 3) {
+        prof_begin(c, CFUST_PROF_CHI);
+        estep_dofs_kernel<<<1, 64, 0, c->st>>>(c->D, c->Ly, c->F, c->dofs);
+        LAUNCHED();
+        const long long total = 3LL * c->g * c->lat.N * c->lat.M;
+        const int blocks = (int)std::min<long long>((total + 127) / 128, 64LL * c->nsm);
+        chi_table_kernel<<<blocks, 128, 0, c->st>>>(3 * c->g, c->dofs, c->lat, c->shf64, c->chi64,
+                                                     c->chi32);
+        LAUNCHED();
+        prof_end(c, CFUST_PROF_CHI, 2);
+    }
+    return CFUST_OK;
+}
+
+static IntegArgs integ_args(const cfust_ctx* c)
+{
+    IntegArgs ia;
+    ia.F = c->F; ia.lat = c->lat;
+    ia.chi64 = c->chi64; ia.chi32 = c->chi32; ia.shf64 = c->shf64; ia.shf32 = c->shf32;
+    ia.glx64 = c->glx64; ia.glw64 = c->glw64; ia.glx32 = c->glx32; ia.glw32 = c->glw32;
+    ia.t2n = c->t2n;
+    return ia;
+}
+
+// S2-S7: plan, integrals of each level, combine, FP64 fix-up of far-tail pairs.
+static cfust_status launch_pairs(cfust_ctx* c, int density_only)
+{
+    const int fp32 = c->opts.precision == CFUST_PREC_FP32;
+    PlanArgs pa;
+    pa.D = c->D; pa.Ly = c->Ly; pa.y = c->y; pa.F = c->F; pa.density_only = density_only;
+    pa.pd = c->pd; pa.pc = c->pc;
+    pa.L0 = c->rec[0]; pa.L1 = c->rec[1]; pa.L2 = c->rec[2];
+    if (density_only) pa.L0.nrec = c->n * c->g;
+    cudaError_t e;
+    long long n0 = c->launches;
+    prof_begin(c, CFUST_PROF_PLAN);
+    if ((e = launch_plan(pa, c->st, &c->launches)) != cudaSuccess)
+        return fail(c, CFUST_ECUDA, std::string("plan kernel: ") + cudaGetErrorString(e));
+    prof_end(c, CFUST_PROF_PLAN, c->launches - n0);
+    const IntegArgs ia = integ_args(c);
+    for (int l = 0; l < (density_only ? 1 : 3); ++l) {
+        RecSet r = l == 0 ? pa.L0 : c->rec[l];
+        n0 = c->launches;
+        prof_begin(c, CFUST_PROF_LEVEL0 + l);
+        if ((e = launch_integrals(r, ia, fp32, c->nsm, c->st, &c->launches)) != cudaSuccess)
+            return fail(c, CFUST_ECUDA, std::string("integral kernel: ") + cudaGetErrorString(e));
+        prof_end(c, CFUST_PROF_LEVEL0 + l, c->launches - n0);
+    }
+    if (fp32) CU(cudaMemsetAsync(c->fix_count, 0, sizeof(int), c->st));
+    CombineArgs ca;
+    ca.D = c->D; ca.Ly = c->Ly; ca.F = c->F; ca.pd = c->pd; ca.pc = c->pc;
+    ca.L0 = pa.L0; ca.L1 = c->rec[1]; ca.L2 = c->rec[2];
+    ca.density_only = density_only; ca.fp32 = fp32;
+    ca.logf = c->logf; ca.u = c->u; ca.elogu = c->elogu; ca.eu = c->eu; ca.euu = c->euu; ca.se = c->se;
+    ca.fix_count = c->fix_count; ca.fix_list = c->fix_list; ca.flags = c->flags;
+    n0 = c->launches;
+    prof_begin(c, CFUST_PROF_COMBINE);
+    if ((e = launch_combine(ca, c->st, &c->launches)) != cudaSuccess)
+        return fail(c, CFUST_ECUDA, std::string("combine kernel: ") + cudaGetErrorString(e));
+    prof_end(c, CFUST_PROF_COMBINE, c->launches - n0);
+    if (fp32) {
+        EstepArgs a;
+        a.D = c->D; a.Ly = c->Ly; a.lat = c->lat;
+        a.y = c->y; a.F = c->F;
+        a.chi64 = c->chi64; a.chi32 = c->chi32;
+        a.shf64 = c->shf64; a.shf32 = c->shf32;
+        a.glx64 = c->glx64; a.glw64 = c->glw64; a.glx32 = c->glx32; a.glw32 = c->glw32;
+        a.t2n = c->t2n;
+        a.density_only = density_only;
+        a.logf = c->logf; a.u = c->u; a.elogu = c->elogu; a.eu = c->eu; a.euu = c->euu; a.se = c->se;
+        a.flags = c->flags;
+        n0 = c->launches;
+        prof_begin(c, CFUST_PROF_FIXUP);
+        if ((e = launch_fixup(a, c->fix_count, c->fix_list, c->nsm, c->st, &c->launches)) != cudaSuccess)
+            return fail(c, CFUST_ECUDA, std::string("fix-up kernel: ") + cudaGetErrorString(e));
+        prof_end(c, CFUST_PROF_FIXUP, c->launches - n0);
+    }
+    return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_estep(cfust_ctx* c, double* loglik_out)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_estep: ctx is NULL");
+    if (!c->have_data || !c->have_params)
+        return fail(c, CFUST_ESTATE, "cfust_estep: set_data and set_params must come first");
+    CU(cudaSetDevice(c->opts.device));
+    CU(cudaMemsetAsync(c->flags, 0, sizeof(int), c->st));
+    cfust_status s;
+    if ((s = launch_setup(c)) != CFUST_OK) return s;
+    if ((s = launch_pairs(c, 0)) != CFUST_OK) return s;
+    ReduceArgs r;
+    r.D = c->D; r.y = c->y; r.pi = c->pi; r.mu = c->mu; r.logf = c->logf; r.u = c->u;
+    r.elogu = c->elogu; r.eu = c->eu; r.euu = c->euu; r.tau = c->tau; r.partial = c->partial;
+    r.chunk = c->chunk; r.row = c->row;
+    const size_t smem = sizeof(double) * ((size_t)c->chunk * c->row + (size_t)c->g * c->chunk + c->chunk);
+    prof_begin(c, CFUST_PROF_REDUCE);
+    estep_reduce_kernel<<<c->nblocks_red, 256, smem, c->st>>>(r);
+    LAUNCHED();
+    const int width = c->g * stats_per_comp(c->p, c->q) + 1;
+    reduce_partials_kernel<<<(width + 127) / 128, 128, 0, c->st>>>(c->partial, c->nblocks_red, width,
+                                                                   c->stats, c->flags);
+    LAUNCHED();
+    prof_end(c, CFUST_PROF_REDUCE, 2);
+    CU(cudaMemcpyAsync(c->h_ll, c->stats + (width - 1), sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    prof_collect(c);
+    if ((s = check_flags(c, *c->h_flags, "cfust_estep")) != CFUST_OK) return s;
+    if (!std::isfinite(*c->h_ll)) return fail(c, CFUST_ENAN, "cfust_estep: non-finite log-likelihood");
+    if (loglik_out) *loglik_out = *c->h_ll;
+    c->have_stats = true;
+    return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_get_pairs(cfust_ctx* c, double* logf, double* tau, double* u,
+                                        double* elogu, double* eu, double* euu, double* se)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_get_pairs: ctx is NULL");
+    if (!c->have_stats) return fail(c, CFUST_ESTATE, "cfust_get_pairs: no E-step results");
+    const size_t ng = (size_t)c->n * c->g;
+    CU(cudaSetDevice(c->opts.device));
+    if (logf) CU(cudaMemcpyAsync(logf, c->logf, sizeof(double) * ng, cudaMemcpyDeviceToHost, c->st));
+    if (tau) CU(cudaMemcpyAsync(tau, c->tau, sizeof(double) * ng, cudaMemcpyDeviceToHost, c->st));
+    if (u) CU(cudaMemcpyAsync(u, c->u, sizeof(double) * ng, cudaMemcpyDeviceToHost, c->st));
+    if (elogu) CU(cudaMemcpyAsync(elogu, c->elogu, sizeof(double) * ng, cudaMemcpyDeviceToHost, c->st));
+    if (eu) CU(cudaMemcpyAsync(eu, c->eu, sizeof(double) * ng * c->q, cudaMemcpyDeviceToHost, c->st));
+    if (euu) CU(cudaMemcpyAsync(euu, c->euu, sizeof(double) * ng * c->q * c->q, cudaMemcpyDeviceToHost, c->st));
+    if (se) CU(cudaMemcpyAsync(se, c->se, sizeof(double) * ng, cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_get_stats(cfust_ctx* c, double* stats)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_get_stats: ctx is NULL");
+    if (!stats) return fail(c, CFUST_EINVAL, "cfust_get_stats: stats is NULL");
+    if (!c->have_stats) return fail(c, CFUST_ESTATE, "cfust_get_stats: no E-step results");
+    CU(cudaSetDevice(c->opts.device));
+    CU(cudaMemcpyAsync(stats, c->stats, sizeof(double) * c->g * stats_per_comp(c->p, c->q),
+                       cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_mstep(cfust_ctx* c)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_mstep: ctx is NULL");
+    if (!c->have_stats) return fail(c, CFUST_ESTATE, "cfust_mstep: run cfust_estep first");
+    CU(cudaSetDevice(c->opts.device));
+    CU(cudaMemsetAsync(c->flags, 0, sizeof(int), c->st));
+    prof_begin(c, CFUST_PROF_MSTEP);
+    mstep_kernel<<<1, 32, 0, c->st>>>(c->D, c->stats, c->opts.nu_min, c->opts.nu_max, c->mu, c->Delta,
+                                      c->nu, c->pi_n, c->mu_n, c->Sigma_n, c->Delta_n, c->nu_n,
+                                      c->flags, c->comp_status);
+    LAUNCHED();
+    prof_end(c, CFUST_PROF_MSTEP, 1);
+    CU(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaMemcpyAsync(c->h_comp, c->comp_status, sizeof(int) * c->g, cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    prof_collect(c);
+    const int f = *c->h_flags;
+    auto first = [&](int bit) {
+        for (int h = 0; h < c->g; ++h)
+            if (c->h_comp[h] & bit) return h;
+        return -1;
+    };
+    if (f & KF_EMPTY)
+        return fail(c, CFUST_EEMPTY, "cfust_mstep: component " + std::to_string(first(KF_EMPTY)) +
+                                         " has no weight (sum tau = 0)");
+    if (f & KF_NOTPD_SEE)
+        return fail(c, CFUST_ENOTPD, "cfust_mstep: component " + std::to_string(first(KF_NOTPD_SEE)) +
+                                         ": sum tau e3 not positive definite");
+    if (f & KF_NOTPD_SIGMA)
+        return fail(c, CFUST_ENOTPD, "cfust_mstep: component " + std::to_string(first(KF_NOTPD_SIGMA)) +
+                                         ": updated Sigma not positive definite");
+    const int p = c->p, q = c->q, g = c->g;
+    CU(cudaMemcpyAsync(c->pi, c->pi_n, sizeof(double) * g, cudaMemcpyDeviceToDevice, c->st));
+    CU(cudaMemcpyAsync(c->mu, c->mu_n, sizeof(double) * g * p, cudaMemcpyDeviceToDevice, c->st));
+    CU(cudaMemcpyAsync(c->Sigma, c->Sigma_n, sizeof(double) * g * p * p, cudaMemcpyDeviceToDevice, c->st));
+    CU(cudaMemcpyAsync(c->Delta, c->Delta_n, sizeof(double) * g * p * q, cudaMemcpyDeviceToDevice, c->st));
+    CU(cudaMemcpyAsync(c->nu, c->nu_n, sizeof(double) * g, cudaMemcpyDeviceToDevice, c->st));
+    c->have_stats = false;
+    if (f & KF_NUROOT)
+        return fail(c, CFUST_ENUROOT, "cfust_mstep: component " + std::to_string(first(KF_NUROOT)) +
+                                          ": eq (22) has no root in [nu_min, nu_max]; nu clamped");
+    return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_loglik(cfust_ctx* c, double* out)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_loglik: ctx is NULL");
+    if (!out) return fail(c, CFUST_EINVAL, "cfust_loglik: out is NULL");
+    if (!c->have_data || !c->have_params)
+        return fail(c, CFUST_ESTATE, "cfust_loglik: set_data and set_params must come first");
+    CU(cudaSetDevice(c->opts.device));
+    CU(cudaMemsetAsync(c->flags, 0, sizeof(int), c->st));
+    cfust_status s;
+    if ((s = launch_setup(c)) != CFUST_OK) return s;
+    if ((s = launch_pairs(c, 1)) != CFUST_OK) return s;
+    prof_begin(c, CFUST_PROF_REDUCE);
+    loglik_partial_kernel<<<c->nblocks_ll, 256, 0, c->st>>>(c->D, c->pi, c->logf, c->partial);
+    LAUNCHED();
+    reduce_partials_kernel<<<1, 32, 0, c->st>>>(c->partial, c->nblocks_ll, 1, c->stats, c->flags);
+    LAUNCHED();
+    prof_end(c, CFUST_PROF_REDUCE, 2);
+    CU(cudaMemcpyAsync(c->h_ll, c->stats, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    prof_collect(c);
+    c->have_stats = false;
+    if ((s = check_flags(c, *c->h_flags, "cfust_loglik")) != CFUST_OK) return s;
+    *out = *c->h_ll;
+    return std::isfinite(*out) ? CFUST_OK : fail(c, CFUST_ENAN, "cfust_loglik: non-finite log-likelihood");
+}
+
+extern "C" cfust_status cfust_fit(cfust_ctx* c, int max_iter, double tol, int* iters_out,
+                                  double* loglik_hist)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_fit: ctx is NULL");
+    if (max_iter < 0) return fail(c, CFUST_EINVAL, "cfust_fit: max_iter < 0");
+    std::vector<double> hist((size_t)max_iter + 1, NAN);
+    int it = 0;
+    cfust_status s = CFUST_OK;
+    bool converged = false;
+    for (it = 0; it < max_iter; ++it) {
+        double L;
+        if ((s = cfust_estep(c, &L)) != CFUST_OK) break;
+        hist[it] = L;
+        if (tol > 0.0 && it >= 2) {
+            // Aitken (eqs 24-26); equal consecutive values count as converged
+            const double den = hist[it - 1] - hist[it - 2];
+            if (den == 0.0) { converged = true; break; }
+            const double acc = (L - hist[it - 1]) / den;
+            const double linf = hist[it - 1] + (L - hist[it - 1]) / (1.0 - acc);
+            if (std::fabs(linf - L) < tol) { converged = true; break; }
+        }
+        s = cfust_mstep(c);
+        if (s == CFUST_ENUROOT) s = CFUST_OK;  // nu clamped: keep iterating
+        if (s != CFUST_OK) break;
+    }
+    if (s == CFUST_OK && !converged) {
+        double L;
+        s = cfust_loglik(c, &L);
+        hist[max_iter] = L;
+        it = max_iter;
+    }
+    if (iters_out) *iters_out = it;
+    if (loglik_hist) std::memcpy(loglik_hist, hist.data(), sizeof(double) * ((size_t)it + 1));
+    return s;
+}
+
+extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const double* b,
+                                      const double* V, const double* nu, double* out, double* se)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_tk_eval: ctx is NULL");
+    if (k < 0 || k > CF_MAXDIM || count < 1 || !b || !V || !nu || !out)
+        return fail(c, CFUST_EINVAL, "cfust_tk_eval: bad arguments (0 <= k <= 8, count >= 1)");
+    for (int i = 0; i < count; ++i)
+        if (!(nu[i] > 0.0)) return fail(c, CFUST_EINVAL, "cfust_tk_eval: nu must be positive");
+    if (k == 0) {
+        for (int i = 0; i < count; ++i) {
+            out[i] = 1.0;
+            if (se) se[i] = 0.0;
+        }
+        return CFUST_OK;
+    }
+    // standardise on the host: limits b_i / sqrt(V_ii), Cholesky factor of corr(V)
+    std::vector<double> bt((size_t)count * k), fac((size_t)count * k * k, 0.0), dofv(nu, nu + count);
+    std::vector<int> foff(count), tab(count);
+    for (int i = 0; i < count; ++i) {
+        const double* Vi = V + (size_t)i * k * k;
+        double* L = fac.data() + (size_t)i * k * k;
+        std::vector<double> ds(k);
+        for (int a = 0; a < k; ++a) {
+            if (!(Vi[a * k + a] > 0.0)) return fail(c, CFUST_EINVAL, "cfust_tk_eval: V not positive definite");
+            ds[a] = 1.0 / std::sqrt(Vi[a * k + a]);
+            bt[(size_t)i * k + a] = b[(size_t)i * k + a] * ds[a];
+        }
+        for (int jj = 0; jj < k; ++jj) {
+            double sum = 1.0;
+            for (int l = 0; l < jj; ++l) sum -= L[jj * k + l] * L[jj * k + l];
+            if (!(sum > 0.0)) return fail(c, CFUST_EINVAL, "cfust_tk_eval: V not positive definite");
+            L[jj * k + jj] = std::sqrt(sum);
+            for (int ii = jj + 1; ii < k; ++ii) {
+                double t = Vi[ii * k + jj] * ds[ii] * ds[jj];
+                for (int l = 0; l < jj; ++l) t -= L[ii * k + l] * L[jj * k + l];
+                L[ii * k + jj] = t / L[jj * k + jj];
+            }
+        }
+        foff[i] = i * k * k;
+        tab[i] = i;
+    }
+    CU(cudaSetDevice(c->opts.device));
+    const size_t NM = (size_t)c->lat.N * c->lat.M;
+    const bool lattice = k >= 3;
+    RecSet r{};
+    r.k = k;
+    r.nrec = count;
+    double *dF = nullptr, *t64 = nullptr;
+    float* t32 = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto cleanup = [&]() {
+        cudaFree(r.bt); cudaFree(r.fac); cudaFree(r.tab); cudaFree(r.dof); cudaFree(r.res);
+        cudaFree(r.se); cudaFree(dF); cudaFree(t64); cudaFree(t32);
+    };
+    if ((e = dalloc(&r.bt, bt.size())) != cudaSuccess || (e = dalloc(&r.fac, count)) != cudaSuccess ||
+        (e = dalloc(&r.tab, count)) != cudaSuccess || (e = dalloc(&r.dof, count)) != cudaSuccess ||
+        (e = dalloc(&r.res, count)) != cudaSuccess || (e = dalloc(&r.se, count)) != cudaSuccess ||
+        (e = dalloc(&dF, fac.size())) != cudaSuccess ||
+        (e = dalloc(&t64, lattice ? NM * count : 1)) != cudaSuccess ||
+        (e = dalloc(&t32, lattice ? NM * count : 1)) != cudaSuccess) {
+        cleanup();
+        return fail(c, CFUST_ENOMEM, std::string("cfust_tk_eval: ") + cudaGetErrorString(e));
+    }
+    do {
+        if ((e = cudaMemcpyAsync(r.bt, bt.data(), sizeof(double) * bt.size(), cudaMemcpyHostToDevice, c->st))) break;
+        if ((e = cudaMemcpyAsync(r.fac, foff.data(), sizeof(int) * count, cudaMemcpyHostToDevice, c->st))) break;
+        if ((e = cudaMemcpyAsync(r.tab, tab.data(), sizeof(int) * count, cudaMemcpyHostToDevice, c->st))) break;
+        if ((e = cudaMemcpyAsync(r.dof, dofv.data(), sizeof(double) * count, cudaMemcpyHostToDevice, c->st))) break;
+        if ((e = cudaMemcpyAsync(dF, fac.data(), sizeof(double) * fac.size(), cudaMemcpyHostToDevice, c->st))) break;
+        if (lattice) {
+            const long long total = (long long)count * NM;
+            const int blocks = (int)std::min<long long>((total + 127) / 128, 64LL * c->nsm);
+            chi_table_kernel<<<blocks, 128, 0, c->st>>>(count, r.dof, c->lat, c->shf64, t64, t32);
+            c->launches++;
+            if ((e = cudaGetLastError())) break;
+        }
+        IntegArgs ia = integ_args(c);
+        ia.F = dF;
+        ia.chi64 = t64;
+        ia.chi32 = t32;
+        if ((e = launch_integrals(r, ia, c->opts.precision == CFUST_PREC_FP32, c->nsm, c->st, &c->launches))) break;
+        if ((e = cudaMemcpyAsync(out, r.res, sizeof(double) * count, cudaMemcpyDeviceToHost, c->st))) break;
+        if (se && (e = cudaMemcpyAsync(se, r.se, sizeof(double) * count, cudaMemcpyDeviceToHost, c->st))) break;
+        e = cudaStreamSynchronize(c->st);
+    } while (0);
+    cfust_status s = CFUST_OK;
+    if (e != cudaSuccess) s = fail(c, CFUST_ECUDA, std::string("cfust_tk_eval: ") + cudaGetErrorString(e));
+    cleanup();
+    return s;
+}

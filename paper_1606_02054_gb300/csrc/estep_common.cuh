@@ -1,0 +1,189 @@
+// estep_common.cuh -- per-pair arithmetic of the E-step shared by the
+// plan / combine kernels and the fused FP64 fix-up routine (FP64 throughout).
+//
+//   whiten        r = y - mu, z = Linv r, d = z^T z, c = A^T z, log t_p   (eqs 3-4)
+//   limits_l0     standardised limits of alpha_s (eq 4, dof nu+p) and alpha
+//                 (eq 13, dof nu+p+2):  c_i sqrt(nu'/(nu+d)) / sqrt(Lambda_ii)
+//   limits_l1     T_{q-1}(c_{-r} - m_r; 0, V_r, nu+p+1) of xi_r, with
+//                 S = ((nu+d)/(nu+p)) Lambda, m_r = S_{-r,r} c_r / S_rr,
+//                 V_r = ((nu+p + c_r^2/S_rr)/(nu+p+1)) (S_{-r,-r} - S_{-r,r} S_{r,-r}/S_rr)
+//   limits_l2     T_{q-2} at dof nu+p of the conditional mean
+//                 E[X_s | X_r = c_r, X_{-r} <= c_{-r}] (same construction one level down
+//                 with V' = nu2 V_r / (nu2 - 2), nu2 = nu+p+1)
+//   assemble      eqs (4), (13), (15), (16), (17) from the integrals
+#pragma once
+
+#include "internal.cuh"
+#include "special.cuh"
+
+struct PairOut {
+    double logf, u, elogu, se;
+    double eu[CF_MAXQ];
+    double euu[CF_MAXQ * CF_MAXQ];
+};
+
+__device__ inline void pair_whiten(const double* F, const Layout& Ly, int p, int q,
+                                   const double* yj, double* d_out, double* c, double* logtp)
+{
+    double rr[CF_MAXP];
+    for (int i = 0; i < p; ++i) rr[i] = yj[i] - F[Ly.mu + i];
+    double d = 0.0;
+    double z[CF_MAXP];
+    for (int i = 0; i < p; ++i) {
+        double s = 0.0;
+        for (int l = 0; l <= i; ++l) s += F[Ly.Linv + i * p + l] * rr[l];
+        z[i] = s;
+        d += s * s;
+    }
+    for (int k = 0; k < q; ++k) {
+        double s = 0.0;
+        for (int i = 0; i < p; ++i) s += F[Ly.A + i * q + k] * z[i];
+        c[k] = s;
+    }
+    const double nu = F[Ly.scal + SC_NU];
+    *d_out = d;
+    *logtp = F[Ly.scal + SC_LOGTP] - 0.5 * (nu + p) * log1p(d / nu);
+}
+
+// which = 0: alpha_s (dof nu+p); which = 1: alpha (dof nu+p+2)
+__device__ inline void limits_l0(const double* F, const Layout& Ly, int p, int q, const double* c,
+                                 double d, int which, double* bt)
+{
+    const double nu = F[Ly.scal + SC_NU], nu1 = nu + p;
+    const double f = sqrt((nu1 + 2.0 * which) / (nu + d));
+    for (int k = 0; k < q; ++k) bt[k] = c[k] * f * F[Ly.dq + k];
+}
+
+// Level-1 limits for coordinate r; returns the scale factor sc1 (V_r = sc1 schur_r).
+__device__ inline double limits_l1(const double* F, const Layout& Ly, int p, int q, const double* c,
+                                   double d, int r, double* bt)
+{
+    const int q1 = q - 1;
+    const double nu = F[Ly.scal + SC_NU], nu1 = nu + p;
+    const double k0 = (nu + d) / nu1;
+    const double Srr = k0 * F[Ly.Lam + r * q + r];
+    const double* blk = F + Ly.l1 + r * Ly.l1s;
+    const double* mvec = blk;
+    const double* dsc = blk + q1 + q1 * q1;
+    const double kap1 = (nu1 + c[r] * c[r] / Srr) / (nu1 + 1.0);
+    const double sc1 = kap1 * k0;
+    const double isc = 1.0 / sqrt(sc1);
+    for (int i = 0; i < q1; ++i) {
+        const int b = i < r ? i : i + 1;
+        bt[i] = (c[b] - mvec[i] * c[r]) * dsc[i] * isc;
+    }
+    return sc1;
+}
+
+__device__ inline void limits_l2(const double* F, const Layout& Ly, int p, int q, const double* c,
+                                 double d, int r, int s, double* bt)
+{
+    const int q1 = q - 1, q2 = q - 2;
+    const double nu = F[Ly.scal + SC_NU], nu1 = nu + p, nu2 = nu1 + 1.0;
+    const double k0 = (nu + d) / nu1;
+    const double Srr = k0 * F[Ly.Lam + r * q + r];
+    const double* blk = F + Ly.l1 + r * Ly.l1s;
+    const double* mvec = blk;
+    const double* sch = blk + q1;
+    double cp[CF_MAXQ];
+    for (int i = 0; i < q1; ++i) {
+        const int b = i < r ? i : i + 1;
+        cp[i] = c[b] - mvec[i] * c[r];
+    }
+    const double sc1 = (nu1 + c[r] * c[r] / Srr) / (nu1 + 1.0) * k0;
+    const double kp = nu2 / (nu2 - 2.0) * sc1;
+    const double Vss = kp * sch[s * q1 + s];
+    const double* b2 = F + Ly.l2 + (r * q1 + s) * Ly.l2s;
+    const double* mv2 = b2;
+    const double* ds2 = b2 + q2;
+    const double kap2 = (nu2 - 2.0 + cp[s] * cp[s] / Vss) / (nu2 - 1.0);
+    const double isc2 = 1.0 / sqrt(kap2 * kp);
+    for (int i = 0; i < q2; ++i) {
+        const int b = i < s ? i : i + 1;
+        bt[i] = (cp[b] - mv2[i] * cp[s]) * ds2[i] * isc2;
+    }
+}
+
+// Offsets of the correlation Cholesky factors used by each level.
+__device__ inline int fac_l0(const Layout& Ly) { return Ly.Lq; }
+__device__ inline int fac_l1(const Layout& Ly, int q, int r)
+{
+    const int q1 = q - 1;
+    return Ly.l1 + r * Ly.l1s + 2 * q1 + q1 * q1;
+}
+__device__ inline int fac_l2(const Layout& Ly, int q, int r, int s)
+{
+    const int q1 = q - 1, q2 = q - 2;
+    return Ly.l2 + (r * q1 + s) * Ly.l2s + 2 * q2;
+}
+
+// tq1[r] = T_{q-1} of level 1 (1 when q = 1); tq2[r*(q-1)+s] = T_{q-2} of
+// level 2 (1 when q <= 2).
+__device__ inline void pair_assemble(const double* F, const Layout& Ly, int p, int q,
+                                     const double* c, double d, double logtp, double alpha_s,
+                                     double alpha, const double* tq1, const double* tq2,
+                                     int density_only, PairOut& o)
+{
+    const double nu = F[Ly.scal + SC_NU], nu1 = nu + p;
+    o.logf = q * 0.6931471805599453 + logtp + log(alpha_s);  // eq (4)
+    if (density_only) return;
+    const double u = nu1 / (nu + d) * alpha / alpha_s;        // eq (13)
+    o.u = u;
+    o.elogu = u - log(0.5 * (nu + d)) - nu1 / (nu + d) + F[Ly.scal + SC_PSI];  // eq (15)
+    const double* Lam = F + Ly.Lam;
+    const double k0 = (nu + d) / nu1;
+    const int q1 = q - 1;
+    double xi[CF_MAXQ], H[CF_MAXQ * CF_MAXQ];
+    for (int i = 0; i < q * q; ++i) H[i] = 0.0;
+    for (int r = 0; r < q; ++r) {
+        const double Srr = k0 * Lam[r * q + r];
+        const double t1q = q1 > 0 ? tq1[r] : 1.0;
+        xi[r] = exp(cf_logt1(c[r], Srr, nu1)) * t1q;
+        H[r * q + r] = c[r] * xi[r];
+        if (q1 == 0 || xi[r] == 0.0) continue;
+        const double* blk = F + Ly.l1 + r * Ly.l1s;
+        const double* mvec = blk;
+        const double* sch = blk + q1;
+        double cp[CF_MAXQ];
+        for (int i = 0; i < q1; ++i) {
+            const int b = i < r ? i : i + 1;
+            cp[i] = c[b] - mvec[i] * c[r];
+        }
+        const double nu2 = nu1 + 1.0;
+        const double sc1 = (nu1 + c[r] * c[r] / Srr) / (nu1 + 1.0) * k0;
+        const double kp = nu2 / (nu2 - 2.0) * sc1;
+        double xip[CF_MAXQ];
+        for (int s = 0; s < q1; ++s) {
+            const double Vss = kp * sch[s * q1 + s];
+            const double t2q = q1 > 1 ? tq2[r * q1 + s] : 1.0;
+            xip[s] = exp(cf_logt1(cp[s], Vss, nu2 - 2.0)) * t2q;
+        }
+        // E[Y 1(Y <= c')] = -(nu2/(nu2-2)) V_r xi', V_r = sc1 schur_r
+        const double fac = -(nu2 / (nu2 - 2.0)) * sc1 / t1q;
+        for (int i = 0; i < q1; ++i) {
+            double s = 0.0;
+            for (int t = 0; t < q1; ++t) s += sch[i * q1 + t] * xip[t];
+            const int b = i < r ? i : i + 1;
+            H[r * q + b] = xi[r] * (mvec[i] * c[r] + fac * s);
+        }
+    }
+    double Lxi[CF_MAXQ];
+    for (int a = 0; a < q; ++a) {
+        double s = 0.0;
+        for (int k = 0; k < q; ++k) s += Lam[a * q + k] * xi[k];
+        Lxi[a] = s;
+        o.eu[a] = u * c[a] + s / alpha_s;  // eq (16)
+    }
+    for (int a = 0; a < q; ++a)
+        for (int b = 0; b <= a; ++b) {  // eq (17), symmetrised
+            double lh1 = 0.0, lh2 = 0.0;
+            for (int k = 0; k < q; ++k) {
+                lh1 += Lam[a * q + k] * H[k * q + b];
+                lh2 += Lam[b * q + k] * H[k * q + a];
+            }
+            const double v = u * c[a] * c[b] + (c[a] * Lxi[b] + Lxi[a] * c[b]) / alpha_s + Lam[a * q + b]
+                           - 0.5 * (lh1 + lh2) / alpha_s;
+            o.euu[a * q + b] = v;
+            o.euu[b * q + a] = v;
+        }
+}

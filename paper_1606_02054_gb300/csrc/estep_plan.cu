@@ -1,0 +1,152 @@
+// estep_plan.cu -- E-step plan and combine kernels (one thread per pair, FP64)
+// and the T_1 record evaluator.
+//
+// Plan: whitening and log t_p of every (observation, component) pair, and the
+// standardised limits of every T_k the pair needs (levels 0-2, see
+// internal.cuh).  Combine: eqs (4), (13), (15)-(17) from the evaluated T_k.
+// Pairs are component-major (pid = h*n + j).
+#include "estep_common.cuh"
+
+__global__ void __launch_bounds__(128) plan_kernel(PlanArgs a)
+{
+    const int p = a.D.p, q = a.D.q;
+    const long long np = a.D.n * a.D.g;
+    const int m0 = a.density_only ? 1 : 2;
+    for (long long pid = blockIdx.x * (long long)blockDim.x + threadIdx.x; pid < np;
+         pid += (long long)gridDim.x * blockDim.x) {
+        const int h = (int)(pid / a.D.n);
+        const long long j = pid - (long long)h * a.D.n;
+        const double* F = a.F + (size_t)h * a.Ly.stride;
+        const int foff = h * a.Ly.stride;
+        const double nu1 = F[a.Ly.scal + SC_NU] + p;
+        double c[CF_MAXQ], d, logtp;
+        pair_whiten(F, a.Ly, p, q, a.y + (size_t)j * p, &d, c, &logtp);
+        a.pd[2 * pid] = d;
+        a.pd[2 * pid + 1] = logtp;
+        for (int k = 0; k < q; ++k) a.pc[pid * q + k] = c[k];
+        double bt[CF_MAXQ];
+        for (int w = 0; w < m0; ++w) {
+            const long long rec = pid * m0 + w;
+            limits_l0(F, a.Ly, p, q, c, d, w, bt);
+            for (int k = 0; k < q; ++k) a.L0.bt[rec * q + k] = bt[k];
+            a.L0.fac[rec] = foff + fac_l0(a.Ly);
+            a.L0.tab[rec] = 3 * h + 2 * w;
+            a.L0.dof[rec] = nu1 + 2.0 * w;
+        }
+        if (a.density_only) continue;
+        const int q1 = q - 1, q2 = q - 2;
+        for (int r = 0; r < q && q1 > 0; ++r) {
+            const long long rec = pid * q + r;
+            limits_l1(F, a.Ly, p, q, c, d, r, bt);
+            for (int k = 0; k < q1; ++k) a.L1.bt[rec * q1 + k] = bt[k];
+            a.L1.fac[rec] = foff + fac_l1(a.Ly, q, r);
+            a.L1.tab[rec] = 3 * h + 1;
+            a.L1.dof[rec] = nu1 + 1.0;
+            for (int s = 0; s < q1 && q2 > 0; ++s) {
+                const long long r2 = pid * q * q1 + r * q1 + s;
+                limits_l2(F, a.Ly, p, q, c, d, r, s, bt);
+                for (int k = 0; k < q2; ++k) a.L2.bt[r2 * q2 + k] = bt[k];
+                a.L2.fac[r2] = foff + fac_l2(a.Ly, q, r, s);
+                a.L2.tab[r2] = 3 * h;
+                a.L2.dof[r2] = nu1;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) combine_kernel(CombineArgs a)
+{
+    const int p = a.D.p, q = a.D.q;
+    const long long np = a.D.n * a.D.g;
+    const int m0 = a.density_only ? 1 : 2;
+    const int q1 = q - 1;
+    for (long long pid = blockIdx.x * (long long)blockDim.x + threadIdx.x; pid < np;
+         pid += (long long)gridDim.x * blockDim.x) {
+        const int h = (int)(pid / a.D.n);
+        const double* F = a.F + (size_t)h * a.Ly.stride;
+        const double d = a.pd[2 * pid], logtp = a.pd[2 * pid + 1];
+        double c[CF_MAXQ];
+        for (int k = 0; k < q; ++k) c[k] = a.pc[pid * q + k];
+        const double alpha_s = a.L0.res[pid * m0];
+        const double se = a.L0.se ? a.L0.se[pid * m0] : 0.0;
+        if (a.fp32 && !(alpha_s >= 1e-35)) {
+            // outside the FP32 range of the lattice products: redo in FP64
+            const int slot = atomicAdd(a.fix_count, 1);
+            a.fix_list[slot] = (int)pid;
+            continue;
+        }
+        const double alpha = a.density_only ? 0.0 : a.L0.res[pid * m0 + 1];
+        double tq1[CF_MAXQ], tq2[CF_MAXQ * CF_MAXQ];
+        if (!a.density_only) {
+            for (int r = 0; r < q && q1 > 0; ++r) tq1[r] = a.L1.res[pid * q + r];
+            if (q1 > 1)
+                for (int i = 0; i < q * q1; ++i) tq2[i] = a.L2.res[pid * q * q1 + i];
+        }
+        PairOut o;
+        pair_assemble(F, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1, tq2, a.density_only, o);
+        a.logf[pid] = o.logf;
+        if (a.se) a.se[pid] = se;
+        if (!isfinite(o.logf)) atomicOr(a.flags, KF_NAN);
+        if (a.density_only) continue;
+        a.u[pid] = o.u;
+        a.elogu[pid] = o.elogu;
+        for (int k = 0; k < q; ++k) a.eu[pid * q + k] = o.eu[k];
+        for (int k = 0; k < q * q; ++k) a.euu[pid * q * q + k] = o.euu[k];
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) t1_records_kernel(RecSet r)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < r.nrec;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double nu = r.dof[i];
+        r.res[i] = (double)t1cdf_dev<R>((R)r.bt[i], (R)nu, (R)t1_lgb(nu));
+        if (r.se) r.se[i] = 0.0;
+    }
+}
+
+static int grid_for(long long work, int threads, int cap)
+{
+    long long b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    return (int)(b < cap ? b : cap);
+}
+
+cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st, long long* launches)
+{
+    const long long np = a.D.n * a.D.g;
+    plan_kernel<<<grid_for(np, 128, 1 << 20), 128, 0, st>>>(a);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st, long long* launches)
+{
+    const long long np = a.D.n * a.D.g;
+    combine_kernel<<<grid_for(np, 128, 1 << 20), 128, 0, st>>>(a);
+    ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_integrals(const RecSet& r, const IntegArgs& a, int fp32, int nsm,
+                             cudaStream_t st, long long* launches)
+{
+    if (r.k == 0 || r.nrec == 0) return cudaSuccess;
+    cudaError_t e;
+    if (r.k == 1) {
+        if (fp32) t1_records_kernel<float><<<grid_for(r.nrec, 128, 1 << 20), 128, 0, st>>>(r);
+        else t1_records_kernel<double><<<grid_for(r.nrec, 128, 1 << 20), 128, 0, st>>>(r);
+        e = cudaGetLastError();
+    } else {
+        // one warp per record, 8 warps per block, enough blocks to fill every SM
+        const long long blocks_needed = (r.nrec + 7) / 8;
+        const int cap = nsm * 16;
+        const int blocks = (int)(blocks_needed < cap ? blocks_needed : cap);
+        if (r.k == 2) e = launch_t2(r, a, fp32, blocks, st);
+        else if (fp32) e = launch_lattice32(r.k, r, a, blocks, st);
+        else e = launch_lattice64(r.k, r, a, blocks, st);
+    }
+    ++*launches;
+    return e;
+}

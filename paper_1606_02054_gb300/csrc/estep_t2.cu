@@ -1,0 +1,28 @@
+// estep_t2.cu -- T_2 records (warp per record, quadrature nodes over lanes).
+#include "internal.cuh"
+#include "special.cuh"
+
+template <typename R>
+__global__ void __launch_bounds__(256) t2_records_kernel(RecSet r, IntegArgs a)
+{
+    const int lane = threadIdx.x & (CF_WARP - 1);
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const R* glx = sizeof(R) == sizeof(float) ? (const R*)a.glx32 : (const R*)a.glx64;
+    const R* glw = sizeof(R) == sizeof(float) ? (const R*)a.glw32 : (const R*)a.glw64;
+    for (long long i = warp; i < r.nrec; i += nwarps) {
+        const double rho = a.F[r.fac[i] + 2];  // L[1][0] of the 2 x 2 correlation factor
+        const double v = t2cdf_warp<R>(r.bt[2 * i], r.bt[2 * i + 1], rho, r.dof[i], a.t2n, glx, glw, lane);
+        if (lane == 0) {
+            r.res[i] = v;
+            if (r.se) r.se[i] = 0.0;
+        }
+    }
+}
+
+cudaError_t launch_t2(const RecSet& r, const IntegArgs& a, int fp32, int blocks, cudaStream_t st)
+{
+    if (fp32) t2_records_kernel<float><<<blocks, 256, 0, st>>>(r, a);
+    else t2_records_kernel<double><<<blocks, 256, 0, st>>>(r, a);
+    return cudaGetLastError();
+}

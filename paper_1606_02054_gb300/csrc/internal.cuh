@@ -1,0 +1,206 @@
+// internal.cuh -- shared definitions of the CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define CF_MAXP 32
+#define CF_MAXQ 8
+#define CF_MAXG 16
+#define CF_MAXSHIFT 64
+#define CF_MAXDIM 8     // lattice dimensions (= largest T_k)
+#define CF_WARP 32
+
+// Sizes of one problem.
+struct Dims {
+    int p, q, g;
+    long long n;
+};
+
+// Offsets (in doubles) inside one component's factor block, written by the
+// set-up kernel from Psi and read by the E-step.  Definitions under eq (4):
+// Omega = Sigma + Delta Delta^T, c = Delta^T Omega^{-1} (y - mu),
+// Lambda = I - Delta^T Omega^{-1} Delta, d = (y-mu)^T Omega^{-1} (y-mu).
+struct Layout {
+    int mu;     // p
+    int Linv;   // p x p, lower-triangular inverse Cholesky factor of Omega
+    int A;      // p x q, Linv * Delta: c = A^T z with z = Linv (y - mu)
+    int scal;   // SC_COUNT scalars
+    int Lam;    // q x q, Lambda
+    int dq;     // q, 1 / sqrt(diag Lambda)
+    int Lq;     // q x q, Cholesky factor of the correlation matrix of Lambda
+    int l1;     // q blocks (one per coordinate r) of size l1s:
+    int l1s;    //   mvec (q-1) = Lambda_{-r,r} / Lambda_rr, schur ((q-1)^2),
+                //   dsc (q-1) = 1/sqrt(diag schur), L ((q-1)^2) chol of corr(schur)
+    int l2;     // q*(q-1) blocks (pairs r, s) of size l2s, for the Schur
+    int l2s;    //   complement of schur_r at s: mvec (q-2), dsc (q-2), L ((q-2)^2)
+    int stride; // doubles per component
+};
+
+enum { SC_NU = 0, SC_LOGTP = 1, SC_PSI = 2, SC_COUNT = 4 };
+
+__host__ __device__ inline Layout make_layout(int p, int q)
+{
+    Layout L;
+    int o = 0;
+    L.mu = o; o += p;
+    L.Linv = o; o += p * p;
+    L.A = o; o += p * q;
+    L.scal = o; o += SC_COUNT;
+    L.Lam = o; o += q * q;
+    L.dq = o; o += q;
+    L.Lq = o; o += q * q;
+    int q1 = q - 1, q2 = q - 2 > 0 ? q - 2 : 0;
+    L.l1s = q1 > 0 ? (2 * q1 + 2 * q1 * q1) : 0;
+    L.l1 = o; o += q * L.l1s;
+    L.l2s = q2 > 0 ? (2 * q2 + q2 * q2) : 0;
+    L.l2 = o; o += q * (q - 1) * L.l2s;
+    L.stride = (o + 1) & ~1;
+    return L;
+}
+
+// Rank-1 lattice of the T_k integrator (k >= 3): z_d = a^d mod N.
+struct Lattice {
+    int N, M;
+    int z[CF_MAXDIM];
+};
+
+// Error flags written by kernels (bitwise OR into one device int).
+enum {
+    KF_NOTPD_OMEGA = 1 << 0,
+    KF_NOTPD_LAMBDA = 1 << 1,
+    KF_NOTPD_SEE = 1 << 2,
+    KF_NOTPD_SIGMA = 1 << 3,
+    KF_EMPTY = 1 << 4,
+    KF_NUROOT = 1 << 5,
+    KF_NAN = 1 << 6,
+};
+
+// Number of statistics per component (see cfust_get_stats).
+__host__ __device__ inline int stats_per_comp(int p, int q)
+{
+    return 3 + p + q + p * q + q * q + p * p;
+}
+
+// ---------------------------------------------------------------------------
+// E-step pipeline.  Every T_k of a pair depends only on (c, d) of that pair,
+// so a plan kernel writes one record per integral, integrator kernels
+// evaluate all records of one dimension, and a combine kernel assembles the
+// E-step quantities.  Records per pair and level:
+//   level 0, dim q:    alpha_s (eq 4) and alpha (eq 13)   [1 when density-only]
+//   level 1, dim q-1:  T_{q-1} of xi_r, r = 0..q-1
+//   level 2, dim q-2:  T_{q-2} of the conditional mean, (r, s), s over the q-1 others
+// ---------------------------------------------------------------------------
+struct RecSet {
+    int k;             // dimension of every integral in the set (0 = none)
+    long long nrec;    // number of records
+    double* bt;        // nrec x k standardised upper limits
+    int* fac;          // offset in F of the k x k correlation Cholesky factor
+    int* tab;          // chi table index 3h + j (dof nu_h + p + j)
+    double* dof;       // degrees of freedom
+    double* res;       // T_k
+    double* se;        // standard error over the lattice shifts (may be null)
+};
+
+struct PlanArgs {
+    Dims D;
+    Layout Ly;
+    const double* y;
+    const double* F;
+    int density_only;
+    double* pd;        // per pair: d, log t_p
+    double* pc;        // per pair: c (q)
+    RecSet L0, L1, L2;
+};
+
+struct IntegArgs {
+    const double* F;
+    Lattice lat;
+    const double* chi64;   // [(3h + j)][M][N] (or per case for cfust_tk_eval)
+    const float* chi32;
+    const double* shf64;   // [M][CF_MAXDIM]
+    const float* shf32;
+    const double* glx64;   // Gauss-Legendre nodes/weights on [0, 1]
+    const double* glw64;
+    const float* glx32;
+    const float* glw32;
+    int t2n;
+};
+
+struct CombineArgs {
+    Dims D;
+    Layout Ly;
+    const double* F;
+    const double* pd;
+    const double* pc;
+    RecSet L0, L1, L2;
+    int density_only;
+    int fp32;              // records evaluated in FP32: pairs with alpha_s < 1e-35 go to the fix-up list
+    double* logf;
+    double* u;
+    double* elogu;
+    double* eu;
+    double* euu;
+    double* se;
+    int* fix_count;
+    int* fix_list;
+    int* flags;
+};
+
+// Arguments of the fused FP64 pair routine (fix-up of FP32 pairs in the far
+// tail of T_q, and the reference path of cfust_tk_eval).
+struct EstepArgs {
+    Dims D;
+    Layout Ly;
+    Lattice lat;
+    const double* y;        // n x p
+    const double* F;        // g x stride factor blocks
+    const double* chi64;    // [(3h + k)][M][N]
+    const float* chi32;
+    const double* shf64;    // [M][CF_MAXDIM]
+    const float* shf32;
+    const double* glx64;    // Gauss-Legendre nodes/weights on [0,1]
+    const double* glw64;
+    const float* glx32;
+    const float* glw32;
+    int t2n;
+    int density_only;
+    double* logf;           // g*n
+    double* u;
+    double* elogu;
+    double* eu;             // g*n*q
+    double* euu;            // g*n*q*q
+    double* se;
+    int* flags;
+};
+
+// host launchers (each issues on `st`; *launches counts kernels issued)
+cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st, long long* launches);
+cudaError_t launch_integrals(const RecSet& r, const IntegArgs& a, int fp32, int nsm,
+                             cudaStream_t st, long long* launches);
+cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st, long long* launches);
+cudaError_t launch_fixup(const EstepArgs& a, const int* count, const int* list, int nsm,
+                         cudaStream_t st, long long* launches);
+cudaError_t launch_tk_eval(int k, int count, const double* b, const double* V, const double* nu,
+                           const IntegArgs& a, int fp32, double* out, double* se, cudaStream_t st,
+                           long long* launches);
+cudaError_t launch_lattice32(int k, const RecSet& r, const IntegArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_lattice64(int k, const RecSet& r, const IntegArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_t2(const RecSet& r, const IntegArgs& a, int fp32, int blocks, cudaStream_t st);
+
+// Arguments of the statistics reduction (reduce.cu).
+struct ReduceArgs {
+    Dims D;
+    const double* y;
+    const double* pi;
+    const double* mu;
+    const double* logf;
+    const double* u;
+    const double* elogu;
+    const double* eu;
+    const double* euu;
+    double* tau;       // g*n
+    double* partial;   // nblocks x (g*S + 1)
+    int chunk;         // observations per block (<= blockDim.x)
+    int row;           // doubles per staged observation row
+};

@@ -1,0 +1,141 @@
+// mstep.cu -- M-step solve (S11), one thread per component, FP64.
+//
+// From the statistics of estep_reduce (centred at mu^(k), r = y - mu^(k)):
+//   eq (18)  pi = N / n
+//   eq (19)  mu^(k+1) = mu^(k) + delta,  delta = (Sr - Delta^(k) Se) / U
+//   eq (20)  Delta^(k+1) = A See^{-1},  A = sum tau (y - mu^(k+1)) e2^T = Sre - delta Se^T
+//   eq (21)  Sigma^(k+1) = [Srr - Sr delta^T - delta Sr^T + U delta delta^T
+//                            - Delta A^T - A Delta^T + Delta See Delta^T] / N
+//            (with Delta = Delta^(k+1); sum tau e2 (y - mu)^T = A^T)
+//   eq (22)  nu: root of N [log(nu/2) - psi(nu/2) + 1] + Snu = 0 (sum over j,
+//            second term with +), safeguarded Newton on [nu_min, nu_max].
+// Results go to separate output arrays; the host commits them only when no
+// component failed (empty component, non-PD See or Sigma), so a failed
+// M-step leaves Psi^(k) untouched.
+#include "internal.cuh"
+#include "special.cuh"
+
+namespace {
+__device__ bool chol_small(int n, const double* A, double* L)
+{
+    for (int j = 0; j < n; ++j) {
+        double s = A[j * n + j];
+        for (int k = 0; k < j; ++k) s -= L[j * n + k] * L[j * n + k];
+        if (!(s > 0.0)) return false;
+        L[j * n + j] = sqrt(s);
+        for (int i = j + 1; i < n; ++i) {
+            double t = A[i * n + j];
+            for (int k = 0; k < j; ++k) t -= L[i * n + k] * L[j * n + k];
+            L[i * n + j] = t / L[j * n + j];
+        }
+    }
+    return true;
+}
+
+__device__ double nu_eq(double v, double N, double Snu)
+{
+    return N * (log(0.5 * v) - cf_digamma(0.5 * v) + 1.0) + Snu;
+}
+}  // namespace
+
+__global__ void mstep_kernel(Dims D, const double* __restrict__ stats, double nu_min, double nu_max,
+                             const double* __restrict__ mu, const double* __restrict__ Delta,
+                             const double* __restrict__ nu, double* pi_o, double* mu_o,
+                             double* Sigma_o, double* Delta_o, double* nu_o, int* flags,
+                             int* comp_status)
+{
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= D.g) return;
+    const int p = D.p, q = D.q;
+    const int S = stats_per_comp(p, q);
+    const double* st = stats + (size_t)h * S;
+    const double N = st[0], U = st[1], Snu = st[2];
+    const double* Sr = st + 3;
+    const double* Se = Sr + p;
+    const double* Sre = Se + q;
+    const double* See = Sre + p * q;
+    const double* Srr = See + q * q;
+    const double* muh = mu + (size_t)h * p;
+    const double* Dh = Delta + (size_t)h * p * q;
+    comp_status[h] = 0;
+    if (!(N > 1e-12 * (double)D.n) || !(U > 0.0)) {
+        atomicOr(flags, KF_EMPTY);
+        comp_status[h] = KF_EMPTY;
+        return;
+    }
+    double delta[CF_MAXP], A[CF_MAXP * CF_MAXQ], Dn[CF_MAXP * CF_MAXQ];
+    for (int i = 0; i < p; ++i) {
+        double s = Sr[i];
+        for (int k = 0; k < q; ++k) s -= Dh[i * q + k] * Se[k];
+        delta[i] = s / U;
+    }
+    for (int i = 0; i < p; ++i)
+        for (int k = 0; k < q; ++k) A[i * q + k] = Sre[i * q + k] - delta[i] * Se[k];
+    double Bs[CF_MAXQ * CF_MAXQ], LB[CF_MAXQ * CF_MAXQ];
+    for (int a = 0; a < q; ++a)
+        for (int b = 0; b < q; ++b) Bs[a * q + b] = 0.5 * (See[a * q + b] + See[b * q + a]);
+    if (!chol_small(q, Bs, LB)) {
+        atomicOr(flags, KF_NOTPD_SEE);
+        comp_status[h] = KF_NOTPD_SEE;
+        return;
+    }
+    // Delta = A See^{-1}: each row solves See x = A_i^T
+    for (int i = 0; i < p; ++i) {
+        double zz[CF_MAXQ];
+        for (int k = 0; k < q; ++k) {
+            double s = A[i * q + k];
+            for (int l = 0; l < k; ++l) s -= LB[k * q + l] * zz[l];
+            zz[k] = s / LB[k * q + k];
+        }
+        for (int k = q - 1; k >= 0; --k) {
+            double s = zz[k];
+            for (int l = k + 1; l < q; ++l) s -= LB[l * q + k] * Dn[i * q + l];
+            Dn[i * q + k] = s / LB[k * q + k];
+        }
+    }
+    // Sigma (eq 21)
+    double Sn[CF_MAXP * CF_MAXP];
+    for (int i = 0; i < p; ++i)
+        for (int l = 0; l <= i; ++l) {
+            double s = Srr[i * p + l] - Sr[i] * delta[l] - delta[i] * Sr[l] + U * delta[i] * delta[l];
+            for (int k = 0; k < q; ++k) s -= Dn[i * q + k] * A[l * q + k] + A[i * q + k] * Dn[l * q + k];
+            for (int a = 0; a < q; ++a) {
+                double t = 0.0;
+                for (int b = 0; b < q; ++b) t += Bs[a * q + b] * Dn[l * q + b];
+                s += Dn[i * q + a] * t;
+            }
+            Sn[i * p + l] = s / N;
+            Sn[l * p + i] = s / N;
+        }
+    double LS[CF_MAXP * CF_MAXP];
+    if (!chol_small(p, Sn, LS)) {
+        atomicOr(flags, KF_NOTPD_SIGMA);
+        comp_status[h] = KF_NOTPD_SIGMA;
+        return;
+    }
+    // nu (eq 22): F decreasing in nu
+    double vnew;
+    const double flo = nu_eq(nu_min, N, Snu), fhi = nu_eq(nu_max, N, Snu);
+    if (!(flo > 0.0)) { vnew = nu_min; atomicOr(flags, KF_NUROOT); comp_status[h] = KF_NUROOT; }
+    else if (!(fhi < 0.0)) { vnew = nu_max; atomicOr(flags, KF_NUROOT); comp_status[h] = KF_NUROOT; }
+    else {
+        double lo = nu_min, hi = nu_max;
+        double v = nu[h] > lo && nu[h] < hi ? nu[h] : 0.5 * (lo + hi);
+        for (int it = 0; it < 200; ++it) {
+            const double f = nu_eq(v, N, Snu);
+            if (f > 0.0) lo = v; else hi = v;
+            const double fp = N * (1.0 / v - 0.5 * cf_trigamma(0.5 * v));
+            double vn = v - f / fp;
+            if (!(vn > lo && vn < hi)) vn = 0.5 * (lo + hi);
+            const bool done = fabs(vn - v) <= 1e-14 * v || hi - lo <= 1e-14 * hi;
+            v = vn;
+            if (done) break;
+        }
+        vnew = v;
+    }
+    pi_o[h] = N / (double)D.n;
+    for (int i = 0; i < p; ++i) mu_o[(size_t)h * p + i] = muh[i] + delta[i];
+    for (int i = 0; i < p * q; ++i) Delta_o[(size_t)h * p * q + i] = Dn[i];
+    for (int i = 0; i < p * p; ++i) Sigma_o[(size_t)h * p * p + i] = Sn[i];
+    nu_o[h] = vnew;
+}

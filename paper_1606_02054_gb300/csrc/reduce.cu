@@ -1,0 +1,153 @@
+// reduce.cu -- posterior weights, log-likelihood and the tau-weighted
+// sufficient statistics of the M-step, FP64, deterministic (no atomics).
+//
+// S8: tau_hj = pi_h f_h(y_j) / sum_h' pi_h' f_h'(y_j)   (eq 12, log-sum-exp)
+//     l_j = log sum_h pi_h f_h(y_j)                     (eq 27; Sec. 4.3: the
+//     same density pass gives l(Psi^(k)) and tau^(k))
+// S9: per block of observations, per component h, with r = y_j - mu_h^(k):
+//     N = sum tau, U = sum tau u, Snu = sum tau (elogu - u),
+//     Sr = sum tau u r, Se = sum tau eu, Sre = sum tau r eu^T,
+//     See = sum tau euu, Srr = sum tau u r r^T
+//     (eqs 18-22 written as sums; centring at mu_h^(k) avoids cancellation).
+// S10: fixed-order sum of the block partials.
+#include "internal.cuh"
+
+
+
+// Staged row of one observation for component h:
+//   [0] tau, [1] tau*u, [2] elogu - u, [3] 1, [4..4+p) r, then eu (q), euu (q*q).
+// Each statistic is the sum over the chunk of row[ia]*row[ib]*row[ic].
+__device__ inline void stat_operands(int e, int p, int q, int& ia, int& ib, int& ic)
+{
+    const int R0 = 4, E0 = 4 + p, EE0 = 4 + p + q;
+    if (e == 0) { ia = 0; ib = 3; ic = 3; return; }                  // N
+    if (e == 1) { ia = 1; ib = 3; ic = 3; return; }                  // U
+    if (e == 2) { ia = 0; ib = 2; ic = 3; return; }                  // Snu
+    e -= 3;
+    if (e < p) { ia = 1; ib = R0 + e; ic = 3; return; }              // Sr
+    e -= p;
+    if (e < q) { ia = 0; ib = E0 + e; ic = 3; return; }              // Se
+    e -= q;
+    if (e < p * q) { ia = 0; ib = R0 + e / q; ic = E0 + e % q; return; }  // Sre
+    e -= p * q;
+    if (e < q * q) { ia = 0; ib = EE0 + e; ic = 3; return; }         // See
+    e -= q * q;
+    ia = 1; ib = R0 + e / p; ic = R0 + e % p;                        // Srr
+}
+
+__global__ void estep_reduce_kernel(ReduceArgs a)
+{
+    extern __shared__ double sm[];
+    const int p = a.D.p, q = a.D.q, g = a.D.g;
+    const long long n = a.D.n;
+    const int S = stats_per_comp(p, q);
+    const long long j0 = (long long)blockIdx.x * a.chunk;
+    const int cnt = (int)((n - j0) < a.chunk ? (n - j0) : a.chunk);
+    double* rows = sm;                           // chunk x row
+    double* taus = rows + (size_t)a.chunk * a.row;  // g x chunk
+    double* lj = taus + (size_t)g * a.chunk;     // chunk
+    double* out = a.partial + (size_t)blockIdx.x * (g * S + 1);
+    const int t = threadIdx.x;
+
+    // S8: tau and l_j for this chunk
+    if (t < cnt) {
+        const long long j = j0 + t;
+        double mx = -INFINITY;
+        for (int h = 0; h < g; ++h) {
+            const double v = log(a.pi[h]) + a.logf[(size_t)h * n + j];
+            mx = v > mx ? v : mx;
+        }
+        double s = 0.0;
+        for (int h = 0; h < g; ++h) s += exp(log(a.pi[h]) + a.logf[(size_t)h * n + j] - mx);
+        const double ls = log(s);
+        lj[t] = mx + ls;
+        for (int h = 0; h < g; ++h) {
+            const double tv = exp(log(a.pi[h]) + a.logf[(size_t)h * n + j] - mx - ls);
+            taus[h * a.chunk + t] = tv;
+            if (a.tau) a.tau[(size_t)h * n + j] = tv;
+        }
+    } else if (t < a.chunk) {
+        lj[t] = 0.0;
+    }
+    __syncthreads();
+    // partial log-likelihood: fixed-order tree over the chunk
+    for (int w = 1; w < a.chunk; w <<= 1) {
+        if ((t % (2 * w)) == 0 && t + w < a.chunk) lj[t] += lj[t + w];
+        __syncthreads();
+    }
+    if (t == 0) out[g * S] = lj[0];
+    __syncthreads();
+
+    // S9: statistics, one component at a time
+    for (int h = 0; h < g; ++h) {
+        if (t < a.chunk) {
+            double* rw = rows + (size_t)t * a.row;
+            if (t < cnt) {
+                const size_t pid = (size_t)h * n + j0 + t;
+                const double tv = taus[h * a.chunk + t];
+                const double uv = a.u[pid];
+                rw[0] = tv;
+                rw[1] = tv * uv;
+                rw[2] = a.elogu[pid] - uv;
+                rw[3] = 1.0;
+                const double* yj = a.y + (size_t)(j0 + t) * p;
+                for (int i = 0; i < p; ++i) rw[4 + i] = yj[i] - a.mu[(size_t)h * p + i];
+                for (int k = 0; k < q; ++k) rw[4 + p + k] = a.eu[pid * q + k];
+                for (int k = 0; k < q * q; ++k) rw[4 + p + q + k] = a.euu[pid * q * q + k];
+            } else {
+                for (int i = 0; i < a.row; ++i) rw[i] = 0.0;
+            }
+        }
+        __syncthreads();
+        for (int e = t; e < S; e += blockDim.x) {
+            int ia, ib, ic;
+            stat_operands(e, p, q, ia, ib, ic);
+            double acc = 0.0;
+            for (int jj = 0; jj < cnt; ++jj) {
+                const double* rw = rows + (size_t)jj * a.row;
+                acc += rw[ia] * rw[ib] * rw[ic];
+            }
+            out[h * S + e] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// S10: stats[e] = sum_b partial[b][e], b in increasing order.
+__global__ void reduce_partials_kernel(const double* __restrict__ partial, int nblocks, int width,
+                                       double* __restrict__ stats, int* flags)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < width; e += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * width + e];
+        stats[e] = s;
+        if (!isfinite(s)) atomicOr(flags, KF_NAN);
+    }
+}
+
+// Density-only pass: l = sum_j log sum_h pi_h f_h(y_j), per-block partials.
+__global__ void loglik_partial_kernel(Dims D, const double* __restrict__ pi,
+                                      const double* __restrict__ logf, double* __restrict__ partial)
+{
+    __shared__ double sh[256];
+    const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (j < D.n) {
+        double mx = -INFINITY;
+        for (int h = 0; h < D.g; ++h) {
+            const double t = log(pi[h]) + logf[(size_t)h * D.n + j];
+            mx = t > mx ? t : mx;
+        }
+        double s = 0.0;
+        for (int h = 0; h < D.g; ++h) s += exp(log(pi[h]) + logf[(size_t)h * D.n + j] - mx);
+        v = mx + log(s);
+    }
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = 1; w < blockDim.x; w <<= 1) {
+        if ((threadIdx.x % (2 * w)) == 0 && threadIdx.x + w < blockDim.x)
+            sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}

@@ -1,0 +1,220 @@
+// setup.cu -- per-component factors (S0) and the chi table (S1).
+//
+// S0, one thread per component, FP64 (definitions under eq (4)):
+//   Omega = Sigma + Delta Delta^T, L = chol(Omega), Linv = L^{-1},
+//   log|Omega|, A = Linv Delta (so c = A^T Linv (y - mu), d = |Linv (y-mu)|^2),
+//   Lambda = I - Delta^T Omega^{-1} Delta, evaluated as (I + Delta^T Sigma^{-1} Delta)^{-1}
+//   (Woodbury identity; no cancellation when Lambda has small eigenvalues),
+//   the constant of the log t_p density (eq 3) and psi((nu+p)/2) of eq (15),
+//   and for the truncated-t moments the correlation Cholesky factors of
+//   Lambda, of its Schur complements at each r, and of theirs at each s.
+// S1: s = sqrt(chi2_nu'^{-1}(w_0)/nu') at every (shift, lattice point) for
+//   each tabulated dof nu'; independent of the observations.
+#include "internal.cuh"
+#include "special.cuh"
+
+namespace {
+
+// Cholesky (lower, row-major, n x n); returns false if not positive definite.
+__device__ bool chol_dev(int n, const double* A, double* L)
+{
+    for (int j = 0; j < n; ++j) {
+        double s = A[j * n + j];
+        for (int k = 0; k < j; ++k) s -= L[j * n + k] * L[j * n + k];
+        if (!(s > 0.0)) return false;
+        const double dj = sqrt(s);
+        L[j * n + j] = dj;
+        for (int i = j + 1; i < n; ++i) {
+            double t = A[i * n + j];
+            for (int k = 0; k < j; ++k) t -= L[i * n + k] * L[j * n + k];
+            L[i * n + j] = t / dj;
+        }
+        for (int i = 0; i < j; ++i) L[i * n + j] = 0.0;
+    }
+    return true;
+}
+
+// inverse of a lower-triangular matrix (row-major)
+__device__ void trinv_dev(int n, const double* L, double* Li)
+{
+    for (int c = 0; c < n; ++c) {
+        for (int i = 0; i < n; ++i) {
+            if (i < c) { Li[i * n + c] = 0.0; continue; }
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = c; k < i; ++k) s -= L[i * n + k] * Li[k * n + c];
+            Li[i * n + c] = s / L[i * n + i];
+        }
+    }
+}
+
+// Correlation Cholesky and 1/sqrt(diag) of an n x n scale matrix S.
+__device__ bool corr_chol_dev(int n, const double* S, double* dsc, double* Lc)
+{
+    double R[CF_MAXQ * CF_MAXQ];
+    for (int i = 0; i < n; ++i) {
+        if (!(S[i * n + i] > 0.0)) return false;
+        dsc[i] = 1.0 / sqrt(S[i * n + i]);
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) R[i * n + j] = S[i * n + j] * dsc[i] * dsc[j];
+    for (int i = 0; i < n; ++i) R[i * n + i] = 1.0;
+    return chol_dev(n, R, Lc);
+}
+
+// Schur complement of an n x n matrix S at index r: (n-1) x (n-1), and the
+// regression coefficients S_{-r,r}/S_rr.
+__device__ void schur_dev(int n, const double* S, int r, double* out, double* mvec)
+{
+    const double srr = S[r * n + r];
+    int ii = 0;
+    for (int i = 0; i < n; ++i) {
+        if (i == r) continue;
+        mvec[ii] = S[i * n + r] / srr;
+        int jj = 0;
+        for (int j = 0; j < n; ++j) {
+            if (j == r) continue;
+            out[ii * (n - 1) + jj] = S[i * n + j] - S[i * n + r] * S[r * n + j] / srr;
+            ++jj;
+        }
+        ++ii;
+    }
+}
+
+}  // namespace
+
+__global__ void setup_components_kernel(Dims D, Layout Ly, const double* __restrict__ mu,
+                                        const double* __restrict__ Sigma,
+                                        const double* __restrict__ Delta,
+                                        const double* __restrict__ nu, double* __restrict__ F,
+                                        int* flags)
+{
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= D.g) return;
+    const int p = D.p, q = D.q;
+    const double* Sg = Sigma + (size_t)h * p * p;
+    const double* Dl = Delta + (size_t)h * p * q;
+    double* Fh = F + (size_t)h * Ly.stride;
+    double W[CF_MAXP * CF_MAXP], Lo[CF_MAXP * CF_MAXP];
+
+    for (int i = 0; i < p; ++i) Fh[Ly.mu + i] = mu[(size_t)h * p + i];
+    // Omega and its Cholesky factor
+    for (int i = 0; i < p; ++i)
+        for (int j = 0; j < p; ++j) {
+            double s = Sg[i * p + j];
+            for (int k = 0; k < q; ++k) s += Dl[i * q + k] * Dl[j * q + k];
+            W[i * p + j] = s;
+        }
+    if (!chol_dev(p, W, Lo)) { atomicOr(flags, KF_NOTPD_OMEGA); return; }
+    double logdet = 0.0;
+    for (int i = 0; i < p; ++i) logdet += 2.0 * log(Lo[i * p + i]);
+    trinv_dev(p, Lo, Fh + Ly.Linv);
+    const double* Li = Fh + Ly.Linv;
+    for (int i = 0; i < p; ++i)
+        for (int k = 0; k < q; ++k) {
+            double s = 0.0;
+            for (int l = 0; l <= i; ++l) s += Li[i * p + l] * Dl[l * q + k];
+            Fh[Ly.A + i * q + k] = s;
+        }
+    // Lambda = (I + B^T B)^{-1}, B = chol(Sigma)^{-1} Delta
+    if (!chol_dev(p, Sg, Lo)) { atomicOr(flags, KF_NOTPD_OMEGA); return; }
+    trinv_dev(p, Lo, W);
+    double B[CF_MAXP * CF_MAXQ];
+    for (int i = 0; i < p; ++i)
+        for (int k = 0; k < q; ++k) {
+            double s = 0.0;
+            for (int l = 0; l <= i; ++l) s += W[i * p + l] * Dl[l * q + k];
+            B[i * q + k] = s;
+        }
+    double Mq[CF_MAXQ * CF_MAXQ], Lm[CF_MAXQ * CF_MAXQ], Lmi[CF_MAXQ * CF_MAXQ];
+    for (int a = 0; a < q; ++a)
+        for (int b = 0; b < q; ++b) {
+            double s = (a == b) ? 1.0 : 0.0;
+            for (int i = 0; i < p; ++i) s += B[i * q + a] * B[i * q + b];
+            Mq[a * q + b] = s;
+        }
+    if (!chol_dev(q, Mq, Lm)) { atomicOr(flags, KF_NOTPD_LAMBDA); return; }
+    trinv_dev(q, Lm, Lmi);
+    double* Lam = Fh + Ly.Lam;
+    for (int a = 0; a < q; ++a)
+        for (int b = 0; b < q; ++b) {
+            double s = 0.0;
+            const int k0 = a > b ? a : b;
+            for (int k = k0; k < q; ++k) s += Lmi[k * q + a] * Lmi[k * q + b];
+            Lam[a * q + b] = s;
+        }
+    const double v = nu[h];
+    Fh[Ly.scal + SC_NU] = v;
+    Fh[Ly.scal + SC_LOGTP] = lgamma(0.5 * (v + p)) - lgamma(0.5 * v) - 0.5 * p * log(v * CF_PI)
+                           - 0.5 * logdet;
+    Fh[Ly.scal + SC_PSI] = cf_digamma(0.5 * (v + p));
+    Fh[Ly.scal + 3] = 0.0;
+    if (!corr_chol_dev(q, Lam, Fh + Ly.dq, Fh + Ly.Lq)) { atomicOr(flags, KF_NOTPD_LAMBDA); return; }
+    // level 1: Schur complement of Lambda at each r
+    const int q1 = q - 1, q2 = q - 2;
+    for (int r = 0; r < q && q1 > 0; ++r) {
+        double* blk = Fh + Ly.l1 + r * Ly.l1s;
+        double* mvec = blk;
+        double* sch = blk + q1;
+        double* dsc = sch + q1 * q1;
+        double* Lc = dsc + q1;
+        schur_dev(q, Lam, r, sch, mvec);
+        if (!corr_chol_dev(q1, sch, dsc, Lc)) { atomicOr(flags, KF_NOTPD_LAMBDA); return; }
+        // level 2: Schur complement of sch at each s
+        for (int s = 0; s < q1 && q2 > 0; ++s) {
+            double* b2 = Fh + Ly.l2 + (r * q1 + s) * Ly.l2s;
+            double sch2[CF_MAXQ * CF_MAXQ];
+            schur_dev(q1, sch, s, sch2, b2);
+            if (!corr_chol_dev(q2, sch2, b2 + q2, b2 + 2 * q2)) {
+                atomicOr(flags, KF_NOTPD_LAMBDA);
+                return;
+            }
+        }
+    }
+}
+
+// s = sqrt(chi2_{dof}^{-1}(w_0)/dof) for every dof in `dofs`, shift m and point i.
+// Lattice coordinate 0: x = frac(i/N + shift(m, 0)), w = 1 - |2x - 1|.
+__global__ void chi_table_kernel(int ndof, const double* __restrict__ dofs, Lattice lat,
+                                 const double* __restrict__ shf, double* __restrict__ t64,
+                                 float* __restrict__ t32)
+{
+    const long long total = (long long)ndof * lat.M * lat.N;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t % lat.N);
+        const int m = (int)((t / lat.N) % lat.M);
+        const int k = (int)(t / ((long long)lat.N * lat.M));
+        const double dof = dofs[k];
+        double x = (double)(((long long)i * lat.z[0]) % lat.N) / (double)lat.N + shf[m * CF_MAXDIM];
+        if (x >= 1.0) x -= 1.0;
+        const double wc = fabs(2.0 * x - 1.0);
+        const double w = 1.0 - wc;
+        const double s = sqrt(cf_chi2_quantile(w, wc, dof) / dof);
+        t64[t] = s;
+        t32[t] = (float)s;
+    }
+}
+
+// dofs of the E-step tables: nu_h + p + k, k = 0, 1, 2 (T_q / T_{q-2},
+// T_{q-1}, T_q at nu+p+2), read from the factor blocks.
+__global__ void estep_dofs_kernel(Dims D, Layout Ly, const double* __restrict__ F, double* dofs)
+{
+    const int t = threadIdx.x;
+    if (t < 3 * D.g) {
+        const int h = t / 3, k = t % 3;
+        dofs[t] = F[(size_t)h * Ly.stride + Ly.scal + SC_NU] + D.p + k;
+    }
+}
+
+// FP32 observations widened to FP64 (row stride ld).
+__global__ void widen_kernel(const float* __restrict__ src, long long ld, Dims D,
+                             double* __restrict__ dst)
+{
+    const long long total = D.n * D.p;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long j = t / D.p;
+        const int i = (int)(t % D.p);
+        dst[t] = (double)src[j * ld + i];
+    }
+}

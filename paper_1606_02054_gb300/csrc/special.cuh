@@ -1,0 +1,381 @@
+// special.cuh -- device special functions and the warp-cooperative T_k
+// integrators of the E-step.
+//
+// T_q(b; 0, V, nu), the multivariate t CDF in eq (4) (dof nu+p), eq (13)
+// (dof nu+p+2) and in the truncated-t moments of eqs (16)-(17), is not
+// specified by the paper.  Here:
+//   k = 0: 1;
+//   k = 1: regularised incomplete beta, continued fraction (modified Lentz);
+//   k = 2: x = sqrt(nu) tan(theta) turns the conditional integral
+//          int_{-inf}^{h} t_nu(x) T_1((k - rho x)/sqrt((1-rho^2)(nu+x^2)/(nu+1)); nu+1) dx
+//          into C_nu int cos^{nu-1}(theta) T_1(...) dtheta on a finite interval
+//          with a smooth integrand; fixed Gauss-Legendre nodes, split where the
+//          inner argument changes sign, nodes spread over the 32 lanes;
+//   k >= 3: Genz's separation of variables for the multivariate t (chi
+//          variable first, fixed order) on a randomised rank-1 Korobov
+//          lattice with the baker's transform; lattice points spread over the
+//          32 lanes, one warp-shuffle reduction per random shift.
+// Every warp-cooperative routine must be called by all 32 lanes with the
+// same arguments; it returns the same value in every lane.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+
+#define CF_PI 3.141592653589793238462643383279502884
+#define CF_FULL 0xffffffffu
+
+// ---------------------------------------------------------------------------
+// precision-generic wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float m_exp(float x) { return expf(x); }
+__device__ __forceinline__ double m_exp(double x) { return exp(x); }
+__device__ __forceinline__ float m_log(float x) { return logf(x); }
+__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float m_abs(float x) { return fabsf(x); }
+__device__ __forceinline__ double m_abs(double x) { return fabs(x); }
+__device__ __forceinline__ float m_ncdf(float x) { return normcdff(x); }
+__device__ __forceinline__ double m_ncdf(double x) { return normcdf(x); }
+__device__ __forceinline__ float m_ncdfinv(float x) { return normcdfinvf(x); }
+__device__ __forceinline__ double m_ncdfinv(double x) { return normcdfinv(x); }
+__device__ __forceinline__ float m_sin(float x) { return sinf(x); }
+__device__ __forceinline__ double m_sin(double x) { return sin(x); }
+__device__ __forceinline__ float m_cos(float x) { return cosf(x); }
+__device__ __forceinline__ double m_cos(double x) { return cos(x); }
+__device__ __forceinline__ float m_atan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double m_atan2(double y, double x) { return atan2(y, x); }
+
+template <typename R> struct Lim;
+template <> struct Lim<float> {
+    static __device__ __forceinline__ float tiny() { return 1e-30f; }
+    static __device__ __forceinline__ float eps() { return 6e-8f; }
+    static __device__ __forceinline__ float one_minus_ulp() { return 0.99999994f; }
+    static __device__ __forceinline__ float vmin() { return 1e-37f; }
+    static constexpr int cf_iters = 200;
+};
+template <> struct Lim<double> {
+    static __device__ __forceinline__ double tiny() { return 1e-300; }
+    static __device__ __forceinline__ double eps() { return 1e-16; }
+    static __device__ __forceinline__ double one_minus_ulp() { return 1.0 - 0x1.0p-53; }
+    static __device__ __forceinline__ double vmin() { return 1e-300; }
+    static constexpr int cf_iters = 600;
+};
+
+// ---------------------------------------------------------------------------
+// warp helpers
+// ---------------------------------------------------------------------------
+// Sum over the warp; the result is lane 0's butterfly total, broadcast, so
+// every lane holds a bitwise-identical value (keeps later branches uniform).
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(CF_FULL, v, o);
+    return __shfl_sync(CF_FULL, v, 0);
+}
+
+// ---------------------------------------------------------------------------
+// digamma (FP64): psi(x) = psi(x + k) - sum 1/(x+i) up to x >= 12, then
+// psi(x) ~ ln x - 1/(2x) - sum_{k>=1} B_{2k} / (2k x^{2k}).
+// ---------------------------------------------------------------------------
+__device__ inline double cf_digamma(double x)
+{
+    double s = 0.0;
+    while (x < 12.0) { s -= 1.0 / x; x += 1.0; }
+    const double r = 1.0 / x, r2 = r * r;
+    // coefficients B_{2k}/(2k) for k = 1..6
+    double ser = r2 * (1.0 / 12 + r2 * (-1.0 / 120 + r2 * (1.0 / 252 + r2 * (-1.0 / 240
+                 + r2 * (1.0 / 132 + r2 * (-691.0 / 32760))))));
+    return s + log(x) - 0.5 * r - ser;
+}
+
+// trigamma (FP64) for Newton steps on eq (22): psi'(x) = sum 1/(x+i)^2 + asymptotic
+__device__ inline double cf_trigamma(double x)
+{
+    double s = 0.0;
+    while (x < 12.0) { s += 1.0 / (x * x); x += 1.0; }
+    const double r = 1.0 / x, r2 = r * r;
+    // psi'(x) ~ 1/x + 1/(2x^2) + sum_k B_{2k} / x^{2k+1}
+    double ser = r * (1.0 + r * (0.5 + r * (1.0 / 6 + r2 * (-1.0 / 30 + r2 * (1.0 / 42
+                 + r2 * (-1.0 / 30 + r2 * (5.0 / 66)))))));
+    return s + ser;
+}
+
+// log of the univariate t density at x with scale^2 v and dof nu (FP64)
+__device__ inline double cf_logt1(double x, double v, double nu)
+{
+    return lgamma(0.5 * (nu + 1.0)) - lgamma(0.5 * nu) - 0.5 * log(nu * CF_PI * v)
+         - 0.5 * (nu + 1.0) * log1p(x * x / (nu * v));
+}
+
+// ---------------------------------------------------------------------------
+// T_1: P(T <= t), T ~ t_nu, from I_x(nu/2, 1/2) with x = nu/(nu+t^2).
+// lgb = lgamma((nu+1)/2) - lgamma(nu/2) - lgamma(1/2), precomputed per dof.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R betacf_dev(R a, R b, R x)
+{
+    const R tiny = Lim<R>::tiny();
+    R c = R(1), d = R(1) - (a + b) * x / (a + R(1));
+    if (m_abs(d) < tiny) d = tiny;
+    d = R(1) / d;
+    R h = d;
+    for (int m = 1; m <= Lim<R>::cf_iters; ++m) {
+        const R mm = R(m), m2 = R(2 * m);
+        R aa = mm * (b - mm) * x / ((a - R(1) + m2) * (a + m2));
+        d = R(1) + aa * d; if (m_abs(d) < tiny) d = tiny;
+        c = R(1) + aa / c; if (m_abs(c) < tiny) c = tiny;
+        d = R(1) / d; h *= d * c;
+        aa = -(a + mm) * (a + b + mm) * x / ((a + m2) * (a + R(1) + m2));
+        d = R(1) + aa * d; if (m_abs(d) < tiny) d = tiny;
+        c = R(1) + aa / c; if (m_abs(c) < tiny) c = tiny;
+        d = R(1) / d;
+        const R del = d * c;
+        h *= del;
+        if (m_abs(del - R(1)) < Lim<R>::eps()) break;
+    }
+    return h;
+}
+
+template <typename R>
+__device__ __forceinline__ R t1cdf_dev(R t, R nu, R lgb)
+{
+    if (t == R(0)) return R(0.5);
+    const R t2 = t * t, den = nu + t2;
+    const R x = nu / den, y = t2 / den;
+    const R a = R(0.5) * nu, b = R(0.5);
+    const R ld = m_log(den);
+    const R lbt = lgb + a * (m_log(nu) - ld) + b * (R(2) * m_log(m_abs(t)) - ld);
+    R I;
+    if (x < (a + R(1)) / (a + b + R(2))) I = m_exp(lbt) * betacf_dev<R>(a, b, x) / a;
+    else I = R(1) - m_exp(lbt) * betacf_dev<R>(b, a, y) / b;
+    const R tail = R(0.5) * I;
+    return t > R(0) ? R(1) - tail : tail;
+}
+
+__device__ __forceinline__ double t1_lgb(double nu)
+{
+    return lgamma(0.5 * (nu + 1.0)) - lgamma(0.5 * nu) - 0.5723649429247001 /* lgamma(1/2) */;
+}
+
+// ---------------------------------------------------------------------------
+// T_2(h, k; rho, nu), standard bivariate t, warp-cooperative.
+// With theta = phi - pi/2 (phi in (0, pi)): cos theta = sin phi and
+// sin theta = -cos phi, so
+//   T_2 = C_nu int_0^{phi_h} sin^{nu-1}(phi) T_1((k sin phi + rho sqrt(nu) cos phi) s_r; nu+1) dphi
+// with C_nu = Gamma((nu+1)/2)/(Gamma(nu/2) sqrt(pi)), s_r = sqrt((nu+1)/((1-rho^2) nu)),
+// phi_h = pi/2 + atan(h/sqrt(nu)).  The inner argument changes sign at
+// phi* with (sin, cos)(phi*) ~ (|rho| sqrt(nu), -k sign(rho)); the interval is
+// split there.  For |rho| > 0.99 the nodes are graded (phi = anchor + L t^3)
+// toward the split point (or toward phi_h when there is no split) to resolve
+// the boundary layer of width ~ sqrt(1 - rho^2).
+// glx/glw: n Gauss-Legendre nodes and weights on [0, 1].
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ double t2cdf_warp(double h, double k, double rho, double nu, int n,
+                             const R* __restrict__ glx, const R* __restrict__ glw, int lane)
+{
+    if (rho >= 1.0) {
+        const double m = h < k ? h : k;
+        return (double)t1cdf_dev<R>((R)m, (R)nu, (R)t1_lgb(nu));
+    }
+    if (rho <= -1.0) {
+        const double lg = t1_lgb(nu);
+        const double v = (double)t1cdf_dev<R>((R)h, (R)nu, (R)lg) + (double)t1cdf_dev<R>((R)k, (R)nu, (R)lg) - 1.0;
+        return v > 0.0 ? v : 0.0;
+    }
+    const double sn = sqrt(nu);
+    // phi_h = pi/2 + atan(h/sqrt(nu)), accurate for h << 0 as atan(sqrt(nu)/(-h))
+    const double phi_h = h < 0.0 ? atan(sn / (-h)) : 0.5 * CF_PI + atan(h / sn);
+    bool split = false;
+    double phis = 0.0;
+    if (rho != 0.0) {
+        phis = atan2(fabs(rho) * sn, rho > 0.0 ? -k : k);
+        split = phis < phi_h;
+    }
+    const int grade = fabs(rho) > 0.99 ? 3 : 1;
+    const double anc0 = split ? phis : phi_h;   // pieces run from the anchor to the far end
+    const double far0 = 0.0;
+    const double anc1 = phis, far1 = phi_h;
+    const int npieces = split ? 2 : 1;
+    const R sr = (R)sqrt((nu + 1.0) / ((1.0 - rho * rho) * nu));
+    const R lgb1 = (R)t1_lgb(nu + 1.0);
+    const R nu1 = (R)(nu + 1.0), num1 = (R)(nu - 1.0);
+    const R rsn = (R)(rho * sn), kk = (R)k;
+    double acc = 0.0;
+    for (int t = lane; t < npieces * n; t += CF_WARP) {
+        const int piece = t >= n;
+        const int i = piece ? t - n : t;
+        const double anc = piece ? anc1 : anc0;
+        const double L = (piece ? far1 : far0) - anc;
+        const R u = glx[i];
+        R um, jac;
+        if (grade == 3) { um = u * u * u; jac = R(3) * u * u; }
+        else { um = u; jac = R(1); }
+        const R ph = (R)anc + (R)L * um;
+        const R sp = m_sin(ph), cp = m_cos(ph);
+        const R z = (kk * sp + rsn * cp) * sr;
+        const R f = m_exp(num1 * m_log(sp)) * t1cdf_dev<R>(z, nu1, lgb1);
+        acc += (double)(glw[i] * jac * f) * fabs(L);
+    }
+    acc = warp_sum(acc);
+    const double C = exp(lgamma(0.5 * (nu + 1.0)) - lgamma(0.5 * nu)) / sqrt(CF_PI);
+    return C * acc;
+}
+
+// ---------------------------------------------------------------------------
+// Regularised incomplete gamma and the chi-square quantile (FP64), used to
+// tabulate s = sqrt(chi2_nu^{-1}(w_0)/nu) at every lattice point.
+// ---------------------------------------------------------------------------
+__device__ inline void cf_gamma_pq(double a, double x, double* P, double* Q)
+{
+    if (x <= 0.0) { *P = 0.0; *Q = 1.0; return; }
+    const double lpre = a * log(x) - x - lgamma(a);
+    if (x < a + 1.0) {
+        // series: P = x^a e^-x / Gamma(a+1) * sum_n x^n / ((a+1)...(a+n))
+        double term = 1.0, sum = 1.0, ap = a;
+        for (int n = 0; n < 2000; ++n) {
+            ap += 1.0;
+            term *= x / ap;
+            sum += term;
+            if (term < sum * 1e-17) break;
+        }
+        *P = exp(lpre) * sum / a;
+        *Q = 1.0 - *P;
+    } else {
+        // Legendre continued fraction for Q, modified Lentz
+        const double tiny = 1e-300;
+        double b = x + 1.0 - a, c = 1.0 / tiny, d = 1.0 / b, hh = d;
+        for (int i = 1; i < 2000; ++i) {
+            const double an = -i * (i - a);
+            b += 2.0;
+            d = an * d + b; if (fabs(d) < tiny) d = tiny;
+            c = b + an / c; if (fabs(c) < tiny) c = tiny;
+            d = 1.0 / d;
+            const double del = d * c;
+            hh *= del;
+            if (fabs(del - 1.0) < 1e-16) break;
+        }
+        *Q = exp(lpre) * hh;
+        *P = 1.0 - *Q;
+    }
+}
+
+// x with P(nu/2, x/2) = w (w <= 1/2) or Q(nu/2, x/2) = wc (w > 1/2):
+// safeguarded Newton on the log of the smaller tail probability.
+__device__ inline double cf_chi2_quantile(double w, double wc, double nu)
+{
+    if (!(w > 0.0)) return 0.0;
+    if (!(wc > 0.0)) return INFINITY;
+    const double a = 0.5 * nu;
+    const bool upper = w > 0.5;
+    const double target = upper ? log(wc) : log(w);
+    // start: Wilson-Hilferty, or the small-x expansion in the far lower tail
+    const double z = upper ? -normcdfinv(wc) : normcdfinv(w);
+    const double c9 = 2.0 / (9.0 * nu);
+    const double base = 1.0 - c9 + z * sqrt(c9);
+    double x = nu * base * base * base;
+    const double xs = 2.0 * exp((log(w) + lgamma(a + 1.0)) / a);
+    if (!(x > 0.0) || (!upper && xs < x)) x = xs;
+    double lo = 0.0, hi = INFINITY;
+    for (int it = 0; it < 200; ++it) {
+        double P, Q;
+        cf_gamma_pq(a, 0.5 * x, &P, &Q);
+        const double tv = upper ? Q : P;
+        const double G = upper ? (target - log(tv)) : (log(tv) - target);  // increasing in x
+        if (G == 0.0) break;
+        if (G > 0.0) hi = x; else lo = x;
+        const double ldens = (a - 1.0) * log(0.5 * x) - 0.5 * x - lgamma(a) - 0.6931471805599453;
+        double xn = x - G * exp(log(tv) - ldens);
+        if (!(xn > lo && xn < hi)) xn = isinf(hi) ? 2.0 * x : 0.5 * (lo + hi);
+        const bool done = fabs(xn - x) <= 1e-15 * x || (isfinite(hi) && hi - lo <= 1e-15 * hi);
+        x = xn;
+        if (done) break;
+    }
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// Lattice T_k, k = K >= 3, warp-cooperative.
+//   bt:   standardised limits b_i / sqrt(V_ii) (K values, FP64)
+//   Lc:   Cholesky factor of the correlation matrix of V (K x K, row-major, FP64)
+//   chi:  s at every lattice point for this dof, [m][i] (N per shift)
+//   shf:  shifts [m][d], d < CF_MAXDIM, in precision R
+// Returns the mean over shifts of the shift means; *se the standard error.
+// ---------------------------------------------------------------------------
+template <typename R, int K>
+__device__ double tk_lattice_warp(const double* bt, const double* Lc, const R* __restrict__ chi,
+                                  const R* __restrict__ shf, const Lattice& lat, int lane, double* se)
+{
+    R b[K], invd[K], Lo[K][K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        b[r] = (R)bt[r];
+        invd[r] = (R)(1.0 / Lc[r * K + r]);
+#pragma unroll
+        for (int l = 0; l < K; ++l) Lo[r][l] = l < r ? (R)Lc[r * K + l] : R(0);
+    }
+    const int N = lat.N, M = lat.M;
+    const R invN = R(1) / (R)N;
+    int step[K];
+    int idx0[K];
+#pragma unroll
+    for (int d = 1; d < K; ++d) {
+        step[d] = (int)(((long long)CF_WARP * lat.z[d]) % N);
+        idx0[d] = (int)(((long long)lane * lat.z[d]) % N);
+    }
+    double mean = 0.0, m2 = 0.0;  // Welford over the shift means
+    for (int m = 0; m < M; ++m) {
+        R sh[K];
+#pragma unroll
+        for (int d = 1; d < K; ++d) sh[d] = shf[m * CF_MAXDIM + d];
+        int idx[K];
+#pragma unroll
+        for (int d = 1; d < K; ++d) idx[d] = idx0[d];
+        R acc = R(0), comp = R(0);  // compensated sum
+        const R* __restrict__ crow = chi + (size_t)m * N;
+        for (int i = lane; i < N; i += CF_WARP) {
+            const R s = crow[i];
+            R y[K];
+            R f = R(1);
+#pragma unroll
+            for (int r = 0; r < K; ++r) {
+                R a = b[r] * s;
+#pragma unroll
+                for (int l = 0; l < r; ++l) a -= Lo[r][l] * y[l];
+                const R e = m_ncdf(a * invd[r]);
+                f *= e;
+                if (r < K - 1) {
+                    R x = (R)idx[r + 1] * invN + sh[r + 1];
+                    if (x >= R(1)) x -= R(1);
+                    const R w = R(1) - m_abs(R(2) * x - R(1));
+                    R v = w * e;
+                    v = v < Lim<R>::vmin() ? Lim<R>::vmin() : v;
+                    v = v > Lim<R>::one_minus_ulp() ? Lim<R>::one_minus_ulp() : v;
+                    y[r] = m_ncdfinv(v);
+                }
+                if (e <= Lim<R>::tiny()) f = R(0);
+            }
+            // Kahan step
+            const R yk = f - comp;
+            const R tk = acc + yk;
+            comp = (tk - acc) - yk;
+            acc = tk;
+#pragma unroll
+            for (int d = 1; d < K; ++d) {
+                idx[d] += step[d];
+                if (idx[d] >= N) idx[d] -= N;
+            }
+        }
+        const double smean = warp_sum((double)acc) / N;
+        const double delta = smean - mean;
+        mean += delta / (m + 1);
+        m2 += delta * (smean - mean);
+    }
+    if (se) *se = M > 1 ? sqrt(m2 / (M - 1) / M) : 0.0;
+    return mean;
+}
