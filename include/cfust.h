@@ -184,6 +184,16 @@ const char* cfust_last_error(const cfust_ctx* ctx);
  * launch accounting in benchmarks). */
 int64_t cfust_launch_count(const cfust_ctx* ctx);
 
+/* Diagnostic read-back of internal device buffers into host memory (at most
+ * `bytes` bytes; *written receives the byte count copied).  what:
+ *   0 per-component factor blocks (g x stride doubles, stride = *written/8/g),
+ *   1 per-pair (d, log t_p), 2 per-pair c (q doubles),
+ *   3-5 standardised limits of the level 0/1/2 integral records,
+ *   6-8 values of the level 0/1/2 integral records,
+ *   9 the kernel error flags (one int).
+ * For tests that localise a mismatch to one pipeline stage. */
+cfust_status cfust_debug_read(cfust_ctx* ctx, int what, void* dst, int64_t bytes, int64_t* written);
+
 /* Accumulated device time (ms, CUDA events) and launch count of each kernel
  * class since creation or the last reset; arrays of CFUST_NPROF entries (either
  * may be NULL).  Requires opts.profile = 1 (else CFUST_ESTATE).  reset = 1

@@ -88,6 +88,8 @@ def lib():
             L.cfust_launch_count.restype = i64
             L.cfust_profile.argtypes = [vp, _dp, C.POINTER(C.c_int64), i]
             L.cfust_profile.restype = i
+            L.cfust_debug_read.argtypes = [vp, i, vp, i64, C.POINTER(C.c_int64)]
+            L.cfust_debug_read.restype = i
             for name in ("cfust_create", "cfust_destroy", "cfust_set_data", "cfust_set_params",
                          "cfust_get_params", "cfust_estep", "cfust_get_pairs", "cfust_get_stats",
                          "cfust_mstep", "cfust_loglik", "cfust_fit", "cfust_tk_eval"):
@@ -263,6 +265,15 @@ def cfust_profile(ctx: Context, reset=False):
     _check(lib().cfust_profile(ctx.handle, _ptr(ms), n.ctypes.data_as(C.POINTER(C.c_int64)),
                                int(bool(reset))), ctx)
     return {PROF_NAMES[k]: (float(ms[k]), int(n[k])) for k in range(CFUST_NPROF)}
+
+
+def cfust_debug_read(ctx: Context, what, nbytes=1 << 30, dtype=np.float64):
+    """Internal device buffer `what` (see include/cfust.h) as a numpy array."""
+    buf = np.zeros(max(1, nbytes // np.dtype(dtype).itemsize), dtype=dtype)
+    wr = C.c_int64(0)
+    _check(lib().cfust_debug_read(ctx.handle, int(what), buf.ctypes.data_as(C.c_void_p),
+                                  buf.nbytes, C.byref(wr)), ctx)
+    return buf[: wr.value // np.dtype(dtype).itemsize]
 
 
 def params_from_workload(params):

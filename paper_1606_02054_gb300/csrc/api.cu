@@ -211,6 +211,37 @@ extern "C" const char* cfust_last_error(const cfust_ctx* c)
 
 extern "C" int64_t cfust_launch_count(const cfust_ctx* c) { return c ? c->launches : 0; }
 
+extern "C" cfust_status cfust_debug_read(cfust_ctx* c, int what, void* dst, int64_t bytes,
+                                         int64_t* written)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_debug_read: ctx is NULL");
+    if (!dst || bytes < 0) return fail(c, CFUST_EINVAL, "cfust_debug_read: bad buffer");
+    const size_t ng = (size_t)c->n * c->g;
+    const void* src = nullptr;
+    size_t avail = 0;
+    switch (what) {
+    case 0: src = c->F; avail = sizeof(double) * (size_t)c->g * c->Ly.stride; break;
+    case 1: src = c->pd; avail = sizeof(double) * 2 * ng; break;
+    case 2: src = c->pc; avail = sizeof(double) * ng * c->q; break;
+    case 3: case 4: case 5: {
+        const RecSet& r = c->rec[what - 3];
+        src = r.bt; avail = sizeof(double) * (size_t)r.nrec * r.k; break;
+    }
+    case 6: case 7: case 8: {
+        const RecSet& r = c->rec[what - 6];
+        src = r.res; avail = sizeof(double) * (size_t)r.nrec; break;
+    }
+    case 9: src = c->flags; avail = sizeof(int); break;
+    default: return fail(c, CFUST_EINVAL, "cfust_debug_read: unknown buffer");
+    }
+    const size_t nb = std::min(avail, (size_t)bytes);
+    CU(cudaSetDevice(c->opts.device));
+    if (nb) CU(cudaMemcpyAsync(dst, src, nb, cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    if (written) *written = (int64_t)nb;
+    return CFUST_OK;
+}
+
 extern "C" cfust_status cfust_profile(cfust_ctx* c, double* ms, int64_t* launches, int reset)
 {
     if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_profile: ctx is NULL");

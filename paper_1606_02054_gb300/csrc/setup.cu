@@ -3,8 +3,7 @@
 // S0, one thread per component, FP64 (definitions under eq (4)):
 //   Omega = Sigma + Delta Delta^T, L = chol(Omega), Linv = L^{-1},
 //   log|Omega|, A = Linv Delta (so c = A^T Linv (y - mu), d = |Linv (y-mu)|^2),
-//   Lambda = I - Delta^T Omega^{-1} Delta, evaluated as (I + Delta^T Sigma^{-1} Delta)^{-1}
-//   (Woodbury identity; no cancellation when Lambda has small eigenvalues),
+//   Lambda = I - Delta^T Omega^{-1} Delta = I - A^T A,
 //   the constant of the log t_p density (eq 3) and psi((nu+p)/2) of eq (15),
 //   and for the truncated-t moments the correlation Cholesky factors of
 //   Lambda, of its Schur complements at each r, and of theirs at each s.
@@ -82,11 +81,8 @@ __device__ void schur_dev(int n, const double* S, int r, double* out, double* mv
 
 }  // namespace
 
-__global__ void setup_components_kernel(Dims D, Layout Ly, const double* __restrict__ mu,
-                                        const double* __restrict__ Sigma,
-                                        const double* __restrict__ Delta,
-                                        const double* __restrict__ nu, double* __restrict__ F,
-                                        int* flags)
+__global__ void setup_components_kernel(Dims D, Layout Ly, const double* mu, const double* Sigma,
+                                        const double* Delta, const double* nu, double* F, int* flags)
 {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= D.g) return;
@@ -94,52 +90,53 @@ __global__ void setup_components_kernel(Dims D, Layout Ly, const double* __restr
     const double* Sg = Sigma + (size_t)h * p * p;
     const double* Dl = Delta + (size_t)h * p * q;
     double* Fh = F + (size_t)h * Ly.stride;
-    double W[CF_MAXP * CF_MAXP], Lo[CF_MAXP * CF_MAXP];
+    double W[CF_MAXP * CF_MAXP];
 
     for (int i = 0; i < p; ++i) Fh[Ly.mu + i] = mu[(size_t)h * p + i];
-    // Omega and its Cholesky factor
+    // Omega = Sigma + Delta Delta^T, factorised in place (lower triangle of W)
     for (int i = 0; i < p; ++i)
-        for (int j = 0; j < p; ++j) {
+        for (int j = 0; j <= i; ++j) {
             double s = Sg[i * p + j];
             for (int k = 0; k < q; ++k) s += Dl[i * q + k] * Dl[j * q + k];
             W[i * p + j] = s;
         }
-    if (!chol_dev(p, W, Lo)) { atomicOr(flags, KF_NOTPD_OMEGA); return; }
     double logdet = 0.0;
-    for (int i = 0; i < p; ++i) logdet += 2.0 * log(Lo[i * p + i]);
-    trinv_dev(p, Lo, Fh + Ly.Linv);
-    const double* Li = Fh + Ly.Linv;
+    for (int j = 0; j < p; ++j) {
+        double s = W[j * p + j];
+        for (int k = 0; k < j; ++k) s -= W[j * p + k] * W[j * p + k];
+        if (!(s > 0.0)) { atomicOr(flags, KF_NOTPD_OMEGA); return; }
+        const double dj = sqrt(s);
+        W[j * p + j] = dj;
+        logdet += 2.0 * log(dj);
+        for (int i = j + 1; i < p; ++i) {
+            double t = W[i * p + j];
+            for (int k = 0; k < j; ++k) t -= W[i * p + k] * W[j * p + k];
+            W[i * p + j] = t / dj;
+        }
+    }
+    // Linv = L^{-1} (forward substitution per column), written to the block
+    double* Li = Fh + Ly.Linv;
+    for (int c = 0; c < p; ++c)
+        for (int i = 0; i < p; ++i) {
+            if (i < c) { Li[i * p + c] = 0.0; continue; }
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = c; k < i; ++k) s -= W[i * p + k] * Li[k * p + c];
+            Li[i * p + c] = s / W[i * p + i];
+        }
+    // A = Linv Delta
+    double* A = Fh + Ly.A;
     for (int i = 0; i < p; ++i)
         for (int k = 0; k < q; ++k) {
             double s = 0.0;
             for (int l = 0; l <= i; ++l) s += Li[i * p + l] * Dl[l * q + k];
-            Fh[Ly.A + i * q + k] = s;
+            A[i * q + k] = s;
         }
-    // Lambda = (I + B^T B)^{-1}, B = chol(Sigma)^{-1} Delta
-    if (!chol_dev(p, Sg, Lo)) { atomicOr(flags, KF_NOTPD_OMEGA); return; }
-    trinv_dev(p, Lo, W);
-    double B[CF_MAXP * CF_MAXQ];
-    for (int i = 0; i < p; ++i)
-        for (int k = 0; k < q; ++k) {
-            double s = 0.0;
-            for (int l = 0; l <= i; ++l) s += W[i * p + l] * Dl[l * q + k];
-            B[i * q + k] = s;
-        }
-    double Mq[CF_MAXQ * CF_MAXQ], Lm[CF_MAXQ * CF_MAXQ], Lmi[CF_MAXQ * CF_MAXQ];
-    for (int a = 0; a < q; ++a)
-        for (int b = 0; b < q; ++b) {
-            double s = (a == b) ? 1.0 : 0.0;
-            for (int i = 0; i < p; ++i) s += B[i * q + a] * B[i * q + b];
-            Mq[a * q + b] = s;
-        }
-    if (!chol_dev(q, Mq, Lm)) { atomicOr(flags, KF_NOTPD_LAMBDA); return; }
-    trinv_dev(q, Lm, Lmi);
+    // Lambda = I - A^T A
     double* Lam = Fh + Ly.Lam;
     for (int a = 0; a < q; ++a)
         for (int b = 0; b < q; ++b) {
-            double s = 0.0;
-            const int k0 = a > b ? a : b;
-            for (int k = k0; k < q; ++k) s += Lmi[k * q + a] * Lmi[k * q + b];
+            double s = (a == b) ? 1.0 : 0.0;
+            for (int i = 0; i < p; ++i) s -= A[i * q + a] * A[i * q + b];
             Lam[a * q + b] = s;
         }
     const double v = nu[h];
