@@ -176,6 +176,37 @@ cfust_status cfust_fit(cfust_ctx* ctx, int max_iter, double tol, int* iters_out,
 cfust_status cfust_tk_eval(cfust_ctx* ctx, int k, int count, const double* b, const double* V,
                            const double* nu, double* out, double* se);
 
+/* Posterior weights, log-likelihood and tau-weighted sufficient statistics
+ * (the reduction half of cfust_estep) from per-pair E-step arrays that the
+ * caller already holds on the device, allocating nothing.  The paper has no
+ * counterpart: it is an entry point for callers that cannot call cudaMalloc
+ * -- code that owns all device memory through its own pool, or that must not
+ * incur the device-wide synchronisation of cudaMalloc/cudaFree inside a
+ * latency-critical loop.
+ *
+ * Every pointer is a device pointer on the current device; layouts as in
+ * cfust_get_pairs (component-major h*n + j) and cfust_get_stats:
+ *   y (n x p), pi (g), mu (g x p) at which r = y - mu is centred, logf, u,
+ *   elogu (g*n), eu (g*n*q), euu (g*n*q*q) in;  tau (g*n, may be NULL) and
+ *   stats (g*(3+p+q+pq+q^2+p^2) + 1 doubles: the per-component statistics,
+ *   then l of eq (27)) out.
+ * Work is issued on cuda_stream (NULL = legacy default stream) and the call
+ * returns after it completes.  Its only scratch, the per-block partial sums
+ * and an error flag, lives in a fixed device array of 2^19 doubles (4 MiB)
+ * that every GPU loading the library holds until exit: sizes needing more
+ * than ceil(n/chunk) x (g*(3+p+q+pq+q^2+p^2)+1) <= 2^19 partial sums (chunk
+ * <= 256 observations per block) are rejected with CFUST_EINVAL.  The first
+ * call on each device looks up the scratch's device address, so make that
+ * first call before any stream capture.  All calls share the scratch and it
+ * keeps the last call's contents: calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Errors are reported through cfust_last_error(NULL). */
+cfust_status cfust_reduce_stats_noalloc(int p, int q, int g, int64_t n, const double* y,
+                                        const double* pi, const double* mu, const double* logf,
+                                        const double* u, const double* elogu, const double* eu,
+                                        const double* euu, double* tau, double* stats,
+                                        void* cuda_stream);
+
 /* Last error message of ctx (or of the last failed cfust_create when ctx is
  * NULL).  Valid until the next call on the same context. */
 const char* cfust_last_error(const cfust_ctx* ctx);

@@ -90,6 +90,8 @@ def lib():
             L.cfust_profile.restype = i
             L.cfust_debug_read.argtypes = [vp, i, vp, i64, C.POINTER(C.c_int64)]
             L.cfust_debug_read.restype = i
+            L.cfust_reduce_stats_noalloc.argtypes = [i, i, i, i64] + [vp] * 11
+            L.cfust_reduce_stats_noalloc.restype = i
             for name in ("cfust_create", "cfust_destroy", "cfust_set_data", "cfust_set_params",
                          "cfust_get_params", "cfust_estep", "cfust_get_pairs", "cfust_get_stats",
                          "cfust_mstep", "cfust_loglik", "cfust_fit", "cfust_tk_eval"):
@@ -274,6 +276,23 @@ def cfust_debug_read(ctx: Context, what, nbytes=1 << 30, dtype=np.float64):
     _check(lib().cfust_debug_read(ctx.handle, int(what), buf.ctypes.data_as(C.c_void_p),
                                   buf.nbytes, C.byref(wr)), ctx)
     return buf[: wr.value // np.dtype(dtype).itemsize]
+
+
+def cfust_reduce_stats_noalloc(p, q, g, n, y, pi, mu, logf, u, elogu, eu, euu, tau, stats,
+                               stream=None):
+    """Allocation-free reduction: all array arguments are CUDA torch tensors
+    (float64, contiguous) on the current device; tau may be None."""
+    def dp(t):
+        if t is None:
+            return None
+        if not (t.is_cuda and t.is_contiguous()) or t.element_size() != 8:
+            raise CfustError(CFUST_EINVAL, "device float64 contiguous tensors required")
+        return C.c_void_p(t.data_ptr())
+
+    st = lib().cfust_reduce_stats_noalloc(int(p), int(q), int(g), int(n), dp(y), dp(pi), dp(mu),
+                                          dp(logf), dp(u), dp(elogu), dp(eu), dp(euu), dp(tau),
+                                          dp(stats), None if stream is None else C.c_void_p(stream))
+    return _check(st, None)
 
 
 def params_from_workload(params):

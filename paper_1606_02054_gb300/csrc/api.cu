@@ -74,6 +74,8 @@ struct cfust_ctx {
 
 static thread_local std::string g_create_err;
 
+void cf_set_global_error(const std::string& msg) { g_create_err = msg; }
+
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------

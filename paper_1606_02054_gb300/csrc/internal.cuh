@@ -174,6 +174,10 @@ struct EstepArgs {
     int* flags;
 };
 
+// message returned by cfust_last_error(NULL) (calls without a context)
+#include <string>
+void cf_set_global_error(const std::string& msg);
+
 // host launchers (each issues on `st`; *launches counts kernels issued)
 cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st, long long* launches);
 cudaError_t launch_integrals(const RecSet& r, const IntegArgs& a, int fp32, int nsm,
