@@ -31,12 +31,18 @@ if ROOT not in sys.path:
 
 METRIC = "E-step obs·comp/s and EM iter/s: chosen form vs plain GPU at stated loglik err"
 UNIT = "obs·comp/s"
-# Executed warp instructions per lattice point of the FP32 integrator, per
-# dimension k, from the ncu capture in profiles/lattice_fp32_flow_p4.md
-# (smsp__inst_executed.sum / points).  None until measured.
-INSTR_PER_POINT = {3: None, 4: None}
+# Executed thread-instructions per lattice point of the FP32 lattice
+# integrator, per dimension k (smsp__inst_executed.sum x
+# smsp__thread_inst_executed_per_inst_executed.ratio / points) from the ncu
+# capture summarised in profiles/lattice_fp32_flow_p4.md.
+INSTR_PER_POINT = {3: 283.3, 4: 385.5}
+# DRAM bytes per integral record in that capture (dram__bytes_read.sum +
+# dram__bytes_write.sum of the launch / its records at n = 4,000: 64,000
+# records for k = 3, 32,000 for k = 4); the records dominate, so traffic
+# scales with the record count.
+INTEG_TRAFFIC_BYTES_PER_RECORD = {3: 2201600 / 64000, 4: 1566720 / 32000}
 SM_COUNT = 152
-SCHEDULERS_PER_SM = 4
+LANES_PER_SM = 128  # 4 sub-partitions x 32 lanes, one instruction per lane per clock
 
 
 def _peaks():
@@ -260,13 +266,16 @@ def main():
     f_sm = (clk.get("sm_mhz") or _peaks().get("sm_max_mhz", 2070.0)) * 1e6
     ipp = INSTR_PER_POINT.get(kdim) if kdim >= 3 and args.precision == "fp32" else None
     if ipp:
-        achieved = ipp * points / (dom_ms_per_launch / 1e3) / 1e9
-        peak = SM_COUNT * SCHEDULERS_PER_SM * f_sm / 1e9
+        achieved = ipp * points / (dom_ms_per_launch / 1e3) / 1e12
+        peak = SM_COUNT * LANES_PER_SM * f_sm / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "Gwarp-inst/s", "frac": achieved / peak, "traffic": None,
+                "unit": "Tinst/s", "frac": achieved / peak,
+                "traffic": INTEG_TRAFFIC_BYTES_PER_RECORD[kdim] * pairs * mult,
                 "kernel": dom, "k": kdim, "points_per_launch": points,
+                "inst_per_point": ipp, "gpoints_per_s": points / (dom_ms_per_launch / 1e3) / 1e9,
                 "ms_per_launch": dom_ms_per_launch,
-                "peak_basis": "152 SMs x 4 schedulers x 1 warp-instruction/clock at the sampled SM clock"}
+                "peak_basis": "152 SMs x 128 lanes x 1 thread-instruction/clock at the sampled "
+                              "median SM clock (issue-slot ceiling)"}
     else:
         roof = {"bound": "alu", "achieved": points / (dom_ms_per_launch / 1e3) / 1e9,
                 "peak": None, "unit": "Gpoints/s", "frac": None, "traffic": None, "kernel": dom,

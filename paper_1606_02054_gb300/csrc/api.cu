@@ -16,7 +16,7 @@
 __global__ void setup_components_kernel(Dims, Layout, const double*, const double*, const double*,
                                         const double*, double*, int*);
 __global__ void chi_table_kernel(int, const double*, Lattice, const double*, double*, float*);
-__global__ void estep_dofs_kernel(Dims, Layout, const double*, double*);
+__global__ void dof_consts_kernel(Dims, Layout, const double*, int, double*, double*, float*);
 __global__ void widen_kernel(const float*, long long, Dims, double*);
 
 
@@ -43,6 +43,8 @@ struct cfust_ctx {
     double *pi_n = nullptr, *mu_n = nullptr, *Sigma_n = nullptr, *Delta_n = nullptr, *nu_n = nullptr;
     double* F = nullptr;
     double* dofs = nullptr;
+    double* cst64 = nullptr;
+    float* cst32 = nullptr;
     double* chi64 = nullptr;
     float* chi32 = nullptr;
     double* shf64 = nullptr;
@@ -259,7 +261,7 @@ extern "C" cfust_status cfust_profile(cfust_ctx* c, double* ms, int64_t* launche
 static void free_all(cfust_ctx* c)
 {
     void* bufs[] = {c->y, c->pi, c->mu, c->Sigma, c->Delta, c->nu, c->pi_n, c->mu_n, c->Sigma_n,
-                    c->Delta_n, c->nu_n, c->F, c->dofs, c->chi64, c->chi32, c->shf64, c->shf32,
+                    c->Delta_n, c->nu_n, c->F, c->dofs, c->cst64, c->cst32, c->chi64, c->chi32, c->shf64, c->shf32,
                     c->glx64, c->glw64, c->glx32, c->glw32, c->logf, c->u, c->elogu, c->eu,
                     c->euu, c->se, c->tau, c->partial, c->stats, c->flags, c->comp_status,
                     c->stage32, c->pd, c->pc, c->fix_count, c->fix_list};
@@ -364,6 +366,8 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     ALLOC(Delta_n, (size_t)g * p * q); ALLOC(nu_n, g);
     ALLOC(F, (size_t)g * c->Ly.stride);
     ALLOC(dofs, 3 * g);
+    ALLOC(cst64, 3 * g * CST_STRIDE);
+    ALLOC(cst32, 3 * g * CST_STRIDE);
     ALLOC(chi64, ntab * NM);
     ALLOC(chi32, ntab * NM);
     ALLOC(shf64, (size_t)o.qmc_shifts * CF_MAXDIM);
@@ -525,17 +529,17 @@ static cfust_status launch_setup(cfust_ctx* c)
     setup_components_kernel<<<1, 32, 0, c->st>>>(c->D, c->Ly, c->mu, c->Sigma, c->Delta, c->nu,
                                                  c->F, c->flags);
     LAUNCHED();
-    prof_end(c, CFUST_PROF_SETUP, 1);
+    dof_consts_kernel<<<1, 64, 0, c->st>>>(c->D, c->Ly, c->F, 3 * c->g, c->dofs, c->cst64, c->cst32);
+    LAUNCHED();
+    prof_end(c, CFUST_PROF_SETUP, 2);
     if (c->q >= 3) {
         prof_begin(c, CFUST_PROF_CHI);
-        estep_dofs_kernel<<<1, 64, 0, c->st>>>(c->D, c->Ly, c->F, c->dofs);
-        LAUNCHED();
         const long long total = 3LL * c->g * c->lat.N * c->lat.M;
         const int blocks = (int)std::min<long long>((total + 127) / 128, 64LL * c->nsm);
         chi_table_kernel<<<blocks, 128, 0, c->st>>>(3 * c->g, c->dofs, c->lat, c->shf64, c->chi64,
                                                      c->chi32);
         LAUNCHED();
-        prof_end(c, CFUST_PROF_CHI, 2);
+        prof_end(c, CFUST_PROF_CHI, 1);
     }
     return CFUST_OK;
 }
@@ -543,6 +547,7 @@ static cfust_status launch_setup(cfust_ctx* c)
 static IntegArgs integ_args(const cfust_ctx* c)
 {
     IntegArgs ia;
+    ia.cst64 = c->cst64; ia.cst32 = c->cst32;
     ia.F = c->F; ia.lat = c->lat;
     ia.chi64 = c->chi64; ia.chi32 = c->chi32; ia.shf64 = c->shf64; ia.shf32 = c->shf32;
     ia.glx64 = c->glx64; ia.glw64 = c->glw64; ia.glx32 = c->glx32; ia.glw32 = c->glw32;
@@ -824,17 +829,19 @@ extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const doub
     RecSet r{};
     r.k = k;
     r.nrec = count;
-    double *dF = nullptr, *t64 = nullptr;
-    float* t32 = nullptr;
+    double *dF = nullptr, *t64 = nullptr, *k64 = nullptr;
+    float *t32 = nullptr, *k32 = nullptr;
     cudaError_t e = cudaSuccess;
     auto cleanup = [&]() {
         cudaFree(r.bt); cudaFree(r.fac); cudaFree(r.tab); cudaFree(r.dof); cudaFree(r.res);
-        cudaFree(r.se); cudaFree(dF); cudaFree(t64); cudaFree(t32);
+        cudaFree(r.se); cudaFree(dF); cudaFree(t64); cudaFree(t32); cudaFree(k64); cudaFree(k32);
     };
     if ((e = dalloc(&r.bt, bt.size())) != cudaSuccess || (e = dalloc(&r.fac, count)) != cudaSuccess ||
         (e = dalloc(&r.tab, count)) != cudaSuccess || (e = dalloc(&r.dof, count)) != cudaSuccess ||
         (e = dalloc(&r.res, count)) != cudaSuccess || (e = dalloc(&r.se, count)) != cudaSuccess ||
         (e = dalloc(&dF, fac.size())) != cudaSuccess ||
+        (e = dalloc(&k64, (size_t)count * CST_STRIDE)) != cudaSuccess ||
+        (e = dalloc(&k32, (size_t)count * CST_STRIDE)) != cudaSuccess ||
         (e = dalloc(&t64, lattice ? NM * count : 1)) != cudaSuccess ||
         (e = dalloc(&t32, lattice ? NM * count : 1)) != cudaSuccess) {
         cleanup();
@@ -846,6 +853,9 @@ extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const doub
         if ((e = cudaMemcpyAsync(r.tab, tab.data(), sizeof(int) * count, cudaMemcpyHostToDevice, c->st))) break;
         if ((e = cudaMemcpyAsync(r.dof, dofv.data(), sizeof(double) * count, cudaMemcpyHostToDevice, c->st))) break;
         if ((e = cudaMemcpyAsync(dF, fac.data(), sizeof(double) * fac.size(), cudaMemcpyHostToDevice, c->st))) break;
+        dof_consts_kernel<<<(count + 127) / 128, 128, 0, c->st>>>(c->D, c->Ly, nullptr, count, r.dof, k64, k32);
+        c->launches++;
+        if ((e = cudaGetLastError())) break;
         if (lattice) {
             const long long total = (long long)count * NM;
             const int blocks = (int)std::min<long long>((total + 127) / 128, 64LL * c->nsm);
@@ -854,6 +864,8 @@ extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const doub
             if ((e = cudaGetLastError())) break;
         }
         IntegArgs ia = integ_args(c);
+        ia.cst64 = k64;
+        ia.cst32 = k32;
         ia.F = dF;
         ia.chi64 = t64;
         ia.chi32 = t32;

@@ -96,12 +96,12 @@ __global__ void __launch_bounds__(128) combine_kernel(CombineArgs a)
 }
 
 template <typename R>
-__global__ void __launch_bounds__(128) t1_records_kernel(RecSet r)
+__global__ void __launch_bounds__(128) t1_records_kernel(RecSet r, IntegArgs a)
 {
+    const R* cst = sizeof(R) == sizeof(float) ? (const R*)a.cst32 : (const R*)a.cst64;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < r.nrec;
          i += (long long)gridDim.x * blockDim.x) {
-        const double nu = r.dof[i];
-        r.res[i] = (double)t1cdf_dev<R>((R)r.bt[i], (R)nu, (R)t1_lgb(nu));
+        r.res[i] = (double)t1cdf_dev<R>((R)r.bt[i], (R)r.dof[i], cst[r.tab[i] * CST_STRIDE + CST_LGB]);
         if (r.se) r.se[i] = 0.0;
     }
 }
@@ -135,8 +135,8 @@ cudaError_t launch_integrals(const RecSet& r, const IntegArgs& a, int fp32, int 
     if (r.k == 0 || r.nrec == 0) return cudaSuccess;
     cudaError_t e;
     if (r.k == 1) {
-        if (fp32) t1_records_kernel<float><<<grid_for(r.nrec, 128, 1 << 20), 128, 0, st>>>(r);
-        else t1_records_kernel<double><<<grid_for(r.nrec, 128, 1 << 20), 128, 0, st>>>(r);
+        if (fp32) t1_records_kernel<float><<<grid_for(r.nrec, 128, 1 << 20), 128, 0, st>>>(r, a);
+        else t1_records_kernel<double><<<grid_for(r.nrec, 128, 1 << 20), 128, 0, st>>>(r, a);
         e = cudaGetLastError();
     } else {
         // one warp per record, 8 warps per block, enough blocks to fill every SM

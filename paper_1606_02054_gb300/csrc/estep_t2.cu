@@ -8,11 +8,15 @@ __global__ void __launch_bounds__(256) t2_records_kernel(RecSet r, IntegArgs a)
     const int lane = threadIdx.x & (CF_WARP - 1);
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const R* glx = sizeof(R) == sizeof(float) ? (const R*)a.glx32 : (const R*)a.glx64;
-    const R* glw = sizeof(R) == sizeof(float) ? (const R*)a.glw32 : (const R*)a.glw64;
+    const bool f32 = sizeof(R) == sizeof(float);
+    const R* glx = f32 ? (const R*)a.glx32 : (const R*)a.glx64;
+    const R* glw = f32 ? (const R*)a.glw32 : (const R*)a.glw64;
+    const R* cst = f32 ? (const R*)a.cst32 : (const R*)a.cst64;
     for (long long i = warp; i < r.nrec; i += nwarps) {
-        const double rho = a.F[r.fac[i] + 2];  // L[1][0] of the 2 x 2 correlation factor
-        const double v = t2cdf_warp<R>(r.bt[2 * i], r.bt[2 * i + 1], rho, r.dof[i], a.t2n, glx, glw, lane);
+        const R* c = cst + r.tab[i] * CST_STRIDE;
+        const R rho = (R)a.F[r.fac[i] + 2];  // L[1][0] of the 2 x 2 correlation factor
+        const double v = t2cdf_warp<R>((R)r.bt[2 * i], (R)r.bt[2 * i + 1], rho, (R)r.dof[i], c[CST_LGB],
+                                       c[CST_LGB1], c[CST_C2], a.t2n, glx, glw, lane);
         if (lane == 0) {
             r.res[i] = v;
             if (r.se) r.se[i] = 0.0;

@@ -113,7 +113,16 @@ struct PlanArgs {
     RecSet L0, L1, L2;
 };
 
+// Per-dof constants of the T_1 / T_2 integrators, 4 per table index
+// (3h + j for the E-step, the case index for cfust_tk_eval):
+//   [0] lgamma((v+1)/2) - lgamma(v/2) - lgamma(1/2)   (T_1 at dof v)
+//   [1] the same at dof v + 1                          (inner T_1 of T_2)
+//   [2] Gamma((v+1)/2) / (Gamma(v/2) sqrt(pi))         (T_2 at dof v)
+enum { CST_LGB = 0, CST_LGB1 = 1, CST_C2 = 2, CST_STRIDE = 4 };
+
 struct IntegArgs {
+    const double* cst64;   // [tab][CST_STRIDE]
+    const float* cst32;
     const double* F;
     Lattice lat;
     const double* chi64;   // [(3h + j)][M][N] (or per case for cfust_tk_eval)

@@ -192,14 +192,30 @@ __global__ void chi_table_kernel(int ndof, const double* __restrict__ dofs, Latt
     }
 }
 
-// dofs of the E-step tables: nu_h + p + k, k = 0, 1, 2 (T_q / T_{q-2},
-// T_{q-1}, T_q at nu+p+2), read from the factor blocks.
-__global__ void estep_dofs_kernel(Dims D, Layout Ly, const double* __restrict__ F, double* dofs)
+// Degrees of freedom and T_1/T_2 constants for every table index t:
+// E-step tables t = 3h + j have dof nu_h + p + j (j = 0: T_q and T_{q-2},
+// j = 1: T_{q-1}, j = 2: T_q at nu+p+2); with F == nullptr the dofs are
+// already given (cfust_tk_eval, one index per case).
+__global__ void dof_consts_kernel(Dims D, Layout Ly, const double* __restrict__ F, int ndof,
+                                  double* dofs, double* c64, float* c32)
 {
-    const int t = threadIdx.x;
-    if (t < 3 * D.g) {
-        const int h = t / 3, k = t % 3;
-        dofs[t] = F[(size_t)h * Ly.stride + Ly.scal + SC_NU] + D.p + k;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ndof; t += gridDim.x * blockDim.x) {
+        double v;
+        if (F) {
+            const int h = t / 3, j = t % 3;
+            v = F[(size_t)h * Ly.stride + Ly.scal + SC_NU] + D.p + j;
+            dofs[t] = v;
+        } else {
+            v = dofs[t];
+        }
+        const double c[3] = {t1_lgb(v), t1_lgb(v + 1.0),
+                             exp(lgamma(0.5 * (v + 1.0)) - lgamma(0.5 * v)) / sqrt(CF_PI)};
+        for (int k = 0; k < 3; ++k) {
+            c64[t * CST_STRIDE + k] = c[k];
+            c32[t * CST_STRIDE + k] = (float)c[k];
+        }
+        c64[t * CST_STRIDE + 3] = 0.0;
+        c32[t * CST_STRIDE + 3] = 0.0f;
     }
 }
 

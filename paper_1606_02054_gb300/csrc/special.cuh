@@ -78,6 +78,18 @@ __device__ __forceinline__ double warp_sum(double v)
     return __shfl_sync(CF_FULL, v, 0);
 }
 
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(CF_FULL, v, o);
+    return __shfl_sync(CF_FULL, v, 0);
+}
+
+__device__ __forceinline__ void m_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void m_sincos(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ float m_atan(float x) { return atanf(x); }
+__device__ __forceinline__ double m_atan(double x) { return atan(x); }
+
 // ---------------------------------------------------------------------------
 // digamma (FP64): psi(x) = psi(x + k) - sum 1/(x+i) up to x >= 12, then
 // psi(x) ~ ln x - 1/(2x) - sum_{k>=1} B_{2k} / (2k x^{2k}).
@@ -176,55 +188,53 @@ __device__ __forceinline__ double t1_lgb(double nu)
 // glx/glw: n Gauss-Legendre nodes and weights on [0, 1].
 // ---------------------------------------------------------------------------
 template <typename R>
-__device__ double t2cdf_warp(double h, double k, double rho, double nu, int n,
+__device__ double t2cdf_warp(R h, R k, R rho, R nu, R lgb, R lgb1, R C2, int n,
                              const R* __restrict__ glx, const R* __restrict__ glw, int lane)
 {
-    if (rho >= 1.0) {
-        const double m = h < k ? h : k;
-        return (double)t1cdf_dev<R>((R)m, (R)nu, (R)t1_lgb(nu));
+    if (rho >= R(1)) {
+        const R m = h < k ? h : k;
+        return (double)t1cdf_dev<R>(m, nu, lgb);
     }
-    if (rho <= -1.0) {
-        const double lg = t1_lgb(nu);
-        const double v = (double)t1cdf_dev<R>((R)h, (R)nu, (R)lg) + (double)t1cdf_dev<R>((R)k, (R)nu, (R)lg) - 1.0;
-        return v > 0.0 ? v : 0.0;
+    if (rho <= R(-1)) {
+        const R v = t1cdf_dev<R>(h, nu, lgb) + t1cdf_dev<R>(k, nu, lgb) - R(1);
+        return v > R(0) ? (double)v : 0.0;
     }
-    const double sn = sqrt(nu);
+    const R sn = m_sqrt(nu);
+    const R hpi = R(0.5 * CF_PI);
     // phi_h = pi/2 + atan(h/sqrt(nu)), accurate for h << 0 as atan(sqrt(nu)/(-h))
-    const double phi_h = h < 0.0 ? atan(sn / (-h)) : 0.5 * CF_PI + atan(h / sn);
+    const R phi_h = h < R(0) ? m_atan(sn / (-h)) : hpi + m_atan(h / sn);
     bool split = false;
-    double phis = 0.0;
-    if (rho != 0.0) {
-        phis = atan2(fabs(rho) * sn, rho > 0.0 ? -k : k);
+    R phis = R(0);
+    if (rho != R(0)) {
+        phis = m_atan2(m_abs(rho) * sn, rho > R(0) ? -k : k);
         split = phis < phi_h;
     }
-    const int grade = fabs(rho) > 0.99 ? 3 : 1;
-    const double anc0 = split ? phis : phi_h;   // pieces run from the anchor to the far end
-    const double far0 = 0.0;
-    const double anc1 = phis, far1 = phi_h;
+    const bool graded = m_abs(rho) > R(0.99);
+    const R anc0 = split ? phis : phi_h;   // pieces run from the anchor to the far end
+    const R L0 = -anc0;                    // piece 0: anchor -> 0
+    const R L1 = phi_h - phis;             // piece 1: phi* -> phi_h
     const int npieces = split ? 2 : 1;
-    const R sr = (R)sqrt((nu + 1.0) / ((1.0 - rho * rho) * nu));
-    const R lgb1 = (R)t1_lgb(nu + 1.0);
-    const R nu1 = (R)(nu + 1.0), num1 = (R)(nu - 1.0);
-    const R rsn = (R)(rho * sn), kk = (R)k;
-    double acc = 0.0;
+    const R sr = m_sqrt((nu + R(1)) / ((R(1) - rho * rho) * nu));
+    const R nu1 = nu + R(1), num1 = nu - R(1);
+    const R rsn = rho * sn;
+    R acc = R(0);
     for (int t = lane; t < npieces * n; t += CF_WARP) {
-        const int piece = t >= n;
-        const int i = piece ? t - n : t;
-        const double anc = piece ? anc1 : anc0;
-        const double L = (piece ? far1 : far0) - anc;
+        const bool p1 = t >= n;
+        const int i = p1 ? t - n : t;
+        const R anc = p1 ? phis : anc0;
+        const R L = p1 ? L1 : L0;
         const R u = glx[i];
-        R um, jac;
-        if (grade == 3) { um = u * u * u; jac = R(3) * u * u; }
-        else { um = u; jac = R(1); }
-        const R ph = (R)anc + (R)L * um;
-        const R sp = m_sin(ph), cp = m_cos(ph);
-        const R z = (kk * sp + rsn * cp) * sr;
+        const R um = graded ? u * u * u : u;
+        const R jac = graded ? R(3) * u * u : R(1);
+        const R ph = anc + L * um;
+        R sp, cp;
+        m_sincos(ph, &sp, &cp);
+        const R z = (k * sp + rsn * cp) * sr;
         const R f = m_exp(num1 * m_log(sp)) * t1cdf_dev<R>(z, nu1, lgb1);
-        acc += (double)(glw[i] * jac * f) * fabs(L);
+        acc += glw[i] * jac * f * m_abs(L);
     }
     acc = warp_sum(acc);
-    const double C = exp(lgamma(0.5 * (nu + 1.0)) - lgamma(0.5 * nu)) / sqrt(CF_PI);
-    return C * acc;
+    return (double)(C2 * acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -315,7 +325,7 @@ __device__ double tk_lattice_warp(const double* bt, const double* Lc, const R* _
 #pragma unroll
     for (int r = 0; r < K; ++r) {
         b[r] = (R)bt[r];
-        invd[r] = (R)(1.0 / Lc[r * K + r]);
+        invd[r] = R(1) / (R)Lc[r * K + r];
 #pragma unroll
         for (int l = 0; l < K; ++l) Lo[r][l] = l < r ? (R)Lc[r * K + l] : R(0);
     }
@@ -328,7 +338,7 @@ __device__ double tk_lattice_warp(const double* bt, const double* Lc, const R* _
         step[d] = (int)(((long long)CF_WARP * lat.z[d]) % N);
         idx0[d] = (int)(((long long)lane * lat.z[d]) % N);
     }
-    double mean = 0.0, m2 = 0.0;  // Welford over the shift means
+    R mean = R(0), m2 = R(0);  // Welford over the shift means
     for (int m = 0; m < M; ++m) {
         R sh[K];
 #pragma unroll
@@ -371,11 +381,11 @@ __device__ double tk_lattice_warp(const double* bt, const double* Lc, const R* _
                 if (idx[d] >= N) idx[d] -= N;
             }
         }
-        const double smean = warp_sum((double)acc) / N;
-        const double delta = smean - mean;
-        mean += delta / (m + 1);
+        const R smean = warp_sum(acc) * invN;
+        const R delta = smean - mean;
+        mean += delta / R(m + 1);
         m2 += delta * (smean - mean);
     }
-    if (se) *se = M > 1 ? sqrt(m2 / (M - 1) / M) : 0.0;
-    return mean;
+    if (se) *se = M > 1 ? (double)m_sqrt(m2 / R(M - 1) / R(M)) : 0.0;
+    return (double)mean;
 }
