@@ -43,7 +43,7 @@ def build(force: bool = False) -> str:
 
 class Qmc(C.Structure):
     _fields_ = [("npoints", C.c_int), ("nshifts", C.c_int), ("korobov_a", C.c_int),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("moments", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -70,6 +70,8 @@ def lib():
             L.ora_qmc_shift.argtypes = [C.POINTER(Qmc), i, i]; L.ora_qmc_shift.restype = d
             L.ora_tkcdf.argtypes = [i, _dp, _dp, d, C.POINTER(Qmc), _dp]
             L.ora_tkcdf.restype = d
+            L.ora_tk_moments.argtypes = [i, _dp, _dp, d, C.POINTER(Qmc), _dp, _dp]
+            L.ora_tk_moments.restype = d
             L.ora_pair.argtypes = [i, i, _dp, _dp, _dp, _dp, d, C.POINTER(Qmc), _dp, _dp, _dp,
                                    _dp, _dp, _dp]
             L.ora_pair.restype = i
@@ -102,9 +104,11 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def qmc(npoints=1024, nshifts=8, korobov_a=119, seed=0):
-    """Lattice settings (both sides receive the same values as inputs)."""
-    return Qmc(int(npoints), int(nshifts), int(korobov_a), int(seed))
+def qmc(npoints=1024, nshifts=8, korobov_a=119, seed=0, moments=0):
+    """Lattice settings (both sides receive the same values as inputs);
+    moments = 1 selects the single-pass ratio estimators of the truncated-t
+    moments (q >= 3)."""
+    return Qmc(int(npoints), int(nshifts), int(korobov_a), int(seed), int(moments))
 
 
 # ---- scalar special functions -------------------------------------------------
@@ -131,6 +135,17 @@ def tkcdf(b, V, nu, spec: Qmc | None = None):
     se = C.c_double(0.0)
     v = lib().ora_tkcdf(k, _ptr(b), _ptr(V), float(nu), C.byref(spec), C.byref(se))
     return v, se.value
+
+
+def tk_moments(b, V, nu, spec: Qmc | None = None):
+    """(alpha, E[X | X <= b], E[X X^T | X <= b]) for X ~ t_k(0, V, nu), ratio estimators."""
+    b = _f64(b).ravel()
+    k = b.size
+    V = _f64(V).reshape(k, k)
+    spec = spec or qmc()
+    m1, m2 = np.zeros(k), np.zeros((k, k))
+    a = lib().ora_tk_moments(k, _ptr(b), _ptr(V), float(nu), C.byref(spec), _ptr(m1), _ptr(m2))
+    return a, m1, m2
 
 
 def pair(y, mu, Sigma, Delta, nu, spec: Qmc | None = None):

@@ -470,6 +470,74 @@ static double tk_qmc(int k, const double* b, const double* V, double nu,
     return mean;
 }
 
+/* Truncated moments of X ~ t_k(0, V, nu) given X <= b from one lattice pass.
+ * The separation of variables is run to the last coordinate as well
+ * (y_k = Phi^{-1}(w_k e_k), lattice dimension k), so every point gives a
+ * draw X = diag(V)^{1/2} L y / s inside the truncation region with weight
+ * f = prod e_i:  alpha = mean f,  E[X | X <= b] = sum f X / sum f,
+ * E[X X^T | X <= b] = sum f X X^T / sum f  (ratio estimators). */
+static double tk_moments_qmc(int k, const double* b, const double* V, double nu,
+                             const ora_qmc* qmc, const double* stab, double* m1, double* m2)
+{
+    double R[ORA_MAXQ * ORA_MAXQ], L[ORA_MAXQ * ORA_MAXQ], bt[ORA_MAXQ], dsc[ORA_MAXQ];
+    for (int i = 0; i < k; ++i) dsc[i] = 1.0 / sqrt(V[i * k + i]);
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) R[i * k + j] = V[i * k + j] * dsc[i] * dsc[j];
+    for (int i = 0; i < k; ++i) bt[i] = b[i] * dsc[i];
+    if (chol(k, R, L)) return NAN;
+    const int N = qmc->npoints, M = qmc->nshifts;
+    double sf = 0.0, sx[ORA_MAXQ], sxx[ORA_MAXQ * ORA_MAXQ];
+    memset(sx, 0, sizeof(sx));
+    memset(sxx, 0, sizeof(sxx));
+    for (int m = 0; m < M; ++m) {
+        for (int i = 0; i < N; ++i) {
+            double w, wc, s;
+            if (stab) s = stab[(size_t)m * N + i];
+            else { lattice_w(qmc, i, m, 0, &w, &wc); s = sqrt(ora_chi2_quantile(w, wc, nu) / nu); }
+            double y[ORA_MAXQ];
+            double f = 1.0;
+            for (int r = 0; r < k; ++r) {
+                double acc = bt[r] * s;
+                for (int l = 0; l < r; ++l) acc -= L[r * k + l] * y[l];
+                double e = ora_phi(acc / L[r * k + r]);
+                if (e <= 1e-300) { f = 0.0; break; }
+                f *= e;
+                lattice_w(qmc, i, m, r + 1, &w, &wc);
+                double v = w * e;
+                if (v >= 1.0) v = 1.0 - 0x1.0p-53;
+                y[r] = ora_phi_inv(v);
+            }
+            if (f == 0.0) continue;
+            /* X (standardised) = L y / s */
+            double x[ORA_MAXQ];
+            for (int r = 0; r < k; ++r) {
+                double z = 0.0;
+                for (int l = 0; l <= r; ++l) z += L[r * k + l] * y[l];
+                x[r] = z / s;
+            }
+            sf += f;
+            for (int a = 0; a < k; ++a) {
+                sx[a] += f * x[a];
+                for (int c2 = 0; c2 < k; ++c2) sxx[a * k + c2] += f * x[a] * x[c2];
+            }
+        }
+    }
+    const double alpha = sf / ((double)N * M);
+    for (int a = 0; a < k; ++a) {
+        m1[a] = sf > 0.0 ? sx[a] / sf / dsc[a] : 0.0;
+        for (int c2 = 0; c2 < k; ++c2)
+            m2[a * k + c2] = sf > 0.0 ? sxx[a * k + c2] / sf / (dsc[a] * dsc[c2]) : 0.0;
+    }
+    return alpha;
+}
+
+double ora_tk_moments(int k, const double* b, const double* V, double nu, const ora_qmc* qmc,
+                      double* m1, double* m2)
+{
+    if (k < 1 || k > ORA_MAXQ) return NAN;
+    return tk_moments_qmc(k, b, V, nu, qmc, NULL, m1, m2);
+}
+
 /* T_k(b; 0, V, nu) dispatcher; stab optional chi table for k >= 3. */
 static double tk_any(int k, const double* b, const double* V, double nu,
                      const ora_qmc* qmc, const double* stab, double* se)
@@ -611,6 +679,24 @@ static int pair_core(const comp_t* C, const ora_qmc* qmc, const double* y, int d
     if (se_out) *se_out = se_s;
     if (density_only) return 0;
 
+    if (qmc->moments && q >= 3) {
+        /* eqs (13), (16), (17) from one lattice pass at dof nu+p+2: X ~ t_q(0, S2, nu+p+2),
+         * S2 = ((nu+d)/(nu+p+2)) Lambda, truncated to X <= c; U = c - X. */
+        double S2[ORA_MAXQ * ORA_MAXQ], m1[ORA_MAXQ], m2[ORA_MAXQ * ORA_MAXQ];
+        for (int i = 0; i < q * q; ++i) S2[i] = (nu + d) / (nu + p + 2.0) * C->Lambda[i];
+        double alpha = tk_moments_qmc(q, c, S2, nu + p + 2.0, qmc, C->stab[2], m1, m2);
+        double u = (nu + p) / (nu + d) * alpha / alpha_s;
+        *u_out = u;
+        *elogu_out = u - log(0.5 * (nu + d)) - (nu + p) / (nu + d) + ora_digamma(0.5 * (nu + p));
+        for (int a = 0; a < q; ++a) eu[a] = u * (c[a] - m1[a]);
+        for (int a = 0; a < q; ++a)
+            for (int bb = 0; bb < q; ++bb) {
+                double e3 = c[a] * c[bb] - c[a] * m1[bb] - m1[a] * c[bb]
+                          + 0.5 * (m2[a * q + bb] + m2[bb * q + a]);
+                euu[a * q + bb] = u * e3;
+            }
+        return 0;
+    }
     /* eq (13): u = ((nu+p)/(nu+d)) T_q(c sqrt((nu+p+2)/(nu+d)); Lambda, nu+p+2) / alpha_s */
     double f2 = sqrt((nu + p + 2.0) / (nu + d));
     for (int k = 0; k < q; ++k) b[k] = c[k] * f2;

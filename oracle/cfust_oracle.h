@@ -42,6 +42,8 @@ typedef struct {
     int nshifts;        /* M */
     int korobov_a;      /* Korobov generator a */
     uint64_t seed;      /* SplitMix64 key for the random shifts */
+    int moments;        /* 0: truncated-t moments by the T_{q-1}/T_{q-2} recursion;
+                           1 (q >= 3): ratio estimators from the lattice pass of alpha */
 } ora_qmc;
 
 /* ---- special functions (exposed for the pin tests) ---- */
@@ -60,6 +62,13 @@ double ora_qmc_shift(const ora_qmc* qmc, int m, int d);
  * V is k x k row-major.  *se receives the QMC standard error (0 for k<=2). */
 double ora_tkcdf(int k, const double* b, const double* V, double nu,
                  const ora_qmc* qmc, double* se);
+
+/* Truncated moments of X ~ t_k(0, V, nu) given X <= b by ratio estimators
+ * on the lattice (dimension k + 1: the last coordinate is sampled too):
+ * alpha = T_k(b; 0, V, nu), m1 = E[X | X <= b] (k), m2 = E[X X^T | X <= b]
+ * (k x k).  Returns alpha. */
+double ora_tk_moments(int k, const double* b, const double* V, double nu, const ora_qmc* qmc,
+                      double* m1, double* m2);
 
 /* ---- E-step for one (observation, component) pair ----
  * Inputs are one component's parameters.  Outputs: log f_h(y) (eq 4),

@@ -194,3 +194,56 @@ def test_estep_invariants(oracle):
     # log-likelihood = sum_j log sum_h pi_h f_h (eq 27)
     lse = sp.logsumexp(np.log(w["truth"]["pi"])[:, None] + e["logf"], axis=0).sum()
     assert abs(e["loglik"] - lse) < 1e-9 * abs(lse)
+
+
+# ---------------------------------------------------------------------------
+# single-pass (ratio-estimator) truncated-t moments, q >= 3
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("q", [3, 4])
+def test_single_pass_moments_match_recursion(oracle, q):
+    rng = np.random.default_rng(30 + q)
+    p = q
+    Sigma = _rand_spd(rng, p)
+    Delta = rng.normal(0, 1.0, (p, q))
+    nu = 6.5
+    big = oracle.qmc(16384, 16, 5693, 11, 1)
+    for _ in range(3):
+        y = rng.normal(0, 1.5, p)
+        rec = oracle.pair(y, np.zeros(p), Sigma, Delta, nu, oracle.qmc(16384, 16, 5693, 11, 0))
+        sp1 = oracle.pair(y, np.zeros(p), Sigma, Delta, nu, big)
+        assert abs(sp1["u"] - rec["u"]) <= 1e-12 * rec["u"] and sp1["logf"] == rec["logf"]
+        scale = np.abs(rec["euu"]).max()
+        assert np.abs(sp1["eu"] - rec["eu"]).max() <= 2e-3 * np.abs(rec["eu"]).max()
+        assert np.abs(sp1["euu"] - rec["euu"]).max() <= 3e-3 * scale
+
+
+def test_single_pass_moments_are_psd_everywhere(oracle):
+    from paper_1606_02054_gb300 import synth
+
+    w = synth.make_workload("flow_p4", n=40, with_init=False)
+    e = oracle.estep(w["y"], w["truth"], oracle.qmc(**dict(w["qmc"], moments=1)))
+    g, n, q = e["eu"].shape
+    for h in range(g):
+        for j in range(n):
+            C = e["u"][h, j] * e["euu"][h, j] - np.outer(e["eu"][h, j], e["eu"][h, j])
+            # a weighted covariance of lattice draws: PSD up to rounding, also far in the tail
+            assert np.linalg.eigvalsh(C).min() >= -1e-9 * max(np.abs(C).max(), 1e-300), (h, j)
+
+
+def test_single_pass_delta_zero(oracle):
+    # Delta = 0: E[W U] = u s 2 sqrt(m) G((m+1)/2)/(sqrt(pi)(m-1)G(m/2)), E[W U U^T] = I + (2/pi)(11^T - I)
+    p = q = 4
+    rng = np.random.default_rng(44)
+    S = _rand_spd(rng, p)
+    nu = 5.7
+    y = rng.normal(0, 2, p)
+    r = oracle.pair(y, np.zeros(p), S, np.zeros((p, q)), nu, oracle.qmc(4096, 16, 1517, 3, 1))
+    d = float(y @ np.linalg.solve(S, y))
+    u = (nu + p) / (nu + d)
+    m = nu + p + 2
+    s = math.sqrt((nu + d) / m)
+    e1 = u * s * 2 * math.sqrt(m) * math.exp(sp.gammaln((m + 1) / 2) - sp.gammaln(m / 2)) \
+        / (math.sqrt(math.pi) * (m - 1))
+    assert np.allclose(r["eu"], e1, rtol=5e-3)
+    E2 = np.eye(q) + (2 / math.pi) * (np.ones((q, q)) - np.eye(q))
+    assert np.allclose(r["euu"], E2, rtol=1e-2, atol=1e-2)
