@@ -34,13 +34,15 @@ UNIT = "obs·comp/s"
 # Executed thread-instructions per lattice point of the FP32 lattice
 # integrator, per dimension k (smsp__inst_executed.sum x
 # smsp__thread_inst_executed_per_inst_executed.ratio / points) from the ncu
-# capture summarised in profiles/lattice_fp32_flow_p4.md.
-INSTR_PER_POINT = {3: 283.3, 4: 385.5}
+# captures summarised in profiles/lattice_fp32_flow_p4.md and
+# profiles/moments_fp32_flow_p4.md.
+INSTR_PER_POINT = {("lattice", 3): 283.3, ("lattice", 4): 385.5, ("moments", 4): 465.8}
 # DRAM bytes per integral record in that capture (dram__bytes_read.sum +
 # dram__bytes_write.sum of the launch / its records at n = 4,000: 64,000
-# records for k = 3, 32,000 for k = 4); the records dominate, so traffic
+# records for k = 3, 32,000 for k = 4, 16,000 moment records); the records dominate, so traffic
 # scales with the record count.
-INTEG_TRAFFIC_BYTES_PER_RECORD = {3: 2201600 / 64000, 4: 1566720 / 32000}
+INTEG_TRAFFIC_BYTES_PER_RECORD = {("lattice", 3): 2201600 / 64000, ("lattice", 4): 1566720 / 32000,
+                                  ("moments", 4): 815872 / 16000}
 SM_COUNT = 152
 LANES_PER_SM = 128  # 4 sub-partitions x 32 lanes, one instruction per lane per clock
 
@@ -107,20 +109,21 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _opts(cf, w, precision, profile=0, stream=None):
+def _opts(cf, w, precision, profile=0, stream=None, moments=1):
     q = w["qmc"]
     return cf.cfust_default_opts(precision=precision, qmc_points=q["npoints"],
                                  qmc_shifts=q["nshifts"], qmc_korobov_a=q["korobov_a"],
                                  seed=q["seed"], profile=profile,
-                                 cuda_stream=stream)
+                                 cuda_stream=stream, moments=moments)
 
 
-def cpu_baseline(w, nsample, steps=1):
-    """The FP64 oracle, as it stands, on `nsample` observations of the workload."""
+def cpu_baseline(w, nsample, steps=1, moments=1):
+    """The FP64 oracle, as it stands, on `nsample` observations of the workload
+    (same moment reading as the timed GPU form)."""
     import oracle
 
     sub = w["y"][:nsample]
-    spec = oracle.qmc(**w["qmc"])
+    spec = oracle.qmc(**dict(w["qmc"], moments=moments))
     cores = os.cpu_count() or 1
     params = {k: np.array(v, dtype=float) for k, v in w["init"].items()}
     t0 = time.perf_counter()
@@ -141,7 +144,7 @@ def run_reference(args, w, rank, world):
     nsample = args.ref_sample
     per = []
     for i in range(args.warmup + args.steps):
-        b = cpu_baseline(w, nsample, 1)
+        b = cpu_baseline(w, nsample, 1, 1 if args.moments == "single-pass" else 0)
         if i >= args.warmup:
             per.append(b["ms_per_step"])
     ms = float(np.mean(per))
@@ -169,6 +172,9 @@ def main():
     ap.add_argument("--workload", default="flow_p4")
     ap.add_argument("--n", type=int, default=None, help="override the workload size")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--moments", choices=["single-pass", "recursion"], default="single-pass",
+                    help="truncated-t moments of the timed form (the plain recursion is "
+                         "also timed when single-pass is chosen)")
     ap.add_argument("--ref-sample", type=int, default=160)
     ap.add_argument("--cpu-sample", type=int, default=240)
     ap.add_argument("--no-e2e", action="store_true")
@@ -193,7 +199,7 @@ def main():
     # CPU baseline first (in-process OpenMP threads; no fork after CUDA init)
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, args.cpu_sample, 1)
+        cpu = cpu_baseline(w, args.cpu_sample, 1, 1 if args.moments == "single-pass" else 0)
 
     torch.cuda.set_device(local)
     dist = None
@@ -209,68 +215,85 @@ def main():
 
     prec = cf.CFUST_PREC_FP32 if args.precision == "fp32" else cf.CFUST_PREC_FP64
     stream = torch.cuda.current_stream()
-    ctx = cf.cfust_create(w["p"], w["q"], w["g"], w["n"],
-                          _opts(cf, w, prec, profile=1, stream=stream.cuda_stream))
     y_dev = torch.tensor(w["y"], dtype=torch.float64, device="cuda")
-    cf.cfust_set_data(ctx, y_dev)
-    cf.cfust_set_params(ctx, w["init"])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    def step():
-        L = cf.cfust_estep(ctx)
-        cf.cfust_mstep(ctx)
-        return L
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    cf.cfust_profile(ctx, reset=True)
-    n_launch0 = cf.cfust_launch_count(ctx)
-    clocks = Clocks(local)
-    clocks.start()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    total_ms = 0.0
-    lls = []
-    for _ in range(args.steps):
-        flush.fill_(1.0)  # evict L2 before each timed step
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        lls.append(step())
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-    launches = cf.cfust_launch_count(ctx) - n_launch0
-    prof = cf.cfust_profile(ctx)
-    ms = total_ms / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     pairs = w["n"] * w["g"]
+
+    def measure(moments, with_clocks):
+        """warm-up, then `steps` timed EM iterations (CUDA events per step, L2
+        flushed before each); returns timings and the library's kernel profile."""
+        ctx = cf.cfust_create(w["p"], w["q"], w["g"], w["n"],
+                              _opts(cf, w, prec, profile=1, stream=stream.cuda_stream,
+                                    moments=moments))
+        cf.cfust_set_data(ctx, y_dev)
+        cf.cfust_set_params(ctx, w["init"])
+
+        def step():
+            L = cf.cfust_estep(ctx)
+            cf.cfust_mstep(ctx)
+            return L
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        cf.cfust_profile(ctx, reset=True)
+        n0 = cf.cfust_launch_count(ctx)
+        clocks = Clocks(local) if with_clocks else None
+        if clocks:
+            clocks.start()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        total_ms, lls = 0.0, []
+        for _ in range(args.steps):
+            flush.fill_(1.0)  # evict L2 before each timed step
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lls.append(step())
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clk = clocks.stop() if clocks else None
+        launches = cf.cfust_launch_count(ctx) - n0
+        prof = cf.cfust_profile(ctx)
+        ms = total_ms / args.steps
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        estep_ms = sum(v[0] for k, v in prof.items() if k != "mstep") / args.steps
+        return dict(ms=ms, prof=prof, launches=launches, ll=lls[-1], clk=clk, estep_ms=estep_ms)
+
+    chosen_moments = 1 if args.moments == "single-pass" else 0
+    main_run = measure(chosen_moments, True)
+    plain_run = measure(0, False) if chosen_moments == 1 and w["q"] >= 3 else None
+    ms, prof, clk = main_run["ms"], main_run["prof"], main_run["clk"]
+    launches = main_run["launches"]
     value = pairs * world / (ms / 1e3)
 
     # dominant kernel class and its roofline
-    lat_classes = [k for k in ("level0_Tq", "level1_Tq-1", "level2_Tq-2") if prof[k][1] > 0]
+    cls = {"level0_Tq": ("lattice", w["q"], 1 if chosen_moments and w["q"] >= 3 else 2),
+           "level1_Tq-1": ("lattice", w["q"] - 1, w["q"]),
+           "level2_Tq-2": ("lattice", w["q"] - 2, w["q"] * (w["q"] - 1)),
+           "moments_Tq": ("moments", w["q"], 1)}
+    lat_classes = [k for k in cls if prof[k][1] > 0 and cls[k][1] >= 2]
     dom = max(lat_classes, key=lambda k: prof[k][0])
     dom_ms_per_launch = prof[dom][0] / prof[dom][1]
-    kdim = {"level0_Tq": w["q"], "level1_Tq-1": w["q"] - 1, "level2_Tq-2": w["q"] - 2}[dom]
-    mult = {"level0_Tq": 2, "level1_Tq-1": w["q"], "level2_Tq-2": w["q"] * (w["q"] - 1)}[dom]
+    kind, kdim, mult = cls[dom]
     points = pairs * mult * w["qmc"]["npoints"] * w["qmc"]["nshifts"]
     f_sm = (clk.get("sm_mhz") or _peaks().get("sm_max_mhz", 2070.0)) * 1e6
-    ipp = INSTR_PER_POINT.get(kdim) if kdim >= 3 and args.precision == "fp32" else None
+    ipp = INSTR_PER_POINT.get((kind, kdim)) if args.precision == "fp32" else None
     if ipp:
         achieved = ipp * points / (dom_ms_per_launch / 1e3) / 1e12
         peak = SM_COUNT * LANES_PER_SM * f_sm / 1e12
+        tb = INTEG_TRAFFIC_BYTES_PER_RECORD.get((kind, kdim))
         roof = {"bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "Tinst/s", "frac": achieved / peak,
-                "traffic": INTEG_TRAFFIC_BYTES_PER_RECORD[kdim] * pairs * mult,
+                "traffic": tb * pairs * mult if tb else None,
                 "kernel": dom, "k": kdim, "points_per_launch": points,
                 "inst_per_point": ipp, "gpoints_per_s": points / (dom_ms_per_launch / 1e3) / 1e9,
                 "ms_per_launch": dom_ms_per_launch,
@@ -285,7 +308,8 @@ def main():
     e2e = None
     if not args.no_e2e:
         p, q, g = w["p"], w["q"], w["g"]
-        ctx2 = cf.cfust_create(p, q, g, w["n"], _opts(cf, w, prec, stream=stream.cuda_stream))
+        ctx2 = cf.cfust_create(p, q, g, w["n"], _opts(cf, w, prec, stream=stream.cuda_stream,
+                                                      moments=chosen_moments))
         y_host = np.ascontiguousarray(w["y"])
         params = {k: np.array(v, dtype=float) for k, v in w["init"].items()}
         pbytes = 8 * (g + g * p + g * p * p + g * p * q + g)
@@ -314,23 +338,32 @@ def main():
                "d2h_bytes_per_step": int(pbytes + 8 + 4 + 4 * g), "ms_per_step": e2e_ms}
 
     if rank == 0:
-        estep_ms = sum(prof[k][0] for k in prof if k != "mstep") / args.steps
+        form = ("single-pass moments" if chosen_moments and w["q"] >= 3 else "moment recursion")
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
                 "config": {"workload": w["name"], "n": w["n"], "p": w["p"], "q": w["q"],
                            "g": w["g"], "qmc": f"{w['qmc']['npoints']}x{w['qmc']['nshifts']}",
+                           "form": form,
                            "precision": f"{args.precision} lattice/quadrature integrals, "
                                         "fp64 whitening, densities, tau, loglik, statistics, M-step",
                            "l2": "flushed (256 MB write) before every timed step",
                            "parallelism": f"replicas x{world}"},
                 "em_iter_per_s": 1e3 / ms,
-                "estep_obs_comp_per_s": pairs * world / (estep_ms / 1e3),
-                "loglik_last": lls[-1],
+                "estep_obs_comp_per_s": pairs * world / (main_run["estep_ms"] / 1e3),
+                "loglik_last": main_run["ll"],
                 "gpu_launches": int(launches),
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
                 "roofline": roof, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+        if plain_run:
+            line["plain_gpu"] = {
+                "form": "moment recursion (T_q, T_{q-1}, T_{q-2} records)",
+                "value": pairs * world / (plain_run["ms"] / 1e3), "unit": UNIT,
+                "ms_per_step": plain_run["ms"], "em_iter_per_s": 1e3 / plain_run["ms"],
+                "estep_obs_comp_per_s": pairs * world / (plain_run["estep_ms"] / 1e3),
+                "loglik_last": plain_run["ll"], "gpu_launches": int(plain_run["launches"]),
+                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in plain_run["prof"].items()}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -73,6 +73,12 @@ typedef struct {
                             (0: 64 in FP64 mode, 32 in FP32 mode) */
     int profile;         /* 1: time every kernel class with CUDA events on the context
                             stream (read with cfust_profile); 0 (default): off */
+    int moments;         /* truncated-t moments of eqs (16)-(17) for q >= 3:
+                            0 (default): exact recursion through T_{q-1} and T_{q-2};
+                            1: ratio estimators E[X], E[X X^T] from the lattice pass of
+                               alpha (eq 13) that also samples the last coordinate
+                               (one integral per pair instead of 1 + q + q(q-1)).
+                            q <= 2 always uses the recursion. */
 } cfust_opts;
 
 /* Kernel classes reported by cfust_profile. */
@@ -83,6 +89,7 @@ enum {
     CFUST_PROF_LEVEL0,      /* T_q of eqs (4) and (13) */
     CFUST_PROF_LEVEL1,      /* T_{q-1} of the truncated-t first moments */
     CFUST_PROF_LEVEL2,      /* T_{q-2} of the truncated-t second moments */
+    CFUST_PROF_MOMENTS,     /* alpha with single-pass moments (opts.moments = 1) */
     CFUST_PROF_COMBINE,     /* eqs (4), (13), (15)-(17) from the integrals */
     CFUST_PROF_FIXUP,       /* FP64 re-evaluation of far-tail pairs (FP32 mode) */
     CFUST_PROF_REDUCE,      /* eqs (12), (27) and the tau-weighted statistics */

@@ -30,7 +30,7 @@ CFUST_PREC_FP64, CFUST_PREC_FP32 = 0, 1
 CFUST_F32, CFUST_F64 = 0, 1
 # kernel classes of cfust_profile
 PROF_NAMES = ("setup", "chi_table", "plan", "level0_Tq", "level1_Tq-1", "level2_Tq-2",
-              "combine", "fixup_fp64", "reduce", "mstep")
+              "moments_Tq", "combine", "fixup_fp64", "reduce", "mstep")
 CFUST_NPROF = len(PROF_NAMES)
 
 
@@ -44,7 +44,7 @@ class cfust_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("qmc_points", C.c_int), ("qmc_shifts", C.c_int),
                 ("qmc_korobov_a", C.c_int), ("seed", C.c_uint64), ("nu_min", C.c_double),
                 ("nu_max", C.c_double), ("device", C.c_int), ("cuda_stream", C.c_void_p),
-                ("t2_nodes", C.c_int), ("profile", C.c_int)]
+                ("t2_nodes", C.c_int), ("profile", C.c_int), ("moments", C.c_int)]
 
 
 class cfust_params(C.Structure):

@@ -58,7 +58,8 @@ struct cfust_ctx {
     float* stage32 = nullptr;
     // E-step pipeline: per-pair (d, log t_p) and c, integral records per level
     double *pd = nullptr, *pc = nullptr;
-    RecSet rec[3]{};
+    RecSet rec[4]{};  // levels 0, 1, 2 and the single-pass moment records
+    bool single_pass = false;
     int *fix_count = nullptr, *fix_list = nullptr;
     // optional per-kernel-class timing (opts.profile)
     cudaEvent_t ev[CFUST_NPROF][2]{};
@@ -268,7 +269,7 @@ static void free_all(cfust_ctx* c)
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (RecSet& r : c->rec) {
-        void* rb[] = {r.bt, r.fac, r.tab, r.dof, r.res, r.se};
+        void* rb[] = {r.bt, r.fac, r.tab, r.dof, r.res, r.se, r.mom};
         for (void* b : rb)
             if (b) cudaFree(b);
     }
@@ -311,12 +312,15 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
         return fail(nullptr, CFUST_EINVAL, "cfust_create: need 0 < nu_min <= nu_max");
     if (o.t2_nodes != 0 && (o.t2_nodes < 8 || o.t2_nodes > 64))
         return fail(nullptr, CFUST_EINVAL, "cfust_create: t2_nodes must be 0 or in [8, 64]");
+    if (o.moments != 0 && o.moments != 1)
+        return fail(nullptr, CFUST_EINVAL, "cfust_create: moments must be 0 or 1");
     cudaError_t e = cudaSetDevice(o.device);
     if (e != cudaSuccess)
         return fail(nullptr, CFUST_ECUDA, std::string("cfust_create: cudaSetDevice: ") + cudaGetErrorString(e));
 
     c = new cfust_ctx();
     c->p = p; c->q = q; c->g = g; c->n = n;
+    c->single_pass = o.moments == 1 && q >= 3;
     c->opts = o;
     c->st = (cudaStream_t)o.cuda_stream;
     c->D = Dims{p, q, g, (long long)n};
@@ -381,9 +385,11 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     ALLOC(pd, 2 * ng); ALLOC(pc, ng * q);
     ALLOC(fix_count, 1); ALLOC(fix_list, ng);
     {
-        const int kdim[3] = {q, q - 1, q - 2};
-        const long long mult[3] = {2, q >= 2 ? q : 0, q >= 3 ? (long long)q * (q - 1) : 0};
-        for (int l = 0; l < 3; ++l) {
+        const bool sp = c->single_pass;
+        const int kdim[4] = {q, q - 1, q - 2, q};
+        const long long mult[4] = {2, (!sp && q >= 2) ? q : 0,
+                                   (!sp && q >= 3) ? (long long)q * (q - 1) : 0, sp ? 1 : 0};
+        for (int l = 0; l < 4; ++l) {
             RecSet& r = c->rec[l];
             r.k = kdim[l] > 0 ? kdim[l] : 0;
             r.nrec = r.k > 0 ? (long long)ng * mult[l] : 0;
@@ -392,6 +398,7 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
             ALLOC(rec[l].fac, nr); ALLOC(rec[l].tab, nr);
             ALLOC(rec[l].dof, nr); ALLOC(rec[l].res, nr);
             if (l == 0) { ALLOC(rec[l].se, nr); }
+            if (l == 3) { ALLOC(rec[l].mom, nr * (q + q * (q + 1) / 2)); }
         }
     }
 #undef ALLOC
@@ -559,11 +566,13 @@ static IntegArgs integ_args(const cfust_ctx* c)
 static cfust_status launch_pairs(cfust_ctx* c, int density_only)
 {
     const int fp32 = c->opts.precision == CFUST_PREC_FP32;
+    const int sp = c->single_pass ? 1 : 0;
     PlanArgs pa;
     pa.D = c->D; pa.Ly = c->Ly; pa.y = c->y; pa.F = c->F; pa.density_only = density_only;
+    pa.single_pass = sp;
     pa.pd = c->pd; pa.pc = c->pc;
-    pa.L0 = c->rec[0]; pa.L1 = c->rec[1]; pa.L2 = c->rec[2];
-    if (density_only) pa.L0.nrec = c->n * c->g;
+    pa.L0 = c->rec[0]; pa.L1 = c->rec[1]; pa.L2 = c->rec[2]; pa.LM = c->rec[3];
+    if (density_only || sp) pa.L0.nrec = c->n * c->g;
     cudaError_t e;
     long long n0 = c->launches;
     prof_begin(c, CFUST_PROF_PLAN);
@@ -571,7 +580,7 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
         return fail(c, CFUST_ECUDA, std::string("plan kernel: ") + cudaGetErrorString(e));
     prof_end(c, CFUST_PROF_PLAN, c->launches - n0);
     const IntegArgs ia = integ_args(c);
-    for (int l = 0; l < (density_only ? 1 : 3); ++l) {
+    for (int l = 0; l < (density_only || sp ? 1 : 3); ++l) {
         RecSet r = l == 0 ? pa.L0 : c->rec[l];
         n0 = c->launches;
         prof_begin(c, CFUST_PROF_LEVEL0 + l);
@@ -579,11 +588,18 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
             return fail(c, CFUST_ECUDA, std::string("integral kernel: ") + cudaGetErrorString(e));
         prof_end(c, CFUST_PROF_LEVEL0 + l, c->launches - n0);
     }
+    if (sp && !density_only) {
+        n0 = c->launches;
+        prof_begin(c, CFUST_PROF_MOMENTS);
+        if ((e = launch_moments(c->rec[3], ia, fp32, c->nsm, c->st, &c->launches)) != cudaSuccess)
+            return fail(c, CFUST_ECUDA, std::string("moment kernel: ") + cudaGetErrorString(e));
+        prof_end(c, CFUST_PROF_MOMENTS, c->launches - n0);
+    }
     if (fp32) CU(cudaMemsetAsync(c->fix_count, 0, sizeof(int), c->st));
     CombineArgs ca;
     ca.D = c->D; ca.Ly = c->Ly; ca.F = c->F; ca.pd = c->pd; ca.pc = c->pc;
-    ca.L0 = pa.L0; ca.L1 = c->rec[1]; ca.L2 = c->rec[2];
-    ca.density_only = density_only; ca.fp32 = fp32;
+    ca.L0 = pa.L0; ca.L1 = c->rec[1]; ca.L2 = c->rec[2]; ca.LM = c->rec[3];
+    ca.density_only = density_only; ca.single_pass = sp; ca.fp32 = fp32;
     ca.logf = c->logf; ca.u = c->u; ca.elogu = c->elogu; ca.eu = c->eu; ca.euu = c->euu; ca.se = c->se;
     ca.fix_count = c->fix_count; ca.fix_list = c->fix_list; ca.flags = c->flags;
     n0 = c->launches;
@@ -600,6 +616,7 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
         a.glx64 = c->glx64; a.glw64 = c->glw64; a.glx32 = c->glx32; a.glw32 = c->glw32;
         a.t2n = c->t2n;
         a.density_only = density_only;
+        a.single_pass = sp;
         a.logf = c->logf; a.u = c->u; a.elogu = c->elogu; a.eu = c->eu; a.euu = c->euu; a.se = c->se;
         a.flags = c->flags;
         n0 = c->launches;

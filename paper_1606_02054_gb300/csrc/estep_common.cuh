@@ -187,3 +187,32 @@ __device__ inline void pair_assemble(const double* F, const Layout& Ly, int p, i
             o.euu[b * q + a] = v;
         }
 }
+
+// Single-pass reading of eqs (13), (16), (17): alpha and the standardised
+// moments m = (E[X~], lower triangle of E[X~ X~^T]) of the truncated
+// X ~ t_q(0, S2, nu+p+2), S2 = ((nu+d)/(nu+p+2)) Lambda, X <= c, come from one
+// lattice pass; X = sigma * X~ with sigma_i = sqrt(S2_ii); U = c - X.
+__device__ inline void pair_assemble_sp(const double* F, const Layout& Ly, int p, int q,
+                                        const double* c, double d, double logtp, double alpha_s,
+                                        double alpha, const double* m, PairOut& o)
+{
+    const double nu = F[Ly.scal + SC_NU], nu1 = nu + p;
+    o.logf = q * 0.6931471805599453 + logtp + log(alpha_s);  // eq (4)
+    const double u = nu1 / (nu + d) * alpha / alpha_s;        // eq (13)
+    o.u = u;
+    o.elogu = u - log(0.5 * (nu + d)) - nu1 / (nu + d) + F[Ly.scal + SC_PSI];  // eq (15)
+    const double sc = sqrt((nu + d) / (nu1 + 2.0));
+    double sig[CF_MAXQ], m1[CF_MAXQ];
+    for (int a = 0; a < q; ++a) {
+        sig[a] = sc / F[Ly.dq + a];
+        m1[a] = sig[a] * m[a];
+        o.eu[a] = u * (c[a] - m1[a]);  // eq (16)
+    }
+    for (int a = 0; a < q; ++a)
+        for (int b = 0; b <= a; ++b) {  // eq (17)
+            const double m2 = sig[a] * sig[b] * m[q + a * (a + 1) / 2 + b];
+            const double v = u * (c[a] * c[b] - c[a] * m1[b] - m1[a] * c[b] + m2);
+            o.euu[a * q + b] = v;
+            o.euu[b * q + a] = v;
+        }
+}

@@ -34,6 +34,8 @@ __global__ void __launch_bounds__(128) fixup_kernel(EstepArgs a, const int* coun
     const int p = a.D.p, q = a.D.q, q1 = q - 1, q2 = q - 2;
     const int cnt = *count;
     const size_t NM = (size_t)a.lat.N * a.lat.M;
+    __shared__ double slot[4][CF_MAXQ + CF_MAXQ * (CF_MAXQ + 1) / 2 + 1];
+    double* acc = slot[threadIdx.x >> 5];
     for (int i = warp; i < cnt; i += nwarps) {
         const long long pid = list[i];
         const int h = (int)(pid / a.D.n);
@@ -46,6 +48,32 @@ __global__ void __launch_bounds__(128) fixup_kernel(EstepArgs a, const int* coun
         limits_l0(F, a.Ly, p, q, c, d, 0, bt);
         const double alpha_s = tk_fp64(q, bt, F + fac_l0(a.Ly), nu1, chi, a, lane, &se);
         double alpha = 0.0, tq1[CF_MAXQ], tq2[CF_MAXQ * CF_MAXQ];
+        if (a.single_pass && !a.density_only) {
+            double m[CF_MAXQ + CF_MAXQ * (CF_MAXQ + 1) / 2];
+            limits_l0(F, a.Ly, p, q, c, d, 1, bt);
+            const double* Lq = F + fac_l0(a.Ly);
+            const double* chi2 = chi + 2 * NM;
+            switch (q) {
+            case 3: alpha = tk_lattice_mom_warp<double, 3>(bt, Lq, chi2, a.shf64, a.lat, lane, m, m + 3, acc); break;
+            case 4: alpha = tk_lattice_mom_warp<double, 4>(bt, Lq, chi2, a.shf64, a.lat, lane, m, m + 4, acc); break;
+            case 5: alpha = tk_lattice_mom_warp<double, 5>(bt, Lq, chi2, a.shf64, a.lat, lane, m, m + 5, acc); break;
+            case 6: alpha = tk_lattice_mom_warp<double, 6>(bt, Lq, chi2, a.shf64, a.lat, lane, m, m + 6, acc); break;
+            case 7: alpha = tk_lattice_mom_warp<double, 7>(bt, Lq, chi2, a.shf64, a.lat, lane, m, m + 7, acc); break;
+            default: alpha = tk_lattice_mom_warp<double, 8>(bt, Lq, chi2, a.shf64, a.lat, lane, m, m + 8, acc); break;
+            }
+            PairOut o;
+            pair_assemble_sp(F, a.Ly, p, q, c, d, logtp, alpha_s, alpha, m, o);
+            if (lane == 0) {
+                a.logf[pid] = o.logf;
+                if (a.se) a.se[pid] = se;
+                if (!isfinite(o.logf)) atomicOr(a.flags, KF_NAN);
+                a.u[pid] = o.u;
+                a.elogu[pid] = o.elogu;
+                for (int k = 0; k < q; ++k) a.eu[pid * q + k] = o.eu[k];
+                for (int k = 0; k < q * q; ++k) a.euu[pid * q * q + k] = o.euu[k];
+            }
+            continue;
+        }
         if (!a.density_only) {
             limits_l0(F, a.Ly, p, q, c, d, 1, bt);
             alpha = tk_fp64(q, bt, F + fac_l0(a.Ly), nu1 + 2.0, chi + 2 * NM, a, lane, nullptr);

@@ -1,0 +1,42 @@
+// estep_mom32.cu -- lattice T_k with truncated moments (single-pass ratio
+// estimators), k = 3..8, in float: warp per record, lattice points over lanes
+// (see tk_lattice_mom_warp in special.cuh).
+#include "internal.cuh"
+#include "special.cuh"
+
+template <int K>
+__global__ void __launch_bounds__(256) lattice_mom_kernel_32(RecSet r, IntegArgs a)
+{
+    constexpr int W = K + K * (K + 1) / 2;
+    const int lane = threadIdx.x & (CF_WARP - 1);
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const size_t NM = (size_t)a.lat.N * a.lat.M;
+    __shared__ double slot[8][W + 1];
+    double* acc = slot[threadIdx.x >> 5];
+    for (long long i = warp; i < r.nrec; i += nwarps) {
+        double bt[K], m[W];
+#pragma unroll
+        for (int k = 0; k < K; ++k) bt[k] = r.bt[i * K + k];
+        const double v = tk_lattice_mom_warp<float, K>(bt, a.F + r.fac[i], a.chi32 + (size_t)r.tab[i] * NM,
+                                                      a.shf32, a.lat, lane, m, m + K, acc);
+        if (lane == 0) {
+            r.res[i] = v;
+            for (int k = 0; k < W; ++k) r.mom[i * W + k] = m[k];
+        }
+    }
+}
+
+cudaError_t launch_mom32(int k, const RecSet& r, const IntegArgs& a, int blocks, cudaStream_t st)
+{
+    switch (k) {
+    case 3: lattice_mom_kernel_32<3><<<blocks, 256, 0, st>>>(r, a); break;
+    case 4: lattice_mom_kernel_32<4><<<blocks, 256, 0, st>>>(r, a); break;
+    case 5: lattice_mom_kernel_32<5><<<blocks, 256, 0, st>>>(r, a); break;
+    case 6: lattice_mom_kernel_32<6><<<blocks, 256, 0, st>>>(r, a); break;
+    case 7: lattice_mom_kernel_32<7><<<blocks, 256, 0, st>>>(r, a); break;
+    case 8: lattice_mom_kernel_32<8><<<blocks, 256, 0, st>>>(r, a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}

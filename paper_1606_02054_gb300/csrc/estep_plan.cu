@@ -11,7 +11,7 @@ __global__ void __launch_bounds__(128) plan_kernel(PlanArgs a)
 {
     const int p = a.D.p, q = a.D.q;
     const long long np = a.D.n * a.D.g;
-    const int m0 = a.density_only ? 1 : 2;
+    const int m0 = (a.density_only || a.single_pass) ? 1 : 2;
     for (long long pid = blockIdx.x * (long long)blockDim.x + threadIdx.x; pid < np;
          pid += (long long)gridDim.x * blockDim.x) {
         const int h = (int)(pid / a.D.n);
@@ -34,6 +34,15 @@ __global__ void __launch_bounds__(128) plan_kernel(PlanArgs a)
             a.L0.dof[rec] = nu1 + 2.0 * w;
         }
         if (a.density_only) continue;
+        if (a.single_pass) {
+            // alpha and the moments: one record at dof nu+p+2 (limits of eq 13)
+            limits_l0(F, a.Ly, p, q, c, d, 1, bt);
+            for (int k = 0; k < q; ++k) a.LM.bt[pid * q + k] = bt[k];
+            a.LM.fac[pid] = foff + fac_l0(a.Ly);
+            a.LM.tab[pid] = 3 * h + 2;
+            a.LM.dof[pid] = nu1 + 2.0;
+            continue;
+        }
         const int q1 = q - 1, q2 = q - 2;
         for (int r = 0; r < q && q1 > 0; ++r) {
             const long long rec = pid * q + r;
@@ -58,8 +67,9 @@ __global__ void __launch_bounds__(128) combine_kernel(CombineArgs a)
 {
     const int p = a.D.p, q = a.D.q;
     const long long np = a.D.n * a.D.g;
-    const int m0 = a.density_only ? 1 : 2;
+    const int m0 = (a.density_only || a.single_pass) ? 1 : 2;
     const int q1 = q - 1;
+    const int W = q + q * (q + 1) / 2;
     for (long long pid = blockIdx.x * (long long)blockDim.x + threadIdx.x; pid < np;
          pid += (long long)gridDim.x * blockDim.x) {
         const int h = (int)(pid / a.D.n);
@@ -75,15 +85,19 @@ __global__ void __launch_bounds__(128) combine_kernel(CombineArgs a)
             a.fix_list[slot] = (int)pid;
             continue;
         }
-        const double alpha = a.density_only ? 0.0 : a.L0.res[pid * m0 + 1];
-        double tq1[CF_MAXQ], tq2[CF_MAXQ * CF_MAXQ];
-        if (!a.density_only) {
-            for (int r = 0; r < q && q1 > 0; ++r) tq1[r] = a.L1.res[pid * q + r];
-            if (q1 > 1)
-                for (int i = 0; i < q * q1; ++i) tq2[i] = a.L2.res[pid * q * q1 + i];
-        }
         PairOut o;
-        pair_assemble(F, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1, tq2, a.density_only, o);
+        if (a.single_pass && !a.density_only) {
+            pair_assemble_sp(F, a.Ly, p, q, c, d, logtp, alpha_s, a.LM.res[pid], a.LM.mom + pid * W, o);
+        } else {
+            const double alpha = a.density_only ? 0.0 : a.L0.res[pid * m0 + 1];
+            double tq1[CF_MAXQ], tq2[CF_MAXQ * CF_MAXQ];
+            if (!a.density_only) {
+                for (int r = 0; r < q && q1 > 0; ++r) tq1[r] = a.L1.res[pid * q + r];
+                if (q1 > 1)
+                    for (int i = 0; i < q * q1; ++i) tq2[i] = a.L2.res[pid * q * q1 + i];
+            }
+            pair_assemble(F, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1, tq2, a.density_only, o);
+        }
         a.logf[pid] = o.logf;
         if (a.se) a.se[pid] = se;
         if (!isfinite(o.logf)) atomicOr(a.flags, KF_NAN);
@@ -127,6 +141,18 @@ cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st, long long* lau
     combine_kernel<<<grid_for(np, 128, 1 << 20), 128, 0, st>>>(a);
     ++*launches;
     return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const RecSet& r, const IntegArgs& a, int fp32, int nsm, cudaStream_t st,
+                           long long* launches)
+{
+    if (r.k < 3 || r.nrec == 0) return cudaSuccess;
+    const long long blocks_needed = (r.nrec + 7) / 8;
+    const int cap = nsm * 16;
+    const int blocks = (int)(blocks_needed < cap ? blocks_needed : cap);
+    cudaError_t e = fp32 ? launch_mom32(r.k, r, a, blocks, st) : launch_mom64(r.k, r, a, blocks, st);
+    ++*launches;
+    return e;
 }
 
 cudaError_t launch_integrals(const RecSet& r, const IntegArgs& a, int fp32, int nsm,

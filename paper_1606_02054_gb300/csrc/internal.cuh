@@ -8,7 +8,7 @@
 #define CF_MAXQ 8
 #define CF_MAXG 16
 #define CF_MAXSHIFT 64
-#define CF_MAXDIM 8     // lattice dimensions (= largest T_k)
+#define CF_MAXDIM 9     // lattice dimensions (largest T_k plus the sampled last coordinate)
 #define CF_WARP 32
 
 // Sizes of one problem.
@@ -93,6 +93,8 @@ __host__ __device__ inline int stats_per_comp(int p, int q)
 // ---------------------------------------------------------------------------
 struct RecSet {
     int k;             // dimension of every integral in the set (0 = none)
+    double* mom;       // moment records only: nrec x (k + k(k+1)/2) standardised
+                       // E[X], E[X X^T] (lower triangle, row-major) given X <= limits
     long long nrec;    // number of records
     double* bt;        // nrec x k standardised upper limits
     int* fac;          // offset in F of the k x k correlation Cholesky factor
@@ -108,9 +110,10 @@ struct PlanArgs {
     const double* y;
     const double* F;
     int density_only;
+    int single_pass;       // moments by ratio estimators (q >= 3): records LM instead of alpha/L1/L2
     double* pd;        // per pair: d, log t_p
     double* pc;        // per pair: c (q)
-    RecSet L0, L1, L2;
+    RecSet L0, L1, L2, LM;
 };
 
 // Per-dof constants of the T_1 / T_2 integrators, 4 per table index
@@ -142,8 +145,9 @@ struct CombineArgs {
     const double* F;
     const double* pd;
     const double* pc;
-    RecSet L0, L1, L2;
+    RecSet L0, L1, L2, LM;
     int density_only;
+    int single_pass;
     int fp32;              // records evaluated in FP32: pairs with alpha_s < 1e-35 go to the fix-up list
     double* logf;
     double* u;
@@ -174,6 +178,7 @@ struct EstepArgs {
     const float* glw32;
     int t2n;
     int density_only;
+    int single_pass;
     double* logf;           // g*n
     double* u;
     double* elogu;
@@ -200,6 +205,10 @@ cudaError_t launch_tk_eval(int k, int count, const double* b, const double* V, c
 cudaError_t launch_lattice32(int k, const RecSet& r, const IntegArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_lattice64(int k, const RecSet& r, const IntegArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_t2(const RecSet& r, const IntegArgs& a, int fp32, int blocks, cudaStream_t st);
+cudaError_t launch_moments(const RecSet& r, const IntegArgs& a, int fp32, int nsm, cudaStream_t st,
+                           long long* launches);
+cudaError_t launch_mom32(int k, const RecSet& r, const IntegArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_mom64(int k, const RecSet& r, const IntegArgs& a, int blocks, cudaStream_t st);
 
 // Arguments of the statistics reduction (reduce.cu).
 struct ReduceArgs {

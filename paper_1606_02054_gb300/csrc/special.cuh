@@ -389,3 +389,118 @@ __device__ double tk_lattice_warp(const double* bt, const double* Lc, const R* _
     if (se) *se = M > 1 ? (double)m_sqrt(m2 / R(M - 1) / R(M)) : 0.0;
     return (double)mean;
 }
+
+// ---------------------------------------------------------------------------
+// Lattice T_K with the truncated moments, warp-cooperative.  The separation
+// of variables also samples the last coordinate (lattice dimension K), so
+// every point gives the standardised draw X = L y / s inside {X <= bt} with
+// weight f = prod e_i.  Returns alpha = mean f (as tk_lattice_warp); m1 (K)
+// and m2 (K(K+1)/2, lower triangle) receive the ratio estimators
+// sum f X / sum f and sum f X X^T / sum f.
+// ---------------------------------------------------------------------------
+template <typename R, int K>
+__device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const R* __restrict__ chi,
+                                      const R* __restrict__ shf, const Lattice& lat, int lane,
+                                      double* m1, double* m2, double* acc_sm)
+{
+    // acc_sm: this warp's shared-memory slot of K + K(K+1)/2 + 1 doubles that
+    // lane 0 uses for the running totals over the shifts
+    constexpr int K2 = K * (K + 1) / 2;
+    R b[K], invd[K], Lf[K][K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        b[r] = (R)bt[r];
+        invd[r] = R(1) / (R)Lc[r * K + r];
+#pragma unroll
+        for (int l = 0; l < K; ++l) Lf[r][l] = l <= r ? (R)Lc[r * K + l] : R(0);
+    }
+    const int N = lat.N, M = lat.M;
+    const R invN = R(1) / (R)N;
+    int step[K + 1], idx0[K + 1];
+#pragma unroll
+    for (int d = 1; d <= K; ++d) {
+        step[d] = (int)(((long long)CF_WARP * lat.z[d]) % N);
+        idx0[d] = (int)(((long long)lane * lat.z[d]) % N);
+    }
+    if (lane == 0)
+        for (int r = 0; r <= K + K2; ++r) acc_sm[r] = 0.0;
+    for (int m = 0; m < M; ++m) {
+        R sh[K + 1];
+#pragma unroll
+        for (int d = 1; d <= K; ++d) sh[d] = shf[m * CF_MAXDIM + d];
+        int idx[K + 1];
+#pragma unroll
+        for (int d = 1; d <= K; ++d) idx[d] = idx0[d];
+        R af = R(0), a1[K], a2[K2];
+#pragma unroll
+        for (int r = 0; r < K; ++r) a1[r] = R(0);
+#pragma unroll
+        for (int r = 0; r < K2; ++r) a2[r] = R(0);
+        const R* __restrict__ crow = chi + (size_t)m * N;
+        for (int i = lane; i < N; i += CF_WARP) {
+            const R s = crow[i];
+            R y[K];
+            R f = R(1);
+#pragma unroll
+            for (int r = 0; r < K; ++r) {
+                R a = b[r] * s;
+#pragma unroll
+                for (int l = 0; l < r; ++l) a -= Lf[r][l] * y[l];
+                const R e = m_ncdf(a * invd[r]);
+                f *= e;
+                R x = (R)idx[r + 1] * invN + sh[r + 1];
+                if (x >= R(1)) x -= R(1);
+                const R w = R(1) - m_abs(R(2) * x - R(1));
+                R v = w * e;
+                v = v < Lim<R>::vmin() ? Lim<R>::vmin() : v;
+                v = v > Lim<R>::one_minus_ulp() ? Lim<R>::one_minus_ulp() : v;
+                y[r] = m_ncdfinv(v);
+                if (e <= Lim<R>::tiny()) f = R(0);
+            }
+            // Z = L y in place, last row first (row r reads y[0..r] only)
+#pragma unroll
+            for (int r = K - 1; r >= 0; --r) {
+                R z = R(0);
+#pragma unroll
+                for (int l = 0; l <= r; ++l) z += Lf[r][l] * y[l];
+                y[r] = z;
+            }
+            const R is = R(1) / s;
+            const R fs = f * is, fs2 = fs * is;  // X = Z / s
+            af += f;
+#pragma unroll
+            for (int r = 0; r < K; ++r) {
+                a1[r] += fs * y[r];
+                const R t = fs2 * y[r];
+#pragma unroll
+                for (int c = 0; c <= r; ++c) a2[r * (r + 1) / 2 + c] += t * y[c];
+            }
+#pragma unroll
+            for (int d = 1; d <= K; ++d) {
+                idx[d] += step[d];
+                if (idx[d] >= N) idx[d] -= N;
+            }
+        }
+        af = warp_sum(af);
+#pragma unroll
+        for (int r = 0; r < K; ++r) a1[r] = warp_sum(a1[r]);
+#pragma unroll
+        for (int r = 0; r < K2; ++r) a2[r] = warp_sum(a2[r]);
+        if (lane == 0) {
+            acc_sm[0] += (double)af;
+#pragma unroll
+            for (int r = 0; r < K; ++r) acc_sm[1 + r] += (double)a1[r];
+#pragma unroll
+            for (int r = 0; r < K2; ++r) acc_sm[1 + K + r] += (double)a2[r];
+        }
+    }
+    __syncwarp();
+    const double Sf = acc_sm[0];
+    const double inv = Sf > 0.0 ? 1.0 / Sf : 0.0;
+#pragma unroll
+    for (int r = 0; r < K; ++r) m1[r] = acc_sm[1 + r] * inv;
+#pragma unroll
+    for (int r = 0; r < K2; ++r) m2[r] = acc_sm[1 + K + r] * inv;
+    __syncwarp();
+    return Sf / ((double)N * M);
+}
