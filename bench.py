@@ -43,6 +43,13 @@ INSTR_PER_POINT = {("lattice", 3): 283.3, ("lattice", 4): 385.5, ("moments", 4):
 # scales with the record count.
 INTEG_TRAFFIC_BYTES_PER_RECORD = {("lattice", 3): 2201600 / 64000, ("lattice", 4): 1566720 / 32000,
                                   ("moments", 4): 815872 / 16000}
+PRECISION_NOTE = {
+    "fp64": "fp64 throughout",
+    "fp32": "fp32 lattice/quadrature integrals; fp64 whitening, densities, tau, loglik, "
+            "statistics, M-step",
+    "mixed": "fp32 whitening, integrals and compensated statistics; fp64 factorisations, "
+             "tau, loglik, M-step, nu",
+}
 SM_COUNT = 152
 LANES_PER_SM = 128  # 4 sub-partitions x 32 lanes, one instruction per lane per clock
 
@@ -171,7 +178,7 @@ def main():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--workload", default="flow_p4")
     ap.add_argument("--n", type=int, default=None, help="override the workload size")
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "fp64", "mixed"], default="fp32")
     ap.add_argument("--moments", choices=["single-pass", "recursion"], default="single-pass",
                     help="truncated-t moments of the timed form (the plain recursion is "
                          "also timed when single-pass is chosen)")
@@ -213,9 +220,12 @@ def main():
     build.build()
     import paper_1606_02054_gb300 as cf
 
-    prec = cf.CFUST_PREC_FP32 if args.precision == "fp32" else cf.CFUST_PREC_FP64
+    prec = {"fp32": cf.CFUST_PREC_FP32, "fp64": cf.CFUST_PREC_FP64,
+            "mixed": cf.CFUST_PREC_MIXED}[args.precision]
     stream = torch.cuda.current_stream()
-    y_dev = torch.tensor(w["y"], dtype=torch.float64, device="cuda")
+    # the wide workload stores its observations in FP32
+    y_dtype = torch.float32 if w["name"] == "wide_p16" else torch.float64
+    y_dev = torch.tensor(w["y"], dtype=y_dtype, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     pairs = w["n"] * w["g"]
 
@@ -286,7 +296,7 @@ def main():
     kind, kdim, mult = cls[dom]
     points = pairs * mult * w["qmc"]["npoints"] * w["qmc"]["nshifts"]
     f_sm = (clk.get("sm_mhz") or _peaks().get("sm_max_mhz", 2070.0)) * 1e6
-    ipp = INSTR_PER_POINT.get((kind, kdim)) if args.precision == "fp32" else None
+    ipp = INSTR_PER_POINT.get((kind, kdim)) if args.precision != "fp64" else None
     if ipp:
         achieved = ipp * points / (dom_ms_per_launch / 1e3) / 1e12
         peak = SM_COUNT * LANES_PER_SM * f_sm / 1e12
@@ -342,12 +352,11 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+                "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
                 "config": {"workload": w["name"], "n": w["n"], "p": w["p"], "q": w["q"],
                            "g": w["g"], "qmc": f"{w['qmc']['npoints']}x{w['qmc']['nshifts']}",
                            "form": form,
-                           "precision": f"{args.precision} lattice/quadrature integrals, "
-                                        "fp64 whitening, densities, tau, loglik, statistics, M-step",
+                           "precision": PRECISION_NOTE[args.precision],
                            "l2": "flushed (256 MB write) before every timed step",
                            "parallelism": f"replicas x{world}"},
                 "em_iter_per_s": 1e3 / ms,

@@ -50,17 +50,24 @@ typedef enum {
     CFUST_ESTATE = 9    /* call out of order (e.g. estep before set_data/set_params) */
 } cfust_status;
 
-/* Arithmetic of the E-step integrals (the T_q terms of eqs (4), (13) and the
- * truncated-t moments of eqs (16)-(17)).  Whitening, log t_p, the
- * log-sum-exp of eq (12), the log-likelihood of eq (27), every sufficient
- * statistic and the M-step stay FP64 in both modes. */
-enum { CFUST_PREC_FP64 = 0, CFUST_PREC_FP32 = 1 };
+/* Arithmetic of the E-step.
+ *   CFUST_PREC_FP64:  everything in FP64.
+ *   CFUST_PREC_FP32:  the integrals (the T_q terms of eqs (4), (13) and the
+ *                     truncated-t moments of eqs (16)-(17)) in FP32; whitening,
+ *                     log t_p, the log-sum-exp of eq (12), the log-likelihood of
+ *                     eq (27), the sufficient statistics and the M-step in FP64.
+ *   CFUST_PREC_MIXED: as FP32, and also the whitening (from FP32 copies of y and
+ *                     of the factors) and the tau-weighted statistics (FP32 sums
+ *                     per block of observations with compensation, FP64 across
+ *                     blocks) in FP32; FP64 stays for the Cholesky factorisations
+ *                     and inverses, tau, the log-likelihood, the M-step and nu. */
+enum { CFUST_PREC_FP64 = 0, CFUST_PREC_FP32 = 1, CFUST_PREC_MIXED = 2 };
 
 /* Element type of the observation matrix passed to cfust_set_data. */
 enum { CFUST_F32 = 0, CFUST_F64 = 1 };
 
 typedef struct {
-    int precision;       /* CFUST_PREC_FP64 (default) or CFUST_PREC_FP32 */
+    int precision;       /* CFUST_PREC_FP64 (default), _FP32 or _MIXED */
     int qmc_points;      /* N: points of the rank-1 Korobov lattice for T_k, k >= 3 (default 1024) */
     int qmc_shifts;      /* M: random shifts of the lattice, 2..64 (default 8) */
     int qmc_korobov_a;   /* Korobov generator a: z_d = a^d mod N (default 119) */
@@ -70,7 +77,7 @@ typedef struct {
     int device;          /* CUDA device ordinal (default 0) */
     void* cuda_stream;   /* cudaStream_t to issue work on (default NULL) */
     int t2_nodes;        /* Gauss-Legendre nodes per piece of the T_2 quadrature, 8..64
-                            (0: 64 in FP64 mode, 32 in FP32 mode) */
+                            (0: 64 in FP64 mode, 32 in FP32 mode, 24 in mixed mode) */
     int profile;         /* 1: time every kernel class with CUDA events on the context
                             stream (read with cfust_profile); 0 (default): off */
     int moments;         /* truncated-t moments of eqs (16)-(17) for q >= 3:

@@ -26,7 +26,7 @@ CFUST_ENAN, CFUST_ETIMEOUT, CFUST_ECUDA, CFUST_ENOMEM, CFUST_ESTATE = 5, 6, 7, 8
 STATUS_NAMES = {0: "CFUST_OK", 1: "CFUST_EINVAL", 2: "CFUST_ENOTPD", 3: "CFUST_EEMPTY",
                 4: "CFUST_ENUROOT", 5: "CFUST_ENAN", 6: "CFUST_ETIMEOUT", 7: "CFUST_ECUDA",
                 8: "CFUST_ENOMEM", 9: "CFUST_ESTATE"}
-CFUST_PREC_FP64, CFUST_PREC_FP32 = 0, 1
+CFUST_PREC_FP64, CFUST_PREC_FP32, CFUST_PREC_MIXED = 0, 1, 2
 CFUST_F32, CFUST_F64 = 0, 1
 # kernel classes of cfust_profile
 PROF_NAMES = ("setup", "chi_table", "plan", "level0_Tq", "level1_Tq-1", "level2_Tq-2",

@@ -18,9 +18,11 @@ __global__ void setup_components_kernel(Dims, Layout, const double*, const doubl
 __global__ void chi_table_kernel(int, const double*, Lattice, const double*, double*, float*);
 __global__ void dof_consts_kernel(Dims, Layout, const double*, int, double*, double*, float*);
 __global__ void widen_kernel(const float*, long long, Dims, double*);
+__global__ void narrow_kernel(const double*, Dims, float*);
 
 
 __global__ void estep_reduce_kernel(ReduceArgs);
+__global__ void estep_reduce_kernel_f32(ReduceArgs);
 __global__ void reduce_partials_kernel(const double*, int, int, double*, int*);
 __global__ void loglik_partial_kernel(Dims, const double*, const double*, double*);
 __global__ void mstep_kernel(Dims, const double*, double, double, const double*, const double*,
@@ -56,6 +58,10 @@ struct cfust_ctx {
     double *partial = nullptr, *stats = nullptr;
     int *flags = nullptr, *comp_status = nullptr;
     float* stage32 = nullptr;
+    // mixed precision: FP32 copies of the observations and factor blocks
+    bool mixed = false;
+    float* y32 = nullptr;
+    float* F32 = nullptr;
     // E-step pipeline: per-pair (d, log t_p) and c, integral records per level
     double *pd = nullptr, *pc = nullptr;
     RecSet rec[4]{};  // levels 0, 1, 2 and the single-pass moment records
@@ -265,7 +271,7 @@ static void free_all(cfust_ctx* c)
                     c->Delta_n, c->nu_n, c->F, c->dofs, c->cst64, c->cst32, c->chi64, c->chi32, c->shf64, c->shf32,
                     c->glx64, c->glw64, c->glx32, c->glw32, c->logf, c->u, c->elogu, c->eu,
                     c->euu, c->se, c->tau, c->partial, c->stats, c->flags, c->comp_status,
-                    c->stage32, c->pd, c->pc, c->fix_count, c->fix_list};
+                    c->stage32, c->pd, c->pc, c->fix_count, c->fix_list, c->y32, c->F32};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (RecSet& r : c->rec) {
@@ -303,8 +309,9 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     cfust_opts o;
     cfust_default_opts(&o);
     if (opts) o = *opts;
-    if (o.precision != CFUST_PREC_FP64 && o.precision != CFUST_PREC_FP32)
-        return fail(nullptr, CFUST_EINVAL, "cfust_create: precision must be CFUST_PREC_FP64 or CFUST_PREC_FP32");
+    if (o.precision != CFUST_PREC_FP64 && o.precision != CFUST_PREC_FP32 &&
+        o.precision != CFUST_PREC_MIXED)
+        return fail(nullptr, CFUST_EINVAL, "cfust_create: precision must be CFUST_PREC_FP64, _FP32 or _MIXED");
     if (o.qmc_points < 32 || o.qmc_points > (1 << 20) || o.qmc_shifts < 2 ||
         o.qmc_shifts > CF_MAXSHIFT || o.qmc_korobov_a < 1)
         return fail(nullptr, CFUST_EINVAL, "cfust_create: lattice needs 32 <= N <= 2^20, 2 <= M <= 64, a >= 1");
@@ -334,7 +341,9 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
             z = (z * o.qmc_korobov_a) % o.qmc_points;
         }
     }
-    c->t2n = o.t2_nodes ? o.t2_nodes : (o.precision == CFUST_PREC_FP64 ? 64 : 32);
+    c->mixed = o.precision == CFUST_PREC_MIXED;
+    c->t2n = o.t2_nodes ? o.t2_nodes
+                        : (o.precision == CFUST_PREC_FP64 ? 64 : (c->mixed ? 24 : 32));
     cudaDeviceProp prop;
     if ((e = cudaGetDeviceProperties(&prop, o.device)) != cudaSuccess) {
         cfust_status s = fail(nullptr, CFUST_ECUDA, std::string("cfust_create: ") + cudaGetErrorString(e));
@@ -347,8 +356,10 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     // reduction staging: rows of 4 + p + q + q^2 doubles, chunk <= 256 observations,
     // at most ~64 KB of shared memory
     c->row = 4 + p + q + q * q;
+    const size_t rowbytes = c->mixed ? sizeof(float) : sizeof(double);
     int chunk = 256;
-    while (chunk > 32 && (size_t)chunk * (c->row + g + 1) * sizeof(double) > 64 * 1024) chunk -= 32;
+    while (chunk > 32 && (size_t)chunk * (c->row * rowbytes + (g + 1) * sizeof(double)) > 64 * 1024)
+        chunk -= 32;
     c->chunk = chunk;
     c->nblocks_red = (int)((n + chunk - 1) / chunk);
     c->nblocks_ll = (int)((n + 255) / 256);
@@ -383,6 +394,10 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     ALLOC(stats, (size_t)g * S + 1);
     ALLOC(flags, 1); ALLOC(comp_status, g);
     ALLOC(pd, 2 * ng); ALLOC(pc, ng * q);
+    if (c->mixed) {
+        ALLOC(y32, (size_t)n * p);
+        ALLOC(F32, (size_t)g * c->Ly.stride);
+    }
     ALLOC(fix_count, 1); ALLOC(fix_list, ng);
     {
         const bool sp = c->single_pass;
@@ -440,6 +455,7 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
         return s;
     }
     cudaFuncSetAttribute(estep_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    cudaFuncSetAttribute(estep_reduce_kernel_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     if (o.profile)
         for (int k = 0; k < CFUST_NPROF; ++k)
             for (int i = 0; i < 2; ++i)
@@ -475,6 +491,13 @@ extern "C" cfust_status cfust_set_data(cfust_ctx* c, const void* y, int dtype, i
         const long long total = (long long)rows * pitch;
         const int blocks = (int)std::min<long long>((total + 255) / 256, 4LL * c->nsm * 8);
         widen_kernel<<<blocks, 256, 0, c->st>>>(src, ld, c->D, c->y);
+        LAUNCHED();
+    }
+    if (c->mixed) {
+        // the FP32 copy: narrowed from the FP64 rows (exact for FP32 input)
+        const long long total = (long long)rows * pitch;
+        const int blocks = (int)std::min<long long>((total + 255) / 256, 4LL * c->nsm * 8);
+        narrow_kernel<<<blocks, 256, 0, c->st>>>(c->y, c->D, c->y32);
         LAUNCHED();
     }
     c->have_data = true;
@@ -538,7 +561,11 @@ static cfust_status launch_setup(cfust_ctx* c)
     LAUNCHED();
     dof_consts_kernel<<<1, 64, 0, c->st>>>(c->D, c->Ly, c->F, 3 * c->g, c->dofs, c->cst64, c->cst32);
     LAUNCHED();
-    prof_end(c, CFUST_PROF_SETUP, 2);
+    if (c->mixed) {
+        cudaError_t e = launch_factors_f32(c->F, c->F32, (long long)c->g * c->Ly.stride, c->st, &c->launches);
+        if (e != cudaSuccess) return fail(c, CFUST_ECUDA, std::string("factor copy: ") + cudaGetErrorString(e));
+    }
+    prof_end(c, CFUST_PROF_SETUP, c->mixed ? 3 : 2);
     if (c->q >= 3) {
         prof_begin(c, CFUST_PROF_CHI);
         const long long total = 3LL * c->g * c->lat.N * c->lat.M;
@@ -565,10 +592,12 @@ static IntegArgs integ_args(const cfust_ctx* c)
 // S2-S7: plan, integrals of each level, combine, FP64 fix-up of far-tail pairs.
 static cfust_status launch_pairs(cfust_ctx* c, int density_only)
 {
-    const int fp32 = c->opts.precision == CFUST_PREC_FP32;
+    const int fp32 = c->opts.precision != CFUST_PREC_FP64;
     const int sp = c->single_pass ? 1 : 0;
     PlanArgs pa;
     pa.D = c->D; pa.Ly = c->Ly; pa.y = c->y; pa.F = c->F; pa.density_only = density_only;
+    pa.y32 = c->mixed ? c->y32 : nullptr;
+    pa.F32 = c->mixed ? c->F32 : nullptr;
     pa.single_pass = sp;
     pa.pd = c->pd; pa.pc = c->pc;
     pa.L0 = c->rec[0]; pa.L1 = c->rec[1]; pa.L2 = c->rec[2]; pa.LM = c->rec[3];
@@ -597,9 +626,10 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
     }
     if (fp32) CU(cudaMemsetAsync(c->fix_count, 0, sizeof(int), c->st));
     CombineArgs ca;
-    ca.D = c->D; ca.Ly = c->Ly; ca.F = c->F; ca.pd = c->pd; ca.pc = c->pc;
+    ca.D = c->D; ca.Ly = c->Ly; ca.cst64 = c->cst64; ca.F = c->F; ca.pd = c->pd; ca.pc = c->pc;
     ca.L0 = pa.L0; ca.L1 = c->rec[1]; ca.L2 = c->rec[2]; ca.LM = c->rec[3];
     ca.density_only = density_only; ca.single_pass = sp; ca.fp32 = fp32;
+    ca.mixed = c->mixed ? 1 : 0;
     ca.logf = c->logf; ca.u = c->u; ca.elogu = c->elogu; ca.eu = c->eu; ca.euu = c->euu; ca.se = c->se;
     ca.fix_count = c->fix_count; ca.fix_list = c->fix_list; ca.flags = c->flags;
     n0 = c->launches;
@@ -609,7 +639,7 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
     prof_end(c, CFUST_PROF_COMBINE, c->launches - n0);
     if (fp32) {
         EstepArgs a;
-        a.D = c->D; a.Ly = c->Ly; a.lat = c->lat;
+        a.D = c->D; a.Ly = c->Ly; a.lat = c->lat; a.cst64 = c->cst64;
         a.y = c->y; a.F = c->F;
         a.chi64 = c->chi64; a.chi32 = c->chi32;
         a.shf64 = c->shf64; a.shf32 = c->shf32;
@@ -642,9 +672,12 @@ extern "C" cfust_status cfust_estep(cfust_ctx* c, double* loglik_out)
     r.D = c->D; r.y = c->y; r.pi = c->pi; r.mu = c->mu; r.logf = c->logf; r.u = c->u;
     r.elogu = c->elogu; r.eu = c->eu; r.euu = c->euu; r.tau = c->tau; r.partial = c->partial;
     r.chunk = c->chunk; r.row = c->row;
-    const size_t smem = sizeof(double) * ((size_t)c->chunk * c->row + (size_t)c->g * c->chunk + c->chunk);
+    r.y32 = c->y32;
+    const size_t smem = (c->mixed ? sizeof(float) : sizeof(double)) * (size_t)c->chunk * c->row +
+                        sizeof(double) * ((size_t)c->g * c->chunk + c->chunk);
     prof_begin(c, CFUST_PROF_REDUCE);
-    estep_reduce_kernel<<<c->nblocks_red, 256, smem, c->st>>>(r);
+    if (c->mixed) estep_reduce_kernel_f32<<<c->nblocks_red, 256, smem, c->st>>>(r);
+    else estep_reduce_kernel<<<c->nblocks_red, 256, smem, c->st>>>(r);
     LAUNCHED();
     const int width = c->g * stats_per_comp(c->p, c->q) + 1;
     reduce_partials_kernel<<<(width + 127) / 128, 128, 0, c->st>>>(c->partial, c->nblocks_red, width,
@@ -886,7 +919,7 @@ extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const doub
         ia.F = dF;
         ia.chi64 = t64;
         ia.chi32 = t32;
-        if ((e = launch_integrals(r, ia, c->opts.precision == CFUST_PREC_FP32, c->nsm, c->st, &c->launches))) break;
+        if ((e = launch_integrals(r, ia, c->opts.precision != CFUST_PREC_FP64, c->nsm, c->st, &c->launches))) break;
         if ((e = cudaMemcpyAsync(out, r.res, sizeof(double) * count, cudaMemcpyDeviceToHost, c->st))) break;
         if (se && (e = cudaMemcpyAsync(se, r.se, sizeof(double) * count, cudaMemcpyDeviceToHost, c->st))) break;
         e = cudaStreamSynchronize(c->st);

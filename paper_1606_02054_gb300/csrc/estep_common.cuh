@@ -45,6 +45,31 @@ __device__ inline void pair_whiten(const double* F, const Layout& Ly, int p, int
     *logtp = F[Ly.scal + SC_LOGTP] - 0.5 * (nu + p) * log1p(d / nu);
 }
 
+// Mixed precision: the same whitening in FP32 from FP32 copies of y and of
+// the factor block; d and c are returned in FP64 for the rest of the pair.
+__device__ inline void pair_whiten_f32(const float* F32, const double* F, const Layout& Ly, int p,
+                                       int q, const float* yj, double* d_out, double* c,
+                                       double* logtp)
+{
+    float rr[CF_MAXP], z[CF_MAXP];
+    for (int i = 0; i < p; ++i) rr[i] = yj[i] - F32[Ly.mu + i];
+    float d = 0.0f;
+    for (int i = 0; i < p; ++i) {
+        float s = 0.0f;
+        for (int l = 0; l <= i; ++l) s = fmaf(F32[Ly.Linv + i * p + l], rr[l], s);
+        z[i] = s;
+        d = fmaf(s, s, d);
+    }
+    for (int k = 0; k < q; ++k) {
+        float s = 0.0f;
+        for (int i = 0; i < p; ++i) s = fmaf(F32[Ly.A + i * q + k], z[i], s);
+        c[k] = (double)s;
+    }
+    const double nu = F[Ly.scal + SC_NU];
+    *d_out = (double)d;
+    *logtp = F[Ly.scal + SC_LOGTP] - 0.5 * (nu + p) * log1p((double)d / nu);
+}
+
 // which = 0: alpha_s (dof nu+p); which = 1: alpha (dof nu+p+2)
 __device__ inline void limits_l0(const double* F, const Layout& Ly, int p, int q, const double* c,
                                  double d, int which, double* bt)
@@ -119,10 +144,11 @@ __device__ inline int fac_l2(const Layout& Ly, int q, int r, int s)
 
 // tq1[r] = T_{q-1} of level 1 (1 when q = 1); tq2[r*(q-1)+s] = T_{q-2} of
 // level 2 (1 when q <= 2).
+// cst: per-dof constants of this component's dof nu+p (table index 3h)
 __device__ inline void pair_assemble(const double* F, const Layout& Ly, int p, int q,
                                      const double* c, double d, double logtp, double alpha_s,
                                      double alpha, const double* tq1, const double* tq2,
-                                     int density_only, PairOut& o)
+                                     int density_only, const double* cst, PairOut& o)
 {
     const double nu = F[Ly.scal + SC_NU], nu1 = nu + p;
     o.logf = q * 0.6931471805599453 + logtp + log(alpha_s);  // eq (4)
@@ -138,7 +164,7 @@ __device__ inline void pair_assemble(const double* F, const Layout& Ly, int p, i
     for (int r = 0; r < q; ++r) {
         const double Srr = k0 * Lam[r * q + r];
         const double t1q = q1 > 0 ? tq1[r] : 1.0;
-        xi[r] = exp(cf_logt1(c[r], Srr, nu1)) * t1q;
+        xi[r] = exp(cf_logt1(c[r], Srr, nu1, cst[CST_LT1])) * t1q;
         H[r * q + r] = c[r] * xi[r];
         if (q1 == 0 || xi[r] == 0.0) continue;
         const double* blk = F + Ly.l1 + r * Ly.l1s;
@@ -156,7 +182,7 @@ __device__ inline void pair_assemble(const double* F, const Layout& Ly, int p, i
         for (int s = 0; s < q1; ++s) {
             const double Vss = kp * sch[s * q1 + s];
             const double t2q = q1 > 1 ? tq2[r * q1 + s] : 1.0;
-            xip[s] = exp(cf_logt1(cp[s], Vss, nu2 - 2.0)) * t2q;
+            xip[s] = exp(cf_logt1(cp[s], Vss, nu2 - 2.0, cst[CST_LT1M])) * t2q;
         }
         // E[Y 1(Y <= c')] = -(nu2/(nu2-2)) V_r xi', V_r = sc1 schur_r
         const double fac = -(nu2 / (nu2 - 2.0)) * sc1 / t1q;
@@ -212,6 +238,82 @@ __device__ inline void pair_assemble_sp(const double* F, const Layout& Ly, int p
         for (int b = 0; b <= a; ++b) {  // eq (17)
             const double m2 = sig[a] * sig[b] * m[q + a * (a + 1) / 2 + b];
             const double v = u * (c[a] * c[b] - c[a] * m1[b] - m1[a] * c[b] + m2);
+            o.euu[a * q + b] = v;
+            o.euu[b * q + a] = v;
+        }
+}
+
+// Mixed precision: the assembly of pair_assemble in FP32 (log f keeps the
+// FP64 log t_p and adds log alpha_s computed in FP32).
+__device__ inline void pair_assemble_f32(const double* F, const Layout& Ly, int p, int q,
+                                         const double* cd, double dd, double logtp, double alpha_s_d,
+                                         double alpha_d, const double* tq1, const double* tq2,
+                                         int density_only, const double* cst, PairOut& o)
+{
+    const float alpha_s = (float)alpha_s_d;
+    o.logf = q * 0.6931471805599453 + logtp + (double)logf(alpha_s);  // eq (4)
+    if (density_only) return;
+    const float nu = (float)F[Ly.scal + SC_NU], nu1 = nu + (float)p, d = (float)dd;
+    float c[CF_MAXQ];
+    for (int k = 0; k < q; ++k) c[k] = (float)cd[k];
+    const float u = nu1 / (nu + d) * (float)alpha_d / alpha_s;  // eq (13)
+    o.u = u;
+    o.elogu = u - logf(0.5f * (nu + d)) - nu1 / (nu + d) + (float)F[Ly.scal + SC_PSI];  // eq (15)
+    float Lam[CF_MAXQ * CF_MAXQ];
+    for (int i = 0; i < q * q; ++i) Lam[i] = (float)F[Ly.Lam + i];
+    const float k0 = (nu + d) / nu1;
+    const float lt1 = (float)cst[CST_LT1], lt1m = (float)cst[CST_LT1M];
+    const int q1 = q - 1;
+    float xi[CF_MAXQ], H[CF_MAXQ * CF_MAXQ];
+    for (int i = 0; i < q * q; ++i) H[i] = 0.0f;
+    for (int r = 0; r < q; ++r) {
+        const float Srr = k0 * Lam[r * q + r];
+        const float t1q = q1 > 0 ? (float)tq1[r] : 1.0f;
+        xi[r] = expf(lt1 - 0.5f * logf(Srr) - 0.5f * (nu1 + 1.0f) * log1pf(c[r] * c[r] / (nu1 * Srr))) * t1q;
+        H[r * q + r] = c[r] * xi[r];
+        if (q1 == 0 || xi[r] == 0.0f) continue;
+        const double* blk = F + Ly.l1 + r * Ly.l1s;
+        float mvec[CF_MAXQ], sch[CF_MAXQ * CF_MAXQ], cp[CF_MAXQ];
+        for (int i = 0; i < q1; ++i) mvec[i] = (float)blk[i];
+        for (int i = 0; i < q1 * q1; ++i) sch[i] = (float)blk[q1 + i];
+        for (int i = 0; i < q1; ++i) {
+            const int b = i < r ? i : i + 1;
+            cp[i] = c[b] - mvec[i] * c[r];
+        }
+        const float nu2 = nu1 + 1.0f;
+        const float sc1 = (nu1 + c[r] * c[r] / Srr) / (nu1 + 1.0f) * k0;
+        const float kp = nu2 / (nu2 - 2.0f) * sc1;
+        float xip[CF_MAXQ];
+        for (int s = 0; s < q1; ++s) {
+            const float Vss = kp * sch[s * q1 + s];
+            const float t2q = q1 > 1 ? (float)tq2[r * q1 + s] : 1.0f;
+            const float nuv = nu2 - 2.0f;
+            xip[s] = expf(lt1m - 0.5f * logf(Vss) - 0.5f * (nuv + 1.0f) * log1pf(cp[s] * cp[s] / (nuv * Vss))) * t2q;
+        }
+        const float fac = -(nu2 / (nu2 - 2.0f)) * sc1 / t1q;
+        for (int i = 0; i < q1; ++i) {
+            float s = 0.0f;
+            for (int t = 0; t < q1; ++t) s += sch[i * q1 + t] * xip[t];
+            const int b = i < r ? i : i + 1;
+            H[r * q + b] = xi[r] * (mvec[i] * c[r] + fac * s);
+        }
+    }
+    float Lxi[CF_MAXQ];
+    for (int a = 0; a < q; ++a) {
+        float s = 0.0f;
+        for (int k = 0; k < q; ++k) s += Lam[a * q + k] * xi[k];
+        Lxi[a] = s;
+        o.eu[a] = u * c[a] + s / alpha_s;  // eq (16)
+    }
+    for (int a = 0; a < q; ++a)
+        for (int b = 0; b <= a; ++b) {  // eq (17), symmetrised
+            float lh1 = 0.0f, lh2 = 0.0f;
+            for (int k = 0; k < q; ++k) {
+                lh1 += Lam[a * q + k] * H[k * q + b];
+                lh2 += Lam[b * q + k] * H[k * q + a];
+            }
+            const float v = u * c[a] * c[b] + (c[a] * Lxi[b] + Lxi[a] * c[b]) / alpha_s + Lam[a * q + b]
+                          - 0.5f * (lh1 + lh2) / alpha_s;
             o.euu[a * q + b] = v;
             o.euu[b * q + a] = v;
         }

@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(128) fixup_kernel(EstepArgs a, const int* coun
             }
         }
         PairOut o;
-        pair_assemble(F, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1, tq2, a.density_only, o);
+        pair_assemble(F, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1, tq2, a.density_only,
+                      a.cst64 + (size_t)(3 * h) * CST_STRIDE, o);
         if (lane == 0) {
             a.logf[pid] = o.logf;
             if (a.se) a.se[pid] = se;

@@ -20,7 +20,11 @@ __global__ void __launch_bounds__(128) plan_kernel(PlanArgs a)
         const int foff = h * a.Ly.stride;
         const double nu1 = F[a.Ly.scal + SC_NU] + p;
         double c[CF_MAXQ], d, logtp;
-        pair_whiten(F, a.Ly, p, q, a.y + (size_t)j * p, &d, c, &logtp);
+        if (a.F32)
+            pair_whiten_f32(a.F32 + (size_t)h * a.Ly.stride, F, a.Ly, p, q, a.y32 + (size_t)j * p, &d,
+                            c, &logtp);
+        else
+            pair_whiten(F, a.Ly, p, q, a.y + (size_t)j * p, &d, c, &logtp);
         a.pd[2 * pid] = d;
         a.pd[2 * pid + 1] = logtp;
         for (int k = 0; k < q; ++k) a.pc[pid * q + k] = c[k];
@@ -96,7 +100,12 @@ __global__ void __launch_bounds__(128) combine_kernel(CombineArgs a)
                 if (q1 > 1)
                     for (int i = 0; i < q * q1; ++i) tq2[i] = a.L2.res[pid * q * q1 + i];
             }
-            pair_assemble(F, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1, tq2, a.density_only, o);
+            if (a.mixed)
+                pair_assemble_f32(F, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1, tq2, a.density_only,
+                                  a.cst64 + (size_t)(3 * h) * CST_STRIDE, o);
+            else
+                pair_assemble(F, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1, tq2, a.density_only,
+                              a.cst64 + (size_t)(3 * h) * CST_STRIDE, o);
         }
         a.logf[pid] = o.logf;
         if (a.se) a.se[pid] = se;
@@ -175,4 +184,20 @@ cudaError_t launch_integrals(const RecSet& r, const IntegArgs& a, int fp32, int 
     }
     ++*launches;
     return e;
+}
+
+// FP32 copies of the factor blocks (mixed precision)
+__global__ void factors_to_f32_kernel(const double* __restrict__ F, float* __restrict__ F32, long long count)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+         t += (long long)gridDim.x * blockDim.x)
+        F32[t] = (float)F[t];
+}
+
+cudaError_t launch_factors_f32(const double* F, float* F32, long long count, cudaStream_t st,
+                               long long* launches)
+{
+    factors_to_f32_kernel<<<grid_for(count, 256, 1024), 256, 0, st>>>(F, F32, count);
+    ++*launches;
+    return cudaGetLastError();
 }

@@ -109,6 +109,8 @@ struct PlanArgs {
     Layout Ly;
     const double* y;
     const double* F;
+    const float* y32;      // mixed precision: FP32 observations and factor blocks
+    const float* F32;      //   (whitening in FP32), else null
     int density_only;
     int single_pass;       // moments by ratio estimators (q >= 3): records LM instead of alpha/L1/L2
     double* pd;        // per pair: d, log t_p
@@ -121,7 +123,9 @@ struct PlanArgs {
 //   [0] lgamma((v+1)/2) - lgamma(v/2) - lgamma(1/2)   (T_1 at dof v)
 //   [1] the same at dof v + 1                          (inner T_1 of T_2)
 //   [2] Gamma((v+1)/2) / (Gamma(v/2) sqrt(pi))         (T_2 at dof v)
-enum { CST_LGB = 0, CST_LGB1 = 1, CST_C2 = 2, CST_STRIDE = 4 };
+//   [3] lgamma((v+1)/2) - lgamma(v/2) - log(v pi)/2    (log t_1 density at dof v)
+//   [4] the same at dof v - 1
+enum { CST_LGB = 0, CST_LGB1 = 1, CST_C2 = 2, CST_LT1 = 3, CST_LT1M = 4, CST_STRIDE = 8 };
 
 struct IntegArgs {
     const double* cst64;   // [tab][CST_STRIDE]
@@ -142,12 +146,14 @@ struct IntegArgs {
 struct CombineArgs {
     Dims D;
     Layout Ly;
+    const double* cst64;   // per-dof constants, [3h + j][CST_STRIDE]
     const double* F;
     const double* pd;
     const double* pc;
     RecSet L0, L1, L2, LM;
     int density_only;
     int single_pass;
+    int mixed;             // assemble the moments in FP32 (mixed precision)
     int fp32;              // records evaluated in FP32: pairs with alpha_s < 1e-35 go to the fix-up list
     double* logf;
     double* u;
@@ -166,6 +172,7 @@ struct EstepArgs {
     Dims D;
     Layout Ly;
     Lattice lat;
+    const double* cst64;
     const double* y;        // n x p
     const double* F;        // g x stride factor blocks
     const double* chi64;    // [(3h + k)][M][N]
@@ -205,6 +212,8 @@ cudaError_t launch_tk_eval(int k, int count, const double* b, const double* V, c
 cudaError_t launch_lattice32(int k, const RecSet& r, const IntegArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_lattice64(int k, const RecSet& r, const IntegArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_t2(const RecSet& r, const IntegArgs& a, int fp32, int blocks, cudaStream_t st);
+cudaError_t launch_factors_f32(const double* F, float* F32, long long count, cudaStream_t st,
+                               long long* launches);
 cudaError_t launch_moments(const RecSet& r, const IntegArgs& a, int fp32, int nsm, cudaStream_t st,
                            long long* launches);
 cudaError_t launch_mom32(int k, const RecSet& r, const IntegArgs& a, int blocks, cudaStream_t st);
@@ -224,5 +233,6 @@ struct ReduceArgs {
     double* tau;       // g*n
     double* partial;   // nblocks x (g*S + 1)
     int chunk;         // observations per block (<= blockDim.x)
-    int row;           // doubles per staged observation row
+    int row;           // values per staged observation row
+    const float* y32;  // FP32 observations (FP32 statistics kernel only)
 };

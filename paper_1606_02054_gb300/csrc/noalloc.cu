@@ -96,6 +96,7 @@ extern "C" cfust_status cfust_reduce_stats_noalloc(int p, int q, int g, int64_t 
     r.partial = partial;
     r.chunk = chunk;
     r.row = row;
+    r.y32 = nullptr;
     const size_t smem = sizeof(double) * ((size_t)chunk * row + (size_t)g * chunk + chunk);
     estep_reduce_kernel<<<nblocks, 256, smem, st>>>(r);
     if ((e = cudaGetLastError()) != cudaSuccess)

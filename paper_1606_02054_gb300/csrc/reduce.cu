@@ -35,17 +35,20 @@ __device__ inline void stat_operands(int e, int p, int q, int& ia, int& ib, int&
     ia = 1; ib = R0 + e / p; ic = R0 + e % p;                        // Srr
 }
 
-__global__ void estep_reduce_kernel(ReduceArgs a)
+// T = double: FP64 rows and sums.  T = float (mixed precision): FP32 rows
+// (centred observations from the FP32 copy of y) and compensated FP32 sums
+// per block; tau, l_j and the block partials stay FP64.
+template <typename T>
+__device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
 {
-    extern __shared__ double sm[];
     const int p = a.D.p, q = a.D.q, g = a.D.g;
     const long long n = a.D.n;
     const int S = stats_per_comp(p, q);
     const long long j0 = (long long)blockIdx.x * a.chunk;
     const int cnt = (int)((n - j0) < a.chunk ? (n - j0) : a.chunk);
-    double* rows = sm;                           // chunk x row
-    double* taus = rows + (size_t)a.chunk * a.row;  // g x chunk
-    double* lj = taus + (size_t)g * a.chunk;     // chunk
+    // chunk is a multiple of 32, so the FP32 rows end on an 8-byte boundary
+    double* taus = (double*)(rows + (size_t)a.chunk * a.row);
+    double* lj = taus + (size_t)g * a.chunk;
     double* out = a.partial + (size_t)blockIdx.x * (g * S + 1);
     const int t = threadIdx.x;
 
@@ -81,36 +84,63 @@ __global__ void estep_reduce_kernel(ReduceArgs a)
     // S9: statistics, one component at a time
     for (int h = 0; h < g; ++h) {
         if (t < a.chunk) {
-            double* rw = rows + (size_t)t * a.row;
+            T* rw = rows + (size_t)t * a.row;
             if (t < cnt) {
                 const size_t pid = (size_t)h * n + j0 + t;
                 const double tv = taus[h * a.chunk + t];
                 const double uv = a.u[pid];
-                rw[0] = tv;
-                rw[1] = tv * uv;
-                rw[2] = a.elogu[pid] - uv;
-                rw[3] = 1.0;
-                const double* yj = a.y + (size_t)(j0 + t) * p;
-                for (int i = 0; i < p; ++i) rw[4 + i] = yj[i] - a.mu[(size_t)h * p + i];
-                for (int k = 0; k < q; ++k) rw[4 + p + k] = a.eu[pid * q + k];
-                for (int k = 0; k < q * q; ++k) rw[4 + p + q + k] = a.euu[pid * q * q + k];
+                rw[0] = (T)tv;
+                rw[1] = (T)(tv * uv);
+                rw[2] = (T)(a.elogu[pid] - uv);
+                rw[3] = T(1);
+                if (sizeof(T) == sizeof(float)) {
+                    const float* yj = a.y32 + (size_t)(j0 + t) * p;
+                    for (int i = 0; i < p; ++i) rw[4 + i] = (T)(yj[i] - (float)a.mu[(size_t)h * p + i]);
+                } else {
+                    const double* yj = a.y + (size_t)(j0 + t) * p;
+                    for (int i = 0; i < p; ++i) rw[4 + i] = (T)(yj[i] - a.mu[(size_t)h * p + i]);
+                }
+                for (int k = 0; k < q; ++k) rw[4 + p + k] = (T)a.eu[pid * q + k];
+                for (int k = 0; k < q * q; ++k) rw[4 + p + q + k] = (T)a.euu[pid * q * q + k];
             } else {
-                for (int i = 0; i < a.row; ++i) rw[i] = 0.0;
+                for (int i = 0; i < a.row; ++i) rw[i] = T(0);
             }
         }
         __syncthreads();
         for (int e = t; e < S; e += blockDim.x) {
             int ia, ib, ic;
             stat_operands(e, p, q, ia, ib, ic);
-            double acc = 0.0;
-            for (int jj = 0; jj < cnt; ++jj) {
-                const double* rw = rows + (size_t)jj * a.row;
-                acc += rw[ia] * rw[ib] * rw[ic];
+            T acc = T(0), comp = T(0);
+            if (sizeof(T) == sizeof(float)) {
+                for (int jj = 0; jj < cnt; ++jj) {
+                    const T* rw = rows + (size_t)jj * a.row;
+                    const T v = rw[ia] * rw[ib] * rw[ic] - comp;  // compensated FP32 sum
+                    const T tt = acc + v;
+                    comp = (tt - acc) - v;
+                    acc = tt;
+                }
+            } else {
+                for (int jj = 0; jj < cnt; ++jj) {
+                    const T* rw = rows + (size_t)jj * a.row;
+                    acc += rw[ia] * rw[ib] * rw[ic];
+                }
             }
-            out[h * S + e] = acc;
+            out[h * S + e] = (double)acc;
         }
         __syncthreads();
     }
+}
+
+__global__ void estep_reduce_kernel(ReduceArgs a)
+{
+    extern __shared__ double sm[];
+    estep_reduce_body<double>(a, sm);
+}
+
+__global__ void estep_reduce_kernel_f32(ReduceArgs a)
+{
+    extern __shared__ double sm[];
+    estep_reduce_body<float>(a, (float*)sm);
 }
 
 // S10: stats[e] = sum_b partial[b][e], b in increasing order.

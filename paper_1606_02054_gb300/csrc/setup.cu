@@ -208,14 +208,15 @@ __global__ void dof_consts_kernel(Dims D, Layout Ly, const double* __restrict__ 
         } else {
             v = dofs[t];
         }
-        const double c[3] = {t1_lgb(v), t1_lgb(v + 1.0),
-                             exp(lgamma(0.5 * (v + 1.0)) - lgamma(0.5 * v)) / sqrt(CF_PI)};
-        for (int k = 0; k < 3; ++k) {
+        const double lt = lgamma(0.5 * (v + 1.0)) - lgamma(0.5 * v) - 0.5 * log(v * CF_PI);
+        const double ltm = lgamma(0.5 * v) - lgamma(0.5 * (v - 1.0)) - 0.5 * log((v - 1.0) * CF_PI);
+        const double c[CST_STRIDE] = {t1_lgb(v), t1_lgb(v + 1.0),
+                                      exp(lgamma(0.5 * (v + 1.0)) - lgamma(0.5 * v)) / sqrt(CF_PI),
+                                      lt, v > 1.0 ? ltm : 0.0, 0.0, 0.0, 0.0};
+        for (int k = 0; k < CST_STRIDE; ++k) {
             c64[t * CST_STRIDE + k] = c[k];
             c32[t * CST_STRIDE + k] = (float)c[k];
         }
-        c64[t * CST_STRIDE + 3] = 0.0;
-        c32[t * CST_STRIDE + 3] = 0.0f;
     }
 }
 
@@ -230,4 +231,13 @@ __global__ void widen_kernel(const float* __restrict__ src, long long ld, Dims D
         const int i = (int)(t % D.p);
         dst[t] = (double)src[j * ld + i];
     }
+}
+
+// FP64 observations narrowed to FP32 (mixed precision copy).
+__global__ void narrow_kernel(const double* __restrict__ src, Dims D, float* __restrict__ dst)
+{
+    const long long total = D.n * D.p;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x)
+        dst[t] = (float)src[t];
 }

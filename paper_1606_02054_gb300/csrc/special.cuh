@@ -117,11 +117,11 @@ __device__ inline double cf_trigamma(double x)
     return s + ser;
 }
 
-// log of the univariate t density at x with scale^2 v and dof nu (FP64)
-__device__ inline double cf_logt1(double x, double v, double nu)
+// log of the univariate t density at x with scale^2 v and dof nu (FP64);
+// lc = lgamma((nu+1)/2) - lgamma(nu/2) - log(nu pi)/2
+__device__ inline double cf_logt1(double x, double v, double nu, double lc)
 {
-    return lgamma(0.5 * (nu + 1.0)) - lgamma(0.5 * nu) - 0.5 * log(nu * CF_PI * v)
-         - 0.5 * (nu + 1.0) * log1p(x * x / (nu * v));
+    return lc - 0.5 * log(v) - 0.5 * (nu + 1.0) * log1p(x * x / (nu * v));
 }
 
 // ---------------------------------------------------------------------------
@@ -162,9 +162,12 @@ __device__ __forceinline__ R t1cdf_dev(R t, R nu, R lgb)
     const R a = R(0.5) * nu, b = R(0.5);
     const R ld = m_log(den);
     const R lbt = lgb + a * (m_log(nu) - ld) + b * (R(2) * m_log(m_abs(t)) - ld);
-    R I;
-    if (x < (a + R(1)) / (a + b + R(2))) I = m_exp(lbt) * betacf_dev<R>(a, b, x) / a;
-    else I = R(1) - m_exp(lbt) * betacf_dev<R>(b, a, y) / b;
+    // one continued fraction per lane: I_x(a,b) directly, or 1 - I_y(b,a)
+    // (arguments selected first, so divergent lanes do not run both)
+    const bool direct = x < (a + R(1)) / (a + b + R(2));
+    const R cf = betacf_dev<R>(direct ? a : b, direct ? b : a, direct ? x : y);
+    const R pre = m_exp(lbt) * cf;
+    const R I = direct ? pre / a : R(1) - pre / b;
     const R tail = R(0.5) * I;
     return t > R(0) ? R(1) - tail : tail;
 }

@@ -95,24 +95,32 @@ def sample(rng, n, params, dtype=np.float64):
 # ----------------------------------------------------------------------------
 # starting values: k-means++ partition, 100 Lloyd steps, then eq (23)
 # ----------------------------------------------------------------------------
-def kmeans(rng, y, g, iters=100):
+def _nearest(y, C):
+    d = (y * y).sum(1)[:, None] - 2.0 * y @ C.T + (C * C).sum(1)[None, :]
+    return d.argmin(1)
+
+
+def kmeans(rng, y, g, iters=100, max_fit=50_000):
+    """k-means++ seeding and Lloyd steps; beyond max_fit observations the
+    centres are fitted on a random subsample and every point is then assigned
+    to its nearest centre."""
     n = y.shape[0]
-    centers = [y[rng.integers(n)]]
-    d2 = np.sum((y - centers[0]) ** 2, axis=1)
+    ys = y[rng.choice(n, max_fit, replace=False)] if n > max_fit else y
+    m = ys.shape[0]
+    centers = [ys[rng.integers(m)]]
+    d2 = np.sum((ys - centers[0]) ** 2, axis=1)
     for _ in range(1, g):
         probs = d2 / d2.sum()
-        c = y[rng.choice(n, p=probs)]
+        c = ys[rng.choice(m, p=probs)]
         centers.append(c)
-        d2 = np.minimum(d2, np.sum((y - c) ** 2, axis=1))
+        d2 = np.minimum(d2, np.sum((ys - c) ** 2, axis=1))
     C = np.array(centers)
-    lab = np.zeros(n, dtype=np.int64)
     for _ in range(iters):
-        D = ((y[:, None, :] - C[None, :, :]) ** 2).sum(-1)
-        lab = D.argmin(1)
+        lab = _nearest(ys, C)
         for h in range(g):
             if np.any(lab == h):
-                C[h] = y[lab == h].mean(0)
-    return lab
+                C[h] = ys[lab == h].mean(0)
+    return _nearest(y, C)
 
 
 def moment_start(yc, q, alpha=0.5, nu0=10.0):

@@ -1,0 +1,89 @@
+"""The mixed-precision form (CFUST_PREC_MIXED): FP32 whitening, FP32
+integrals and FP32 compensated statistics, FP64 factorisations, tau,
+log-likelihood, M-step and nu.  Its error against the FP64 oracle is
+reported (printed) and bounded:
+  per-pair log f: 5e-5 max(1, |ref|)   (FP32 whitening: d and c to ~1e-6 relative;
+                                        24-node FP32 T_2: ~1e-5 relative)
+  statistics: 2e-5 of each component's largest statistic
+  log-likelihood: 1e-6 relative;  10-iteration fit: l 1e-6, each parameter block
+  1e-4 in norm-wise relative error."""
+import numpy as np
+import pytest
+
+from paper_1606_02054_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cf():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1606_02054_gb300 import build
+
+    build.build()
+    import paper_1606_02054_gb300 as cf
+
+    return cf
+
+
+def _ctx(cf, w, params, precision, y=None, moments=0):
+    y = w["y"] if y is None else y
+    q = w["qmc"]
+    opts = cf.cfust_default_opts(precision=precision, qmc_points=q["npoints"],
+                                 qmc_shifts=q["nshifts"], qmc_korobov_a=q["korobov_a"],
+                                 seed=q["seed"], moments=moments)
+    ctx = cf.cfust_create(w["p"], w["q"], w["g"], y.shape[0], opts)
+    cf.cfust_set_data(ctx, y)
+    cf.cfust_set_params(ctx, params)
+    return ctx
+
+
+@pytest.mark.parametrize("name,n,moments", [("wide_p16", 1500, 0), ("flow_p4", 300, 0),
+                                            ("flow_p4", 300, 1)])
+def test_mixed_estep_error(cf, oracle, name, n, moments):
+    w = synth.make_workload(name, n=n)
+    y32 = w["y"].astype(np.float32)  # the mixed form stores y in FP32
+    ctx = _ctx(cf, w, w["init"], cf.CFUST_PREC_MIXED, y=y32, moments=moments)
+    L = cf.cfust_estep(ctx)
+    g = cf.cfust_get_pairs(ctx)
+    S = cf.cfust_get_stats(ctx)
+    o = oracle.estep(y32.astype(np.float64), w["init"], oracle.qmc(**dict(w["qmc"], moments=moments)))
+    err_lf = np.abs(g["logf"] - o["logf"]) / np.maximum(1.0, np.abs(o["logf"]))
+    print(f"{name} moments={moments}: max log f err {err_lf.max():.2e}, "
+          f"loglik rel err {abs(L - o['loglik']) / abs(o['loglik']):.2e}")
+    se_rel = o["se"] / np.maximum(np.exp(o["logf"]), 1e-300)
+    assert np.all(err_lf <= 5e-5 + 3 * se_rel)
+    assert abs(L - o["loglik"]) <= 1e-6 * abs(o["loglik"])
+    # statistics from the oracle's pairs (FP64 sums)
+    p, q = w["p"], w["q"]
+    for h in range(w["g"]):
+        t, u = o["tau"][h], o["u"][h]
+        r = y32.astype(np.float64) - w["init"]["mu"][h]
+        ref = np.concatenate([[t.sum(), (t * u).sum(), (t * (o["elogu"][h] - u)).sum()],
+                              (t * u) @ r, t @ o["eu"][h],
+                              np.einsum("j,ja,jb->ab", t, r, o["eu"][h]).ravel(),
+                              np.einsum("j,jab->ab", t, o["euu"][h]).ravel(),
+                              np.einsum("j,ja,jb->ab", t * u, r, r).ravel()])
+        tol = 2e-5 if moments == 0 and name == "wide_p16" else 5e-4
+        assert np.max(np.abs(S[h] - ref)) <= tol * np.abs(ref).max(), h
+
+
+def test_mixed_fit_error(cf, oracle):
+    w = synth.make_workload("wide_p16", n=1500)
+    y32 = w["y"].astype(np.float32)
+    iters = 10
+    ctx = _ctx(cf, w, w["init"], cf.CFUST_PREC_MIXED, y=y32)
+    it, hist = cf.cfust_fit(ctx, iters)
+    got = cf.cfust_get_params(ctx)
+    ref, rhist, _ = oracle.fit(y32.astype(np.float64), w["init"], iters, oracle.qmc(**w["qmc"]))
+    rel = abs(hist[-1] - rhist[-1]) / abs(rhist[-1])
+    # norm-wise relative error of each parameter block of each component
+    perr = {k: float(max(np.linalg.norm(got[k][h] - ref[k][h]) / np.linalg.norm(ref[k][h])
+                         for h in range(w["g"])))
+            for k in ("pi", "mu", "Sigma", "Delta", "nu")}
+    print(f"mixed fit: final loglik rel err {rel:.2e}, parameter rel errors {perr}")
+    assert rel <= 1e-6
+    assert max(perr.values()) <= 1e-4
