@@ -6,7 +6,9 @@ synthetic workload `flow_p4`: p = q = g = 4 (the HSCT flow-cytometry shape),
 n = 200,000 observations drawn from the latent hierarchy of eq (6), T_4 and
 T_3 by the randomised lattice (1024 points x 8 shifts).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64|mixed]
+  python bench.py --workload wide_p16 --precision mixed   (p = 16, q = 2, g = 8, n = 2e6)
+  python bench.py --workload batch [--nfits 64 --starts 4] (concurrent graph-driven fits)
   python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
 
 value: observation-component pairs per second of whole EM iterations, summed
@@ -24,6 +26,10 @@ import threading
 import time
 
 import numpy as np
+
+# concurrent fits of the batch workload use many streams: give them more
+# hardware work queues than the default 8 (read when the CUDA context starts)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -170,6 +176,104 @@ def run_reference(args, w, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank, world):
+    """Batched fits (config 4 shapes): every fit's EM loop is one device-controlled
+    CUDA graph and all fits run concurrently (cfust_fit_batch).  One step = one EM
+    iteration of every fit; value = sum over fits of n*g per second.  The same
+    iteration run fit by fit through cfust_estep/cfust_mstep is timed beside it."""
+    import torch
+
+    from paper_1606_02054_gb300 import build, synth
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    build.build()
+    import paper_1606_02054_gb300 as cf
+
+    prec = {"fp32": cf.CFUST_PREC_FP32, "fp64": cf.CFUST_PREC_FP64,
+            "mixed": cf.CFUST_PREC_MIXED}[args.precision]
+    moments = 1 if args.moments == "single-pass" else 0
+    B = synth.make_batch(nfits=args.nfits, starts=args.starts)
+    qmc = B["qmc"]
+    ctxs, pairs = [], 0
+    for f in B["fits"]:
+        for st in f["starts"]:
+            o = cf.cfust_default_opts(precision=prec, qmc_points=qmc["npoints"],
+                                      qmc_shifts=qmc["nshifts"], qmc_korobov_a=qmc["korobov_a"],
+                                      seed=qmc["seed"], moments=moments)
+            c = cf.cfust_create(f["p"], f["q"], f["g"], f["n"], o)
+            cf.cfust_set_data(c, f["y"])
+            cf.cfust_set_params(c, st)
+            ctxs.append(c)
+            pairs += f["n"] * f["g"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def batched():
+        it, hist, status = cf.cfust_fit_batch(ctxs, 1, 0.0, flags=cf.CFUST_FIT_NO_FINAL)
+        return int(np.sum(status != cf.CFUST_OK))
+
+    def sequential():
+        bad = 0
+        for c in ctxs:
+            try:
+                cf.cfust_estep(c)
+                cf.cfust_mstep(c)
+            except cf.CfustError:
+                bad += 1
+        return bad
+
+    def timed(fn, steps, with_clocks):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        n0 = sum(cf.cfust_launch_count(c) for c in ctxs)
+        clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0"))) if with_clocks else None
+        if clocks:
+            clocks.start()
+        per, failed = [], 0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            failed += fn()
+            torch.cuda.synchronize()
+            per.append((time.perf_counter() - t0) * 1e3)
+        clk = clocks.stop() if clocks else None
+        launches = sum(cf.cfust_launch_count(c) for c in ctxs) - n0
+        return float(np.mean(per)), clk, launches, failed
+
+    ms_b, clk, launches, failed_b = timed(batched, args.steps, True)
+    ms_s, _, launches_s, failed_s = timed(sequential, max(1, args.steps // 2), False)
+    if rank != 0:
+        return
+    shapes = sorted({(f["p"], f["g"]) for f in B["fits"]})
+    line = {"metric": METRIC, "value": pairs * world / (ms_b / 1e3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
+            "config": {"workload": "batch", "fits": len(ctxs), "problems": args.nfits,
+                       "starts": args.starts, "pairs_per_iteration": pairs,
+                       "p=q": "uniform 2..8",
+                       "g": "uniform 2..6", "n": "log-uniform 1e3..1e5",
+                       "n_total": int(sum(f["n"] for f in B["fits"])),
+                       "qmc": f"{qmc['npoints']}x{qmc['nshifts']}",
+                       "form": "single-pass moments" if moments else "moment recursion",
+                       "precision": PRECISION_NOTE[args.precision],
+                       "step": "one EM iteration of every fit (cfust_fit_batch, max_iter 1, "
+                               "no final density pass)",
+                       "timing": "host clock around the synchronous batch call, device "
+                                 "synchronised on both sides",
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": int(launches / args.steps), "failed_fits": failed_b // args.steps,
+            "clocks": clk,
+            "sequential": {"form": "cfust_estep + cfust_mstep fit by fit on one stream",
+                           "value": pairs * world / (ms_s / 1e3), "unit": UNIT,
+                           "ms_per_step": ms_s,
+                           "speedup_of_batched": ms_s / ms_b},
+            "distinct_shapes_pg": len(shapes)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -186,11 +290,21 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=240)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nfits", type=int, default=64, help="batch workload: problems")
+    ap.add_argument("--starts", type=int, default=4, help="batch workload: starts per problem")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.workload == "batch":
+        if args.impl == "gpu":
+            run_batch(args, rank, world)
+        elif rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the batch workload has no "
+                              "oracle leg; time the oracle on a single-fit workload"}))
+        return
 
     from paper_1606_02054_gb300 import synth
 

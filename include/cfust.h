@@ -182,6 +182,26 @@ cfust_status cfust_loglik(cfust_ctx* ctx, double* out);
 cfust_status cfust_fit(cfust_ctx* ctx, int max_iter, double tol, int* iters_out,
                        double* loglik_hist);
 
+/* Flags of cfust_fit_batch. */
+#define CFUST_FIT_NO_FINAL 1 /* skip the density pass that gives l(Psi^(max_iter)) */
+
+/* Batched form of cfust_fit: nfits independent fits (different contexts,
+ * any sizes) run concurrently on the device.  Each context's whole fit --
+ * the loop of cfust_fit (Sec. 3; Aitken rule eqs 24-26; l from the E-step's
+ * density pass, Sec. 4.3) -- is one CUDA graph whose loop control runs on
+ * the device, so no host synchronisation happens between iterations; the
+ * graph is built on first use and reused while (max_iter, tol, flags) stay
+ * the same.  Results equal those of cfust_fit on the same context bit for
+ * bit.  Outputs (each may be NULL): iters_out[i] = M-steps run by fit i;
+ * loglik_hist[i*(max_iter+1) + k] = l(Psi^(k)) of fit i, NaN where not
+ * reached; status_out[i] = the status cfust_fit would return (a failing fit
+ * keeps its last good Psi and its message is in cfust_last_error(ctxs[i])).
+ * Returns the first failing fit's status, or CFUST_OK.  Contexts must be
+ * distinct, and no other call may use them until this one returns. */
+cfust_status cfust_fit_batch(int nfits, cfust_ctx* const* ctxs, int max_iter, double tol,
+                             int flags, int* iters_out, double* loglik_hist,
+                             cfust_status* status_out);
+
 /* Evaluate T_k(b; 0, V, nu) for `count` independent cases with the
  * library's device integrators (k <= 2 deterministic, k >= 3 lattice), host
  * buffers: b (count x k), V (count x k x k scale matrices), nu (count);

@@ -27,6 +27,7 @@ STATUS_NAMES = {0: "CFUST_OK", 1: "CFUST_EINVAL", 2: "CFUST_ENOTPD", 3: "CFUST_E
                 4: "CFUST_ENUROOT", 5: "CFUST_ENAN", 6: "CFUST_ETIMEOUT", 7: "CFUST_ECUDA",
                 8: "CFUST_ENOMEM", 9: "CFUST_ESTATE"}
 CFUST_PREC_FP64, CFUST_PREC_FP32, CFUST_PREC_MIXED = 0, 1, 2
+CFUST_FIT_NO_FINAL = 1
 CFUST_F32, CFUST_F64 = 0, 1
 # kernel classes of cfust_profile
 PROF_NAMES = ("setup", "chi_table", "plan", "level0_Tq", "level1_Tq-1", "level2_Tq-2",
@@ -81,6 +82,8 @@ def lib():
             L.cfust_mstep.argtypes = [vp]
             L.cfust_loglik.argtypes = [vp, _dp]
             L.cfust_fit.argtypes = [vp, i, d, C.POINTER(i), _dp]
+            L.cfust_fit_batch.argtypes = [i, C.POINTER(vp), i, d, i, C.POINTER(i), _dp, C.POINTER(i)]
+            L.cfust_fit_batch.restype = i
             L.cfust_tk_eval.argtypes = [vp, i, i, _dp, _dp, _dp, _dp, _dp]
             L.cfust_last_error.argtypes = [vp]
             L.cfust_last_error.restype = C.c_char_p
@@ -236,6 +239,25 @@ def cfust_fit(ctx: Context, max_iter, tol=0.0):
     it = C.c_int(0)
     _check(lib().cfust_fit(ctx.handle, int(max_iter), float(tol), C.byref(it), _ptr(hist)), ctx)
     return it.value, hist[: it.value + 1]
+
+
+def cfust_fit_batch(ctxs, max_iter, tol=0.0, flags=0):
+    """Runs cfust_fit on every context concurrently (one device-controlled graph per fit).
+
+    Returns (iters, hist, status): iters (nfits,), hist (nfits, max_iter+1) with NaN where
+    not reached, status (nfits,) of per-fit cfust_status codes (no exception for a failing
+    fit; read its message with cfust_last_error)."""
+    nf = len(ctxs)
+    handles = (C.c_void_p * max(nf, 1))(*[c.handle for c in ctxs])
+    iters = np.zeros(nf, dtype=np.int32)
+    hist = np.full((nf, int(max_iter) + 1), np.nan)
+    status = np.zeros(nf, dtype=np.int32)
+    st = lib().cfust_fit_batch(nf, handles, int(max_iter), float(tol), int(flags),
+                               iters.ctypes.data_as(C.POINTER(C.c_int)), _ptr(hist),
+                               status.ctypes.data_as(C.POINTER(C.c_int)))
+    if st != CFUST_OK and not np.any(status != CFUST_OK):
+        raise CfustError(st, cfust_last_error(None))
+    return iters, hist, status
 
 
 def cfust_tk_eval(ctx: Context, b, V, nu):

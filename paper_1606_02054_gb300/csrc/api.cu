@@ -26,7 +26,8 @@ __global__ void estep_reduce_kernel_f32(ReduceArgs);
 __global__ void reduce_partials_kernel(const double*, int, int, double*, int*);
 __global__ void loglik_partial_kernel(Dims, const double*, const double*, double*);
 __global__ void mstep_kernel(Dims, const double*, double, double, const double*, const double*,
-                             const double*, double*, double*, double*, double*, double*, int*, int*);
+                             const double*, double*, double*, double*, double*, double*, int*, int*,
+                             const int*);
 
 struct cfust_ctx {
     int p = 0, q = 0, g = 0;
@@ -79,6 +80,19 @@ struct cfust_ctx {
     bool have_data = false, have_params = false, have_stats = false;
     long long launches = 0;
     std::string err;
+    // whole-fit CUDA graph (cfust_fit_batch): captured on gst, cached per (max_iter, tol, flags)
+    bool capturing = false;
+    cudaStream_t gst = nullptr;
+    cudaGraph_t fgraph = nullptr;
+    cudaGraphExec_t fexec = nullptr;
+    int fg_max_iter = -1, fg_flags = -1;
+    double fg_tol = 0.0;
+    long long fg_body_kernels = 0, fg_final_kernels = 0;
+    FitState* fstate = nullptr;
+    double* fhist = nullptr;
+    int fhist_cap = 0;
+    FitState* h_fstate = nullptr;
+    double* h_fhist = nullptr;
 };
 
 static thread_local std::string g_create_err;
@@ -176,10 +190,11 @@ static cfust_status check_flags(cfust_ctx* c, int f, const char* where)
 // are read after the next stream synchronisation
 static void prof_begin(cfust_ctx* c, int k)
 {
-    if (c->opts.profile) cudaEventRecord(c->ev[k][0], c->st);
+    if (c->opts.profile && !c->capturing) cudaEventRecord(c->ev[k][0], c->st);
 }
 static void prof_end(cfust_ctx* c, int k, long long launches)
 {
+    if (c->capturing) return;  // graph nodes are counted when the graph runs
     c->prof_n[k] += launches;
     if (!c->opts.profile) return;
     cudaEventRecord(c->ev[k][1], c->st);
@@ -285,6 +300,13 @@ static void free_all(cfust_ctx* c)
     if (c->h_ll) cudaFreeHost(c->h_ll);
     if (c->h_flags) cudaFreeHost(c->h_flags);
     if (c->h_comp) cudaFreeHost(c->h_comp);
+    if (c->fexec) cudaGraphExecDestroy(c->fexec);
+    if (c->fgraph) cudaGraphDestroy(c->fgraph);
+    if (c->gst) cudaStreamDestroy(c->gst);
+    if (c->fstate) cudaFree(c->fstate);
+    if (c->fhist) cudaFree(c->fhist);
+    if (c->h_fstate) cudaFreeHost(c->h_fstate);
+    if (c->h_fhist) cudaFreeHost(c->h_fhist);
 }
 
 extern "C" cfust_status cfust_destroy(cfust_ctx* c)
@@ -292,6 +314,7 @@ extern "C" cfust_status cfust_destroy(cfust_ctx* c)
     if (!c) return CFUST_OK;
     cudaSetDevice(c->opts.device);
     if (c->st) cudaStreamSynchronize(c->st);
+    if (c->gst) cudaStreamSynchronize(c->gst);
     free_all(c);
     delete c;
     return CFUST_OK;
@@ -658,12 +681,10 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
     return CFUST_OK;
 }
 
-extern "C" cfust_status cfust_estep(cfust_ctx* c, double* loglik_out)
+// S0-S10 for every pair, enqueued on c->st without any host synchronisation
+// (also captured into the whole-fit graph).  l(Psi) lands in stats[width - 1].
+static cfust_status enqueue_estep(cfust_ctx* c)
 {
-    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_estep: ctx is NULL");
-    if (!c->have_data || !c->have_params)
-        return fail(c, CFUST_ESTATE, "cfust_estep: set_data and set_params must come first");
-    CU(cudaSetDevice(c->opts.device));
     CU(cudaMemsetAsync(c->flags, 0, sizeof(int), c->st));
     cfust_status s;
     if ((s = launch_setup(c)) != CFUST_OK) return s;
@@ -684,6 +705,18 @@ extern "C" cfust_status cfust_estep(cfust_ctx* c, double* loglik_out)
                                                                    c->stats, c->flags);
     LAUNCHED();
     prof_end(c, CFUST_PROF_REDUCE, 2);
+    return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_estep(cfust_ctx* c, double* loglik_out)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_estep: ctx is NULL");
+    if (!c->have_data || !c->have_params)
+        return fail(c, CFUST_ESTATE, "cfust_estep: set_data and set_params must come first");
+    CU(cudaSetDevice(c->opts.device));
+    cfust_status s;
+    if ((s = enqueue_estep(c)) != CFUST_OK) return s;
+    const int width = c->g * stats_per_comp(c->p, c->q) + 1;
     CU(cudaMemcpyAsync(c->h_ll, c->stats + (width - 1), sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CU(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CU(cudaStreamSynchronize(c->st));
@@ -725,18 +758,26 @@ extern "C" cfust_status cfust_get_stats(cfust_ctx* c, double* stats)
     return CFUST_OK;
 }
 
+// S11 into the *_n buffers; gate (device flag, may be NULL) skips it.
+static cfust_status enqueue_mstep(cfust_ctx* c, const int* gate)
+{
+    CU(cudaMemsetAsync(c->flags, 0, sizeof(int), c->st));
+    prof_begin(c, CFUST_PROF_MSTEP);
+    mstep_kernel<<<1, 32, 0, c->st>>>(c->D, c->stats, c->opts.nu_min, c->opts.nu_max, c->mu, c->Delta,
+                                      c->nu, c->pi_n, c->mu_n, c->Sigma_n, c->Delta_n, c->nu_n,
+                                      c->flags, c->comp_status, gate);
+    LAUNCHED();
+    prof_end(c, CFUST_PROF_MSTEP, 1);
+    return CFUST_OK;
+}
+
 extern "C" cfust_status cfust_mstep(cfust_ctx* c)
 {
     if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_mstep: ctx is NULL");
     if (!c->have_stats) return fail(c, CFUST_ESTATE, "cfust_mstep: run cfust_estep first");
     CU(cudaSetDevice(c->opts.device));
-    CU(cudaMemsetAsync(c->flags, 0, sizeof(int), c->st));
-    prof_begin(c, CFUST_PROF_MSTEP);
-    mstep_kernel<<<1, 32, 0, c->st>>>(c->D, c->stats, c->opts.nu_min, c->opts.nu_max, c->mu, c->Delta,
-                                      c->nu, c->pi_n, c->mu_n, c->Sigma_n, c->Delta_n, c->nu_n,
-                                      c->flags, c->comp_status);
-    LAUNCHED();
-    prof_end(c, CFUST_PROF_MSTEP, 1);
+    cfust_status s;
+    if ((s = enqueue_mstep(c, nullptr)) != CFUST_OK) return s;
     CU(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CU(cudaMemcpyAsync(c->h_comp, c->comp_status, sizeof(int) * c->g, cudaMemcpyDeviceToHost, c->st));
     CU(cudaStreamSynchronize(c->st));
@@ -769,13 +810,9 @@ extern "C" cfust_status cfust_mstep(cfust_ctx* c)
     return CFUST_OK;
 }
 
-extern "C" cfust_status cfust_loglik(cfust_ctx* c, double* out)
+// density-only pass (eq 27); l(Psi) lands in stats[0]
+static cfust_status enqueue_loglik(cfust_ctx* c)
 {
-    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_loglik: ctx is NULL");
-    if (!out) return fail(c, CFUST_EINVAL, "cfust_loglik: out is NULL");
-    if (!c->have_data || !c->have_params)
-        return fail(c, CFUST_ESTATE, "cfust_loglik: set_data and set_params must come first");
-    CU(cudaSetDevice(c->opts.device));
     CU(cudaMemsetAsync(c->flags, 0, sizeof(int), c->st));
     cfust_status s;
     if ((s = launch_setup(c)) != CFUST_OK) return s;
@@ -786,6 +823,18 @@ extern "C" cfust_status cfust_loglik(cfust_ctx* c, double* out)
     reduce_partials_kernel<<<1, 32, 0, c->st>>>(c->partial, c->nblocks_ll, 1, c->stats, c->flags);
     LAUNCHED();
     prof_end(c, CFUST_PROF_REDUCE, 2);
+    return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_loglik(cfust_ctx* c, double* out)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_loglik: ctx is NULL");
+    if (!out) return fail(c, CFUST_EINVAL, "cfust_loglik: out is NULL");
+    if (!c->have_data || !c->have_params)
+        return fail(c, CFUST_ESTATE, "cfust_loglik: set_data and set_params must come first");
+    CU(cudaSetDevice(c->opts.device));
+    cfust_status s;
+    if ((s = enqueue_loglik(c)) != CFUST_OK) return s;
     CU(cudaMemcpyAsync(c->h_ll, c->stats, sizeof(double), cudaMemcpyDeviceToHost, c->st));
     CU(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CU(cudaStreamSynchronize(c->st));
@@ -822,14 +871,249 @@ extern "C" cfust_status cfust_fit(cfust_ctx* c, int max_iter, double tol, int* i
         if (s != CFUST_OK) break;
     }
     if (s == CFUST_OK && !converged) {
-        double L;
+        double L = NAN;
         s = cfust_loglik(c, &L);
-        hist[max_iter] = L;
+        if (s == CFUST_OK) hist[max_iter] = L;
         it = max_iter;
     }
     if (iters_out) *iters_out = it;
     if (loglik_hist) std::memcpy(loglik_hist, hist.data(), sizeof(double) * ((size_t)it + 1));
     return s;
+}
+
+// ---------------------------------------------------------------------------
+// Whole-fit CUDA graph: the loop of cfust_fit with its control on the device
+// (fit_graph.cu), so a batch of fits runs concurrently without host round trips.
+// ---------------------------------------------------------------------------
+__global__ void fit_init_kernel(FitState*, int);
+__global__ void fit_gate_kernel(FitState*, const double*, const int*, double*, double);
+__global__ void fit_commit_kernel(Dims, FitState*, const int*, const int*, const double*, const double*,
+                                  const double*, const double*, const double*, double*, double*, double*,
+                                  double*, double*, int, cudaGraphConditionalHandle);
+__global__ void fit_final_gate_kernel(const FitState*, cudaGraphConditionalHandle);
+__global__ void fit_final_kernel(FitState*, const double*, const int*, double*, int);
+
+static void drop_fit_graph(cfust_ctx* c)
+{
+    if (c->fexec) cudaGraphExecDestroy(c->fexec);
+    if (c->fgraph) cudaGraphDestroy(c->fgraph);
+    c->fexec = nullptr;
+    c->fgraph = nullptr;
+    c->fg_max_iter = -1;
+}
+
+// Adds a conditional node (WHILE or IF) after dep and captures its body with fill().
+template <typename Fill>
+static cfust_status add_conditional(cfust_ctx* c, cudaGraph_t g, cudaGraphNode_t* dep,
+                                    cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                                    cudaGraphNode_t* node, long long* kernels, Fill fill)
+{
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = type;
+    cp.conditional.size = 1;
+    CU(cudaGraphAddNode(node, g, dep, nullptr, dep ? 1 : 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CU(cudaStreamBeginCaptureToGraph(c->gst, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const cudaStream_t saved = c->st;
+    c->st = c->gst;
+    c->capturing = true;
+    const long long n0 = c->launches;
+    cfust_status s = fill();
+    *kernels = c->launches - n0;
+    c->launches = n0;
+    c->capturing = false;
+    c->st = saved;
+    cudaGraph_t out = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->gst, &out);
+    if (s != CFUST_OK) return s;
+    if (e != cudaSuccess)
+        return fail(c, CFUST_ECUDA, std::string("fit graph capture: ") + cudaGetErrorString(e));
+    return CFUST_OK;
+}
+
+static cfust_status add_kernel_node(cfust_ctx* c, cudaGraph_t g, cudaGraphNode_t* dep, cudaGraphNode_t* node,
+                                    void* func, void** args, int threads)
+{
+    cudaKernelNodeParams kp{};
+    kp.func = func;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(threads);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    CU(cudaGraphAddKernelNode(node, g, dep, dep ? 1 : 0, &kp));
+    return CFUST_OK;
+}
+
+static cfust_status build_fit_graph(cfust_ctx* c, int max_iter, double tol, int flags)
+{
+    if (c->fexec && c->fg_max_iter == max_iter && c->fg_tol == tol && c->fg_flags == flags)
+        return CFUST_OK;
+    drop_fit_graph(c);
+    if (!c->gst) CU(cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking));
+    if (!c->fstate) CU(cudaMalloc((void**)&c->fstate, sizeof(FitState)));
+    if (!c->h_fstate) CU(cudaMallocHost((void**)&c->h_fstate, sizeof(FitState)));
+    if (c->fhist_cap < max_iter + 1) {
+        if (c->fhist) cudaFree(c->fhist);
+        if (c->h_fhist) cudaFreeHost(c->h_fhist);
+        c->fhist = nullptr;
+        c->h_fhist = nullptr;
+        c->fhist_cap = 0;
+        CU(cudaMalloc((void**)&c->fhist, sizeof(double) * (max_iter + 1)));
+        CU(cudaMallocHost((void**)&c->h_fhist, sizeof(double) * (max_iter + 1)));
+        c->fhist_cap = max_iter + 1;
+    }
+    cudaGraph_t g = nullptr;
+    CU(cudaGraphCreate(&g, 0));
+    c->fgraph = g;
+    cudaGraphNode_t n_hist, n_init, n_loop, n_fgate, n_final;
+    // hist := NaN (all-ones bytes), state := initial
+    cudaMemsetParams mp{};
+    mp.dst = c->fhist;
+    mp.pitch = 0;
+    mp.value = 0xFF;
+    mp.elementSize = 1;
+    mp.width = sizeof(double) * (max_iter + 1);
+    mp.height = 1;
+    CU(cudaGraphAddMemsetNode(&n_hist, g, nullptr, 0, &mp));
+    FitState* st = c->fstate;
+    int mi = max_iter;
+    {
+        void* args[] = {&st, &mi};
+        cfust_status s = add_kernel_node(c, g, &n_hist, &n_init, (void*)fit_init_kernel, args, 1);
+        if (s != CFUST_OK) return s;
+    }
+    // WHILE: one EM iteration per pass
+    cudaGraphConditionalHandle hloop;
+    CU(cudaGraphConditionalHandleCreate(&hloop, g, max_iter > 0 ? 1u : 0u, cudaGraphCondAssignDefault));
+    const int width = c->g * stats_per_comp(c->p, c->q) + 1;
+    cfust_status s = add_conditional(c, g, &n_init, hloop, cudaGraphCondTypeWhile, &n_loop,
+                                     &c->fg_body_kernels, [&]() -> cfust_status {
+        cfust_status r;
+        if ((r = enqueue_estep(c)) != CFUST_OK) return r;
+        fit_gate_kernel<<<1, 1, 0, c->st>>>(c->fstate, c->stats + (width - 1), c->flags, c->fhist, tol);
+        LAUNCHED();
+        if ((r = enqueue_mstep(c, (const int*)((char*)c->fstate + offsetof(FitState, done)))) != CFUST_OK)
+            return r;
+        fit_commit_kernel<<<1, 128, 0, c->st>>>(c->D, c->fstate, c->flags, c->comp_status, c->pi_n, c->mu_n,
+                                                c->Sigma_n, c->Delta_n, c->nu_n, c->pi, c->mu, c->Sigma,
+                                                c->Delta, c->nu, max_iter, hloop);
+        LAUNCHED();
+        return CFUST_OK;
+    });
+    if (s != CFUST_OK) return s;
+    c->fg_final_kernels = 0;
+    if (!(flags & CFUST_FIT_NO_FINAL)) {
+        // every handle must belong to a conditional node: create this one only when used
+        cudaGraphConditionalHandle hfinal;
+        CU(cudaGraphConditionalHandleCreate(&hfinal, g, 0u, cudaGraphCondAssignDefault));
+        {
+            const FitState* cst = c->fstate;
+            void* args[] = {(void*)&cst, &hfinal};
+            if ((s = add_kernel_node(c, g, &n_loop, &n_fgate, (void*)fit_final_gate_kernel, args, 1)) != CFUST_OK)
+                return s;
+        }
+        s = add_conditional(c, g, &n_fgate, hfinal, cudaGraphCondTypeIf, &n_final, &c->fg_final_kernels,
+                            [&]() -> cfust_status {
+            cfust_status r;
+            if ((r = enqueue_loglik(c)) != CFUST_OK) return r;
+            fit_final_kernel<<<1, 1, 0, c->st>>>(c->fstate, c->stats, c->flags, c->fhist, max_iter);
+            LAUNCHED();
+            return CFUST_OK;
+        });
+        if (s != CFUST_OK) return s;
+    }
+    CU(cudaGraphInstantiate(&c->fexec, g, 0));
+    c->fg_max_iter = max_iter;
+    c->fg_tol = tol;
+    c->fg_flags = flags;
+    return CFUST_OK;
+}
+
+static const char* status_name(int s)
+{
+    switch (s) {
+    case CFUST_EEMPTY: return "has no weight (sum tau = 0)";
+    case CFUST_ENOTPD: return "not positive definite";
+    default: return "failed";
+    }
+}
+
+extern "C" cfust_status cfust_fit_batch(int nfits, cfust_ctx* const* ctxs, int max_iter, double tol,
+                                        int flags, int* iters_out, double* loglik_hist,
+                                        cfust_status* status_out)
+{
+    if (nfits < 0 || (nfits > 0 && !ctxs))
+        return fail(nullptr, CFUST_EINVAL, "cfust_fit_batch: bad nfits or ctxs");
+    if (max_iter < 0) return fail(nullptr, CFUST_EINVAL, "cfust_fit_batch: max_iter < 0");
+    if (flags & ~CFUST_FIT_NO_FINAL) return fail(nullptr, CFUST_EINVAL, "cfust_fit_batch: unknown flags");
+    for (int i = 0; i < nfits; ++i) {
+        cfust_ctx* c = ctxs[i];
+        if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_fit_batch: ctxs[" + std::to_string(i) + "] is NULL");
+        if (!c->have_data || !c->have_params)
+            return fail(c, CFUST_ESTATE, "cfust_fit_batch: set_data and set_params must come first");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) return fail(nullptr, CFUST_EINVAL, "cfust_fit_batch: a context appears twice");
+    }
+    // build (or reuse) each fit's graph, then launch them all: each context's
+    // graph runs on its own stream, ordered after the work already on c->st
+    for (int i = 0; i < nfits; ++i) {
+        cfust_ctx* c = ctxs[i];
+        CU(cudaSetDevice(c->opts.device));
+        cfust_status s = build_fit_graph(c, max_iter, tol, flags);
+        if (s != CFUST_OK) {
+            drop_fit_graph(c);
+            g_create_err = "fit " + std::to_string(i) + ": " + c->err;
+            return s;
+        }
+    }
+    // a CUDA error here is not one fit's failure: report it for the batch
+    auto cuda_fail = [&](int i, const char* what, cudaError_t e) {
+        g_create_err = "cfust_fit_batch: fit " + std::to_string(i) + ": " + what + ": " +
+                       cudaGetErrorString(e);
+        ctxs[i]->err = g_create_err;
+        return CFUST_ECUDA;
+    };
+    cudaError_t e;
+    for (int i = 0; i < nfits; ++i) {
+        cfust_ctx* c = ctxs[i];
+        if ((e = cudaSetDevice(c->opts.device)) != cudaSuccess) return cuda_fail(i, "cudaSetDevice", e);
+        if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(i, "stream sync", e);
+        if ((e = cudaGraphLaunch(c->fexec, c->gst)) != cudaSuccess) return cuda_fail(i, "cudaGraphLaunch", e);
+        if ((e = cudaMemcpyAsync(c->h_fstate, c->fstate, sizeof(FitState), cudaMemcpyDeviceToHost, c->gst)) ||
+            (e = cudaMemcpyAsync(c->h_fhist, c->fhist, sizeof(double) * (max_iter + 1),
+                                 cudaMemcpyDeviceToHost, c->gst)))
+            return cuda_fail(i, "result copy", e);
+    }
+    cfust_status first = CFUST_OK;
+    for (int i = 0; i < nfits; ++i) {
+        cfust_ctx* c = ctxs[i];
+        if ((e = cudaSetDevice(c->opts.device)) != cudaSuccess) return cuda_fail(i, "cudaSetDevice", e);
+        if ((e = cudaStreamSynchronize(c->gst)) != cudaSuccess) return cuda_fail(i, "fit graph", e);
+        const FitState& fs = *c->h_fstate;
+        const int body_runs = max_iter == 0 ? 0 : (fs.final_pass ? max_iter : fs.it + 1);
+        c->launches += 1 + c->fg_body_kernels * body_runs + (fs.final_pass ? 1 + c->fg_final_kernels : 0);
+        c->have_stats = false;
+        const int it = fs.it;
+        if (iters_out) iters_out[i] = it;
+        if (loglik_hist) std::memcpy(loglik_hist + (size_t)i * (max_iter + 1), c->h_fhist,
+                                     sizeof(double) * (max_iter + 1));
+        cfust_status s = (cfust_status)fs.status;
+        if (s != CFUST_OK) {
+            if (fs.comp >= 0)
+                fail(c, s, "cfust_fit_batch: iteration " + std::to_string(it) + ": component " +
+                               std::to_string(fs.comp) + " " + status_name(s));
+            else
+                fail(c, s, "cfust_fit_batch: iteration " + std::to_string(it) +
+                               (s == CFUST_ENAN ? ": non-finite density or log-likelihood"
+                                                : ": Sigma, Omega or Lambda not positive definite"));
+            if (first == CFUST_OK) first = s;
+        }
+        if (status_out) status_out[i] = s;
+    }
+    return first;
 }
 
 extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const double* b,

@@ -196,6 +196,20 @@ struct EstepArgs {
 };
 
 // message returned by cfust_last_error(NULL) (calls without a context)
+// Device-side state of one EM fit run as a single CUDA graph (fit_graph.cu):
+// the iteration counter and the stopping decision live on the device so the
+// whole loop runs without host round trips.
+struct FitState {
+    int it;          // completed EM iterations (E-step + committed M-step)
+    int done;        // the loop has stopped
+    int converged;   // stopped by the Aitken rule
+    int status;      // cfust_status of the fit
+    int comp;        // component named by a failing M-step, else -1
+    int nuroot;      // M-steps whose nu was clamped at a bound
+    int final_pass;  // the loop ran max_iter iterations: evaluate l(Psi^(K))
+    int pad;
+};
+
 #include <string>
 void cf_set_global_error(const std::string& msg);
 

@@ -42,10 +42,11 @@ __global__ void mstep_kernel(Dims D, const double* __restrict__ stats, double nu
                              const double* __restrict__ mu, const double* __restrict__ Delta,
                              const double* __restrict__ nu, double* pi_o, double* mu_o,
                              double* Sigma_o, double* Delta_o, double* nu_o, int* flags,
-                             int* comp_status)
+                             int* comp_status, const int* gate)
 {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= D.g) return;
+    if (gate && *gate) return;  // a fit captured in a graph has already stopped
     const int p = D.p, q = D.q;
     const int S = stats_per_comp(p, q);
     const double* st = stats + (size_t)h * S;

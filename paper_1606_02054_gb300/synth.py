@@ -152,7 +152,18 @@ def init_params(rng, y, g, q, alpha=0.5, nu0=10.0):
     """Starting values for EM: k-means partition, then eq (23) per cluster
     with alpha raised in 0.1 steps (to 0.9) while Sigma is not positive
     definite."""
-    lab = kmeans(rng, y, g)
+    return params_from_labels(y, kmeans(rng, y, g), g, q, alpha, nu0)
+
+
+def random_partition_start(rng, y, g, q, alpha=0.5, nu0=10.0):
+    """Starting values from a uniformly random partition into g parts, then
+    eq (23) per part (the random-start variant of Algorithm 1)."""
+    return params_from_labels(y, rng.integers(0, g, size=y.shape[0]), g, q, alpha, nu0)
+
+
+def params_from_labels(y, lab, g, q, alpha=0.5, nu0=10.0):
+    """Eq (23) per labelled cluster (clusters with fewer than p + 2 points use
+    all of y)."""
     n, p = y.shape
     pi = np.zeros(g)
     mu = np.zeros((g, p))
@@ -190,6 +201,35 @@ WORKLOADS = {
     "wide_p16": dict(config=3, p=16, q=2, g=8, n=2_000_000, iters=20),
     "learned_p6": dict(config=5, p=6, q=6, g=6, n=1_000_000, iters=30),
 }
+
+
+# Batched fits: nfits independent problems, p uniform on {2..8}, q = p, g
+# uniform on {2..6}, n log-uniform on [1e3, 1e5], parameters drawn as for
+# flow_p4, `starts` random-partition starts per problem, 30 iterations.
+BATCH = dict(config=4, nfits=256, starts=4, p=(2, 8), g=(2, 6), n=(1_000, 100_000), iters=30)
+
+
+def make_batch(nfits=None, starts=None, n_range=None, p_range=None, g_range=None):
+    """Return dict(fits=[dict(y, truth, starts=[params...], p, q, g, n)], qmc, iters).
+    The first k problems are the same for every nfits >= k."""
+    B = BATCH
+    nfits = B["nfits"] if nfits is None else int(nfits)
+    starts = B["starts"] if starts is None else int(starts)
+    n_lo, n_hi = B["n"] if n_range is None else n_range
+    p_lo, p_hi = B["p"] if p_range is None else p_range
+    g_lo, g_hi = B["g"] if g_range is None else g_range
+    fits = []
+    for f in range(nfits):
+        rng = np.random.default_rng([seed_for(B["config"]), f])
+        p = int(rng.integers(p_lo, p_hi + 1))
+        g = int(rng.integers(g_lo, g_hi + 1))
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        truth = draw_params(rng, p, p, g)
+        y, z = sample(rng, n, truth)
+        st = [random_partition_start(np.random.default_rng([seed_for(B["config"], s + 1), f]), y, g, p)
+              for s in range(starts)]
+        fits.append(dict(y=y, z=z, truth=truth, starts=st, p=p, q=p, g=g, n=n))
+    return dict(fits=fits, qmc=qmc_settings(B["config"]), iters=B["iters"])
 
 
 def make_workload(name, n=None, start=0, with_init=True):
