@@ -37,18 +37,28 @@ if ROOT not in sys.path:
 
 METRIC = "E-step obs·comp/s and EM iter/s: chosen form vs plain GPU at stated loglik err"
 UNIT = "obs·comp/s"
-# Executed thread-instructions per lattice point of the FP32 lattice
-# integrator, per dimension k (smsp__inst_executed.sum x
-# smsp__thread_inst_executed_per_inst_executed.ratio / points) from the ncu
-# captures summarised in profiles/lattice_fp32_flow_p4.md and
-# profiles/moments_fp32_flow_p4.md.
-INSTR_PER_POINT = {("lattice", 3): 283.3, ("lattice", 4): 385.5, ("moments", 4): 465.8}
-# DRAM bytes per integral record in that capture (dram__bytes_read.sum +
-# dram__bytes_write.sum of the launch / its records at n = 4,000: 64,000
-# records for k = 3, 32,000 for k = 4, 16,000 moment records); the records dominate, so traffic
-# scales with the record count.
-INTEG_TRAFFIC_BYTES_PER_RECORD = {("lattice", 3): 2201600 / 64000, ("lattice", 4): 1566720 / 32000,
-                                  ("moments", 4): 815872 / 16000}
+# Executed thread-instructions per unit of work of the FP32 integrators
+# (smsp__inst_executed.sum x smsp__thread_inst_executed_per_inst_executed.ratio
+# / units) from the ncu captures summarised in profiles/lattice_fp32_flow_p4.md,
+# profiles/moments_fp32_flow_p4.md and profiles/t2_mixed_wide_p16.md.  Lattice
+# kernels count per lattice point (records x N x M; the same kernels run in the
+# fp32 and mixed forms), the T_2 quadrature per record (its node count depends
+# on the precision form, so the key names it).
+INSTR_PER_UNIT = {("lattice", 4): 200.5, ("moments", 4): 273.9, ("t2", 2, "mixed"): 28811.0}
+# DRAM bytes per integral record in the same captures (dram__bytes_read.sum +
+# dram__bytes_write.sum of the launch / its records: 16,000 records of each
+# lattice kind at flow_p4 n = 4,000; 320,000 T_2 records at wide_p16 n = 20,000);
+# the records dominate, so traffic scales with the record count.
+INTEG_TRAFFIC_BYTES_PER_RECORD = {("lattice", 4): 791552 / 16000, ("moments", 4): 812032 / 16000,
+                                  ("t2", 2, "mixed"): 10277120 / 320000}
+
+
+def _unit_key(kind, k, precision):
+    if precision == "fp64":
+        return None
+    return (kind, k, precision) if kind == "t2" else (kind, k)
+
+
 PRECISION_NOTE = {
     "fp64": "fp64 throughout",
     "fp32": "fp32 lattice/quadrature integrals; fp64 whitening, densities, tau, loglik, "
@@ -400,33 +410,40 @@ def main():
     value = pairs * world / (ms / 1e3)
 
     # dominant kernel class and its roofline
-    cls = {"level0_Tq": ("lattice", w["q"], 1 if chosen_moments and w["q"] >= 3 else 2),
-           "level1_Tq-1": ("lattice", w["q"] - 1, w["q"]),
-           "level2_Tq-2": ("lattice", w["q"] - 2, w["q"] * (w["q"] - 1)),
-           "moments_Tq": ("moments", w["q"], 1)}
-    lat_classes = [k for k in cls if prof[k][1] > 0 and cls[k][1] >= 2]
+    cls = {"level0_Tq": (w["q"], 1 if chosen_moments and w["q"] >= 3 else 2),
+           "level1_Tq-1": (w["q"] - 1, w["q"]),
+           "level2_Tq-2": (w["q"] - 2, w["q"] * (w["q"] - 1)),
+           "moments_Tq": (w["q"], 1)}
+    lat_classes = [k for k in cls if prof[k][1] > 0 and cls[k][0] >= 2]
     dom = max(lat_classes, key=lambda k: prof[k][0])
     dom_ms_per_launch = prof[dom][0] / prof[dom][1]
-    kind, kdim, mult = cls[dom]
-    points = pairs * mult * w["qmc"]["npoints"] * w["qmc"]["nshifts"]
+    kdim, mult = cls[dom]
+    kind = "moments" if dom == "moments_Tq" else ("t2" if kdim == 2 else "lattice")
+    records = pairs * mult
+    units = records * (w["qmc"]["npoints"] * w["qmc"]["nshifts"] if kind != "t2" else 1)
+    unit_name = "record" if kind == "t2" else "lattice point"
     f_sm = (clk.get("sm_mhz") or _peaks().get("sm_max_mhz", 2070.0)) * 1e6
-    ipp = INSTR_PER_POINT.get((kind, kdim)) if args.precision != "fp64" else None
-    if ipp:
-        achieved = ipp * points / (dom_ms_per_launch / 1e3) / 1e12
+    key = _unit_key(kind, kdim, args.precision)
+    ipu = INSTR_PER_UNIT.get(key) if key else None
+    secs = dom_ms_per_launch / 1e3
+    if ipu:
+        achieved = ipu * units / secs / 1e12
         peak = SM_COUNT * LANES_PER_SM * f_sm / 1e12
-        tb = INTEG_TRAFFIC_BYTES_PER_RECORD.get((kind, kdim))
+        tb = INTEG_TRAFFIC_BYTES_PER_RECORD.get(key)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "Tinst/s", "frac": achieved / peak,
-                "traffic": tb * pairs * mult if tb else None,
-                "kernel": dom, "k": kdim, "points_per_launch": points,
-                "inst_per_point": ipp, "gpoints_per_s": points / (dom_ms_per_launch / 1e3) / 1e9,
+                "traffic": tb * records if tb else None,
+                "kernel": dom, "k": kdim, "units_per_launch": units, "unit_of_work": unit_name,
+                "inst_per_unit": ipu, "g_units_per_s": units / secs / 1e9,
                 "ms_per_launch": dom_ms_per_launch,
                 "peak_basis": "152 SMs x 128 lanes x 1 thread-instruction/clock at the sampled "
                               "median SM clock (issue-slot ceiling)"}
     else:
-        roof = {"bound": "alu", "achieved": points / (dom_ms_per_launch / 1e3) / 1e9,
-                "peak": None, "unit": "Gpoints/s", "frac": None, "traffic": None, "kernel": dom,
-                "k": kdim, "points_per_launch": points, "ms_per_launch": dom_ms_per_launch}
+        roof = {"bound": "alu", "achieved": units / secs / 1e9, "peak": None,
+                "unit": f"G{unit_name.split()[-1]}s/s", "frac": None, "traffic": None,
+                "kernel": dom, "k": kdim, "units_per_launch": units, "unit_of_work": unit_name,
+                "ms_per_launch": dom_ms_per_launch,
+                "note": "no instruction count measured for this kernel and precision"}
 
     # end to end through the C ABI with host buffers
     e2e = None

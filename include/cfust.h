@@ -182,6 +182,13 @@ cfust_status cfust_loglik(cfust_ctx* ctx, double* out);
 cfust_status cfust_fit(cfust_ctx* ctx, int max_iter, double tol, int* iters_out,
                        double* loglik_hist);
 
+/* Diagnostic: evaluates, on `device`, the FP32 normal CDF Phi (fn = 0) or its
+ * inverse (fn = 1) exactly as the FP32 lattice integrators of T_k (k >= 3)
+ * compute them, or the CUDA math library's normcdff (fn = 2) / normcdfinvf
+ * (fn = 3) for comparison.  x and y are host arrays of count floats.  The
+ * paper needs Phi and Phi^-1 only inside T_q (Sec. 3.1); it fixes no method. */
+cfust_status cfust_special_f32(int fn, int64_t count, const float* x, float* y, int device);
+
 /* Flags of cfust_fit_batch. */
 #define CFUST_FIT_NO_FINAL 1 /* skip the density pass that gives l(Psi^(max_iter)) */
 

@@ -84,6 +84,8 @@ def lib():
             L.cfust_fit.argtypes = [vp, i, d, C.POINTER(i), _dp]
             L.cfust_fit_batch.argtypes = [i, C.POINTER(vp), i, d, i, C.POINTER(i), _dp, C.POINTER(i)]
             L.cfust_fit_batch.restype = i
+            L.cfust_special_f32.argtypes = [i, i64, vp, vp, i]
+            L.cfust_special_f32.restype = i
             L.cfust_tk_eval.argtypes = [vp, i, i, _dp, _dp, _dp, _dp, _dp]
             L.cfust_last_error.argtypes = [vp]
             L.cfust_last_error.restype = C.c_char_p
@@ -258,6 +260,15 @@ def cfust_fit_batch(ctxs, max_iter, tol=0.0, flags=0):
     if st != CFUST_OK and not np.any(status != CFUST_OK):
         raise CfustError(st, cfust_last_error(None))
     return iters, hist, status
+
+
+def cfust_special_f32(fn, x, device=0):
+    """fn 0: Phi, 1: Phi^-1 as the FP32 lattice integrators compute them;
+    2 / 3: the CUDA library's normcdff / normcdfinvf."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.empty_like(x)
+    _check(lib().cfust_special_f32(int(fn), x.size, x.ctypes.data, y.ctypes.data, int(device)))
+    return y
 
 
 def cfust_tk_eval(ctx: Context, b, V, nu):

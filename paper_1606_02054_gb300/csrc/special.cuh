@@ -39,9 +39,85 @@ __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float m_abs(float x) { return fabsf(x); }
 __device__ __forceinline__ double m_abs(double x) { return fabs(x); }
-__device__ __forceinline__ float m_ncdf(float x) { return normcdff(x); }
+// ---------------------------------------------------------------------------
+// FP32 normal CDF and inverse of the lattice integrators: this project's own
+// near-minimax polynomial fits (csrc/fit_ncdf_f32.py derives every constant
+// below), evaluated with the approximate PTX reciprocal, exp2 and log2.
+//   Phi(a) = tau 2^(P(t) - z^2 log2 e), z = |a|/sqrt 2, tau = 1/(1 + z/2), a <= 0;
+//            1 - Phi(-a) for a > 0.  Error (measured on the device against FP64):
+//            2.5e-6 relative for a >= -5, 1.3e-5 at the bottom of FP32's normal
+//            range (a = -13); it comes from the FP32 rounding of z sqrt(log2 e)
+//            and of the exponent, and stays far below the lattice's QMC error.
+//   Phi^-1(p) = x Q(t), x = log2(-log2 pm), t affine in x, pm = min(p, 1 - p); negated for
+//            p > 1/2.  Error (measured on the device): 7.6e-7 absolute for
+//            |y| <= 1 (the approximate log2 near p = 1/2), 5.7e-7 relative
+//            beyond, on p in [1e-37, 1 - 6e-8].  No branch: every lane runs one
+//            polynomial.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ptx_rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ptx_ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ptx_lg2_approx(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float cf_ncdf_f32(float a)
+{
+    const float zs = fabsf(a) * 0.8493218f;  // z sqrt(log2 e)
+    const float tau = ptx_rcp_approx(fmaf(zs, 0.41627732f, 1.0f));
+    const float t = fmaf(tau, 2.4210527f, -1.4210526f);
+    float P = 9.749631e-05f;
+    P = fmaf(P, t, -0.00055511825f);
+    P = fmaf(P, t, -0.00034124474f);
+    P = fmaf(P, t, 0.0049820864f);
+    P = fmaf(P, t, -0.0012651688f);
+    P = fmaf(P, t, -0.041432276f);
+    P = fmaf(P, t, 0.021236187f);
+    P = fmaf(P, t, 0.81600434f);
+    P = fmaf(P, t, -1.7987266f);
+    const float h = tau * ptx_ex2_approx(fmaf(-zs, zs, P));
+    return a > 0.0f ? 1.0f - h : h;
+}
+
+__device__ __forceinline__ float cf_ncdfinv_f32(float p)
+{
+    const float pm = fminf(p, 1.0f - p);
+    const float x = ptx_lg2_approx(-ptx_lg2_approx(pm));
+    const float t = fmaf(x, 0.2857142984867096f, -1.0f);
+    float Q = -6.053980087017408e-06f;
+    Q = fmaf(Q, t, -0.0001364098279736936f);
+    Q = fmaf(Q, t, -0.0008223482873290777f);
+    Q = fmaf(Q, t, -0.004026791080832481f);
+    Q = fmaf(Q, t, -0.020278355106711388f);
+    Q = fmaf(Q, t, -0.08408169448375702f);
+    Q = fmaf(Q, t, -0.25317469239234924f);
+    Q = fmaf(Q, t, -0.5432434678077698f);
+    Q = fmaf(Q, t, -0.9593654870986938f);
+    Q *= x;  // Phi^-1(1/2) = 0 exactly
+    return p > 0.5f ? -Q : Q;
+}
+
+// FP32 reciprocal and division by the approximate PTX reciprocal (relative
+// error ~1 ulp); the FP64 versions stay exact IEEE operations.
+__device__ __forceinline__ float m_rcp(float x) { return ptx_rcp_approx(x); }
+__device__ __forceinline__ double m_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float m_div(float a, float b) { return a * ptx_rcp_approx(b); }
+__device__ __forceinline__ double m_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float m_ncdf(float x) { return cf_ncdf_f32(x); }
 __device__ __forceinline__ double m_ncdf(double x) { return normcdf(x); }
-__device__ __forceinline__ float m_ncdfinv(float x) { return normcdfinvf(x); }
+__device__ __forceinline__ float m_ncdfinv(float x) { return cf_ncdfinv_f32(x); }
 __device__ __forceinline__ double m_ncdfinv(double x) { return normcdfinv(x); }
 __device__ __forceinline__ float m_sin(float x) { return sinf(x); }
 __device__ __forceinline__ double m_sin(double x) { return sin(x); }
@@ -132,20 +208,20 @@ template <typename R>
 __device__ __forceinline__ R betacf_dev(R a, R b, R x)
 {
     const R tiny = Lim<R>::tiny();
-    R c = R(1), d = R(1) - (a + b) * x / (a + R(1));
+    R c = R(1), d = R(1) - m_div((a + b) * x, a + R(1));
     if (m_abs(d) < tiny) d = tiny;
-    d = R(1) / d;
+    d = m_rcp(d);
     R h = d;
     for (int m = 1; m <= Lim<R>::cf_iters; ++m) {
         const R mm = R(m), m2 = R(2 * m);
-        R aa = mm * (b - mm) * x / ((a - R(1) + m2) * (a + m2));
+        R aa = m_div(mm * (b - mm) * x, (a - R(1) + m2) * (a + m2));
         d = R(1) + aa * d; if (m_abs(d) < tiny) d = tiny;
-        c = R(1) + aa / c; if (m_abs(c) < tiny) c = tiny;
-        d = R(1) / d; h *= d * c;
-        aa = -(a + mm) * (a + b + mm) * x / ((a + m2) * (a + R(1) + m2));
+        c = R(1) + m_div(aa, c); if (m_abs(c) < tiny) c = tiny;
+        d = m_rcp(d); h *= d * c;
+        aa = m_div(-(a + mm) * (a + b + mm) * x, (a + m2) * (a + R(1) + m2));
         d = R(1) + aa * d; if (m_abs(d) < tiny) d = tiny;
-        c = R(1) + aa / c; if (m_abs(c) < tiny) c = tiny;
-        d = R(1) / d;
+        c = R(1) + m_div(aa, c); if (m_abs(c) < tiny) c = tiny;
+        d = m_rcp(d);
         const R del = d * c;
         h *= del;
         if (m_abs(del - R(1)) < Lim<R>::eps()) break;
@@ -158,7 +234,7 @@ __device__ __forceinline__ R t1cdf_dev(R t, R nu, R lgb)
 {
     if (t == R(0)) return R(0.5);
     const R t2 = t * t, den = nu + t2;
-    const R x = nu / den, y = t2 / den;
+    const R x = m_div(nu, den), y = m_div(t2, den);
     const R a = R(0.5) * nu, b = R(0.5);
     const R ld = m_log(den);
     const R lbt = lgb + a * (m_log(nu) - ld) + b * (R(2) * m_log(m_abs(t)) - ld);
@@ -167,7 +243,7 @@ __device__ __forceinline__ R t1cdf_dev(R t, R nu, R lgb)
     const bool direct = x < (a + R(1)) / (a + b + R(2));
     const R cf = betacf_dev<R>(direct ? a : b, direct ? b : a, direct ? x : y);
     const R pre = m_exp(lbt) * cf;
-    const R I = direct ? pre / a : R(1) - pre / b;
+    const R I = direct ? m_div(pre, a) : R(1) - m_div(pre, b);
     const R tail = R(0.5) * I;
     return t > R(0) ? R(1) - tail : tail;
 }
@@ -468,7 +544,7 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
                 for (int l = 0; l <= r; ++l) z += Lf[r][l] * y[l];
                 y[r] = z;
             }
-            const R is = R(1) / s;
+            const R is = m_rcp(s);
             const R fs = f * is, fs2 = fs * is;  // X = Z / s
             af += f;
 #pragma unroll
