@@ -77,7 +77,9 @@ typedef struct {
     int device;          /* CUDA device ordinal (default 0) */
     void* cuda_stream;   /* cudaStream_t to issue work on (default NULL) */
     int t2_nodes;        /* Gauss-Legendre nodes per piece of the T_2 quadrature, 8..64
-                            (0: 64 in FP64 mode, 32 in FP32 mode, 24 in mixed mode) */
+                            (0: 64 in FP64 mode, 32 in the FP32 and mixed modes, where
+                            the T_1 inside each node is interpolated from a per-dof
+                            table built once per E-step) */
     int profile;         /* 1: time every kernel class with CUDA events on the context
                             stream (read with cfust_profile); 0 (default): off */
     int moments;         /* truncated-t moments of eqs (16)-(17) for q >= 3:

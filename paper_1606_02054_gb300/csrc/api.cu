@@ -17,6 +17,7 @@ __global__ void setup_components_kernel(Dims, Layout, const double*, const doubl
                                         const double*, double*, int*);
 __global__ void chi_table_kernel(int, const double*, Lattice, const double*, double*, float*);
 __global__ void dof_consts_kernel(Dims, Layout, const double*, int, double*, double*, float*);
+__global__ void t1_table_kernel(int, const double*, float2*);
 __global__ void widen_kernel(const float*, long long, Dims, double*);
 __global__ void narrow_kernel(const double*, Dims, float*);
 
@@ -59,6 +60,7 @@ struct cfust_ctx {
     double *partial = nullptr, *stats = nullptr;
     int *flags = nullptr, *comp_status = nullptr;
     float* stage32 = nullptr;
+    float2* t1tab = nullptr;  // FP32 T_2: per-dof tables of T_1 at dof + 1
     // mixed precision: FP32 copies of the observations and factor blocks
     bool mixed = false;
     float* y32 = nullptr;
@@ -286,7 +288,7 @@ static void free_all(cfust_ctx* c)
                     c->Delta_n, c->nu_n, c->F, c->dofs, c->cst64, c->cst32, c->chi64, c->chi32, c->shf64, c->shf32,
                     c->glx64, c->glw64, c->glx32, c->glw32, c->logf, c->u, c->elogu, c->eu,
                     c->euu, c->se, c->tau, c->partial, c->stats, c->flags, c->comp_status,
-                    c->stage32, c->pd, c->pc, c->fix_count, c->fix_list, c->y32, c->F32};
+                    c->stage32, c->pd, c->pc, c->fix_count, c->fix_list, c->y32, c->F32, c->t1tab};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (RecSet& r : c->rec) {
@@ -365,8 +367,8 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
         }
     }
     c->mixed = o.precision == CFUST_PREC_MIXED;
-    c->t2n = o.t2_nodes ? o.t2_nodes
-                        : (o.precision == CFUST_PREC_FP64 ? 64 : (c->mixed ? 24 : 32));
+    // a warp evaluates 32 nodes at a time: fewer than 32 per piece saves nothing
+    c->t2n = o.t2_nodes ? o.t2_nodes : (o.precision == CFUST_PREC_FP64 ? 64 : 32);
     cudaDeviceProp prop;
     if ((e = cudaGetDeviceProperties(&prop, o.device)) != cudaSuccess) {
         cfust_status s = fail(nullptr, CFUST_ECUDA, std::string("cfust_create: ") + cudaGetErrorString(e));
@@ -422,6 +424,10 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
         ALLOC(F32, (size_t)g * c->Ly.stride);
     }
     ALLOC(fix_count, 1); ALLOC(fix_list, ng);
+    // T_2 records exist at q = 2 (level 0) and, in the recursion form, at q = 3, 4 (levels 1, 2)
+    if (o.precision != CFUST_PREC_FP64 && (q == 2 || (!c->single_pass && (q == 3 || q == 4)))) {
+        ALLOC(t1tab, (size_t)3 * g * T1TAB_N);
+    }
     {
         const bool sp = c->single_pass;
         const int kdim[4] = {q, q - 1, q - 2, q};
@@ -584,11 +590,16 @@ static cfust_status launch_setup(cfust_ctx* c)
     LAUNCHED();
     dof_consts_kernel<<<1, 64, 0, c->st>>>(c->D, c->Ly, c->F, 3 * c->g, c->dofs, c->cst64, c->cst32);
     LAUNCHED();
+    if (c->t1tab) {
+        const int total = 3 * c->g * T1TAB_N;
+        t1_table_kernel<<<(total + 255) / 256, 256, 0, c->st>>>(3 * c->g, c->dofs, c->t1tab);
+        LAUNCHED();
+    }
     if (c->mixed) {
         cudaError_t e = launch_factors_f32(c->F, c->F32, (long long)c->g * c->Ly.stride, c->st, &c->launches);
         if (e != cudaSuccess) return fail(c, CFUST_ECUDA, std::string("factor copy: ") + cudaGetErrorString(e));
     }
-    prof_end(c, CFUST_PROF_SETUP, c->mixed ? 3 : 2);
+    prof_end(c, CFUST_PROF_SETUP, 2 + (c->mixed ? 1 : 0) + (c->t1tab ? 1 : 0));
     if (c->q >= 3) {
         prof_begin(c, CFUST_PROF_CHI);
         const long long total = 3LL * c->g * c->lat.N * c->lat.M;
@@ -609,6 +620,7 @@ static IntegArgs integ_args(const cfust_ctx* c)
     ia.chi64 = c->chi64; ia.chi32 = c->chi32; ia.shf64 = c->shf64; ia.shf32 = c->shf32;
     ia.glx64 = c->glx64; ia.glw64 = c->glw64; ia.glx32 = c->glx32; ia.glw32 = c->glw32;
     ia.t2n = c->t2n;
+    ia.t1tab = c->t1tab;
     return ia;
 }
 
@@ -1165,10 +1177,14 @@ extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const doub
     r.nrec = count;
     double *dF = nullptr, *t64 = nullptr, *k64 = nullptr;
     float *t32 = nullptr, *k32 = nullptr;
+    float2* t1t = nullptr;
+    // FP32 T_2 reads per-case T_1 tables (32 KB each) when the cases are few
+    const bool use_t1tab = k == 2 && c->opts.precision != CFUST_PREC_FP64 && count <= 4096;
     cudaError_t e = cudaSuccess;
     auto cleanup = [&]() {
         cudaFree(r.bt); cudaFree(r.fac); cudaFree(r.tab); cudaFree(r.dof); cudaFree(r.res);
         cudaFree(r.se); cudaFree(dF); cudaFree(t64); cudaFree(t32); cudaFree(k64); cudaFree(k32);
+        cudaFree(t1t);
     };
     if ((e = dalloc(&r.bt, bt.size())) != cudaSuccess || (e = dalloc(&r.fac, count)) != cudaSuccess ||
         (e = dalloc(&r.tab, count)) != cudaSuccess || (e = dalloc(&r.dof, count)) != cudaSuccess ||
@@ -1177,7 +1193,8 @@ extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const doub
         (e = dalloc(&k64, (size_t)count * CST_STRIDE)) != cudaSuccess ||
         (e = dalloc(&k32, (size_t)count * CST_STRIDE)) != cudaSuccess ||
         (e = dalloc(&t64, lattice ? NM * count : 1)) != cudaSuccess ||
-        (e = dalloc(&t32, lattice ? NM * count : 1)) != cudaSuccess) {
+        (e = dalloc(&t32, lattice ? NM * count : 1)) != cudaSuccess ||
+        (e = dalloc(&t1t, use_t1tab ? (size_t)count * T1TAB_N : 1)) != cudaSuccess) {
         cleanup();
         return fail(c, CFUST_ENOMEM, std::string("cfust_tk_eval: ") + cudaGetErrorString(e));
     }
@@ -1197,7 +1214,14 @@ extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const doub
             c->launches++;
             if ((e = cudaGetLastError())) break;
         }
+        if (use_t1tab) {
+            const int total = count * T1TAB_N;
+            t1_table_kernel<<<(total + 255) / 256, 256, 0, c->st>>>(count, r.dof, t1t);
+            c->launches++;
+            if ((e = cudaGetLastError())) break;
+        }
         IntegArgs ia = integ_args(c);
+        ia.t1tab = use_t1tab ? t1t : nullptr;
         ia.cst64 = k64;
         ia.cst32 = k32;
         ia.F = dF;

@@ -54,13 +54,15 @@ __global__ void __launch_bounds__(128) fixup_kernel(EstepArgs a, const int* coun
             const double* Lq = F + fac_l0(a.Ly);
             const double* chi2 = chi + 2 * NM;
             switch (q) {
-            case 3: alpha = tk_lattice_mom_warp<double, 3>(bt, Lq, chi2, a.shf64, a.lat, lane, m, m + 3, acc); break;
-            case 4: alpha = tk_lattice_mom_warp<double, 4>(bt, Lq, chi2, a.shf64, a.lat, lane, m, m + 4, acc); break;
-            case 5: alpha = tk_lattice_mom_warp<double, 5>(bt, Lq, chi2, a.shf64, a.lat, lane, m, m + 5, acc); break;
-            case 6: alpha = tk_lattice_mom_warp<double, 6>(bt, Lq, chi2, a.shf64, a.lat, lane, m, m + 6, acc); break;
-            case 7: alpha = tk_lattice_mom_warp<double, 7>(bt, Lq, chi2, a.shf64, a.lat, lane, m, m + 7, acc); break;
-            default: alpha = tk_lattice_mom_warp<double, 8>(bt, Lq, chi2, a.shf64, a.lat, lane, m, m + 8, acc); break;
+            case 3: alpha = tk_lattice_mom_warp<double, 3>(bt, Lq, chi2, a.shf64, a.lat, lane, acc); break;
+            case 4: alpha = tk_lattice_mom_warp<double, 4>(bt, Lq, chi2, a.shf64, a.lat, lane, acc); break;
+            case 5: alpha = tk_lattice_mom_warp<double, 5>(bt, Lq, chi2, a.shf64, a.lat, lane, acc); break;
+            case 6: alpha = tk_lattice_mom_warp<double, 6>(bt, Lq, chi2, a.shf64, a.lat, lane, acc); break;
+            case 7: alpha = tk_lattice_mom_warp<double, 7>(bt, Lq, chi2, a.shf64, a.lat, lane, acc); break;
+            default: alpha = tk_lattice_mom_warp<double, 8>(bt, Lq, chi2, a.shf64, a.lat, lane, acc); break;
             }
+            for (int k = 0; k < q + q * (q + 1) / 2; ++k) m[k] = acc[1 + k];
+            __syncwarp();
             PairOut o;
             pair_assemble_sp(F, a.Ly, p, q, c, d, logtp, alpha_s, alpha, m, o);
             if (lane == 0) {

@@ -15,15 +15,14 @@ __global__ void __launch_bounds__(256) lattice_mom_kernel_32(RecSet r, IntegArgs
     __shared__ double slot[8][W + 1];
     double* acc = slot[threadIdx.x >> 5];
     for (long long i = warp; i < r.nrec; i += nwarps) {
-        double bt[K], m[W];
+        double bt[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) bt[k] = r.bt[i * K + k];
         const double v = tk_lattice_mom_warp<float, K>(bt, a.F + r.fac[i], a.chi32 + (size_t)r.tab[i] * NM,
-                                                      a.shf32, a.lat, lane, m, m + K, acc);
-        if (lane == 0) {
-            r.res[i] = v;
-            for (int k = 0; k < W; ++k) r.mom[i * W + k] = m[k];
-        }
+                                                      a.shf32, a.lat, lane, acc);
+        if (lane == 0) r.res[i] = v;
+        for (int k = lane; k < W; k += CF_WARP) r.mom[i * W + k] = acc[1 + k];
+        __syncwarp();  // the slot is reset by the next record
     }
 }
 

@@ -15,8 +15,9 @@ __global__ void __launch_bounds__(256) t2_records_kernel(RecSet r, IntegArgs a)
     for (long long i = warp; i < r.nrec; i += nwarps) {
         const R* c = cst + r.tab[i] * CST_STRIDE;
         const R rho = (R)a.F[r.fac[i] + 2];  // L[1][0] of the 2 x 2 correlation factor
+        const float2* tab = f32 && a.t1tab ? a.t1tab + (size_t)r.tab[i] * T1TAB_N : nullptr;
         const double v = t2cdf_warp<R>((R)r.bt[2 * i], (R)r.bt[2 * i + 1], rho, (R)r.dof[i], c[CST_LGB],
-                                       c[CST_LGB1], c[CST_C2], a.t2n, glx, glw, lane);
+                                       c[CST_LGB1], c[CST_C2], a.t2n, glx, glw, lane, tab);
         if (lane == 0) {
             r.res[i] = v;
             if (r.se) r.se[i] = 0.0;

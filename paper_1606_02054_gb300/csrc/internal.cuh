@@ -141,7 +141,14 @@ struct IntegArgs {
     const float* glx32;
     const float* glw32;
     int t2n;
+    // FP32 T_2: per tab, log2 T_1(-|z|; dof + 1) on the grid of T1TAB_N points
+    // uniform in v = asinh(|z|)/ln 2 over [0, T1TAB_V], with d/dv (float2 each);
+    // NULL: the continued fraction is used instead
+    const float2* t1tab;
 };
+
+constexpr int T1TAB_N = 4096;
+constexpr float T1TAB_V = 48.0f;
 
 struct CombineArgs {
     Dims D;

@@ -241,3 +241,37 @@ __global__ void narrow_kernel(const double* __restrict__ src, Dims D, float* __r
          t += (long long)gridDim.x * blockDim.x)
         dst[t] = (float)src[t];
 }
+
+// log T_1(-w; nu) for w >= 0 in FP64, without underflow: with x = nu/(nu+w^2),
+// T_1(-w) = I_x(nu/2, 1/2)/2 from the continued fraction in log form.
+static __device__ double log_t1_lower(double w, double nu)
+{
+    if (w == 0.0) return -CF_LN2;
+    const double w2 = w * w, den = nu + w2;
+    const double x = nu / den, y = w2 / den;
+    const double a = 0.5 * nu, b = 0.5;
+    const double lbt = lgamma(a + b) - lgamma(a) - lgamma(b) + a * log(x) + b * log(y);
+    if (x < (a + 1.0) / (a + b + 2.0))
+        return lbt + log(betacf_dev<double>(a, b, x)) - log(a) - CF_LN2;
+    return log1p(-exp(lbt) * betacf_dev<double>(b, a, y) / b) - CF_LN2;
+}
+
+// Tables of log2 T_1(-|z|; dofs[t] + 1) and d/dv on the asinh grid (see IntegArgs::t1tab).
+__global__ void t1_table_kernel(int ndof, const double* __restrict__ dofs, float2* __restrict__ tab)
+{
+    const long long total = (long long)ndof * T1TAB_N;
+    const double hv = (double)T1TAB_V / (T1TAB_N - 1);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int t = (int)(e / T1TAB_N), i = (int)(e % T1TAB_N);
+        const double nu = dofs[t] + 1.0;
+        const double v = i * hv;
+        const double w = sinh(v * CF_LN2);
+        const double lT = log_t1_lower(w, nu);
+        // d/dv log2 T_1(-w(v)) = -t_nu(w) cosh(v ln 2) / T_1(-w)
+        const double lt = lgamma(0.5 * (nu + 1.0)) - lgamma(0.5 * nu) - 0.5 * log(nu * CF_PI) -
+                          0.5 * (nu + 1.0) * log1p(w * w / nu);
+        const double d = -exp(lt - lT) * cosh(v * CF_LN2);
+        tab[e] = make_float2((float)(lT / CF_LN2), (float)d);
+    }
+}

@@ -26,6 +26,7 @@
 #include "internal.cuh"
 
 #define CF_PI 3.141592653589793238462643383279502884
+#define CF_LN2 0.693147180559945309417232121458176568
 #define CF_FULL 0xffffffffu
 
 // ---------------------------------------------------------------------------
@@ -254,6 +255,31 @@ __device__ __forceinline__ double t1_lgb(double nu)
 }
 
 // ---------------------------------------------------------------------------
+// T_1(z; nu + 1) inside an FP32 T_2 from its per-dof table (IntegArgs::t1tab):
+// cubic Hermite interpolation of log2 T_1(-|z|) in v = asinh(|z|)/ln 2 (values
+// and derivatives tabulated in FP64, see t1_table_kernel), continued linearly
+// beyond the grid, where log2 T_1 approaches its asymptote -(nu+1) v + const.
+// T_1(z) = 1 - T_1(-z) for z > 0.  Interpolation error ~1e-8 in log2 T_1;
+// the FP32 table values bound the result at ~5e-6 relative in the far tail.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float t1cdf_table(float z, const float2* __restrict__ tab)
+{
+    constexpr float hv = T1TAB_V / (T1TAB_N - 1);
+    const float w = fabsf(z);
+    const float v = ptx_lg2_approx(w + sqrtf(fmaf(w, w, 1.0f)));
+    const float pos = fminf(v * (1.0f / hv), (float)(T1TAB_N - 1));
+    const int i = min((int)pos, T1TAB_N - 2);
+    const float t = pos - (float)i;
+    const float2 a = __ldg(tab + i), b = __ldg(tab + i + 1);
+    const float m0 = hv * a.y, m1 = hv * b.y, dl = b.x - a.x;
+    const float c2 = 3.0f * dl - 2.0f * m0 - m1, c3 = m0 + m1 - 2.0f * dl;
+    float lg = fmaf(fmaf(fmaf(c3, t, c2), t, m0), t, a.x);
+    lg = v > T1TAB_V ? fmaf(v - T1TAB_V, b.y, b.x) : lg;
+    const float T = ptx_ex2_approx(lg);
+    return z > 0.0f ? 1.0f - T : T;
+}
+
+// ---------------------------------------------------------------------------
 // T_2(h, k; rho, nu), standard bivariate t, warp-cooperative.
 // With theta = phi - pi/2 (phi in (0, pi)): cos theta = sin phi and
 // sin theta = -cos phi, so
@@ -266,9 +292,11 @@ __device__ __forceinline__ double t1_lgb(double nu)
 // the boundary layer of width ~ sqrt(1 - rho^2).
 // glx/glw: n Gauss-Legendre nodes and weights on [0, 1].
 // ---------------------------------------------------------------------------
+// t1tab (FP32 only, may be NULL): this record's table of T_1 at dof nu + 1.
 template <typename R>
 __device__ double t2cdf_warp(R h, R k, R rho, R nu, R lgb, R lgb1, R C2, int n,
-                             const R* __restrict__ glx, const R* __restrict__ glw, int lane)
+                             const R* __restrict__ glx, const R* __restrict__ glw, int lane,
+                             const float2* __restrict__ t1tab = nullptr)
 {
     if (rho >= R(1)) {
         const R m = h < k ? h : k;
@@ -309,7 +337,13 @@ __device__ double t2cdf_warp(R h, R k, R rho, R nu, R lgb, R lgb1, R C2, int n,
         R sp, cp;
         m_sincos(ph, &sp, &cp);
         const R z = (k * sp + rsn * cp) * sr;
-        const R f = m_exp(num1 * m_log(sp)) * t1cdf_dev<R>(z, nu1, lgb1);
+        R t1;
+        if constexpr (sizeof(R) == sizeof(float)) {
+            t1 = t1tab ? t1cdf_table(z, t1tab) : t1cdf_dev<R>(z, nu1, lgb1);
+        } else {
+            t1 = t1cdf_dev<R>(z, nu1, lgb1);
+        }
+        const R f = m_exp(num1 * m_log(sp)) * t1;
         acc += glw[i] * jac * f * m_abs(L);
     }
     acc = warp_sum(acc);
@@ -473,14 +507,16 @@ __device__ double tk_lattice_warp(const double* bt, const double* Lc, const R* _
 // Lattice T_K with the truncated moments, warp-cooperative.  The separation
 // of variables also samples the last coordinate (lattice dimension K), so
 // every point gives the standardised draw X = L y / s inside {X <= bt} with
-// weight f = prod e_i.  Returns alpha = mean f (as tk_lattice_warp); m1 (K)
-// and m2 (K(K+1)/2, lower triangle) receive the ratio estimators
-// sum f X / sum f and sum f X X^T / sum f.
+// weight f = prod e_i.  Returns alpha = mean f (as tk_lattice_warp) and leaves
+// the ratio estimators in acc_sm[1..K] (m1 = sum f X / sum f) and
+// acc_sm[1+K..K+K(K+1)/2] (m2 = sum f X X^T / sum f, lower triangle), visible
+// to the whole warp until the next call; they are accumulated in the whitened
+// coordinates y (X = L y / s) and mapped through L once per record.
 // ---------------------------------------------------------------------------
 template <typename R, int K>
 __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const R* __restrict__ chi,
                                       const R* __restrict__ shf, const Lattice& lat, int lane,
-                                      double* m1, double* m2, double* acc_sm)
+                                      double* acc_sm)
 {
     // acc_sm: this warp's shared-memory slot of K + K(K+1)/2 + 1 doubles that
     // lane 0 uses for the running totals over the shifts
@@ -536,16 +572,10 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
                 y[r] = m_ncdfinv(v);
                 if (e <= Lim<R>::tiny()) f = R(0);
             }
-            // Z = L y in place, last row first (row r reads y[0..r] only)
-#pragma unroll
-            for (int r = K - 1; r >= 0; --r) {
-                R z = R(0);
-#pragma unroll
-                for (int l = 0; l <= r; ++l) z += Lf[r][l] * y[l];
-                y[r] = z;
-            }
+            // X = L y / s is linear in y: accumulate f y / s and f y y^T / s^2
+            // here and apply L once per record at the end
             const R is = m_rcp(s);
-            const R fs = f * is, fs2 = fs * is;  // X = Z / s
+            const R fs = f * is, fs2 = fs * is;
             af += f;
 #pragma unroll
             for (int r = 0; r < K; ++r) {
@@ -576,10 +606,37 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
     __syncwarp();
     const double Sf = acc_sm[0];
     const double inv = Sf > 0.0 ? 1.0 / Sf : 0.0;
+    // m1 = L E[y/s], m2 = L E[y y^T / s^2] L^T in FP64 (Lc is the full lower
+    // factor), one output per lane, written back over the totals
+    double o[2] = {0.0, 0.0};
 #pragma unroll
-    for (int r = 0; r < K; ++r) m1[r] = acc_sm[1 + r] * inv;
+    for (int u = 0; u < 2; ++u) {
+        const int t = lane + u * CF_WARP;
+        if (t >= K + K2) break;
+        double v = 0.0;
+        if (t < K) {
+            for (int l = 0; l <= t; ++l) v += Lc[t * K + l] * acc_sm[1 + l];
+        } else {
+            const int e = t - K;
+            int r = 0;
+            while ((r + 1) * (r + 2) / 2 <= e) ++r;
+            const int c = e - r * (r + 1) / 2;
+            for (int i = 0; i <= r; ++i) {
+                double w = 0.0;
+                for (int j = 0; j <= c; ++j)
+                    w += acc_sm[1 + K + (i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i)] * Lc[c * K + j];
+                v += Lc[r * K + i] * w;
+            }
+        }
+        o[u] = v * inv;
+    }
+    __syncwarp();
 #pragma unroll
-    for (int r = 0; r < K2; ++r) m2[r] = acc_sm[1 + K + r] * inv;
+    for (int u = 0; u < 2; ++u) {
+        const int t = lane + u * CF_WARP;
+        if (t < K + K2) acc_sm[1 + t] = o[u];
+    }
+    __syncwarp();
     __syncwarp();
     return Sf / ((double)N * M);
 }
