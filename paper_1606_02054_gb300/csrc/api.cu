@@ -55,6 +55,7 @@ struct cfust_ctx {
     float* shf32 = nullptr;
     double *glx64 = nullptr, *glw64 = nullptr;
     float *glx32 = nullptr, *glw32 = nullptr;
+    float *glx32h = nullptr, *glw32h = nullptr;  // T2_NH nodes for graded T_2 pieces
     double *logf = nullptr, *u = nullptr, *elogu = nullptr, *eu = nullptr, *euu = nullptr,
            *se = nullptr, *tau = nullptr;
     double *partial = nullptr, *stats = nullptr;
@@ -286,13 +287,13 @@ static void free_all(cfust_ctx* c)
 {
     void* bufs[] = {c->y, c->pi, c->mu, c->Sigma, c->Delta, c->nu, c->pi_n, c->mu_n, c->Sigma_n,
                     c->Delta_n, c->nu_n, c->F, c->dofs, c->cst64, c->cst32, c->chi64, c->chi32, c->shf64, c->shf32,
-                    c->glx64, c->glw64, c->glx32, c->glw32, c->logf, c->u, c->elogu, c->eu,
+                    c->glx64, c->glw64, c->glx32, c->glw32, c->glx32h, c->glw32h, c->logf, c->u, c->elogu, c->eu,
                     c->euu, c->se, c->tau, c->partial, c->stats, c->flags, c->comp_status,
                     c->stage32, c->pd, c->pc, c->fix_count, c->fix_list, c->y32, c->F32, c->t1tab};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (RecSet& r : c->rec) {
-        void* rb[] = {r.bt, r.fac, r.tab, r.dof, r.res, r.se, r.mom};
+        void* rb[] = {r.bt, r.fac, r.tab, r.dof, r.res, r.se, r.mom, r.t2f};
         for (void* b : rb)
             if (b) cudaFree(b);
     }
@@ -413,6 +414,7 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     ALLOC(shf64, (size_t)o.qmc_shifts * CF_MAXDIM);
     ALLOC(shf32, (size_t)o.qmc_shifts * CF_MAXDIM);
     ALLOC(glx64, c->t2n); ALLOC(glw64, c->t2n); ALLOC(glx32, c->t2n); ALLOC(glw32, c->t2n);
+    ALLOC(glx32h, T2_NH); ALLOC(glw32h, T2_NH);
     ALLOC(logf, ng); ALLOC(u, ng); ALLOC(elogu, ng); ALLOC(se, ng); ALLOC(tau, ng);
     ALLOC(eu, ng * q); ALLOC(euu, ng * q * q);
     ALLOC(partial, part);
@@ -442,6 +444,7 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
             ALLOC(rec[l].fac, nr); ALLOC(rec[l].tab, nr);
             ALLOC(rec[l].dof, nr); ALLOC(rec[l].res, nr);
             if (l == 0) { ALLOC(rec[l].se, nr); }
+            if (r.k == 2 && o.precision != CFUST_PREC_FP64) { ALLOC(rec[l].t2f, 2 * nr); }
             if (l == 3) { ALLOC(rec[l].mom, nr * (q + q * (q + 1) / 2)); }
         }
     }
@@ -466,6 +469,9 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     std::vector<double> gx, gw;
     gauss_legendre01(c->t2n, gx, gw);
     std::vector<float> gx32(gx.begin(), gx.end()), gw32(gw.begin(), gw.end());
+    std::vector<double> gxh, gwh;
+    gauss_legendre01(T2_NH, gxh, gwh);
+    std::vector<float> gxh32(gxh.begin(), gxh.end()), gwh32(gwh.begin(), gwh.end());
     cfust_status s = CFUST_OK;
     auto cp = [&](void* dst, const void* src, size_t bytes) {
         cudaError_t ee = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
@@ -478,6 +484,8 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     cp(c->glw64, gw.data(), sizeof(double) * gw.size());
     cp(c->glx32, gx32.data(), sizeof(float) * gx32.size());
     cp(c->glw32, gw32.data(), sizeof(float) * gw32.size());
+    cp(c->glx32h, gxh32.data(), sizeof(float) * gxh32.size());
+    cp(c->glw32h, gwh32.data(), sizeof(float) * gwh32.size());
     if (s != CFUST_OK) {
         free_all(c);
         delete c;
@@ -620,6 +628,7 @@ static IntegArgs integ_args(const cfust_ctx* c)
     ia.chi64 = c->chi64; ia.chi32 = c->chi32; ia.shf64 = c->shf64; ia.shf32 = c->shf32;
     ia.glx64 = c->glx64; ia.glw64 = c->glw64; ia.glx32 = c->glx32; ia.glw32 = c->glw32;
     ia.t2n = c->t2n;
+    ia.glx32h = c->glx32h; ia.glw32h = c->glw32h;
     ia.t1tab = c->t1tab;
     return ia;
 }
@@ -1184,7 +1193,7 @@ extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const doub
     auto cleanup = [&]() {
         cudaFree(r.bt); cudaFree(r.fac); cudaFree(r.tab); cudaFree(r.dof); cudaFree(r.res);
         cudaFree(r.se); cudaFree(dF); cudaFree(t64); cudaFree(t32); cudaFree(k64); cudaFree(k32);
-        cudaFree(t1t);
+        cudaFree(t1t); cudaFree(r.t2f);
     };
     if ((e = dalloc(&r.bt, bt.size())) != cudaSuccess || (e = dalloc(&r.fac, count)) != cudaSuccess ||
         (e = dalloc(&r.tab, count)) != cudaSuccess || (e = dalloc(&r.dof, count)) != cudaSuccess ||
@@ -1194,7 +1203,8 @@ extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const doub
         (e = dalloc(&k32, (size_t)count * CST_STRIDE)) != cudaSuccess ||
         (e = dalloc(&t64, lattice ? NM * count : 1)) != cudaSuccess ||
         (e = dalloc(&t32, lattice ? NM * count : 1)) != cudaSuccess ||
-        (e = dalloc(&t1t, use_t1tab ? (size_t)count * T1TAB_N : 1)) != cudaSuccess) {
+        (e = dalloc(&t1t, use_t1tab ? (size_t)count * T1TAB_N : 1)) != cudaSuccess ||
+        (k == 2 && c->opts.precision != CFUST_PREC_FP64 && (e = dalloc(&r.t2f, (size_t)2 * count)) != cudaSuccess)) {
         cleanup();
         return fail(c, CFUST_ENOMEM, std::string("cfust_tk_eval: ") + cudaGetErrorString(e));
     }
@@ -1204,6 +1214,13 @@ extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const doub
         if ((e = cudaMemcpyAsync(r.tab, tab.data(), sizeof(int) * count, cudaMemcpyHostToDevice, c->st))) break;
         if ((e = cudaMemcpyAsync(r.dof, dofv.data(), sizeof(double) * count, cudaMemcpyHostToDevice, c->st))) break;
         if ((e = cudaMemcpyAsync(dF, fac.data(), sizeof(double) * fac.size(), cudaMemcpyHostToDevice, c->st))) break;
+        std::vector<float4> t2f;
+        if (r.t2f) {
+            t2f.resize((size_t)2 * count);
+            for (int i = 0; i < count; ++i)
+                t2_record_f32(bt[2 * i], bt[2 * i + 1], fac[(size_t)i * 4 + 2], dofv[i], &t2f[2 * i]);
+            if ((e = cudaMemcpyAsync(r.t2f, t2f.data(), sizeof(float4) * t2f.size(), cudaMemcpyHostToDevice, c->st))) break;
+        }
         dof_consts_kernel<<<(count + 127) / 128, 128, 0, c->st>>>(c->D, c->Ly, nullptr, count, r.dof, k64, k32);
         c->launches++;
         if ((e = cudaGetLastError())) break;

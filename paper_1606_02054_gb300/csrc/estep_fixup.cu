@@ -14,9 +14,14 @@ __device__ double tk_fp64(int k, const double* bt, const double* Lc, double nu, 
     switch (k) {
     case 0: return 1.0;
     case 1: return t1cdf_dev<double>(bt[0], nu, t1_lgb(nu));
-    case 2: return t2cdf_warp<double>(bt[0], bt[1], Lc[2], nu, t1_lgb(nu), t1_lgb(nu + 1.0),
-                                      exp(lgamma(0.5 * (nu + 1.0)) - lgamma(0.5 * nu)) / sqrt(CF_PI),
-                                      a.t2n, a.glx64, a.glw64, lane);
+    case 2: {
+        const double rho = Lc[2];
+        return t2cdf_warp<double>(bt[0], bt[1], rho, nu, (1.0 - rho) * (1.0 + rho),
+                                  bt[0] * (rho > 0.0 ? rho : -rho) - (rho > 0.0 ? bt[1] : -bt[1]),
+                                  t1_lgb(nu), t1_lgb(nu + 1.0),
+                                  exp(lgamma(0.5 * (nu + 1.0)) - lgamma(0.5 * nu)) / sqrt(CF_PI),
+                                  a.t2n, a.glx64, a.glw64, a.t2n, a.glx64, a.glw64, lane);
+    }
     case 3: return tk_lattice_warp<double, 3>(bt, Lc, chi, a.shf64, a.lat, lane, se);
     case 4: return tk_lattice_warp<double, 4>(bt, Lc, chi, a.shf64, a.lat, lane, se);
     case 5: return tk_lattice_warp<double, 5>(bt, Lc, chi, a.shf64, a.lat, lane, se);

@@ -7,6 +7,14 @@
 // Pairs are component-major (pid = h*n + j).
 #include "estep_common.cuh"
 
+// FP32 modes: the T_2 record's FP32 inputs (RecSet::t2f); F is the component's
+// factor block, fac the record's 2 x 2 correlation factor within it.
+__device__ __forceinline__ void put_t2f(const RecSet& L, long long rec, const double* bt,
+                                        const double* F, int fac, double dof)
+{
+    if (L.t2f) t2_record_f32(bt[0], bt[1], F[fac + 2], dof, L.t2f + 2 * rec);
+}
+
 __global__ void __launch_bounds__(128) plan_kernel(PlanArgs a)
 {
     const int p = a.D.p, q = a.D.q;
@@ -36,6 +44,7 @@ __global__ void __launch_bounds__(128) plan_kernel(PlanArgs a)
             a.L0.fac[rec] = foff + fac_l0(a.Ly);
             a.L0.tab[rec] = 3 * h + 2 * w;
             a.L0.dof[rec] = nu1 + 2.0 * w;
+            if (q == 2) put_t2f(a.L0, rec, bt, F, fac_l0(a.Ly), nu1 + 2.0 * w);
         }
         if (a.density_only) continue;
         if (a.single_pass) {
@@ -55,6 +64,7 @@ __global__ void __launch_bounds__(128) plan_kernel(PlanArgs a)
             a.L1.fac[rec] = foff + fac_l1(a.Ly, q, r);
             a.L1.tab[rec] = 3 * h + 1;
             a.L1.dof[rec] = nu1 + 1.0;
+            if (q1 == 2) put_t2f(a.L1, rec, bt, F, fac_l1(a.Ly, q, r), nu1 + 1.0);
             for (int s = 0; s < q1 && q2 > 0; ++s) {
                 const long long r2 = pid * q * q1 + r * q1 + s;
                 limits_l2(F, a.Ly, p, q, c, d, r, s, bt);
@@ -62,6 +72,7 @@ __global__ void __launch_bounds__(128) plan_kernel(PlanArgs a)
                 a.L2.fac[r2] = foff + fac_l2(a.Ly, q, r, s);
                 a.L2.tab[r2] = 3 * h;
                 a.L2.dof[r2] = nu1;
+                if (q2 == 2) put_t2f(a.L2, r2, bt, F, fac_l2(a.Ly, q, r, s), nu1);
             }
         }
     }

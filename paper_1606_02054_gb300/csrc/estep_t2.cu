@@ -14,10 +14,23 @@ __global__ void __launch_bounds__(256) t2_records_kernel(RecSet r, IntegArgs a)
     const R* cst = f32 ? (const R*)a.cst32 : (const R*)a.cst64;
     for (long long i = warp; i < r.nrec; i += nwarps) {
         const R* c = cst + r.tab[i] * CST_STRIDE;
-        const R rho = (R)a.F[r.fac[i] + 2];  // L[1][0] of the 2 x 2 correlation factor
+        R h, k, rho, nu, omr2, cr;
+        if (f32 && r.t2f) {
+            // FP32 record fields written by the plan: no FP64 instruction here
+            const float4 u0 = r.t2f[2 * i], u1 = r.t2f[2 * i + 1];
+            h = u0.x; k = u0.y; rho = u0.z; nu = u0.w; omr2 = u1.x; cr = u1.y;
+        } else {
+            const double h64 = r.bt[2 * i], k64 = r.bt[2 * i + 1];
+            const double rho64 = a.F[r.fac[i] + 2];  // L[1][0] of the 2 x 2 correlation factor
+            h = (R)h64; k = (R)k64; rho = (R)rho64; nu = (R)r.dof[i];
+            omr2 = (R)((1.0 - rho64) * (1.0 + rho64));
+            cr = (R)(h64 * (rho64 > 0.0 ? rho64 : -rho64) - (rho64 > 0.0 ? k64 : -k64));
+        }
         const float2* tab = f32 && a.t1tab ? a.t1tab + (size_t)r.tab[i] * T1TAB_N : nullptr;
-        const double v = t2cdf_warp<R>((R)r.bt[2 * i], (R)r.bt[2 * i + 1], rho, (R)r.dof[i], c[CST_LGB],
-                                       c[CST_LGB1], c[CST_C2], a.t2n, glx, glw, lane, tab);
+        const double v = t2cdf_warp<R>(h, k, rho, nu, omr2, cr, c[CST_LGB], c[CST_LGB1], c[CST_C2], a.t2n,
+                                       glx, glw, f32 ? T2_NH : a.t2n,
+                                       f32 ? (const R*)a.glx32h : glx, f32 ? (const R*)a.glw32h : glw,
+                                       lane, tab);
         if (lane == 0) {
             r.res[i] = v;
             if (r.se) r.se[i] = 0.0;

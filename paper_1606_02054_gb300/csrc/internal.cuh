@@ -102,7 +102,18 @@ struct RecSet {
     double* dof;       // degrees of freedom
     double* res;       // T_k
     double* se;        // standard error over the lattice shifts (may be null)
+    float4* t2f;       // FP32 modes, k = 2 only (else null): per record two float4,
+                       // (h, k, rho, dof) and (1 - rho^2, h|rho| - sign(rho) k, 0, 0),
+                       // the last two formed in FP64, so the T_2 kernel runs no FP64
 };
+
+// FP32 inputs of one T_2 record (see RecSet::t2f); rho = 0 counts as negative.
+__host__ __device__ inline void t2_record_f32(double h, double k, double rho, double dof, float4* out)
+{
+    out[0] = make_float4((float)h, (float)k, (float)rho, (float)dof);
+    out[1] = make_float4((float)((1.0 - rho) * (1.0 + rho)),
+                         (float)(h * (rho > 0.0 ? rho : -rho) - (rho > 0.0 ? k : -k)), 0.0f, 0.0f);
+}
 
 struct PlanArgs {
     Dims D;
@@ -141,6 +152,9 @@ struct IntegArgs {
     const float* glx32;
     const float* glw32;
     int t2n;
+    // nodes of the graded T_2 pieces (|rho| > 0.99): T2_NH per piece
+    const float* glx32h;
+    const float* glw32h;
     // FP32 T_2: per tab, log2 T_1(-|z|; dof + 1) on the grid of T1TAB_N points
     // uniform in v = asinh(|z|)/ln 2 over [0, T1TAB_V], with d/dv (float2 each);
     // NULL: the continued fraction is used instead
@@ -148,6 +162,7 @@ struct IntegArgs {
 };
 
 constexpr int T1TAB_N = 4096;
+constexpr int T2_NH = 64;
 constexpr float T1TAB_V = 48.0f;
 
 struct CombineArgs {

@@ -285,17 +285,55 @@ __device__ __forceinline__ float t1cdf_table(float z, const float2* __restrict__
 // sin theta = -cos phi, so
 //   T_2 = C_nu int_0^{phi_h} sin^{nu-1}(phi) T_1((k sin phi + rho sqrt(nu) cos phi) s_r; nu+1) dphi
 // with C_nu = Gamma((nu+1)/2)/(Gamma(nu/2) sqrt(pi)), s_r = sqrt((nu+1)/((1-rho^2) nu)),
-// phi_h = pi/2 + atan(h/sqrt(nu)).  The inner argument changes sign at
-// phi* with (sin, cos)(phi*) ~ (|rho| sqrt(nu), -k sign(rho)); the interval is
-// split there.  For |rho| > 0.99 the nodes are graded (phi = anchor + L t^3)
-// toward the split point (or toward phi_h when there is no split) to resolve
-// the boundary layer of width ~ sqrt(1 - rho^2).
-// glx/glw: n Gauss-Legendre nodes and weights on [0, 1].
-// ---------------------------------------------------------------------------
+// phi_h = pi/2 + atan(h/sqrt(nu)).  The inner argument changes sign at phi*,
+// (sin, cos)(phi*) = (|rho| sqrt(nu), -k sign(rho)) / R with R = sqrt(k^2 + rho^2 nu),
+// and equals -sign(rho) R sin(phi - phi*) exactly (rho = 0 counts as negative);
+// that form is used, with phi - phi* taken from the node's offset, so nothing
+// cancels near phi*.  The interval is split at phi*.  For |rho| > 0.99 the
+// nodes are graded (phi = anchor + L t^3) toward the split point (or toward
+// phi_h when there is no split) to resolve the boundary layer of width
+// ~ sqrt(1 - rho^2), and glxh/glwh (nh nodes) replace glx/glw (n nodes).
+// The second piece's length phi_h - phi* is computed directly (not as a
+// difference of the two angles, which can be far shorter than FP32 resolves
+// them), and it also places the upper end, so the split point and the upper
+// end move together.  Inputs are the records' FP64 values; 1 - rho^2 is
+// formed as (1 - rho)(1 + rho) in FP64.
 // t1tab (FP32 only, may be NULL): this record's table of T_1 at dof nu + 1.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct T2Setup {
+    T phis, anc0, L0, L1, d0, zs;
+    bool split;
+};
+
+// omr2 = 1 - rho^2 and cr = h |rho| - sign(rho) k come formed in FP64 (the
+// rounding of h, k and rho to FP32 would otherwise dominate both near |rho| = 1).
+template <typename T>
+__device__ __forceinline__ T2Setup<T> t2_setup(T h, T k, T rho, T nu, T omr2, T cr)
+{
+    T2Setup<T> o;
+    const T sn = m_sqrt(nu);
+    const T sg = rho > T(0) ? T(1) : T(-1);  // sign(rho), rho = 0 counting as negative
+    const T ar = m_abs(rho);
+    // phi_h = pi/2 + atan(h/sqrt(nu)), accurate for h << 0 as atan(sqrt(nu)/(-h))
+    const T phi_h = h < T(0) ? m_atan(sn / (-h)) : T(0.5 * CF_PI) + m_atan(h / sn);
+    o.phis = m_atan2(ar * sn, -sg * k);
+    // D = phi_h - phi*: the angle between (-h, sqrt nu) and (-sign(rho) k, |rho| sqrt nu)
+    const T D = m_atan2(sn * cr, sg * h * k + ar * nu);
+    o.split = rho != T(0) && D > T(0);
+    o.anc0 = o.split ? o.phis : phi_h;  // pieces run from the anchor to the far end
+    o.L0 = -o.anc0;                     // piece 0: anchor -> 0
+    o.L1 = D;                           // piece 1: phi* -> phi* + D
+    o.d0 = o.split ? T(0) : D;          // phi - phi* at piece 0's anchor
+    const T Rr = m_sqrt(rho * rho * nu + k * k);
+    o.zs = -sg * Rr * m_sqrt((nu + T(1)) / (omr2 * nu));
+    return o;
+}
+
 template <typename R>
-__device__ double t2cdf_warp(R h, R k, R rho, R nu, R lgb, R lgb1, R C2, int n,
-                             const R* __restrict__ glx, const R* __restrict__ glw, int lane,
+__device__ double t2cdf_warp(R h, R k, R rho, R nu, R omr2, R cr, R lgb, R lgb1, R C2, int n,
+                             const R* __restrict__ glx, const R* __restrict__ glw, int nh,
+                             const R* __restrict__ glxh, const R* __restrict__ glwh, int lane,
                              const float2* __restrict__ t1tab = nullptr)
 {
     if (rho >= R(1)) {
@@ -306,45 +344,34 @@ __device__ double t2cdf_warp(R h, R k, R rho, R nu, R lgb, R lgb1, R C2, int n,
         const R v = t1cdf_dev<R>(h, nu, lgb) + t1cdf_dev<R>(k, nu, lgb) - R(1);
         return v > R(0) ? (double)v : 0.0;
     }
-    const R sn = m_sqrt(nu);
-    const R hpi = R(0.5 * CF_PI);
-    // phi_h = pi/2 + atan(h/sqrt(nu)), accurate for h << 0 as atan(sqrt(nu)/(-h))
-    const R phi_h = h < R(0) ? m_atan(sn / (-h)) : hpi + m_atan(h / sn);
-    bool split = false;
-    R phis = R(0);
-    if (rho != R(0)) {
-        phis = m_atan2(m_abs(rho) * sn, rho > R(0) ? -k : k);
-        split = phis < phi_h;
-    }
     const bool graded = m_abs(rho) > R(0.99);
-    const R anc0 = split ? phis : phi_h;   // pieces run from the anchor to the far end
-    const R L0 = -anc0;                    // piece 0: anchor -> 0
-    const R L1 = phi_h - phis;             // piece 1: phi* -> phi_h
-    const int npieces = split ? 2 : 1;
-    const R sr = m_sqrt((nu + R(1)) / ((R(1) - rho * rho) * nu));
+    const T2Setup<R> S = t2_setup<R>(h, k, rho, nu, omr2, cr);
+    const int nn = graded ? nh : n;
+    const R* __restrict__ gx = graded ? glxh : glx;
+    const R* __restrict__ gw = graded ? glwh : glw;
+    const int npieces = S.split ? 2 : 1;
     const R nu1 = nu + R(1), num1 = nu - R(1);
-    const R rsn = rho * sn;
     R acc = R(0);
-    for (int t = lane; t < npieces * n; t += CF_WARP) {
-        const bool p1 = t >= n;
-        const int i = p1 ? t - n : t;
-        const R anc = p1 ? phis : anc0;
-        const R L = p1 ? L1 : L0;
-        const R u = glx[i];
+    for (int t = lane; t < npieces * nn; t += CF_WARP) {
+        const bool p1 = t >= nn;
+        const int i = p1 ? t - nn : t;
+        const R anc = p1 ? S.phis : S.anc0;
+        const R L = p1 ? S.L1 : S.L0;
+        const R u = gx[i];
         const R um = graded ? u * u * u : u;
         const R jac = graded ? R(3) * u * u : R(1);
-        const R ph = anc + L * um;
-        R sp, cp;
-        m_sincos(ph, &sp, &cp);
-        const R z = (k * sp + rsn * cp) * sr;
-        R t1;
+        const R off = L * um;
+        const R sp = m_sin(anc + off);
+        const R z = S.zs * m_sin((p1 ? R(0) : S.d0) + off);
+        R f;
         if constexpr (sizeof(R) == sizeof(float)) {
-            t1 = t1tab ? t1cdf_table(z, t1tab) : t1cdf_dev<R>(z, nu1, lgb1);
+            // sin^(nu-1) by the approximate log2/exp2 (~5e-6 relative at nu ~ 40)
+            f = ptx_ex2_approx(num1 * ptx_lg2_approx(sp)) *
+                (t1tab ? t1cdf_table(z, t1tab) : t1cdf_dev<R>(z, nu1, lgb1));
         } else {
-            t1 = t1cdf_dev<R>(z, nu1, lgb1);
+            f = m_exp(num1 * m_log(sp)) * t1cdf_dev<R>(z, nu1, lgb1);
         }
-        const R f = m_exp(num1 * m_log(sp)) * t1;
-        acc += glw[i] * jac * f * m_abs(L);
+        acc += gw[i] * jac * f * m_abs(L);
     }
     acc = warp_sum(acc);
     return (double)(C2 * acc);
@@ -537,8 +564,8 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
         step[d] = (int)(((long long)CF_WARP * lat.z[d]) % N);
         idx0[d] = (int)(((long long)lane * lat.z[d]) % N);
     }
-    if (lane == 0)
-        for (int r = 0; r <= K + K2; ++r) acc_sm[r] = 0.0;
+    for (int r = lane; r <= K + K2; r += CF_WARP) acc_sm[r] = 0.0;
+    __syncwarp();
     for (int m = 0; m < M; ++m) {
         R sh[K + 1];
 #pragma unroll

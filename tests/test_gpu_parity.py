@@ -134,6 +134,26 @@ def test_tk_integrator_edge_cases(cf, oracle):
         assert abs(v[0] - ref) <= 1e-9 * ref, (h, kk, rho, nu, v[0], ref)
 
 
+def test_t2_fp32_edge_cases(cf, oracle):
+    """FP32 T_2 (quadrature with the tabulated inner T_1) at strong correlations
+    on both sides of the node-grading threshold |rho| = 0.99, far tails down to
+    ~1e-20, and dofs from 1.5 to 200: FP32 bound 5e-5 relative."""
+    w = synth.make_workload("two_comp_p2", n=10, with_init=False)
+    ctx = cf.cfust_create(2, 2, 2, 10, _opts(cf, w, 1))
+    cases = [(-3.0, -3.0, 0.999, 5.0), (2.0, -2.0, -0.9999, 7.0), (-8.0, -7.0, 0.5, 6.0),
+             (-20.0, 3.0, 0.3, 9.0), (0.0, 0.0, 0.0, 4.0), (-6.0, -6.0, 0.95, 200.0),
+             (1.5, 0.5, 0.985, 1.5), (-30.0, -30.0, 0.2, 2.5), (0.3, -0.2, -0.989, 30.0),
+             (-4.0, 6.0, -0.7, 60.0), (5.0, 5.0, 0.1, 3.0), (-12.0, -9.0, 0.9, 15.0),
+             (-10.0, -10.0, 0.5, 60.0), (-14.0, -12.0, 0.3, 40.0)]
+    b = np.array([[h, kk] for h, kk, _, _ in cases])
+    V = np.array([[[1.0, r], [r, 1.0]] for _, _, r, _ in cases])
+    nu = np.array([c[3] for c in cases])
+    got, _ = cf.cfust_tk_eval(ctx, b, V, nu)
+    ref = np.array([oracle.t2cdf(h, kk, r, v) for h, kk, r, v in cases])
+    rel = np.abs(got - ref) / ref
+    assert np.all(rel <= 5e-5), list(zip(cases, rel))
+
+
 # ---------------------------------------------------------------------------
 # E-step, M-step, fit
 # ---------------------------------------------------------------------------
