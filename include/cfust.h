@@ -191,6 +191,26 @@ cfust_status cfust_fit(cfust_ctx* ctx, int max_iter, double tol, int* iters_out,
  * paper needs Phi and Phi^-1 only inside T_q (Sec. 3.1); it fixes no method. */
 cfust_status cfust_special_f32(int fn, int64_t count, const float* x, float* y, int device);
 
+/* Initial values by Algorithm 1 (Sec. 3.3): for each of nstarts partitions of the
+ * observations and each alpha of the grid, the moment-based start of eq (23) per cluster
+ * (cluster mean, covariance S with divisor n_h - 1 and its diagonal s*, the sign of the
+ * third moment about the mean; delta = sign sqrt(pi (1 - alpha) s* / (pi - 2)) element-wise,
+ * Sigma = S - (1 - alpha) diag(s*), mu = mean - sqrt(2/pi) delta, nu = nu0, pi_h = n_h/n;
+ * Delta is diag(delta) for q = p, the column delta for q = 1, otherwise delta on its leading
+ * diagonal) and its log-likelihood (eq 27, the density pass of cfust_loglik).  The first
+ * candidate with the highest log-likelihood becomes the context's Psi.
+ *   labels: host array nstarts x n of cluster labels in [0, g), or NULL for random
+ *           partitions drawn on the device (label_j = floor(u g), u the SplitMix64 output
+ *           for key seed ^ ((start + 1) << 40) ^ (j + 1));
+ *   alphas: nalpha values in (0, 1), or NULL for 0.1, 0.2, ..., 0.9 (nalpha 0 or 9);
+ *   loglik_out (nstarts x nalpha, may be NULL): each candidate's log-likelihood, -inf when
+ *           a cluster has fewer than 2 points or Sigma^(0) is not positive definite;
+ *   best_out (may be NULL): start * nalpha + alpha index of the chosen candidate.
+ * Returns CFUST_ENOTPD (Psi unset) when no candidate is valid.  Needs cfust_set_data. */
+cfust_status cfust_init(cfust_ctx* ctx, int nstarts, const int32_t* labels, uint64_t seed,
+                        int nalpha, const double* alphas, double nu0, double* loglik_out,
+                        int* best_out);
+
 /* Flags of cfust_fit_batch. */
 #define CFUST_FIT_NO_FINAL 1 /* skip the density pass that gives l(Psi^(max_iter)) */
 

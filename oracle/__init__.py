@@ -88,6 +88,13 @@ def lib():
             L.ora_fit.argtypes = [i, i, i, i, _dp, _dp, _dp, _dp, _dp, _dp, C.POINTER(Qmc), i, d,
                                   d, d, i, _ip, _dp]
             L.ora_fit.restype = i
+            L.ora_random_partition.argtypes = [i, i, C.c_uint64, i, _ip]
+            L.ora_random_partition.restype = None
+            L.ora_moment_start.argtypes = [i, i, i, i, _dp, _ip, d, d, _dp, _dp, _dp, _dp, _dp]
+            L.ora_moment_start.restype = i
+            L.ora_init.argtypes = [i, i, i, i, _dp, i, _ip, C.c_uint64, i, _dp, d, C.POINTER(Qmc),
+                                   i, _dp, _ip, _dp, _dp, _dp, _dp, _dp]
+            L.ora_init.restype = i
             L.ora_aitken_converged.argtypes = [d, d, d, d, _dp]
             L.ora_aitken_converged.restype = i
             _lib = L
@@ -258,3 +265,48 @@ def fit(y, params, iters, spec: Qmc | None = None, tol=0.0, nu_min=1.0, nu_max=2
         raise RuntimeError(f"ora_fit failed ({rc})")
     k = done.value
     return dict(pi=pi, mu=mu, Sigma=Sigma, Delta=Delta, nu=nu), hist[: k + 1], k
+
+
+# ---- initialisation (Sec. 3.3, Algorithm 1, eq 23) ---------------------------
+ALPHAS = tuple(round(0.1 * k, 1) for k in range(1, 10))
+
+
+def random_partition(n, g, seed, start):
+    lab = np.zeros(int(n), dtype=np.int32)
+    lib().ora_random_partition(int(n), int(g), int(seed) & 0xFFFFFFFFFFFFFFFF, int(start),
+                               lab.ctypes.data_as(_ip))
+    return lab
+
+
+def moment_start(y, labels, g, q, alpha, nu0=10.0):
+    """Eq (23) per cluster; returns (params, rc) with rc = 0 or 1 + first failing cluster."""
+    y = _f64(y)
+    n, p = y.shape
+    lab = np.ascontiguousarray(labels, dtype=np.int32)
+    out = dict(pi=np.zeros(g), mu=np.zeros((g, p)), Sigma=np.zeros((g, p, p)),
+               Delta=np.zeros((g, p, q)), nu=np.zeros(g))
+    rc = lib().ora_moment_start(n, p, q, g, _ptr(y), lab.ctypes.data_as(_ip), float(alpha),
+                                float(nu0), *[_ptr(out[k]) for k in ("pi", "mu", "Sigma", "Delta", "nu")])
+    return out, rc
+
+
+def init(y, g, q, spec: Qmc | None = None, nstarts=4, labels=None, seed=0, alphas=ALPHAS,
+         nu0=10.0, nthreads=None):
+    """Algorithm 1: returns (best params, loglik per candidate [nstarts, nalpha], best index)."""
+    y = _f64(y)
+    n, p = y.shape
+    spec = spec or qmc()
+    al = _f64(alphas)
+    lab = None if labels is None else np.ascontiguousarray(labels, dtype=np.int32).reshape(nstarts, n)
+    ll = np.zeros((nstarts, al.size))
+    best = C.c_int(-1)
+    out = dict(pi=np.zeros(g), mu=np.zeros((g, p)), Sigma=np.zeros((g, p, p)),
+               Delta=np.zeros((g, p, q)), nu=np.zeros(g))
+    rc = lib().ora_init(n, p, q, g, _ptr(y), int(nstarts),
+                        None if lab is None else lab.ctypes.data_as(_ip),
+                        int(seed) & 0xFFFFFFFFFFFFFFFF, al.size, _ptr(al), float(nu0),
+                        C.byref(spec), int(nthreads or DEFAULT_NTHREADS), _ptr(ll), C.byref(best),
+                        *[_ptr(out[k]) for k in ("pi", "mu", "Sigma", "Delta", "nu")])
+    if rc:
+        raise RuntimeError(f"ora_init failed ({rc})")
+    return out, ll, best.value

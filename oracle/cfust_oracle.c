@@ -1058,3 +1058,116 @@ int ora_fit(int n, int p, int q, int g, const double* y, double* pi, double* mu,
     free(tau); free(u); free(el); free(eu); free(euu);
     return rc;
 }
+
+/* ------------------------------------------------------------------ */
+/* Initialisation: Algorithm 1 with the moment starts of eq (23)       */
+/* (Sec. 3.3).                                                          */
+/* ------------------------------------------------------------------ */
+void ora_random_partition(int n, int g, uint64_t seed, int start, int* labels)
+{
+    /* one SplitMix64 draw per observation, label = floor(u g) */
+    for (int j = 0; j < n; ++j) {
+        uint64_t key = seed ^ ((uint64_t)(start + 1) << 40) ^ (uint64_t)(j + 1);
+        int h = (int)(ora_splitmix64_u01(key) * g);
+        labels[j] = h < g ? h : g - 1;
+    }
+}
+
+int ora_moment_start(int n, int p, int q, int g, const double* y, const int* labels,
+                     double alpha, double nu0, double* pi, double* mu, double* Sigma,
+                     double* Delta, double* nu)
+{
+    const double PI = 3.14159265358979323846;
+    double* ybar = (double*)calloc((size_t)p, sizeof(double));
+    double* S = (double*)calloc((size_t)p * p, sizeof(double));
+    double* m3 = (double*)calloc((size_t)p, sizeof(double));
+    double* L = (double*)malloc(sizeof(double) * p * p);
+    int rc = 0;
+    for (int h = 0; h < g && !rc; ++h) {
+        /* line 9: sample mean, covariance S and its diagonal s* of cluster h */
+        long long nh = 0;
+        for (int i = 0; i < p; ++i) ybar[i] = m3[i] = 0.0;
+        for (int i = 0; i < p * p; ++i) S[i] = 0.0;
+        for (int j = 0; j < n; ++j)
+            if (labels[j] == h) {
+                ++nh;
+                for (int i = 0; i < p; ++i) ybar[i] += y[(size_t)j * p + i];
+            }
+        if (nh < 2) { rc = 1 + h; break; }
+        for (int i = 0; i < p; ++i) ybar[i] /= (double)nh;
+        for (int j = 0; j < n; ++j)
+            if (labels[j] == h) {
+                const double* yj = y + (size_t)j * p;
+                for (int a = 0; a < p; ++a) {
+                    const double ra = yj[a] - ybar[a];
+                    for (int b = 0; b < p; ++b) S[a * p + b] += ra * (yj[b] - ybar[b]);
+                    m3[a] += ra * ra * ra;
+                }
+            }
+        for (int i = 0; i < p * p; ++i) S[i] /= (double)(nh - 1);
+        /* line 6: pi from the partition */
+        pi[h] = (double)nh / n;
+        /* line 10, eq (23): delta = sign(m3) sqrt(pi (1 - alpha) s* / (pi - 2)) element-wise,
+           Sigma = S - (1 - alpha) diag(s*), mu = ybar - sqrt(2/pi) delta, nu = nu0.
+           Delta (p x q): diag(delta) for q = p, the column delta for q = 1, otherwise delta
+           on the leading diagonal; only the coordinates that carry a delta are skewed. */
+        double* Dh = Delta + (size_t)h * p * q;
+        double* Sh = Sigma + (size_t)h * p * p;
+        for (int i = 0; i < p * q; ++i) Dh[i] = 0.0;
+        for (int a = 0; a < p; ++a) {
+            const int skewed = (q == 1 || q >= p || a < q);
+            const double sa = S[a * p + a];
+            const double d = skewed ? (m3[a] >= 0.0 ? 1.0 : -1.0) *
+                                          sqrt(PI * (1.0 - alpha) * sa / (PI - 2.0))
+                                    : 0.0;
+            if (q == 1) Dh[a * q] = d;
+            else if (a < q) Dh[a * q + a] = d;
+            mu[(size_t)h * p + a] = ybar[a] - sqrt(2.0 / PI) * d;
+            for (int b = 0; b < p; ++b)
+                Sh[a * p + b] = S[a * p + b] - (a == b && skewed ? (1.0 - alpha) * sa : 0.0);
+        }
+        nu[h] = nu0;
+        if (chol(p, Sh, L)) rc = 1 + h;   /* Sigma^(0) not positive definite */
+    }
+    free(ybar); free(S); free(m3); free(L);
+    return rc;
+}
+
+int ora_init(int n, int p, int q, int g, const double* y, int nstarts, const int* labels,
+             uint64_t seed, int nalpha, const double* alphas, double nu0, const ora_qmc* qmc,
+             int nthreads, double* loglik_out, int* best, double* pi, double* mu,
+             double* Sigma, double* Delta, double* nu)
+{
+    double* cp = (double*)malloc(sizeof(double) * g);
+    double* cm = (double*)malloc(sizeof(double) * g * p);
+    double* cS = (double*)malloc(sizeof(double) * g * p * p);
+    double* cD = (double*)malloc(sizeof(double) * g * p * q);
+    double* cn = (double*)malloc(sizeof(double) * g);
+    int* lab = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
+    double lbest = -INFINITY;       /* line 2 */
+    int ibest = -1, rc = 0;         /* line 3: Psi empty */
+    for (int s = 0; s < nstarts && !rc; ++s) {              /* line 4 */
+        if (labels) memcpy(lab, labels + (size_t)s * n, sizeof(int) * n);
+        else ora_random_partition(n, g, seed, s, lab);       /* line 5 */
+        for (int a = 0; a < nalpha && !rc; ++a) {            /* line 7 */
+            double L = -INFINITY;
+            if (ora_moment_start(n, p, q, g, y, lab, alphas[a], nu0, cp, cm, cS, cD, cn) == 0) {
+                rc = ora_loglik(n, p, q, g, y, cp, cm, cS, cD, cn, qmc, nthreads, &L);  /* line 12 */
+                if (rc || !isfinite(L)) { rc = 0; L = -INFINITY; }
+            }
+            if (loglik_out) loglik_out[(size_t)s * nalpha + a] = L;
+            if (L > lbest) {                                 /* lines 13-14 (and l <- l*) */
+                lbest = L;
+                ibest = s * nalpha + a;
+                memcpy(pi, cp, sizeof(double) * g);
+                memcpy(mu, cm, sizeof(double) * g * p);
+                memcpy(Sigma, cS, sizeof(double) * g * p * p);
+                memcpy(Delta, cD, sizeof(double) * g * p * q);
+                memcpy(nu, cn, sizeof(double) * g);
+            }
+        }
+    }
+    if (best) *best = ibest;
+    free(cp); free(cm); free(cS); free(cD); free(cn); free(lab);
+    return rc ? rc : (ibest < 0 ? 1 : 0);
+}

@@ -13,6 +13,7 @@
  *   Sec. 2, eqs (1)-(4): mixture and CFUST component density.
  *   Sec. 3.1, eqs (12)-(17): E-step conditional expectations.
  *   Sec. 3.2, eqs (18)-(22): M-step updates.
+ *   Sec. 3.3, eq (23), Algorithm 1: initialisation.
  *   Sec. 3.4, eqs (24)-(26): Aitken stopping rule.
  *   Sec. 4.3, eq (27): log-likelihood.
  *
@@ -117,6 +118,26 @@ int ora_fit(int n, int p, int q, int g, const double* y, double* pi,
             const ora_qmc* qmc, int max_iter, double tol, double nu_min,
             double nu_max, int nthreads, int* iters_done,
             double* loglik_hist);
+
+/* ---- Initialisation (Sec. 3.3, Algorithm 1, eq 23) ----
+ * Random partition of start s: label_j = floor(u g), u = SplitMix64 output for the key
+ * seed ^ ((s+1) << 40) ^ (j+1). */
+void ora_random_partition(int n, int g, uint64_t seed, int start, int* labels);
+/* Eq (23) per cluster of a partition (sample covariance with divisor n_h - 1, third moment
+ * about the mean for the sign of delta, nu = nu0, pi = n_h/n).  Returns 0, or 1 + h for the
+ * first cluster with fewer than 2 points or a non-PD Sigma^(0). */
+int ora_moment_start(int n, int p, int q, int g, const double* y, const int* labels,
+                     double alpha, double nu0, double* pi, double* mu, double* Sigma,
+                     double* Delta, double* nu);
+/* Algorithm 1: for each start (labels: nstarts x n, or NULL for random partitions from seed)
+ * and each alpha, the moment start and its log-likelihood (eq 27); the first candidate with
+ * the highest l is returned (l is updated as candidates improve).  loglik_out (nstarts x
+ * nalpha, may be NULL) gets -inf for invalid candidates; *best = s*nalpha + a or -1.
+ * Returns 0, or 1 when no candidate is valid. */
+int ora_init(int n, int p, int q, int g, const double* y, int nstarts, const int* labels,
+             uint64_t seed, int nalpha, const double* alphas, double nu0, const ora_qmc* qmc,
+             int nthreads, double* loglik_out, int* best, double* pi, double* mu,
+             double* Sigma, double* Delta, double* nu);
 
 /* Aitken rule (eqs 24-26) on three consecutive log-likelihoods. */
 int ora_aitken_converged(double l_km1, double l_k, double l_kp1, double eps,

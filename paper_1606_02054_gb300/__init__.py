@@ -84,6 +84,8 @@ def lib():
             L.cfust_fit.argtypes = [vp, i, d, C.POINTER(i), _dp]
             L.cfust_fit_batch.argtypes = [i, C.POINTER(vp), i, d, i, C.POINTER(i), _dp, C.POINTER(i)]
             L.cfust_fit_batch.restype = i
+            L.cfust_init.argtypes = [vp, i, vp, C.c_uint64, i, _dp, d, _dp, C.POINTER(i)]
+            L.cfust_init.restype = i
             L.cfust_special_f32.argtypes = [i, i64, vp, vp, i]
             L.cfust_special_f32.restype = i
             L.cfust_tk_eval.argtypes = [vp, i, i, _dp, _dp, _dp, _dp, _dp]
@@ -260,6 +262,22 @@ def cfust_fit_batch(ctxs, max_iter, tol=0.0, flags=0):
     if st != CFUST_OK and not np.any(status != CFUST_OK):
         raise CfustError(st, cfust_last_error(None))
     return iters, hist, status
+
+
+def cfust_init(ctx: Context, nstarts=4, labels=None, seed=0, alphas=None, nu0=10.0):
+    """Algorithm 1: sets the context's Psi to the best moment start; returns (loglik per
+    candidate [nstarts, nalpha], best index)."""
+    al = None if alphas is None else _f64(alphas)
+    nal = 9 if al is None else al.size
+    lab = None
+    if labels is not None:
+        lab = np.ascontiguousarray(labels, dtype=np.int32).reshape(nstarts, ctx.n)
+    ll = np.zeros((nstarts, nal))
+    best = C.c_int(-1)
+    _check(lib().cfust_init(ctx.handle, int(nstarts), None if lab is None else lab.ctypes.data,
+                            int(seed) & 0xFFFFFFFFFFFFFFFF, 0 if al is None else nal, _ptr(al),
+                            float(nu0), _ptr(ll), C.byref(best)), ctx)
+    return ll, best.value
 
 
 def cfust_special_f32(fn, x, device=0):

@@ -1137,6 +1137,153 @@ extern "C" cfust_status cfust_fit_batch(int nfits, cfust_ctx* const* ctxs, int m
     return first;
 }
 
+// ---------------------------------------------------------------------------
+// Initialisation (Sec. 3.3, Algorithm 1 with the moment starts of eq 23).
+// ---------------------------------------------------------------------------
+extern "C" cfust_status cfust_init(cfust_ctx* c, int nstarts, const int32_t* labels, uint64_t seed,
+                                   int nalpha, const double* alphas, double nu0, double* loglik_out,
+                                   int* best_out)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_init: ctx is NULL");
+    if (!c->have_data) return fail(c, CFUST_ESTATE, "cfust_init: set_data must come first");
+    static const double grid[9] = {0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9};
+    if (!alphas) {
+        if (nalpha != 0 && nalpha != 9)
+            return fail(c, CFUST_EINVAL, "cfust_init: with alphas NULL, nalpha must be 0 or 9");
+        alphas = grid;
+        nalpha = 9;
+    }
+    if (nstarts < 1 || nalpha < 1) return fail(c, CFUST_EINVAL, "cfust_init: need nstarts >= 1, nalpha >= 1");
+    for (int a = 0; a < nalpha; ++a)
+        if (!(alphas[a] > 0.0 && alphas[a] < 1.0))
+            return fail(c, CFUST_EINVAL, "cfust_init: alpha must lie in (0, 1)");
+    if (!(nu0 > 0.0)) return fail(c, CFUST_EINVAL, "cfust_init: nu0 must be positive");
+    const int p = c->p, q = c->q, g = c->g;
+    const long long n = c->n;
+    if (labels)
+        for (long long t = 0; t < (long long)nstarts * n; ++t)
+            if (labels[t] < 0 || labels[t] >= g)
+                return fail(c, CFUST_EINVAL, "cfust_init: labels must lie in [0, g)");
+    CU(cudaSetDevice(c->opts.device));
+    const int chunk = 64;
+    const long long nchunks = (n + chunk - 1) / chunk;
+    const int blocks = (int)std::min<long long>(nchunks, 4LL * c->nsm);
+    const int W0 = 1 + p, W1 = p * (p + 1) / 2 + p;
+    int* dlab = nullptr;
+    double *partial = nullptr, *sums = nullptr, *dmean = nullptr;
+    cudaError_t e;
+    auto cleanup = [&]() { cudaFree(dlab); cudaFree(partial); cudaFree(sums); cudaFree(dmean); };
+    if ((e = dalloc(&dlab, (size_t)n)) != cudaSuccess || (e = dalloc(&partial, (size_t)blocks * g * W1)) != cudaSuccess ||
+        (e = dalloc(&sums, (size_t)g * W1)) != cudaSuccess || (e = dalloc(&dmean, (size_t)g * p)) != cudaSuccess) {
+        cleanup();
+        return fail(c, CFUST_ENOMEM, std::string("cfust_init: ") + cudaGetErrorString(e));
+    }
+    const double PI = 3.14159265358979323846;
+    std::vector<double> s0((size_t)g * W0), s1((size_t)g * W1), mean((size_t)g * p);
+    std::vector<double> cp(g), cm((size_t)g * p), cS((size_t)g * p * p), cD((size_t)g * p * q), cn(g);
+    std::vector<double> bp, bm, bS, bD, bn;
+    double lbest = -INFINITY;  // line 2
+    int ibest = -1;            // line 3: Psi empty
+    cfust_status s = CFUST_OK;
+    for (int st = 0; st < nstarts && s == CFUST_OK; ++st) {  // line 4
+        // line 5: the partition
+        if (labels) e = cudaMemcpyAsync(dlab, labels + (size_t)st * n, sizeof(int) * n, cudaMemcpyHostToDevice, c->st);
+        else e = launch_random_partition(n, g, seed, st, dlab, c->st);
+        if (e == cudaSuccess) e = launch_cluster_moments(0, c->D, c->y, dlab, nullptr, chunk, blocks, partial, c->st);
+        if (e == cudaSuccess) {
+            reduce_partials_kernel<<<(g * W0 + 127) / 128, 128, 0, c->st>>>(partial, blocks, g * W0, sums, c->flags);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s0.data(), sums, sizeof(double) * g * W0, cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) { s = fail(c, CFUST_ECUDA, std::string("cfust_init: ") + cudaGetErrorString(e)); break; }
+        c->launches += (labels ? 0 : 1) + 2;
+        // line 9: cluster means, then the centred second and third moments
+        std::vector<long long> nh(g);
+        for (int h = 0; h < g; ++h) {
+            nh[h] = (long long)s0[(size_t)h * W0];
+            for (int i = 0; i < p; ++i) mean[(size_t)h * p + i] = nh[h] > 0 ? s0[(size_t)h * W0 + 1 + i] / nh[h] : 0.0;
+        }
+        e = cudaMemcpyAsync(dmean, mean.data(), sizeof(double) * g * p, cudaMemcpyHostToDevice, c->st);
+        if (e == cudaSuccess) e = launch_cluster_moments(1, c->D, c->y, dlab, dmean, chunk, blocks, partial, c->st);
+        if (e == cudaSuccess) {
+            reduce_partials_kernel<<<(g * W1 + 127) / 128, 128, 0, c->st>>>(partial, blocks, g * W1, sums, c->flags);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s1.data(), sums, sizeof(double) * g * W1, cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) { s = fail(c, CFUST_ECUDA, std::string("cfust_init: ") + cudaGetErrorString(e)); break; }
+        c->launches += 2;
+        for (int a = 0; a < nalpha; ++a) {  // line 7
+            const double alpha = alphas[a];
+            bool valid = true;
+            for (int h = 0; h < g && valid; ++h) {  // line 8
+                if (nh[h] < 2) { valid = false; break; }
+                const double* Sr = s1.data() + (size_t)h * W1;  // packed lower sum r r^T, then sum r^3
+                auto Sab = [&](int x, int y2) {
+                    const int hi = x > y2 ? x : y2, lo = x > y2 ? y2 : x;
+                    return Sr[hi * (hi + 1) / 2 + lo] / (double)(nh[h] - 1);
+                };
+                cp[h] = (double)nh[h] / (double)n;  // line 6
+                double* Dh = cD.data() + (size_t)h * p * q;
+                double* Sh = cS.data() + (size_t)h * p * p;
+                for (int t = 0; t < p * q; ++t) Dh[t] = 0.0;
+                // line 10, eq (23): delta = sign(m3) sqrt(pi (1 - alpha) s* / (pi - 2)) element-wise,
+                // Sigma = S - (1 - alpha) diag(s*), mu = ybar - sqrt(2/pi) delta, nu = nu0; Delta is
+                // diag(delta) (q = p), the column delta (q = 1), else delta on the leading diagonal
+                for (int x = 0; x < p; ++x) {
+                    const bool skewed = q == 1 || q >= p || x < q;
+                    const double sa = Sab(x, x);
+                    const double m3 = Sr[p * (p + 1) / 2 + x];
+                    const double d = skewed ? (m3 >= 0.0 ? 1.0 : -1.0) * std::sqrt(PI * (1.0 - alpha) * sa / (PI - 2.0)) : 0.0;
+                    if (q == 1) Dh[x * q] = d;
+                    else if (x < q) Dh[x * q + x] = d;
+                    cm[(size_t)h * p + x] = mean[(size_t)h * p + x] - std::sqrt(2.0 / PI) * d;
+                    for (int y2 = 0; y2 < p; ++y2)
+                        Sh[x * p + y2] = Sab(x, y2) - (x == y2 && skewed ? (1.0 - alpha) * sa : 0.0);
+                }
+                cn[h] = nu0;
+                // Sigma^(0) must be positive definite
+                std::vector<double> L((size_t)p * p, 0.0);
+                for (int j = 0; j < p && valid; ++j) {
+                    double sum = Sh[j * p + j];
+                    for (int k = 0; k < j; ++k) sum -= L[j * p + k] * L[j * p + k];
+                    if (!(sum > 0.0)) { valid = false; break; }
+                    L[j * p + j] = std::sqrt(sum);
+                    for (int i2 = j + 1; i2 < p; ++i2) {
+                        double t = Sh[i2 * p + j];
+                        for (int k = 0; k < j; ++k) t -= L[i2 * p + k] * L[j * p + k];
+                        L[i2 * p + j] = t / L[j * p + j];
+                    }
+                }
+            }
+            double L = -INFINITY;
+            if (valid) {
+                cfust_params P{cp.data(), cm.data(), cS.data(), cD.data(), cn.data()};
+                cfust_status r = cfust_set_params(c, &P);
+                if (r == CFUST_OK) r = cfust_loglik(c, &L);  // line 12
+                if (r == CFUST_ECUDA || r == CFUST_ENOMEM) { s = r; break; }
+                if (r != CFUST_OK || !std::isfinite(L)) L = -INFINITY;
+            }
+            if (loglik_out) loglik_out[(size_t)st * nalpha + a] = L;
+            if (L > lbest) {  // lines 13-14, with l <- l*
+                lbest = L;
+                ibest = st * nalpha + a;
+                bp = cp; bm = cm; bS = cS; bD = cD; bn = cn;
+            }
+        }
+    }
+    cleanup();
+    if (s != CFUST_OK) return s;
+    if (best_out) *best_out = ibest;
+    if (ibest < 0) {
+        c->have_params = false;
+        return fail(c, CFUST_ENOTPD, "cfust_init: no candidate start has a positive definite Sigma^(0)");
+    }
+    cfust_params P{bp.data(), bm.data(), bS.data(), bD.data(), bn.data()};
+    return cfust_set_params(c, &P);
+}
+
 extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const double* b,
                                       const double* V, const double* nu, double* out, double* se)
 {

@@ -235,6 +235,14 @@ struct FitState {
 #include <string>
 void cf_set_global_error(const std::string& msg);
 
+// initialisation (init.cu)
+size_t cluster_moments_smem(int pass, int p, int g, int chunk);
+cudaError_t launch_random_partition(long long n, int g, uint64_t seed, int start, int* labels,
+                                    cudaStream_t st);
+cudaError_t launch_cluster_moments(int pass, const Dims& D, const double* y, const int* labels,
+                                   const double* mean, int chunk, int blocks, double* partial,
+                                   cudaStream_t st);
+
 // host launchers (each issues on `st`; *launches counts kernels issued)
 cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st, long long* launches);
 cudaError_t launch_integrals(const RecSet& r, const IntegArgs& a, int fp32, int nsm,
