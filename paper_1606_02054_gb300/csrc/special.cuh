@@ -471,21 +471,24 @@ __device__ double tk_lattice_warp(const double* bt, const double* Lc, const R* _
     }
     const int N = lat.N, M = lat.M;
     const R invN = R(1) / (R)N;
-    int step[K];
-    int idx0[K];
+    // lattice coordinates x_d = frac(i z_d / N + shift_d), advanced by dx_d = frac(32 z_d / N)
+    // per point of this lane: x - (1 - dx) when that is >= 0 (exact), else x + dx (exact but
+    // for one rounding when x enters a higher binade: a few ulp over a lane's points)
+    R x0[K], dx[K], omdx[K];
 #pragma unroll
     for (int d = 1; d < K; ++d) {
-        step[d] = (int)(((long long)CF_WARP * lat.z[d]) % N);
-        idx0[d] = (int)(((long long)lane * lat.z[d]) % N);
+        dx[d] = (R)(((long long)CF_WARP * lat.z[d]) % N) * invN;
+        omdx[d] = R(1) - dx[d];
+        x0[d] = (R)(((long long)lane * lat.z[d]) % N) * invN;
     }
     R mean = R(0), m2 = R(0);  // Welford over the shift means
     for (int m = 0; m < M; ++m) {
-        R sh[K];
+        R xs[K];
 #pragma unroll
-        for (int d = 1; d < K; ++d) sh[d] = shf[m * CF_MAXDIM + d];
-        int idx[K];
-#pragma unroll
-        for (int d = 1; d < K; ++d) idx[d] = idx0[d];
+        for (int d = 1; d < K; ++d) {
+            xs[d] = x0[d] + shf[m * CF_MAXDIM + d];
+            if (xs[d] >= R(1)) xs[d] -= R(1);
+        }
         R acc = R(0), comp = R(0);  // compensated sum
         const R* __restrict__ crow = chi + (size_t)m * N;
         for (int i = lane; i < N; i += CF_WARP) {
@@ -500,9 +503,7 @@ __device__ double tk_lattice_warp(const double* bt, const double* Lc, const R* _
                 const R e = m_ncdf(a * invd[r]);
                 f *= e;
                 if (r < K - 1) {
-                    R x = (R)idx[r + 1] * invN + sh[r + 1];
-                    if (x >= R(1)) x -= R(1);
-                    const R w = R(1) - m_abs(R(2) * x - R(1));
+                    const R w = R(1) - m_abs(R(2) * xs[r + 1] - R(1));
                     R v = w * e;
                     v = v < Lim<R>::vmin() ? Lim<R>::vmin() : v;
                     v = v > Lim<R>::one_minus_ulp() ? Lim<R>::one_minus_ulp() : v;
@@ -517,8 +518,8 @@ __device__ double tk_lattice_warp(const double* bt, const double* Lc, const R* _
             acc = tk;
 #pragma unroll
             for (int d = 1; d < K; ++d) {
-                idx[d] += step[d];
-                if (idx[d] >= N) idx[d] -= N;
+                const R t = xs[d] - omdx[d];
+                xs[d] = t >= R(0) ? t : xs[d] + dx[d];
             }
         }
         const R smean = warp_sum(acc) * invN;
@@ -558,21 +559,22 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
     }
     const int N = lat.N, M = lat.M;
     const R invN = R(1) / (R)N;
-    int step[K + 1], idx0[K + 1];
+    R x0[K + 1], dx[K + 1], omdx[K + 1];  // lattice coordinates as in tk_lattice_warp
 #pragma unroll
     for (int d = 1; d <= K; ++d) {
-        step[d] = (int)(((long long)CF_WARP * lat.z[d]) % N);
-        idx0[d] = (int)(((long long)lane * lat.z[d]) % N);
+        dx[d] = (R)(((long long)CF_WARP * lat.z[d]) % N) * invN;
+        omdx[d] = R(1) - dx[d];
+        x0[d] = (R)(((long long)lane * lat.z[d]) % N) * invN;
     }
     for (int r = lane; r <= K + K2; r += CF_WARP) acc_sm[r] = 0.0;
     __syncwarp();
     for (int m = 0; m < M; ++m) {
-        R sh[K + 1];
+        R xs[K + 1];
 #pragma unroll
-        for (int d = 1; d <= K; ++d) sh[d] = shf[m * CF_MAXDIM + d];
-        int idx[K + 1];
-#pragma unroll
-        for (int d = 1; d <= K; ++d) idx[d] = idx0[d];
+        for (int d = 1; d <= K; ++d) {
+            xs[d] = x0[d] + shf[m * CF_MAXDIM + d];
+            if (xs[d] >= R(1)) xs[d] -= R(1);
+        }
         R af = R(0), a1[K], a2[K2];
 #pragma unroll
         for (int r = 0; r < K; ++r) a1[r] = R(0);
@@ -590,9 +592,7 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
                 for (int l = 0; l < r; ++l) a -= Lf[r][l] * y[l];
                 const R e = m_ncdf(a * invd[r]);
                 f *= e;
-                R x = (R)idx[r + 1] * invN + sh[r + 1];
-                if (x >= R(1)) x -= R(1);
-                const R w = R(1) - m_abs(R(2) * x - R(1));
+                const R w = R(1) - m_abs(R(2) * xs[r + 1] - R(1));
                 R v = w * e;
                 v = v < Lim<R>::vmin() ? Lim<R>::vmin() : v;
                 v = v > Lim<R>::one_minus_ulp() ? Lim<R>::one_minus_ulp() : v;
@@ -613,8 +613,8 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
             }
 #pragma unroll
             for (int d = 1; d <= K; ++d) {
-                idx[d] += step[d];
-                if (idx[d] >= N) idx[d] -= N;
+                const R t = xs[d] - omdx[d];
+                xs[d] = t >= R(0) ? t : xs[d] + dx[d];
             }
         }
         af = warp_sum(af);
