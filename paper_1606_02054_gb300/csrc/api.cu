@@ -15,7 +15,8 @@
 // kernels (defined in the other translation units)
 __global__ void setup_components_kernel(Dims, Layout, const double*, const double*, const double*,
                                         const double*, double*, int*);
-__global__ void chi_table_kernel(int, const double*, Lattice, const double*, double*, float*);
+__global__ void chi_table_kernel(int, const double*, const double*, Lattice, const double*, double, double*,
+                                 float*);
 __global__ void dof_consts_kernel(Dims, Layout, const double*, int, double*, double*, float*);
 __global__ void t1_table_kernel(int, const double*, float2*);
 __global__ void widen_kernel(const float*, long long, Dims, double*);
@@ -612,8 +613,11 @@ static cfust_status launch_setup(cfust_ctx* c)
         prof_begin(c, CFUST_PROF_CHI);
         const long long total = 3LL * c->g * c->lat.N * c->lat.M;
         const int blocks = (int)std::min<long long>((total + 127) / 128, 64LL * c->nsm);
-        chi_table_kernel<<<blocks, 128, 0, c->st>>>(3 * c->g, c->dofs, c->lat, c->shf64, c->chi64,
-                                                     c->chi32);
+        // the FP64 table serves the FP64 integrators; in the FP32 modes only the rare FP64
+        // fix-up reads it, and 1e-9 is far inside what a pair sent there needs
+        const double rtol = c->opts.precision == CFUST_PREC_FP64 ? 1e-15 : 1e-9;
+        chi_table_kernel<<<blocks, 128, 0, c->st>>>(3 * c->g, c->dofs, c->cst64, c->lat, c->shf64, rtol,
+                                                     c->chi64, c->chi32);
         LAUNCHED();
         prof_end(c, CFUST_PROF_CHI, 1);
     }
@@ -1374,7 +1378,9 @@ extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const doub
         if (lattice) {
             const long long total = (long long)count * NM;
             const int blocks = (int)std::min<long long>((total + 127) / 128, 64LL * c->nsm);
-            chi_table_kernel<<<blocks, 128, 0, c->st>>>(count, r.dof, c->lat, c->shf64, t64, t32);
+            chi_table_kernel<<<blocks, 128, 0, c->st>>>(count, r.dof, k64, c->lat, c->shf64,
+                                                         c->opts.precision == CFUST_PREC_FP64 ? 1e-15 : 1e-9,
+                                                         t64, t32);
             c->launches++;
             if ((e = cudaGetLastError())) break;
         }

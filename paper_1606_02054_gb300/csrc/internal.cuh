@@ -136,7 +136,8 @@ struct PlanArgs {
 //   [2] Gamma((v+1)/2) / (Gamma(v/2) sqrt(pi))         (T_2 at dof v)
 //   [3] lgamma((v+1)/2) - lgamma(v/2) - log(v pi)/2    (log t_1 density at dof v)
 //   [4] the same at dof v - 1
-enum { CST_LGB = 0, CST_LGB1 = 1, CST_C2 = 2, CST_LT1 = 3, CST_LT1M = 4, CST_STRIDE = 8 };
+//   [5] lgamma(v/2)                                    (chi-square quantile at dof v)
+enum { CST_LGB = 0, CST_LGB1 = 1, CST_C2 = 2, CST_LT1 = 3, CST_LT1M = 4, CST_LGA = 5, CST_STRIDE = 8 };
 
 struct IntegArgs {
     const double* cst64;   // [tab][CST_STRIDE]

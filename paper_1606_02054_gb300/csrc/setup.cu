@@ -171,9 +171,11 @@ __global__ void setup_components_kernel(Dims D, Layout Ly, const double* mu, con
 
 // s = sqrt(chi2_{dof}^{-1}(w_0)/dof) for every dof in `dofs`, shift m and point i.
 // Lattice coordinate 0: x = frac(i/N + shift(m, 0)), w = 1 - |2x - 1|.
-__global__ void chi_table_kernel(int ndof, const double* __restrict__ dofs, Lattice lat,
-                                 const double* __restrict__ shf, double* __restrict__ t64,
-                                 float* __restrict__ t32)
+// rtol: Newton tolerance of the quantile (1e-15 when the FP64 table is used, 1e-9 when only
+// the FP32 table is); cst: the per-dof constants (lgamma(dof/2) at CST_LGA).
+__global__ void chi_table_kernel(int ndof, const double* __restrict__ dofs, const double* __restrict__ cst,
+                                 Lattice lat, const double* __restrict__ shf, double rtol,
+                                 double* __restrict__ t64, float* __restrict__ t32)
 {
     const long long total = (long long)ndof * lat.M * lat.N;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -186,7 +188,7 @@ __global__ void chi_table_kernel(int ndof, const double* __restrict__ dofs, Latt
         if (x >= 1.0) x -= 1.0;
         const double wc = fabs(2.0 * x - 1.0);
         const double w = 1.0 - wc;
-        const double s = sqrt(cf_chi2_quantile(w, wc, dof) / dof);
+        const double s = sqrt(cf_chi2_quantile(w, wc, dof, cst[k * CST_STRIDE + CST_LGA], rtol) / dof);
         t64[t] = s;
         t32[t] = (float)s;
     }
@@ -212,7 +214,7 @@ __global__ void dof_consts_kernel(Dims D, Layout Ly, const double* __restrict__ 
         const double ltm = lgamma(0.5 * v) - lgamma(0.5 * (v - 1.0)) - 0.5 * log((v - 1.0) * CF_PI);
         const double c[CST_STRIDE] = {t1_lgb(v), t1_lgb(v + 1.0),
                                       exp(lgamma(0.5 * (v + 1.0)) - lgamma(0.5 * v)) / sqrt(CF_PI),
-                                      lt, v > 1.0 ? ltm : 0.0, 0.0, 0.0, 0.0};
+                                      lt, v > 1.0 ? ltm : 0.0, lgamma(0.5 * v), 0.0, 0.0};
         for (int k = 0; k < CST_STRIDE; ++k) {
             c64[t * CST_STRIDE + k] = c[k];
             c32[t * CST_STRIDE + k] = (float)c[k];

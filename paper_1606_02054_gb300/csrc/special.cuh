@@ -381,10 +381,11 @@ __device__ double t2cdf_warp(R h, R k, R rho, R nu, R omr2, R cr, R lgb, R lgb1,
 // Regularised incomplete gamma and the chi-square quantile (FP64), used to
 // tabulate s = sqrt(chi2_nu^{-1}(w_0)/nu) at every lattice point.
 // ---------------------------------------------------------------------------
-__device__ inline void cf_gamma_pq(double a, double x, double* P, double* Q)
+// lga = lgamma(a)
+__device__ inline void cf_gamma_pq(double a, double lga, double x, double* P, double* Q)
 {
     if (x <= 0.0) { *P = 0.0; *Q = 1.0; return; }
-    const double lpre = a * log(x) - x - lgamma(a);
+    const double lpre = a * log(x) - x - lga;
     if (x < a + 1.0) {
         // series: P = x^a e^-x / Gamma(a+1) * sum_n x^n / ((a+1)...(a+n))
         double term = 1.0, sum = 1.0, ap = a;
@@ -417,7 +418,8 @@ __device__ inline void cf_gamma_pq(double a, double x, double* P, double* Q)
 
 // x with P(nu/2, x/2) = w (w <= 1/2) or Q(nu/2, x/2) = wc (w > 1/2):
 // safeguarded Newton on the log of the smaller tail probability.
-__device__ inline double cf_chi2_quantile(double w, double wc, double nu)
+// lga = lgamma(nu/2); Newton stops at relative change rtol (1e-15 for FP64 tables).
+__device__ inline double cf_chi2_quantile(double w, double wc, double nu, double lga, double rtol)
 {
     if (!(w > 0.0)) return 0.0;
     if (!(wc > 0.0)) return INFINITY;
@@ -429,20 +431,20 @@ __device__ inline double cf_chi2_quantile(double w, double wc, double nu)
     const double c9 = 2.0 / (9.0 * nu);
     const double base = 1.0 - c9 + z * sqrt(c9);
     double x = nu * base * base * base;
-    const double xs = 2.0 * exp((log(w) + lgamma(a + 1.0)) / a);
+    const double xs = 2.0 * exp((log(w) + lga + log(a)) / a);
     if (!(x > 0.0) || (!upper && xs < x)) x = xs;
     double lo = 0.0, hi = INFINITY;
     for (int it = 0; it < 200; ++it) {
         double P, Q;
-        cf_gamma_pq(a, 0.5 * x, &P, &Q);
+        cf_gamma_pq(a, lga, 0.5 * x, &P, &Q);
         const double tv = upper ? Q : P;
         const double G = upper ? (target - log(tv)) : (log(tv) - target);  // increasing in x
         if (G == 0.0) break;
         if (G > 0.0) hi = x; else lo = x;
-        const double ldens = (a - 1.0) * log(0.5 * x) - 0.5 * x - lgamma(a) - 0.6931471805599453;
+        const double ldens = (a - 1.0) * log(0.5 * x) - 0.5 * x - lga - 0.6931471805599453;
         double xn = x - G * exp(log(tv) - ldens);
         if (!(xn > lo && xn < hi)) xn = isinf(hi) ? 2.0 * x : 0.5 * (lo + hi);
-        const bool done = fabs(xn - x) <= 1e-15 * x || (isfinite(hi) && hi - lo <= 1e-15 * hi);
+        const bool done = fabs(xn - x) <= rtol * x || (isfinite(hi) && hi - lo <= rtol * hi);
         x = xn;
         if (done) break;
     }
