@@ -55,7 +55,7 @@ extern "C" cfust_status cfust_reduce_stats_noalloc(int p, int q, int g, int64_t 
     // chunk <= 256 observations, at most 48 KB of shared memory per block
     const int row = 4 + p + q + q * q;
     int chunk = 256;
-    while (chunk > 32 && (size_t)chunk * (row + g + 1) * sizeof(double) > 48 * 1024) chunk -= 32;
+    while (chunk > 32 && ((size_t)chunk * (row + g + 1) + CF_MAXG) * sizeof(double) > 48 * 1024) chunk -= 32;
     const int nblocks = (int)((n + chunk - 1) / chunk);
     const int width = g * stats_per_comp(p, q) + 1;
     if ((long long)nblocks * width > CF_NOALLOC_PARTIAL_DOUBLES)
@@ -97,7 +97,7 @@ extern "C" cfust_status cfust_reduce_stats_noalloc(int p, int q, int g, int64_t 
     r.chunk = chunk;
     r.row = row;
     r.y32 = nullptr;
-    const size_t smem = sizeof(double) * ((size_t)chunk * row + (size_t)g * chunk + chunk);
+    const size_t smem = sizeof(double) * ((size_t)chunk * row + (size_t)g * chunk + chunk + CF_MAXG);
     estep_reduce_kernel<<<nblocks, 256, smem, st>>>(r);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return nerr(CFUST_ECUDA, std::string("cfust_reduce_stats_noalloc: ") + cudaGetErrorString(e));

@@ -16,23 +16,46 @@
 
 // Staged row of one observation for component h:
 //   [0] tau, [1] tau*u, [2] elogu - u, [3] 1, [4..4+p) r, then eu (q), euu (q*q).
-// Each statistic is the sum over the chunk of row[ia]*row[ib]*row[ic].
-__device__ inline void stat_operands(int e, int p, int q, int& ia, int& ib, int& ic)
+// Each statistic is the sum over the chunk of row[ia]*row[ib]*row[ic].  The
+// symmetric See and Srr are computed for their lower triangles only
+// (stats_reduced(p, q) statistics) and written to both positions o1, o2 of the
+// full layout (o2 = -1 when there is one).
+__device__ inline int stats_reduced(int p, int q)
+{
+    return 3 + p + q + p * q + q * (q + 1) / 2 + p * (p + 1) / 2;
+}
+
+__device__ inline void stat_operands(int e, int p, int q, int& ia, int& ib, int& ic, int& o1, int& o2)
 {
     const int R0 = 4, E0 = 4 + p, EE0 = 4 + p + q;
-    if (e == 0) { ia = 0; ib = 3; ic = 3; return; }                  // N
-    if (e == 1) { ia = 1; ib = 3; ic = 3; return; }                  // U
-    if (e == 2) { ia = 0; ib = 2; ic = 3; return; }                  // Snu
+    const int fSee = 3 + p + q + p * q, fSrr = fSee + q * q;
+    o2 = -1;
+    if (e == 0) { ia = 0; ib = 3; ic = 3; o1 = 0; return; }                   // N
+    if (e == 1) { ia = 1; ib = 3; ic = 3; o1 = 1; return; }                   // U
+    if (e == 2) { ia = 0; ib = 2; ic = 3; o1 = 2; return; }                   // Snu
+    o1 = e;
     e -= 3;
-    if (e < p) { ia = 1; ib = R0 + e; ic = 3; return; }              // Sr
+    if (e < p) { ia = 1; ib = R0 + e; ic = 3; return; }                       // Sr
     e -= p;
-    if (e < q) { ia = 0; ib = E0 + e; ic = 3; return; }              // Se
+    if (e < q) { ia = 0; ib = E0 + e; ic = 3; return; }                       // Se
     e -= q;
-    if (e < p * q) { ia = 0; ib = R0 + e / q; ic = E0 + e % q; return; }  // Sre
+    if (e < p * q) { ia = 0; ib = R0 + e / q; ic = E0 + e % q; return; }      // Sre
     e -= p * q;
-    if (e < q * q) { ia = 0; ib = EE0 + e; ic = 3; return; }         // See
-    e -= q * q;
-    ia = 1; ib = R0 + e / p; ic = R0 + e % p;                        // Srr
+    int a = 0;
+    if (e < q * (q + 1) / 2) {                                                // See (lower)
+        while ((a + 1) * (a + 2) / 2 <= e) ++a;
+        const int b = e - a * (a + 1) / 2;
+        ia = 0; ib = EE0 + a * q + b; ic = 3;
+        o1 = fSee + a * q + b;
+        if (a != b) o2 = fSee + b * q + a;
+        return;
+    }
+    e -= q * (q + 1) / 2;
+    while ((a + 1) * (a + 2) / 2 <= e) ++a;                                   // Srr (lower)
+    const int b = e - a * (a + 1) / 2;
+    ia = 1; ib = R0 + a; ic = R0 + b;
+    o1 = fSrr + a * p + b;
+    if (a != b) o2 = fSrr + b * p + a;
 }
 
 // T = double: FP64 rows and sums.  T = float (mixed precision): FP32 rows
@@ -49,25 +72,41 @@ __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
     // chunk is a multiple of 32, so the FP32 rows end on an 8-byte boundary
     double* taus = (double*)(rows + (size_t)a.chunk * a.row);
     double* lj = taus + (size_t)g * a.chunk;
+    double* lpi = lj + a.chunk;  // log pi_h (CF_MAXG slots)
     double* out = a.partial + (size_t)blockIdx.x * (g * S + 1);
     const int t = threadIdx.x;
 
-    // S8: tau and l_j for this chunk
+    // S8: tau and l_j for this chunk (FP64 log-sum-exp: one exp per component)
+    if (t < g) lpi[t] = log(a.pi[t]);
+    __syncthreads();
     if (t < cnt) {
         const long long j = j0 + t;
+        double v[CF_MAXG];
         double mx = -INFINITY;
-        for (int h = 0; h < g; ++h) {
-            const double v = log(a.pi[h]) + a.logf[(size_t)h * n + j];
-            mx = v > mx ? v : mx;
+#pragma unroll
+        for (int h = 0; h < CF_MAXG; ++h) {
+            if (h < g) {
+                v[h] = lpi[h] + a.logf[(size_t)h * n + j];
+                mx = v[h] > mx ? v[h] : mx;
+            }
         }
         double s = 0.0;
-        for (int h = 0; h < g; ++h) s += exp(log(a.pi[h]) + a.logf[(size_t)h * n + j] - mx);
-        const double ls = log(s);
-        lj[t] = mx + ls;
-        for (int h = 0; h < g; ++h) {
-            const double tv = exp(log(a.pi[h]) + a.logf[(size_t)h * n + j] - mx - ls);
-            taus[h * a.chunk + t] = tv;
-            if (a.tau) a.tau[(size_t)h * n + j] = tv;
+#pragma unroll
+        for (int h = 0; h < CF_MAXG; ++h) {
+            if (h < g) {
+                v[h] = exp(v[h] - mx);
+                s += v[h];
+            }
+        }
+        lj[t] = mx + log(s);
+        const double rs = 1.0 / s;
+#pragma unroll
+        for (int h = 0; h < CF_MAXG; ++h) {
+            if (h < g) {
+                const double tv = v[h] * rs;
+                taus[h * a.chunk + t] = tv;
+                if (a.tau) a.tau[(size_t)h * n + j] = tv;
+            }
         }
     } else if (t < a.chunk) {
         lj[t] = 0.0;
@@ -107,9 +146,10 @@ __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
             }
         }
         __syncthreads();
-        for (int e = t; e < S; e += blockDim.x) {
-            int ia, ib, ic;
-            stat_operands(e, p, q, ia, ib, ic);
+        const int Sred = stats_reduced(p, q);
+        for (int e = t; e < Sred; e += blockDim.x) {
+            int ia, ib, ic, o1, o2;
+            stat_operands(e, p, q, ia, ib, ic, o1, o2);
             T acc = T(0), comp = T(0);
             if (sizeof(T) == sizeof(float)) {
                 for (int jj = 0; jj < cnt; ++jj) {
@@ -125,7 +165,8 @@ __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
                     acc += rw[ia] * rw[ib] * rw[ic];
                 }
             }
-            out[h * S + e] = (double)acc;
+            out[h * S + o1] = (double)acc;
+            if (o2 >= 0) out[h * S + o2] = (double)acc;
         }
         __syncthreads();
     }
