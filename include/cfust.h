@@ -88,7 +88,15 @@ typedef struct {
                                alpha (eq 13) that also samples the last coordinate
                                (one integral per pair instead of 1 + q + q(q-1)).
                             q <= 2 always uses the recursion. */
+    int hold;            /* parameters the M-step keeps at their current values, a bitwise
+                            OR of CFUST_HOLD_DELTA (eq 20 skipped; eq 21 then uses Delta^(k):
+                            from Delta^(0) = 0 the fit is the EM of a mixture of multivariate
+                            t, the Delta = 0 special case of Sec. 2) and CFUST_HOLD_NU (eq 22
+                            skipped); 0 (default): none */
 } cfust_opts;
+
+#define CFUST_HOLD_DELTA 1
+#define CFUST_HOLD_NU 2
 
 /* Kernel classes reported by cfust_profile. */
 enum {

@@ -84,10 +84,16 @@ def lib():
             L.ora_mstep.argtypes = [i, i, i, i, _dp, _dp, _dp, _dp, _dp, _dp, d, d, _dp, _dp,
                                     _dp, _dp, _dp, _ip]
             L.ora_mstep.restype = i
+            L.ora_mstep_hold.argtypes = [i, i, i, i, _dp, _dp, _dp, _dp, _dp, _dp, d, d, _dp, _dp,
+                                         _dp, _dp, _dp, _ip, i]
+            L.ora_mstep_hold.restype = i
             L.ora_nu_root.argtypes = [d, d, d, d, _ip]; L.ora_nu_root.restype = d
             L.ora_fit.argtypes = [i, i, i, i, _dp, _dp, _dp, _dp, _dp, _dp, C.POINTER(Qmc), i, d,
                                   d, d, i, _ip, _dp]
             L.ora_fit.restype = i
+            L.ora_fit_hold.argtypes = [i, i, i, i, _dp, _dp, _dp, _dp, _dp, _dp, C.POINTER(Qmc), i,
+                                       d, d, d, i, _ip, _dp, i]
+            L.ora_fit_hold.restype = i
             L.ora_random_partition.argtypes = [i, i, C.c_uint64, i, _ip]
             L.ora_random_partition.restype = None
             L.ora_moment_start.argtypes = [i, i, i, i, _dp, _ip, d, d, _dp, _dp, _dp, _dp, _dp]
@@ -218,17 +224,21 @@ def loglik(y, params, spec: Qmc | None = None, nthreads=None):
     return L.value
 
 
-def mstep(y, e, params, nu_min=1.0, nu_max=200.0):
-    """M-step from E-step arrays; returns (new params dict, nu_flag)."""
+HOLD_DELTA, HOLD_NU = 1, 2
+
+
+def mstep(y, e, params, nu_min=1.0, nu_max=200.0, hold=0):
+    """M-step from E-step arrays; returns (new params dict, nu_flag).  hold: HOLD_DELTA
+    and/or HOLD_NU keep those parameters at their current values."""
     y = _f64(y)
     n, p = y.shape
     pi, mu, Sigma, Delta, nu = (a.copy() for a in _params(params))
     g, q = pi.size, Delta.shape[-1]
     flag = np.zeros(g, dtype=np.int32)
-    rc = lib().ora_mstep(n, p, q, g, _ptr(y), _ptr(_f64(e["tau"])), _ptr(_f64(e["u"])),
-                         _ptr(_f64(e["elogu"])), _ptr(_f64(e["eu"])), _ptr(_f64(e["euu"])),
-                         float(nu_min), float(nu_max), _ptr(pi), _ptr(mu), _ptr(Sigma),
-                         _ptr(Delta), _ptr(nu), flag.ctypes.data_as(_ip))
+    rc = lib().ora_mstep_hold(n, p, q, g, _ptr(y), _ptr(_f64(e["tau"])), _ptr(_f64(e["u"])),
+                              _ptr(_f64(e["elogu"])), _ptr(_f64(e["eu"])), _ptr(_f64(e["euu"])),
+                              float(nu_min), float(nu_max), _ptr(pi), _ptr(mu), _ptr(Sigma),
+                              _ptr(Delta), _ptr(nu), flag.ctypes.data_as(_ip), int(hold))
     if rc:
         raise RuntimeError(f"ora_mstep failed ({rc})")
     return dict(pi=pi, mu=mu, Sigma=Sigma, Delta=Delta, nu=nu), flag
@@ -248,7 +258,7 @@ def aitken_converged(l_km1, l_k, l_kp1, eps):
 
 
 def fit(y, params, iters, spec: Qmc | None = None, tol=0.0, nu_min=1.0, nu_max=200.0,
-        nthreads=None):
+        nthreads=None, hold=0):
     """EM fit; returns (params, loglik history [iters_done+1], iters_done)."""
     y = _f64(y)
     n, p = y.shape
@@ -257,10 +267,10 @@ def fit(y, params, iters, spec: Qmc | None = None, tol=0.0, nu_min=1.0, nu_max=2
     spec = spec or qmc()
     hist = np.full(iters + 1, np.nan)
     done = C.c_int(0)
-    rc = lib().ora_fit(n, p, q, g, _ptr(y), _ptr(pi), _ptr(mu), _ptr(Sigma), _ptr(Delta),
-                       _ptr(nu), C.byref(spec), int(iters), float(tol), float(nu_min),
-                       float(nu_max), int(nthreads or DEFAULT_NTHREADS), C.byref(done),
-                       _ptr(hist))
+    rc = lib().ora_fit_hold(n, p, q, g, _ptr(y), _ptr(pi), _ptr(mu), _ptr(Sigma), _ptr(Delta),
+                            _ptr(nu), C.byref(spec), int(iters), float(tol), float(nu_min),
+                            float(nu_max), int(nthreads or DEFAULT_NTHREADS), C.byref(done),
+                            _ptr(hist), int(hold))
     if rc:
         raise RuntimeError(f"ora_fit failed ({rc})")
     k = done.value

@@ -917,6 +917,15 @@ int ora_mstep(int n, int p, int q, int g, const double* y, const double* tau,
               double nu_min, double nu_max, double* pi, double* mu, double* Sigma,
               double* Delta, double* nu, int* nu_flag)
 {
+    return ora_mstep_hold(n, p, q, g, y, tau, u, elogu, eu, euu, nu_min, nu_max, pi, mu, Sigma,
+                          Delta, nu, nu_flag, 0);
+}
+
+int ora_mstep_hold(int n, int p, int q, int g, const double* y, const double* tau,
+                   const double* u, const double* elogu, const double* eu, const double* euu,
+                   double nu_min, double nu_max, double* pi, double* mu, double* Sigma,
+                   double* Delta, double* nu, int* nu_flag, int hold)
+{
     if (p < 1 || p > ORA_MAXP || q < 1 || q > ORA_MAXQ) return -1;
     for (int h = 0; h < g; ++h) {
         const double* th = tau + (size_t)h * n;
@@ -955,14 +964,19 @@ int ora_mstep(int n, int p, int q, int g, const double* y, const double* tau,
                     A[i * q + k] += th[j] * (y[(size_t)j * p + i] - mun[i]) * e2[(size_t)j * q + k];
             for (int a = 0; a < q * q; ++a) B[a] += th[j] * e3[(size_t)j * q * q + a];
         }
-        if (chol(q, B, LB)) return 1 + h;
         double Dn[ORA_MAXP * ORA_MAXQ];
+        if (hold & ORA_HOLD_DELTA) {
+            /* Delta held at Delta^(k): eq (21) below uses it in place of Delta^(k+1) */
+            memcpy(Dn, Dh, sizeof(double) * p * q);
+        } else {
+        if (chol(q, B, LB)) return 1 + h;
         for (int i = 0; i < p; ++i) {
             /* row i of A B^{-1}: solve B x = A_i^T (B symmetric) */
             double rhs[ORA_MAXQ], sol[ORA_MAXQ];
             for (int k = 0; k < q; ++k) rhs[k] = A[i * q + k];
             chol_solve(q, LB, rhs, sol);
             for (int k = 0; k < q; ++k) Dn[i * q + k] = sol[k];
+        }
         }
         /* eq (21), with mu^(k+1) and Delta^(k+1) */
         double Sn[ORA_MAXP * ORA_MAXP];
@@ -1001,7 +1015,7 @@ int ora_mstep(int n, int p, int q, int g, const double* y, const double* tau,
         double snu = 0.0;
         for (int j = 0; j < n; ++j) snu += th[j] * (lh[j] - uh[j]);
         int fl = 0;
-        double nun = ora_nu_root(N, snu, nu_min, nu_max, &fl);
+        double nun = (hold & ORA_HOLD_NU) ? nu[h] : ora_nu_root(N, snu, nu_min, nu_max, &fl);
         if (nu_flag) nu_flag[h] = fl;
         memcpy(muh, mun, sizeof(double) * p);
         memcpy(Dh, Dn, sizeof(double) * p * q);
@@ -1029,6 +1043,15 @@ int ora_fit(int n, int p, int q, int g, const double* y, double* pi, double* mu,
             double tol, double nu_min, double nu_max, int nthreads, int* iters_done,
             double* loglik_hist)
 {
+    return ora_fit_hold(n, p, q, g, y, pi, mu, Sigma, Delta, nu, qmc, max_iter, tol, nu_min, nu_max,
+                        nthreads, iters_done, loglik_hist, 0);
+}
+
+int ora_fit_hold(int n, int p, int q, int g, const double* y, double* pi, double* mu,
+            double* Sigma, double* Delta, double* nu, const ora_qmc* qmc, int max_iter,
+            double tol, double nu_min, double nu_max, int nthreads, int* iters_done,
+            double* loglik_hist, int hold)
+{
     size_t ng = (size_t)n * g;
     double* tau = (double*)malloc(sizeof(double) * ng);
     double* u = (double*)malloc(sizeof(double) * ng);
@@ -1045,8 +1068,8 @@ int ora_fit(int n, int p, int q, int g, const double* y, double* pi, double* mu,
         if (tol > 0.0 && it >= 2 && loglik_hist &&
             ora_aitken_converged(loglik_hist[it - 2], loglik_hist[it - 1], L, tol, NULL))
             break;
-        rc = ora_mstep(n, p, q, g, y, tau, u, el, eu, euu, nu_min, nu_max, pi, mu, Sigma,
-                       Delta, nu, NULL);
+        rc = ora_mstep_hold(n, p, q, g, y, tau, u, el, eu, euu, nu_min, nu_max, pi, mu, Sigma,
+                            Delta, nu, NULL, hold);
         if (rc) break;
     }
     if (!rc && it == max_iter) {

@@ -105,6 +105,16 @@ int ora_mstep(int n, int p, int q, int g, const double* y,
               double nu_max, double* pi, double* mu, double* Sigma,
               double* Delta, double* nu, int* nu_flag);
 
+/* The same M-step with parameters held at their current values: hold is a
+ * bitwise OR of ORA_HOLD_DELTA (eq 20 skipped, eq 21 uses Delta^(k); from
+ * Delta^(0) = 0 this is the EM of a t mixture) and ORA_HOLD_NU (eq 22 skipped). */
+#define ORA_HOLD_DELTA 1
+#define ORA_HOLD_NU 2
+int ora_mstep_hold(int n, int p, int q, int g, const double* y, const double* tau,
+                   const double* u, const double* elogu, const double* eu, const double* euu,
+                   double nu_min, double nu_max, double* pi, double* mu, double* Sigma,
+                   double* Delta, double* nu, int* nu_flag, int hold);
+
 /* Root of eq (22) (sign read as + and sum over j) for one component:
  * n_h [log(nu/2) - psi(nu/2) + 1] + s_h = 0 on [nu_min, nu_max]. */
 double ora_nu_root(double n_h, double s_h, double nu_min, double nu_max,
@@ -138,6 +148,13 @@ int ora_init(int n, int p, int q, int g, const double* y, int nstarts, const int
              uint64_t seed, int nalpha, const double* alphas, double nu0, const ora_qmc* qmc,
              int nthreads, double* loglik_out, int* best, double* pi, double* mu,
              double* Sigma, double* Delta, double* nu);
+
+/* ora_fit with the M-step's held parameters (see ora_mstep_hold). */
+int ora_fit_hold(int n, int p, int q, int g, const double* y, double* pi,
+                 double* mu, double* Sigma, double* Delta, double* nu,
+                 const ora_qmc* qmc, int max_iter, double tol, double nu_min,
+                 double nu_max, int nthreads, int* iters_done,
+                 double* loglik_hist, int hold);
 
 /* Aitken rule (eqs 24-26) on three consecutive log-likelihoods. */
 int ora_aitken_converged(double l_km1, double l_k, double l_kp1, double eps,

@@ -29,7 +29,7 @@ __global__ void reduce_partials_kernel(const double*, int, int, double*, int*);
 __global__ void loglik_partial_kernel(Dims, const double*, const double*, double*);
 __global__ void mstep_kernel(Dims, const double*, double, double, const double*, const double*,
                              const double*, double*, double*, double*, double*, double*, int*, int*,
-                             const int*);
+                             const int*, int);
 
 struct cfust_ctx {
     int p = 0, q = 0, g = 0;
@@ -348,6 +348,8 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
         return fail(nullptr, CFUST_EINVAL, "cfust_create: t2_nodes must be 0 or in [8, 64]");
     if (o.moments != 0 && o.moments != 1)
         return fail(nullptr, CFUST_EINVAL, "cfust_create: moments must be 0 or 1");
+    if (o.hold & ~(CFUST_HOLD_DELTA | CFUST_HOLD_NU))
+        return fail(nullptr, CFUST_EINVAL, "cfust_create: hold must combine CFUST_HOLD_DELTA and CFUST_HOLD_NU");
     cudaError_t e = cudaSetDevice(o.device);
     if (e != cudaSuccess)
         return fail(nullptr, CFUST_ECUDA, std::string("cfust_create: cudaSetDevice: ") + cudaGetErrorString(e));
@@ -790,7 +792,7 @@ static cfust_status enqueue_mstep(cfust_ctx* c, const int* gate)
     prof_begin(c, CFUST_PROF_MSTEP);
     mstep_kernel<<<1, 32, 0, c->st>>>(c->D, c->stats, c->opts.nu_min, c->opts.nu_max, c->mu, c->Delta,
                                       c->nu, c->pi_n, c->mu_n, c->Sigma_n, c->Delta_n, c->nu_n,
-                                      c->flags, c->comp_status, gate);
+                                      c->flags, c->comp_status, gate, c->opts.hold);
     LAUNCHED();
     prof_end(c, CFUST_PROF_MSTEP, 1);
     return CFUST_OK;

@@ -12,6 +12,7 @@
 // Results go to separate output arrays; the host commits them only when no
 // component failed (empty component, non-PD See or Sigma), so a failed
 // M-step leaves Psi^(k) untouched.
+#include "cfust.h"
 #include "internal.cuh"
 #include "special.cuh"
 
@@ -42,7 +43,7 @@ __global__ void mstep_kernel(Dims D, const double* __restrict__ stats, double nu
                              const double* __restrict__ mu, const double* __restrict__ Delta,
                              const double* __restrict__ nu, double* pi_o, double* mu_o,
                              double* Sigma_o, double* Delta_o, double* nu_o, int* flags,
-                             int* comp_status, const int* gate)
+                             int* comp_status, const int* gate, int hold)
 {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= D.g) return;
@@ -75,13 +76,17 @@ __global__ void mstep_kernel(Dims D, const double* __restrict__ stats, double nu
     double Bs[CF_MAXQ * CF_MAXQ], LB[CF_MAXQ * CF_MAXQ];
     for (int a = 0; a < q; ++a)
         for (int b = 0; b < q; ++b) Bs[a * q + b] = 0.5 * (See[a * q + b] + See[b * q + a]);
-    if (!chol_small(q, Bs, LB)) {
+    const bool hold_delta = hold & CFUST_HOLD_DELTA;
+    if (hold_delta) {
+        // Delta held at Delta^(k): eq (21) below uses it in place of Delta^(k+1)
+        for (int i = 0; i < p * q; ++i) Dn[i] = Dh[i];
+    } else if (!chol_small(q, Bs, LB)) {
         atomicOr(flags, KF_NOTPD_SEE);
         comp_status[h] = KF_NOTPD_SEE;
         return;
     }
     // Delta = A See^{-1}: each row solves See x = A_i^T
-    for (int i = 0; i < p; ++i) {
+    for (int i = 0; i < p && !hold_delta; ++i) {
         double zz[CF_MAXQ];
         for (int k = 0; k < q; ++k) {
             double s = A[i * q + k];
@@ -117,7 +122,8 @@ __global__ void mstep_kernel(Dims D, const double* __restrict__ stats, double nu
     // nu (eq 22): F decreasing in nu
     double vnew;
     const double flo = nu_eq(nu_min, N, Snu), fhi = nu_eq(nu_max, N, Snu);
-    if (!(flo > 0.0)) { vnew = nu_min; atomicOr(flags, KF_NUROOT); comp_status[h] = KF_NUROOT; }
+    if (hold & CFUST_HOLD_NU) vnew = nu[h];
+    else if (!(flo > 0.0)) { vnew = nu_min; atomicOr(flags, KF_NUROOT); comp_status[h] = KF_NUROOT; }
     else if (!(fhi < 0.0)) { vnew = nu_max; atomicOr(flags, KF_NUROOT); comp_status[h] = KF_NUROOT; }
     else {
         double lo = nu_min, hi = nu_max;

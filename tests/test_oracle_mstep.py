@@ -130,3 +130,61 @@ def test_fit_recovers_generating_parameters(oracle):
                               - t["mu"][s] - t["Delta"][s].sum(1) * 0.8) < 0.6
         assert np.linalg.norm(Om_e - Om_t) / np.linalg.norm(Om_t) < 0.5
     assert hist[-1] > hist[0]
+
+
+def _t_mixture_em(y, pi, mu, Sigma, nu, iters):
+    """Textbook ECM for a mixture of multivariate t (McLachlan & Peel), written
+    independently: E-step tau, u = (nu+p)/(nu+d); CM-steps pi, mu = sum tau u y /
+    sum tau u, Sigma = sum tau u r r^T / sum tau, then nu from
+    log(nu/2) - psi(nu/2) + 1 + (1/N) sum tau (log u - u) + psi((nu_k+p)/2) - log((nu_k+p)/2) = 0."""
+    import scipy.optimize as so
+    import scipy.special as sps
+    from scipy.stats import multivariate_t
+
+    n, p = y.shape
+    g = len(pi)
+    pi, mu, Sigma, nu = pi.copy(), mu.copy(), Sigma.copy(), nu.copy()
+    for _ in range(iters):
+        logf = np.array([multivariate_t(mu[h], Sigma[h], df=nu[h]).logpdf(y) for h in range(g)])
+        a = np.log(pi)[:, None] + logf
+        tau = np.exp(a - np.logaddexp.reduce(a, axis=0))
+        for h in range(g):
+            r = y - mu[h]
+            d = np.einsum("ij,jk,ik->i", r, np.linalg.inv(Sigma[h]), r)
+            u = (nu[h] + p) / (nu[h] + d)
+            N = tau[h].sum()
+            pi[h] = N / n
+            mu[h] = (tau[h] * u) @ y / (tau[h] * u).sum()
+            r = y - mu[h]
+            Sigma[h] = (r * (tau[h] * u)[:, None]).T @ r / N
+            c = (tau[h] * (np.log(u) - u)).sum() / N + sps.digamma((nu[h] + p) / 2) - np.log((nu[h] + p) / 2)
+            f = lambda v: np.log(v / 2) - sps.digamma(v / 2) + 1 + c
+            nu[h] = so.brentq(f, 1.0, 200.0, xtol=1e-14, rtol=1e-15) if f(1.0) > 0 > f(200.0) else nu[h]
+    return pi, mu, Sigma, nu
+
+
+def test_held_delta_zero_is_the_t_mixture_em(oracle):
+    """Delta^(0) = 0 held by the M-step: the CFUST EM reduces to the t-mixture EM
+    (the T_q factor of eq 4 is 2^-q, u is (nu+p)/(nu+d) and eq 15 is exact)."""
+    w = synth.make_workload("flow_p4", n=400, with_init=False)
+    y = w["y"][:, :3]
+    g, q = 2, 2
+    rng = np.random.default_rng(8)
+    lab = rng.integers(0, g, len(y))
+    P = dict(pi=np.array([0.5, 0.5]), mu=np.array([y[lab == h].mean(0) for h in range(g)]),
+             Sigma=np.array([np.cov(y[lab == h], rowvar=False) for h in range(g)]),
+             Delta=np.zeros((g, 3, q)), nu=np.array([8.0, 12.0]))
+    got, hist, it = oracle.fit(y, P, 12, oracle.qmc(**w["qmc"]), hold=oracle.HOLD_DELTA)
+    pi, mu, Sigma, nu = _t_mixture_em(y, P["pi"], P["mu"], P["Sigma"], P["nu"], 12)
+    assert np.all(got["Delta"] == 0.0)
+    np.testing.assert_allclose(got["pi"], pi, rtol=1e-9)
+    np.testing.assert_allclose(got["mu"], mu, rtol=1e-9, atol=1e-11)
+    np.testing.assert_allclose(got["Sigma"], Sigma, rtol=1e-9, atol=1e-11)
+    np.testing.assert_allclose(got["nu"], nu, rtol=1e-8)
+
+
+def test_held_nu_stays(oracle):
+    w = synth.make_workload("two_comp_p2", n=300)
+    got, hist, it = oracle.fit(w["y"], w["init"], 5, oracle.qmc(**w["qmc"]), hold=oracle.HOLD_NU)
+    np.testing.assert_array_equal(got["nu"], np.asarray(w["init"]["nu"], dtype=float))
+    assert np.all(np.diff(hist) > -1e-6 * np.abs(hist[:-1]))  # still an ECM (q = 2: exact moments)
