@@ -45,11 +45,10 @@ __device__ inline void pair_whiten(const double* F, const Layout& Ly, int p, int
     *logtp = F[Ly.scal + SC_LOGTP] - 0.5 * (nu + p) * log1p(d / nu);
 }
 
-// Mixed precision: the same whitening in FP32 from FP32 copies of y and of
-// the factor block; d and c are returned in FP64 for the rest of the pair.
-__device__ inline void pair_whiten_f32(const float* F32, const double* F, const Layout& Ly, int p,
-                                       int q, const float* yj, double* d_out, double* c,
-                                       double* logtp)
+// Mixed precision: the same whitening and log t_p in FP32 from FP32 copies of y
+// and of the factor block.
+__device__ inline void pair_whiten_f32(const float* F32, const Layout& Ly, int p, int q, const float* yj,
+                                       float* d_out, float* c, float* logtp)
 {
     float rr[CF_MAXP], z[CF_MAXP];
     for (int i = 0; i < p; ++i) rr[i] = yj[i] - F32[Ly.mu + i];
@@ -63,36 +62,38 @@ __device__ inline void pair_whiten_f32(const float* F32, const double* F, const 
     for (int k = 0; k < q; ++k) {
         float s = 0.0f;
         for (int i = 0; i < p; ++i) s = fmaf(F32[Ly.A + i * q + k], z[i], s);
-        c[k] = (double)s;
+        c[k] = s;
     }
-    const double nu = F[Ly.scal + SC_NU];
-    *d_out = (double)d;
-    *logtp = F[Ly.scal + SC_LOGTP] - 0.5 * (nu + p) * log1p((double)d / nu);
+    const float nu = F32[Ly.scal + SC_NU];
+    *d_out = d;
+    *logtp = F32[Ly.scal + SC_LOGTP] - 0.5f * (nu + p) * log1pf(d / nu);
 }
 
+// Limits of the records, in T = double (F the factor block) or, in the mixed
+// form, T = float (F its FP32 copy).
 // which = 0: alpha_s (dof nu+p); which = 1: alpha (dof nu+p+2)
-__device__ inline void limits_l0(const double* F, const Layout& Ly, int p, int q, const double* c,
-                                 double d, int which, double* bt)
+template <typename T>
+__device__ inline void limits_l0(const T* F, const Layout& Ly, int p, int q, const T* c, T d, int which, T* bt)
 {
-    const double nu = F[Ly.scal + SC_NU], nu1 = nu + p;
-    const double f = sqrt((nu1 + 2.0 * which) / (nu + d));
+    const T nu = F[Ly.scal + SC_NU], nu1 = nu + p;
+    const T f = m_sqrt((nu1 + T(2) * which) / (nu + d));
     for (int k = 0; k < q; ++k) bt[k] = c[k] * f * F[Ly.dq + k];
 }
 
 // Level-1 limits for coordinate r; returns the scale factor sc1 (V_r = sc1 schur_r).
-__device__ inline double limits_l1(const double* F, const Layout& Ly, int p, int q, const double* c,
-                                   double d, int r, double* bt)
+template <typename T>
+__device__ inline T limits_l1(const T* F, const Layout& Ly, int p, int q, const T* c, T d, int r, T* bt)
 {
     const int q1 = q - 1;
-    const double nu = F[Ly.scal + SC_NU], nu1 = nu + p;
-    const double k0 = (nu + d) / nu1;
-    const double Srr = k0 * F[Ly.Lam + r * q + r];
-    const double* blk = F + Ly.l1 + r * Ly.l1s;
-    const double* mvec = blk;
-    const double* dsc = blk + q1 + q1 * q1;
-    const double kap1 = (nu1 + c[r] * c[r] / Srr) / (nu1 + 1.0);
-    const double sc1 = kap1 * k0;
-    const double isc = 1.0 / sqrt(sc1);
+    const T nu = F[Ly.scal + SC_NU], nu1 = nu + p;
+    const T k0 = (nu + d) / nu1;
+    const T Srr = k0 * F[Ly.Lam + r * q + r];
+    const T* blk = F + Ly.l1 + r * Ly.l1s;
+    const T* mvec = blk;
+    const T* dsc = blk + q1 + q1 * q1;
+    const T kap1 = (nu1 + c[r] * c[r] / Srr) / (nu1 + T(1));
+    const T sc1 = kap1 * k0;
+    const T isc = T(1) / m_sqrt(sc1);
     for (int i = 0; i < q1; ++i) {
         const int b = i < r ? i : i + 1;
         bt[i] = (c[b] - mvec[i] * c[r]) * dsc[i] * isc;
@@ -100,29 +101,29 @@ __device__ inline double limits_l1(const double* F, const Layout& Ly, int p, int
     return sc1;
 }
 
-__device__ inline void limits_l2(const double* F, const Layout& Ly, int p, int q, const double* c,
-                                 double d, int r, int s, double* bt)
+template <typename T>
+__device__ inline void limits_l2(const T* F, const Layout& Ly, int p, int q, const T* c, T d, int r, int s, T* bt)
 {
     const int q1 = q - 1, q2 = q - 2;
-    const double nu = F[Ly.scal + SC_NU], nu1 = nu + p, nu2 = nu1 + 1.0;
-    const double k0 = (nu + d) / nu1;
-    const double Srr = k0 * F[Ly.Lam + r * q + r];
-    const double* blk = F + Ly.l1 + r * Ly.l1s;
-    const double* mvec = blk;
-    const double* sch = blk + q1;
-    double cp[CF_MAXQ];
+    const T nu = F[Ly.scal + SC_NU], nu1 = nu + p, nu2 = nu1 + T(1);
+    const T k0 = (nu + d) / nu1;
+    const T Srr = k0 * F[Ly.Lam + r * q + r];
+    const T* blk = F + Ly.l1 + r * Ly.l1s;
+    const T* mvec = blk;
+    const T* sch = blk + q1;
+    T cp[CF_MAXQ];
     for (int i = 0; i < q1; ++i) {
         const int b = i < r ? i : i + 1;
         cp[i] = c[b] - mvec[i] * c[r];
     }
-    const double sc1 = (nu1 + c[r] * c[r] / Srr) / (nu1 + 1.0) * k0;
-    const double kp = nu2 / (nu2 - 2.0) * sc1;
-    const double Vss = kp * sch[s * q1 + s];
-    const double* b2 = F + Ly.l2 + (r * q1 + s) * Ly.l2s;
-    const double* mv2 = b2;
-    const double* ds2 = b2 + q2;
-    const double kap2 = (nu2 - 2.0 + cp[s] * cp[s] / Vss) / (nu2 - 1.0);
-    const double isc2 = 1.0 / sqrt(kap2 * kp);
+    const T sc1 = (nu1 + c[r] * c[r] / Srr) / (nu1 + T(1)) * k0;
+    const T kp = nu2 / (nu2 - T(2)) * sc1;
+    const T Vss = kp * sch[s * q1 + s];
+    const T* b2 = F + Ly.l2 + (r * q1 + s) * Ly.l2s;
+    const T* mv2 = b2;
+    const T* ds2 = b2 + q2;
+    const T kap2 = (nu2 - T(2) + cp[s] * cp[s] / Vss) / (nu2 - T(1));
+    const T isc2 = T(1) / m_sqrt(kap2 * kp);
     for (int i = 0; i < q2; ++i) {
         const int b = i < s ? i : i + 1;
         bt[i] = (cp[b] - mv2[i] * cp[s]) * ds2[i] * isc2;

@@ -15,6 +15,80 @@ __device__ __forceinline__ void put_t2f(const RecSet& L, long long rec, const do
     if (L.t2f) t2_record_f32(bt[0], bt[1], F[fac + 2], dof, L.t2f + 2 * rec);
 }
 
+// Mixed form: the same record inputs from FP32 limits and the FP32 copy of the
+// factor (Fc: the record's 2 x 2 correlation factor [1, 0; rho, sqrt(1 - rho^2)]),
+// so 1 - rho^2 is the square of its last entry and h|rho| - sign(rho) k one FMA.
+__device__ __forceinline__ void put_t2f32(const RecSet& L, long long rec, const float* bt, const float* Fc,
+                                          float dof)
+{
+    const float rho = Fc[2], l11 = Fc[3];
+    L.t2f[2 * rec] = make_float4(bt[0], bt[1], rho, dof);
+    L.t2f[2 * rec + 1] = make_float4(l11 * l11, fmaf(bt[0], fabsf(rho), rho > 0.0f ? -bt[1] : bt[1]), 0.0f, 0.0f);
+}
+
+// Mixed form: one pair in FP32 (whitening, log t_p, limits, FP32 T_2 inputs);
+// T_2 records of the FP32 modes need no FP64 fields, the others get them.
+__device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, long long j)
+{
+    const int p = a.D.p, q = a.D.q;
+    const int m0 = (a.density_only || a.single_pass) ? 1 : 2;
+    const float* F = a.F32 + (size_t)h * a.Ly.stride;
+    const int foff = h * a.Ly.stride;
+    const double nu1d = a.F[(size_t)h * a.Ly.stride + a.Ly.scal + SC_NU] + p;
+    const float nu1 = F[a.Ly.scal + SC_NU] + p;
+    float c[CF_MAXQ], d, logtp, bt[CF_MAXQ];
+    pair_whiten_f32(F, a.Ly, p, q, a.y32 + (size_t)j * p, &d, c, &logtp);
+    a.pd[2 * pid] = d;
+    a.pd[2 * pid + 1] = logtp;
+    for (int k = 0; k < q; ++k) a.pc[pid * q + k] = c[k];
+    for (int w = 0; w < m0; ++w) {
+        const long long rec = pid * m0 + w;
+        limits_l0<float>(F, a.Ly, p, q, c, d, w, bt);
+        a.L0.fac[rec] = foff + fac_l0(a.Ly);
+        a.L0.tab[rec] = 3 * h + 2 * w;
+        if (q == 2 && a.L0.t2f) {
+            put_t2f32(a.L0, rec, bt, F + fac_l0(a.Ly), nu1 + 2.0f * w);
+        } else {
+            for (int k = 0; k < q; ++k) a.L0.bt[rec * q + k] = bt[k];
+            a.L0.dof[rec] = nu1d + 2.0 * w;
+        }
+    }
+    if (a.density_only) return;
+    if (a.single_pass) {
+        limits_l0<float>(F, a.Ly, p, q, c, d, 1, bt);
+        for (int k = 0; k < q; ++k) a.LM.bt[pid * q + k] = bt[k];
+        a.LM.fac[pid] = foff + fac_l0(a.Ly);
+        a.LM.tab[pid] = 3 * h + 2;
+        a.LM.dof[pid] = nu1d + 2.0;
+        return;
+    }
+    const int q1 = q - 1, q2 = q - 2;
+    for (int r = 0; r < q && q1 > 0; ++r) {
+        const long long rec = pid * q + r;
+        limits_l1<float>(F, a.Ly, p, q, c, d, r, bt);
+        a.L1.fac[rec] = foff + fac_l1(a.Ly, q, r);
+        a.L1.tab[rec] = 3 * h + 1;
+        if (q1 == 2 && a.L1.t2f) {
+            put_t2f32(a.L1, rec, bt, F + fac_l1(a.Ly, q, r), nu1 + 1.0f);
+        } else {
+            for (int k = 0; k < q1; ++k) a.L1.bt[rec * q1 + k] = bt[k];
+            a.L1.dof[rec] = nu1d + 1.0;
+        }
+        for (int s = 0; s < q1 && q2 > 0; ++s) {
+            const long long r2 = pid * q * q1 + r * q1 + s;
+            limits_l2<float>(F, a.Ly, p, q, c, d, r, s, bt);
+            a.L2.fac[r2] = foff + fac_l2(a.Ly, q, r, s);
+            a.L2.tab[r2] = 3 * h;
+            if (q2 == 2 && a.L2.t2f) {
+                put_t2f32(a.L2, r2, bt, F + fac_l2(a.Ly, q, r, s), nu1);
+            } else {
+                for (int k = 0; k < q2; ++k) a.L2.bt[r2 * q2 + k] = bt[k];
+                a.L2.dof[r2] = nu1d;
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(128) plan_kernel(PlanArgs a)
 {
     const int p = a.D.p, q = a.D.q;
@@ -24,15 +98,15 @@ __global__ void __launch_bounds__(128) plan_kernel(PlanArgs a)
          pid += (long long)gridDim.x * blockDim.x) {
         const int h = (int)(pid / a.D.n);
         const long long j = pid - (long long)h * a.D.n;
+        if (a.F32) {
+            plan_pair_f32(a, pid, h, j);
+            continue;
+        }
         const double* F = a.F + (size_t)h * a.Ly.stride;
         const int foff = h * a.Ly.stride;
         const double nu1 = F[a.Ly.scal + SC_NU] + p;
         double c[CF_MAXQ], d, logtp;
-        if (a.F32)
-            pair_whiten_f32(a.F32 + (size_t)h * a.Ly.stride, F, a.Ly, p, q, a.y32 + (size_t)j * p, &d,
-                            c, &logtp);
-        else
-            pair_whiten(F, a.Ly, p, q, a.y + (size_t)j * p, &d, c, &logtp);
+        pair_whiten(F, a.Ly, p, q, a.y + (size_t)j * p, &d, c, &logtp);
         a.pd[2 * pid] = d;
         a.pd[2 * pid + 1] = logtp;
         for (int k = 0; k < q; ++k) a.pc[pid * q + k] = c[k];

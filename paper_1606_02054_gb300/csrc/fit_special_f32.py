@@ -1,5 +1,6 @@
-"""Derives the coefficients of the FP32 normal CDF and inverse used by the
-lattice integrators (special.cuh: cf_ncdf_f32, cf_ncdfinv_f32).
+"""Derives the coefficients of the FP32 special functions of the integrators
+(special.cuh): the normal CDF and its inverse of the lattice integrators
+(cf_ncdf_f32, cf_ncdfinv_f32) and the sine of the T_2 quadrature (cf_sin_pi).
 
 Both are this project's own fits (Lawson's iteratively reweighted least
 squares in the Chebyshev basis, i.e. a near-minimax polynomial), made in FP64
@@ -14,8 +15,11 @@ mapped variable t in [-1, 1]:
   Phi^-1(p), pm = min(p, 1 - p) in [1e-37, 1/2]:
       x = log2(-log2 pm) in [0, 7],  Phi^-1(pm) = x Q(t), t = affine(x)
       (the factor x makes Phi^-1(1/2) = 0 exactly);  Phi^-1(p) = -x Q for p > 1/2.
+  sin(x), |x| <= pi:  r = |x| folded to [0, pi/2] (pi - |x| beyond pi/2),
+      sin(r) = r S(r^2) with S fitted on [0, (pi/2)^2] (relative error of sin/r),
+      then the sign of x.
 
-Run:  python fit_ncdf_f32.py   (prints the constants and the fit errors)
+Run:  python fit_special_f32.py   (prints the constants and the fit errors)
 """
 import numpy as np
 import scipy.special as sp
@@ -56,6 +60,19 @@ def fit_ncdfinv(deg=8, xmax=7.0):
     return m, 2.0 / xmax, -1.0, err
 
 
+def fit_sin(deg=4):
+    r = np.linspace(1e-6, np.pi / 2, 400001)
+    t2 = r * r
+    hi = (np.pi / 2) ** 2
+    m, _ = lawson(t2, np.sin(r) / r, deg, 0.0, hi)
+    # monomial coefficients in r^2 itself (t = 2 r^2 / hi - 1 expanded)
+    tpoly = Pm.Polynomial([-1.0, 2.0 / hi])
+    S = sum(c * tpoly ** k for k, c in enumerate(m))
+    coef = S.coef
+    err = np.abs(r * Pm.polyval(t2, coef) - np.sin(r)).max()
+    return coef, err
+
+
 if __name__ == "__main__":
     m, A, B, e = fit_ncdf()
     print(f"// Phi: max |error of the log2 exponent| {e:.2e}")
@@ -65,3 +82,6 @@ if __name__ == "__main__":
     print(f"// Phi^-1: max |error| {e:.2e}  (value = x * Q(t))")
     print(f"t = x * {A!r}f + {B!r}f")
     print("Q =", ", ".join(f"{c:.9e}f" for c in m))
+    coef, e = fit_sin()
+    print(f"// sin: max |error| {e:.2e}  (value = r * S(r^2), S in powers of r^2)")
+    print("S =", ", ".join(f"{c:.9e}f" for c in coef))

@@ -42,7 +42,7 @@ __device__ __forceinline__ float m_abs(float x) { return fabsf(x); }
 __device__ __forceinline__ double m_abs(double x) { return fabs(x); }
 // ---------------------------------------------------------------------------
 // FP32 normal CDF and inverse of the lattice integrators: this project's own
-// near-minimax polynomial fits (csrc/fit_ncdf_f32.py derives every constant
+// near-minimax polynomial fits (csrc/fit_special_f32.py derives every constant
 // below), evaluated with the approximate PTX reciprocal, exp2 and log2.
 //   Phi(a) = tau 2^(P(t) - z^2 log2 e), z = |a|/sqrt 2, tau = 1/(1 + z/2), a <= 0;
 //            1 - Phi(-a) for a > 0.  Error (measured on the device against FP64):
@@ -108,6 +108,23 @@ __device__ __forceinline__ float cf_ncdfinv_f32(float p)
     Q = fmaf(Q, t, -0.9593654870986938f);
     Q *= x;  // Phi^-1(1/2) = 0 exactly
     return p > 0.5f ? -Q : Q;
+}
+
+// sin(x) for |x| <= pi (the arguments of the FP32 T_2 quadrature): |x| folded onto
+// [0, pi/2] by pi - |x| (pi in two FP32 parts), then r S(r^2) with S a degree-4
+// near-minimax fit (csrc/fit_special_f32.py); error 1.2e-7 relative where
+// |sin x| > 1e-3, 1.7e-7 absolute near +-pi.
+__device__ __forceinline__ float cf_sin_pi(float x)
+{
+    const float ax = fabsf(x);
+    const float r = ax > 1.57079637f ? (3.14159274f - ax) + -8.74227766e-08f : ax;
+    const float r2 = r * r;
+    float S = 2.605247118e-06f;
+    S = fmaf(S, r2, -1.980908564e-04f);
+    S = fmaf(S, r2, 8.333051577e-03f);
+    S = fmaf(S, r2, -1.666665822e-01f);
+    S = fmaf(S, r2, 1.0f);
+    return copysignf(r * S, x);
 }
 
 // FP32 reciprocal and division by the approximate PTX reciprocal (relative
@@ -361,8 +378,15 @@ __device__ double t2cdf_warp(R h, R k, R rho, R nu, R omr2, R cr, R lgb, R lgb1,
         const R um = graded ? u * u * u : u;
         const R jac = graded ? R(3) * u * u : R(1);
         const R off = L * um;
-        const R sp = m_sin(anc + off);
-        const R z = S.zs * m_sin((p1 ? R(0) : S.d0) + off);
+        R sp, sd;
+        if constexpr (sizeof(R) == sizeof(float)) {
+            sp = cf_sin_pi(anc + off);  // both arguments lie in [-pi, pi]
+            sd = cf_sin_pi((p1 ? R(0) : S.d0) + off);
+        } else {
+            sp = m_sin(anc + off);
+            sd = m_sin((p1 ? R(0) : S.d0) + off);
+        }
+        const R z = S.zs * sd;
         R f;
         if constexpr (sizeof(R) == sizeof(float)) {
             // sin^(nu-1) by the approximate log2/exp2 (~5e-6 relative at nu ~ 40)

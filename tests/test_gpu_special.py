@@ -1,9 +1,9 @@
 """GPU: the FP32 normal CDF and inverse of the lattice integrators (own
-polynomial fits, see csrc/fit_ncdf_f32.py) against scipy's FP64 values, with
+polynomial fits, see csrc/fit_special_f32.py) against scipy's FP64 values, with
 the CUDA library's normcdff / normcdfinvf measured beside them.
 
 Bounds (FP32 evaluation of the fits, emulated on the CPU in
-csrc/fit_ncdf_f32.py's terms): Phi 4e-6 relative for a >= -5 and 3e-5 relative
+csrc/fit_special_f32.py's terms): Phi 4e-6 relative for a >= -5 and 3e-5 relative
 down to a = -13 (the bottom of FP32's normal range) -- the FP32 rounding of
 z sqrt(log2 e) and of the exponent dominates;
 Phi^-1 1e-6 absolute where |y| <= 1 (the approximate log2 near p = 1/2) and
