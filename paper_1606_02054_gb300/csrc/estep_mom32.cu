@@ -4,15 +4,20 @@
 #include "internal.cuh"
 #include "special.cuh"
 
+// K = 7, 8 need 147-168 registers: blocks of 4 warps let 3 blocks (12 warps) share
+// an SM where one block of 8 would leave it at 8
 template <int K>
-__global__ void __launch_bounds__(256) lattice_mom_kernel_32(RecSet r, IntegArgs a)
+__host__ __device__ constexpr int mom32_block() { return K >= 7 ? 128 : 256; }
+
+template <int K>
+__global__ void __launch_bounds__(mom32_block<K>()) lattice_mom_kernel_32(RecSet r, IntegArgs a)
 {
     constexpr int W = K + K * (K + 1) / 2;
     const int lane = threadIdx.x & (CF_WARP - 1);
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const size_t NM = (size_t)a.lat.N * a.lat.M;
-    __shared__ double slot[8][W + 1];
+    __shared__ double slot[mom32_block<K>() / CF_WARP][W + 1];
     double* acc = slot[threadIdx.x >> 5];
     for (long long i = warp; i < r.nrec; i += nwarps) {
         double bt[K];
@@ -33,8 +38,8 @@ cudaError_t launch_mom32(int k, const RecSet& r, const IntegArgs& a, int blocks,
     case 4: lattice_mom_kernel_32<4><<<blocks, 256, 0, st>>>(r, a); break;
     case 5: lattice_mom_kernel_32<5><<<blocks, 256, 0, st>>>(r, a); break;
     case 6: lattice_mom_kernel_32<6><<<blocks, 256, 0, st>>>(r, a); break;
-    case 7: lattice_mom_kernel_32<7><<<blocks, 256, 0, st>>>(r, a); break;
-    case 8: lattice_mom_kernel_32<8><<<blocks, 256, 0, st>>>(r, a); break;
+    case 7: lattice_mom_kernel_32<7><<<2 * blocks, 128, 0, st>>>(r, a); break;  // same warps
+    case 8: lattice_mom_kernel_32<8><<<2 * blocks, 128, 0, st>>>(r, a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

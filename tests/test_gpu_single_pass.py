@@ -104,3 +104,21 @@ def test_single_pass_shapes_fp64(cf, oracle, p, q, g, n):
     _row_close(gp["eu"], o["eu"], 1e-8)
     _row_close(gp["euu"], o["euu"], 1e-8, axes=(-1, -2))
     assert abs(L - o["loglik"]) <= 1e-10 * abs(o["loglik"])
+
+
+@pytest.mark.parametrize("p,q,g,n", [(5, 5, 2, 40), (7, 6, 2, 24), (8, 7, 2, 24), (8, 8, 2, 20)])
+def test_single_pass_shapes_fp32(cf, oracle, p, q, g, n):
+    """FP32 moment kernels of every record dimension up to 8 (K = 7, 8 run in 4-warp
+    blocks) against the FP64 oracle on the same lattice: FP32 bounds."""
+    rng = np.random.default_rng(3000 + 97 * p + 13 * q + g)
+    params = synth.draw_params(rng, p, q, g, delta_sd=0.8)
+    y, _ = synth.sample(rng, n, params)
+    w = dict(p=p, q=q, g=g, n=n, y=y, qmc=synth.qmc_settings(2))
+    ctx = _ctx(cf, w, params, precision=1)
+    L = cf.cfust_estep(ctx)
+    gp = cf.cfust_get_pairs(ctx)
+    o = oracle.estep(y, params, _spec(oracle, w))
+    assert abs(L - o["loglik"]) <= 1e-6 * abs(o["loglik"])
+    np.testing.assert_allclose(gp["u"], o["u"], rtol=2e-4)
+    _row_close(gp["eu"], o["eu"], 5e-4)
+    _row_close(gp["euu"], o["euu"], 5e-4, axes=(-1, -2))
