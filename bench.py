@@ -150,14 +150,16 @@ def cpu_baseline(w, nsample, steps=1, moments=1):
     cores = os.cpu_count() or 1
     params = {k: np.array(v, dtype=float) for k, v in w["init"].items()}
     t0 = time.perf_counter()
+    ll0 = None
     for _ in range(steps):
         e = oracle.estep(sub, params, spec, nthreads=cores)
+        ll0 = e["loglik"] if ll0 is None else ll0
         params, _ = oracle.mstep(sub, e, params)
     dt = (time.perf_counter() - t0) / steps
     return {"value": nsample * w["g"] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {nsample} of {w['n']} observations of {w['name']}, "
                       f"E-step + M-step in FP64 on {cores} host threads, {steps} step(s)",
-            "ms_per_step": dt * 1e3}
+            "ms_per_step": dt * 1e3, "loglik_at_start": ll0}
 
 
 def run_reference(args, w, rank, world):
@@ -178,6 +180,10 @@ def run_reference(args, w, rank, world):
             "data": "synthetic", "impl": "reference",
             "config": {"workload": w["name"], "n": w["n"], "p": w["p"], "q": w["q"], "g": w["g"],
                        "qmc": f"{w['qmc']['npoints']}x{w['qmc']['nshifts']}",
+                       "form": ("single-pass moments" if args.moments == "single-pass" and w["q"] >= 3
+                                else "moment recursion"),
+                       "precision": "fp64 throughout (the CPU oracle)",
+                       "parallelism": f"{cores} host threads (OpenMP over observations)",
                        "sample_n": nsample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"first {nsample} observations per step"},
@@ -187,10 +193,11 @@ def run_reference(args, w, rank, world):
 
 
 def run_batch(args, rank, world):
-    """Batched fits (config 4 shapes): every fit's EM loop is one device-controlled
-    CUDA graph and all fits run concurrently (cfust_fit_batch).  One step = one EM
-    iteration of every fit; value = sum over fits of n*g per second.  The same
-    iteration run fit by fit through cfust_estep/cfust_mstep is timed beside it."""
+    """Batched fits (p = q uniform on 2..8, g on 2..6, n log-uniform on 1e3..1e5): every
+    fit's EM loop is one device-controlled CUDA graph and all fits run concurrently
+    (cfust_fit_batch).  One step = one EM iteration of every fit; value = sum over fits
+    of n*g per second.  The same iteration run fit by fit through cfust_estep /
+    cfust_mstep is timed beside it."""
     import torch
 
     from paper_1606_02054_gb300 import build, synth
@@ -445,6 +452,19 @@ def main():
                 "ms_per_launch": dom_ms_per_launch,
                 "note": "no instruction count measured for this kernel and precision"}
 
+    # the stated loglik error: the GPU's E-step l on the CPU baseline's sample (same
+    # observations, starting values and lattice) against the oracle's
+    ll_check = None
+    if cpu is not None and cpu.get("loglik_at_start") is not None:
+        ns = args.cpu_sample
+        cchk = cf.cfust_create(w["p"], w["q"], w["g"], ns, _opts(cf, w, prec, moments=chosen_moments))
+        cf.cfust_set_data(cchk, np.ascontiguousarray(w["y"][:ns]))
+        cf.cfust_set_params(cchk, w["init"])
+        lg = cf.cfust_estep(cchk)
+        lo = cpu["loglik_at_start"]
+        ll_check = {"rel_err": abs(lg - lo) / abs(lo), "gpu": lg, "oracle": lo,
+                    "sample": f"first {ns} observations at the starting values, same lattice"}
+
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -497,7 +517,8 @@ def main():
                 "loglik_last": main_run["ll"],
                 "gpu_launches": int(launches),
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
-                "roofline": roof, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu}
+                "roofline": roof, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+                "loglik_check": ll_check}
         if plain_run:
             line["plain_gpu"] = {
                 "form": "moment recursion (T_q, T_{q-1}, T_{q-2} records)",

@@ -30,14 +30,14 @@ DEFAULT_QMC_SHIFTS = 8
 SEED_BASE = 1606_0000
 
 
-def seed_for(config: int, start: int = 0) -> int:
-    return SEED_BASE + 100 * config + start
+def seed_for(stream: int, start: int = 0) -> int:
+    return SEED_BASE + 100 * stream + start
 
 
-def qmc_settings(config: int = 2, npoints=DEFAULT_QMC_POINTS, nshifts=DEFAULT_QMC_SHIFTS,
+def qmc_settings(stream: int = 2, npoints=DEFAULT_QMC_POINTS, nshifts=DEFAULT_QMC_SHIFTS,
                  korobov_a=DEFAULT_KOROBOV_A):
     return dict(npoints=npoints, nshifts=nshifts, korobov_a=korobov_a,
-                seed=seed_for(config) * 7919 + 13)
+                seed=seed_for(stream) * 7919 + 13)
 
 
 # ----------------------------------------------------------------------------
@@ -196,17 +196,17 @@ def params_from_labels(y, lab, g, q, alpha=0.5, nu0=10.0):
 # workloads
 # ----------------------------------------------------------------------------
 WORKLOADS = {
-    "two_comp_p2": dict(config=1, p=2, q=2, g=2, n=1000, iters=100),
-    "flow_p4": dict(config=2, p=4, q=4, g=4, n=200_000, iters=50),
-    "wide_p16": dict(config=3, p=16, q=2, g=8, n=2_000_000, iters=20),
-    "learned_p6": dict(config=5, p=6, q=6, g=6, n=1_000_000, iters=30),
+    "two_comp_p2": dict(stream=1, p=2, q=2, g=2, n=1000, iters=100),
+    "flow_p4": dict(stream=2, p=4, q=4, g=4, n=200_000, iters=50),
+    "wide_p16": dict(stream=3, p=16, q=2, g=8, n=2_000_000, iters=20),
+    "learned_p6": dict(stream=5, p=6, q=6, g=6, n=1_000_000, iters=30),
 }
 
 
 # Batched fits: nfits independent problems, p uniform on {2..8}, q = p, g
 # uniform on {2..6}, n log-uniform on [1e3, 1e5], parameters drawn as for
 # flow_p4, `starts` random-partition starts per problem, 30 iterations.
-BATCH = dict(config=4, nfits=256, starts=4, p=(2, 8), g=(2, 6), n=(1_000, 100_000), iters=30)
+BATCH = dict(stream=4, nfits=256, starts=4, p=(2, 8), g=(2, 6), n=(1_000, 100_000), iters=30)
 
 
 def make_batch(nfits=None, starts=None, n_range=None, p_range=None, g_range=None):
@@ -220,16 +220,16 @@ def make_batch(nfits=None, starts=None, n_range=None, p_range=None, g_range=None
     g_lo, g_hi = B["g"] if g_range is None else g_range
     fits = []
     for f in range(nfits):
-        rng = np.random.default_rng([seed_for(B["config"]), f])
+        rng = np.random.default_rng([seed_for(B["stream"]), f])
         p = int(rng.integers(p_lo, p_hi + 1))
         g = int(rng.integers(g_lo, g_hi + 1))
         n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
         truth = draw_params(rng, p, p, g)
         y, z = sample(rng, n, truth)
-        st = [random_partition_start(np.random.default_rng([seed_for(B["config"], s + 1), f]), y, g, p)
+        st = [random_partition_start(np.random.default_rng([seed_for(B["stream"], s + 1), f]), y, g, p)
               for s in range(starts)]
         fits.append(dict(y=y, z=z, truth=truth, starts=st, p=p, q=p, g=g, n=n))
-    return dict(fits=fits, qmc=qmc_settings(B["config"]), iters=B["iters"])
+    return dict(fits=fits, qmc=qmc_settings(B["stream"]), iters=B["iters"])
 
 
 def make_workload(name, n=None, start=0, with_init=True):
@@ -237,7 +237,7 @@ def make_workload(name, n=None, start=0, with_init=True):
     n overrides the size (the first n observations of the same draw are not
     reused; the whole draw is repeated at the new size with the same seed)."""
     w = WORKLOADS[name]
-    cfg = w["config"]
+    cfg = w["stream"]
     rng = np.random.default_rng(seed_for(cfg, start))
     p, q, g = w["p"], w["q"], w["g"]
     nn = int(n if n is not None else w["n"])

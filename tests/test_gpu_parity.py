@@ -7,7 +7,7 @@ Tolerances:
   FP64 mode, q >= 3: both sides evaluate the same lattice points, so they
       agree far inside 3 standard errors; asserted at 1e-8 relative.
   FP32 mode: |alpha_s diff| <= 3 SE + 5e-5 alpha_s (FP32 rounding of the
-      lattice products and of the T_2 quadrature, see DESIGN.md).
+      lattice products and of the T_2 quadrature).
   Fits: final log-likelihood relative error <= 1e-6, parameters <= 1e-4
       after the same iteration count.
 """
