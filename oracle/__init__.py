@@ -66,6 +66,7 @@ def lib():
             L.ora_t1pdf.argtypes = [d, d]; L.ora_t1pdf.restype = d
             L.ora_t1cdf.argtypes = [d, d]; L.ora_t1cdf.restype = d
             L.ora_t2cdf.argtypes = [d, d, d, d]; L.ora_t2cdf.restype = d
+            L.ora_phi2.argtypes = [d, d, d]; L.ora_phi2.restype = d
             L.ora_splitmix64_u01.argtypes = [C.c_uint64]; L.ora_splitmix64_u01.restype = d
             L.ora_qmc_shift.argtypes = [C.POINTER(Qmc), i, i]; L.ora_qmc_shift.restype = d
             L.ora_tkcdf.argtypes = [i, _dp, _dp, d, C.POINTER(Qmc), _dp]
@@ -135,6 +136,7 @@ def chi2_quantile(w, nu, wc=None):
 def t1pdf(x, nu): return lib().ora_t1pdf(float(x), float(nu))
 def t1cdf(x, nu): return lib().ora_t1cdf(float(x), float(nu))
 def t2cdf(h, k, rho, nu): return lib().ora_t2cdf(float(h), float(k), float(rho), float(nu))
+def phi2(h, k, rho): return lib().ora_phi2(float(h), float(k), float(rho))
 def splitmix64_u01(key): return lib().ora_splitmix64_u01(int(key) & 0xFFFFFFFFFFFFFFFF)
 def qmc_shift(spec: Qmc, m, d): return lib().ora_qmc_shift(C.byref(spec), int(m), int(d))
 

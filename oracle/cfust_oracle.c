@@ -217,6 +217,7 @@ double ora_chi2_quantile(double w, double wc, double nu)
 /* ------------------------------------------------------------------ */
 double ora_t1pdf(double x, double nu)
 {
+    if (isinf(nu)) return exp(-0.5 * x * x) / sqrt(2.0 * ORA_PI);  /* the normal limit */
     return exp(lgamma(0.5 * (nu + 1.0)) - lgamma(0.5 * nu) - 0.5 * log(nu * ORA_PI)
                - 0.5 * (nu + 1.0) * log1p(x * x / nu));
 }
@@ -224,6 +225,7 @@ double ora_t1pdf(double x, double nu)
 /* T_1(x; nu): P(T > |x|) = 1/2 I_{nu/(nu+x^2)}(nu/2, 1/2). */
 double ora_t1cdf(double x, double nu)
 {
+    if (isinf(nu)) return ora_phi(x);  /* the normal limit */
     if (x == 0.0) return 0.5;
     if (isinf(x)) return x > 0 ? 1.0 : 0.0;
     double x2 = x * x;
@@ -334,8 +336,30 @@ static double t2_integrand(double s, const void* vctx)
     return pdf * cdf / (s * s);
 }
 
+/* Standard bivariate normal CDF (the nu -> infinity limit of T_2):
+ * Phi_2(h, k; rho) = Phi(h) Phi(k) + int_0^rho phi_2(h, k; r) dr, and with r = sin(theta)
+ * the integrand exp(-(h^2 - 2 h k sin(theta) + k^2) / (2 cos^2(theta))) / (2 pi) is bounded
+ * on [0, asin(rho)]. */
+typedef struct { double h, k; } phi2_ctx;
+static double phi2_integrand(double th, const void* vctx)
+{
+    const phi2_ctx* c = (const phi2_ctx*)vctx;
+    const double st = sin(th), ct = cos(th);
+    if (ct <= 0.0) return 0.0;
+    return exp(-(c->h * c->h - 2.0 * c->h * c->k * st + c->k * c->k) / (2.0 * ct * ct)) / (2.0 * ORA_PI);
+}
+
+double ora_phi2(double h, double k, double rho)
+{
+    if (rho >= 1.0) return ora_phi(h < k ? h : k);
+    if (rho <= -1.0) { double v = ora_phi(h) + ora_phi(k) - 1.0; return v > 0.0 ? v : 0.0; }
+    phi2_ctx c = {h, k};
+    return ora_phi(h) * ora_phi(k) + integrate(phi2_integrand, &c, 0.0, asin(rho));
+}
+
 double ora_t2cdf(double h, double k, double rho, double nu)
 {
+    if (isinf(nu)) return ora_phi2(h, k, rho);
     if (h == -INFINITY || k == -INFINITY) return 0.0;
     if (h == INFINITY) return ora_t1cdf(k, nu);
     if (k == INFINITY) return ora_t1cdf(h, nu);
@@ -392,6 +416,10 @@ static void lattice_w(const ora_qmc* qmc, int i, int m, int d, double* w, double
 /* s = sqrt(chi2_nu^{-1}(w_0) / nu) at every lattice point (shift-major). */
 static void chi_table(const ora_qmc* qmc, double nu, double* tab)
 {
+    if (isinf(nu)) {  /* the normal limit: no chi variable, s = 1 */
+        for (size_t t = 0; t < (size_t)qmc->npoints * qmc->nshifts; ++t) tab[t] = 1.0;
+        return;
+    }
     for (int m = 0; m < qmc->nshifts; ++m)
         for (int i = 0; i < qmc->npoints; ++i) {
             double w, wc;
@@ -440,6 +468,7 @@ static double tk_qmc(int k, const double* b, const double* V, double nu,
             double w, wc;
             double s;
             if (stab) s = stab[(size_t)m * N + i];
+            else if (isinf(nu)) s = 1.0;
             else { lattice_w(qmc, i, m, 0, &w, &wc); s = sqrt(ora_chi2_quantile(w, wc, nu) / nu); }
             double y[ORA_MAXQ];
             double f = 1.0;
@@ -493,6 +522,7 @@ static double tk_moments_qmc(int k, const double* b, const double* V, double nu,
         for (int i = 0; i < N; ++i) {
             double w, wc, s;
             if (stab) s = stab[(size_t)m * N + i];
+            else if (isinf(nu)) s = 1.0;
             else { lattice_w(qmc, i, m, 0, &w, &wc); s = sqrt(ora_chi2_quantile(w, wc, nu) / nu); }
             double y[ORA_MAXQ];
             double f = 1.0;
@@ -618,9 +648,11 @@ static int comp_init(comp_t* C, int p, int q, const double* mu, const double* Si
             for (int i = 0; i < p; ++i) s += Delta[i * q + a] * OiD[i * q + b];
             C->Lambda[a * q + b] = (a == b ? 1.0 : 0.0) - s;
         }
-    /* eq (3): Gamma((nu+p)/2) / Gamma(nu/2) (nu pi)^{-p/2} |Omega|^{-1/2} */
-    C->logtp_const = lgamma(0.5 * (nu + p)) - lgamma(0.5 * nu)
-                   - 0.5 * p * log(nu * ORA_PI) - 0.5 * C->logdet;
+    /* eq (3): Gamma((nu+p)/2) / Gamma(nu/2) (nu pi)^{-p/2} |Omega|^{-1/2};
+       nu = infinity: the normal density of eq (2), (2 pi)^{-p/2} |Omega|^{-1/2} */
+    if (isinf(nu)) C->logtp_const = -0.5 * p * log(2.0 * ORA_PI) - 0.5 * C->logdet;
+    else C->logtp_const = lgamma(0.5 * (nu + p)) - lgamma(0.5 * nu)
+                        - 0.5 * p * log(nu * ORA_PI) - 0.5 * C->logdet;
     return 0;
 }
 
@@ -650,10 +682,125 @@ static void condition_on(int k, const double* S, int r, double* mvec, double* sc
 }
 
 /* One (observation, component) pair: eqs (3), (4), (13), (15), (16), (17). */
+/* The pair quantities of the nu -> infinity limit, the CFUSN model of eq (5):
+ * f = 2^q phi_p(y; mu, Omega) Phi_q(c; 0, Lambda); the latent scale W is 1, so u = 1
+ * (eq 13), eq (15) is not needed (no nu step), and eqs (16)-(17) are the moments of
+ * U = c - X with X ~ N_q(0, Lambda) truncated to X <= c.  Every scaling of the t case
+ * ((nu+d)/(nu+p), the conditional-scale factors, nu/(nu-2)) is 1 here. */
+static int pair_core_normal(const comp_t* C, const ora_qmc* qmc, const double* y, int density_only,
+                            double* logf, double* u_out, double* elogu_out, double* eu,
+                            double* euu, double* se_out)
+{
+    const int p = C->p, q = C->q;
+    const double inf = INFINITY;
+    double r[ORA_MAXP], Oir[ORA_MAXP];
+    for (int i = 0; i < p; ++i) r[i] = y[i] - C->mu[i];
+    chol_solve(p, C->Lo, r, Oir);
+    double d = 0.0;
+    for (int i = 0; i < p; ++i) d += r[i] * Oir[i];
+    double c[ORA_MAXQ];
+    for (int k = 0; k < q; ++k) {
+        double sum = 0.0;
+        for (int i = 0; i < p; ++i) sum += C->Delta[i * q + k] * Oir[i];
+        c[k] = sum;
+    }
+    /* eq (5): log 2^q + log phi_p(y; mu, Omega) + log Phi_q(c; 0, Lambda) */
+    double se_a = 0.0;
+    const double alpha = tk_any(q, c, C->Lambda, inf, qmc, C->stab[0], &se_a);
+    *logf = q * log(2.0) + C->logtp_const - 0.5 * d + log(alpha);
+    if (se_out) *se_out = se_a;
+    if (density_only) return 0;
+    *u_out = 1.0;
+    *elogu_out = 0.0;
+    if (qmc->moments && q >= 3) {
+        double m1[ORA_MAXQ], m2[ORA_MAXQ * ORA_MAXQ];
+        tk_moments_qmc(q, c, C->Lambda, inf, qmc, C->stab[2], m1, m2);
+        for (int a = 0; a < q; ++a) eu[a] = c[a] - m1[a];
+        for (int a = 0; a < q; ++a)
+            for (int bb = 0; bb < q; ++bb)
+                euu[a * q + bb] = c[a] * c[bb] - c[a] * m1[bb] - m1[a] * c[bb]
+                                + 0.5 * (m2[a * q + bb] + m2[bb * q + a]);
+        return 0;
+    }
+    /* x phi(x; S) = -S grad phi(x; S): E[X 1(X <= c)] = -Lambda xi with
+     * xi_r = phi_1(c_r; Lambda_rr) Phi_{q-1}(c_{-r} - m_r c_r; V_r) */
+    const double* S = C->Lambda;
+    double xi[ORA_MAXQ], H[ORA_MAXQ * ORA_MAXQ];
+    memset(H, 0, sizeof(H));
+    for (int rr = 0; rr < q; ++rr) {
+        const int k1 = q - 1;
+        double mvec[ORA_MAXQ], Vr[ORA_MAXQ * ORA_MAXQ], cp[ORA_MAXQ], mr[ORA_MAXQ];
+        double tq1 = 1.0;
+        if (k1 > 0) {
+            condition_on(q, S, rr, mvec, Vr);
+            int ii = 0;
+            for (int i = 0; i < q; ++i) {
+                if (i == rr) continue;
+                mr[ii] = mvec[ii] * c[rr];
+                cp[ii] = c[i] - mr[ii];
+                ++ii;
+            }
+            tq1 = tk_any(k1, cp, Vr, inf, qmc, C->stab[1], NULL);
+        }
+        xi[rr] = t1pdf_scaled(c[rr], S[rr * q + rr], inf) * tq1;
+        H[rr * q + rr] = c[rr] * xi[rr];
+        if (k1 == 0 || xi[rr] == 0.0) continue;
+        /* E[X_{-r} | X_r = c_r, X_{-r} <= c_{-r}] = m_r + E[Y | Y <= c'], Y ~ N(0, V_r) */
+        double xip[ORA_MAXQ];
+        for (int s2 = 0; s2 < k1; ++s2) {
+            const int k2 = k1 - 1;
+            double tq2 = 1.0;
+            if (k2 > 0) {
+                double mv2[ORA_MAXQ], Vs[ORA_MAXQ * ORA_MAXQ], cpp[ORA_MAXQ];
+                condition_on(k1, Vr, s2, mv2, Vs);
+                int ii = 0;
+                for (int i = 0; i < k1; ++i) {
+                    if (i == s2) continue;
+                    cpp[ii] = cp[i] - mv2[ii] * cp[s2];
+                    ++ii;
+                }
+                tq2 = tk_any(k2, cpp, Vs, inf, qmc, C->stab[0], NULL);
+            }
+            xip[s2] = t1pdf_scaled(cp[s2], Vr[s2 * k1 + s2], inf) * tq2;
+        }
+        int ii = 0;
+        for (int bcol = 0; bcol < q; ++bcol) {
+            if (bcol == rr) continue;
+            double ey = 0.0;
+            for (int s2 = 0; s2 < k1; ++s2) ey += Vr[ii * k1 + s2] * xip[s2];
+            H[rr * q + bcol] = xi[rr] * (mr[ii] - ey / tq1);
+            ++ii;
+        }
+    }
+    /* e2 = c + Lambda xi / alpha; e3 = c c^T + c (Lambda xi)^T/alpha + (Lambda xi) c^T/alpha
+     * + Lambda - Lambda H / alpha */
+    double Lxi[ORA_MAXQ];
+    for (int a = 0; a < q; ++a) {
+        double sum = 0.0;
+        for (int k = 0; k < q; ++k) sum += S[a * q + k] * xi[k];
+        Lxi[a] = sum;
+        eu[a] = c[a] + sum / alpha;
+    }
+    double E3[ORA_MAXQ * ORA_MAXQ];
+    for (int a = 0; a < q; ++a)
+        for (int bb = 0; bb < q; ++bb) {
+            double LH = 0.0;
+            for (int k = 0; k < q; ++k) LH += S[a * q + k] * H[k * q + bb];
+            E3[a * q + bb] = c[a] * c[bb] + (c[a] * Lxi[bb] + Lxi[a] * c[bb]) / alpha
+                           + S[a * q + bb] - LH / alpha;
+        }
+    for (int a = 0; a < q; ++a)
+        for (int bb = 0; bb < q; ++bb)
+            euu[a * q + bb] = 0.5 * (E3[a * q + bb] + E3[bb * q + a]);
+    return 0;
+}
+
 static int pair_core(const comp_t* C, const ora_qmc* qmc, const double* y, int density_only,
                      double* logf, double* u_out, double* elogu_out, double* eu,
                      double* euu, double* se_out)
 {
+    if (isinf(C->nu))
+        return pair_core_normal(C, qmc, y, density_only, logf, u_out, elogu_out, eu, euu, se_out);
     const int p = C->p, q = C->q;
     const double nu = C->nu;
     double r[ORA_MAXP], Oir[ORA_MAXP];

@@ -57,6 +57,9 @@ double ora_chi2_quantile(double w, double wc, double nu);  /* P(nu/2,x/2)=w; wc 
 double ora_t1pdf(double x, double nu);    /* univariate standard t density */
 double ora_t1cdf(double x, double nu);    /* T_1(x; nu) */
 double ora_t2cdf(double h, double k, double rho, double nu);  /* standard bivariate T_2 */
+double ora_phi2(double h, double k, double rho);              /* standard bivariate normal CDF */
+/* nu = +infinity anywhere (T_1, T_2, T_k, the density and the E-step) selects the normal limit:
+ * the CFUSN model of eq (5) for the E-step; fit it with ORA_HOLD_NU. */
 double ora_splitmix64_u01(uint64_t key);  /* one SplitMix64 output as a double in [0,1) */
 double ora_qmc_shift(const ora_qmc* qmc, int m, int d);
 /* T_k(b; 0, V, nu) for any k (k<=2 deterministic, k>=3 lattice QMC).

@@ -124,7 +124,7 @@ def _mc_moments(y, mu, Sigma, Delta, nu, n, seed):
     m = n // nb
     rows = []
     for _ in range(nb):
-        Wd = rng.gamma(nu / 2, 2 / nu, m)
+        Wd = np.ones(m) if np.isinf(nu) else rng.gamma(nu / 2, 2 / nu, m)
         U = np.abs(rng.standard_normal((m, q))) / np.sqrt(Wd)[:, None]
         z = (y - mu - U @ Delta.T) @ Li.T
         wt = np.exp(-0.5 * Wd * (z * z).sum(1) + 0.5 * p * np.log(Wd)
@@ -247,3 +247,93 @@ def test_single_pass_delta_zero(oracle):
     assert np.allclose(r["eu"], e1, rtol=5e-3)
     E2 = np.eye(q) + (2 / math.pi) * (np.ones((q, q)) - np.eye(q))
     assert np.allclose(r["euu"], E2, rtol=1e-2, atol=1e-2)
+
+
+
+# ---------------------------------------------------------------------------
+# nu = infinity: the CFUSN model of eq (5)
+# ---------------------------------------------------------------------------
+def test_phi2_closed_forms_and_scipy(oracle):
+    import scipy.stats as st
+    for rho in (-0.9, -0.3, 0.0, 0.45, 0.99):
+        assert abs(oracle.phi2(0.0, 0.0, rho) - (0.25 + math.asin(rho) / (2 * math.pi))) < 1e-14
+    assert abs(oracle.phi2(0.7, -0.4, 0.0) - st.norm.cdf(0.7) * st.norm.cdf(-0.4)) < 1e-15
+    assert abs(oracle.phi2(0.3, 1.1, 1.0) - st.norm.cdf(0.3)) < 1e-15
+    for h, k, rho in ((0.5, -1.2, 0.6), (-2.0, -1.5, -0.7), (1.3, 0.2, 0.95), (-3.0, 2.0, 0.3)):
+        mvn = st.multivariate_normal(mean=[0, 0], cov=[[1, rho], [rho, 1]])
+        assert abs(oracle.phi2(h, k, rho) - mvn.cdf([h, k])) < 1e-9
+    # T_2 -> Phi_2 at rate 1/nu
+    g1 = oracle.t2cdf(0.5, -1.2, 0.6, 1e2) - oracle.phi2(0.5, -1.2, 0.6)
+    g2 = oracle.t2cdf(0.5, -1.2, 0.6, 1e3) - oracle.phi2(0.5, -1.2, 0.6)
+    assert 7 < g1 / g2 < 13
+    assert oracle.t2cdf(0.5, -1.2, 0.6, math.inf) == oracle.phi2(0.5, -1.2, 0.6)
+
+
+def test_skew_normal_univariate_closed_form(oracle):
+    """p = q = 1, nu = inf: Azzalini's skew normal 2 phi(y; mu, omega^2) Phi(a (y - mu)/omega),
+    omega^2 = sigma^2 + delta^2, a = delta / sigma."""
+    import scipy.stats as st
+    mu, sig2, dl = 0.4, 1.3, -0.9
+    om = math.sqrt(sig2 + dl * dl)
+    a = dl / math.sqrt(sig2)
+    for y in (-3.0, -0.5, 0.4, 1.7, 4.0):
+        r = oracle.pair(np.array([y]), np.array([mu]), np.array([[sig2]]), np.array([[dl]]), math.inf,
+                        _spec(oracle))
+        ref = math.log(2 * st.norm.pdf(y, mu, om) * st.norm.cdf(a * (y - mu) / om))
+        assert abs(r["logf"] - ref) < 1e-12
+        assert r["u"] == 1.0
+
+
+@pytest.mark.parametrize("q", [1, 2])
+def test_skew_normal_density_integrates_to_one(oracle, q):
+    p = 2
+    if q == 2:
+        Sigma = np.array([[1.0, 0.5], [0.5, 1.0]])
+        Delta = np.array([[1.0, 0.5], [0.0, 1.5]])
+    else:
+        Sigma = np.array([[1.0, 0.3], [0.3, 0.8]])
+        Delta = np.array([[1.2], [-0.7]])
+    mu = np.array([0.5, -0.2])
+    x, wts = np.polynomial.legendre.leggauss(64)
+    sc = 4.0
+    Y, W = [], []
+    for i in range(64):
+        for j in range(64):
+            Y.append(mu + sc * np.array([x[i], x[j]]) * 2.5)
+            W.append(wts[i] * wts[j] * (sc * 2.5) ** 2)
+    params = dict(pi=[1.0], mu=[mu], Sigma=[Sigma], Delta=[Delta], nu=[math.inf])
+    e = oracle.estep(np.array(Y), params, _spec(oracle))
+    total = float(np.sum(np.exp(e["logf"][0]) * np.array(W)))
+    assert abs(total - 1.0) < 1e-6
+
+
+@pytest.mark.parametrize("case", ["p2q2", "p3q3"])
+def test_skew_normal_moments_brute_force(oracle, case):
+    rng = np.random.default_rng(21)
+    if case == "p2q2":
+        y, mu = np.array([5.5, 6.0]), np.array([4.0, 4.0])
+        Sigma = np.array([[1.0, 0.5], [0.5, 1.0]])
+        Delta = np.array([[1.0, 0.5], [0.0, 1.5]])
+    else:
+        y, mu = np.array([0.8, -0.3, 1.5]), np.zeros(3)
+        Sigma = _rand_spd(rng, 3)
+        Delta = rng.normal(0, 1, (3, 3))
+    r = oracle.pair(y, mu, Sigma, Delta, math.inf, _spec(oracle))
+    est, se = _mc_moments(y, mu, Sigma, Delta, math.inf, 3_200_000, 9)
+    got = np.concatenate([[math.exp(r["logf"]), r["u"]], r["eu"], r["euu"].ravel()])
+    z = np.abs(got - est) / np.maximum(se, 1e-12)
+    assert np.all(z < 5.0), (case, got, est, se)
+
+
+def test_skew_normal_single_pass_matches_recursion(oracle):
+    rng = np.random.default_rng(22)
+    p, q = 3, 3
+    Sigma = _rand_spd(rng, p)
+    Delta = rng.normal(0, 1, (p, q))
+    mu = np.zeros(p)
+    for y in (np.array([0.8, -0.3, 1.5]), np.array([-1.0, 2.0, 0.2])):
+        a = oracle.pair(y, mu, Sigma, Delta, math.inf, _spec(oracle))
+        b = oracle.pair(y, mu, Sigma, Delta, math.inf, oracle.qmc(1024, 8, 119, 5, moments=1))
+        assert a["logf"] == b["logf"]
+        np.testing.assert_allclose(b["eu"], a["eu"], rtol=0, atol=5e-3 * np.abs(a["eu"]).max())
+        np.testing.assert_allclose(b["euu"], a["euu"], rtol=0, atol=5e-3 * np.abs(a["euu"]).max())
