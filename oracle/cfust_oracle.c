@@ -352,9 +352,16 @@ static double phi2_integrand(double th, const void* vctx)
 double ora_phi2(double h, double k, double rho)
 {
     if (rho >= 1.0) return ora_phi(h < k ? h : k);
-    if (rho <= -1.0) { double v = ora_phi(h) + ora_phi(k) - 1.0; return v > 0.0 ? v : 0.0; }
+    /* Phi_2 at rho = -1: P(-k < X <= h) = P(-h <= X < k), taken in the form whose larger
+       endpoint is the one nearer the lower tail, where Phi keeps its relative precision */
+    double lower = 0.0;
+    if (h + k > 0.0) lower = h - k < 0.0 ? ora_phi(h) - ora_phi(-k) : ora_phi(k) - ora_phi(-h);
+    if (rho <= -1.0) return lower;
     phi2_ctx c = {h, k};
-    return ora_phi(h) * ora_phi(k) + integrate(phi2_integrand, &c, 0.0, asin(rho));
+    /* the integrand is positive: from rho = 0 for rho >= 0, and from rho = -1 (the lower
+       Frechet bound) for rho < 0, so small values are not differences of large ones */
+    if (rho >= 0.0) return ora_phi(h) * ora_phi(k) + integrate(phi2_integrand, &c, 0.0, asin(rho));
+    return lower + integrate(phi2_integrand, &c, -0.5 * ORA_PI, asin(rho));
 }
 
 double ora_t2cdf(double h, double k, double rho, double nu)
@@ -681,6 +688,20 @@ static void condition_on(int k, const double* S, int r, double* mvec, double* sc
     }
 }
 
+/* A pair whose T_q is 0 in FP64 (the observation lies beyond the range of the arithmetic
+ * on this component's skewing side): log f = -inf there, so tau = 0 (eq 12), and the
+ * conditional expectations, which enter eqs (18)-(22) only multiplied by tau, are set to
+ * u = 1, E[log w] = 0, e2 = 0, e3 = 0 instead of the 0/0 of eqs (13)-(17). */
+static int pair_null(int q, int density_only, double* u_out, double* elogu_out, double* eu, double* euu)
+{
+    if (density_only) return 0;
+    *u_out = 1.0;
+    *elogu_out = 0.0;
+    for (int a = 0; a < q; ++a) eu[a] = 0.0;
+    for (int a = 0; a < q * q; ++a) euu[a] = 0.0;
+    return 0;
+}
+
 /* One (observation, component) pair: eqs (3), (4), (13), (15), (16), (17). */
 /* The pair quantities of the nu -> infinity limit, the CFUSN model of eq (5):
  * f = 2^q phi_p(y; mu, Omega) Phi_q(c; 0, Lambda); the latent scale W is 1, so u = 1
@@ -709,6 +730,7 @@ static int pair_core_normal(const comp_t* C, const ora_qmc* qmc, const double* y
     const double alpha = tk_any(q, c, C->Lambda, inf, qmc, C->stab[0], &se_a);
     *logf = q * log(2.0) + C->logtp_const - 0.5 * d + log(alpha);
     if (se_out) *se_out = se_a;
+    if (!(alpha > 0.0)) return pair_null(q, density_only, u_out, elogu_out, eu, euu);
     if (density_only) return 0;
     *u_out = 1.0;
     *elogu_out = 0.0;
@@ -824,6 +846,7 @@ static int pair_core(const comp_t* C, const ora_qmc* qmc, const double* y, int d
     double alpha_s = tk_any(q, b, C->Lambda, nu + p, qmc, C->stab[0], &se_s);
     *logf = q * log(2.0) + logtp + log(alpha_s);
     if (se_out) *se_out = se_s;
+    if (!(alpha_s > 0.0)) return pair_null(q, density_only, u_out, elogu_out, eu, euu);
     if (density_only) return 0;
 
     if (qmc->moments && q >= 3) {

@@ -337,3 +337,52 @@ def test_skew_normal_single_pass_matches_recursion(oracle):
         assert a["logf"] == b["logf"]
         np.testing.assert_allclose(b["eu"], a["eu"], rtol=0, atol=5e-3 * np.abs(a["eu"]).max())
         np.testing.assert_allclose(b["euu"], a["euu"], rtol=0, atol=5e-3 * np.abs(a["euu"]).max())
+
+
+PHI2_TAILS = ((-6.27, 7.12, -0.311), (7.1, -6.3, -0.5), (-8.0, -9.0, 0.6), (-6.0, 6.5, -0.95),
+              (-30.0, -2.5, 0.93), (3.0, -2.6, -0.999), (-4.0, -4.0, 0.999))
+
+
+def test_phi2_far_tails(oracle):
+    """Far-tail values against a 40-digit integral of phi(x) Phi((k - rho x)/sqrt(1 - rho^2))
+    over x <= h: relative 1e-10, including the two lower-tail orientations of the
+    rho = -1 bound and values far below 1e-100."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    for h, k, rho in PHI2_TAILS:
+        H, K, R = mp.mpf(h), mp.mpf(k), mp.mpf(rho)
+        f = lambda x: mp.npdf(x) * mp.ncdf((K - R * x) / mp.sqrt(1 - R * R))
+        # the integrand falls off over ~1/|h| below h: geometric breakpoints toward h
+        pts = [-mp.inf] + [H - mp.mpf(2) ** j for j in range(5, -8, -1)] + [H]
+        ref = float(mp.quad(f, pts))
+        got = oracle.phi2(h, k, rho)
+        assert abs(got - ref) <= 1e-10 * ref, (h, k, rho, got, ref)
+
+
+def test_null_pair_beyond_fp64(oracle):
+    """An observation on the far non-skewed side of a skew-normal component: Phi_q(c)
+    is below the FP64 range (log Phi_2 < -745 by the Mills-ratio bound), so the pair has
+    log f = -inf, tau = 0 and zeroed expectations, and the E-step and M-step stay finite."""
+    Sigma = np.array([[1.0, 0.2], [0.2, 1.0]])
+    Delta = np.array([[3.0, 0.0], [0.0, 3.0]])
+    mu0, mu1 = np.array([0.0, 0.0]), np.array([-60.0, -60.0])
+    y = np.array([-60.0, -60.0])  # 60 units below component 0 on both skewed axes
+    r = oracle.pair(y, mu0, Sigma, Delta, math.inf, _spec(oracle))
+    Om = Sigma + Delta @ Delta.T
+    c = Delta.T @ np.linalg.solve(Om, y - mu0)
+    Lam = np.eye(2) - Delta.T @ np.linalg.solve(Om, Delta)
+    z = c[0] / math.sqrt(Lam[0, 0])
+    # Phi_2(c) <= Phi(z) < phi(z)/|z|
+    assert -0.5 * z * z - math.log(-z) - 0.5 * math.log(2 * math.pi) < -745.0
+    assert r["logf"] == -math.inf and r["u"] == 1.0 and r["elogu"] == 0.0
+    assert np.all(r["eu"] == 0.0) and np.all(r["euu"] == 0.0)
+    rng = np.random.default_rng(4)
+    Y = np.vstack([rng.normal(0, 1, (50, 2)), rng.normal(-60, 1, (50, 2)), y])
+    params = dict(pi=[0.5, 0.5], mu=[mu0, mu1], Sigma=[Sigma, Sigma], Delta=[Delta, Delta],
+                  nu=[math.inf, math.inf])
+    e = oracle.estep(Y, params, _spec(oracle))
+    assert e["logf"][0, -1] == -math.inf and e["tau"][0, -1] == 0.0 and e["tau"][1, -1] == 1.0
+    assert np.isfinite(e["loglik"]) and np.all(np.isfinite(e["eu"])) and np.all(np.isfinite(e["euu"]))
+    P, _ = oracle.mstep(Y, e, params, hold=oracle.HOLD_NU)
+    for key in ("pi", "mu", "Sigma", "Delta"):
+        assert np.all(np.isfinite(P[key])), key
