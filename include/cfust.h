@@ -93,7 +93,14 @@ typedef struct {
                             from Delta^(0) = 0 the fit is the EM of a mixture of multivariate
                             t, the Delta = 0 special case of Sec. 2) and CFUST_HOLD_NU (eq 22
                             skipped); 0 (default): none */
+    int model;           /* CFUST_MODEL_CFUST (0, default): the CFUST mixture of eq (4);
+                            CFUST_MODEL_CFUSN: its nu -> infinity limit, the CFUSN mixture
+                            of eq (5) (density 2^q phi_p(y; mu, Omega) Phi_q(c; 0, Lambda),
+                            u = 1, no nu step: nu is held and stored as +infinity) */
 } cfust_opts;
+
+#define CFUST_MODEL_CFUST 0
+#define CFUST_MODEL_CFUSN 1
 
 #define CFUST_HOLD_DELTA 1
 #define CFUST_HOLD_NU 2

@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "CFUST_OK", 1: "CFUST_EINVAL", 2: "CFUST_ENOTPD", 3: "CFUST_E
 CFUST_PREC_FP64, CFUST_PREC_FP32, CFUST_PREC_MIXED = 0, 1, 2
 CFUST_FIT_NO_FINAL = 1
 CFUST_HOLD_DELTA, CFUST_HOLD_NU = 1, 2
+CFUST_MODEL_CFUST, CFUST_MODEL_CFUSN = 0, 1
 CFUST_F32, CFUST_F64 = 0, 1
 # kernel classes of cfust_profile
 PROF_NAMES = ("setup", "chi_table", "plan", "level0_Tq", "level1_Tq-1", "level2_Tq-2",
@@ -47,7 +48,7 @@ class cfust_opts(C.Structure):
                 ("qmc_korobov_a", C.c_int), ("seed", C.c_uint64), ("nu_min", C.c_double),
                 ("nu_max", C.c_double), ("device", C.c_int), ("cuda_stream", C.c_void_p),
                 ("t2_nodes", C.c_int), ("profile", C.c_int), ("moments", C.c_int),
-                ("hold", C.c_int)]
+                ("hold", C.c_int), ("model", C.c_int)]
 
 
 class cfust_params(C.Structure):

@@ -350,6 +350,9 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
         return fail(nullptr, CFUST_EINVAL, "cfust_create: moments must be 0 or 1");
     if (o.hold & ~(CFUST_HOLD_DELTA | CFUST_HOLD_NU))
         return fail(nullptr, CFUST_EINVAL, "cfust_create: hold must combine CFUST_HOLD_DELTA and CFUST_HOLD_NU");
+    if (o.model != CFUST_MODEL_CFUST && o.model != CFUST_MODEL_CFUSN)
+        return fail(nullptr, CFUST_EINVAL, "cfust_create: model must be CFUST_MODEL_CFUST or CFUST_MODEL_CFUSN");
+    if (o.model == CFUST_MODEL_CFUSN) o.hold |= CFUST_HOLD_NU;  // no nu step in the normal limit
     cudaError_t e = cudaSetDevice(o.device);
     if (e != cudaSuccess)
         return fail(nullptr, CFUST_ECUDA, std::string("cfust_create: cudaSetDevice: ") + cudaGetErrorString(e));
@@ -554,7 +557,7 @@ extern "C" cfust_status cfust_set_params(cfust_ctx* c, const cfust_params* P)
     for (int h = 0; h < g; ++h) {
         if (!(P->pi[h] > 0.0 && P->pi[h] <= 1.0))
             return fail(c, CFUST_EINVAL, "cfust_set_params: pi[" + std::to_string(h) + "] not in (0, 1]");
-        if (!(P->nu[h] >= c->opts.nu_min && P->nu[h] <= c->opts.nu_max))
+        if (c->opts.model != CFUST_MODEL_CFUSN && !(P->nu[h] >= c->opts.nu_min && P->nu[h] <= c->opts.nu_max))
             return fail(c, CFUST_EINVAL, "cfust_set_params: nu[" + std::to_string(h) + "] outside [nu_min, nu_max]");
     }
     for (size_t i = 0; i < (size_t)g * p; ++i)
@@ -568,7 +571,13 @@ extern "C" cfust_status cfust_set_params(cfust_ctx* c, const cfust_params* P)
     CU(cudaMemcpyAsync(c->mu, P->mu, sizeof(double) * g * p, cudaMemcpyHostToDevice, c->st));
     CU(cudaMemcpyAsync(c->Sigma, P->Sigma, sizeof(double) * g * p * p, cudaMemcpyHostToDevice, c->st));
     CU(cudaMemcpyAsync(c->Delta, P->Delta, sizeof(double) * g * p * q, cudaMemcpyHostToDevice, c->st));
-    CU(cudaMemcpyAsync(c->nu, P->nu, sizeof(double) * g, cudaMemcpyHostToDevice, c->st));
+    if (c->opts.model == CFUST_MODEL_CFUSN) {
+        // the normal limit: nu = +infinity selects it in every kernel
+        const std::vector<double> inf(g, INFINITY);
+        CU(cudaMemcpyAsync(c->nu, inf.data(), sizeof(double) * g, cudaMemcpyHostToDevice, c->st));
+    } else {
+        CU(cudaMemcpyAsync(c->nu, P->nu, sizeof(double) * g, cudaMemcpyHostToDevice, c->st));
+    }
     CU(cudaStreamSynchronize(c->st));
     c->have_params = true;
     c->have_stats = false;

@@ -42,7 +42,8 @@ __device__ inline void pair_whiten(const double* F, const Layout& Ly, int p, int
     }
     const double nu = F[Ly.scal + SC_NU];
     *d_out = d;
-    *logtp = F[Ly.scal + SC_LOGTP] - 0.5 * (nu + p) * log1p(d / nu);
+    *logtp = isinf(nu) ? F[Ly.scal + SC_LOGTP] - 0.5 * d  // the normal limit (eq 2)
+                       : F[Ly.scal + SC_LOGTP] - 0.5 * (nu + p) * log1p(d / nu);
 }
 
 // Mixed precision: the same whitening and log t_p in FP32 from FP32 copies of y
@@ -66,7 +67,8 @@ __device__ inline void pair_whiten_f32(const float* F32, const Layout& Ly, int p
     }
     const float nu = F32[Ly.scal + SC_NU];
     *d_out = d;
-    *logtp = F32[Ly.scal + SC_LOGTP] - 0.5f * (nu + p) * log1pf(d / nu);
+    *logtp = isinf(nu) ? F32[Ly.scal + SC_LOGTP] - 0.5f * d
+                       : F32[Ly.scal + SC_LOGTP] - 0.5f * (nu + p) * log1pf(d / nu);
 }
 
 // Limits of the records, in T = double (F the factor block) or, in the mixed
@@ -76,7 +78,7 @@ template <typename T>
 __device__ inline void limits_l0(const T* F, const Layout& Ly, int p, int q, const T* c, T d, int which, T* bt)
 {
     const T nu = F[Ly.scal + SC_NU], nu1 = nu + p;
-    const T f = m_sqrt((nu1 + T(2) * which) / (nu + d));
+    const T f = isinf(nu) ? T(1) : m_sqrt((nu1 + T(2) * which) / (nu + d));  // 1 in the normal limit
     for (int k = 0; k < q; ++k) bt[k] = c[k] * f * F[Ly.dq + k];
 }
 
@@ -86,12 +88,13 @@ __device__ inline T limits_l1(const T* F, const Layout& Ly, int p, int q, const 
 {
     const int q1 = q - 1;
     const T nu = F[Ly.scal + SC_NU], nu1 = nu + p;
-    const T k0 = (nu + d) / nu1;
+    const bool nrm = isinf(nu);  // the normal limit: every t scaling is 1
+    const T k0 = nrm ? T(1) : (nu + d) / nu1;
     const T Srr = k0 * F[Ly.Lam + r * q + r];
     const T* blk = F + Ly.l1 + r * Ly.l1s;
     const T* mvec = blk;
     const T* dsc = blk + q1 + q1 * q1;
-    const T kap1 = (nu1 + c[r] * c[r] / Srr) / (nu1 + T(1));
+    const T kap1 = nrm ? T(1) : (nu1 + c[r] * c[r] / Srr) / (nu1 + T(1));
     const T sc1 = kap1 * k0;
     const T isc = T(1) / m_sqrt(sc1);
     for (int i = 0; i < q1; ++i) {
@@ -106,7 +109,8 @@ __device__ inline void limits_l2(const T* F, const Layout& Ly, int p, int q, con
 {
     const int q1 = q - 1, q2 = q - 2;
     const T nu = F[Ly.scal + SC_NU], nu1 = nu + p, nu2 = nu1 + T(1);
-    const T k0 = (nu + d) / nu1;
+    const bool nrm = isinf(nu);  // the normal limit: every t scaling is 1
+    const T k0 = nrm ? T(1) : (nu + d) / nu1;
     const T Srr = k0 * F[Ly.Lam + r * q + r];
     const T* blk = F + Ly.l1 + r * Ly.l1s;
     const T* mvec = blk;
@@ -116,13 +120,13 @@ __device__ inline void limits_l2(const T* F, const Layout& Ly, int p, int q, con
         const int b = i < r ? i : i + 1;
         cp[i] = c[b] - mvec[i] * c[r];
     }
-    const T sc1 = (nu1 + c[r] * c[r] / Srr) / (nu1 + T(1)) * k0;
-    const T kp = nu2 / (nu2 - T(2)) * sc1;
+    const T sc1 = nrm ? T(1) : (nu1 + c[r] * c[r] / Srr) / (nu1 + T(1)) * k0;
+    const T kp = nrm ? T(1) : nu2 / (nu2 - T(2)) * sc1;
     const T Vss = kp * sch[s * q1 + s];
     const T* b2 = F + Ly.l2 + (r * q1 + s) * Ly.l2s;
     const T* mv2 = b2;
     const T* ds2 = b2 + q2;
-    const T kap2 = (nu2 - T(2) + cp[s] * cp[s] / Vss) / (nu2 - T(1));
+    const T kap2 = nrm ? T(1) : (nu2 - T(2) + cp[s] * cp[s] / Vss) / (nu2 - T(1));
     const T isc2 = T(1) / m_sqrt(kap2 * kp);
     for (int i = 0; i < q2; ++i) {
         const int b = i < s ? i : i + 1;
@@ -143,6 +147,20 @@ __device__ inline int fac_l2(const Layout& Ly, int q, int r, int s)
     return Ly.l2 + (r * q1 + s) * Ly.l2s + 2 * q2;
 }
 
+// A pair whose T_q is 0 in the working precision (beyond the range of the
+// arithmetic on this component's skewing side): log f = -inf, so tau = 0 (eq 12),
+// and the conditional expectations, which enter eqs (18)-(22) only multiplied by
+// tau, are set to u = 1, E[log w] = 0, e2 = 0, e3 = 0 instead of a 0/0.
+__device__ inline void pair_null(int q, int density_only, PairOut& o)
+{
+    o.logf = -INFINITY;
+    if (density_only) return;
+    o.u = 1.0;
+    o.elogu = 0.0;
+    for (int a = 0; a < q; ++a) o.eu[a] = 0.0;
+    for (int a = 0; a < q * q; ++a) o.euu[a] = 0.0;
+}
+
 // tq1[r] = T_{q-1} of level 1 (1 when q = 1); tq2[r*(q-1)+s] = T_{q-2} of
 // level 2 (1 when q <= 2).
 // cst: per-dof constants of this component's dof nu+p (table index 3h)
@@ -152,20 +170,22 @@ __device__ inline void pair_assemble(const double* F, const Layout& Ly, int p, i
                                      int density_only, const double* cst, PairOut& o)
 {
     const double nu = F[Ly.scal + SC_NU], nu1 = nu + p;
+    const bool nrm = isinf(nu);  // the normal limit (eq 5): u = 1, every t scaling is 1
+    if (!(alpha_s > 0.0)) return pair_null(q, density_only, o);
     o.logf = q * 0.6931471805599453 + logtp + log(alpha_s);  // eq (4)
     if (density_only) return;
-    const double u = nu1 / (nu + d) * alpha / alpha_s;        // eq (13)
+    const double u = nrm ? 1.0 : nu1 / (nu + d) * alpha / alpha_s;  // eq (13)
     o.u = u;
-    o.elogu = u - log(0.5 * (nu + d)) - nu1 / (nu + d) + F[Ly.scal + SC_PSI];  // eq (15)
+    o.elogu = nrm ? 0.0 : u - log(0.5 * (nu + d)) - nu1 / (nu + d) + F[Ly.scal + SC_PSI];  // eq (15)
     const double* Lam = F + Ly.Lam;
-    const double k0 = (nu + d) / nu1;
+    const double k0 = nrm ? 1.0 : (nu + d) / nu1;
     const int q1 = q - 1;
     double xi[CF_MAXQ], H[CF_MAXQ * CF_MAXQ];
     for (int i = 0; i < q * q; ++i) H[i] = 0.0;
     for (int r = 0; r < q; ++r) {
         const double Srr = k0 * Lam[r * q + r];
         const double t1q = q1 > 0 ? tq1[r] : 1.0;
-        xi[r] = exp(cf_logt1(c[r], Srr, nu1, cst[CST_LT1])) * t1q;
+        xi[r] = exp(nrm ? cf_lognorm1(c[r], Srr) : cf_logt1(c[r], Srr, nu1, cst[CST_LT1])) * t1q;
         H[r * q + r] = c[r] * xi[r];
         if (q1 == 0 || xi[r] == 0.0) continue;
         const double* blk = F + Ly.l1 + r * Ly.l1s;
@@ -177,21 +197,22 @@ __device__ inline void pair_assemble(const double* F, const Layout& Ly, int p, i
             cp[i] = c[b] - mvec[i] * c[r];
         }
         const double nu2 = nu1 + 1.0;
-        const double sc1 = (nu1 + c[r] * c[r] / Srr) / (nu1 + 1.0) * k0;
-        const double kp = nu2 / (nu2 - 2.0) * sc1;
+        const double sc1 = nrm ? 1.0 : (nu1 + c[r] * c[r] / Srr) / (nu1 + 1.0) * k0;
+        const double kp = nrm ? 1.0 : nu2 / (nu2 - 2.0) * sc1;
         double xip[CF_MAXQ];
         for (int s = 0; s < q1; ++s) {
             const double Vss = kp * sch[s * q1 + s];
             const double t2q = q1 > 1 ? tq2[r * q1 + s] : 1.0;
-            xip[s] = exp(cf_logt1(cp[s], Vss, nu2 - 2.0, cst[CST_LT1M])) * t2q;
+            xip[s] = exp(nrm ? cf_lognorm1(cp[s], Vss) : cf_logt1(cp[s], Vss, nu2 - 2.0, cst[CST_LT1M])) * t2q;
         }
-        // E[Y 1(Y <= c')] = -(nu2/(nu2-2)) V_r xi', V_r = sc1 schur_r
-        const double fac = -(nu2 / (nu2 - 2.0)) * sc1 / t1q;
+        // E[Y 1(Y <= c')] = -(nu2/(nu2-2)) V_r xi', V_r = sc1 schur_r (-V_r xi' when normal)
+        // divided last: t1q may be subnormal while s / t1q (a Mills-type ratio) is moderate
+        const double fac = nrm ? -1.0 : -(nu2 / (nu2 - 2.0)) * sc1;
         for (int i = 0; i < q1; ++i) {
             double s = 0.0;
             for (int t = 0; t < q1; ++t) s += sch[i * q1 + t] * xip[t];
             const int b = i < r ? i : i + 1;
-            H[r * q + b] = xi[r] * (mvec[i] * c[r] + fac * s);
+            H[r * q + b] = xi[r] * (mvec[i] * c[r] + fac * s / t1q);
         }
     }
     double Lxi[CF_MAXQ];
@@ -224,11 +245,13 @@ __device__ inline void pair_assemble_sp(const double* F, const Layout& Ly, int p
                                         double alpha, const double* m, PairOut& o)
 {
     const double nu = F[Ly.scal + SC_NU], nu1 = nu + p;
+    const bool nrm = isinf(nu);  // the normal limit (eq 5): u = 1, X ~ N(0, Lambda)
+    if (!(alpha_s > 0.0)) return pair_null(q, 0, o);
     o.logf = q * 0.6931471805599453 + logtp + log(alpha_s);  // eq (4)
-    const double u = nu1 / (nu + d) * alpha / alpha_s;        // eq (13)
+    const double u = nrm ? 1.0 : nu1 / (nu + d) * alpha / alpha_s;  // eq (13)
     o.u = u;
-    o.elogu = u - log(0.5 * (nu + d)) - nu1 / (nu + d) + F[Ly.scal + SC_PSI];  // eq (15)
-    const double sc = sqrt((nu + d) / (nu1 + 2.0));
+    o.elogu = nrm ? 0.0 : u - log(0.5 * (nu + d)) - nu1 / (nu + d) + F[Ly.scal + SC_PSI];  // eq (15)
+    const double sc = nrm ? 1.0 : sqrt((nu + d) / (nu1 + 2.0));
     double sig[CF_MAXQ], m1[CF_MAXQ];
     for (int a = 0; a < q; ++a) {
         sig[a] = sc / F[Ly.dq + a];
@@ -252,17 +275,19 @@ __device__ inline void pair_assemble_f32(const double* F, const Layout& Ly, int 
                                          int density_only, const double* cst, PairOut& o)
 {
     const float alpha_s = (float)alpha_s_d;
+    if (!(alpha_s > 0.0f)) return pair_null(q, density_only, o);
     o.logf = q * 0.6931471805599453 + logtp + (double)logf(alpha_s);  // eq (4)
     if (density_only) return;
     const float nu = (float)F[Ly.scal + SC_NU], nu1 = nu + (float)p, d = (float)dd;
     float c[CF_MAXQ];
     for (int k = 0; k < q; ++k) c[k] = (float)cd[k];
-    const float u = nu1 / (nu + d) * (float)alpha_d / alpha_s;  // eq (13)
+    const bool nrm = isinf(nu);  // the normal limit (eq 5): u = 1, every t scaling is 1
+    const float u = nrm ? 1.0f : nu1 / (nu + d) * (float)alpha_d / alpha_s;  // eq (13)
     o.u = u;
-    o.elogu = u - logf(0.5f * (nu + d)) - nu1 / (nu + d) + (float)F[Ly.scal + SC_PSI];  // eq (15)
+    o.elogu = nrm ? 0.0f : u - logf(0.5f * (nu + d)) - nu1 / (nu + d) + (float)F[Ly.scal + SC_PSI];  // eq (15)
     float Lam[CF_MAXQ * CF_MAXQ];
     for (int i = 0; i < q * q; ++i) Lam[i] = (float)F[Ly.Lam + i];
-    const float k0 = (nu + d) / nu1;
+    const float k0 = nrm ? 1.0f : (nu + d) / nu1;
     const float lt1 = (float)cst[CST_LT1], lt1m = (float)cst[CST_LT1M];
     const int q1 = q - 1;
     float xi[CF_MAXQ], H[CF_MAXQ * CF_MAXQ];
@@ -270,7 +295,8 @@ __device__ inline void pair_assemble_f32(const double* F, const Layout& Ly, int 
     for (int r = 0; r < q; ++r) {
         const float Srr = k0 * Lam[r * q + r];
         const float t1q = q1 > 0 ? (float)tq1[r] : 1.0f;
-        xi[r] = expf(lt1 - 0.5f * logf(Srr) - 0.5f * (nu1 + 1.0f) * log1pf(c[r] * c[r] / (nu1 * Srr))) * t1q;
+        xi[r] = expf(nrm ? -0.5f * logf(2.0f * (float)CF_PI * Srr) - 0.5f * c[r] * c[r] / Srr
+                         : lt1 - 0.5f * logf(Srr) - 0.5f * (nu1 + 1.0f) * log1pf(c[r] * c[r] / (nu1 * Srr))) * t1q;
         H[r * q + r] = c[r] * xi[r];
         if (q1 == 0 || xi[r] == 0.0f) continue;
         const double* blk = F + Ly.l1 + r * Ly.l1s;
@@ -282,21 +308,22 @@ __device__ inline void pair_assemble_f32(const double* F, const Layout& Ly, int 
             cp[i] = c[b] - mvec[i] * c[r];
         }
         const float nu2 = nu1 + 1.0f;
-        const float sc1 = (nu1 + c[r] * c[r] / Srr) / (nu1 + 1.0f) * k0;
-        const float kp = nu2 / (nu2 - 2.0f) * sc1;
+        const float sc1 = nrm ? 1.0f : (nu1 + c[r] * c[r] / Srr) / (nu1 + 1.0f) * k0;
+        const float kp = nrm ? 1.0f : nu2 / (nu2 - 2.0f) * sc1;
         float xip[CF_MAXQ];
         for (int s = 0; s < q1; ++s) {
             const float Vss = kp * sch[s * q1 + s];
             const float t2q = q1 > 1 ? (float)tq2[r * q1 + s] : 1.0f;
             const float nuv = nu2 - 2.0f;
-            xip[s] = expf(lt1m - 0.5f * logf(Vss) - 0.5f * (nuv + 1.0f) * log1pf(cp[s] * cp[s] / (nuv * Vss))) * t2q;
+            xip[s] = expf(nrm ? -0.5f * logf(2.0f * (float)CF_PI * Vss) - 0.5f * cp[s] * cp[s] / Vss
+                              : lt1m - 0.5f * logf(Vss) - 0.5f * (nuv + 1.0f) * log1pf(cp[s] * cp[s] / (nuv * Vss))) * t2q;
         }
-        const float fac = -(nu2 / (nu2 - 2.0f)) * sc1 / t1q;
+        const float fac = nrm ? -1.0f : -(nu2 / (nu2 - 2.0f)) * sc1;  // divided last, as above
         for (int i = 0; i < q1; ++i) {
             float s = 0.0f;
             for (int t = 0; t < q1; ++t) s += sch[i * q1 + t] * xip[t];
             const int b = i < r ? i : i + 1;
-            H[r * q + b] = xi[r] * (mvec[i] * c[r] + fac * s);
+            H[r * q + b] = xi[r] * (mvec[i] * c[r] + fac * s / t1q);
         }
     }
     float Lxi[CF_MAXQ];

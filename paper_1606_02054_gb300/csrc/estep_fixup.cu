@@ -13,9 +13,11 @@ __device__ double tk_fp64(int k, const double* bt, const double* Lc, double nu, 
     if (se) *se = 0.0;
     switch (k) {
     case 0: return 1.0;
-    case 1: return t1cdf_dev<double>(bt[0], nu, t1_lgb(nu));
+    case 1: return isinf(nu) ? normcdf(bt[0]) : t1cdf_dev<double>(bt[0], nu, t1_lgb(nu));
     case 2: {
         const double rho = Lc[2];
+        if (isinf(nu))
+            return phi2_warp<double>(bt[0], bt[1], rho, a.t2n, a.glx64, a.glw64, lane);
         return t2cdf_warp<double>(bt[0], bt[1], rho, nu, (1.0 - rho) * (1.0 + rho),
                                   bt[0] * (rho > 0.0 ? rho : -rho) - (rho > 0.0 ? bt[1] : -bt[1]),
                                   t1_lgb(nu), t1_lgb(nu + 1.0),
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(128) fixup_kernel(EstepArgs a, const int* coun
             if (lane == 0) {
                 a.logf[pid] = o.logf;
                 if (a.se) a.se[pid] = se;
-                if (!isfinite(o.logf)) atomicOr(a.flags, KF_NAN);
+                if (!(o.logf < INFINITY)) atomicOr(a.flags, KF_NAN);  // NaN or +inf; -inf is a null pair
                 a.u[pid] = o.u;
                 a.elogu[pid] = o.elogu;
                 for (int k = 0; k < q; ++k) a.eu[pid * q + k] = o.eu[k];
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(128) fixup_kernel(EstepArgs a, const int* coun
         if (lane == 0) {
             a.logf[pid] = o.logf;
             if (a.se) a.se[pid] = se;
-            if (!isfinite(o.logf)) atomicOr(a.flags, KF_NAN);
+            if (!(o.logf < INFINITY)) atomicOr(a.flags, KF_NAN);  // NaN or +inf; -inf is a null pair
             if (!a.density_only) {
                 a.u[pid] = o.u;
                 a.elogu[pid] = o.elogu;

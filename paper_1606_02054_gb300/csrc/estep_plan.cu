@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(128) combine_kernel(CombineArgs a)
         }
         a.logf[pid] = o.logf;
         if (a.se) a.se[pid] = se;
-        if (!isfinite(o.logf)) atomicOr(a.flags, KF_NAN);
+        if (!(o.logf < INFINITY)) atomicOr(a.flags, KF_NAN);  // NaN or +inf; -inf is a null pair
         if (a.density_only) continue;
         a.u[pid] = o.u;
         a.elogu[pid] = o.elogu;
@@ -209,7 +209,9 @@ __global__ void __launch_bounds__(128) t1_records_kernel(RecSet r, IntegArgs a)
     const R* cst = sizeof(R) == sizeof(float) ? (const R*)a.cst32 : (const R*)a.cst64;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < r.nrec;
          i += (long long)gridDim.x * blockDim.x) {
-        r.res[i] = (double)t1cdf_dev<R>((R)r.bt[i], (R)r.dof[i], cst[r.tab[i] * CST_STRIDE + CST_LGB]);
+        const R dof = (R)r.dof[i];  // infinite: the normal limit, Phi
+        r.res[i] = isinf(dof) ? (double)m_ncdf((R)r.bt[i])
+                              : (double)t1cdf_dev<R>((R)r.bt[i], dof, cst[r.tab[i] * CST_STRIDE + CST_LGB]);
         if (r.se) r.se[i] = 0.0;
     }
 }

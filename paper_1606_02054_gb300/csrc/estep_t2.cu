@@ -27,7 +27,8 @@ __global__ void __launch_bounds__(256) t2_records_kernel(RecSet r, IntegArgs a)
             cr = (R)(h64 * (rho64 > 0.0 ? rho64 : -rho64) - (rho64 > 0.0 ? k64 : -k64));
         }
         const float2* tab = f32 && a.t1tab ? a.t1tab + (size_t)r.tab[i] * T1TAB_N : nullptr;
-        const double v = t2cdf_warp<R>(h, k, rho, nu, omr2, cr, c[CST_LGB], c[CST_LGB1], c[CST_C2], a.t2n,
+        const double v = isinf(nu) ? phi2_warp<R>(h, k, rho, a.t2n, glx, glw, lane)
+                                   : t2cdf_warp<R>(h, k, rho, nu, omr2, cr, c[CST_LGB], c[CST_LGB1], c[CST_C2], a.t2n,
                                        glx, glw, f32 ? T2_NH : a.t2n,
                                        f32 ? (const R*)a.glx32h : glx, f32 ? (const R*)a.glw32h : glw,
                                        lane, tab);

@@ -141,9 +141,14 @@ __global__ void setup_components_kernel(Dims D, Layout Ly, const double* mu, con
         }
     const double v = nu[h];
     Fh[Ly.scal + SC_NU] = v;
-    Fh[Ly.scal + SC_LOGTP] = lgamma(0.5 * (v + p)) - lgamma(0.5 * v) - 0.5 * p * log(v * CF_PI)
-                           - 0.5 * logdet;
-    Fh[Ly.scal + SC_PSI] = cf_digamma(0.5 * (v + p));
+    if (isinf(v)) {  // nu = infinity: the normal density of eq (2) (CFUSN, eq 5); no eq (15)
+        Fh[Ly.scal + SC_LOGTP] = -0.5 * p * log(2.0 * CF_PI) - 0.5 * logdet;
+        Fh[Ly.scal + SC_PSI] = 0.0;
+    } else {
+        Fh[Ly.scal + SC_LOGTP] = lgamma(0.5 * (v + p)) - lgamma(0.5 * v) - 0.5 * p * log(v * CF_PI)
+                               - 0.5 * logdet;
+        Fh[Ly.scal + SC_PSI] = cf_digamma(0.5 * (v + p));
+    }
     Fh[Ly.scal + 3] = 0.0;
     if (!corr_chol_dev(q, Lam, Fh + Ly.dq, Fh + Ly.Lq)) { atomicOr(flags, KF_NOTPD_LAMBDA); return; }
     // level 1: Schur complement of Lambda at each r
@@ -188,7 +193,8 @@ __global__ void chi_table_kernel(int ndof, const double* __restrict__ dofs, cons
         if (x >= 1.0) x -= 1.0;
         const double wc = fabs(2.0 * x - 1.0);
         const double w = 1.0 - wc;
-        const double s = sqrt(cf_chi2_quantile(w, wc, dof, cst[k * CST_STRIDE + CST_LGA], rtol) / dof);
+        // dof = infinity (the normal limit): no chi variable, s = 1
+        const double s = isinf(dof) ? 1.0 : sqrt(cf_chi2_quantile(w, wc, dof, cst[k * CST_STRIDE + CST_LGA], rtol) / dof);
         t64[t] = s;
         t32[t] = (float)s;
     }
@@ -209,6 +215,13 @@ __global__ void dof_consts_kernel(Dims D, Layout Ly, const double* __restrict__ 
             dofs[t] = v;
         } else {
             v = dofs[t];
+        }
+        if (isinf(v)) {  // the normal limit uses none of these constants
+            for (int k = 0; k < CST_STRIDE; ++k) {
+                c64[t * CST_STRIDE + k] = 0.0;
+                c32[t * CST_STRIDE + k] = 0.0f;
+            }
+            continue;
         }
         const double lt = lgamma(0.5 * (v + 1.0)) - lgamma(0.5 * v) - 0.5 * log(v * CF_PI);
         const double ltm = lgamma(0.5 * v) - lgamma(0.5 * (v - 1.0)) - 0.5 * log((v - 1.0) * CF_PI);
@@ -267,6 +280,10 @@ __global__ void t1_table_kernel(int ndof, const double* __restrict__ dofs, float
          e += (long long)gridDim.x * blockDim.x) {
         const int t = (int)(e / T1TAB_N), i = (int)(e % T1TAB_N);
         const double nu = dofs[t] + 1.0;
+        if (isinf(nu)) {  // the normal limit evaluates Phi_2 directly, not through this table
+            tab[e] = make_float2(0.0f, 0.0f);
+            continue;
+        }
         const double v = i * hv;
         const double w = sinh(v * CF_LN2);
         const double lT = log_t1_lower(w, nu);

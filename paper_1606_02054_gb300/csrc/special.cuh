@@ -213,6 +213,12 @@ __device__ inline double cf_trigamma(double x)
 
 // log of the univariate t density at x with scale^2 v and dof nu (FP64);
 // lc = lgamma((nu+1)/2) - lgamma(nu/2) - log(nu pi)/2
+// log of the N(0, v) density at x (the nu -> infinity limit of cf_logt1)
+__device__ inline double cf_lognorm1(double x, double v)
+{
+    return -0.5 * log(2.0 * CF_PI * v) - 0.5 * x * x / v;
+}
+
 __device__ inline double cf_logt1(double x, double v, double nu, double lc)
 {
     return lc - 0.5 * log(v) - 0.5 * (nu + 1.0) * log1p(x * x / (nu * v));
@@ -399,6 +405,67 @@ __device__ double t2cdf_warp(R h, R k, R rho, R nu, R omr2, R cr, R lgb, R lgb1,
     }
     acc = warp_sum(acc);
     return (double)(C2 * acc);
+}
+
+// ---------------------------------------------------------------------------
+// Phi_2(h, k; rho), the nu -> infinity limit of T_2 (the CFUSN model of eq 5),
+// warp-cooperative.  With e(theta) = exp(-(h^2 - 2 h k sin theta + k^2) / (2 cos^2 theta)),
+// which is positive (Sheppard's integral, r = sin theta):
+//   rho >= 0:  Phi(h) Phi(k) + (1/2pi) int_0^{asin rho} e,
+//   rho < 0:   P(-k < X <= h) + (1/2pi) int_{-pi/2}^{asin rho} e   (Phi_2 at rho = -1 plus
+//              the rest),
+// so small values are never differences of large ones.  In the tails e is concentrated
+// at one end of the interval, and for rho < 0 it rises over a width ~|h + k| at -pi/2:
+// the interval is split in halves, each with n nodes graded (t^3) toward its own end.
+// P(-k < X <= h) by 4-point Gauss-Legendre where the interval is narrow against the
+// Gaussian's scale there, else as a difference of Phi values in the lower tail.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ double phi2_warp(R h, R k, R rho, int n, const R* __restrict__ glx, const R* __restrict__ glw,
+                            int lane)
+{
+    if (rho >= R(1)) return (double)m_ncdf(h < k ? h : k);
+    const R hk = h + k;
+    R lower = R(0);
+    if (hk > R(0)) {
+        const R mid = R(0.5) * (h - k), half = R(0.5) * hk;  // the interval (-k, h]
+        if (hk * (R(1) + fabs(mid)) < R(0.5)) {
+            // narrow against the Gaussian's scale there: 4-point Gauss-Legendre
+            const R x4[2] = {R(0.8611363115940526), R(0.3399810435848563)};
+            const R w4[2] = {R(0.3478548451374538), R(0.6521451548625461)};
+            R s4 = R(0);
+            for (int i = 0; i < 2; ++i) {
+                const R xa = mid + half * x4[i], xb = mid - half * x4[i];
+                s4 += w4[i] * (m_exp(R(-0.5) * xa * xa) + m_exp(R(-0.5) * xb * xb));
+            }
+            lower = s4 * half * R(0.3989422804014327);  // 1/sqrt(2 pi)
+        } else {
+            // P(-k < X <= h) = P(-h <= X < k): the form whose endpoints are nearer the lower
+            // tail, where Phi keeps its relative precision; outside the Gauss-Legendre range
+            // the smaller term is at most about 2/3 of the larger, so at most a few ulps go
+            lower = mid < R(0) ? m_ncdf(h) - m_ncdf(-k) : m_ncdf(k) - m_ncdf(-h);
+        }
+    }
+    if (rho <= R(-1)) return (double)lower;
+    const bool neg = rho < R(0);
+    const R b = asin(rho);
+    const R a = neg ? R(-0.5 * CF_PI) : R(0);
+    const R hL = R(0.5) * (b - a);
+    R acc = R(0);
+    for (int t = lane; t < 2 * n; t += CF_WARP) {
+        const bool top = t >= n;  // second half: anchored at b, running down
+        const R u = glx[top ? t - n : t];
+        const R th = top ? b - hL * u * u * u : a + hL * u * u * u;
+        R sn;
+        if constexpr (sizeof(R) == sizeof(float)) sn = cf_sin_pi(th);
+        else sn = sin(th);
+        const R c2 = (R(1) - sn) * (R(1) + sn);
+        const R e = c2 > R(0) ? m_exp(-(h * h - R(2) * h * k * sn + k * k) / (R(2) * c2)) : R(0);
+        acc += glw[top ? t - n : t] * R(3) * u * u * e;
+    }
+    acc = warp_sum(acc);
+    const R base = neg ? lower : m_ncdf(h) * m_ncdf(k);
+    return (double)(base + acc * hL * R(0.15915494309189535));  // 1/(2 pi)
 }
 
 // ---------------------------------------------------------------------------
