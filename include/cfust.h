@@ -152,7 +152,8 @@ cfust_status cfust_set_data(cfust_ctx* ctx, const void* y, int dtype, int64_t ld
 
 /* Copy Psi = (pi, mu, Sigma, Delta, nu) in (Sec. 2, eq (1)).  Returns
  * CFUST_EINVAL if a pi is not in (0, 1], a nu not in [nu_min, nu_max], or a
- * non-finite value is present. */
+ * non-finite value is present (under CFUST_MODEL_CFUSN nu is not read and is
+ * set to +inf). */
 cfust_status cfust_set_params(cfust_ctx* ctx, const cfust_params* params);
 
 /* Copy the current Psi out into caller buffers. */
@@ -162,7 +163,10 @@ cfust_status cfust_get_params(cfust_ctx* ctx, cfust_params* out);
  * the tau-weighted sufficient statistics of eqs (18)-(22).  *loglik_out
  * (may be NULL) receives l(Psi^(k)) of eq (27), computed from the same
  * density pass (Sec. 4.3).  The statistics stay on the device for
- * cfust_mstep. */
+ * cfust_mstep.  A pair whose T_q is 0 in the working precision is null:
+ * log f = -inf, tau = 0, u = 1, E log w = 0, e2 = e3 = 0.  CFUST_ENAN when a
+ * density or statistic is NaN or +inf, or l is not finite (an observation
+ * whose every pair is null). */
 cfust_status cfust_estep(cfust_ctx* ctx, double* loglik_out);
 
 /* Copy the per-pair E-step arrays of the last cfust_estep to host buffers
@@ -308,6 +312,91 @@ cfust_status cfust_debug_read(cfust_ctx* ctx, int what, void* dst, int64_t bytes
  * may be NULL).  Requires opts.profile = 1 (else CFUST_ESTATE).  reset = 1
  * zeroes the totals after reading. */
 cfust_status cfust_profile(cfust_ctx* ctx, double* ms, int64_t* launches, int reset);
+
+/* ------------------------------------------------------------------------
+ * Learned surrogate (not part of the paper).  A 3 x 256 tanh MLP with BF16
+ * operands and FP32 accumulation maps one integral record of the
+ * single-pass E-step -- features (b_1..b_q standardised limits, the
+ * correlations R_ij, i > j, of Lambda in row-major order, 1/dof) -- to
+ * log T_q (eq 4 at dof nu+p, eq 13 at nu+p+2) and the standardised
+ * truncated moments of eqs (16)-(17) (E[X], then the lower triangle of
+ * E[X X^T] row-major).  Features are standardised by training-set means
+ * and deviations (stats: fmean, fstd, zlo, zhi [48 each], tmean, tstd
+ * [48 each]); a record whose standardised feature leaves the training
+ * range [zlo, zhi] widened by margin (in standard deviations) is left to
+ * the lattice.
+ * Parameter vector (CFUST_MLP_NPARAM floats): W1 [48 x 256], b1, W2
+ * [256 x 256], b2, W3 [256 x 256], b3, W4 [256 x 48], b4, matrices
+ * row-major with the input index first; inputs and outputs zero-padded to
+ * 48.
+ * ------------------------------------------------------------------------ */
+#define CFUST_MLP_IN 48
+#define CFUST_MLP_H 256
+#define CFUST_MLP_OUT 48
+#define CFUST_MLP_NPARAM 156464
+#define CFUST_MLP_NSTAT 288
+
+/* Device initialisation of a parameter vector: W ~ U(-1/sqrt(fan_in),
+ * 1/sqrt(fan_in)) on the used rows of W1 (nin) and columns of W4 (nout),
+ * element e drawn by SplitMix64 at key seed ^ (e + 1); padding and biases 0.
+ * theta_out: host, CFUST_MLP_NPARAM floats. */
+cfust_status cfust_mlp_init(uint64_t seed, int nin, int nout, float* theta_out, int device);
+
+/* Forward and backward pass over rows x 48 standardised features f (host,
+ * FP32; rounded to BF16 as the network's input), targets t and masks m (rows
+ * x 48): loss = sum m (y - t)^2 / (2 rows nout).  grad_out (NPARAM), y_out
+ * (rows x 48) and loss_out may be NULL.  rows <= 2^22.  Host buffers. */
+cfust_status cfust_mlp_grad(const float* theta, int64_t rows, int nout, const float* f, const float* t,
+                            const float* m, float* grad_out, float* y_out, double* loss_out, int device);
+
+/* One Adam step (Kingma & Ba; beta1 0.9, beta2 0.999, eps 1e-8, step >= 1
+ * counts this step) on host vectors theta, m, v (updated in place). */
+cfust_status cfust_mlp_adam(float* theta, const float* grad, float* m, float* v, int64_t step, float lr,
+                            int device);
+
+/* The fused inference kernel on records given on the host: bt (rows x q),
+ * Lc (rows x q x q, lower Cholesky factors of correlation matrices,
+ * row-major), dof (rows).  logT (rows) and mom (rows x (q + q(q+1)/2), may be
+ * NULL) receive the network's outputs for in-range records; inbox[i] = 0 (and
+ * logT NaN) for a record outside the training range.  3 <= q <= 8. */
+cfust_status cfust_mlp_records(const float* theta, const float* stats, float margin, int q, int64_t rows,
+                               const double* bt, const double* Lc, const double* dof, double* logT,
+                               double* mom, int* inbox, int device);
+
+typedef struct {
+    int epochs;                /* passes over samples_per_epoch samples (default 48) */
+    int batch;                 /* minibatch rows (default 8192) */
+    int64_t samples_per_epoch; /* at most (default 2^20); <= 0: every collected sample */
+    float lr;                  /* Adam step size (default 3e-3) */
+    float margin;              /* training-range margin in standard deviations (default 0.5) */
+    uint64_t seed;             /* initial weights and shuffles */
+} cfust_surrogate_opts;
+
+cfust_surrogate_opts cfust_surrogate_default_opts(void);
+
+/* Train the surrogate on the records of one lattice E-step at the current
+ * Psi: runs cfust_estep with the lattice (its statistics and *loglik_out
+ * stand, so cfust_mstep may follow), collects every record with T > 1e-300
+ * (level 0 at dof nu+p: log T only; moment records at nu+p+2: log T and
+ * moments), standardises, and trains.  The first call initialises the
+ * weights and fixes the standardisation; later calls (at later iterates of a
+ * fit) continue from the current weights and only widen the training range.  Then switches the surrogate on.  Requires
+ * single-pass moments (moments = 1, q >= 3).  losses (opts.epochs entries,
+ * may be NULL) receive each epoch's last minibatch loss. */
+cfust_status cfust_surrogate_train(cfust_ctx* ctx, const cfust_surrogate_opts* opts, double* loglik_out,
+                                   double* losses);
+
+/* on = 1: E-steps and cfust_loglik take level-0 and moment records from the
+ * network (out-of-range records from the lattice); 0: the lattice only. */
+cfust_status cfust_surrogate_use(cfust_ctx* ctx, int on);
+
+/* Records evaluated and records left to the lattice by the last E-step's
+ * surrogate pass (both sets). */
+cfust_status cfust_surrogate_info(cfust_ctx* ctx, int64_t* records, int64_t* fallbacks);
+
+/* Copy the trained parameters (NPARAM floats) and statistics (NSTAT floats)
+ * out (either may be NULL). */
+cfust_status cfust_surrogate_params(cfust_ctx* ctx, float* theta, float* stats);
 
 #ifdef __cplusplus
 }

@@ -31,6 +31,7 @@ CFUST_FIT_NO_FINAL = 1
 CFUST_HOLD_DELTA, CFUST_HOLD_NU = 1, 2
 CFUST_MODEL_CFUST, CFUST_MODEL_CFUSN = 0, 1
 CFUST_F32, CFUST_F64 = 0, 1
+CFUST_MLP_IN, CFUST_MLP_H, CFUST_MLP_OUT, CFUST_MLP_NPARAM, CFUST_MLP_NSTAT = 48, 256, 48, 156464, 288
 # kernel classes of cfust_profile
 PROF_NAMES = ("setup", "chi_table", "plan", "level0_Tq", "level1_Tq-1", "level2_Tq-2",
               "moments_Tq", "combine", "fixup_fp64", "reduce", "mstep")
@@ -41,6 +42,11 @@ class CfustError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
         self.status = status
+
+
+class cfust_surrogate_opts(C.Structure):
+    _fields_ = [("epochs", C.c_int), ("batch", C.c_int), ("samples_per_epoch", C.c_int64),
+                ("lr", C.c_float), ("margin", C.c_float), ("seed", C.c_uint64)]
 
 
 class cfust_opts(C.Structure):
@@ -102,6 +108,21 @@ def lib():
             L.cfust_debug_read.restype = i
             L.cfust_reduce_stats_noalloc.argtypes = [i, i, i, i64] + [vp] * 11
             L.cfust_reduce_stats_noalloc.restype = i
+            f32p = C.POINTER(C.c_float)
+            L.cfust_mlp_init.argtypes = [C.c_uint64, i, i, vp, i]
+            L.cfust_mlp_grad.argtypes = [vp, i64, i, vp, vp, vp, vp, vp, _dp, i]
+            L.cfust_mlp_adam.argtypes = [vp, vp, vp, vp, i64, C.c_float, i]
+            L.cfust_mlp_records.argtypes = [vp, vp, C.c_float, i, i64, vp, vp, vp, vp, vp, vp, i]
+            L.cfust_surrogate_default_opts.argtypes = []
+            L.cfust_surrogate_default_opts.restype = cfust_surrogate_opts
+            L.cfust_surrogate_train.argtypes = [vp, C.POINTER(cfust_surrogate_opts), _dp, _dp]
+            L.cfust_surrogate_use.argtypes = [vp, i]
+            L.cfust_surrogate_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+            L.cfust_surrogate_params.argtypes = [vp, f32p, f32p]
+            for name in ("cfust_mlp_init", "cfust_mlp_grad", "cfust_mlp_adam", "cfust_mlp_records",
+                         "cfust_surrogate_train", "cfust_surrogate_use", "cfust_surrogate_info",
+                         "cfust_surrogate_params"):
+                getattr(L, name).restype = i
             for name in ("cfust_create", "cfust_destroy", "cfust_set_data", "cfust_set_params",
                          "cfust_get_params", "cfust_estep", "cfust_get_pairs", "cfust_get_stats",
                          "cfust_mstep", "cfust_loglik", "cfust_fit", "cfust_tk_eval"):
@@ -290,6 +311,88 @@ def cfust_special_f32(fn, x, device=0):
     y = np.empty_like(x)
     _check(lib().cfust_special_f32(int(fn), x.size, x.ctypes.data, y.ctypes.data, int(device)))
     return y
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def cfust_mlp_init(seed, nin, nout, device=0):
+    th = np.empty(CFUST_MLP_NPARAM, dtype=np.float32)
+    _check(lib().cfust_mlp_init(int(seed) & 0xFFFFFFFFFFFFFFFF, int(nin), int(nout), th.ctypes.data, int(device)))
+    return th
+
+
+def cfust_mlp_grad(theta, f, t, m, nout, device=0):
+    """Returns (grad, y, loss) of the masked loss over rows of standardised features."""
+    theta, f, t, m = _f32(theta), _f32(f), _f32(t), _f32(m)
+    rows = f.shape[0]
+    g = np.empty(CFUST_MLP_NPARAM, dtype=np.float32)
+    y = np.empty((rows, CFUST_MLP_OUT), dtype=np.float32)
+    loss = C.c_double(0.0)
+    _check(lib().cfust_mlp_grad(theta.ctypes.data, rows, int(nout), f.ctypes.data, t.ctypes.data, m.ctypes.data,
+                                g.ctypes.data, y.ctypes.data, C.byref(loss), int(device)))
+    return g, y, loss.value
+
+
+def cfust_mlp_adam(theta, grad, m, v, step, lr, device=0):
+    """One Adam step; returns new (theta, m, v)."""
+    theta, m, v = _f32(theta).copy(), _f32(m).copy(), _f32(v).copy()
+    grad = _f32(grad)
+    _check(lib().cfust_mlp_adam(theta.ctypes.data, grad.ctypes.data, m.ctypes.data, v.ctypes.data, int(step),
+                                float(lr), int(device)))
+    return theta, m, v
+
+
+def cfust_mlp_records(theta, stats, margin, bt, Lc, dof, device=0):
+    """The fused inference kernel on records: returns (logT, mom, inbox)."""
+    theta, stats = _f32(theta), _f32(stats)
+    bt = _f64(bt)
+    rows, q = bt.shape
+    Lc = _f64(Lc).reshape(rows, q, q)
+    dof = _f64(dof).reshape(rows)
+    W = q + q * (q + 1) // 2
+    logT = np.empty(rows)
+    mom = np.empty((rows, W))
+    inbox = np.empty(rows, dtype=np.int32)
+    _check(lib().cfust_mlp_records(theta.ctypes.data, stats.ctypes.data, float(margin), int(q), rows,
+                                   bt.ctypes.data, Lc.ctypes.data, dof.ctypes.data, logT.ctypes.data,
+                                   mom.ctypes.data, inbox.ctypes.data, int(device)))
+    return logT, mom, inbox
+
+
+def cfust_surrogate_default_opts(**kw):
+    o = lib().cfust_surrogate_default_opts()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def cfust_surrogate_train(ctx: Context, opts=None, **kw):
+    """Returns (loglik of the lattice E-step, per-epoch losses)."""
+    o = opts if opts is not None else cfust_surrogate_default_opts(**kw)
+    ll = C.c_double(0.0)
+    losses = np.zeros(max(o.epochs, 1))
+    _check(lib().cfust_surrogate_train(ctx.handle, C.byref(o), C.byref(ll), _ptr(losses)), ctx)
+    return ll.value, losses[:o.epochs]
+
+
+def cfust_surrogate_use(ctx: Context, on):
+    _check(lib().cfust_surrogate_use(ctx.handle, int(bool(on))), ctx)
+
+
+def cfust_surrogate_info(ctx: Context):
+    r, f = C.c_int64(0), C.c_int64(0)
+    _check(lib().cfust_surrogate_info(ctx.handle, C.byref(r), C.byref(f)), ctx)
+    return r.value, f.value
+
+
+def cfust_surrogate_params(ctx: Context):
+    th = np.empty(CFUST_MLP_NPARAM, dtype=np.float32)
+    st = np.empty(CFUST_MLP_NSTAT, dtype=np.float32)
+    _check(lib().cfust_surrogate_params(ctx.handle, th.ctypes.data_as(C.POINTER(C.c_float)),
+                                        st.ctypes.data_as(C.POINTER(C.c_float))), ctx)
+    return th, st
 
 
 def cfust_tk_eval(ctx: Context, b, V, nu):

@@ -70,6 +70,7 @@ struct cfust_ctx {
     // E-step pipeline: per-pair (d, log t_p) and c, integral records per level
     double *pd = nullptr, *pc = nullptr;
     RecSet rec[4]{};  // levels 0, 1, 2 and the single-pass moment records
+    Surrogate sur;    // learned surrogate of the level-0 and moment records
     bool single_pass = false;
     int *fix_count = nullptr, *fix_list = nullptr;
     // optional per-kernel-class timing (opts.profile)
@@ -286,6 +287,7 @@ extern "C" cfust_status cfust_profile(cfust_ctx* c, double* ms, int64_t* launche
 
 static void free_all(cfust_ctx* c)
 {
+    sur_free(c->sur);
     void* bufs[] = {c->y, c->pi, c->mu, c->Sigma, c->Delta, c->nu, c->pi_n, c->mu_n, c->Sigma_n,
                     c->Delta_n, c->nu_n, c->F, c->dofs, c->cst64, c->cst32, c->chi64, c->chi32, c->shf64, c->shf32,
                     c->glx64, c->glw64, c->glx32, c->glw32, c->glx32h, c->glw32h, c->logf, c->u, c->elogu, c->eu,
@@ -668,10 +670,24 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
         return fail(c, CFUST_ECUDA, std::string("plan kernel: ") + cudaGetErrorString(e));
     prof_end(c, CFUST_PROF_PLAN, c->launches - n0);
     const IntegArgs ia = integ_args(c);
+    // learned surrogate: the network evaluates the level-0 and moment records, the
+    // lattice only those outside its training range (selection lists)
+    const bool sur = c->sur.on && sp;
+    if (sur) {
+        CU(cudaMemsetAsync(c->sur.nfall, 0, 2 * sizeof(int), c->st));
+        c->sur.last_records = pa.L0.nrec + (density_only ? 0 : c->rec[3].nrec);
+    }
     for (int l = 0; l < (density_only || sp ? 1 : 3); ++l) {
         RecSet r = l == 0 ? pa.L0 : c->rec[l];
         n0 = c->launches;
         prof_begin(c, CFUST_PROF_LEVEL0 + l);
+        if (sur && l == 0) {
+            if ((e = sur_infer(c->sur, r, c->F, 0, c->sur.fall0, c->sur.nfall, c->st)) != cudaSuccess)
+                return fail(c, CFUST_ECUDA, std::string("surrogate kernel: ") + cudaGetErrorString(e));
+            ++c->launches;
+            r.sel = c->sur.fall0;
+            r.nsel = c->sur.nfall;
+        }
         if ((e = launch_integrals(r, ia, fp32, c->nsm, c->st, &c->launches)) != cudaSuccess)
             return fail(c, CFUST_ECUDA, std::string("integral kernel: ") + cudaGetErrorString(e));
         prof_end(c, CFUST_PROF_LEVEL0 + l, c->launches - n0);
@@ -679,7 +695,15 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
     if (sp && !density_only) {
         n0 = c->launches;
         prof_begin(c, CFUST_PROF_MOMENTS);
-        if ((e = launch_moments(c->rec[3], ia, fp32, c->nsm, c->st, &c->launches)) != cudaSuccess)
+        RecSet rm = c->rec[3];
+        if (sur) {
+            if ((e = sur_infer(c->sur, rm, c->F, 1, c->sur.fallM, c->sur.nfall + 1, c->st)) != cudaSuccess)
+                return fail(c, CFUST_ECUDA, std::string("surrogate kernel: ") + cudaGetErrorString(e));
+            ++c->launches;
+            rm.sel = c->sur.fallM;
+            rm.nsel = c->sur.nfall + 1;
+        }
+        if ((e = launch_moments(rm, ia, fp32, c->nsm, c->st, &c->launches)) != cudaSuccess)
             return fail(c, CFUST_ECUDA, std::string("moment kernel: ") + cudaGetErrorString(e));
         prof_end(c, CFUST_PROF_MOMENTS, c->launches - n0);
     }
@@ -1417,4 +1441,87 @@ extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const doub
     if (e != cudaSuccess) s = fail(c, CFUST_ECUDA, std::string("cfust_tk_eval: ") + cudaGetErrorString(e));
     cleanup();
     return s;
+}
+
+// ---------------------------------------------------------------------------
+// Learned surrogate (not part of the paper)
+// ---------------------------------------------------------------------------
+extern "C" cfust_surrogate_opts cfust_surrogate_default_opts(void)
+{
+    cfust_surrogate_opts o;
+    o.epochs = 48;
+    o.batch = 8192;
+    o.samples_per_epoch = 1 << 20;
+    o.lr = 3e-3f;
+    o.margin = 0.5f;
+    o.seed = 1;
+    return o;
+}
+
+extern "C" cfust_status cfust_surrogate_train(cfust_ctx* c, const cfust_surrogate_opts* opts, double* loglik_out,
+                                              double* losses)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_surrogate_train: ctx is NULL");
+    if (!opts) return fail(c, CFUST_EINVAL, "cfust_surrogate_train: opts is NULL");
+    if (!c->single_pass)
+        return fail(c, CFUST_EINVAL, "cfust_surrogate_train: needs single-pass moments (moments = 1, q >= 3)");
+    if (opts->epochs < 0 || opts->batch < 64 || opts->batch > (1 << 20) || opts->batch % 64 ||
+        !(opts->lr > 0.f) || !(opts->margin >= 0.f))
+        return fail(c, CFUST_EINVAL, "cfust_surrogate_train: epochs >= 0, batch a multiple of 64 in [64, 2^20], "
+                                     "lr > 0, margin >= 0");
+    CU(cudaSetDevice(c->opts.device));
+    const bool was = c->sur.on;
+    c->sur.on = false;
+    cfust_status s = cfust_estep(c, loglik_out);  // the lattice E-step whose records are the samples
+    if (s != CFUST_OK) {
+        c->sur.on = was;
+        return s;
+    }
+    const long long nr = c->n * c->g;
+    cudaError_t e = sur_reserve(c->sur, c->q, nr, c->st);
+    RecSet L0 = c->rec[0];
+    L0.nrec = nr;
+    if (!e) e = sur_collect(c->sur, L0, c->rec[3], c->F, c->st);
+    if (e == cudaErrorInvalidValue)
+        return fail(c, CFUST_ESTATE, "cfust_surrogate_train: fewer than 64 usable records");
+    SurOpts so;
+    so.epochs = opts->epochs; so.batch = opts->batch; so.samples_per_epoch = opts->samples_per_epoch;
+    so.lr = opts->lr; so.margin = opts->margin; so.seed = opts->seed;
+    if (!e) e = sur_train(c->sur, so, c->st, losses);
+    if (e) return fail(c, CFUST_ECUDA, std::string("cfust_surrogate_train: ") + cudaGetErrorString(e));
+    c->sur.on = true;
+    return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_surrogate_use(cfust_ctx* c, int on)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_surrogate_use: ctx is NULL");
+    if (on && !c->sur.trained) return fail(c, CFUST_ESTATE, "cfust_surrogate_use: train the surrogate first");
+    c->sur.on = on != 0;
+    return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_surrogate_info(cfust_ctx* c, int64_t* records, int64_t* fallbacks)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_surrogate_info: ctx is NULL");
+    int nf[2] = {0, 0};
+    if (c->sur.nfall) {
+        CU(cudaSetDevice(c->opts.device));
+        CU(cudaMemcpyAsync(nf, c->sur.nfall, sizeof(nf), cudaMemcpyDeviceToHost, c->st));
+        CU(cudaStreamSynchronize(c->st));
+    }
+    if (records) *records = c->sur.last_records;
+    if (fallbacks) *fallbacks = (int64_t)nf[0] + nf[1];
+    return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_surrogate_params(cfust_ctx* c, float* theta, float* stats)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_surrogate_params: ctx is NULL");
+    if (!c->sur.trained) return fail(c, CFUST_ESTATE, "cfust_surrogate_params: not trained");
+    CU(cudaSetDevice(c->opts.device));
+    if (theta) CU(cudaMemcpyAsync(theta, c->sur.theta, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost, c->st));
+    if (stats) CU(cudaMemcpyAsync(stats, c->sur.stats, sizeof(float) * MLP_NSTAT, cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    return CFUST_OK;
 }

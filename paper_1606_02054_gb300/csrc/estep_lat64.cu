@@ -10,7 +10,9 @@ __global__ void __launch_bounds__(256) lattice_records_kernel_64(RecSet r, Integ
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const size_t NM = (size_t)a.lat.N * a.lat.M;
-    for (long long i = warp; i < r.nrec; i += nwarps) {
+    const long long nr = rec_count(r);
+    for (long long t = warp; t < nr; t += nwarps) {
+        const long long i = rec_index(r, t);
         double bt[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) bt[k] = r.bt[i * K + k];

@@ -19,7 +19,9 @@ __global__ void __launch_bounds__(mom32_block<K>()) lattice_mom_kernel_32(RecSet
     const size_t NM = (size_t)a.lat.N * a.lat.M;
     __shared__ double slot[mom32_block<K>() / CF_WARP][W + 1];
     double* acc = slot[threadIdx.x >> 5];
-    for (long long i = warp; i < r.nrec; i += nwarps) {
+    const long long nr = rec_count(r);
+    for (long long t = warp; t < nr; t += nwarps) {
+        const long long i = rec_index(r, t);
         double bt[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) bt[k] = r.bt[i * K + k];

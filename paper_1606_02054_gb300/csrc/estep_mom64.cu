@@ -14,7 +14,9 @@ __global__ void __launch_bounds__(256) lattice_mom_kernel_64(RecSet r, IntegArgs
     const size_t NM = (size_t)a.lat.N * a.lat.M;
     __shared__ double slot[8][W + 1];
     double* acc = slot[threadIdx.x >> 5];
-    for (long long i = warp; i < r.nrec; i += nwarps) {
+    const long long nr = rec_count(r);
+    for (long long t = warp; t < nr; t += nwarps) {
+        const long long i = rec_index(r, t);
         double bt[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) bt[k] = r.bt[i * K + k];

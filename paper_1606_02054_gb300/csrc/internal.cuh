@@ -105,7 +105,13 @@ struct RecSet {
     float4* t2f;       // FP32 modes, k = 2 only (else null): per record two float4,
                        // (h, k, rho, dof) and (1 - rho^2, h|rho| - sign(rho) k, 0, 0),
                        // the last two formed in FP64, so the T_2 kernel runs no FP64
+    const int* sel;    // lattice kernels (k >= 3): if set, only records sel[0 .. *nsel)
+    const int* nsel;   //   (the learned surrogate's fallback list; device count)
 };
+
+// Record index t of a set: every record, or the t-th selected one.
+__device__ __forceinline__ long long rec_count(const RecSet& r) { return r.sel ? (long long)*r.nsel : r.nrec; }
+__device__ __forceinline__ long long rec_index(const RecSet& r, long long t) { return r.sel ? (long long)r.sel[t] : t; }
 
 // FP32 inputs of one T_2 record (see RecSet::t2f); rho = 0 counts as negative.
 __host__ __device__ inline void t2_record_f32(double h, double k, double rho, double dof, float4* out)
@@ -281,3 +287,57 @@ struct ReduceArgs {
     int row;           // values per staged observation row
     const float* y32;  // FP32 observations (FP32 statistics kernel only)
 };
+
+// ---------------------------------------------------------------------------
+// Learned surrogate (not part of the paper): a 3 x 256 tanh MLP mapping a
+// record's features (standardised limits, correlations of Lambda, 1/dof) to
+// log T_q and the standardised truncated moments of the single-pass form.
+// Parameters: FP32 master vector W1 b1 W2 b2 W3 b3 W4 b4 (matrices row-major,
+// input index first); BF16 copies for the GEMMs.
+// ---------------------------------------------------------------------------
+constexpr int MLP_IN = 48, MLP_H = 256, MLP_OUT = 48;
+constexpr long long MLP_W1 = 0, MLP_B1 = MLP_W1 + MLP_IN * MLP_H, MLP_W2 = MLP_B1 + MLP_H,
+                    MLP_B2 = MLP_W2 + MLP_H * MLP_H, MLP_W3 = MLP_B2 + MLP_H, MLP_B3 = MLP_W3 + MLP_H * MLP_H,
+                    MLP_W4 = MLP_B3 + MLP_H, MLP_B4 = MLP_W4 + MLP_H * MLP_OUT, MLP_NPARAM = MLP_B4 + MLP_OUT;
+// feature / target statistics: fmean, fstd, zlo, zhi (MLP_IN each), tmean, tstd (MLP_OUT each)
+constexpr int MLP_NSTAT = 4 * MLP_IN + 2 * MLP_OUT;
+
+struct SurOpts {
+    int epochs, batch;
+    long long samples_per_epoch;
+    float lr, margin;
+    unsigned long long seed;
+};
+
+struct Surrogate {
+    int q = 0, nin = 0, nout = 0;
+    bool trained = false, on = false;
+    long long step = 0;          // Adam steps taken
+    long long cap = 0;           // records per set the buffers hold
+    float margin = 0.25f;
+    float *theta = nullptr, *grad = nullptr, *am = nullptr, *av = nullptr, *stats = nullptr;
+    void* wb = nullptr;          // BF16 row-major copy of theta
+    void* wf = nullptr;          // BF16 weights in mma fragment order (inference)
+    // training set
+    long long ns = 0, ns_cap = 0;
+    float *X = nullptr, *T = nullptr;
+    unsigned char* type = nullptr;   // 0: log T only (dof nu + p); 1: log T and moments
+    unsigned long long* count = nullptr;
+    // minibatch buffers
+    int bcap = 0;
+    void *xb = nullptr, *h1 = nullptr, *h2 = nullptr, *h3 = nullptr, *dz = nullptr, *dz2 = nullptr, *one = nullptr;
+    float *y = nullptr, *tb = nullptr, *mb = nullptr, *part = nullptr;
+    double* lpart = nullptr;
+    double* host_part = nullptr;
+    // fallback lists of the E-step
+    int *fall0 = nullptr, *fallM = nullptr, *nfall = nullptr;
+    long long last_records = 0;
+    float hstats[MLP_NSTAT] = {};  // host copy of stats (standardisation fixed at the first training)
+};
+
+cudaError_t sur_reserve(Surrogate& s, int q, long long records, cudaStream_t st);
+void sur_free(Surrogate& s);
+cudaError_t sur_collect(Surrogate& s, const RecSet& L0, const RecSet& LM, const double* F, cudaStream_t st);
+cudaError_t sur_train(Surrogate& s, const SurOpts& o, cudaStream_t st, double* losses);
+cudaError_t sur_infer(const Surrogate& s, const RecSet& r, const double* F, int moments, int* fall, int* nfall,
+                      cudaStream_t st);

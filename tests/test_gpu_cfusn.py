@@ -7,7 +7,9 @@ relative in FP64; Phi_2 1e-7 relative (two graded Gauss-Legendre pieces of 64
 nodes against the oracle's adaptive quadrature; 4e-8 emulated at these sizes);
 per-pair E-step values 2e-7 when Phi_2 enters (far-tail pairs included), 1e-9
 otherwise, and a pair that is null (T_q = 0 in FP64: log f = -inf) on one side has
-log f < -700 on the other; FP32 modes: l 1e-6 relative; fits: final l 1e-6, parameters 1e-4.
+log f < -700 on the other; FP32 modes: l 1e-6 relative; fits: final l 1e-6,
+parameters 1e-4; the normal mixture (Delta = 0 held, T_q = 2^-q exactly): l 1e-9,
+parameters 1e-8.
 """
 import math
 
@@ -138,3 +140,30 @@ def test_cfusn_fit(cf, oracle):
     for k in ("pi", "mu", "Sigma", "Delta"):
         np.testing.assert_allclose(got[k], ref[k], rtol=1e-4, atol=1e-6, err_msg=k)
     assert np.all(np.isinf(got["nu"]))
+
+
+def test_normal_mixture_fit(cf, oracle):
+    """The normal mixture: CFUSN with Delta^(0) = 0 held (cfust_opts.hold =
+    CFUST_HOLD_DELTA), against the oracle's held fit (pinned on the CPU against a
+    textbook normal-mixture EM): final l 1e-9, parameters 1e-8."""
+    w = synth.make_workload("flow_p4", n=600, with_init=False)
+    y = np.ascontiguousarray(w["y"][:, :3])
+    g, q = 2, 2
+    lab = np.random.default_rng(9).integers(0, g, len(y))
+    P = dict(pi=np.array([0.5, 0.5]), mu=np.array([y[lab == h].mean(0) for h in range(g)]),
+             Sigma=np.array([np.cov(y[lab == h], rowvar=False) for h in range(g)]),
+             Delta=np.zeros((g, 3, q)), nu=np.array([np.inf, np.inf]))
+    qm = w["qmc"]
+    o = cf.cfust_default_opts(qmc_points=qm["npoints"], qmc_shifts=qm["nshifts"], qmc_korobov_a=qm["korobov_a"],
+                              seed=qm["seed"], model=cf.CFUST_MODEL_CFUSN, hold=cf.CFUST_HOLD_DELTA)
+    c = cf.cfust_create(3, q, g, len(y), o)
+    cf.cfust_set_data(c, y)
+    cf.cfust_set_params(c, P)
+    it, hist = cf.cfust_fit(c, 12)
+    ref, rhist, rit = oracle.fit(y, P, 12, oracle.qmc(**qm), hold=oracle.HOLD_DELTA | oracle.HOLD_NU)
+    assert it == rit == 12
+    assert abs(hist[-1] - rhist[-1]) <= 1e-9 * abs(rhist[-1])
+    got = cf.cfust_get_params(c)
+    assert np.all(got["Delta"] == 0.0) and np.all(np.isinf(got["nu"]))
+    for k in ("pi", "mu", "Sigma"):
+        np.testing.assert_allclose(got[k], ref[k], rtol=1e-8, atol=1e-10, err_msg=k)

@@ -188,3 +188,41 @@ def test_held_nu_stays(oracle):
     got, hist, it = oracle.fit(w["y"], w["init"], 5, oracle.qmc(**w["qmc"]), hold=oracle.HOLD_NU)
     np.testing.assert_array_equal(got["nu"], np.asarray(w["init"]["nu"], dtype=float))
     assert np.all(np.diff(hist) > -1e-6 * np.abs(hist[:-1]))  # still an ECM (q = 2: exact moments)
+
+
+def _normal_mixture_em(y, pi, mu, Sigma, iters):
+    """Textbook EM for a mixture of multivariate normals, written independently."""
+    from scipy.stats import multivariate_normal
+
+    n, p = y.shape
+    g = len(pi)
+    pi, mu, Sigma = pi.copy(), mu.copy(), Sigma.copy()
+    for _ in range(iters):
+        a = np.log(pi)[:, None] + np.array([multivariate_normal(mu[h], Sigma[h]).logpdf(y) for h in range(g)])
+        tau = np.exp(a - np.logaddexp.reduce(a, axis=0))
+        for h in range(g):
+            N = tau[h].sum()
+            pi[h] = N / n
+            mu[h] = tau[h] @ y / N
+            r = y - mu[h]
+            Sigma[h] = (r * tau[h][:, None]).T @ r / N
+    return pi, mu, Sigma
+
+
+def test_normal_limit_with_delta_zero_is_the_normal_mixture_em(oracle):
+    """nu = inf (eq 5) with Delta^(0) = 0 held: the E-step has u = 1 and T_q = 2^-q, so the
+    fit is the EM of a normal mixture."""
+    w = synth.make_workload("flow_p4", n=400, with_init=False)
+    y = w["y"][:, :3]
+    g, q = 2, 2
+    rng = np.random.default_rng(9)
+    lab = rng.integers(0, g, len(y))
+    P = dict(pi=np.array([0.5, 0.5]), mu=np.array([y[lab == h].mean(0) for h in range(g)]),
+             Sigma=np.array([np.cov(y[lab == h], rowvar=False) for h in range(g)]),
+             Delta=np.zeros((g, 3, q)), nu=np.array([np.inf, np.inf]))
+    got, hist, it = oracle.fit(y, P, 12, oracle.qmc(**w["qmc"]), hold=oracle.HOLD_DELTA | oracle.HOLD_NU)
+    pi, mu, Sigma = _normal_mixture_em(y, P["pi"], P["mu"], P["Sigma"], 12)
+    assert np.all(got["Delta"] == 0.0) and np.all(np.isinf(got["nu"]))
+    np.testing.assert_allclose(got["pi"], pi, rtol=1e-10)
+    np.testing.assert_allclose(got["mu"], mu, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(got["Sigma"], Sigma, rtol=1e-10, atol=1e-12)
