@@ -309,6 +309,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nfits", type=int, default=64, help="batch workload: problems")
     ap.add_argument("--starts", type=int, default=4, help="batch workload: starts per problem")
+    ap.add_argument("--surrogate", action="store_true",
+                    help="learned surrogate form (single-pass moments, q >= 3): train at the start "
+                         "values (untimed), then time E-steps through the network")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -360,7 +363,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     pairs = w["n"] * w["g"]
 
-    def measure(moments, with_clocks):
+    def measure(moments, with_clocks, surrogate=False):
         """warm-up, then `steps` timed EM iterations (CUDA events per step, L2
         flushed before each); returns timings and the library's kernel profile."""
         ctx = cf.cfust_create(w["p"], w["q"], w["g"], w["n"],
@@ -368,6 +371,20 @@ def main():
                                     moments=moments))
         cf.cfust_set_data(ctx, y_dev)
         cf.cfust_set_params(ctx, w["init"])
+        sur = None
+        if surrogate:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ll_lat, losses = cf.cfust_surrogate_train(ctx)
+            torch.cuda.synchronize()
+            t_train = time.perf_counter() - t0
+            ll_sur = cf.cfust_loglik(ctx)  # the density pass through the network, same Psi
+            o = cf.cfust_surrogate_default_opts()
+            sur = {"train_s": t_train, "epochs": o.epochs, "batch": o.batch,
+                   "samples_per_epoch": o.samples_per_epoch, "loss_first": float(losses[0]),
+                   "loss_last": float(losses[-1]), "loglik_lattice_at_start": ll_lat,
+                   "loglik_surrogate_at_start": ll_sur,
+                   "loglik_rel_err_at_start": abs(ll_sur - ll_lat) / abs(ll_lat)}
 
         def step():
             L = cf.cfust_estep(ctx)
@@ -407,11 +424,17 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
         estep_ms = sum(v[0] for k, v in prof.items() if k != "mstep") / args.steps
-        return dict(ms=ms, prof=prof, launches=launches, ll=lls[-1], clk=clk, estep_ms=estep_ms)
+        if sur is not None:
+            recs, fb = cf.cfust_surrogate_info(ctx)
+            sur["fallback_fraction_last_step"] = fb / max(recs, 1)
+        return dict(ms=ms, prof=prof, launches=launches, ll=lls[-1], clk=clk, estep_ms=estep_ms, sur=sur)
 
     chosen_moments = 1 if args.moments == "single-pass" else 0
-    main_run = measure(chosen_moments, True)
-    plain_run = measure(0, False) if chosen_moments == 1 and w["q"] >= 3 else None
+    if args.surrogate and not (chosen_moments == 1 and w["q"] >= 3):
+        raise SystemExit("--surrogate needs single-pass moments and q >= 3")
+    main_run = measure(chosen_moments, True, surrogate=args.surrogate)
+    plain_run = measure(0, False) if chosen_moments == 1 and w["q"] >= 3 and not args.surrogate else None
+    lattice_run = measure(chosen_moments, False) if args.surrogate else None
     ms, prof, clk = main_run["ms"], main_run["prof"], main_run["clk"]
     launches = main_run["launches"]
     value = pairs * world / (ms / 1e3)
@@ -433,7 +456,22 @@ def main():
     key = _unit_key(kind, kdim, args.precision)
     ipu = INSTR_PER_UNIT.get(key) if key else None
     secs = dom_ms_per_launch / 1e3
-    if ipu:
+    if args.surrogate and prof["surrogate"][1] > 0:
+        # the network's inference kernel: one launch per record set (n g records), a dense
+        # BF16 contraction; algorithmic FLOPs of the used widths (nin -> 256 -> 256 -> 256 -> nout)
+        q = w["q"]
+        nin, nout = q + q * (q - 1) // 2 + 1, 1 + q + q * (q + 1) // 2
+        flops_rec = 2 * (nin * 256 + 2 * 256 * 256 + 256 * nout)
+        ms_l = prof["surrogate"][0] / prof["surrogate"][1]
+        achieved = flops_rec * pairs / (ms_l / 1e3) / 1e12
+        peak = _peaks().get("bf16_tflops")
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if peak else None, "traffic": None,
+                "kernel": "mlp_infer_kernel", "flops_per_record": flops_rec, "records_per_launch": pairs,
+                "ms_per_launch": ms_l,
+                "peak_basis": "MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS 8192^3) of measured",
+                "note": "mma.sync m16n8k16 BF16 (legacy tensor path), weights staged per layer in shared memory"}
+    elif ipu:
         achieved = ipu * units / secs / 1e12
         peak = SM_COUNT * LANES_PER_SM * f_sm / 1e12
         tb = INTEG_TRAFFIC_BYTES_PER_RECORD.get(key)
@@ -519,6 +557,14 @@ def main():
                 "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
                 "roofline": roof, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
                 "loglik_check": ll_check}
+        if main_run["sur"] is not None:
+            line["config"]["form"] = "learned surrogate (BF16 MLP, lattice fallback) + single-pass moments"
+            line["surrogate"] = main_run["sur"]
+            line["lattice_gpu"] = {
+                "form": "single-pass moments, lattice only", "value": pairs * world / (lattice_run["ms"] / 1e3),
+                "unit": UNIT, "ms_per_step": lattice_run["ms"],
+                "estep_obs_comp_per_s": pairs * world / (lattice_run["estep_ms"] / 1e3),
+                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in lattice_run["prof"].items()}}
         if plain_run:
             line["plain_gpu"] = {
                 "form": "moment recursion (T_q, T_{q-1}, T_{q-2} records)",

@@ -118,6 +118,7 @@ enum {
     CFUST_PROF_FIXUP,       /* FP64 re-evaluation of far-tail pairs (FP32 mode) */
     CFUST_PROF_REDUCE,      /* eqs (12), (27) and the tau-weighted statistics */
     CFUST_PROF_MSTEP,       /* eqs (18)-(22) */
+    CFUST_PROF_SURROGATE,   /* the learned surrogate's inference (level-0 and moment records) */
     CFUST_NPROF
 };
 

@@ -34,7 +34,7 @@ CFUST_F32, CFUST_F64 = 0, 1
 CFUST_MLP_IN, CFUST_MLP_H, CFUST_MLP_OUT, CFUST_MLP_NPARAM, CFUST_MLP_NSTAT = 48, 256, 48, 156464, 288
 # kernel classes of cfust_profile
 PROF_NAMES = ("setup", "chi_table", "plan", "level0_Tq", "level1_Tq-1", "level2_Tq-2",
-              "moments_Tq", "combine", "fixup_fp64", "reduce", "mstep")
+              "moments_Tq", "combine", "fixup_fp64", "reduce", "mstep", "surrogate")
 CFUST_NPROF = len(PROF_NAMES)
 
 

@@ -676,15 +676,23 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
     if (sur) {
         CU(cudaMemsetAsync(c->sur.nfall, 0, 2 * sizeof(int), c->st));
         c->sur.last_records = pa.L0.nrec + (density_only ? 0 : c->rec[3].nrec);
+        n0 = c->launches;
+        prof_begin(c, CFUST_PROF_SURROGATE);
+        if ((e = sur_infer(c->sur, pa.L0, c->F, 0, c->sur.fall0, c->sur.nfall, c->st)) != cudaSuccess)
+            return fail(c, CFUST_ECUDA, std::string("surrogate kernel: ") + cudaGetErrorString(e));
+        ++c->launches;
+        if (!density_only) {
+            if ((e = sur_infer(c->sur, c->rec[3], c->F, 1, c->sur.fallM, c->sur.nfall + 1, c->st)) != cudaSuccess)
+                return fail(c, CFUST_ECUDA, std::string("surrogate kernel: ") + cudaGetErrorString(e));
+            ++c->launches;
+        }
+        prof_end(c, CFUST_PROF_SURROGATE, c->launches - n0);
     }
     for (int l = 0; l < (density_only || sp ? 1 : 3); ++l) {
         RecSet r = l == 0 ? pa.L0 : c->rec[l];
         n0 = c->launches;
         prof_begin(c, CFUST_PROF_LEVEL0 + l);
-        if (sur && l == 0) {
-            if ((e = sur_infer(c->sur, r, c->F, 0, c->sur.fall0, c->sur.nfall, c->st)) != cudaSuccess)
-                return fail(c, CFUST_ECUDA, std::string("surrogate kernel: ") + cudaGetErrorString(e));
-            ++c->launches;
+        if (sur && l == 0) {  // the records outside the network's training range
             r.sel = c->sur.fall0;
             r.nsel = c->sur.nfall;
         }
@@ -697,9 +705,6 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
         prof_begin(c, CFUST_PROF_MOMENTS);
         RecSet rm = c->rec[3];
         if (sur) {
-            if ((e = sur_infer(c->sur, rm, c->F, 1, c->sur.fallM, c->sur.nfall + 1, c->st)) != cudaSuccess)
-                return fail(c, CFUST_ECUDA, std::string("surrogate kernel: ") + cudaGetErrorString(e));
-            ++c->launches;
             rm.sel = c->sur.fallM;
             rm.nsel = c->sur.nfall + 1;
         }
