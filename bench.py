@@ -49,7 +49,7 @@ INSTR_PER_UNIT = {("lattice", 4): 188.8, ("moments", 4): 236.3, ("t2", 2, "mixed
 # dram__bytes_write.sum of the launch / its records: 16,000 records of each
 # lattice kind at flow_p4 n = 4,000; 320,000 T_2 records at wide_p16 n = 20,000);
 # the records dominate, so traffic scales with the record count.
-INTEG_TRAFFIC_BYTES_PER_RECORD = {("lattice", 4): 856064 / 16000, ("moments", 4): 816640 / 16000,
+INTEG_TRAFFIC_BYTES_PER_RECORD = {("lattice", 4): 797440 / 16000, ("moments", 4): 816640 / 16000,
                                   ("t2", 2, "mixed"): 11594752 / 320000}
 
 

@@ -3,16 +3,16 @@
 #include "internal.cuh"
 #include "special.cuh"
 
-template <int K>
+template <int K, bool SEL>
 __global__ void __launch_bounds__(256) lattice_records_kernel_64(RecSet r, IntegArgs a)
 {
     const int lane = threadIdx.x & (CF_WARP - 1);
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const size_t NM = (size_t)a.lat.N * a.lat.M;
-    const long long nr = rec_count(r);
+    const long long nr = rec_count<SEL>(r);
     for (long long t = warp; t < nr; t += nwarps) {
-        const long long i = rec_index(r, t);
+        const long long i = rec_index<SEL>(r, t);
         double bt[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) bt[k] = r.bt[i * K + k];
@@ -26,15 +26,23 @@ __global__ void __launch_bounds__(256) lattice_records_kernel_64(RecSet r, Integ
     }
 }
 
+// the selection-list instantiation only where a list is given
+template <int K>
+static void go(const RecSet& r, const IntegArgs& a, int blocks, int threads, cudaStream_t st)
+{
+    if (r.sel) lattice_records_kernel_64<K, true><<<blocks, threads, 0, st>>>(r, a);
+    else lattice_records_kernel_64<K, false><<<blocks, threads, 0, st>>>(r, a);
+}
+
 cudaError_t launch_lattice64(int k, const RecSet& r, const IntegArgs& a, int blocks, cudaStream_t st)
 {
     switch (k) {
-    case 3: lattice_records_kernel_64<3><<<blocks, 256, 0, st>>>(r, a); break;
-    case 4: lattice_records_kernel_64<4><<<blocks, 256, 0, st>>>(r, a); break;
-    case 5: lattice_records_kernel_64<5><<<blocks, 256, 0, st>>>(r, a); break;
-    case 6: lattice_records_kernel_64<6><<<blocks, 256, 0, st>>>(r, a); break;
-    case 7: lattice_records_kernel_64<7><<<blocks, 256, 0, st>>>(r, a); break;
-    case 8: lattice_records_kernel_64<8><<<blocks, 256, 0, st>>>(r, a); break;
+    case 3: go<3>(r, a, blocks, 256, st); break;
+    case 4: go<4>(r, a, blocks, 256, st); break;
+    case 5: go<5>(r, a, blocks, 256, st); break;
+    case 6: go<6>(r, a, blocks, 256, st); break;
+    case 7: go<7>(r, a, blocks, 256, st); break;
+    case 8: go<8>(r, a, blocks, 256, st); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -9,7 +9,7 @@
 template <int K>
 __host__ __device__ constexpr int mom32_block() { return K >= 7 ? 128 : 256; }
 
-template <int K>
+template <int K, bool SEL>
 __global__ void __launch_bounds__(mom32_block<K>()) lattice_mom_kernel_32(RecSet r, IntegArgs a)
 {
     constexpr int W = K + K * (K + 1) / 2;
@@ -19,9 +19,9 @@ __global__ void __launch_bounds__(mom32_block<K>()) lattice_mom_kernel_32(RecSet
     const size_t NM = (size_t)a.lat.N * a.lat.M;
     __shared__ double slot[mom32_block<K>() / CF_WARP][W + 1];
     double* acc = slot[threadIdx.x >> 5];
-    const long long nr = rec_count(r);
+    const long long nr = rec_count<SEL>(r);
     for (long long t = warp; t < nr; t += nwarps) {
-        const long long i = rec_index(r, t);
+        const long long i = rec_index<SEL>(r, t);
         double bt[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) bt[k] = r.bt[i * K + k];
@@ -33,15 +33,23 @@ __global__ void __launch_bounds__(mom32_block<K>()) lattice_mom_kernel_32(RecSet
     }
 }
 
+// the selection-list instantiation only where a list is given
+template <int K>
+static void go(const RecSet& r, const IntegArgs& a, int blocks, int threads, cudaStream_t st)
+{
+    if (r.sel) lattice_mom_kernel_32<K, true><<<blocks, threads, 0, st>>>(r, a);
+    else lattice_mom_kernel_32<K, false><<<blocks, threads, 0, st>>>(r, a);
+}
+
 cudaError_t launch_mom32(int k, const RecSet& r, const IntegArgs& a, int blocks, cudaStream_t st)
 {
     switch (k) {
-    case 3: lattice_mom_kernel_32<3><<<blocks, 256, 0, st>>>(r, a); break;
-    case 4: lattice_mom_kernel_32<4><<<blocks, 256, 0, st>>>(r, a); break;
-    case 5: lattice_mom_kernel_32<5><<<blocks, 256, 0, st>>>(r, a); break;
-    case 6: lattice_mom_kernel_32<6><<<blocks, 256, 0, st>>>(r, a); break;
-    case 7: lattice_mom_kernel_32<7><<<2 * blocks, 128, 0, st>>>(r, a); break;  // same warps
-    case 8: lattice_mom_kernel_32<8><<<2 * blocks, 128, 0, st>>>(r, a); break;
+    case 3: go<3>(r, a, blocks, 256, st); break;
+    case 4: go<4>(r, a, blocks, 256, st); break;
+    case 5: go<5>(r, a, blocks, 256, st); break;
+    case 6: go<6>(r, a, blocks, 256, st); break;
+    case 7: go<7>(r, a, 2 * blocks, 128, st); break;  // same warps
+    case 8: go<8>(r, a, 2 * blocks, 128, st); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

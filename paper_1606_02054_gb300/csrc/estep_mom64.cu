@@ -4,7 +4,7 @@
 #include "internal.cuh"
 #include "special.cuh"
 
-template <int K>
+template <int K, bool SEL>
 __global__ void __launch_bounds__(256) lattice_mom_kernel_64(RecSet r, IntegArgs a)
 {
     constexpr int W = K + K * (K + 1) / 2;
@@ -14,9 +14,9 @@ __global__ void __launch_bounds__(256) lattice_mom_kernel_64(RecSet r, IntegArgs
     const size_t NM = (size_t)a.lat.N * a.lat.M;
     __shared__ double slot[8][W + 1];
     double* acc = slot[threadIdx.x >> 5];
-    const long long nr = rec_count(r);
+    const long long nr = rec_count<SEL>(r);
     for (long long t = warp; t < nr; t += nwarps) {
-        const long long i = rec_index(r, t);
+        const long long i = rec_index<SEL>(r, t);
         double bt[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) bt[k] = r.bt[i * K + k];
@@ -28,15 +28,23 @@ __global__ void __launch_bounds__(256) lattice_mom_kernel_64(RecSet r, IntegArgs
     }
 }
 
+// the selection-list instantiation only where a list is given
+template <int K>
+static void go(const RecSet& r, const IntegArgs& a, int blocks, int threads, cudaStream_t st)
+{
+    if (r.sel) lattice_mom_kernel_64<K, true><<<blocks, threads, 0, st>>>(r, a);
+    else lattice_mom_kernel_64<K, false><<<blocks, threads, 0, st>>>(r, a);
+}
+
 cudaError_t launch_mom64(int k, const RecSet& r, const IntegArgs& a, int blocks, cudaStream_t st)
 {
     switch (k) {
-    case 3: lattice_mom_kernel_64<3><<<blocks, 256, 0, st>>>(r, a); break;
-    case 4: lattice_mom_kernel_64<4><<<blocks, 256, 0, st>>>(r, a); break;
-    case 5: lattice_mom_kernel_64<5><<<blocks, 256, 0, st>>>(r, a); break;
-    case 6: lattice_mom_kernel_64<6><<<blocks, 256, 0, st>>>(r, a); break;
-    case 7: lattice_mom_kernel_64<7><<<blocks, 256, 0, st>>>(r, a); break;
-    case 8: lattice_mom_kernel_64<8><<<blocks, 256, 0, st>>>(r, a); break;
+    case 3: go<3>(r, a, blocks, 256, st); break;
+    case 4: go<4>(r, a, blocks, 256, st); break;
+    case 5: go<5>(r, a, blocks, 256, st); break;
+    case 6: go<6>(r, a, blocks, 256, st); break;
+    case 7: go<7>(r, a, blocks, 256, st); break;
+    case 8: go<8>(r, a, blocks, 256, st); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

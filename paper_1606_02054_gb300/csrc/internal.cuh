@@ -109,9 +109,12 @@ struct RecSet {
     const int* nsel;   //   (the learned surrogate's fallback list; device count)
 };
 
-// Record index t of a set: every record, or the t-th selected one.
-__device__ __forceinline__ long long rec_count(const RecSet& r) { return r.sel ? (long long)*r.nsel : r.nrec; }
-__device__ __forceinline__ long long rec_index(const RecSet& r, long long t) { return r.sel ? (long long)r.sel[t] : t; }
+// Record index t of a set: every record, or (SEL: a kernel instantiated for
+// selection lists) the t-th selected one.
+template <bool SEL>
+__device__ __forceinline__ long long rec_count(const RecSet& r) { return SEL ? (long long)*r.nsel : r.nrec; }
+template <bool SEL>
+__device__ __forceinline__ long long rec_index(const RecSet& r, long long t) { return SEL ? (long long)r.sel[t] : t; }
 
 // FP32 inputs of one T_2 record (see RecSet::t2f); rho = 0 counts as negative.
 __host__ __device__ inline void t2_record_f32(double h, double k, double rho, double dof, float4* out)
@@ -321,7 +324,7 @@ struct Surrogate {
     // training set
     long long ns = 0, ns_cap = 0;
     float *X = nullptr, *T = nullptr;
-    unsigned char* type = nullptr;   // 0: log T only (dof nu + p); 1: log T and moments
+    unsigned char* type = nullptr;   // 0: log T only (dof nu + p); 1: log T and moments; 2: unused
     unsigned long long* count = nullptr;
     // minibatch buffers
     int bcap = 0;

@@ -306,15 +306,21 @@ __device__ int sur_features(int q, const double* bt, const double* Lc, double do
 // Training-set collection from a finished lattice E-step (records of level 0 at
 // dof nu + p and the moment records at nu + p + 2).
 // ---------------------------------------------------------------------------
-__global__ void sur_collect_kernel(RecSet r, const double* __restrict__ F, int q, int type, float* __restrict__ X,
-                                   float* __restrict__ T, unsigned char* __restrict__ ty,
-                                   unsigned long long* __restrict__ count, long long cap)
+// Sample base + i is record i of the set (fixed positions: the training order does
+// not depend on thread scheduling); unusable records get type 2 (no loss, no statistics).
+__global__ void sur_collect_kernel(RecSet r, const double* __restrict__ F, int q, int type, long long base,
+                                   float* __restrict__ X, float* __restrict__ T, unsigned char* __restrict__ ty,
+                                   unsigned long long* __restrict__ count)
 {
     const int W = q + q * (q + 1) / 2;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < r.nrec;
          i += (long long)gridDim.x * blockDim.x) {
+        const long long slot = base + i;
         const double v = r.res[i];
-        if (!(v > 1e-300) || !isfinite(v)) continue;  // null or far-tail records stay with the lattice
+        if (!(v > 1e-300) || !isfinite(v)) {  // null or far-tail records stay with the lattice
+            ty[slot] = 2;
+            continue;
+        }
         // moment targets: m1 and the Cholesky factor of Cov = E[X X^T] - m1 m1^T with log
         // diagonal; a record whose lattice covariance is not positive definite keeps
         // only its log T target
@@ -341,8 +347,7 @@ __global__ void sur_collect_kernel(RecSet r, const double* __restrict__ F, int q
                     for (int b = 0; b <= a; ++b) tg[q + a * (a + 1) / 2 + b] = a == b ? log(L[a][a]) : L[a][b];
             }
         }
-        const unsigned long long slot = atomicAdd(count, 1ULL);
-        if ((long long)slot >= cap) continue;
+        atomicAdd(count, 1ULL);  // usable records (a count only)
         float f[MLP_IN];
         const int nin = sur_features(q, r.bt + i * q, F + r.fac[i], r.dof[i], f);
         float* x = X + slot * MLP_IN;
@@ -365,7 +370,7 @@ __global__ void col_stats_kernel(const float* __restrict__ Z, const unsigned cha
     const long long r0 = blockIdx.x * chunk, r1 = min(rows, r0 + chunk);
     double s = 0.0, s2 = 0.0, n = 0.0, lo = INFINITY, hi = -INFINITY;
     for (long long r = r0; r < r1; ++r) {
-        if (target && c > 0 && ty[r] == 0) continue;
+        if (ty[r] == 2 || (target && c > 0 && ty[r] == 0)) continue;
         const double v = Z[r * cols + c];
         s += v; s2 += v * v; n += 1.0;
         lo = v < lo ? v : lo; hi = v > hi ? v : hi;
@@ -401,7 +406,7 @@ __global__ void gather_kernel(const float* __restrict__ X, const float* __restri
                                        (unsigned long long)ns;
         if (k < MLP_IN) xb[b * MLP_IN + k] = to_bf16(X[row * MLP_IN + k]);
         tb[e] = T[row * MLP_OUT + k];
-        mb[e] = k < nout && (k == 0 || ty[row] == 1) ? 1.f : 0.f;
+        mb[e] = ty[row] != 2 && k < nout && (k == 0 || ty[row] == 1) ? 1.f : 0.f;
     }
 }
 
@@ -806,17 +811,17 @@ cudaError_t sur_collect(Surrogate& s, const RecSet& L0, const RecSet& LM, const 
     }
     if ((e = cudaMemsetAsync(s.count, 0, sizeof(unsigned long long), st))) return e;
     const int nsm = sm_count();
-    sur_collect_kernel<<<grid_of(L0.nrec, 256, nsm * 8), 256, 0, st>>>(L0, F, s.q, 0, s.X, s.T, s.type, s.count,
-                                                                       s.ns_cap);
+    sur_collect_kernel<<<grid_of(L0.nrec, 256, nsm * 8), 256, 0, st>>>(L0, F, s.q, 0, 0, s.X, s.T, s.type,
+                                                                       s.count);
     if ((e = cudaGetLastError())) return e;
-    sur_collect_kernel<<<grid_of(LM.nrec, 256, nsm * 8), 256, 0, st>>>(LM, F, s.q, 1, s.X, s.T, s.type, s.count,
-                                                                       s.ns_cap);
+    sur_collect_kernel<<<grid_of(LM.nrec, 256, nsm * 8), 256, 0, st>>>(LM, F, s.q, 1, L0.nrec, s.X, s.T, s.type,
+                                                                       s.count);
     if ((e = cudaGetLastError())) return e;
     unsigned long long n = 0;
     if ((e = cudaMemcpyAsync(&n, s.count, sizeof(n), cudaMemcpyDeviceToHost, st))) return e;
     if ((e = cudaStreamSynchronize(st))) return e;
-    s.ns = (long long)(n < (unsigned long long)s.ns_cap ? n : (unsigned long long)s.ns_cap);
-    if (s.ns < 64) return cudaErrorInvalidValue;
+    if (n < 64) return cudaErrorInvalidValue;
+    s.ns = need;
     // feature and target statistics (double partials, summed on the host)
     const int nb = 1024;
     double* part = nullptr;
