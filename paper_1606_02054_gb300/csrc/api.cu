@@ -392,7 +392,7 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     c->row = 4 + p + q + q * q;
     const size_t rowbytes = c->mixed ? sizeof(float) : sizeof(double);
     int chunk = 256;
-    while (chunk > 32 && (size_t)chunk * (c->row * rowbytes + (g + 1) * sizeof(double)) + CF_MAXG * sizeof(double) > 64 * 1024)
+    while (chunk > 32 && (size_t)chunk * ((c->row + g) * rowbytes + sizeof(double)) + CF_MAXG * sizeof(double) > 64 * 1024)
         chunk -= 32;
     c->chunk = chunk;
     c->nblocks_red = (int)((n + chunk - 1) / chunk);
@@ -759,8 +759,8 @@ static cfust_status enqueue_estep(cfust_ctx* c)
     r.elogu = c->elogu; r.eu = c->eu; r.euu = c->euu; r.tau = c->tau; r.partial = c->partial;
     r.chunk = c->chunk; r.row = c->row;
     r.y32 = c->y32;
-    const size_t smem = (c->mixed ? sizeof(float) : sizeof(double)) * (size_t)c->chunk * c->row +
-                        sizeof(double) * ((size_t)c->g * c->chunk + c->chunk + CF_MAXG);
+    const size_t smem = (c->mixed ? sizeof(float) : sizeof(double)) * ((size_t)c->chunk * c->row + (size_t)c->g * c->chunk) +
+                        sizeof(double) * ((size_t)c->chunk + CF_MAXG);
     prof_begin(c, CFUST_PROF_REDUCE);
     if (c->mixed) estep_reduce_kernel_f32<<<c->nblocks_red, 256, smem, c->st>>>(r);
     else estep_reduce_kernel<<<c->nblocks_red, 256, smem, c->st>>>(r);

@@ -70,8 +70,8 @@ __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
     const long long j0 = (long long)blockIdx.x * a.chunk;
     const int cnt = (int)((n - j0) < a.chunk ? (n - j0) : a.chunk);
     // chunk is a multiple of 32, so the FP32 rows end on an 8-byte boundary
-    double* taus = (double*)(rows + (size_t)a.chunk * a.row);
-    double* lj = taus + (size_t)g * a.chunk;
+    T* taus = rows + (size_t)a.chunk * a.row;  // in the row type: the rows hold tau as T anyway
+    double* lj = (double*)(taus + (size_t)g * a.chunk);
     double* lpi = lj + a.chunk;  // log pi_h (CF_MAXG slots)
     double* out = a.partial + (size_t)blockIdx.x * (g * S + 1);
     const int t = threadIdx.x;
@@ -104,7 +104,7 @@ __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
         for (int h = 0; h < CF_MAXG; ++h) {
             if (h < g) {
                 const double tv = v[h] * rs;
-                taus[h * a.chunk + t] = tv;
+                taus[h * a.chunk + t] = (T)tv;
                 if (a.tau) a.tau[(size_t)h * n + j] = tv;
             }
         }
@@ -126,7 +126,7 @@ __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
             T* rw = rows + (size_t)t * a.row;
             if (t < cnt) {
                 const size_t pid = (size_t)h * n + j0 + t;
-                const double tv = taus[h * a.chunk + t];
+                const double tv = (double)taus[h * a.chunk + t];
                 const double uv = a.u[pid];
                 rw[0] = (T)tv;
                 rw[1] = (T)(tv * uv);

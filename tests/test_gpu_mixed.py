@@ -87,3 +87,36 @@ def test_mixed_fit_error(cf, oracle):
     print(f"mixed fit: final loglik rel err {rel:.2e}, parameter rel errors {perr}")
     assert rel <= 1e-6
     assert max(perr.values()) <= 1e-4
+
+
+@pytest.mark.parametrize("p,q,g,n", [(32, 8, 2, 300), (17, 3, 3, 257), (5, 1, 2, 1000)])
+def test_mixed_cross_statistics(cf, p, q, g, n):
+    """Sre = sum tau r eu^T and Srr = sum tau u r r^T of the mixed form (compensated
+    FP32 sums per block of at most 256 rows, FP64 across blocks) at the largest
+    shape (p = 32, q = 8) and ragged n, against FP64 sums of the same FP32 row values
+    built from the context's own tau, u and eu: 1e-5 of each block's largest entry;
+    Srr exactly symmetric."""
+    rng = np.random.default_rng(100 * p + q)
+    P = synth.draw_params(rng, p, q, g, wishart_df=p + 8)
+    y32 = np.ascontiguousarray(synth.sample(rng, n, P)[0], dtype=np.float32)
+    ctx = cf.cfust_create(p, q, g, n, cf.cfust_default_opts(precision=cf.CFUST_PREC_MIXED, moments=1))
+    cf.cfust_set_data(ctx, y32)
+    cf.cfust_set_params(ctx, P)
+    cf.cfust_estep(ctx)
+    pr = cf.cfust_get_pairs(ctx)
+    S = cf.cfust_get_stats(ctx)
+    f64 = np.float64
+    off = 3 + p + q
+    fSrr = off + p * q + q * q
+    for h in range(g):
+        t = pr["tau"][h].astype(np.float32).astype(f64)
+        tu = (pr["tau"][h] * pr["u"][h]).astype(np.float32).astype(f64)
+        r = (y32 - P["mu"][h].astype(np.float32)).astype(f64)
+        e = pr["eu"][h].astype(np.float32).astype(f64)
+        Sre = np.einsum("j,ja,jb->ab", t, r, e)
+        Srr = np.einsum("j,ja,jb->ab", tu, r, r)
+        got_re = S[h][off:off + p * q].reshape(p, q)
+        got_rr = S[h][fSrr:fSrr + p * p].reshape(p, p)
+        assert np.max(np.abs(got_re - Sre)) <= 1e-5 * np.abs(Sre).max(), h
+        assert np.max(np.abs(got_rr - Srr)) <= 1e-5 * np.abs(Srr).max(), h
+        assert np.array_equal(got_rr, got_rr.T)
