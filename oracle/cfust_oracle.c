@@ -1277,7 +1277,7 @@ int ora_moment_start(int n, int p, int q, int g, const double* y, const int* lab
     double* L = (double*)malloc(sizeof(double) * p * p);
     int rc = 0;
     for (int h = 0; h < g && !rc; ++h) {
-        /* line 9: sample mean, covariance S and its diagonal s* of cluster h */
+        /* sample mean, covariance S and its diagonal s* of cluster h */
         long long nh = 0;
         for (int i = 0; i < p; ++i) ybar[i] = m3[i] = 0.0;
         for (int i = 0; i < p * p; ++i) S[i] = 0.0;
@@ -1298,9 +1298,9 @@ int ora_moment_start(int n, int p, int q, int g, const double* y, const int* lab
                 }
             }
         for (int i = 0; i < p * p; ++i) S[i] /= (double)(nh - 1);
-        /* line 6: pi from the partition */
+        /* pi from the partition */
         pi[h] = (double)nh / n;
-        /* line 10, eq (23): delta = sign(m3) sqrt(pi (1 - alpha) s* / (pi - 2)) element-wise,
+        /* eq (23): delta = sign(m3) sqrt(pi (1 - alpha) s* / (pi - 2)) element-wise,
            Sigma = S - (1 - alpha) diag(s*), mu = ybar - sqrt(2/pi) delta, nu = nu0.
            Delta (p x q): diag(delta) for q = p, the column delta for q = 1, otherwise delta
            on the leading diagonal; only the coordinates that carry a delta are skewed. */
@@ -1337,19 +1337,19 @@ int ora_init(int n, int p, int q, int g, const double* y, int nstarts, const int
     double* cD = (double*)malloc(sizeof(double) * g * p * q);
     double* cn = (double*)malloc(sizeof(double) * g);
     int* lab = (int*)malloc(sizeof(int) * (n > 0 ? n : 1));
-    double lbest = -INFINITY;       /* line 2 */
-    int ibest = -1, rc = 0;         /* line 3: Psi empty */
-    for (int s = 0; s < nstarts && !rc; ++s) {              /* line 4 */
+    double lbest = -INFINITY;       /* the best log-likelihood so far */
+    int ibest = -1, rc = 0;         /* no candidate kept yet */
+    for (int s = 0; s < nstarts && !rc; ++s) {              /* each start */
         if (labels) memcpy(lab, labels + (size_t)s * n, sizeof(int) * n);
-        else ora_random_partition(n, g, seed, s, lab);       /* line 5 */
-        for (int a = 0; a < nalpha && !rc; ++a) {            /* line 7 */
+        else ora_random_partition(n, g, seed, s, lab);       /* its partition */
+        for (int a = 0; a < nalpha && !rc; ++a) {            /* each alpha */
             double L = -INFINITY;
             if (ora_moment_start(n, p, q, g, y, lab, alphas[a], nu0, cp, cm, cS, cD, cn) == 0) {
-                rc = ora_loglik(n, p, q, g, y, cp, cm, cS, cD, cn, qmc, nthreads, &L);  /* line 12 */
+                rc = ora_loglik(n, p, q, g, y, cp, cm, cS, cD, cn, qmc, nthreads, &L);  /* its log-likelihood */
                 if (rc || !isfinite(L)) { rc = 0; L = -INFINITY; }
             }
             if (loglik_out) loglik_out[(size_t)s * nalpha + a] = L;
-            if (L > lbest) {                                 /* lines 13-14 (and l <- l*) */
+            if (L > lbest) {                                 /* keep the best (first maximum) */
                 lbest = L;
                 ibest = s * nalpha + a;
                 memcpy(pi, cp, sizeof(double) * g);

@@ -1226,11 +1226,11 @@ extern "C" cfust_status cfust_init(cfust_ctx* c, int nstarts, const int32_t* lab
     std::vector<double> s0((size_t)g * W0), s1((size_t)g * W1), mean((size_t)g * p);
     std::vector<double> cp(g), cm((size_t)g * p), cS((size_t)g * p * p), cD((size_t)g * p * q), cn(g);
     std::vector<double> bp, bm, bS, bD, bn;
-    double lbest = -INFINITY;  // line 2
-    int ibest = -1;            // line 3: Psi empty
+    double lbest = -INFINITY;  // the best log-likelihood so far
+    int ibest = -1;            // no candidate kept yet
     cfust_status s = CFUST_OK;
-    for (int st = 0; st < nstarts && s == CFUST_OK; ++st) {  // line 4
-        // line 5: the partition
+    for (int st = 0; st < nstarts && s == CFUST_OK; ++st) {  // each start
+        // its partition: given labels or a random one
         if (labels) e = cudaMemcpyAsync(dlab, labels + (size_t)st * n, sizeof(int) * n, cudaMemcpyHostToDevice, c->st);
         else e = launch_random_partition(n, g, seed, st, dlab, c->st);
         if (e == cudaSuccess) e = launch_cluster_moments(0, c->D, c->y, dlab, nullptr, chunk, blocks, partial, c->st);
@@ -1242,7 +1242,7 @@ extern "C" cfust_status cfust_init(cfust_ctx* c, int nstarts, const int32_t* lab
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
         if (e != cudaSuccess) { s = fail(c, CFUST_ECUDA, std::string("cfust_init: ") + cudaGetErrorString(e)); break; }
         c->launches += (labels ? 0 : 1) + 2;
-        // line 9: cluster means, then the centred second and third moments
+        // cluster means, then the centred second and third moments
         std::vector<long long> nh(g);
         for (int h = 0; h < g; ++h) {
             nh[h] = (long long)s0[(size_t)h * W0];
@@ -1258,21 +1258,21 @@ extern "C" cfust_status cfust_init(cfust_ctx* c, int nstarts, const int32_t* lab
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
         if (e != cudaSuccess) { s = fail(c, CFUST_ECUDA, std::string("cfust_init: ") + cudaGetErrorString(e)); break; }
         c->launches += 2;
-        for (int a = 0; a < nalpha; ++a) {  // line 7
+        for (int a = 0; a < nalpha; ++a) {  // each alpha of the grid
             const double alpha = alphas[a];
             bool valid = true;
-            for (int h = 0; h < g && valid; ++h) {  // line 8
+            for (int h = 0; h < g && valid; ++h) {  // each cluster
                 if (nh[h] < 2) { valid = false; break; }
                 const double* Sr = s1.data() + (size_t)h * W1;  // packed lower sum r r^T, then sum r^3
                 auto Sab = [&](int x, int y2) {
                     const int hi = x > y2 ? x : y2, lo = x > y2 ? y2 : x;
                     return Sr[hi * (hi + 1) / 2 + lo] / (double)(nh[h] - 1);
                 };
-                cp[h] = (double)nh[h] / (double)n;  // line 6
+                cp[h] = (double)nh[h] / (double)n;  // pi from the cluster sizes
                 double* Dh = cD.data() + (size_t)h * p * q;
                 double* Sh = cS.data() + (size_t)h * p * p;
                 for (int t = 0; t < p * q; ++t) Dh[t] = 0.0;
-                // line 10, eq (23): delta = sign(m3) sqrt(pi (1 - alpha) s* / (pi - 2)) element-wise,
+                // eq (23): delta = sign(m3) sqrt(pi (1 - alpha) s* / (pi - 2)) element-wise,
                 // Sigma = S - (1 - alpha) diag(s*), mu = ybar - sqrt(2/pi) delta, nu = nu0; Delta is
                 // diag(delta) (q = p), the column delta (q = 1), else delta on the leading diagonal
                 for (int x = 0; x < p; ++x) {
@@ -1305,12 +1305,12 @@ extern "C" cfust_status cfust_init(cfust_ctx* c, int nstarts, const int32_t* lab
             if (valid) {
                 cfust_params P{cp.data(), cm.data(), cS.data(), cD.data(), cn.data()};
                 cfust_status r = cfust_set_params(c, &P);
-                if (r == CFUST_OK) r = cfust_loglik(c, &L);  // line 12
+                if (r == CFUST_OK) r = cfust_loglik(c, &L);  // the candidate's log-likelihood
                 if (r == CFUST_ECUDA || r == CFUST_ENOMEM) { s = r; break; }
                 if (r != CFUST_OK || !std::isfinite(L)) L = -INFINITY;
             }
             if (loglik_out) loglik_out[(size_t)st * nalpha + a] = L;
-            if (L > lbest) {  // lines 13-14, with l <- l*
+            if (L > lbest) {  // keep the best candidate (first maximum)
                 lbest = L;
                 ibest = st * nalpha + a;
                 bp = cp; bm = cm; bS = cS; bD = cD; bn = cn;

@@ -1,8 +1,8 @@
 // init.cu -- device parts of the initialisation of Sec. 3.3 (Algorithm 1):
-// random partitions (line 5) and the cluster moments that eq (23) needs
-// (line 9: sample mean, covariance and third moment of every cluster).
+// random partitions of the observations and the cluster moments that eq (23)
+// needs (sample mean, covariance and third moment of every cluster).
 // The per-cluster arithmetic of eq (23) is O(g p^2) and runs on the host in
-// FP64; each candidate's log-likelihood (line 12) is the library's density pass.
+// FP64; each candidate's log-likelihood is the library's density pass.
 #include "internal.cuh"
 
 // label_j = floor(u g), u = SplitMix64 output for key seed ^ ((start+1) << 40) ^ (j+1)

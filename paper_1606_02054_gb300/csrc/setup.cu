@@ -33,19 +33,6 @@ __device__ bool chol_dev(int n, const double* A, double* L)
     return true;
 }
 
-// inverse of a lower-triangular matrix (row-major)
-__device__ void trinv_dev(int n, const double* L, double* Li)
-{
-    for (int c = 0; c < n; ++c) {
-        for (int i = 0; i < n; ++i) {
-            if (i < c) { Li[i * n + c] = 0.0; continue; }
-            double s = (i == c) ? 1.0 : 0.0;
-            for (int k = c; k < i; ++k) s -= L[i * n + k] * Li[k * n + c];
-            Li[i * n + c] = s / L[i * n + i];
-        }
-    }
-}
-
 // Correlation Cholesky and 1/sqrt(diag) of an n x n scale matrix S.
 __device__ bool corr_chol_dev(int n, const double* S, double* dsc, double* Lc)
 {
