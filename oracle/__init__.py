@@ -72,6 +72,8 @@ def lib():
             L.ora_tkcdf.argtypes = [i, _dp, _dp, d, C.POINTER(Qmc), _dp]
             L.ora_tkcdf.restype = d
             L.ora_tk_moments.argtypes = [i, _dp, _dp, d, C.POINTER(Qmc), _dp, _dp]
+            L.ora_tk_joint.argtypes = [i, _dp, _dp, d, d, C.POINTER(Qmc), _dp, _dp]
+            L.ora_tk_joint.restype = d
             L.ora_tk_moments.restype = d
             L.ora_pair.argtypes = [i, i, _dp, _dp, _dp, _dp, d, C.POINTER(Qmc), _dp, _dp, _dp,
                                    _dp, _dp, _dp]
@@ -160,6 +162,18 @@ def tk_moments(b, V, nu, spec: Qmc | None = None):
     spec = spec or qmc()
     m1, m2 = np.zeros(k), np.zeros((k, k))
     a = lib().ora_tk_moments(k, _ptr(b), _ptr(V), float(nu), C.byref(spec), _ptr(m1), _ptr(m2))
+    return a, m1, m2
+
+
+def tk_joint(c, Lam, nud, k1, spec: Qmc | None = None):
+    """The single-pass estimator sharing alpha_s's lattice pass: (alpha at dof k1 + 2,
+    E[X | X <= c], E[X X^T | X <= c]) for X ~ t_k(0, (nud/(k1+2)) Lam, k1 + 2)."""
+    c = _f64(c).ravel()
+    k = c.size
+    Lam = _f64(Lam).reshape(k, k)
+    spec = spec or qmc()
+    m1, m2 = np.zeros(k), np.zeros((k, k))
+    a = lib().ora_tk_joint(k, _ptr(c), _ptr(Lam), float(nud), float(k1), C.byref(spec), _ptr(m1), _ptr(m2))
     return a, m1, m2
 
 

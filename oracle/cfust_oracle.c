@@ -568,6 +568,80 @@ static double tk_moments_qmc(int k, const double* b, const double* V, double nu,
     return alpha;
 }
 
+/* The single-pass reading of eqs (13), (16), (17), sharing the lattice pass of alpha_s.
+ * Each point of the pass at k1 = nu + p dof carries its chi-square(k1) variate W through
+ * s = sqrt(W/k1), which scales the standardised limits of alpha_s.  The chi-square density at
+ * k2 = k1 + 2 dof is the one at k1 times w/k1, so weighting every point by s^2 = W/k1 turns
+ * the pass into one at k2: the weighted mean is alpha = T_q(c sqrt(k2/(nu+d)); 0, Lambda, k2)
+ * of eq (13), and the weighted means of X = diag(S2)^{1/2} L y / s2, s2 = sqrt(W/k2),
+ * S2 = ((nu+d)/k2) Lambda, are the moments of the truncated t_q(0, S2, k2) of eqs (16)-(17).
+ * The unweighted mean of the same points is alpha_s (eq 4).  Returns alpha; m1 (k) and
+ * m2 (k x k) in the units of X.  stab: chi table at k1 dof (optional). */
+static double tk_joint_qmc(int k, const double* c, const double* Lam, double nud, double k1,
+                           const ora_qmc* qmc, const double* stab, double* m1, double* m2)
+{
+    const double k2 = k1 + 2.0;
+    double R[ORA_MAXQ * ORA_MAXQ], L[ORA_MAXQ * ORA_MAXQ], bt[ORA_MAXQ], dl[ORA_MAXQ];
+    for (int i = 0; i < k; ++i) dl[i] = sqrt(Lam[i * k + i]);
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) R[i * k + j] = Lam[i * k + j] / (dl[i] * dl[j]);
+    for (int i = 0; i < k; ++i) bt[i] = c[i] * sqrt(k1 / nud) / dl[i];
+    if (chol(k, R, L)) return NAN;
+    const double ratio = sqrt(k1 / k2);
+    const int N = qmc->npoints, M = qmc->nshifts;
+    double sw = 0.0, sx[ORA_MAXQ], sxx[ORA_MAXQ * ORA_MAXQ];
+    memset(sx, 0, sizeof(sx));
+    memset(sxx, 0, sizeof(sxx));
+    for (int m = 0; m < M; ++m) {
+        for (int i = 0; i < N; ++i) {
+            double w, wc, s;
+            if (stab) s = stab[(size_t)m * N + i];
+            else { lattice_w(qmc, i, m, 0, &w, &wc); s = sqrt(ora_chi2_quantile(w, wc, k1) / k1); }
+            double y[ORA_MAXQ];
+            double f = 1.0;
+            for (int r = 0; r < k; ++r) {
+                double acc = bt[r] * s;
+                for (int l = 0; l < r; ++l) acc -= L[r * k + l] * y[l];
+                double e = ora_phi(acc / L[r * k + r]);
+                if (e <= 1e-300) { f = 0.0; break; }
+                f *= e;
+                lattice_w(qmc, i, m, r + 1, &w, &wc);
+                double v = w * e;
+                if (v >= 1.0) v = 1.0 - 0x1.0p-53;
+                y[r] = ora_phi_inv(v);
+            }
+            if (f == 0.0) continue;
+            const double fw = f * s * s, s2 = s * ratio;
+            double x[ORA_MAXQ];
+            for (int r = 0; r < k; ++r) {
+                double z = 0.0;
+                for (int l = 0; l <= r; ++l) z += L[r * k + l] * y[l];
+                x[r] = z / s2;
+            }
+            sw += fw;
+            for (int a = 0; a < k; ++a) {
+                sx[a] += fw * x[a];
+                for (int c2 = 0; c2 < k; ++c2) sxx[a * k + c2] += fw * x[a] * x[c2];
+            }
+        }
+    }
+    const double alpha = sw / ((double)N * M);
+    for (int a = 0; a < k; ++a) {
+        const double sa = sqrt(nud / k2) * dl[a];
+        m1[a] = sw > 0.0 ? sx[a] / sw * sa : 0.0;
+        for (int c2 = 0; c2 < k; ++c2)
+            m2[a * k + c2] = sw > 0.0 ? sxx[a * k + c2] / sw * sa * sqrt(nud / k2) * dl[c2] : 0.0;
+    }
+    return alpha;
+}
+
+double ora_tk_joint(int k, const double* c, const double* Lam, double nud, double k1, const ora_qmc* qmc,
+                    double* m1, double* m2)
+{
+    if (k < 1 || k > ORA_MAXQ || !(k1 > 0.0) || !(nud > 0.0)) return NAN;
+    return tk_joint_qmc(k, c, Lam, nud, k1, qmc, NULL, m1, m2);
+}
+
 double ora_tk_moments(int k, const double* b, const double* V, double nu, const ora_qmc* qmc,
                       double* m1, double* m2)
 {
@@ -850,11 +924,10 @@ static int pair_core(const comp_t* C, const ora_qmc* qmc, const double* y, int d
     if (density_only) return 0;
 
     if (qmc->moments && q >= 3) {
-        /* eqs (13), (16), (17) from one lattice pass at dof nu+p+2: X ~ t_q(0, S2, nu+p+2),
-         * S2 = ((nu+d)/(nu+p+2)) Lambda, truncated to X <= c; U = c - X. */
-        double S2[ORA_MAXQ * ORA_MAXQ], m1[ORA_MAXQ], m2[ORA_MAXQ * ORA_MAXQ];
-        for (int i = 0; i < q * q; ++i) S2[i] = (nu + d) / (nu + p + 2.0) * C->Lambda[i];
-        double alpha = tk_moments_qmc(q, c, S2, nu + p + 2.0, qmc, C->stab[2], m1, m2);
+        /* eqs (13), (16), (17) from the lattice pass of alpha_s (points weighted by W/(nu+p)):
+         * X ~ t_q(0, S2, nu+p+2), S2 = ((nu+d)/(nu+p+2)) Lambda, truncated to X <= c; U = c - X. */
+        double m1[ORA_MAXQ], m2[ORA_MAXQ * ORA_MAXQ];
+        double alpha = tk_joint_qmc(q, c, C->Lambda, nu + d, nu + p, qmc, C->stab[0], m1, m2);
         double u = (nu + p) / (nu + d) * alpha / alpha_s;
         *u_out = u;
         *elogu_out = u - log(0.5 * (nu + d)) - (nu + p) / (nu + d) + ora_digamma(0.5 * (nu + p));

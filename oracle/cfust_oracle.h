@@ -71,6 +71,11 @@ double ora_tkcdf(int k, const double* b, const double* V, double nu,
  * on the lattice (dimension k + 1: the last coordinate is sampled too):
  * alpha = T_k(b; 0, V, nu), m1 = E[X | X <= b] (k), m2 = E[X X^T | X <= b]
  * (k x k).  Returns alpha. */
+/* The single-pass pass of alpha_s (dof k1 = nu + p, limits c sqrt(k1/nud), nud = nu + d) with
+ * points weighted by W/k1: returns alpha = T_k at dof k1 + 2 of c sqrt((k1+2)/nud), and the
+ * moments of X ~ t_k(0, (nud/(k1+2)) Lam, k1 + 2) truncated to X <= c. */
+double ora_tk_joint(int k, const double* c, const double* Lam, double nud, double k1, const ora_qmc* qmc,
+                    double* m1, double* m2);
 double ora_tk_moments(int k, const double* b, const double* V, double nu, const ora_qmc* qmc,
                       double* m1, double* m2);
 
