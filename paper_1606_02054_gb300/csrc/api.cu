@@ -15,7 +15,7 @@
 // kernels (defined in the other translation units)
 __global__ void setup_components_kernel(Dims, Layout, const double*, const double*, const double*,
                                         const double*, double*, int*);
-__global__ void chi_table_kernel(int, const double*, const double*, Lattice, const double*, double, double*,
+__global__ void chi_table_kernel(int, int, const double*, const double*, Lattice, const double*, double, double*,
                                  float*);
 __global__ void dof_consts_kernel(Dims, Layout, const double*, int, double*, double*, float*);
 __global__ void t1_table_kernel(int, const double*, float2*);
@@ -624,12 +624,14 @@ static cfust_status launch_setup(cfust_ctx* c)
     prof_end(c, CFUST_PROF_SETUP, 2 + (c->mixed ? 1 : 0) + (c->t1tab ? 1 : 0));
     if (c->q >= 3) {
         prof_begin(c, CFUST_PROF_CHI);
-        const long long total = 3LL * c->g * c->lat.N * c->lat.M;
+        // the single-pass E-step reads only the dof nu+p tables (index 3h)
+        const int every = c->single_pass ? 3 : 1;
+        const long long total = 3LL * c->g / every * c->lat.N * c->lat.M;
         const int blocks = (int)std::min<long long>((total + 127) / 128, 64LL * c->nsm);
         // the FP64 table serves the FP64 integrators; in the FP32 modes only the rare FP64
         // fix-up reads it, and 1e-9 is far inside what a pair sent there needs
         const double rtol = c->opts.precision == CFUST_PREC_FP64 ? 1e-15 : 1e-9;
-        chi_table_kernel<<<blocks, 128, 0, c->st>>>(3 * c->g, c->dofs, c->cst64, c->lat, c->shf64, rtol,
+        chi_table_kernel<<<blocks, 128, 0, c->st>>>(3 * c->g, every, c->dofs, c->cst64, c->lat, c->shf64, rtol,
                                                      c->chi64, c->chi32);
         LAUNCHED();
         prof_end(c, CFUST_PROF_CHI, 1);
@@ -689,6 +691,9 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
         prof_end(c, CFUST_PROF_SURROGATE, c->launches - n0);
     }
     for (int l = 0; l < (density_only || sp ? 1 : 3); ++l) {
+        // single-pass E-step: alpha_s comes from the moment pass (the same lattice points),
+        // so level 0 runs only for the surrogate's out-of-range records
+        if (l == 0 && sp && !density_only && !sur) continue;
         RecSet r = l == 0 ? pa.L0 : c->rec[l];
         n0 = c->launches;
         prof_begin(c, CFUST_PROF_LEVEL0 + l);
@@ -704,6 +709,8 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
         n0 = c->launches;
         prof_begin(c, CFUST_PROF_MOMENTS);
         RecSet rm = c->rec[3];
+        rm.res0 = pa.L0.res;  // alpha_s and its standard error from the same pass
+        rm.se0 = pa.L0.se;
         if (sur) {
             rm.sel = c->sur.fallM;
             rm.nsel = c->sur.nfall + 1;
@@ -1418,7 +1425,7 @@ extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const doub
         if (lattice) {
             const long long total = (long long)count * NM;
             const int blocks = (int)std::min<long long>((total + 127) / 128, 64LL * c->nsm);
-            chi_table_kernel<<<blocks, 128, 0, c->st>>>(count, r.dof, k64, c->lat, c->shf64,
+            chi_table_kernel<<<blocks, 128, 0, c->st>>>(count, 1, r.dof, k64, c->lat, c->shf64,
                                                          c->opts.precision == CFUST_PREC_FP64 ? 1e-15 : 1e-9,
                                                          t64, t32);
             c->launches++;

@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(128) fixup_kernel(EstepArgs a, const int* coun
     const int p = a.D.p, q = a.D.q, q1 = q - 1, q2 = q - 2;
     const int cnt = *count;
     const size_t NM = (size_t)a.lat.N * a.lat.M;
-    __shared__ double slot[4][CF_MAXQ + CF_MAXQ * (CF_MAXQ + 1) / 2 + 1];
+    __shared__ double slot[4][CF_MAXQ + CF_MAXQ * (CF_MAXQ + 1) / 2 + 3 + CF_MAXSHIFT];
     double* acc = slot[threadIdx.x >> 5];
     for (int i = warp; i < cnt; i += nwarps) {
         const long long pid = list[i];
@@ -57,16 +57,17 @@ __global__ void __launch_bounds__(128) fixup_kernel(EstepArgs a, const int* coun
         double alpha = 0.0, tq1[CF_MAXQ], tq2[CF_MAXQ * CF_MAXQ];
         if (a.single_pass && !a.density_only) {
             double m[CF_MAXQ + CF_MAXQ * (CF_MAXQ + 1) / 2];
-            limits_l0(F, a.Ly, p, q, c, d, 1, bt);
+            // the pass of alpha_s (bt still holds its limits) weighted to dof nu+p+2
             const double* Lq = F + fac_l0(a.Ly);
-            const double* chi2 = chi + 2 * NM;
+            const double rk = isinf(nu1) ? 1.0 : sqrt((nu1 + 2.0) / nu1);
+            double as = 0.0, sej = 0.0;
             switch (q) {
-            case 3: alpha = tk_lattice_mom_warp<double, 3>(bt, Lq, chi2, a.shf64, a.lat, lane, acc); break;
-            case 4: alpha = tk_lattice_mom_warp<double, 4>(bt, Lq, chi2, a.shf64, a.lat, lane, acc); break;
-            case 5: alpha = tk_lattice_mom_warp<double, 5>(bt, Lq, chi2, a.shf64, a.lat, lane, acc); break;
-            case 6: alpha = tk_lattice_mom_warp<double, 6>(bt, Lq, chi2, a.shf64, a.lat, lane, acc); break;
-            case 7: alpha = tk_lattice_mom_warp<double, 7>(bt, Lq, chi2, a.shf64, a.lat, lane, acc); break;
-            default: alpha = tk_lattice_mom_warp<double, 8>(bt, Lq, chi2, a.shf64, a.lat, lane, acc); break;
+            case 3: alpha = tk_lattice_mom_warp<double, 3>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej); break;
+            case 4: alpha = tk_lattice_mom_warp<double, 4>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej); break;
+            case 5: alpha = tk_lattice_mom_warp<double, 5>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej); break;
+            case 6: alpha = tk_lattice_mom_warp<double, 6>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej); break;
+            case 7: alpha = tk_lattice_mom_warp<double, 7>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej); break;
+            default: alpha = tk_lattice_mom_warp<double, 8>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej); break;
             }
             for (int k = 0; k < q + q * (q + 1) / 2; ++k) m[k] = acc[1 + k];
             __syncwarp();

@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(mom32_block<K>()) lattice_mom_kernel_32(RecSet
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const size_t NM = (size_t)a.lat.N * a.lat.M;
-    __shared__ double slot[mom32_block<K>() / CF_WARP][W + 1];
+    __shared__ double slot[mom32_block<K>() / CF_WARP][W + 3 + CF_MAXSHIFT];
     double* acc = slot[threadIdx.x >> 5];
     const long long nr = rec_count<SEL>(r);
     for (long long t = warp; t < nr; t += nwarps) {
@@ -25,9 +25,17 @@ __global__ void __launch_bounds__(mom32_block<K>()) lattice_mom_kernel_32(RecSet
         double bt[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) bt[k] = r.bt[i * K + k];
+        // the pass of alpha_s (chi table at dof k1 = dof - 2) weighted to dof k2 = r.dof
+        const double k2 = r.dof[i];
+        const float rk = isinf(k2) ? float(1) : (float)sqrt(k2 / (k2 - 2.0));
+        double as = 0.0, se = 0.0;
         const double v = tk_lattice_mom_warp<float, K>(bt, a.F + r.fac[i], a.chi32 + (size_t)r.tab[i] * NM,
-                                                      a.shf32, a.lat, lane, acc);
-        if (lane == 0) r.res[i] = v;
+                                                      a.shf32, a.lat, lane, acc, rk, &as, &se);
+        if (lane == 0) {
+            r.res[i] = v;
+            if (r.res0) r.res0[i] = as;
+            if (r.se0) r.se0[i] = se;
+        }
         for (int k = lane; k < W; k += CF_WARP) r.mom[i * W + k] = acc[1 + k];
         __syncwarp();  // the slot is reset by the next record
     }

@@ -12,7 +12,7 @@ __global__ void __launch_bounds__(256) lattice_mom_kernel_64(RecSet r, IntegArgs
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const size_t NM = (size_t)a.lat.N * a.lat.M;
-    __shared__ double slot[8][W + 1];
+    __shared__ double slot[8][W + 3 + CF_MAXSHIFT];
     double* acc = slot[threadIdx.x >> 5];
     const long long nr = rec_count<SEL>(r);
     for (long long t = warp; t < nr; t += nwarps) {
@@ -20,9 +20,17 @@ __global__ void __launch_bounds__(256) lattice_mom_kernel_64(RecSet r, IntegArgs
         double bt[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) bt[k] = r.bt[i * K + k];
+        // the pass of alpha_s (chi table at dof k1 = dof - 2) weighted to dof k2 = r.dof
+        const double k2 = r.dof[i];
+        const double rk = isinf(k2) ? double(1) : (double)sqrt(k2 / (k2 - 2.0));
+        double as = 0.0, se = 0.0;
         const double v = tk_lattice_mom_warp<double, K>(bt, a.F + r.fac[i], a.chi64 + (size_t)r.tab[i] * NM,
-                                                      a.shf64, a.lat, lane, acc);
-        if (lane == 0) r.res[i] = v;
+                                                      a.shf64, a.lat, lane, acc, rk, &as, &se);
+        if (lane == 0) {
+            r.res[i] = v;
+            if (r.res0) r.res0[i] = as;
+            if (r.se0) r.se0[i] = se;
+        }
         for (int k = lane; k < W; k += CF_WARP) r.mom[i * W + k] = acc[1 + k];
         __syncwarp();  // the slot is reset by the next record
     }

@@ -55,10 +55,11 @@ __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, long long
     }
     if (a.density_only) return;
     if (a.single_pass) {
-        limits_l0<float>(F, a.Ly, p, q, c, d, 1, bt);
+        // alpha and the moments at dof nu+p+2 from the pass of alpha_s: its limits and chi table
+        limits_l0<float>(F, a.Ly, p, q, c, d, 0, bt);
         for (int k = 0; k < q; ++k) a.LM.bt[pid * q + k] = bt[k];
         a.LM.fac[pid] = foff + fac_l0(a.Ly);
-        a.LM.tab[pid] = 3 * h + 2;
+        a.LM.tab[pid] = 3 * h;
         a.LM.dof[pid] = nu1d + 2.0;
         return;
     }
@@ -122,11 +123,12 @@ __global__ void __launch_bounds__(128) plan_kernel(PlanArgs a)
         }
         if (a.density_only) continue;
         if (a.single_pass) {
-            // alpha and the moments: one record at dof nu+p+2 (limits of eq 13)
-            limits_l0(F, a.Ly, p, q, c, d, 1, bt);
+            // alpha and the moments at dof nu+p+2 (eqs 13, 16, 17) from the pass of
+            // alpha_s: its limits and chi table, points weighted by W/(nu+p)
+            limits_l0(F, a.Ly, p, q, c, d, 0, bt);
             for (int k = 0; k < q; ++k) a.LM.bt[pid * q + k] = bt[k];
             a.LM.fac[pid] = foff + fac_l0(a.Ly);
-            a.LM.tab[pid] = 3 * h + 2;
+            a.LM.tab[pid] = 3 * h;
             a.LM.dof[pid] = nu1 + 2.0;
             continue;
         }

@@ -105,6 +105,8 @@ struct RecSet {
     float4* t2f;       // FP32 modes, k = 2 only (else null): per record two float4,
                        // (h, k, rho, dof) and (1 - rho^2, h|rho| - sign(rho) k, 0, 0),
                        // the last two formed in FP64, so the T_2 kernel runs no FP64
+    double* res0;      // moment records: alpha_s of the same pair from the shared pass (level 0
+    double* se0;       //   results and standard error; may be null)
     const int* sel;    // lattice kernels (k >= 3): if set, only records sel[0 .. *nsel)
     const int* nsel;   //   (the learned surrogate's fallback list; device count)
 };

@@ -165,16 +165,20 @@ __global__ void setup_components_kernel(Dims D, Layout Ly, const double* mu, con
 // Lattice coordinate 0: x = frac(i/N + shift(m, 0)), w = 1 - |2x - 1|.
 // rtol: Newton tolerance of the quantile (1e-15 when the FP64 table is used, 1e-9 when only
 // the FP32 table is); cst: the per-dof constants (lgamma(dof/2) at CST_LGA).
-__global__ void chi_table_kernel(int ndof, const double* __restrict__ dofs, const double* __restrict__ cst,
+// Tables k = 0, every, 2 every, ... < ndof (every = 3: only the dof nu+p tables,
+// all that the single-pass E-step reads).
+__global__ void chi_table_kernel(int ndof, int every, const double* __restrict__ dofs, const double* __restrict__ cst,
                                  Lattice lat, const double* __restrict__ shf, double rtol,
                                  double* __restrict__ t64, float* __restrict__ t32)
 {
-    const long long total = (long long)ndof * lat.M * lat.N;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(t % lat.N);
-        const int m = (int)((t / lat.N) % lat.M);
-        const int k = (int)(t / ((long long)lat.N * lat.M));
+    const long long NM = (long long)lat.M * lat.N;
+    const long long total = (long long)((ndof + every - 1) / every) * NM;
+    for (long long te = blockIdx.x * (long long)blockDim.x + threadIdx.x; te < total;
+         te += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(te % lat.N);
+        const int m = (int)((te / lat.N) % lat.M);
+        const int k = (int)(te / NM) * every;
+        const long long t = k * NM + (te % NM);
         const double dof = dofs[k];
         double x = (double)(((long long)i * lat.z[0]) % lat.N) / (double)lat.N + shf[m * CF_MAXDIM];
         if (x >= 1.0) x -= 1.0;

@@ -625,22 +625,28 @@ __device__ double tk_lattice_warp(const double* bt, const double* Lc, const R* _
 }
 
 // ---------------------------------------------------------------------------
-// Lattice T_K with the truncated moments, warp-cooperative.  The separation
-// of variables also samples the last coordinate (lattice dimension K), so
-// every point gives the standardised draw X = L y / s inside {X <= bt} with
-// weight f = prod e_i.  Returns alpha = mean f (as tk_lattice_warp) and leaves
-// the ratio estimators in acc_sm[1..K] (m1 = sum f X / sum f) and
-// acc_sm[1+K..K+K(K+1)/2] (m2 = sum f X X^T / sum f, lower triangle), visible
-// to the whole warp until the next call; they are accumulated in the whitened
-// coordinates y (X = L y / s) and mapped through L once per record.
+// Lattice T_K with the truncated moments, warp-cooperative: the pass of
+// alpha_s at k1 dof (chi table chi, limits bt) that also yields alpha and the
+// moments at k2 = k1 + 2 dof.  Each point carries s = sqrt(W/k1), W its
+// chi-square(k1) variate; the chi-square(k2) density is the chi-square(k1)
+// density times W/k1, so weighting a point by s^2 moves the pass to k2 dof.
+// The separation of variables also samples the last coordinate (lattice
+// dimension K), so every point gives the draw X = L y / s2 (standardised at
+// k2 dof, s2 = s sqrt(k1/k2); rk = sqrt(k2/k1), 1 in the normal limit) inside
+// the truncation region with weight f = prod e_i.  Returns alpha = mean f s^2;
+// *alpha_s = mean f (as tk_lattice_warp: the same points) and *se its standard
+// error over the shifts (all lanes).  Leaves the ratio estimators in
+// acc_sm[1..K] (m1 = sum f s^2 X / sum f s^2) and acc_sm[1+K..K+K(K+1)/2]
+// (m2, lower triangle), visible to the whole warp until the next call; they are
+// accumulated in the whitened coordinates y and mapped through L once per record.
 // ---------------------------------------------------------------------------
 template <typename R, int K>
 __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const R* __restrict__ chi,
                                       const R* __restrict__ shf, const Lattice& lat, int lane,
-                                      double* acc_sm)
+                                      double* acc_sm, R rk, double* alpha_s, double* se)
 {
-    // acc_sm: this warp's shared-memory slot of K + K(K+1)/2 + 1 doubles that
-    // lane 0 uses for the running totals over the shifts
+    // acc_sm: this warp's shared-memory slot of K + K(K+1)/2 + 3 + CF_MAXSHIFT doubles
+    // that lane 0 uses for the running totals and the per-shift sums of f
     constexpr int K2 = K * (K + 1) / 2;
     R b[K], invd[K], Lf[K][K];
 #pragma unroll
@@ -668,7 +674,7 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
             xs[d] = x0[d] + shf[m * CF_MAXDIM + d];
             if (xs[d] >= R(1)) xs[d] -= R(1);
         }
-        R af = R(0), a1[K], a2[K2];
+        R af = R(0), aw = R(0), a1[K], a2[K2];
 #pragma unroll
         for (int r = 0; r < K; ++r) a1[r] = R(0);
 #pragma unroll
@@ -692,15 +698,16 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
                 y[r] = m_ncdfinv(v);
                 if (e <= Lim<R>::tiny()) f = R(0);
             }
-            // X = L y / s is linear in y: accumulate f y / s and f y y^T / s^2
-            // here and apply L once per record at the end
-            const R is = m_rcp(s);
-            const R fs = f * is, fs2 = fs * is;
+            // weight f s^2; X = L y / s2 is linear in y: accumulate f s^2 y / s2 =
+            // f s rk y and f s^2 y y^T / s2^2 = f rk^2 y y^T, and apply L once per record
+            const R fs = f * s;
+            const R w1 = fs * rk, w2 = f * (rk * rk);
             af += f;
+            aw += fs * s;
 #pragma unroll
             for (int r = 0; r < K; ++r) {
-                a1[r] += fs * y[r];
-                const R t = fs2 * y[r];
+                a1[r] += w1 * y[r];
+                const R t = w2 * y[r];
 #pragma unroll
                 for (int c = 0; c <= r; ++c) a2[r * (r + 1) / 2 + c] += t * y[c];
             }
@@ -711,12 +718,14 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
             }
         }
         af = warp_sum(af);
+        aw = warp_sum(aw);
 #pragma unroll
         for (int r = 0; r < K; ++r) a1[r] = warp_sum(a1[r]);
 #pragma unroll
         for (int r = 0; r < K2; ++r) a2[r] = warp_sum(a2[r]);
         if (lane == 0) {
-            acc_sm[0] += (double)af;
+            acc_sm[3 + K + K2 + m] = (double)af;  // alpha_s: this shift's sum
+            acc_sm[0] += (double)aw;
 #pragma unroll
             for (int r = 0; r < K; ++r) acc_sm[1 + r] += (double)a1[r];
 #pragma unroll
@@ -758,5 +767,19 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
     }
     __syncwarp();
     __syncwarp();
+    if (lane == 0) {  // alpha_s: mean of the shift means and its standard error (Welford)
+        double mean = 0.0, m2 = 0.0;
+        for (int m = 0; m < M; ++m) {
+            const double smean = acc_sm[3 + K + K2 + m] / (double)N;
+            const double delta = smean - mean;
+            mean += delta / (double)(m + 1);
+            m2 += delta * (smean - mean);
+        }
+        acc_sm[1 + K + K2] = mean;
+        acc_sm[2 + K + K2] = M > 1 ? sqrt(m2 / (double)(M - 1) / (double)M) : 0.0;
+    }
+    __syncwarp();
+    *alpha_s = acc_sm[1 + K + K2];
+    *se = acc_sm[2 + K + K2];
     return Sf / ((double)N * M);
 }
