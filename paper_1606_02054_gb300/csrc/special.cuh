@@ -680,8 +680,10 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
 #pragma unroll
         for (int r = 0; r < K2; ++r) a2[r] = R(0);
         const R* __restrict__ crow = chi + (size_t)m * N;
+        R s_next = lane < N ? crow[lane] : R(1);  // the chi value one point ahead
         for (int i = lane; i < N; i += CF_WARP) {
-            const R s = crow[i];
+            const R s = s_next;
+            if (i + CF_WARP < N) s_next = crow[i + CF_WARP];
             R y[K];
             R f = R(1);
 #pragma unroll
