@@ -392,7 +392,9 @@ cfust_status cfust_surrogate_train(cfust_ctx* ctx, const cfust_surrogate_opts* o
 cfust_status cfust_surrogate_use(cfust_ctx* ctx, int on);
 
 /* Records evaluated and records left to the lattice by the last E-step's
- * surrogate pass (both sets). */
+ * surrogate pass (both sets; in a full E-step a pair whose level-0 or moment
+ * record leaves the training range has both records taken by the shared
+ * lattice pass). */
 cfust_status cfust_surrogate_info(cfust_ctx* ctx, int64_t* records, int64_t* fallbacks);
 
 /* Copy the trained parameters (NPARAM floats) and statistics (NSTAT floats)

@@ -680,20 +680,27 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
         c->sur.last_records = pa.L0.nrec + (density_only ? 0 : c->rec[3].nrec);
         n0 = c->launches;
         prof_begin(c, CFUST_PROF_SURROGATE);
-        if ((e = sur_infer(c->sur, pa.L0, c->F, 0, c->sur.fall0, c->sur.nfall, c->st)) != cudaSuccess)
-            return fail(c, CFUST_ECUDA, std::string("surrogate kernel: ") + cudaGetErrorString(e));
-        ++c->launches;
-        if (!density_only) {
-            if ((e = sur_infer(c->sur, c->rec[3], c->F, 1, c->sur.fallM, c->sur.nfall + 1, c->st)) != cudaSuccess)
+        if (density_only) {
+            if ((e = sur_infer(c->sur, pa.L0, c->F, 0, c->sur.fall0, c->sur.nfall, c->st)) != cudaSuccess)
                 return fail(c, CFUST_ECUDA, std::string("surrogate kernel: ") + cudaGetErrorString(e));
             ++c->launches;
+        } else {
+            // moment records first (marking the pairs they leave to the lattice); a level-0
+            // record out of range sends its pair to the same list, since the shared lattice
+            // pass gives alpha_s as well
+            if ((e = sur_infer(c->sur, c->rec[3], c->F, 1, c->sur.fallM, c->sur.nfall + 1, c->st,
+                               c->sur.mark)) != cudaSuccess ||
+                (e = sur_infer(c->sur, pa.L0, c->F, 0, c->sur.fallM, c->sur.nfall + 1, c->st, c->sur.mark)) !=
+                    cudaSuccess)
+                return fail(c, CFUST_ECUDA, std::string("surrogate kernel: ") + cudaGetErrorString(e));
+            c->launches += 2;
         }
         prof_end(c, CFUST_PROF_SURROGATE, c->launches - n0);
     }
     for (int l = 0; l < (density_only || sp ? 1 : 3); ++l) {
         // single-pass E-step: alpha_s comes from the moment pass (the same lattice points),
-        // so level 0 runs only for the surrogate's out-of-range records
-        if (l == 0 && sp && !density_only && !sur) continue;
+        // also for the surrogate's out-of-range pairs; level 0 runs only in density passes
+        if (l == 0 && sp && !density_only) continue;
         RecSet r = l == 0 ? pa.L0 : c->rec[l];
         n0 = c->launches;
         prof_begin(c, CFUST_PROF_LEVEL0 + l);
@@ -1523,7 +1530,9 @@ extern "C" cfust_status cfust_surrogate_info(cfust_ctx* c, int64_t* records, int
         CU(cudaStreamSynchronize(c->st));
     }
     if (records) *records = c->sur.last_records;
-    if (fallbacks) *fallbacks = (int64_t)nf[0] + nf[1];
+    // a pair in the moment list has both of its records (alpha_s, and alpha with the
+    // moments) evaluated by the shared lattice pass
+    if (fallbacks) *fallbacks = (int64_t)nf[0] + 2 * (int64_t)nf[1];
     return CFUST_OK;
 }
 

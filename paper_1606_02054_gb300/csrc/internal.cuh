@@ -336,6 +336,7 @@ struct Surrogate {
     double* host_part = nullptr;
     // fallback lists of the E-step
     int *fall0 = nullptr, *fallM = nullptr, *nfall = nullptr;
+    unsigned char* mark = nullptr;  // per pair: its moment record is in fallM
     long long last_records = 0;
     float hstats[MLP_NSTAT] = {};  // host copy of stats (standardisation fixed at the first training)
 };
@@ -344,5 +345,7 @@ cudaError_t sur_reserve(Surrogate& s, int q, long long records, cudaStream_t st)
 void sur_free(Surrogate& s);
 cudaError_t sur_collect(Surrogate& s, const RecSet& L0, const RecSet& LM, const double* F, cudaStream_t st);
 cudaError_t sur_train(Surrogate& s, const SurOpts& o, cudaStream_t st, double* losses);
+// mark (optional): with moments = 1 records which pairs went to the fallback list;
+// with moments = 0 a level-0 record whose pair is marked is not appended again
 cudaError_t sur_infer(const Surrogate& s, const RecSet& r, const double* F, int moments, int* fall, int* nfall,
-                      cudaStream_t st);
+                      cudaStream_t st, unsigned char* mark = nullptr);

@@ -423,6 +423,8 @@ struct InferArgs {
     const double* F;
     int* fall;
     int* nfall;
+    unsigned char* mark;  // moment records: mark[i] = 1 when record i went to the fallback list;
+                          // level-0 records with mark set: skip pairs already in that list
 };
 
 constexpr int INF_WARPS = 8, INF_ROWS = 16;
@@ -586,6 +588,7 @@ __global__ void __launch_bounds__(INF_WARPS * 32, 1) mlp_infer_kernel(InferArgs 
         __syncwarp();
         if (lane < INF_ROWS && i < nrec) {
             const float* row = tile + lane * TILE_LD;
+            if (a.mark && a.moments) a.mark[i] = ok[lane] ? 0 : 1;
             if (ok[lane]) {
                 const double logT = (double)(row[0] * tstd[0] + tmean[0]);
                 a.r.res[i] = exp(logT);
@@ -609,7 +612,7 @@ __global__ void __launch_bounds__(INF_WARPS * 32, 1) mlp_infer_kernel(InferArgs 
                             out[q + r2 * (r2 + 1) / 2 + c2] = sm;
                         }
                 }
-            } else {
+            } else if (!(a.mark && !a.moments && a.mark[i])) {
                 a.fall[atomicAdd(a.nfall, 1)] = (int)i;
             }
         }
@@ -779,10 +782,12 @@ cudaError_t sur_reserve(Surrogate& s, int q, long long records, cudaStream_t)
     s.nin = q + q * (q - 1) / 2 + 1;
     s.nout = 1 + q + q * (q + 1) / 2;
     if (s.cap < records) {
-        cudaFree(s.fall0); cudaFree(s.fallM);
+        cudaFree(s.fall0); cudaFree(s.fallM); cudaFree(s.mark);
         s.fall0 = s.fallM = nullptr;
+        s.mark = nullptr;
         s.cap = 0;
-        if ((e = dalloc(&s.fall0, records)) || (e = dalloc(&s.fallM, records))) return e;
+        if ((e = dalloc(&s.fall0, records)) || (e = dalloc(&s.fallM, records)) || (e = dalloc(&s.mark, records)))
+            return e;
         s.cap = records;
     }
     return cudaSuccess;
@@ -791,7 +796,8 @@ cudaError_t sur_reserve(Surrogate& s, int q, long long records, cudaStream_t)
 void sur_free(Surrogate& s)
 {
     void* ps[] = {s.theta, s.grad, s.am, s.av, s.stats, s.wb, s.wf, s.X, s.T, s.type, s.count, s.xb, s.h1,
-                  s.h2, s.h3, s.dz, s.dz2, s.one, s.y, s.tb, s.mb, s.part, s.lpart, s.fall0, s.fallM, s.nfall};
+                  s.h2, s.h3, s.dz, s.dz2, s.one, s.y, s.tb, s.mb, s.part, s.lpart, s.fall0, s.fallM, s.nfall,
+                  s.mark};
     for (void* p : ps) cudaFree(p);
     cudaFreeHost(s.host_part);
     s = Surrogate{};
@@ -931,13 +937,13 @@ cudaError_t sur_train(Surrogate& s, const SurOpts& o, cudaStream_t st, double* l
 }
 
 cudaError_t sur_infer(const Surrogate& s, const RecSet& r, const double* F, int moments, int* fall, int* nfall,
-                      cudaStream_t st)
+                      cudaStream_t st, unsigned char* mark)
 {
     if (r.nrec == 0) return cudaSuccess;
     InferArgs a;
     a.wf = (const uint2*)s.wf; a.theta = s.theta; a.stats = s.stats; a.margin = s.margin;
     a.q = s.q; a.nin = s.nin; a.nout = s.nout; a.moments = moments;
-    a.r = r; a.F = F; a.fall = fall; a.nfall = nfall;
+    a.r = r; a.F = F; a.fall = fall; a.nfall = nfall; a.mark = mark;
     const long long groups = (r.nrec + INF_WARPS * INF_ROWS - 1) / (INF_WARPS * INF_ROWS);
     const int nsm = sm_count();
     const int blocks = (int)(groups < nsm ? groups : nsm);
