@@ -54,6 +54,7 @@ struct cfust_ctx {
     float* chi32 = nullptr;
     double* shf64 = nullptr;
     float* shf32 = nullptr;
+    float4* wtab = nullptr;  // FP32 single pass: lattice coordinates of every (shift, point)
     double *glx64 = nullptr, *glw64 = nullptr;
     float *glx32 = nullptr, *glw32 = nullptr;
     float *glx32h = nullptr, *glw32h = nullptr;  // T2_NH nodes for graded T_2 pieces
@@ -289,7 +290,7 @@ static void free_all(cfust_ctx* c)
 {
     sur_free(c->sur);
     void* bufs[] = {c->y, c->pi, c->mu, c->Sigma, c->Delta, c->nu, c->pi_n, c->mu_n, c->Sigma_n,
-                    c->Delta_n, c->nu_n, c->F, c->dofs, c->cst64, c->cst32, c->chi64, c->chi32, c->shf64, c->shf32,
+                    c->Delta_n, c->nu_n, c->F, c->dofs, c->cst64, c->cst32, c->chi64, c->chi32, c->shf64, c->shf32, c->wtab,
                     c->glx64, c->glw64, c->glx32, c->glw32, c->glx32h, c->glw32h, c->logf, c->u, c->elogu, c->eu,
                     c->euu, c->se, c->tau, c->partial, c->stats, c->flags, c->comp_status,
                     c->stage32, c->pd, c->pc, c->fix_count, c->fix_list, c->y32, c->F32, c->t1tab};
@@ -488,6 +489,24 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     };
     cp(c->shf64, s64.data(), sizeof(double) * s64.size());
     cp(c->shf32, s32.data(), sizeof(float) * s32.size());
+    if (c->single_pass && o.precision != CFUST_PREC_FP64) {
+        // baker-transformed lattice coordinates d = 1..q of every (shift, point), FP64 -> FP32
+        const int N = o.qmc_points, M = o.qmc_shifts, WQ = (q + 3) / 4;
+        std::vector<float> wt((size_t)M * N * 4 * WQ, 0.0f);
+        for (int m = 0; m < M; ++m)
+            for (int i = 0; i < N; ++i)
+                for (int d = 1; d <= q; ++d) {
+                    double x = (double)(((long long)i * c->lat.z[d]) % N) / (double)N + s64[m * CF_MAXDIM + d];
+                    if (x >= 1.0) x -= 1.0;
+                    wt[((size_t)m * N + i) * 4 * WQ + (d - 1)] = (float)(1.0 - std::fabs(2.0 * x - 1.0));
+                }
+        if (cudaMalloc((void**)&c->wtab, sizeof(float) * wt.size()) != cudaSuccess) {
+            free_all(c);
+            delete c;
+            return fail(nullptr, CFUST_ENOMEM, "cfust_create: cudaMalloc failed (lattice coordinates)");
+        }
+        cp(c->wtab, wt.data(), sizeof(float) * wt.size());
+    }
     cp(c->glx64, gx.data(), sizeof(double) * gx.size());
     cp(c->glw64, gw.data(), sizeof(double) * gw.size());
     cp(c->glx32, gx32.data(), sizeof(float) * gx32.size());
@@ -649,6 +668,7 @@ static IntegArgs integ_args(const cfust_ctx* c)
     ia.t2n = c->t2n;
     ia.glx32h = c->glx32h; ia.glw32h = c->glw32h;
     ia.t1tab = c->t1tab;
+    ia.wtab = c->wtab;
     return ia;
 }
 

@@ -4,13 +4,16 @@
 #include "internal.cuh"
 #include "special.cuh"
 
-// K = 7, 8 need 147-168 registers: blocks of 4 warps let 3 blocks (12 warps) share
-// an SM where one block of 8 would leave it at 8
+// Blocks of 4 warps.  K = 7, 8 need 147-168 registers: 3 such blocks (12 warps) share an
+// SM where one block of 8 would leave it at 8.  K <= 4 (with the coordinate table: 73
+// registers) is capped at 72 so that 7 blocks (28 warps) fit where blocks of 8 fit 24.
 template <int K>
-__host__ __device__ constexpr int mom32_block() { return K >= 7 ? 128 : 256; }
+__host__ __device__ constexpr int mom32_block() { return K >= 7 || K <= 4 ? 128 : 256; }
+template <int K>
+__host__ __device__ constexpr int mom32_minb() { return K <= 4 ? 7 : 1; }
 
 template <int K, bool SEL>
-__global__ void __launch_bounds__(mom32_block<K>()) lattice_mom_kernel_32(RecSet r, IntegArgs a)
+__global__ void __launch_bounds__(mom32_block<K>(), mom32_minb<K>()) lattice_mom_kernel_32(RecSet r, IntegArgs a)
 {
     constexpr int W = K + K * (K + 1) / 2;
     const int lane = threadIdx.x & (CF_WARP - 1);
@@ -29,8 +32,8 @@ __global__ void __launch_bounds__(mom32_block<K>()) lattice_mom_kernel_32(RecSet
         const double k2 = r.dof[i];
         const float rk = isinf(k2) ? float(1) : (float)sqrt(k2 / (k2 - 2.0));
         double as = 0.0, se = 0.0;
-        const double v = tk_lattice_mom_warp<float, K>(bt, a.F + r.fac[i], a.chi32 + (size_t)r.tab[i] * NM,
-                                                      a.shf32, a.lat, lane, acc, rk, &as, &se);
+        const double v = tk_lattice_mom_warp<float, K, true>(bt, a.F + r.fac[i], a.chi32 + (size_t)r.tab[i] * NM,
+                                                            a.shf32, a.lat, lane, acc, rk, &as, &se, a.wtab);
         if (lane == 0) {
             r.res[i] = v;
             if (r.res0) r.res0[i] = as;
@@ -52,8 +55,8 @@ static void go(const RecSet& r, const IntegArgs& a, int blocks, int threads, cud
 cudaError_t launch_mom32(int k, const RecSet& r, const IntegArgs& a, int blocks, cudaStream_t st)
 {
     switch (k) {
-    case 3: go<3>(r, a, blocks, 256, st); break;
-    case 4: go<4>(r, a, blocks, 256, st); break;
+    case 3: go<3>(r, a, 2 * blocks, 128, st); break;  // same warps
+    case 4: go<4>(r, a, 2 * blocks, 128, st); break;
     case 5: go<5>(r, a, blocks, 256, st); break;
     case 6: go<6>(r, a, blocks, 256, st); break;
     case 7: go<7>(r, a, 2 * blocks, 128, st); break;  // same warps

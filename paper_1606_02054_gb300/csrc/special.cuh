@@ -640,11 +640,16 @@ __device__ double tk_lattice_warp(const double* bt, const double* Lc, const R* _
 // (m2, lower triangle), visible to the whole warp until the next call; they are
 // accumulated in the whitened coordinates y and mapped through L once per record.
 // ---------------------------------------------------------------------------
-template <typename R, int K>
+// TAB (FP32 only): the baker-transformed coordinates of each point come from wtab
+// ((K+3)/4 float4 per (shift, point), see IntegArgs::wtab) instead of being advanced
+// in floating point here.
+template <typename R, int K, bool TAB = false>
 __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const R* __restrict__ chi,
                                       const R* __restrict__ shf, const Lattice& lat, int lane,
-                                      double* acc_sm, R rk, double* alpha_s, double* se)
+                                      double* acc_sm, R rk, double* alpha_s, double* se,
+                                      const float4* __restrict__ wtab = nullptr)
 {
+    constexpr int WQ = (K + 3) / 4;
     // acc_sm: this warp's shared-memory slot of K + K(K+1)/2 + 3 + CF_MAXSHIFT doubles
     // that lane 0 uses for the running totals and the per-shift sums of f
     constexpr int K2 = K * (K + 1) / 2;
@@ -681,9 +686,27 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
         for (int r = 0; r < K2; ++r) a2[r] = R(0);
         const R* __restrict__ crow = chi + (size_t)m * N;
         R s_next = lane < N ? crow[lane] : R(1);  // the chi value one point ahead
+        const float4* __restrict__ wrow = TAB ? wtab + (size_t)m * N * WQ : nullptr;
+        float4 w_next[WQ];  // TAB: the coordinates one point ahead
+        if constexpr (TAB) {
+#pragma unroll
+            for (int u = 0; u < WQ; ++u) w_next[u] = lane < N ? wrow[(size_t)lane * WQ + u] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         for (int i = lane; i < N; i += CF_WARP) {
             const R s = s_next;
             if (i + CF_WARP < N) s_next = crow[i + CF_WARP];
+            float wc[4 * WQ];
+            if constexpr (TAB) {
+#pragma unroll
+                for (int u = 0; u < WQ; ++u) {
+                    wc[4 * u] = w_next[u].x; wc[4 * u + 1] = w_next[u].y;
+                    wc[4 * u + 2] = w_next[u].z; wc[4 * u + 3] = w_next[u].w;
+                }
+                if (i + CF_WARP < N) {
+#pragma unroll
+                    for (int u = 0; u < WQ; ++u) w_next[u] = wrow[(size_t)(i + CF_WARP) * WQ + u];
+                }
+            }
             R y[K];
             R f = R(1);
 #pragma unroll
@@ -693,7 +716,9 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
                 for (int l = 0; l < r; ++l) a -= Lf[r][l] * y[l];
                 const R e = m_ncdf(a * invd[r]);
                 f *= e;
-                const R w = R(1) - m_abs(R(2) * xs[r + 1] - R(1));
+                R w;
+                if constexpr (TAB) w = (R)wc[r];
+                else w = R(1) - m_abs(R(2) * xs[r + 1] - R(1));
                 R v = w * e;
                 v = v < Lim<R>::vmin() ? Lim<R>::vmin() : v;
                 v = v > Lim<R>::one_minus_ulp() ? Lim<R>::one_minus_ulp() : v;
@@ -713,10 +738,12 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
 #pragma unroll
                 for (int c = 0; c <= r; ++c) a2[r * (r + 1) / 2 + c] += t * y[c];
             }
+            if constexpr (!TAB) {
 #pragma unroll
-            for (int d = 1; d <= K; ++d) {
-                const R t = xs[d] - omdx[d];
-                xs[d] = t >= R(0) ? t : xs[d] + dx[d];
+                for (int d = 1; d <= K; ++d) {
+                    const R t = xs[d] - omdx[d];
+                    xs[d] = t >= R(0) ? t : xs[d] + dx[d];
+                }
             }
         }
         af = warp_sum(af);
