@@ -489,8 +489,9 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     };
     cp(c->shf64, s64.data(), sizeof(double) * s64.size());
     cp(c->shf32, s32.data(), sizeof(float) * s32.size());
-    if (c->single_pass && o.precision != CFUST_PREC_FP64) {
+    if (c->single_pass && o.precision != CFUST_PREC_FP64 && q <= 4) {
         // baker-transformed lattice coordinates d = 1..q of every (shift, point), FP64 -> FP32
+        // (read by the FP32 moment pass at q <= 4)
         const int N = o.qmc_points, M = o.qmc_shifts, WQ = (q + 3) / 4;
         std::vector<float> wt((size_t)M * N * 4 * WQ, 0.0f);
         for (int m = 0; m < M; ++m)

@@ -9,8 +9,11 @@
 // registers) is capped at 72 so that 7 blocks (28 warps) fit where blocks of 8 fit 24.
 template <int K>
 __host__ __device__ constexpr int mom32_block() { return K >= 7 || K <= 4 ? 128 : 256; }
+// minimum resident blocks (an explicit 1 would let ptxas take up to 255 registers: K = 6
+// went from 128 to 154, halving its resident warps): K <= 4: 7 (72 registers); K = 5, 6: 2
+// (128); K = 7, 8: 3 (170)
 template <int K>
-__host__ __device__ constexpr int mom32_minb() { return K <= 4 ? 7 : 1; }
+__host__ __device__ constexpr int mom32_minb() { return K <= 4 ? 7 : (K <= 6 ? 2 : 3); }
 
 template <int K, bool SEL>
 __global__ void __launch_bounds__(mom32_block<K>(), mom32_minb<K>()) lattice_mom_kernel_32(RecSet r, IntegArgs a)
@@ -32,8 +35,15 @@ __global__ void __launch_bounds__(mom32_block<K>(), mom32_minb<K>()) lattice_mom
         const double k2 = r.dof[i];
         const float rk = isinf(k2) ? float(1) : (float)sqrt(k2 / (k2 - 2.0));
         double as = 0.0, se = 0.0;
-        const double v = tk_lattice_mom_warp<float, K, true>(bt, a.F + r.fac[i], a.chi32 + (size_t)r.tab[i] * NM,
-                                                            a.shf32, a.lat, lane, acc, rk, &as, &se, a.wtab);
+        // the coordinate table only at K <= 4 (one float4 per point, with the 4-warp blocks
+        // it pays for); at K = 6 it measured 1.6x slower than advancing the coordinates
+        double v;
+        if constexpr (K <= 4)
+            v = tk_lattice_mom_tab_warp<float, K>(bt, a.F + r.fac[i], a.chi32 + (size_t)r.tab[i] * NM, a.shf32,
+                                                  a.lat, lane, acc, rk, &as, &se, a.wtab);
+        else
+            v = tk_lattice_mom_warp<float, K>(bt, a.F + r.fac[i], a.chi32 + (size_t)r.tab[i] * NM, a.shf32,
+                                              a.lat, lane, acc, rk, &as, &se);
         if (lane == 0) {
             r.res[i] = v;
             if (r.res0) r.res0[i] = as;

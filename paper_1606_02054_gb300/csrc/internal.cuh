@@ -171,9 +171,9 @@ struct IntegArgs {
     // uniform in v = asinh(|z|)/ln 2 over [0, T1TAB_V], with d/dv (float2 each);
     // NULL: the continued fraction is used instead
     const float2* t1tab;
-    // FP32 single-pass moments: per shift m and lattice point i, the baker-transformed
-    // coordinates w_d = 1 - |2 frac(i z_d / N + shift_md) - 1|, d = 1..q, in (q+3)/4 float4
-    // (computed in FP64 at creation; they are the same for every record)
+    // FP32 single-pass moments at q <= 4 (else null): per shift m and lattice point i, the
+    // baker-transformed coordinates w_d = 1 - |2 frac(i z_d / N + shift_md) - 1|, d = 1..q,
+    // in one float4 (computed in FP64 at creation; they are the same for every record)
     const float4* wtab;
 };
 

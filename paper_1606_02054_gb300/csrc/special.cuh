@@ -640,11 +640,160 @@ __device__ double tk_lattice_warp(const double* bt, const double* Lc, const R* _
 // (m2, lower triangle), visible to the whole warp until the next call; they are
 // accumulated in the whitened coordinates y and mapped through L once per record.
 // ---------------------------------------------------------------------------
-// TAB (FP32 only): the baker-transformed coordinates of each point come from wtab
-// ((K+3)/4 float4 per (shift, point), see IntegArgs::wtab) instead of being advanced
-// in floating point here.
-template <typename R, int K, bool TAB = false>
+template <typename R, int K>
 __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const R* __restrict__ chi,
+                                      const R* __restrict__ shf, const Lattice& lat, int lane,
+                                      double* acc_sm, R rk, double* alpha_s, double* se)
+{
+    // acc_sm: this warp's shared-memory slot of K + K(K+1)/2 + 3 + CF_MAXSHIFT doubles
+    // that lane 0 uses for the running totals and the per-shift sums of f
+    constexpr int K2 = K * (K + 1) / 2;
+    R b[K], invd[K], Lf[K][K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        b[r] = (R)bt[r];
+        invd[r] = R(1) / (R)Lc[r * K + r];
+#pragma unroll
+        for (int l = 0; l < K; ++l) Lf[r][l] = l <= r ? (R)Lc[r * K + l] : R(0);
+    }
+    const int N = lat.N, M = lat.M;
+    const R invN = R(1) / (R)N;
+    R x0[K + 1], dx[K + 1], omdx[K + 1];  // lattice coordinates as in tk_lattice_warp
+#pragma unroll
+    for (int d = 1; d <= K; ++d) {
+        dx[d] = (R)(((long long)CF_WARP * lat.z[d]) % N) * invN;
+        omdx[d] = R(1) - dx[d];
+        x0[d] = (R)(((long long)lane * lat.z[d]) % N) * invN;
+    }
+    for (int r = lane; r <= K + K2; r += CF_WARP) acc_sm[r] = 0.0;
+    __syncwarp();
+    for (int m = 0; m < M; ++m) {
+        R xs[K + 1];
+#pragma unroll
+        for (int d = 1; d <= K; ++d) {
+            xs[d] = x0[d] + shf[m * CF_MAXDIM + d];
+            if (xs[d] >= R(1)) xs[d] -= R(1);
+        }
+        R af = R(0), aw = R(0), a1[K], a2[K2];
+#pragma unroll
+        for (int r = 0; r < K; ++r) a1[r] = R(0);
+#pragma unroll
+        for (int r = 0; r < K2; ++r) a2[r] = R(0);
+        const R* __restrict__ crow = chi + (size_t)m * N;
+        R s_next = lane < N ? crow[lane] : R(1);  // the chi value one point ahead
+        for (int i = lane; i < N; i += CF_WARP) {
+            const R s = s_next;
+            if (i + CF_WARP < N) s_next = crow[i + CF_WARP];
+            R y[K];
+            R f = R(1);
+#pragma unroll
+            for (int r = 0; r < K; ++r) {
+                R a = b[r] * s;
+#pragma unroll
+                for (int l = 0; l < r; ++l) a -= Lf[r][l] * y[l];
+                const R e = m_ncdf(a * invd[r]);
+                f *= e;
+                const R w = R(1) - m_abs(R(2) * xs[r + 1] - R(1));
+                R v = w * e;
+                v = v < Lim<R>::vmin() ? Lim<R>::vmin() : v;
+                v = v > Lim<R>::one_minus_ulp() ? Lim<R>::one_minus_ulp() : v;
+                y[r] = m_ncdfinv(v);
+                if (e <= Lim<R>::tiny()) f = R(0);
+            }
+            // weight f s^2; X = L y / s2 is linear in y: accumulate f s^2 y / s2 =
+            // f s rk y and f s^2 y y^T / s2^2 = f rk^2 y y^T, and apply L once per record
+            const R fs = f * s;
+            const R w1 = fs * rk, w2 = f * (rk * rk);
+            af += f;
+            aw += fs * s;
+#pragma unroll
+            for (int r = 0; r < K; ++r) {
+                a1[r] += w1 * y[r];
+                const R t = w2 * y[r];
+#pragma unroll
+                for (int c = 0; c <= r; ++c) a2[r * (r + 1) / 2 + c] += t * y[c];
+            }
+#pragma unroll
+            for (int d = 1; d <= K; ++d) {
+                const R t = xs[d] - omdx[d];
+                xs[d] = t >= R(0) ? t : xs[d] + dx[d];
+            }
+        }
+        af = warp_sum(af);
+        aw = warp_sum(aw);
+#pragma unroll
+        for (int r = 0; r < K; ++r) a1[r] = warp_sum(a1[r]);
+#pragma unroll
+        for (int r = 0; r < K2; ++r) a2[r] = warp_sum(a2[r]);
+        if (lane == 0) {
+            acc_sm[3 + K + K2 + m] = (double)af;  // alpha_s: this shift's sum
+            acc_sm[0] += (double)aw;
+#pragma unroll
+            for (int r = 0; r < K; ++r) acc_sm[1 + r] += (double)a1[r];
+#pragma unroll
+            for (int r = 0; r < K2; ++r) acc_sm[1 + K + r] += (double)a2[r];
+        }
+    }
+    __syncwarp();
+    const double Sf = acc_sm[0];
+    const double inv = Sf > 0.0 ? 1.0 / Sf : 0.0;
+    // m1 = L E[y/s], m2 = L E[y y^T / s^2] L^T in FP64 (Lc is the full lower
+    // factor), one output per lane, written back over the totals
+    double o[2] = {0.0, 0.0};
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int t = lane + u * CF_WARP;
+        if (t >= K + K2) break;
+        double v = 0.0;
+        if (t < K) {
+            for (int l = 0; l <= t; ++l) v += Lc[t * K + l] * acc_sm[1 + l];
+        } else {
+            const int e = t - K;
+            int r = 0;
+            while ((r + 1) * (r + 2) / 2 <= e) ++r;
+            const int c = e - r * (r + 1) / 2;
+            for (int i = 0; i <= r; ++i) {
+                double w = 0.0;
+                for (int j = 0; j <= c; ++j)
+                    w += acc_sm[1 + K + (i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i)] * Lc[c * K + j];
+                v += Lc[r * K + i] * w;
+            }
+        }
+        o[u] = v * inv;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int t = lane + u * CF_WARP;
+        if (t < K + K2) acc_sm[1 + t] = o[u];
+    }
+    __syncwarp();
+    __syncwarp();
+    if (lane == 0) {  // alpha_s: mean of the shift means and its standard error (Welford)
+        double mean = 0.0, m2 = 0.0;
+        for (int m = 0; m < M; ++m) {
+            const double smean = acc_sm[3 + K + K2 + m] / (double)N;
+            const double delta = smean - mean;
+            mean += delta / (double)(m + 1);
+            m2 += delta * (smean - mean);
+        }
+        acc_sm[1 + K + K2] = mean;
+        acc_sm[2 + K + K2] = M > 1 ? sqrt(m2 / (double)(M - 1) / (double)M) : 0.0;
+    }
+    __syncwarp();
+    *alpha_s = acc_sm[1 + K + K2];
+    *se = acc_sm[2 + K + K2];
+    return Sf / ((double)N * M);
+}
+
+// ---------------------------------------------------------------------------
+// tk_lattice_mom_warp with the baker-transformed coordinates of each point read from
+// wtab (IntegArgs::wtab, one float4 per (shift, point), K <= 4) instead of advanced in
+// floating point: same results up to the coordinates' rounding.  A separate function,
+// so that the code generated for the other dimensions stays as it was.
+// ---------------------------------------------------------------------------
+template <typename R, int K, bool TAB = true>
+__device__ double tk_lattice_mom_tab_warp(const double* bt, const double* Lc, const R* __restrict__ chi,
                                       const R* __restrict__ shf, const Lattice& lat, int lane,
                                       double* acc_sm, R rk, double* alpha_s, double* se,
                                       const float4* __restrict__ wtab = nullptr)
