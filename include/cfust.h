@@ -85,8 +85,10 @@ typedef struct {
     int moments;         /* truncated-t moments of eqs (16)-(17) for q >= 3:
                             0 (default): exact recursion through T_{q-1} and T_{q-2};
                             1: ratio estimators E[X], E[X X^T] from the lattice pass of
-                               alpha (eq 13) that also samples the last coordinate
-                               (one integral per pair instead of 1 + q + q(q-1)).
+                               alpha_s (eq 4), which also samples the last coordinate;
+                               its points weighted by W/(nu+p) give alpha of eq (13)
+                               and the moments at dof nu+p+2 (one integral per pair
+                               instead of 2 + q + q(q-1)).
                             q <= 2 always uses the recursion. */
     int hold;            /* parameters the M-step keeps at their current values, a bitwise
                             OR of CFUST_HOLD_DELTA (eq 20 skipped; eq 21 then uses Delta^(k):

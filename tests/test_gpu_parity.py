@@ -324,23 +324,30 @@ def test_estep_shapes_fp64(cf, oracle, p, q, g, n):
     assert abs(cf.cfust_loglik(ctx) - L) <= 1e-12 * abs(L)
 
 
-def test_fp32_far_tail_pairs_use_fp64(cf, oracle):
+@pytest.mark.parametrize("moments", [0, 1])
+def test_fp32_far_tail_pairs_use_fp64(cf, oracle, moments):
     # an observation far on the wrong side of the skewing directions makes
-    # alpha_s tiny; the FP32 mode recomputes such pairs in FP64
+    # alpha_s tiny; the FP32 mode recomputes such pairs in FP64 (in the single-pass
+    # form with the shared pass of alpha_s weighted to dof nu+p+2, as the FP64 mode)
     p = q = 3
     params = dict(pi=[1.0], mu=[np.zeros(3)], Sigma=[0.3 * np.eye(3)],
                   Delta=[3.0 * np.eye(3)], nu=[30.0])
     y = np.array([[-40.0, -40.0, -40.0], [0.5, 0.2, 0.1]])
     w = dict(p=p, q=q, g=1, n=2, y=y, qmc=synth.qmc_settings(2))
-    c32 = _ctx(cf, w, params, precision=1)
-    c64 = _ctx(cf, w, params, precision=0)
+    c32 = _ctx(cf, w, params, precision=1, moments=moments)
+    c64 = _ctx(cf, w, params, precision=0, moments=moments)
     cf.cfust_estep(c32)
     cf.cfust_estep(c64)
     g32, g64 = cf.cfust_get_pairs(c32), cf.cfust_get_pairs(c64)
-    o = oracle.estep(y, params, oracle.qmc(**w["qmc"]))
+    o = oracle.estep(y, params, oracle.qmc(**dict(w["qmc"], moments=moments)))
     assert o["logf"][0, 0] < -100
     _close(g32["logf"][0, 0], g64["logf"][0, 0], 1e-12)
     _close(g64["logf"], o["logf"], 1e-9, 1e-9)
+    # the far pair's E-step values: FP32-mode fix-up (FP64) against the FP64 mode
+    _close(g32["u"][0, 0], g64["u"][0, 0], 1e-10)
+    _close(g32["eu"][0, 0], g64["eu"][0, 0], 1e-9, 1e-9 * np.abs(g64["eu"][0, 0]).max())
+    _close(g32["euu"][0, 0], g64["euu"][0, 0], 1e-9, 1e-9 * np.abs(g64["euu"][0, 0]).max())
+    _close(g64["u"][0, 0], o["u"][0, 0], 1e-8)
 
 
 def test_determinism(cf, flow_small):
