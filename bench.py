@@ -312,6 +312,10 @@ def main():
     ap.add_argument("--surrogate", action="store_true",
                     help="learned surrogate form (single-pass moments, q >= 3): train at the start "
                          "values (untimed), then time E-steps through the network")
+    ap.add_argument("--surrogate-refresh", type=int, default=5,
+                    help="surrogate form: every R-th step is a lattice E-step that also fine-tunes "
+                         "the network on its records (timed); 0: never")
+    ap.add_argument("--surrogate-refresh-epochs", type=int, default=4)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -386,9 +390,17 @@ def main():
                    "loglik_surrogate_at_start": ll_sur,
                    "loglik_rel_err_at_start": abs(ll_sur - ll_lat) / abs(ll_lat)}
 
+        count = [0]
+        ft = cf.cfust_surrogate_default_opts(epochs=args.surrogate_refresh_epochs) if surrogate else None
+
         def step():
-            L = cf.cfust_estep(ctx)
+            R = args.surrogate_refresh
+            if surrogate and R > 0 and count[0] > 0 and count[0] % R == 0:
+                L, _ = cf.cfust_surrogate_train(ctx, ft)  # a lattice E-step, then fine-tuning
+            else:
+                L = cf.cfust_estep(ctx)
             cf.cfust_mstep(ctx)
+            count[0] += 1
             return L
 
         for _ in range(args.warmup):
@@ -426,8 +438,13 @@ def main():
         estep_ms = sum(v[0] for k, v in prof.items() if k != "mstep") / args.steps
         if sur is not None:
             recs, fb = cf.cfust_surrogate_info(ctx)
-            sur["fallback_fraction_last_step"] = fb / max(recs, 1)
-        return dict(ms=ms, prof=prof, launches=launches, ll=lls[-1], clk=clk, estep_ms=estep_ms, sur=sur)
+            sur["fallback_fraction_last_surrogate_step"] = fb / max(recs, 1)
+            sur["refresh_every"] = args.surrogate_refresh
+            sur["refresh_epochs"] = args.surrogate_refresh_epochs
+            cf.cfust_surrogate_use(ctx, 0)
+        # l at the final parameters by the lattice density pass (the same yardstick for every form)
+        ll_final = cf.cfust_loglik(ctx) if args.surrogate else None
+        return dict(ll_final=ll_final, ms=ms, prof=prof, launches=launches, ll=lls[-1], clk=clk, estep_ms=estep_ms, sur=sur)
 
     chosen_moments = 1 if args.moments == "single-pass" else 0
     if args.surrogate and not (chosen_moments == 1 and w["q"] >= 3):
@@ -558,8 +575,14 @@ def main():
                 "roofline": roof, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
                 "loglik_check": ll_check}
         if main_run["sur"] is not None:
-            line["config"]["form"] = "learned surrogate (BF16 MLP, lattice fallback) + single-pass moments"
+            line["config"]["form"] = ("learned surrogate (BF16 MLP, lattice fallback; every "
+                                      f"{args.surrogate_refresh}th step a lattice E-step that fine-tunes it) "
+                                      "+ single-pass moments")
             line["surrogate"] = main_run["sur"]
+            line["surrogate"]["loglik_final_by_lattice"] = main_run["ll_final"]
+            line["surrogate"]["loglik_final_lattice_form"] = lattice_run["ll_final"]
+            line["surrogate"]["loglik_final_rel_diff"] = (abs(main_run["ll_final"] - lattice_run["ll_final"])
+                                                          / abs(lattice_run["ll_final"]))
             line["lattice_gpu"] = {
                 "form": "single-pass moments, lattice only", "value": pairs * world / (lattice_run["ms"] / 1e3),
                 "unit": UNIT, "ms_per_step": lattice_run["ms"],
