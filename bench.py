@@ -579,6 +579,8 @@ def main():
                                       f"{args.surrogate_refresh}th step a lattice E-step that fine-tunes it) "
                                       "+ single-pass moments")
             line["surrogate"] = main_run["sur"]
+            line["gpu_launches_note"] = ("E- and M-step kernels; the refresh steps' training kernels "
+                                         "(GEMMs, Adam) are not counted")
             line["surrogate"]["loglik_final_by_lattice"] = main_run["ll_final"]
             line["surrogate"]["loglik_final_lattice_form"] = lattice_run["ll_final"]
             line["surrogate"]["loglik_final_rel_diff"] = (abs(main_run["ll_final"] - lattice_run["ll_final"])
