@@ -44,12 +44,12 @@ UNIT = "obs·comp/s"
 # kernels count per lattice point (records x N x M; the same kernels run in the
 # fp32 and mixed forms), the T_2 quadrature per record (its node count depends
 # on the precision form, so the key names it).
-INSTR_PER_UNIT = {("lattice", 4): 188.8, ("moments", 4): 227.5, ("t2", 2, "mixed"): 14128.0}
+INSTR_PER_UNIT = {("lattice", 4): 188.8, ("moments", 4): 219.5, ("t2", 2, "mixed"): 14128.0}
 # DRAM bytes per integral record in the same captures (dram__bytes_read.sum +
 # dram__bytes_write.sum of the launch / its records: 16,000 records of each
 # lattice kind at flow_p4 n = 4,000; 320,000 T_2 records at wide_p16 n = 20,000);
 # the records dominate, so traffic scales with the record count.
-INTEG_TRAFFIC_BYTES_PER_RECORD = {("lattice", 4): 797440 / 16000, ("moments", 4): 1091328 / 16000,
+INTEG_TRAFFIC_BYTES_PER_RECORD = {("lattice", 4): 797440 / 16000, ("moments", 4): 1091072 / 16000,
                                   ("t2", 2, "mixed"): 11594752 / 320000}
 
 

@@ -872,7 +872,8 @@ __device__ double tk_lattice_mom_tab_warp(const double* bt, const double* Lc, co
                 v = v < Lim<R>::vmin() ? Lim<R>::vmin() : v;
                 v = v > Lim<R>::one_minus_ulp() ? Lim<R>::one_minus_ulp() : v;
                 y[r] = m_ncdfinv(v);
-                if (e <= Lim<R>::tiny()) f = R(0);
+                // no cut-off at Lim::tiny: a factor that underflows zeroes f by itself, and
+                // the clamped v keeps y finite
             }
             // weight f s^2; X = L y / s2 is linear in y: accumulate f s^2 y / s2 =
             // f s rk y and f s^2 y y^T / s2^2 = f rk^2 y y^T, and apply L once per record
