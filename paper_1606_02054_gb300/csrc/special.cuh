@@ -789,8 +789,10 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
 // ---------------------------------------------------------------------------
 // tk_lattice_mom_warp with the baker-transformed coordinates of each point read from
 // wtab (IntegArgs::wtab, one float4 per (shift, point), K <= 4) instead of advanced in
-// floating point: same results up to the coordinates' rounding.  A separate function,
-// so that the code generated for the other dimensions stays as it was.
+// floating point, and without the cut-off of factors below Lim::tiny (an underflowed
+// factor zeroes the product by itself): the same estimator up to the coordinates'
+// rounding.  A separate function, so that the code generated for the other dimensions
+// stays as it was.
 // ---------------------------------------------------------------------------
 template <typename R, int K, bool TAB = true>
 __device__ double tk_lattice_mom_tab_warp(const double* bt, const double* Lc, const R* __restrict__ chi,
