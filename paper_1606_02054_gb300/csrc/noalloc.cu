@@ -11,7 +11,6 @@
 // which every GPU that loads the library holds until the process exits.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "cfust.h"
@@ -26,11 +25,6 @@ static __device__ __align__(256) double g_noalloc_partial[CF_NOALLOC_PARTIAL_DOU
 static __device__ __align__(256) int g_noalloc_flag[64];
 
 namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double* g_partial_addr[kMaxDevices] = {};
-int* g_flag_addr[kMaxDevices] = {};
-
 // failures are reported through cfust_last_error(NULL)
 cfust_status nerr(cfust_status s, const std::string& m)
 {
@@ -51,8 +45,10 @@ extern "C" cfust_status cfust_reduce_stats_noalloc(int p, int q, int g, int64_t 
         return nerr(CFUST_EINVAL, "cfust_reduce_stats_noalloc: sizes out of range");
     if (!y || !pi || !mu || !logf || !u || !elogu || !eu || !euu || !stats)
         return nerr(CFUST_EINVAL, "cfust_reduce_stats_noalloc: NULL device pointer");
-    // same blocking as the allocating path: rows of 4 + p + q + q^2 doubles,
-    // chunk <= 256 observations, at most 48 KB of shared memory per block
+    // rows of 4 + p + q + q^2 doubles, chunk <= 256 observations, at most 48 KB of
+    // shared memory per block (the default limit: no attribute is set here).  The
+    // allocating path raises its limit to 64 KB and may stage more observations per
+    // block, so the two agree to rounding, not bit for bit.
     const int row = 4 + p + q + q * q;
     int chunk = 256;
     while (chunk > 32 && ((size_t)chunk * (row + g + 1) + CF_MAXG) * sizeof(double) > 48 * 1024) chunk -= 32;
@@ -63,29 +59,20 @@ extern "C" cfust_status cfust_reduce_stats_noalloc(int p, int q, int g, int64_t 
                     "cfust_reduce_stats_noalloc: ceil(n/" + std::to_string(chunk) + ") x (g*(3+p+q+pq+q^2+p^2)+1) = " +
                         std::to_string((long long)nblocks * width) + " partial sums exceed the fixed scratch of " +
                         std::to_string(CF_NOALLOC_PARTIAL_DOUBLES) + " doubles");
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return nerr(CFUST_ECUDA, std::string("cfust_reduce_stats_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
-    double* partial = nullptr;
-    int* flag = nullptr;
-    {
-        // first call on each device: resolve the device addresses of the
-        // file-scope scratch (host code cannot use the symbols directly)
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_partial_addr[dev]) {
-            void* a = nullptr;
-            if ((e = cudaGetSymbolAddress(&a, g_noalloc_partial)) != cudaSuccess)
-                return nerr(CFUST_ECUDA, std::string("cfust_reduce_stats_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            void* b = nullptr;
-            if ((e = cudaGetSymbolAddress(&b, g_noalloc_flag)) != cudaSuccess)
-                return nerr(CFUST_ECUDA, std::string("cfust_reduce_stats_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            g_partial_addr[dev] = (double*)a;
-            g_flag_addr[dev] = (int*)b;
-        }
-        partial = g_partial_addr[dev];
-        flag = g_flag_addr[dev];
-    }
+    // device addresses of the file-scope scratch in the current context (host code
+    // cannot use the symbols directly).  Looked up on every call rather than cached:
+    // the address belongs to the context, and a context created after
+    // cudaDeviceReset, or another context on the same device, has its own copy.
+    // The first lookup in a context also loads the library's device code there.
+    cudaError_t e;
+    void* a = nullptr;
+    if ((e = cudaGetSymbolAddress(&a, g_noalloc_partial)) != cudaSuccess)
+        return nerr(CFUST_ECUDA, std::string("cfust_reduce_stats_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    void* b = nullptr;
+    if ((e = cudaGetSymbolAddress(&b, g_noalloc_flag)) != cudaSuccess)
+        return nerr(CFUST_ECUDA, std::string("cfust_reduce_stats_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    double* partial = (double*)a;
+    int* flag = (int*)b;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if ((e = cudaMemsetAsync(flag, 0, sizeof(int), st)) != cudaSuccess)
         return nerr(CFUST_ECUDA, std::string("cfust_reduce_stats_noalloc: ") + cudaGetErrorString(e));

@@ -54,8 +54,18 @@ def test_reduce_stats_noalloc_matches_allocating_path():
         assert abs(got[-1] - L) <= 1e-12 * abs(L), (call, got[-1], L)
         np.testing.assert_allclose(tau.cpu().numpy().reshape(g, n), pairs["tau"], rtol=0, atol=1e-14)
 
-    # beyond the fixed scratch: a clear error, nothing launched
+    # beyond the fixed scratch: a clear error from the library itself, nothing launched
+    # (called through ctypes directly: the Python wrapper would already reject the
+    # tensors as shorter than n = 10^7 needs)
+    import ctypes as C
+
     big_n = 10_000_000
+    vp = lambda t: C.c_void_p(t.data_ptr())
+    st = cf.lib().cfust_reduce_stats_noalloc(p, q, g, big_n, vp(y), vp(pi), vp(mu), vp(logf), vp(u),
+                                             vp(el), vp(eu), vp(euu), None, vp(stats), None)
+    assert st == cf.CFUST_EINVAL and "scratch" in cf.cfust_last_error(None)
+
+    # a tensor shorter than its stated size: rejected before the library is called
     with pytest.raises(cf.CfustError) as e:
-        cf.cfust_reduce_stats_noalloc(p, q, g, big_n, y, pi, mu, logf, u, el, eu, euu, None, stats)
-    assert e.value.status == cf.CFUST_EINVAL and "scratch" in str(e.value)
+        cf.cfust_reduce_stats_noalloc(p, q, g, n, y, pi, mu, logf, u, el, eu[:-1], euu, None, stats)
+    assert e.value.status == cf.CFUST_EINVAL and "eu holds" in str(e.value)
