@@ -1,19 +1,36 @@
 """Benchmark of the FM-CFUST EM hot path on GB300 (one JSON line on stdout).
 
-A step is one EM iteration (E-step over every observation-component pair with
-the tau-weighted sufficient statistics, then the M-step) over the whole
-synthetic workload `flow_p4`: p = q = g = 4 (the HSCT flow-cytometry shape),
-n = 200,000 observations drawn from the latent hierarchy of eq (6), T_4 and
-T_3 by the randomised lattice (1024 points x 8 shifts).
+A step is one EM iteration -- the E-step over every observation-component pair
+with the tau-weighted sufficient statistics (Sec. 3.1, 3.2), then the M-step --
+over the whole synthetic workload.  The default workload is `wide_p16`
+(p = 16, q = 2, g = 8, n = 2,000,000 observations stored in FP32, drawn from
+the latent hierarchy of eq (6)): the largest single-GPU configuration.  The
+line reports, on that workload,
+  - the chosen form (value, ms_per_step): the mixed-precision form (FP32
+    whitening, integrals and compensated statistics; FP64 factorisations, tau,
+    log-likelihood, M-step and nu);
+  - `plain_gpu`: the plain method (moments by the T_{q-1}/T_{q-2} recursion,
+    FP32 integrals, FP64 everything else) timed the same way;
+  - `loglik_err`: each form's final log-likelihood and parameters after the
+    same EM iterations on a sample of the workload, against the FP64 oracle fit
+    in the same reading (computed in the CPU leg, before the GPU work);
+  - `roofline`: the dominant kernel's counted algorithmic work per second
+    (T_2 quadrature nodes, or lattice points) over the rate of the same
+    per-unit arithmetic alone, measured on this GPU in this run
+    (cfust_measure_rates);
+  - `sub`: the same for flow_p4 (p = q = g = 4, n = 200,000; single-pass vs
+    recursion moments), learned_p6 (p = q = g = 6, n = 1,000,000) and the batch
+    of concurrent fits (cfust_fit_batch against the fit-by-fit loop).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64|mixed]
-  python bench.py --workload wide_p16 --precision mixed   (p = 16, q = 2, g = 8, n = 2e6)
-  python bench.py --workload batch [--nfits 64 --starts 4] (concurrent graph-driven fits)
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--sub LIST]
+  python bench.py --workload batch [--nfits 64 --starts 4]
   python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
 
-value: observation-component pairs per second of whole EM iterations, summed
-over ranks (each rank runs its own replica: weak scaling).  Inputs are
-resident in HBM; L2 (129 MB) is flushed before every timed step.
+Under torchrun (N > 1) the observations are split by rows across the ranks
+and one all-gather of the per-segment statistics per iteration gives every
+rank the same sums (paper_1606_02054_gb300.shard): strong scaling, value =
+all pairs per second of the slowest rank.  Inputs are resident in HBM; L2
+(129 MB) is flushed before every timed step.
 """
 from __future__ import annotations
 
@@ -37,27 +54,6 @@ if ROOT not in sys.path:
 
 METRIC = "E-step obs·comp/s and EM iter/s: chosen form vs plain GPU at stated loglik err"
 UNIT = "obs·comp/s"
-# Executed thread-instructions per unit of work of the FP32 integrators
-# (smsp__inst_executed.sum x smsp__thread_inst_executed_per_inst_executed.ratio
-# / units) from the ncu captures summarised in profiles/lattice_fp32_flow_p4.md,
-# profiles/moments_fp32_flow_p4.md and profiles/t2_mixed_wide_p16.md.  Lattice
-# kernels count per lattice point (records x N x M; the same kernels run in the
-# fp32 and mixed forms), the T_2 quadrature per record (its node count depends
-# on the precision form, so the key names it).
-INSTR_PER_UNIT = {("lattice", 4): 188.8, ("moments", 4): 219.5, ("t2", 2, "mixed"): 14128.0}
-# DRAM bytes per integral record in the same captures (dram__bytes_read.sum +
-# dram__bytes_write.sum of the launch / its records: 16,000 records of each
-# lattice kind at flow_p4 n = 4,000; 320,000 T_2 records at wide_p16 n = 20,000);
-# the records dominate, so traffic scales with the record count.
-INTEG_TRAFFIC_BYTES_PER_RECORD = {("lattice", 4): 797440 / 16000, ("moments", 4): 1091072 / 16000,
-                                  ("t2", 2, "mixed"): 11594752 / 320000}
-
-
-def _unit_key(kind, k, precision):
-    if precision == "fp64":
-        return None
-    return (kind, k, precision) if kind == "t2" else (kind, k)
-
 
 PRECISION_NOTE = {
     "fp64": "fp64 throughout",
@@ -66,16 +62,32 @@ PRECISION_NOTE = {
     "mixed": "fp32 whitening, integrals and compensated statistics; fp64 factorisations, "
              "tau, loglik, M-step, nu",
 }
-SM_COUNT = 152
-LANES_PER_SM = 128  # 4 sub-partitions x 32 lanes, one instruction per lane per clock
 
-
-def _peaks():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f)
-    except OSError:
-        return {}
+# (chosen form, plain form) per workload; the plain method is the moment recursion with
+# FP32 integrals and FP64 everything else
+FORMS = {
+    "wide_p16": (dict(label="mixed precision", precision="mixed", moments=1),
+                 dict(label="plain: recursion moments, fp32 integrals, fp64 rest", precision="fp32", moments=0)),
+    "flow_p4": (dict(label="single-pass moments, fp32 integrals", precision="fp32", moments=1),
+                dict(label="plain: recursion moments, fp32 integrals, fp64 rest", precision="fp32", moments=0)),
+    "learned_p6": (dict(label="single-pass moments, fp32 integrals", precision="fp32", moments=1),
+                   dict(label="plain: recursion moments, fp32 integrals, fp64 rest", precision="fp32", moments=0)),
+    "two_comp_p2": (dict(label="fp64", precision="fp64", moments=0),
+                    dict(label="plain: fp64", precision="fp64", moments=0)),
+}
+Y32_WORKLOADS = ("wide_p16",)  # observations stored in FP32
+# CPU samples (observations) and sample fits (observations, EM iterations) per workload,
+# sized for a few seconds of oracle time on 16 host cores
+CPU_SAMPLE = {"wide_p16": 20000, "flow_p4": 2000, "learned_p6": 120, "two_comp_p2": 1000}
+REF_SAMPLE = {"wide_p16": 8000, "flow_p4": 400, "learned_p6": 40, "two_comp_p2": 1000}
+FIT_SAMPLE = {"wide_p16": (1000, 8), "flow_p4": (200, 6), "learned_p6": (40, 3), "two_comp_p2": (1000, 20)}
+# the plain recursion at p = q = g = 6 takes seconds per iteration (2 T_6 + 6 T_5 + 30 T_4
+# lattice integrals per pair): one warm-up and one timed step
+SUB_PLAIN_STEPS = {"learned_p6": 1}
+# DRAM bytes per algorithmic unit of the dominant kernels, from ncu captures of this
+# build (dram__bytes_read.sum + dram__bytes_write.sum of one launch / its units); None
+# where no capture of the current kernel exists
+TRAFFIC_PER_UNIT = {}
 
 
 class Clocks:
@@ -132,97 +144,247 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _opts(cf, w, precision, profile=0, stream=None, moments=1):
+def _prec(cf, name):
+    return {"fp32": cf.CFUST_PREC_FP32, "fp64": cf.CFUST_PREC_FP64, "mixed": cf.CFUST_PREC_MIXED}[name]
+
+
+def _opts(cf, w, form, profile=0, stream=None):
     q = w["qmc"]
-    return cf.cfust_default_opts(precision=precision, qmc_points=q["npoints"],
+    return cf.cfust_default_opts(precision=_prec(cf, form["precision"]), qmc_points=q["npoints"],
                                  qmc_shifts=q["nshifts"], qmc_korobov_a=q["korobov_a"],
-                                 seed=q["seed"], profile=profile,
-                                 cuda_stream=stream, moments=moments)
+                                 seed=q["seed"], profile=profile, cuda_stream=stream,
+                                 moments=form["moments"])
 
 
-def cpu_baseline(w, nsample, steps=1, moments=1):
-    """The FP64 oracle, as it stands, on `nsample` observations of the workload
-    (same moment reading as the timed GPU form)."""
+def _y_store(w):
+    """The observations as the workload stores them (FP32 for the wide workload)."""
+    return np.ascontiguousarray(w["y"], dtype=np.float32 if w["name"] in Y32_WORKLOADS else np.float64)
+
+
+def _form_name(w, form):
+    m = "single-pass moments" if form["moments"] and w["q"] >= 3 else "moment recursion"
+    return f"{form['label']} ({m}; {PRECISION_NOTE[form['precision']]})"
+
+
+# ---------------------------------------------------------------------------
+# CPU leg: the FP64 oracle (timed baseline, and the reference fits of every form)
+# ---------------------------------------------------------------------------
+def cpu_baseline(w, nsample, moments):
+    """The FP64 oracle, as it stands, on the first `nsample` observations of the
+    workload: one E-step + M-step (the same moment reading as the timed form)."""
     import oracle
 
-    sub = w["y"][:nsample]
+    sub = _y_store(w)[:nsample].astype(np.float64)
     spec = oracle.qmc(**dict(w["qmc"], moments=moments))
     cores = os.cpu_count() or 1
     params = {k: np.array(v, dtype=float) for k, v in w["init"].items()}
     t0 = time.perf_counter()
-    ll0 = None
-    for _ in range(steps):
-        e = oracle.estep(sub, params, spec, nthreads=cores)
-        ll0 = e["loglik"] if ll0 is None else ll0
-        params, _ = oracle.mstep(sub, e, params)
-    dt = (time.perf_counter() - t0) / steps
+    e = oracle.estep(sub, params, spec, nthreads=cores)
+    oracle.mstep(sub, e, params)
+    dt = time.perf_counter() - t0
     return {"value": nsample * w["g"] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {nsample} of {w['n']} observations of {w['name']}, "
-                      f"E-step + M-step in FP64 on {cores} host threads, {steps} step(s)",
-            "ms_per_step": dt * 1e3, "loglik_at_start": ll0}
+            "sample": f"first {nsample} of {w['n']} observations of {w['name']}, one E-step + "
+                      f"M-step in FP64 on {cores} host threads",
+            "ms_per_step": dt * 1e3}
 
 
-def run_reference(args, w, rank, world):
-    if rank != 0:
-        return
-    cores = os.cpu_count() or 1
-    nsample = args.ref_sample
-    per = []
-    for i in range(args.warmup + args.steps):
-        b = cpu_baseline(w, nsample, 1, 1 if args.moments == "single-pass" else 0)
-        if i >= args.warmup:
-            per.append(b["ms_per_step"])
-    ms = float(np.mean(per))
-    value = nsample * w["g"] / (ms / 1e3)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference",
-            "config": {"workload": w["name"], "n": w["n"], "p": w["p"], "q": w["q"], "g": w["g"],
-                       "qmc": f"{w['qmc']['npoints']}x{w['qmc']['nshifts']}",
-                       "form": ("single-pass moments" if args.moments == "single-pass" and w["q"] >= 3
-                                else "moment recursion"),
-                       "precision": "fp64 throughout (the CPU oracle)",
-                       "parallelism": f"{cores} host threads (OpenMP over observations)",
-                       "sample_n": nsample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"first {nsample} observations per step"},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+def oracle_fits(w, forms, nsample, iters):
+    """Oracle fits of the first `nsample` observations (as the workload stores them)
+    from the workload's starting values, one per distinct moment reading."""
+    import oracle
+
+    y = _y_store(w)[:nsample].astype(np.float64)
+    out = {}
+    for f in forms:
+        m = f["moments"] if w["q"] >= 3 else 0
+        if m not in out:
+            ref, hist, _ = oracle.fit(y, w["init"], iters, oracle.qmc(**dict(w["qmc"], moments=m)),
+                                      nthreads=os.cpu_count() or 1)
+            out[m] = (ref, hist)
+    return out
 
 
-def run_batch(args, rank, world):
+def fit_error(cf, w, form, refs, nsample, iters):
+    """The GPU fit of the same sample in `form` against the oracle's."""
+    m = form["moments"] if w["q"] >= 3 else 0
+    ref, rhist = refs[m]
+    ctx = cf.cfust_create(w["p"], w["q"], w["g"], nsample, _opts(cf, w, form))
+    cf.cfust_set_data(ctx, _y_store(w)[:nsample])
+    cf.cfust_set_params(ctx, w["init"])
+    _, hist = cf.cfust_fit(ctx, iters)
+    got = cf.cfust_get_params(ctx)
+    perr = max(float(np.linalg.norm(np.atleast_1d(got[k][h] - ref[k][h])) /
+                     max(float(np.linalg.norm(np.atleast_1d(ref[k][h]))), 1e-300))
+               for k in ("pi", "mu", "Sigma", "Delta", "nu") for h in range(w["g"]))
+    return {"loglik_rel_err": abs(hist[-1] - rhist[-1]) / abs(rhist[-1]), "param_rel_err": perr,
+            "loglik_gpu": float(hist[-1]), "loglik_oracle": float(rhist[-1]),
+            "sample": f"first {nsample} observations, {iters} EM iterations from the same start, "
+                      f"oracle in the same moment reading and lattice"}
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+def measure(cf, torch, w, form, y_dev, flush, stream, steps, warmup, with_clocks=False, shard=None):
+    """`warmup` untimed, then `steps` timed EM iterations (CUDA events on the launching
+    stream around each step, L2 flushed before each); the library's kernel profile and
+    algorithmic work counts of the timed steps."""
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if shard is not None:
+        fit = shard.make_fit(cf, w, _opts(cf, w, form, profile=1, stream=stream.cuda_stream), y_dev)
+        step = fit.step
+        ctx = fit.ctx
+    else:
+        ctx = cf.cfust_create(w["p"], w["q"], w["g"], w["n"],
+                              _opts(cf, w, form, profile=1, stream=stream.cuda_stream))
+        cf.cfust_set_data(ctx, y_dev)
+        cf.cfust_set_params(ctx, w["init"])
+
+        def step():
+            L = cf.cfust_estep(ctx)
+            cf.cfust_mstep(ctx)
+            return L
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    cf.cfust_profile(ctx, reset=True)
+    n0 = cf.cfust_launch_count(ctx)
+    clocks = Clocks(local) if with_clocks else None
+    if clocks:
+        clocks.start()
+    if shard is not None:
+        shard.barrier()
+    torch.cuda.synchronize()
+    total_ms, lls = 0.0, []
+    for _ in range(steps):
+        flush.fill_(1.0)  # evict L2 before each timed step
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lls.append(step())
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    if shard is not None:
+        shard.barrier()
+    clk = clocks.stop() if clocks else None
+    ms = total_ms / steps
+    if shard is not None:
+        ms = shard.max_over_ranks(ms)
+    prof = cf.cfust_profile(ctx)
+    work = cf.cfust_profile_work(ctx)
+    estep_ms = sum(v[0] for k, v in prof.items() if k != "mstep") / steps
+    return dict(ms=ms, estep_ms=estep_ms, prof=prof, work=work, ll=lls[-1], clk=clk,
+                launches=cf.cfust_launch_count(ctx) - n0, ctx=ctx)
+
+
+def roofline(w, run, rates):
+    """The dominant integrator class of a run: counted algorithmic units per second
+    (lattice points, T_2 quadrature nodes) over the measured rate of the same per-unit
+    arithmetic alone (cfust_measure_rates)."""
+    prof, work = run["prof"], run["work"]
+    classes = [k for k in ("level0_Tq", "level1_Tq-1", "level2_Tq-2", "moments_Tq")
+               if prof[k][1] > 0 and work[k] > 0]
+    if not classes:
+        return None
+    dom = max(classes, key=lambda k: prof[k][0])
+    ms_launch = prof[dom][0] / prof[dom][1]
+    units_launch = work[dom] / prof[dom][1]
+    dims = {"level0_Tq": w["q"], "level1_Tq-1": w["q"] - 1, "level2_Tq-2": w["q"] - 2, "moments_Tq": w["q"]}
+    k = dims[dom]
+    if k == 2:
+        unit, peak_rate = "T_2 quadrature node", rates.get("t2_nodes")
+        basis = ("cfust_measure_rates t2_nodes: the FP32 T_2 node alone (two sines, sin^(nu-1), "
+                 "tabulated inner T_1), measured on this GPU in this run")
+    else:
+        unit, peak_rate = "lattice point", rates.get("mix_points", {}).get(k)
+        basis = (f"cfust_measure_rates mix_points[{k}]: the single-pass integrand of dimension {k} "
+                 f"alone ({k} Phi, {k} Phi^-1, {k * (k - 1) // 2 + 3 * k} + {2 + k + k * (k + 1) // 2} FMA "
+                 f"per point), measured on this GPU in this run")
+        if dom != "moments_Tq":
+            basis += " (an upper bound of the plain T_k integrand's rate: it has one Phi^-1 and the moment sums more)"
+    achieved = units_launch / (ms_launch / 1e3) / 1e9
+    peak = peak_rate / 1e9 if peak_rate else None
+    tb = TRAFFIC_PER_UNIT.get((dom, k))
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": f"G{unit.split()[-1]}s/s",
+            "frac": achieved / peak if peak else None,
+            "traffic": tb * units_launch if tb else None,
+            "kernel": dom, "k": k, "unit_of_work": unit, "units_per_launch": units_launch,
+            "ms_per_launch": ms_launch, "peak_basis": basis}
+
+
+def form_summary(w, run, pairs, world):
+    return {"value": pairs / (run["ms"] / 1e3), "unit": UNIT, "ms_per_step": run["ms"],
+            "steps": run["steps"], "warmup": run["warmup"],
+            "em_iter_per_s": 1e3 / run["ms"],
+            "estep_obs_comp_per_s": pairs / (run["estep_ms"] / 1e3),
+            "loglik_last": run["ll"], "gpu_launches": int(run["launches"]),
+            "kernel_ms_per_step": {k: v[0] / max(1, run["steps"]) for k, v in run["prof"].items()}}
+
+
+def run_workload(cf, torch, name, args, stream, flush, steps, warmup, with_clocks, refs, fitcfg,
+                 rates, shard=None, w=None, plain_steps=None, plain_warmup=None):
+    """Chosen and plain forms of one workload, each with its fit error."""
+    from paper_1606_02054_gb300 import synth
+
+    if w is None:
+        w = synth.make_workload(name)
+        w["name"] = name
+    chosen, plain = FORMS[name]
+    ydt = torch.float32 if name in Y32_WORKLOADS else torch.float64
+    if shard is not None:
+        lo, hi = shard.rows(w["n"], cf, w, _opts(cf, w, chosen))
+        y_dev = torch.tensor(_y_store(w)[lo:hi], dtype=ydt, device="cuda")
+    else:
+        y_dev = torch.tensor(_y_store(w), dtype=ydt, device="cuda")
+    pairs = w["n"] * w["g"]
+    runs = {}
+    for key, form in (("chosen", chosen), ("plain", plain)):
+        st = steps if key == "chosen" or plain_steps is None else plain_steps
+        wu = warmup if key == "chosen" or plain_warmup is None else plain_warmup
+        r = measure(cf, torch, w, form, y_dev, flush, stream, st, wu,
+                    with_clocks=with_clocks and key == "chosen", shard=shard)
+        r["steps"], r["warmup"] = st, wu
+        runs[key] = r
+    out = {"workload": name, "n": w["n"], "p": w["p"], "q": w["q"], "g": w["g"],
+           "qmc": f"{w['qmc']['npoints']}x{w['qmc']['nshifts']}"}
+    for key, form in (("chosen", chosen), ("plain", plain)):
+        s = form_summary(w, runs[key], pairs, 1)
+        s["form"] = _form_name(w, form)
+        s["roofline"] = roofline(w, runs[key], rates) if key == "chosen" else None
+        if refs is not None:
+            ns, it = fitcfg
+            s["loglik_err"] = fit_error(cf, w, form, refs, ns, it)
+        out[key] = s
+    out["speedup_of_chosen"] = runs["plain"]["ms"] / runs["chosen"]["ms"]
+    return out, runs, w, y_dev
+
+
+def run_batch(args, cf, torch, stream, flush, with_clocks=False, steps=None, warmup=None):
     """Batched fits (p = q uniform on 2..8, g on 2..6, n log-uniform on 1e3..1e5): every
     fit's EM loop is one device-controlled CUDA graph and all fits run concurrently
     (cfust_fit_batch).  One step = one EM iteration of every fit; value = sum over fits
     of n*g per second.  The same iteration run fit by fit through cfust_estep /
     cfust_mstep is timed beside it."""
-    import torch
+    from paper_1606_02054_gb300 import synth
 
-    from paper_1606_02054_gb300 import build, synth
-
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    build.build()
-    import paper_1606_02054_gb300 as cf
-
-    prec = {"fp32": cf.CFUST_PREC_FP32, "fp64": cf.CFUST_PREC_FP64,
-            "mixed": cf.CFUST_PREC_MIXED}[args.precision]
-    moments = 1 if args.moments == "single-pass" else 0
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     B = synth.make_batch(nfits=args.nfits, starts=args.starts)
     qmc = B["qmc"]
     ctxs, pairs = [], 0
     for f in B["fits"]:
         for st in f["starts"]:
-            o = cf.cfust_default_opts(precision=prec, qmc_points=qmc["npoints"],
+            o = cf.cfust_default_opts(precision=cf.CFUST_PREC_FP32, qmc_points=qmc["npoints"],
                                       qmc_shifts=qmc["nshifts"], qmc_korobov_a=qmc["korobov_a"],
-                                      seed=qmc["seed"], moments=moments)
+                                      seed=qmc["seed"], moments=1)
             c = cf.cfust_create(f["p"], f["q"], f["g"], f["n"], o)
             cf.cfust_set_data(c, f["y"])
             cf.cfust_set_params(c, st)
             ctxs.append(c)
             pairs += f["n"] * f["g"]
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def batched():
         it, hist, status = cf.cfust_fit_batch(ctxs, 1, 0.0, flags=cf.CFUST_FIT_NO_FINAL)
@@ -238,16 +400,16 @@ def run_batch(args, rank, world):
                 bad += 1
         return bad
 
-    def timed(fn, steps, with_clocks):
-        for _ in range(args.warmup):
+    def timed(fn, nsteps, clocked):
+        for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
         n0 = sum(cf.cfust_launch_count(c) for c in ctxs)
-        clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0"))) if with_clocks else None
+        clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0"))) if clocked else None
         if clocks:
             clocks.start()
         per, failed = [], 0
-        for _ in range(steps):
+        for _ in range(nsteps):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -258,36 +420,52 @@ def run_batch(args, rank, world):
         launches = sum(cf.cfust_launch_count(c) for c in ctxs) - n0
         return float(np.mean(per)), clk, launches, failed
 
-    ms_b, clk, launches, failed_b = timed(batched, args.steps, True)
-    ms_s, _, launches_s, failed_s = timed(sequential, max(1, args.steps // 2), False)
+    ms_b, clk, launches, failed_b = timed(batched, steps, with_clocks)
+    ms_s, _, _, _ = timed(sequential, max(1, steps // 2), False)
+    out = {"workload": "batch", "fits": len(ctxs), "problems": args.nfits, "starts": args.starts,
+           "pairs_per_iteration": pairs, "p=q": "uniform 2..8", "g": "uniform 2..6",
+           "n": "log-uniform 1e3..1e5", "n_total": int(sum(f["n"] for f in B["fits"])),
+           "qmc": f"{qmc['npoints']}x{qmc['nshifts']}",
+           "form": "single-pass moments, " + PRECISION_NOTE["fp32"],
+           "step": "one EM iteration of every fit (cfust_fit_batch, max_iter 1, no final density pass)",
+           "timing": "host clock around the synchronous batch call, device synchronised on both sides",
+           "chosen": {"form": "batched: one device-controlled CUDA graph per fit, all fits concurrent",
+                      "value": pairs / (ms_b / 1e3), "unit": UNIT, "ms_per_step": ms_b,
+                      "gpu_launches": int(launches / steps), "failed_fits": failed_b // steps},
+           "plain": {"form": "cfust_estep + cfust_mstep fit by fit on one stream",
+                     "value": pairs / (ms_s / 1e3), "unit": UNIT, "ms_per_step": ms_s},
+           "speedup_of_chosen": ms_s / ms_b}
+    return out, clk
+
+
+def run_reference(args, w, rank, world):
     if rank != 0:
         return
-    shapes = sorted({(f["p"], f["g"]) for f in B["fits"]})
-    line = {"metric": METRIC, "value": pairs * world / (ms_b / 1e3), "unit": UNIT,
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
-            "config": {"workload": "batch", "fits": len(ctxs), "problems": args.nfits,
-                       "starts": args.starts, "pairs_per_iteration": pairs,
-                       "p=q": "uniform 2..8",
-                       "g": "uniform 2..6", "n": "log-uniform 1e3..1e5",
-                       "n_total": int(sum(f["n"] for f in B["fits"])),
-                       "qmc": f"{qmc['npoints']}x{qmc['nshifts']}",
-                       "form": "single-pass moments" if moments else "moment recursion",
-                       "precision": PRECISION_NOTE[args.precision],
-                       "step": "one EM iteration of every fit (cfust_fit_batch, max_iter 1, "
-                               "no final density pass)",
-                       "timing": "host clock around the synchronous batch call, device "
-                                 "synchronised on both sides",
-                       "l2": "flushed (256 MB write) before every timed step",
-                       "parallelism": f"replicas x{world}"},
-            "gpu_launches": int(launches / args.steps), "failed_fits": failed_b // args.steps,
-            "clocks": clk,
-            "sequential": {"form": "cfust_estep + cfust_mstep fit by fit on one stream",
-                           "value": pairs * world / (ms_s / 1e3), "unit": UNIT,
-                           "ms_per_step": ms_s,
-                           "speedup_of_batched": ms_s / ms_b},
-            "distinct_shapes_pg": len(shapes)}
+    cores = os.cpu_count() or 1
+    nsample = args.ref_sample or REF_SAMPLE.get(w["name"], 200)
+    chosen = FORMS[w["name"]][0]
+    per = []
+    for i in range(args.warmup + args.steps):
+        b = cpu_baseline(w, nsample, chosen["moments"] if w["q"] >= 3 else 0)
+        if i >= args.warmup:
+            per.append(b["ms_per_step"])
+    ms = float(np.mean(per))
+    value = nsample * w["g"] / (ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": w["name"], "n": w["n"], "p": w["p"], "q": w["q"], "g": w["g"],
+                       "qmc": f"{w['qmc']['npoints']}x{w['qmc']['nshifts']}",
+                       "form": ("single-pass moments" if chosen["moments"] and w["q"] >= 3
+                                else "moment recursion"),
+                       "precision": "fp64 throughout (the CPU oracle)",
+                       "parallelism": f"{cores} host threads (OpenMP over observations)",
+                       "sample_n": nsample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"first {nsample} observations per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -297,238 +475,110 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--workload", default="flow_p4")
+    ap.add_argument("--workload", default="wide_p16")
     ap.add_argument("--n", type=int, default=None, help="override the workload size")
-    ap.add_argument("--precision", choices=["fp32", "fp64", "mixed"], default="fp32")
-    ap.add_argument("--moments", choices=["single-pass", "recursion"], default="single-pass",
-                    help="truncated-t moments of the timed form (the plain recursion is "
-                         "also timed when single-pass is chosen)")
-    ap.add_argument("--ref-sample", type=int, default=160)
-    ap.add_argument("--cpu-sample", type=int, default=240)
+    ap.add_argument("--sub", default="flow_p4,learned_p6,batch",
+                    help="comma-separated workloads measured as sub-objects ('' for none)")
+    ap.add_argument("--sub-steps", type=int, default=3)
+    ap.add_argument("--sub-warmup", type=int, default=3)
+    ap.add_argument("--ref-sample", type=int, default=None)
+    ap.add_argument("--cpu-sample", type=int, default=None)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fit-check", action="store_true")
+    ap.add_argument("--rates-seconds", type=float, default=1.5)
     ap.add_argument("--nfits", type=int, default=64, help="batch workload: problems")
     ap.add_argument("--starts", type=int, default=4, help="batch workload: starts per problem")
-    ap.add_argument("--surrogate", action="store_true",
-                    help="learned surrogate form (single-pass moments, q >= 3): train at the start "
-                         "values (untimed), then time E-steps through the network")
-    ap.add_argument("--surrogate-refresh", type=int, default=5,
-                    help="surrogate form: every R-th step is a lattice E-step that also fine-tunes "
-                         "the network on its records (timed); 0: never")
-    ap.add_argument("--surrogate-refresh-epochs", type=int, default=4)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    subs = [s for s in args.sub.split(",") if s] if world == 1 else []
 
     if args.workload == "batch":
-        if args.impl == "gpu":
-            run_batch(args, rank, world)
-        elif rank == 0:
-            print(json.dumps({"impl": "reference", "unavailable": "the batch workload has no "
-                              "oracle leg; time the oracle on a single-fit workload"}))
-        return
-
+        if args.impl == "reference":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable": "the batch workload has no "
+                                  "oracle leg; time the oracle on a single-fit workload"}))
+            return
     from paper_1606_02054_gb300 import synth
 
-    w = synth.make_workload(args.workload, n=args.n)
-    w["name"] = args.workload
-
+    w = None
+    if args.workload != "batch":
+        w = synth.make_workload(args.workload, n=args.n)
+        w["name"] = args.workload
     if args.impl == "reference":
         run_reference(args, w, rank, world)
         return
 
+    # CPU leg first (in-process OpenMP threads; no fork after CUDA initialisation): the
+    # timed oracle baseline and the oracle fits every form's error is measured against
+    cpu, refs, sub_w, sub_refs = None, None, {}, {}
+    if rank == 0 and w is not None:
+        chosen = FORMS[w["name"]][0]
+        if not args.no_cpu_baseline:
+            cpu = cpu_baseline(w, args.cpu_sample or CPU_SAMPLE.get(w["name"], 200),
+                               chosen["moments"] if w["q"] >= 3 else 0)
+        if not args.no_fit_check:
+            refs = oracle_fits(w, FORMS[w["name"]], *FIT_SAMPLE[w["name"]])
+        for s in subs:
+            if s == "batch":
+                continue
+            ws = synth.make_workload(s)
+            ws["name"] = s
+            sub_w[s] = ws
+            if not args.no_fit_check:
+                sub_refs[s] = oracle_fits(ws, FORMS[s], *FIT_SAMPLE[s])
+
     import torch
 
-    # CPU baseline first (in-process OpenMP threads; no fork after CUDA init)
-    cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w, args.cpu_sample, 1, 1 if args.moments == "single-pass" else 0)
-
     torch.cuda.set_device(local)
-    dist = None
+    shard = None
     if world > 1:
-        import torch.distributed as dist
+        from paper_1606_02054_gb300 import shard as shard_mod
 
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        shard = shard_mod.TorchGroup.from_env("nccl", local)
 
     from paper_1606_02054_gb300 import build
 
     build.build()
     import paper_1606_02054_gb300 as cf
 
-    prec = {"fp32": cf.CFUST_PREC_FP32, "fp64": cf.CFUST_PREC_FP64,
-            "mixed": cf.CFUST_PREC_MIXED}[args.precision]
     stream = torch.cuda.current_stream()
-    # the wide workload stores its observations in FP32
-    y_dtype = torch.float32 if w["name"] == "wide_p16" else torch.float64
-    y_dev = torch.tensor(w["y"], dtype=y_dtype, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    rates = cf.cfust_measure_rates(local, args.rates_seconds)
+
+    if w is None:  # the batch workload alone
+        b, clk = run_batch(args, cf, torch, stream, flush, with_clocks=True)
+        if rank == 0:
+            line = {"metric": METRIC, "value": b["chosen"]["value"] * world, "unit": UNIT, "n_gpus": world,
+                    "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["chosen"]["ms_per_step"],
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                    "data": "synthetic", "config": {**{k: v for k, v in b.items() if k not in ("chosen", "plain")},
+                                                     "l2": "flushed (256 MB write) before every timed step",
+                                                     "parallelism": f"replicas x{world}"},
+                    "gpu_launches": b["chosen"]["gpu_launches"], "clocks": clk,
+                    "plain_gpu": b["plain"], "speedup_of_chosen": b["speedup_of_chosen"], "rates": rates}
+            print(json.dumps(line), flush=True)
+        return
+
+    main_out, runs, w, y_dev = run_workload(cf, torch, w["name"], args, stream, flush, args.steps,
+                                            args.warmup, True, refs, FIT_SAMPLE[w["name"]], rates,
+                                            shard=shard, w=w)
+    chosen_form = FORMS[w["name"]][0]
+    run = runs["chosen"]
+    ms = run["ms"]
     pairs = w["n"] * w["g"]
+    value = pairs / (ms / 1e3)  # every rank's rows together: the whole problem
 
-    def measure(moments, with_clocks, surrogate=False):
-        """warm-up, then `steps` timed EM iterations (CUDA events per step, L2
-        flushed before each); returns timings and the library's kernel profile."""
-        ctx = cf.cfust_create(w["p"], w["q"], w["g"], w["n"],
-                              _opts(cf, w, prec, profile=1, stream=stream.cuda_stream,
-                                    moments=moments))
-        cf.cfust_set_data(ctx, y_dev)
-        cf.cfust_set_params(ctx, w["init"])
-        sur = None
-        if surrogate:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            ll_lat, losses = cf.cfust_surrogate_train(ctx)
-            torch.cuda.synchronize()
-            t_train = time.perf_counter() - t0
-            ll_sur = cf.cfust_loglik(ctx)  # the density pass through the network, same Psi
-            o = cf.cfust_surrogate_default_opts()
-            sur = {"train_s": t_train, "epochs": o.epochs, "batch": o.batch,
-                   "samples_per_epoch": o.samples_per_epoch, "loss_first": float(losses[0]),
-                   "loss_last": float(losses[-1]), "loglik_lattice_at_start": ll_lat,
-                   "loglik_surrogate_at_start": ll_sur,
-                   "loglik_rel_err_at_start": abs(ll_sur - ll_lat) / abs(ll_lat)}
-
-        count = [0]
-        ft = cf.cfust_surrogate_default_opts(epochs=args.surrogate_refresh_epochs) if surrogate else None
-
-        def step():
-            R = args.surrogate_refresh
-            if surrogate and R > 0 and count[0] > 0 and count[0] % R == 0:
-                L, _ = cf.cfust_surrogate_train(ctx, ft)  # a lattice E-step, then fine-tuning
-            else:
-                L = cf.cfust_estep(ctx)
-            cf.cfust_mstep(ctx)
-            count[0] += 1
-            return L
-
-        for _ in range(args.warmup):
-            step()
-        torch.cuda.synchronize()
-        cf.cfust_profile(ctx, reset=True)
-        n0 = cf.cfust_launch_count(ctx)
-        clocks = Clocks(local) if with_clocks else None
-        if clocks:
-            clocks.start()
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        total_ms, lls = 0.0, []
-        for _ in range(args.steps):
-            flush.fill_(1.0)  # evict L2 before each timed step
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            lls.append(step())
-            e1.record(stream)
-            e1.synchronize()
-            total_ms += e0.elapsed_time(e1)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        clk = clocks.stop() if clocks else None
-        launches = cf.cfust_launch_count(ctx) - n0
-        prof = cf.cfust_profile(ctx)
-        ms = total_ms / args.steps
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        estep_ms = sum(v[0] for k, v in prof.items() if k != "mstep") / args.steps
-        if sur is not None:
-            recs, fb = cf.cfust_surrogate_info(ctx)
-            sur["fallback_fraction_last_surrogate_step"] = fb / max(recs, 1)
-            sur["refresh_every"] = args.surrogate_refresh
-            sur["refresh_epochs"] = args.surrogate_refresh_epochs
-            cf.cfust_surrogate_use(ctx, 0)
-        # l at the final parameters by the lattice density pass (the same yardstick for every form)
-        ll_final = cf.cfust_loglik(ctx) if args.surrogate else None
-        return dict(ll_final=ll_final, ms=ms, prof=prof, launches=launches, ll=lls[-1], clk=clk, estep_ms=estep_ms, sur=sur)
-
-    chosen_moments = 1 if args.moments == "single-pass" else 0
-    if args.surrogate and not (chosen_moments == 1 and w["q"] >= 3):
-        raise SystemExit("--surrogate needs single-pass moments and q >= 3")
-    main_run = measure(chosen_moments, True, surrogate=args.surrogate)
-    plain_run = measure(0, False) if chosen_moments == 1 and w["q"] >= 3 and not args.surrogate else None
-    lattice_run = measure(chosen_moments, False) if args.surrogate else None
-    ms, prof, clk = main_run["ms"], main_run["prof"], main_run["clk"]
-    launches = main_run["launches"]
-    value = pairs * world / (ms / 1e3)
-
-    # dominant kernel class and its roofline
-    cls = {"level0_Tq": (w["q"], 1 if chosen_moments and w["q"] >= 3 else 2),
-           "level1_Tq-1": (w["q"] - 1, w["q"]),
-           "level2_Tq-2": (w["q"] - 2, w["q"] * (w["q"] - 1)),
-           "moments_Tq": (w["q"], 1)}
-    lat_classes = [k for k in cls if prof[k][1] > 0 and cls[k][0] >= 2]
-    dom = max(lat_classes, key=lambda k: prof[k][0])
-    dom_ms_per_launch = prof[dom][0] / prof[dom][1]
-    kdim, mult = cls[dom]
-    kind = "moments" if dom == "moments_Tq" else ("t2" if kdim == 2 else "lattice")
-    records = pairs * mult
-    units = records * (w["qmc"]["npoints"] * w["qmc"]["nshifts"] if kind != "t2" else 1)
-    unit_name = "record" if kind == "t2" else "lattice point"
-    f_sm = (clk.get("sm_mhz") or _peaks().get("sm_max_mhz", 2070.0)) * 1e6
-    key = _unit_key(kind, kdim, args.precision)
-    ipu = INSTR_PER_UNIT.get(key) if key else None
-    secs = dom_ms_per_launch / 1e3
-    if args.surrogate and prof["surrogate"][1] > 0:
-        # the network's inference kernel: one launch per record set (n g records), a dense
-        # BF16 contraction; algorithmic FLOPs of the used widths (nin -> 256 -> 256 -> 256 -> nout)
-        q = w["q"]
-        nin, nout = q + q * (q - 1) // 2 + 1, 1 + q + q * (q + 1) // 2
-        flops_rec = 2 * (nin * 256 + 2 * 256 * 256 + 256 * nout)
-        ms_l = prof["surrogate"][0] / prof["surrogate"][1]
-        achieved = flops_rec * pairs / (ms_l / 1e3) / 1e12
-        peak = _peaks().get("bf16_tflops")
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak if peak else None, "traffic": None,
-                "kernel": "mlp_infer_kernel", "flops_per_record": flops_rec, "records_per_launch": pairs,
-                "ms_per_launch": ms_l,
-                "peak_basis": "MEASURED_PEAKS.json bf16_tflops (burst, cuBLAS 8192^3) of measured",
-                "note": "mma.sync m16n8k16 BF16 (legacy tensor path), weights staged per layer in shared memory"}
-    elif ipu:
-        achieved = ipu * units / secs / 1e12
-        peak = SM_COUNT * LANES_PER_SM * f_sm / 1e12
-        tb = INTEG_TRAFFIC_BYTES_PER_RECORD.get(key)
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "Tinst/s", "frac": achieved / peak,
-                "traffic": tb * records if tb else None,
-                "kernel": dom, "k": kdim, "units_per_launch": units, "unit_of_work": unit_name,
-                "inst_per_unit": ipu, "g_units_per_s": units / secs / 1e9,
-                "ms_per_launch": dom_ms_per_launch,
-                "peak_basis": "152 SMs x 128 lanes x 1 thread-instruction/clock at the sampled "
-                              "median SM clock (issue-slot ceiling)"}
-    else:
-        roof = {"bound": "alu", "achieved": units / secs / 1e9, "peak": None,
-                "unit": f"G{unit_name.split()[-1]}s/s", "frac": None, "traffic": None,
-                "kernel": dom, "k": kdim, "units_per_launch": units, "unit_of_work": unit_name,
-                "ms_per_launch": dom_ms_per_launch,
-                "note": "no instruction count measured for this kernel and precision"}
-
-    # the stated loglik error: the GPU's E-step l on the CPU baseline's sample (same
-    # observations, starting values and lattice) against the oracle's
-    ll_check = None
-    if cpu is not None and cpu.get("loglik_at_start") is not None:
-        ns = args.cpu_sample
-        cchk = cf.cfust_create(w["p"], w["q"], w["g"], ns, _opts(cf, w, prec, moments=chosen_moments))
-        cf.cfust_set_data(cchk, np.ascontiguousarray(w["y"][:ns]))
-        cf.cfust_set_params(cchk, w["init"])
-        lg = cf.cfust_estep(cchk)
-        lo = cpu["loglik_at_start"]
-        ll_check = {"rel_err": abs(lg - lo) / abs(lo), "gpu": lg, "oracle": lo,
-                    "sample": f"first {ns} observations at the starting values, same lattice"}
-
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers: each step copies the observations
+    # and the parameters in, runs the EM iteration, and copies the parameters out
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and shard is None:
         p, q, g = w["p"], w["q"], w["g"]
-        ctx2 = cf.cfust_create(p, q, g, w["n"], _opts(cf, w, prec, stream=stream.cuda_stream,
-                                                      moments=chosen_moments))
-        # pinned host copy in the workload's storage type (FP32 for the wide workload)
-        y_host = torch.from_numpy(np.ascontiguousarray(
-            w["y"], dtype=np.float32 if w["name"] == "wide_p16" else np.float64)).pin_memory()
+        ctx2 = cf.cfust_create(p, q, g, w["n"], _opts(cf, w, chosen_form, stream=stream.cuda_stream))
+        y_host = torch.from_numpy(_y_store(w)).pin_memory()
         params = {k: np.array(v, dtype=float) for k, v in w["init"].items()}
         pbytes = 8 * (g + g * p + g * p * p + g * p * q + g)
 
@@ -547,60 +597,47 @@ def main():
             params = e2e_step(params)
         torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-        if dist:
-            t = torch.tensor([e2e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": pairs * world / (e2e_ms / 1e3), "unit": UNIT,
+        e2e = {"value": pairs / (e2e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(y_host.numel() * y_host.element_size() + pbytes),
                "d2h_bytes_per_step": int(pbytes + 8 + 4 + 4 * g), "ms_per_step": e2e_ms}
+        del ctx2
+
+    sub = {}
+    for s in subs:
+        torch.cuda.synchronize()
+        if s == "batch":
+            sub[s], _ = run_batch(args, cf, torch, stream, flush, steps=args.sub_steps, warmup=args.sub_warmup)
+        else:
+            sub[s], _, _, _ = run_workload(cf, torch, s, args, stream, flush, args.sub_steps, args.sub_warmup,
+                                           False, sub_refs.get(s), FIT_SAMPLE[s], rates, w=sub_w.get(s),
+                                           plain_steps=SUB_PLAIN_STEPS.get(s), plain_warmup=SUB_PLAIN_STEPS.get(s))
+        torch.cuda.empty_cache()
 
     if rank == 0:
-        form = ("single-pass moments" if chosen_moments and w["q"] >= 3 else "moment recursion")
+        ch = main_out["chosen"]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic",
-                "config": {"workload": w["name"], "n": w["n"], "p": w["p"], "q": w["q"],
-                           "g": w["g"], "qmc": f"{w['qmc']['npoints']}x{w['qmc']['nshifts']}",
-                           "form": form,
-                           "precision": PRECISION_NOTE[args.precision],
-                           "l2": "flushed (256 MB write) before every timed step",
-                           "parallelism": f"replicas x{world}"},
+                "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
+                "vs_baseline": None,
+                "dtype": "f64" if chosen_form["precision"] == "fp64" else "f32", "data": "synthetic",
+                "config": {"workload": w["name"], "n": w["n"], "p": w["p"], "q": w["q"], "g": w["g"],
+                           "qmc": main_out["qmc"], "form": ch["form"],
+                           "y_storage": "fp32" if w["name"] in Y32_WORKLOADS else "fp64",
+                           "l2": "flushed (256 MB write) before every timed step; inputs > L2",
+                           "parallelism": (f"rows sharded over {world} ranks, one all-gather of the "
+                                           f"segment statistics per iteration" if world > 1 else "1 GPU")},
                 "em_iter_per_s": 1e3 / ms,
-                "estep_obs_comp_per_s": pairs * world / (main_run["estep_ms"] / 1e3),
-                "loglik_last": main_run["ll"],
-                "gpu_launches": int(launches),
-                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
-                "roofline": roof, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
-                "loglik_check": ll_check}
-        if main_run["sur"] is not None:
-            line["config"]["form"] = ("learned surrogate (BF16 MLP, lattice fallback; every "
-                                      f"{args.surrogate_refresh}th step a lattice E-step that fine-tunes it) "
-                                      "+ single-pass moments")
-            line["surrogate"] = main_run["sur"]
-            line["gpu_launches_note"] = ("E- and M-step kernels; the refresh steps' training kernels "
-                                         "(GEMMs, Adam) are not counted")
-            line["surrogate"]["loglik_final_by_lattice"] = main_run["ll_final"]
-            line["surrogate"]["loglik_final_lattice_form"] = lattice_run["ll_final"]
-            line["surrogate"]["loglik_final_rel_diff"] = (abs(main_run["ll_final"] - lattice_run["ll_final"])
-                                                          / abs(lattice_run["ll_final"]))
-            line["lattice_gpu"] = {
-                "form": "single-pass moments, lattice only", "value": pairs * world / (lattice_run["ms"] / 1e3),
-                "unit": UNIT, "ms_per_step": lattice_run["ms"],
-                "estep_obs_comp_per_s": pairs * world / (lattice_run["estep_ms"] / 1e3),
-                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in lattice_run["prof"].items()}}
-        if plain_run:
-            line["plain_gpu"] = {
-                "form": "moment recursion (T_q, T_{q-1}, T_{q-2} records)",
-                "value": pairs * world / (plain_run["ms"] / 1e3), "unit": UNIT,
-                "ms_per_step": plain_run["ms"], "em_iter_per_s": 1e3 / plain_run["ms"],
-                "estep_obs_comp_per_s": pairs * world / (plain_run["estep_ms"] / 1e3),
-                "loglik_last": plain_run["ll"], "gpu_launches": int(plain_run["launches"]),
-                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in plain_run["prof"].items()}}
+                "estep_obs_comp_per_s": ch["estep_obs_comp_per_s"],
+                "loglik_last": ch["loglik_last"],
+                "gpu_launches": ch["gpu_launches"],
+                "kernel_ms_per_step": ch["kernel_ms_per_step"],
+                "roofline": ch["roofline"], "clocks": run["clk"], "e2e": e2e, "cpu_baseline": cpu,
+                "loglik_err": ch.get("loglik_err"),
+                "plain_gpu": main_out["plain"], "speedup_of_chosen": main_out["speedup_of_chosen"],
+                "rates": rates, "sub": sub}
         print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
+    if shard is not None:
+        shard.close()
 
 
 if __name__ == "__main__":

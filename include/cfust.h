@@ -274,15 +274,20 @@ cfust_status cfust_tk_eval(cfust_ctx* ctx, int k, int count, const double* b, co
  *   y (n x p), pi (g), mu (g x p) at which r = y - mu is centred, logf, u,
  *   elogu (g*n), eu (g*n*q), euu (g*n*q*q) in;  tau (g*n, may be NULL) and
  *   stats (g*(3+p+q+pq+q^2+p^2) + 1 doubles: the per-component statistics,
- *   then l of eq (27)) out.
+ *   then the log-likelihood sum over observations) out.
  * Work is issued on cuda_stream (NULL = legacy default stream) and the call
  * returns after it completes.  Its only scratch, the per-block partial sums
  * and an error flag, lives in a fixed device array of 2^19 doubles (4 MiB)
  * that every GPU loading the library holds until exit: sizes needing more
  * than ceil(n/chunk) x (g*(3+p+q+pq+q^2+p^2)+1) <= 2^19 partial sums (chunk
- * <= 256 observations per block) are rejected with CFUST_EINVAL.  The first
- * call on each device looks up the scratch's device address, so make that
- * first call before any stream capture.  All calls share the scratch and it
+ * <= 256 observations per block, fewer when p, q or g are large) are
+ * rejected with CFUST_EINVAL.  Every call looks up the scratch's device
+ * address in the current context (the address belongs to the context, so a
+ * context created after cudaDeviceReset gets its own); the first call in a
+ * context also loads the library's device code there, so make the first
+ * call on each device before any stream capture.  The block size is chosen
+ * without raising the default shared-memory limit, so the statistics equal
+ * those of cfust_estep to rounding, not bit for bit.  All calls share the scratch and it
  * keeps the last call's contents: calls that overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.
  * Errors are reported through cfust_last_error(NULL). */
@@ -291,6 +296,37 @@ cfust_status cfust_reduce_stats_noalloc(int p, int q, int g, int64_t n, const do
                                         const double* u, const double* elogu, const double* eu,
                                         const double* euu, double* tau, double* stats,
                                         void* cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Pipe rates (not part of the paper): the denominators of the E-step's
+ * roofline.  The lattice integrators of T_k are bound by per-point arithmetic
+ * (normal CDF and inverse on the MUFU and FMA pipes, FP32 FMAs), for which no
+ * data-sheet figure states an achievable rate, so the library measures them
+ * on the device it runs on.  All rates are whole-GPU operations per second.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double sm_mhz;        /* SM clock during the measurement: clock64() cycles / event time */
+    double fp32_fma;      /* FP32 FMA per second (8 independent chains per thread) */
+    double fp64_fma;      /* FP64 FMA per second */
+    double mufu_ex2;      /* ex2.approx.ftz.f32 per second */
+    double mufu_lg2;      /* lg2.approx.ftz.f32 per second */
+    double mufu_rcp;      /* rcp.approx.ftz.f32 per second */
+    double mix_points[9]; /* [K], K = 3..8: lattice points per second of the single-pass
+                             integrand of dimension K alone -- K normal CDFs, K inverse
+                             normal CDFs (the FP32 forms of the integrators), the
+                             K(K-1)/2 + 3K FMAs of the chain and the 2 + K + K(K+1)/2
+                             FMAs of the weighted moment sums per point, two independent
+                             points per thread, no memory traffic; [0..2] unused (0) */
+    double t2_nodes;      /* nodes per second of the FP32 T_2 quadrature alone -- per node
+                             two sines, the sin^(nu-1) weight (lg2, ex2) and the inner T_1
+                             from its per-dof table -- two independent nodes per thread */
+} cfust_rates;
+
+/* Run the microbenchmarks on `device` for about `seconds` (0 < seconds <= 5) in
+ * all, on the legacy default stream, and fill *out.  Allocates one scratch
+ * buffer (8 x SMs x 256 doubles and a 32 KB table) for the duration of the call.  Changes no
+ * device setting (clocks are read, never set). */
+cfust_status cfust_measure_rates(int device, double seconds, cfust_rates* out);
 
 /* Last error message of ctx (or of the last failed cfust_create when ctx is
  * NULL).  Valid until the next call on the same context. */
@@ -315,6 +351,15 @@ cfust_status cfust_debug_read(cfust_ctx* ctx, int what, void* dst, int64_t bytes
  * may be NULL).  Requires opts.profile = 1 (else CFUST_ESTATE).  reset = 1
  * zeroes the totals after reading. */
 cfust_status cfust_profile(cfust_ctx* ctx, double* ms, int64_t* launches, int reset);
+
+/* Algorithmic work done by each kernel class since creation or the last
+ * cfust_profile reset (units: CFUST_NPROF entries): lattice points (records x
+ * N x M) for the lattice T_k classes (k >= 3: level 0-2 and the single-pass
+ * moments), quadrature nodes for T_2 records (counted on the device), records
+ * for T_1; 0 for the other classes and for records a surrogate selection list
+ * sends to the lattice.  Requires opts.profile = 1 (else CFUST_ESTATE).  The
+ * numerator of the integrators' roofline (see cfust_measure_rates). */
+cfust_status cfust_profile_work(cfust_ctx* ctx, double* units);
 
 /* ------------------------------------------------------------------------
  * Learned surrogate (not part of the paper).  A 3 x 256 tanh MLP with BF16

@@ -57,6 +57,12 @@ class cfust_opts(C.Structure):
                 ("hold", C.c_int), ("model", C.c_int)]
 
 
+class cfust_rates(C.Structure):
+    _fields_ = [("sm_mhz", C.c_double), ("fp32_fma", C.c_double), ("fp64_fma", C.c_double),
+                ("mufu_ex2", C.c_double), ("mufu_lg2", C.c_double), ("mufu_rcp", C.c_double),
+                ("mix_points", C.c_double * 9), ("t2_nodes", C.c_double)]
+
+
 class cfust_params(C.Structure):
     _fields_ = [("pi", C.POINTER(C.c_double)), ("mu", C.POINTER(C.c_double)),
                 ("Sigma", C.POINTER(C.c_double)), ("Delta", C.POINTER(C.c_double)),
@@ -104,10 +110,14 @@ def lib():
             L.cfust_launch_count.restype = i64
             L.cfust_profile.argtypes = [vp, _dp, C.POINTER(C.c_int64), i]
             L.cfust_profile.restype = i
+            L.cfust_profile_work.argtypes = [vp, _dp]
+            L.cfust_profile_work.restype = i
             L.cfust_debug_read.argtypes = [vp, i, vp, i64, C.POINTER(C.c_int64)]
             L.cfust_debug_read.restype = i
             L.cfust_reduce_stats_noalloc.argtypes = [i, i, i, i64] + [vp] * 11
             L.cfust_reduce_stats_noalloc.restype = i
+            L.cfust_measure_rates.argtypes = [i, d, C.POINTER(cfust_rates)]
+            L.cfust_measure_rates.restype = i
             f32p = C.POINTER(C.c_float)
             L.cfust_mlp_init.argtypes = [C.c_uint64, i, i, vp, i]
             L.cfust_mlp_grad.argtypes = [vp, i64, i, vp, vp, vp, vp, vp, _dp, i]
@@ -426,6 +436,14 @@ def cfust_profile(ctx: Context, reset=False):
     return {PROF_NAMES[k]: (float(ms[k]), int(n[k])) for k in range(CFUST_NPROF)}
 
 
+def cfust_profile_work(ctx: Context):
+    """{class name: algorithmic units} since creation or the last profile reset
+    (lattice points, T_2 quadrature nodes or T_1 records; see include/cfust.h)."""
+    u = np.zeros(CFUST_NPROF)
+    _check(lib().cfust_profile_work(ctx.handle, _ptr(u)), ctx)
+    return {PROF_NAMES[k]: float(u[k]) for k in range(CFUST_NPROF)}
+
+
 def cfust_debug_read(ctx: Context, what, nbytes=1 << 30, dtype=np.float64):
     """Internal device buffer `what` (see include/cfust.h) as a numpy array."""
     buf = np.zeros(max(1, nbytes // np.dtype(dtype).itemsize), dtype=dtype)
@@ -438,18 +456,46 @@ def cfust_debug_read(ctx: Context, what, nbytes=1 << 30, dtype=np.float64):
 def cfust_reduce_stats_noalloc(p, q, g, n, y, pi, mu, logf, u, elogu, eu, euu, tau, stats,
                                stream=None):
     """Allocation-free reduction: all array arguments are CUDA torch tensors
-    (float64, contiguous) on the current device; tau may be None."""
-    def dp(t):
+    (float64, contiguous) on the current device; tau may be None.  Every
+    tensor must hold at least the elements the library reads or writes
+    (y n*p; pi g; mu g*p; logf, u, elogu, tau g*n; eu g*n*q; euu g*n*q*q;
+    stats g*(3+p+q+pq+q^2+p^2)+1): a short one is rejected here, before the
+    call, since the library cannot check a device pointer's extent."""
+    p, q, g, n = int(p), int(q), int(g), int(n)
+    need = {"y": n * p, "pi": g, "mu": g * p, "logf": g * n, "u": g * n, "elogu": g * n,
+            "eu": g * n * q, "euu": g * n * q * q, "tau": g * n,
+            "stats": g * (3 + p + q + p * q + q * q + p * p) + 1}
+
+    def dp(t, name):
         if t is None:
             return None
         if not (t.is_cuda and t.is_contiguous()) or t.element_size() != 8:
             raise CfustError(CFUST_EINVAL, "device float64 contiguous tensors required")
+        if t.numel() < need[name]:
+            raise CfustError(CFUST_EINVAL, f"cfust_reduce_stats_noalloc: {name} holds {t.numel()} "
+                                           f"elements, {need[name]} needed")
         return C.c_void_p(t.data_ptr())
 
-    st = lib().cfust_reduce_stats_noalloc(int(p), int(q), int(g), int(n), dp(y), dp(pi), dp(mu),
-                                          dp(logf), dp(u), dp(elogu), dp(eu), dp(euu), dp(tau),
-                                          dp(stats), None if stream is None else C.c_void_p(stream))
+    if p < 1 or q < 1 or g < 1 or n < 1:
+        raise CfustError(CFUST_EINVAL, "cfust_reduce_stats_noalloc: sizes out of range")
+    if any(t is None for t in (y, pi, mu, logf, u, elogu, eu, euu, stats)):
+        raise CfustError(CFUST_EINVAL, "cfust_reduce_stats_noalloc: NULL device pointer")
+    st = lib().cfust_reduce_stats_noalloc(p, q, g, n, dp(y, "y"), dp(pi, "pi"), dp(mu, "mu"),
+                                          dp(logf, "logf"), dp(u, "u"), dp(elogu, "elogu"),
+                                          dp(eu, "eu"), dp(euu, "euu"), dp(tau, "tau"),
+                                          dp(stats, "stats"), None if stream is None else C.c_void_p(stream))
     return _check(st, None)
+
+
+def cfust_measure_rates(device=0, seconds=1.5):
+    """Pipe-rate microbenchmarks of the device (see include/cfust.h): a dict of
+    whole-GPU rates per second, mix_points keyed by dimension K = 3..8."""
+    r = cfust_rates()
+    _check(lib().cfust_measure_rates(int(device), float(seconds), C.byref(r)), None)
+    out = {k: float(getattr(r, k)) for k in ("sm_mhz", "fp32_fma", "fp64_fma", "mufu_ex2",
+                                             "mufu_lg2", "mufu_rcp", "t2_nodes")}
+    out["mix_points"] = {K: float(r.mix_points[K]) for K in range(3, 9)}
+    return out
 
 
 def params_from_workload(params):

@@ -79,6 +79,8 @@ struct cfust_ctx {
     bool pending[CFUST_NPROF]{};
     double prof_ms[CFUST_NPROF]{};
     long long prof_n[CFUST_NPROF]{};
+    double prof_units[CFUST_NPROF]{};            // algorithmic work (cfust_profile_work)
+    unsigned long long* work_dev = nullptr;      // device counts of T_2 quadrature nodes per class
     // pinned host scratch
     double* h_ll = nullptr;
     int* h_flags = nullptr;
@@ -209,6 +211,13 @@ static void prof_end(cfust_ctx* c, int k, long long launches)
 static void prof_collect(cfust_ctx* c)
 {
     if (!c->opts.profile) return;
+    if (c->work_dev) {  // device-counted work (T_2 nodes), after the stream synchronised
+        unsigned long long w[CFUST_NPROF];
+        if (cudaMemcpy(w, c->work_dev, sizeof(w), cudaMemcpyDeviceToHost) == cudaSuccess) {
+            for (int k = 0; k < CFUST_NPROF; ++k) c->prof_units[k] += (double)w[k];
+            cudaMemset(c->work_dev, 0, sizeof(w));
+        }
+    }
     for (int k = 0; k < CFUST_NPROF; ++k)
         if (c->pending[k]) {
             float ms = 0.f;
@@ -281,8 +290,17 @@ extern "C" cfust_status cfust_profile(cfust_ctx* c, double* ms, int64_t* launche
     for (int k = 0; k < CFUST_NPROF; ++k) {
         if (ms) ms[k] = c->prof_ms[k];
         if (launches) launches[k] = c->prof_n[k];
-        if (reset) { c->prof_ms[k] = 0.0; c->prof_n[k] = 0; }
+        if (reset) { c->prof_ms[k] = 0.0; c->prof_n[k] = 0; c->prof_units[k] = 0.0; }
     }
+    return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_profile_work(cfust_ctx* c, double* units)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_profile_work: ctx is NULL");
+    if (!units) return fail(c, CFUST_EINVAL, "cfust_profile_work: units is NULL");
+    if (!c->opts.profile) return fail(c, CFUST_ESTATE, "cfust_profile_work: context created without opts.profile");
+    for (int k = 0; k < CFUST_NPROF; ++k) units[k] = c->prof_units[k];
     return CFUST_OK;
 }
 
@@ -293,7 +311,8 @@ static void free_all(cfust_ctx* c)
                     c->Delta_n, c->nu_n, c->F, c->dofs, c->cst64, c->cst32, c->chi64, c->chi32, c->shf64, c->shf32, c->wtab,
                     c->glx64, c->glw64, c->glx32, c->glw32, c->glx32h, c->glw32h, c->logf, c->u, c->elogu, c->eu,
                     c->euu, c->se, c->tau, c->partial, c->stats, c->flags, c->comp_status,
-                    c->stage32, c->pd, c->pc, c->fix_count, c->fix_list, c->y32, c->F32, c->t1tab};
+                    c->stage32, c->pd, c->pc, c->fix_count, c->fix_list, c->y32, c->F32, c->t1tab,
+                    c->work_dev};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (RecSet& r : c->rec) {
@@ -521,6 +540,13 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     }
     cudaFuncSetAttribute(estep_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     cudaFuncSetAttribute(estep_reduce_kernel_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    if (o.profile &&
+        (cudaMalloc((void**)&c->work_dev, sizeof(unsigned long long) * CFUST_NPROF) != cudaSuccess ||
+         cudaMemset(c->work_dev, 0, sizeof(unsigned long long) * CFUST_NPROF) != cudaSuccess)) {
+        free_all(c);
+        delete c;
+        return fail(nullptr, CFUST_ENOMEM, "cfust_create: profiler counters");
+    }
     if (o.profile)
         for (int k = 0; k < CFUST_NPROF; ++k)
             for (int i = 0; i < 2; ++i)
@@ -670,6 +696,7 @@ static IntegArgs integ_args(const cfust_ctx* c)
     ia.glx32h = c->glx32h; ia.glw32h = c->glw32h;
     ia.t1tab = c->t1tab;
     ia.wtab = c->wtab;
+    ia.nodes = nullptr;
     return ia;
 }
 
@@ -729,7 +756,15 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
             r.sel = c->sur.fall0;
             r.nsel = c->sur.nfall;
         }
-        if ((e = launch_integrals(r, ia, fp32, c->nsm, c->st, &c->launches)) != cudaSuccess)
+        IntegArgs il = ia;
+        if (c->opts.profile && !c->capturing) {
+            // algorithmic work: T_2 nodes counted on the device; lattice points (records x
+            // N x M) and T_1 records here (selection lists: counted by the surrogate's info)
+            if (r.k == 2) il.nodes = c->work_dev + CFUST_PROF_LEVEL0 + l;
+            else if (r.k >= 3 && !(sur && l == 0)) c->prof_units[CFUST_PROF_LEVEL0 + l] += (double)r.nrec * c->lat.N * c->lat.M;
+            else if (r.k == 1) c->prof_units[CFUST_PROF_LEVEL0 + l] += (double)r.nrec;
+        }
+        if ((e = launch_integrals(r, il, fp32, c->nsm, c->st, &c->launches)) != cudaSuccess)
             return fail(c, CFUST_ECUDA, std::string("integral kernel: ") + cudaGetErrorString(e));
         prof_end(c, CFUST_PROF_LEVEL0 + l, c->launches - n0);
     }
@@ -742,6 +777,8 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
         if (sur) {
             rm.sel = c->sur.fallM;
             rm.nsel = c->sur.nfall + 1;
+        } else if (c->opts.profile && !c->capturing) {
+            c->prof_units[CFUST_PROF_MOMENTS] += (double)rm.nrec * c->lat.N * c->lat.M;
         }
         if ((e = launch_moments(rm, ia, fp32, c->nsm, c->st, &c->launches)) != cudaSuccess)
             return fail(c, CFUST_ECUDA, std::string("moment kernel: ") + cudaGetErrorString(e));

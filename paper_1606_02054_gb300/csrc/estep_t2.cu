@@ -12,6 +12,7 @@ __global__ void __launch_bounds__(256) t2_records_kernel(RecSet r, IntegArgs a)
     const R* glx = f32 ? (const R*)a.glx32 : (const R*)a.glx64;
     const R* glw = f32 ? (const R*)a.glw32 : (const R*)a.glw64;
     const R* cst = f32 ? (const R*)a.cst32 : (const R*)a.cst64;
+    unsigned long long nodes = 0;  // this warp's quadrature nodes (profiler count)
     for (long long i = warp; i < r.nrec; i += nwarps) {
         const R* c = cst + r.tab[i] * CST_STRIDE;
         R h, k, rho, nu, omr2, cr;
@@ -27,16 +28,19 @@ __global__ void __launch_bounds__(256) t2_records_kernel(RecSet r, IntegArgs a)
             cr = (R)(h64 * (rho64 > 0.0 ? rho64 : -rho64) - (rho64 > 0.0 ? k64 : -k64));
         }
         const float2* tab = f32 && a.t1tab ? a.t1tab + (size_t)r.tab[i] * T1TAB_N : nullptr;
+        int nn = 2 * a.t2n;
         const double v = isinf(nu) ? phi2_warp<R>(h, k, rho, a.t2n, glx, glw, lane)
                                    : t2cdf_warp<R>(h, k, rho, nu, omr2, cr, c[CST_LGB], c[CST_LGB1], c[CST_C2], a.t2n,
                                        glx, glw, f32 ? T2_NH : a.t2n,
                                        f32 ? (const R*)a.glx32h : glx, f32 ? (const R*)a.glw32h : glw,
-                                       lane, tab);
+                                       lane, tab, &nn);
+        nodes += (unsigned long long)nn;
         if (lane == 0) {
             r.res[i] = v;
             if (r.se) r.se[i] = 0.0;
         }
     }
+    if (a.nodes && lane == 0 && nodes) atomicAdd(a.nodes, nodes);
 }
 
 cudaError_t launch_t2(const RecSet& r, const IntegArgs& a, int fp32, int blocks, cudaStream_t st)

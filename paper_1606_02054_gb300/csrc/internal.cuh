@@ -175,6 +175,9 @@ struct IntegArgs {
     // baker-transformed coordinates w_d = 1 - |2 frac(i z_d / N + shift_md) - 1|, d = 1..q,
     // in one float4 (computed in FP64 at creation; they are the same for every record)
     const float4* wtab;
+    // T_2 records only (may be null): quadrature nodes evaluated, added once per warp
+    // (the profiler's algorithmic work count)
+    unsigned long long* nodes;
 };
 
 constexpr int T1TAB_N = 4096;

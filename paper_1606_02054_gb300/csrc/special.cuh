@@ -357,8 +357,9 @@ template <typename R>
 __device__ double t2cdf_warp(R h, R k, R rho, R nu, R omr2, R cr, R lgb, R lgb1, R C2, int n,
                              const R* __restrict__ glx, const R* __restrict__ glw, int nh,
                              const R* __restrict__ glxh, const R* __restrict__ glwh, int lane,
-                             const float2* __restrict__ t1tab = nullptr)
+                             const float2* __restrict__ t1tab = nullptr, int* nodes_out = nullptr)
 {
+    if (nodes_out) *nodes_out = 0;
     if (rho >= R(1)) {
         const R m = h < k ? h : k;
         return (double)t1cdf_dev<R>(m, nu, lgb);
@@ -373,6 +374,7 @@ __device__ double t2cdf_warp(R h, R k, R rho, R nu, R omr2, R cr, R lgb, R lgb1,
     const R* __restrict__ gx = graded ? glxh : glx;
     const R* __restrict__ gw = graded ? glwh : glw;
     const int npieces = S.split ? 2 : 1;
+    if (nodes_out) *nodes_out = npieces * nn;
     const R nu1 = nu + R(1), num1 = nu - R(1);
     R acc = R(0);
     for (int t = lane; t < npieces * nn; t += CF_WARP) {

@@ -19,7 +19,7 @@ def _run(*args):
 
 
 def test_reference_arm_line():
-    d = _run("--impl", "reference", "--steps", "1", "--warmup", "0", "--ref-sample", "12")
+    d = _run("--impl", "reference", "--workload", "flow_p4", "--steps", "1", "--warmup", "0", "--ref-sample", "12")
     assert d["impl"] == "reference"
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
@@ -46,10 +46,18 @@ def test_reference_arm_under_torchrun_prints_once():
     r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
                         "--master-addr", "127.0.0.1", "--master-port", str(port),
                         os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--steps", "1",
-                        "--warmup", "0", "--ref-sample", "8"],
+                        "--warmup", "0", "--ref-sample", "8", "--workload", "flow_p4"],
                        cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0
+
+
+def test_reference_arm_default_workload():
+    """With no workload named, the reference arm times the oracle on the default
+    (largest single-GPU) workload, p = 16, q = 2, g = 8, n = 2e6."""
+    d = _run("--impl", "reference", "--steps", "1", "--warmup", "0", "--ref-sample", "50")
+    assert d["config"]["workload"] == "wide_p16" and d["config"]["n"] == 2_000_000
+    assert d["config"]["sample_n"] == 50 and d["value"] > 0
