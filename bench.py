@@ -80,7 +80,10 @@ Y32_WORKLOADS = ("wide_p16",)  # observations stored in FP32
 # sized for a few seconds of oracle time on 16 host cores
 CPU_SAMPLE = {"wide_p16": 20000, "flow_p4": 2000, "learned_p6": 120, "two_comp_p2": 1000}
 REF_SAMPLE = {"wide_p16": 8000, "flow_p4": 400, "learned_p6": 40, "two_comp_p2": 1000}
-FIT_SAMPLE = {"wide_p16": (1000, 8), "flow_p4": (200, 6), "learned_p6": (40, 3), "two_comp_p2": (1000, 20)}
+FIT_SAMPLE = {"wide_p16": (1000, 8), "flow_p4": (200, 6), "learned_p6": (240, 3), "two_comp_p2": (1000, 20)}
+# the oracle's recursion at q = 6 (38 lattice integrals per pair) is too slow for a sample fit
+# inside the benchmark: there only the chosen form's fit is checked
+FIT_CHOSEN_ONLY = ("learned_p6",)
 # the plain recursion at p = q = g = 6 takes seconds per iteration (2 T_6 + 6 T_5 + 30 T_4
 # lattice integrals per pair): one warm-up and one timed step
 SUB_PLAIN_STEPS = {"learned_p6": 1}
@@ -195,6 +198,8 @@ def oracle_fits(w, forms, nsample, iters):
 
     y = _y_store(w)[:nsample].astype(np.float64)
     out = {}
+    if w["name"] in FIT_CHOSEN_ONLY:
+        forms = forms[:1]
     for f in forms:
         m = f["moments"] if w["q"] >= 3 else 0
         if m not in out:
@@ -354,7 +359,7 @@ def run_workload(cf, torch, name, args, stream, flush, steps, warmup, with_clock
         s = form_summary(w, runs[key], pairs, 1)
         s["form"] = _form_name(w, form)
         s["roofline"] = roofline(w, runs[key], rates) if key == "chosen" else None
-        if refs is not None:
+        if refs is not None and (form["moments"] if w["q"] >= 3 else 0) in refs:
             ns, it = fitcfg
             s["loglik_err"] = fit_error(cf, w, form, refs, ns, it)
         out[key] = s

@@ -253,6 +253,51 @@ cfust_status cfust_fit_batch(int nfits, cfust_ctx* const* ctxs, int max_iter, do
                              int flags, int* iters_out, double* loglik_hist,
                              cfust_status* status_out);
 
+/* ------------------------------------------------------------------------
+ * Row-sharded E-step over several processes (one GPU each).  The paper's
+ * parallel EM (Sec. 4) computes per-component partial results in threads and
+ * collects them once per iteration (Sec. 4.3); here the observations are split
+ * by rows instead, each process computes the sufficient statistics of its rows,
+ * and one exchange per iteration gives every process the same sums, after which
+ * each runs the identical M-step (eqs 18-22).
+ *
+ * The statistics are reduced in two fixed-order levels: sums over blocks of
+ * observations, then sums of consecutive segments of SEG blocks, then the
+ * segments in order.  A shard whose first row is a multiple of
+ * cfust_rows_per_segment has exactly the segments the whole problem has over
+ * those rows, so gathering every shard's segments in rank order and reducing
+ * them reproduces the single-process statistics bit for bit.
+ * ------------------------------------------------------------------------ */
+
+/* Rows per segment for a problem of these sizes and precision (it does not
+ * depend on n): shard boundaries must be multiples of it. */
+cfust_status cfust_rows_per_segment(int p, int q, int g, int precision, int64_t* rows);
+
+/* Segments of this context's rows (*nseg, may be NULL) and doubles per segment
+ * (*width = g*(3+p+q+pq+q^2+p^2) + 1: the statistics of cfust_get_stats, then
+ * the log-likelihood sum, may be NULL). */
+cfust_status cfust_segment_count(cfust_ctx* ctx, int64_t* nseg, int* width);
+
+/* Enqueue the E-step at the current Psi (eqs 4, 12-17) and the segment sums of
+ * its statistics into seg: a device buffer of nseg_out x width doubles,
+ * nseg_out >= the context's segment count; rows past that count are written
+ * as 0 (padding to a common count per process).  Asynchronous on the context
+ * stream: kernel errors surface in cfust_reduce_segments. */
+cfust_status cfust_estep_segments(cfust_ctx* ctx, double* seg, int64_t nseg_out);
+
+/* Reduce nseg segment rows (device, nseg x width; the gathered segments of all
+ * processes in rank order, zero padding allowed) into the context's statistics
+ * and log-likelihood, in order; *loglik_out (may be NULL) receives the total
+ * l(Psi) of eq (27).  Synchronises; then cfust_mstep may follow.  CFUST_ENAN
+ * for a non-finite sum; the per-component set-up checks as in cfust_estep. */
+cfust_status cfust_reduce_segments(cfust_ctx* ctx, const double* seg, int64_t nseg, double* loglik_out);
+
+/* Aitken's stopping rule (Sec. 3.4, eqs 24-26) on three consecutive
+ * log-likelihoods: 1 when |l_inf^(k+1) - l^(k+1)| < tol (or l^k = l^(k-1)),
+ * else 0.  The rule cfust_fit applies, for drivers that run the loop
+ * themselves (the sharded fit). */
+int cfust_aitken_converged(double l_km1, double l_k, double l_kp1, double tol);
+
 /* Evaluate T_k(b; 0, V, nu) for `count` independent cases with the
  * library's device integrators (k <= 2 deterministic, k >= 3 lattice), host
  * buffers: b (count x k), V (count x k x k scale matrices), nu (count);

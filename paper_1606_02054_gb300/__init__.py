@@ -112,6 +112,16 @@ def lib():
             L.cfust_profile.restype = i
             L.cfust_profile_work.argtypes = [vp, _dp]
             L.cfust_profile_work.restype = i
+            L.cfust_rows_per_segment.argtypes = [i, i, i, i, C.POINTER(i64)]
+            L.cfust_rows_per_segment.restype = i
+            L.cfust_segment_count.argtypes = [vp, C.POINTER(i64), C.POINTER(i)]
+            L.cfust_segment_count.restype = i
+            L.cfust_estep_segments.argtypes = [vp, vp, i64]
+            L.cfust_estep_segments.restype = i
+            L.cfust_reduce_segments.argtypes = [vp, vp, i64, _dp]
+            L.cfust_reduce_segments.restype = i
+            L.cfust_aitken_converged.argtypes = [d, d, d, d]
+            L.cfust_aitken_converged.restype = i
             L.cfust_debug_read.argtypes = [vp, i, vp, i64, C.POINTER(C.c_int64)]
             L.cfust_debug_read.restype = i
             L.cfust_reduce_stats_noalloc.argtypes = [i, i, i, i64] + [vp] * 11
@@ -442,6 +452,42 @@ def cfust_profile_work(ctx: Context):
     u = np.zeros(CFUST_NPROF)
     _check(lib().cfust_profile_work(ctx.handle, _ptr(u)), ctx)
     return {PROF_NAMES[k]: float(u[k]) for k in range(CFUST_NPROF)}
+
+
+def cfust_rows_per_segment(p, q, g, precision=CFUST_PREC_FP64) -> int:
+    r = C.c_int64(0)
+    _check(lib().cfust_rows_per_segment(int(p), int(q), int(g), int(precision), C.byref(r)), None)
+    return int(r.value)
+
+
+def cfust_segment_count(ctx: Context):
+    """(segments of this context's rows, doubles per segment)."""
+    n, w = C.c_int64(0), C.c_int(0)
+    _check(lib().cfust_segment_count(ctx.handle, C.byref(n), C.byref(w)), ctx)
+    return int(n.value), int(w.value)
+
+
+def cfust_estep_segments(ctx: Context, seg):
+    """Enqueue the E-step and its segment sums into `seg`, a CUDA float64 tensor of
+    shape (nseg_out, width), nseg_out >= the context's segment count."""
+    if not (seg.is_cuda and seg.is_contiguous()) or seg.element_size() != 8 or seg.dim() != 2:
+        raise CfustError(CFUST_EINVAL, "seg: contiguous 2-D CUDA float64 tensor required")
+    _check(lib().cfust_estep_segments(ctx.handle, C.c_void_p(seg.data_ptr()), int(seg.shape[0])), ctx)
+
+
+def cfust_reduce_segments(ctx: Context, seg) -> float:
+    """Reduce the gathered segments (CUDA float64 tensor (nseg, width), rank order);
+    returns l(Psi)."""
+    if not (seg.is_cuda and seg.is_contiguous()) or seg.element_size() != 8 or seg.dim() != 2:
+        raise CfustError(CFUST_EINVAL, "seg: contiguous 2-D CUDA float64 tensor required")
+    L = C.c_double()
+    _check(lib().cfust_reduce_segments(ctx.handle, C.c_void_p(seg.data_ptr()), int(seg.shape[0]),
+                                       C.byref(L)), ctx)
+    return L.value
+
+
+def cfust_aitken_converged(l_km1, l_k, l_kp1, tol) -> bool:
+    return bool(lib().cfust_aitken_converged(float(l_km1), float(l_k), float(l_kp1), float(tol)))
 
 
 def cfust_debug_read(ctx: Context, what, nbytes=1 << 30, dtype=np.float64):

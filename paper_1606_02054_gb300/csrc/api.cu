@@ -26,6 +26,7 @@ __global__ void narrow_kernel(const double*, Dims, float*);
 __global__ void estep_reduce_kernel(ReduceArgs);
 __global__ void estep_reduce_kernel_f32(ReduceArgs);
 __global__ void reduce_partials_kernel(const double*, int, int, double*, int*);
+__global__ void segment_partials_kernel(const double*, int, int, int, double*, long long);
 __global__ void loglik_partial_kernel(Dims, const double*, const double*, double*);
 __global__ void mstep_kernel(Dims, const double*, double, double, const double*, const double*,
                              const double*, double*, double*, double*, double*, double*, int*, int*,
@@ -61,6 +62,8 @@ struct cfust_ctx {
     double *logf = nullptr, *u = nullptr, *elogu = nullptr, *eu = nullptr, *euu = nullptr,
            *se = nullptr, *tau = nullptr;
     double *partial = nullptr, *stats = nullptr;
+    double* seg = nullptr;  // segment sums of the block partials (nseg x width)
+    long long nseg = 0;
     int *flags = nullptr, *comp_status = nullptr;
     float* stage32 = nullptr;
     float2* t1tab = nullptr;  // FP32 T_2: per-dof tables of T_1 at dof + 1
@@ -194,11 +197,40 @@ static cfust_status check_flags(cfust_ctx* c, int f, const char* where)
     return CFUST_OK;
 }
 
+// Observations per block of the statistics reduction: rows of 4 + p + q + q^2 values
+// (FP32 in the mixed form) plus g posterior weights staged in at most ~64 KB of
+// shared memory, chunk <= 256.  Depends on the sizes and the precision only, not on n.
+static int reduce_chunk(int p, int q, int g, bool mixed)
+{
+    const int row = 4 + p + q + q * q;
+    const size_t rowbytes = mixed ? sizeof(float) : sizeof(double);
+    int chunk = 256;
+    while (chunk > 32 && (size_t)chunk * ((row + g) * rowbytes + sizeof(double)) + CF_MAXG * sizeof(double) > 64 * 1024)
+        chunk -= 32;
+    return chunk;
+}
+
+// Blocks per segment of the two-level statistics reduction (segment_partials_kernel).
+constexpr int SEG_BLOCKS = 32;
+
+// Aitken's acceleration (eqs 24-26) on l^(k-1), l^k, l^(k+1): converged when
+// |l_inf^(k+1) - l^(k+1)| < tol; equal consecutive values count as converged.
+static bool aitken_converged(double l_km1, double l_k, double l_kp1, double tol)
+{
+    const double den = l_k - l_km1;
+    if (den == 0.0) return true;
+    const double acc = (l_kp1 - l_k) / den;
+    const double linf = l_k + (l_kp1 - l_k) / (1.0 - acc);
+    return std::fabs(linf - l_kp1) < tol;
+}
+
 // kernel-class timing: events bracket each class on the context stream and
 // are read after the next stream synchronisation
+// A class entered again before its events were read (the two levels of the statistics
+// reduction) keeps its first begin event, so its time spans both.
 static void prof_begin(cfust_ctx* c, int k)
 {
-    if (c->opts.profile && !c->capturing) cudaEventRecord(c->ev[k][0], c->st);
+    if (c->opts.profile && !c->capturing && !c->pending[k]) cudaEventRecord(c->ev[k][0], c->st);
 }
 static void prof_end(cfust_ctx* c, int k, long long launches)
 {
@@ -312,7 +344,7 @@ static void free_all(cfust_ctx* c)
                     c->glx64, c->glw64, c->glx32, c->glw32, c->glx32h, c->glw32h, c->logf, c->u, c->elogu, c->eu,
                     c->euu, c->se, c->tau, c->partial, c->stats, c->flags, c->comp_status,
                     c->stage32, c->pd, c->pc, c->fix_count, c->fix_list, c->y32, c->F32, c->t1tab,
-                    c->work_dev};
+                    c->work_dev, c->seg};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (RecSet& r : c->rec) {
@@ -410,12 +442,10 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     // reduction staging: rows of 4 + p + q + q^2 doubles, chunk <= 256 observations,
     // at most ~64 KB of shared memory
     c->row = 4 + p + q + q * q;
-    const size_t rowbytes = c->mixed ? sizeof(float) : sizeof(double);
-    int chunk = 256;
-    while (chunk > 32 && (size_t)chunk * ((c->row + g) * rowbytes + sizeof(double)) + CF_MAXG * sizeof(double) > 64 * 1024)
-        chunk -= 32;
+    const int chunk = reduce_chunk(p, q, g, c->mixed);
     c->chunk = chunk;
     c->nblocks_red = (int)((n + chunk - 1) / chunk);
+    c->nseg = (c->nblocks_red + SEG_BLOCKS - 1) / SEG_BLOCKS;
     c->nblocks_ll = (int)((n + 255) / 256);
     const size_t NM = (size_t)o.qmc_points * o.qmc_shifts;
     const int ntab = q >= 3 ? 3 * g : 0;
@@ -446,6 +476,7 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     ALLOC(logf, ng); ALLOC(u, ng); ALLOC(elogu, ng); ALLOC(se, ng); ALLOC(tau, ng);
     ALLOC(eu, ng * q); ALLOC(euu, ng * q * q);
     ALLOC(partial, part);
+    ALLOC(seg, (size_t)c->nseg * (g * S + 1));
     ALLOC(stats, (size_t)g * S + 1);
     ALLOC(flags, 1); ALLOC(comp_status, g);
     ALLOC(pd, 2 * ng); ALLOC(pc, ng * q);
@@ -818,9 +849,10 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
     return CFUST_OK;
 }
 
-// S0-S10 for every pair, enqueued on c->st without any host synchronisation
-// (also captured into the whole-fit graph).  l(Psi) lands in stats[width - 1].
-static cfust_status enqueue_estep(cfust_ctx* c)
+// S0-S9 for every pair and the segment sums of the block partials (the first level
+// of S10) into seg (nseg_out segments, those past this context's own count zero),
+// enqueued on c->st without any host synchronisation.
+static cfust_status enqueue_estep_segments(cfust_ctx* c, double* seg, long long nseg_out)
 {
     CU(cudaMemsetAsync(c->flags, 0, sizeof(int), c->st));
     cfust_status s;
@@ -838,11 +870,33 @@ static cfust_status enqueue_estep(cfust_ctx* c)
     else estep_reduce_kernel<<<c->nblocks_red, 256, smem, c->st>>>(r);
     LAUNCHED();
     const int width = c->g * stats_per_comp(c->p, c->q) + 1;
-    reduce_partials_kernel<<<(width + 127) / 128, 128, 0, c->st>>>(c->partial, c->nblocks_red, width,
-                                                                   c->stats, c->flags);
+    const long long tot = nseg_out * width;
+    segment_partials_kernel<<<(int)std::min<long long>((tot + 255) / 256, 8LL * c->nsm), 256, 0, c->st>>>(
+        c->partial, c->nblocks_red, SEG_BLOCKS, width, seg, nseg_out);
     LAUNCHED();
     prof_end(c, CFUST_PROF_REDUCE, 2);
     return CFUST_OK;
+}
+
+// Second level of S10: stats = sum of nseg segment rows in order, and the flag of a
+// non-finite sum.
+static cfust_status enqueue_reduce_segments(cfust_ctx* c, const double* seg, long long nseg)
+{
+    const int width = c->g * stats_per_comp(c->p, c->q) + 1;
+    prof_begin(c, CFUST_PROF_REDUCE);
+    reduce_partials_kernel<<<(width + 127) / 128, 128, 0, c->st>>>(seg, (int)nseg, width, c->stats, c->flags);
+    LAUNCHED();
+    prof_end(c, CFUST_PROF_REDUCE, 1);
+    return CFUST_OK;
+}
+
+// S0-S10 for every pair, enqueued on c->st without any host synchronisation
+// (also captured into the whole-fit graph).  l(Psi) lands in stats[width - 1].
+static cfust_status enqueue_estep(cfust_ctx* c)
+{
+    cfust_status s;
+    if ((s = enqueue_estep_segments(c, c->seg, c->nseg)) != CFUST_OK) return s;
+    return enqueue_reduce_segments(c, c->seg, c->nseg);
 }
 
 extern "C" cfust_status cfust_estep(cfust_ctx* c, double* loglik_out)
@@ -995,13 +1049,9 @@ extern "C" cfust_status cfust_fit(cfust_ctx* c, int max_iter, double tol, int* i
         double L;
         if ((s = cfust_estep(c, &L)) != CFUST_OK) break;
         hist[it] = L;
-        if (tol > 0.0 && it >= 2) {
-            // Aitken (eqs 24-26); equal consecutive values count as converged
-            const double den = hist[it - 1] - hist[it - 2];
-            if (den == 0.0) { converged = true; break; }
-            const double acc = (L - hist[it - 1]) / den;
-            const double linf = hist[it - 1] + (L - hist[it - 1]) / (1.0 - acc);
-            if (std::fabs(linf - L) < tol) { converged = true; break; }
+        if (tol > 0.0 && it >= 2 && aitken_converged(hist[it - 2], hist[it - 1], L, tol)) {
+            converged = true;  // Aitken (eqs 24-26)
+            break;
         }
         s = cfust_mstep(c);
         if (s == CFUST_ENUROOT) s = CFUST_OK;  // nu clamped: keep iterating
@@ -1016,6 +1066,67 @@ extern "C" cfust_status cfust_fit(cfust_ctx* c, int max_iter, double tol, int* i
     if (iters_out) *iters_out = it;
     if (loglik_hist) std::memcpy(loglik_hist, hist.data(), sizeof(double) * ((size_t)it + 1));
     return s;
+}
+
+// ---------------------------------------------------------------------------
+// Row-sharded E-step (Sec. 4's collection step over processes instead of threads):
+// each process holds a contiguous range of observations that starts on a segment
+// boundary, computes the segment sums of its statistics, the caller gathers the
+// segments of every process in rank order, and each process reduces them in that
+// order and runs the same M-step.
+// ---------------------------------------------------------------------------
+extern "C" cfust_status cfust_rows_per_segment(int p, int q, int g, int precision, int64_t* rows)
+{
+    if (!rows || p < 1 || p > CF_MAXP || q < 1 || q > CF_MAXQ || g < 1 || g > CF_MAXG ||
+        precision < CFUST_PREC_FP64 || precision > CFUST_PREC_MIXED)
+        return fail(nullptr, CFUST_EINVAL, "cfust_rows_per_segment: sizes or precision out of range");
+    *rows = (int64_t)reduce_chunk(p, q, g, precision == CFUST_PREC_MIXED) * SEG_BLOCKS;
+    return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_segment_count(cfust_ctx* c, int64_t* nseg, int* width)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_segment_count: ctx is NULL");
+    if (nseg) *nseg = c->nseg;
+    if (width) *width = c->g * stats_per_comp(c->p, c->q) + 1;
+    return CFUST_OK;
+}
+
+extern "C" cfust_status cfust_estep_segments(cfust_ctx* c, double* seg, int64_t nseg_out)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_estep_segments: ctx is NULL");
+    if (!seg || nseg_out < c->nseg)
+        return fail(c, CFUST_EINVAL, "cfust_estep_segments: need a device buffer of at least " +
+                                         std::to_string(c->nseg) + " segments");
+    if (!c->have_data || !c->have_params)
+        return fail(c, CFUST_ESTATE, "cfust_estep_segments: set_data and set_params must come first");
+    CU(cudaSetDevice(c->opts.device));
+    c->have_stats = false;
+    return enqueue_estep_segments(c, seg, nseg_out);
+}
+
+extern "C" cfust_status cfust_reduce_segments(cfust_ctx* c, const double* seg, int64_t nseg, double* loglik_out)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_reduce_segments: ctx is NULL");
+    if (!seg || nseg < 1 || nseg > INT32_MAX) return fail(c, CFUST_EINVAL, "cfust_reduce_segments: bad segments");
+    CU(cudaSetDevice(c->opts.device));
+    cfust_status s;
+    if ((s = enqueue_reduce_segments(c, seg, nseg)) != CFUST_OK) return s;
+    const int width = c->g * stats_per_comp(c->p, c->q) + 1;
+    CU(cudaMemcpyAsync(c->h_ll, c->stats + (width - 1), sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaMemcpyAsync(c->h_flags, c->flags, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    prof_collect(c);
+    if ((s = check_flags(c, *c->h_flags, "cfust_reduce_segments")) != CFUST_OK) return s;
+    if (!std::isfinite(*c->h_ll)) return fail(c, CFUST_ENAN, "cfust_reduce_segments: non-finite log-likelihood");
+    if (loglik_out) *loglik_out = *c->h_ll;
+    c->have_stats = true;
+    return CFUST_OK;
+}
+
+extern "C" int cfust_aitken_converged(double l_km1, double l_k, double l_kp1, double tol)
+{
+    return aitken_converged(l_km1, l_k, l_kp1, tol) ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------

@@ -184,6 +184,28 @@ __global__ void estep_reduce_kernel_f32(ReduceArgs a)
     estep_reduce_body<float>(a, (float*)sm);
 }
 
+// S10, first level: seg[s][e] = sum of partial[b][e] over the blocks b of segment s
+// (blocks s*per .. s*per + per - 1, the last segment possibly shorter), b in increasing
+// order; segments at or beyond ceil(nblocks/per) (padding up to nseg) are 0.  A shard of
+// the observations that starts on a segment boundary has the same segments as the whole
+// problem, so the second level (reduce_partials_kernel over the segments of every shard
+// in order) gives the same sums bit for bit.
+__global__ void segment_partials_kernel(const double* __restrict__ partial, int nblocks, int per, int width,
+                                        double* __restrict__ seg, long long nseg)
+{
+    const long long total = nseg * width;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long s = t / width;
+        const int e = (int)(t - s * width);
+        const long long b0 = s * per;
+        const long long b1 = b0 + per < nblocks ? b0 + per : nblocks;
+        double v = 0.0;
+        for (long long b = b0; b < b1; ++b) v += partial[b * width + e];
+        seg[t] = v;
+    }
+}
+
 // S10: stats[e] = sum_b partial[b][e], b in increasing order.
 __global__ void reduce_partials_kernel(const double* __restrict__ partial, int nblocks, int width,
                                        double* __restrict__ stats, int* flags)
