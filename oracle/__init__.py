@@ -99,6 +99,8 @@ def lib():
             L.ora_fit_hold.restype = i
             L.ora_random_partition.argtypes = [i, i, C.c_uint64, i, _ip]
             L.ora_random_partition.restype = None
+            L.ora_kmeans.argtypes = [i, i, i, _dp, i, C.c_uint64, i, _ip, _ip, _dp]
+            L.ora_kmeans.restype = i
             L.ora_moment_start.argtypes = [i, i, i, i, _dp, _ip, d, d, _dp, _dp, _dp, _dp, _dp]
             L.ora_moment_start.restype = i
             L.ora_init.argtypes = [i, i, i, i, _dp, i, _ip, C.c_uint64, i, _dp, d, C.POINTER(Qmc),
@@ -302,6 +304,21 @@ def random_partition(n, g, seed, start):
     lib().ora_random_partition(int(n), int(g), int(seed) & 0xFFFFFFFFFFFFFFFF, int(start),
                                lab.ctypes.data_as(_ip))
     return lab
+
+
+def kmeans(y, g, nstarts=1, seed=0, max_iter=100):
+    """k-means partitions (Lloyd, seeded starting centres; see ora_kmeans): returns
+    (labels (nstarts, n), iterations (nstarts,), centres (nstarts, g, p))."""
+    y = _f64(y)
+    n, p = y.shape
+    lab = np.zeros((nstarts, n), dtype=np.int32)
+    its = np.zeros(nstarts, dtype=np.int32)
+    cen = np.zeros((nstarts, g, p))
+    rc = lib().ora_kmeans(n, p, int(g), _ptr(y), int(nstarts), int(seed) & 0xFFFFFFFFFFFFFFFF, int(max_iter),
+                          lab.ctypes.data_as(_ip), its.ctypes.data_as(_ip), _ptr(cen))
+    if rc:
+        raise ValueError("kmeans: fewer observations than clusters")
+    return lab, its, cen
 
 
 def moment_start(y, labels, g, q, alpha, nu0=10.0):

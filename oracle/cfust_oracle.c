@@ -1339,6 +1339,66 @@ void ora_random_partition(int n, int g, uint64_t seed, int start, int* labels)
     }
 }
 
+int ora_kmeans(int n, int p, int g, const double* y, int nstarts, uint64_t seed, int max_iter,
+               int* labels, int* iters, double* centres)
+{
+    if (n < g) return 1;
+    double* c = (double*)malloc(sizeof(double) * (size_t)g * p);
+    double* sum = (double*)malloc(sizeof(double) * (size_t)g * p);
+    long* cnt = (long*)malloc(sizeof(long) * (size_t)g);
+    int* idx = (int*)malloc(sizeof(int) * (size_t)g);
+    for (int s = 0; s < nstarts; ++s) {
+        int* lab = labels + (size_t)s * n;
+        /* starting centres: g distinct observations */
+        for (int h = 0; h < g; ++h) {
+            for (uint64_t a = 0;; ++a) {
+                uint64_t key = seed ^ ((uint64_t)(s + 1) << 40) ^ ((uint64_t)1 << 36) ^ (uint64_t)(h + 1 + (uint64_t)g * a);
+                int j = (int)(ora_splitmix64_u01(key) * n);
+                if (j > n - 1) j = n - 1;
+                int dup = 0;
+                for (int l = 0; l < h; ++l) dup |= idx[l] == j;
+                if (!dup) { idx[h] = j; break; }
+            }
+            for (int d = 0; d < p; ++d) c[(size_t)h * p + d] = y[(size_t)idx[h] * p + d];
+        }
+        for (int j = 0; j < n; ++j) lab[j] = -1;
+        int it = 0;
+        while (it < max_iter) {
+            /* assignment */
+            long changes = 0;
+            for (int j = 0; j < n; ++j) {
+                double best = INFINITY;
+                int hb = 0;
+                for (int h = 0; h < g; ++h) {
+                    double dist = 0.0;
+                    for (int d = 0; d < p; ++d) {
+                        double t = y[(size_t)j * p + d] - c[(size_t)h * p + d];
+                        dist += t * t;
+                    }
+                    if (dist < best) { best = dist; hb = h; }
+                }
+                if (lab[j] != hb) { ++changes; lab[j] = hb; }
+            }
+            ++it;
+            if (changes == 0 || it == max_iter) break;
+            /* update: cluster means */
+            for (int t = 0; t < g * p; ++t) sum[t] = 0.0;
+            for (int h = 0; h < g; ++h) cnt[h] = 0;
+            for (int j = 0; j < n; ++j) {
+                ++cnt[lab[j]];
+                for (int d = 0; d < p; ++d) sum[(size_t)lab[j] * p + d] += y[(size_t)j * p + d];
+            }
+            for (int h = 0; h < g; ++h)
+                if (cnt[h] > 0)
+                    for (int d = 0; d < p; ++d) c[(size_t)h * p + d] = sum[(size_t)h * p + d] / (double)cnt[h];
+        }
+        if (iters) iters[s] = it;
+        if (centres) memcpy(centres + (size_t)s * g * p, c, sizeof(double) * (size_t)g * p);
+    }
+    free(c); free(sum); free(cnt); free(idx);
+    return 0;
+}
+
 int ora_moment_start(int n, int p, int q, int g, const double* y, const int* labels,
                      double alpha, double nu0, double* pi, double* mu, double* Sigma,
                      double* Delta, double* nu)

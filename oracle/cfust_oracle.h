@@ -141,6 +141,17 @@ int ora_fit(int n, int p, int q, int g, const double* y, double* pi,
  * Random partition of start s: label_j = floor(u g), u = SplitMix64 output for the key
  * seed ^ ((s+1) << 40) ^ (j+1). */
 void ora_random_partition(int n, int g, uint64_t seed, int start, int* labels);
+/* k-means partitions for Algorithm 1 (Sec. 3.3: the initial clusterings are typically
+ * k-means or random).  Lloyd's iteration from g distinct observations chosen by SplitMix64:
+ * centre h of start s is observation floor(u n), u = u01(seed ^ ((s+1) << 40) ^ (1 << 36) ^
+ * (h + 1 + g a)), a = 0, 1, ... until the index differs from those of centres 0..h-1.  Each
+ * iteration assigns every observation to the nearest centre (squared Euclidean distance,
+ * the first centre on ties); it stops when an assignment changes no label or after max_iter
+ * assignments, otherwise the centres become the cluster means (an empty cluster keeps its
+ * centre).  labels (nstarts x n), iters (nstarts, assignments run) and centres (nstarts x
+ * g x p, those of the last assignment; may be NULL).  Returns 0, or 1 if n < g. */
+int ora_kmeans(int n, int p, int g, const double* y, int nstarts, uint64_t seed, int max_iter,
+               int* labels, int* iters, double* centres);
 /* Eq (23) per cluster of a partition (sample covariance with divisor n_h - 1, third moment
  * about the mean for the sign of delta, nu = nu0, pi = n_h/n).  Returns 0, or 1 + h for the
  * first cluster with fewer than 2 points or a non-PD Sigma^(0). */

@@ -132,3 +132,53 @@ def test_init_with_given_labels_prefers_the_true_partition(oracle):
     _, ll, ib = oracle.init(y, 2, 2, spec, nstarts=3, labels=labels)
     assert ib // ll.shape[1] == 2
     assert np.max(ll[2]) > np.max(ll[:2]) + 50.0
+
+
+# ---- k-means partitions (Sec. 3.3: the initial clusterings of Algorithm 1) ----------
+def _kmeans_start_indices(oracle, n, g, seed, start):
+    """The starting centres' observation indices, from the stated SplitMix64 rule."""
+    idx = []
+    for h in range(g):
+        a = 0
+        while True:
+            key = seed ^ ((start + 1) << 40) ^ (1 << 36) ^ (h + 1 + g * a)
+            j = min(int(oracle.splitmix64_u01(key) * n), n - 1)
+            if j not in idx:
+                idx.append(j)
+                break
+            a += 1
+    return idx
+
+
+@pytest.mark.parametrize("name,n,g_over", [("flow_p4", 3000, None), ("wide_p16", 2000, None), ("two_comp_p2", 1000, 5)])
+def test_kmeans_matches_sklearn_lloyd(oracle, name, n, g_over):
+    """Pin: from the same starting centres, scikit-learn's Lloyd iteration (tol 0, one
+    initialisation) reaches the same labels and centres."""
+    sk = pytest.importorskip("sklearn.cluster")
+    w = synth.make_workload(name, n=n, with_init=False)
+    y, g = w["y"], g_over or w["g"]
+    seed = 77
+    labels, iters, cen = oracle.kmeans(y, g, nstarts=2, seed=seed, max_iter=300)
+    for s in range(2):
+        idx = _kmeans_start_indices(oracle, n, g, seed, s)
+        km = sk.KMeans(n_clusters=g, init=y[idx], n_init=1, max_iter=300, tol=0.0, algorithm="lloyd").fit(y)
+        assert iters[s] < 300  # converged: an assignment that changed nothing
+        assert np.array_equal(labels[s], km.labels_)
+        np.testing.assert_allclose(cen[s], km.cluster_centers_, rtol=1e-10, atol=1e-12)
+
+
+def test_kmeans_fixed_point_and_first_tie(oracle):
+    """At convergence every label is the nearest centre's and every centre is its
+    cluster's mean; an observation equidistant from two centres takes the first."""
+    w = synth.make_workload("flow_p4", n=1500, with_init=False)
+    labels, iters, cen = oracle.kmeans(w["y"], 4, nstarts=1, seed=3, max_iter=500)
+    d = ((w["y"][:, None, :] - cen[0][None]) ** 2).sum(-1)
+    assert np.array_equal(labels[0], d.argmin(1))
+    for h in range(4):
+        np.testing.assert_allclose(cen[0][h], w["y"][labels[0] == h].mean(0), rtol=1e-12, atol=1e-12)
+    # ties: two identical observations as the only points, g = 2 -> both centres equal
+    y = np.array([[1.0, 2.0], [1.0, 2.0], [1.0, 2.0]])
+    lab, _, _ = oracle.kmeans(y, 2, nstarts=1, seed=5, max_iter=10)
+    assert np.all(lab == 0)
+    with pytest.raises(ValueError):
+        oracle.kmeans(y[:1], 2)
