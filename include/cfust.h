@@ -233,7 +233,21 @@ cfust_status cfust_init(cfust_ctx* ctx, int nstarts, const int32_t* labels, uint
                         int nalpha, const double* alphas, double nu0, double* loglik_out,
                         int* best_out);
 
-/* Flags of cfust_fit_batch. */
+/* k-means partitions for Algorithm 1 (Sec. 3.3: the initial clusterings are typically
+ * k-means or random), on the device, for cfust_init's labels.  For each of nstarts starts,
+ * Lloyd's iteration from g distinct observations: centre h is observation floor(u n), u the
+ * SplitMix64 output for key seed ^ ((start + 1) << 40) ^ (1 << 36) ^ (h + 1 + g a), with
+ * a = 0, 1, ... until the index differs from those of centres 0..h-1.  Each iteration assigns
+ * every observation to the nearest centre (squared Euclidean distance in FP64, products and
+ * sums rounded one at a time, the first centre on ties) and stops when no label changes or
+ * after max_iter assignments; otherwise each centre becomes its cluster's mean (an empty
+ * cluster keeps its centre).  labels_out: host, nstarts x n; iters_out (nstarts, may be
+ * NULL): assignments run; centres_out (nstarts x g x p, may be NULL): the centres of the
+ * last assignment.  Needs cfust_set_data and n >= g. */
+cfust_status cfust_kmeans(cfust_ctx* ctx, int nstarts, uint64_t seed, int max_iter, int32_t* labels_out,
+                          int* iters_out, double* centres_out);
+
+/* Flags of cfust_fit_batch. *//* Flags of cfust_fit_batch. */
 #define CFUST_FIT_NO_FINAL 1 /* skip the density pass that gives l(Psi^(max_iter)) */
 
 /* Batched form of cfust_fit: nfits independent fits (different contexts,
@@ -288,9 +302,12 @@ cfust_status cfust_estep_segments(cfust_ctx* ctx, double* seg, int64_t nseg_out)
 /* Reduce nseg segment rows (device, nseg x width; the gathered segments of all
  * processes in rank order, zero padding allowed) into the context's statistics
  * and log-likelihood, in order; *loglik_out (may be NULL) receives the total
- * l(Psi) of eq (27).  Synchronises; then cfust_mstep may follow.  CFUST_ENAN
- * for a non-finite sum; the per-component set-up checks as in cfust_estep. */
-cfust_status cfust_reduce_segments(cfust_ctx* ctx, const double* seg, int64_t nseg, double* loglik_out);
+ * l(Psi) of eq (27).  n_total: the observations of all shards together, the n
+ * of eq (18) that the following cfust_mstep divides by (>= this context's n).
+ * Synchronises; then cfust_mstep may follow.  CFUST_ENAN for a non-finite sum;
+ * the per-component set-up checks as in cfust_estep. */
+cfust_status cfust_reduce_segments(cfust_ctx* ctx, const double* seg, int64_t nseg, int64_t n_total,
+                                   double* loglik_out);
 
 /* Aitken's stopping rule (Sec. 3.4, eqs 24-26) on three consecutive
  * log-likelihoods: 1 when |l_inf^(k+1) - l^(k+1)| < tol (or l^k = l^(k-1)),
@@ -360,11 +377,13 @@ typedef struct {
                              integrand of dimension K alone -- K normal CDFs, K inverse
                              normal CDFs (the FP32 forms of the integrators), the
                              K(K-1)/2 + 3K FMAs of the chain and the 2 + K + K(K+1)/2
-                             FMAs of the weighted moment sums per point, two independent
-                             points per thread, no memory traffic; [0..2] unused (0) */
+                             FMAs of the weighted moment sums per point, no memory
+                             traffic; the best of 1, 2 and 4 independent points per
+                             thread; [0..2] unused (0) */
     double t2_nodes;      /* nodes per second of the FP32 T_2 quadrature alone -- per node
                              two sines, the sin^(nu-1) weight (lg2, ex2) and the inner T_1
-                             from its per-dof table -- two independent nodes per thread */
+                             from its per-dof table -- the best of 1, 2 and 4 independent
+                             nodes per thread */
 } cfust_rates;
 
 /* Run the microbenchmarks on `device` for about `seconds` (0 < seconds <= 5) in

@@ -101,6 +101,8 @@ def lib():
             L.cfust_fit_batch.restype = i
             L.cfust_init.argtypes = [vp, i, vp, C.c_uint64, i, _dp, d, _dp, C.POINTER(i)]
             L.cfust_init.restype = i
+            L.cfust_kmeans.argtypes = [vp, i, C.c_uint64, i, vp, C.POINTER(i), _dp]
+            L.cfust_kmeans.restype = i
             L.cfust_special_f32.argtypes = [i, i64, vp, vp, i]
             L.cfust_special_f32.restype = i
             L.cfust_tk_eval.argtypes = [vp, i, i, _dp, _dp, _dp, _dp, _dp]
@@ -118,7 +120,7 @@ def lib():
             L.cfust_segment_count.restype = i
             L.cfust_estep_segments.argtypes = [vp, vp, i64]
             L.cfust_estep_segments.restype = i
-            L.cfust_reduce_segments.argtypes = [vp, vp, i64, _dp]
+            L.cfust_reduce_segments.argtypes = [vp, vp, i64, i64, _dp]
             L.cfust_reduce_segments.restype = i
             L.cfust_aitken_converged.argtypes = [d, d, d, d]
             L.cfust_aitken_converged.restype = i
@@ -308,6 +310,18 @@ def cfust_fit_batch(ctxs, max_iter, tol=0.0, flags=0):
     return iters, hist, status
 
 
+def cfust_kmeans(ctx: Context, nstarts=1, seed=0, max_iter=100):
+    """k-means partitions on the device (see include/cfust.h): (labels (nstarts, n) int32,
+    iterations (nstarts,), centres (nstarts, g, p))."""
+    lab = np.zeros((int(nstarts), ctx.n), dtype=np.int32)
+    its = np.zeros(int(nstarts), dtype=np.int32)
+    cen = np.zeros((int(nstarts), ctx.g, ctx.p))
+    _check(lib().cfust_kmeans(ctx.handle, int(nstarts), int(seed) & 0xFFFFFFFFFFFFFFFF, int(max_iter),
+                              lab.ctypes.data_as(C.c_void_p), its.ctypes.data_as(C.POINTER(C.c_int)),
+                              _ptr(cen)), ctx)
+    return lab, its, cen
+
+
 def cfust_init(ctx: Context, nstarts=4, labels=None, seed=0, alphas=None, nu0=10.0):
     """Algorithm 1: sets the context's Psi to the best moment start; returns (loglik per
     candidate [nstarts, nalpha], best index)."""
@@ -475,14 +489,14 @@ def cfust_estep_segments(ctx: Context, seg):
     _check(lib().cfust_estep_segments(ctx.handle, C.c_void_p(seg.data_ptr()), int(seg.shape[0])), ctx)
 
 
-def cfust_reduce_segments(ctx: Context, seg) -> float:
-    """Reduce the gathered segments (CUDA float64 tensor (nseg, width), rank order);
-    returns l(Psi)."""
+def cfust_reduce_segments(ctx: Context, seg, n_total) -> float:
+    """Reduce the gathered segments (CUDA float64 tensor (nseg, width), rank order) of
+    n_total observations in all; returns l(Psi)."""
     if not (seg.is_cuda and seg.is_contiguous()) or seg.element_size() != 8 or seg.dim() != 2:
         raise CfustError(CFUST_EINVAL, "seg: contiguous 2-D CUDA float64 tensor required")
     L = C.c_double()
     _check(lib().cfust_reduce_segments(ctx.handle, C.c_void_p(seg.data_ptr()), int(seg.shape[0]),
-                                       C.byref(L)), ctx)
+                                       int(n_total), C.byref(L)), ctx)
     return L.value
 
 

@@ -64,6 +64,7 @@ struct cfust_ctx {
     double *partial = nullptr, *stats = nullptr;
     double* seg = nullptr;  // segment sums of the block partials (nseg x width)
     long long nseg = 0;
+    long long n_stats = 0;  // observations behind the current statistics (all shards'), the n of eq (18)
     int *flags = nullptr, *comp_status = nullptr;
     float* stage32 = nullptr;
     float2* t1tab = nullptr;  // FP32 T_2: per-dof tables of T_1 at dof + 1
@@ -728,6 +729,7 @@ static IntegArgs integ_args(const cfust_ctx* c)
     ia.t1tab = c->t1tab;
     ia.wtab = c->wtab;
     ia.nodes = nullptr;
+    ia.t2_grouped = c->opts.model == CFUST_MODEL_CFUSN ? 0 : 1;
     return ia;
 }
 
@@ -895,6 +897,7 @@ static cfust_status enqueue_reduce_segments(cfust_ctx* c, const double* seg, lon
 static cfust_status enqueue_estep(cfust_ctx* c)
 {
     cfust_status s;
+    c->n_stats = c->n;
     if ((s = enqueue_estep_segments(c, c->seg, c->nseg)) != CFUST_OK) return s;
     return enqueue_reduce_segments(c, c->seg, c->nseg);
 }
@@ -954,7 +957,9 @@ static cfust_status enqueue_mstep(cfust_ctx* c, const int* gate)
 {
     CU(cudaMemsetAsync(c->flags, 0, sizeof(int), c->st));
     prof_begin(c, CFUST_PROF_MSTEP);
-    mstep_kernel<<<1, 32, 0, c->st>>>(c->D, c->stats, c->opts.nu_min, c->opts.nu_max, c->mu, c->Delta,
+    Dims Dm = c->D;
+    Dm.n = c->n_stats;  // pi_h = N_h / n over every observation the statistics cover
+    mstep_kernel<<<1, 32, 0, c->st>>>(Dm, c->stats, c->opts.nu_min, c->opts.nu_max, c->mu, c->Delta,
                                       c->nu, c->pi_n, c->mu_n, c->Sigma_n, c->Delta_n, c->nu_n,
                                       c->flags, c->comp_status, gate, c->opts.hold);
     LAUNCHED();
@@ -1105,10 +1110,13 @@ extern "C" cfust_status cfust_estep_segments(cfust_ctx* c, double* seg, int64_t 
     return enqueue_estep_segments(c, seg, nseg_out);
 }
 
-extern "C" cfust_status cfust_reduce_segments(cfust_ctx* c, const double* seg, int64_t nseg, double* loglik_out)
+extern "C" cfust_status cfust_reduce_segments(cfust_ctx* c, const double* seg, int64_t nseg, int64_t n_total,
+                                              double* loglik_out)
 {
     if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_reduce_segments: ctx is NULL");
     if (!seg || nseg < 1 || nseg > INT32_MAX) return fail(c, CFUST_EINVAL, "cfust_reduce_segments: bad segments");
+    if (n_total < c->n) return fail(c, CFUST_EINVAL, "cfust_reduce_segments: n_total below this shard's rows");
+    c->n_stats = n_total;
     CU(cudaSetDevice(c->opts.device));
     cfust_status s;
     if ((s = enqueue_reduce_segments(c, seg, nseg)) != CFUST_OK) return s;
@@ -1367,6 +1375,95 @@ extern "C" cfust_status cfust_fit_batch(int nfits, cfust_ctx* const* ctxs, int m
 // ---------------------------------------------------------------------------
 // Initialisation (Sec. 3.3, Algorithm 1 with the moment starts of eq 23).
 // ---------------------------------------------------------------------------
+// k-means partitions for Algorithm 1 (Sec. 3.3): Lloyd's iteration on the device from
+// seeded starting centres; the assignment and the fixed-order cluster sums run as kernels,
+// the g x p centre update (a division per entry) on the host.
+extern "C" cfust_status cfust_kmeans(cfust_ctx* c, int nstarts, uint64_t seed, int max_iter, int32_t* labels_out,
+                                     int* iters_out, double* centres_out)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_kmeans: ctx is NULL");
+    if (!c->have_data) return fail(c, CFUST_ESTATE, "cfust_kmeans: set_data must come first");
+    if (nstarts < 1 || max_iter < 1 || !labels_out)
+        return fail(c, CFUST_EINVAL, "cfust_kmeans: need nstarts >= 1, max_iter >= 1 and labels_out");
+    const int p = c->p, g = c->g;
+    const long long n = c->n;
+    if (n < g) return fail(c, CFUST_EINVAL, "cfust_kmeans: fewer observations than clusters");
+    CU(cudaSetDevice(c->opts.device));
+    const int chunk = 64;
+    const long long nchunks = (n + chunk - 1) / chunk;
+    const int blocks = (int)std::min<long long>(nchunks, 4LL * c->nsm);
+    const int W0 = 1 + p;
+    int *dlab = nullptr, *dchg = nullptr;
+    double *partial = nullptr, *sums = nullptr, *dcen = nullptr;
+    cudaError_t e;
+    auto cleanup = [&]() { cudaFree(dlab); cudaFree(dchg); cudaFree(partial); cudaFree(sums); cudaFree(dcen); };
+    if ((e = dalloc(&dlab, (size_t)n)) != cudaSuccess || (e = dalloc(&dchg, 1)) != cudaSuccess ||
+        (e = dalloc(&partial, (size_t)blocks * g * W0)) != cudaSuccess ||
+        (e = dalloc(&sums, (size_t)g * W0)) != cudaSuccess || (e = dalloc(&dcen, (size_t)g * p)) != cudaSuccess) {
+        cleanup();
+        return fail(c, CFUST_ENOMEM, std::string("cfust_kmeans: ") + cudaGetErrorString(e));
+    }
+    std::vector<double> cen((size_t)g * p), s0((size_t)g * W0);
+    std::vector<long long> idx(g);
+    cfust_status s = CFUST_OK;
+    for (int st = 0; st < nstarts && s == CFUST_OK; ++st) {
+        // starting centres: g distinct observations, index floor(u n) with u the SplitMix64
+        // output for key seed ^ ((st+1) << 40) ^ (1 << 36) ^ (h + 1 + g a), a = 0, 1, ...
+        for (int h = 0; h < g; ++h)
+            for (uint64_t a = 0;; ++a) {
+                const uint64_t key = seed ^ ((uint64_t)(st + 1) << 40) ^ ((uint64_t)1 << 36) ^
+                                     (uint64_t)(h + 1 + (uint64_t)g * a);
+                long long j = (long long)(splitmix_u01(key) * (double)n);
+                if (j > n - 1) j = n - 1;
+                bool dup = false;
+                for (int l = 0; l < h; ++l) dup |= idx[l] == j;
+                if (!dup) { idx[h] = j; break; }
+            }
+        e = cudaSuccess;
+        for (int h = 0; h < g && e == cudaSuccess; ++h)
+            e = cudaMemcpyAsync(dcen + (size_t)h * p, c->y + (size_t)idx[h] * p, sizeof(double) * p,
+                                cudaMemcpyDeviceToDevice, c->st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(dlab, 0xff, sizeof(int) * n, c->st);  // -1: no label yet
+        int it = 0;
+        while (e == cudaSuccess) {
+            int chg = 0;
+            e = cudaMemsetAsync(dchg, 0, sizeof(int), c->st);
+            if (e == cudaSuccess) e = launch_kmeans_assign(c->D, c->y, dcen, dlab, dchg, c->nsm, c->st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&chg, dchg, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+            if (e != cudaSuccess) break;
+            ++c->launches;
+            ++it;
+            if (chg == 0 || it == max_iter) break;
+            // update: the cluster means (an empty cluster keeps its centre)
+            e = launch_cluster_moments(0, c->D, c->y, dlab, nullptr, chunk, blocks, partial, c->st);
+            if (e == cudaSuccess) {
+                reduce_partials_kernel<<<(g * W0 + 127) / 128, 128, 0, c->st>>>(partial, blocks, g * W0, sums, c->flags);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaMemcpyAsync(s0.data(), sums, sizeof(double) * g * W0, cudaMemcpyDeviceToHost, c->st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(cen.data(), dcen, sizeof(double) * g * p, cudaMemcpyDeviceToHost, c->st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+            if (e != cudaSuccess) break;
+            c->launches += 2;
+            for (int h = 0; h < g; ++h) {
+                const double cnt = s0[(size_t)h * W0];
+                if (cnt > 0.0)
+                    for (int d = 0; d < p; ++d) cen[(size_t)h * p + d] = s0[(size_t)h * W0 + 1 + d] / cnt;
+            }
+            e = cudaMemcpyAsync(dcen, cen.data(), sizeof(double) * g * p, cudaMemcpyHostToDevice, c->st);
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(labels_out + (size_t)st * n, dlab, sizeof(int) * n, cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess && centres_out)
+            e = cudaMemcpyAsync(centres_out + (size_t)st * g * p, dcen, sizeof(double) * g * p, cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) s = fail(c, CFUST_ECUDA, std::string("cfust_kmeans: ") + cudaGetErrorString(e));
+        if (iters_out) iters_out[st] = it;
+    }
+    cleanup();
+    return s;
+}
+
 extern "C" cfust_status cfust_init(cfust_ctx* c, int nstarts, const int32_t* labels, uint64_t seed,
                                    int nalpha, const double* alphas, double nu0, double* loglik_out,
                                    int* best_out)

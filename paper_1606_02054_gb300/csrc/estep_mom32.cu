@@ -4,16 +4,22 @@
 #include "internal.cuh"
 #include "special.cuh"
 
+// Lattice points in flight per lane (with the coordinate table, K <= 4).
+#ifndef CF_MOM_P
+#define CF_MOM_P 2
+#endif
 // Blocks of 4 warps.  K = 7, 8 need 147-168 registers: 3 such blocks (12 warps) share an
-// SM where one block of 8 would leave it at 8.  K <= 4 (with the coordinate table: 73
-// registers) is capped at 72 so that 7 blocks (28 warps) fit where blocks of 8 fit 24.
+// SM where one block of 8 would leave it at 8.
 template <int K>
 __host__ __device__ constexpr int mom32_block() { return K >= 7 || K <= 4 ? 128 : 256; }
 // minimum resident blocks (an explicit 1 would let ptxas take up to 255 registers: K = 6
-// went from 128 to 154, halving its resident warps): K <= 4: 7 (72 registers); K = 5, 6: 2
+// went from 128 to 154, halving its resident warps): K <= 4: CF_MOM_MINB4; K = 5, 6: 2
 // (128); K = 7, 8: 3 (170)
+#ifndef CF_MOM_MINB4
+#define CF_MOM_MINB4 5
+#endif
 template <int K>
-__host__ __device__ constexpr int mom32_minb() { return K <= 4 ? 7 : (K <= 6 ? 2 : 3); }
+__host__ __device__ constexpr int mom32_minb() { return K <= 4 ? CF_MOM_MINB4 : (K <= 6 ? 2 : 3); }
 
 template <int K, bool SEL>
 __global__ void __launch_bounds__(mom32_block<K>(), mom32_minb<K>()) lattice_mom_kernel_32(RecSet r, IntegArgs a)
@@ -32,18 +38,18 @@ __global__ void __launch_bounds__(mom32_block<K>(), mom32_minb<K>()) lattice_mom
 #pragma unroll
         for (int k = 0; k < K; ++k) bt[k] = r.bt[i * K + k];
         // the pass of alpha_s (chi table at dof k1 = dof - 2) weighted to dof k2 = r.dof
-        const double k2 = r.dof[i];
-        const float rk = isinf(k2) ? float(1) : (float)sqrt(k2 / (k2 - 2.0));
+        const float k2 = (float)r.dof[i];
+        const float rk = isinf(k2) ? 1.0f : sqrtf(k2 / (k2 - 2.0f));
         double as = 0.0, se = 0.0;
-        // the coordinate table only at K <= 4 (one float4 per point, with the 4-warp blocks
-        // it pays for); at K = 6 it measured 1.6x slower than advancing the coordinates
+        // the coordinate table only at K <= 4 (one float4 per point); at K = 6 it measured
+        // 1.6x slower than advancing the coordinates
         double v;
         if constexpr (K <= 4)
-            v = tk_lattice_mom_tab_warp<float, K>(bt, a.F + r.fac[i], a.chi32 + (size_t)r.tab[i] * NM, a.shf32,
-                                                  a.lat, lane, acc, rk, &as, &se, a.wtab);
+            v = tk_lattice_mom_f32<K, true, CF_MOM_P>(bt, a.F + r.fac[i], a.chi32 + (size_t)r.tab[i] * NM, a.shf32,
+                                                      a.lat, lane, acc, rk, &as, &se, a.wtab);
         else
-            v = tk_lattice_mom_warp<float, K>(bt, a.F + r.fac[i], a.chi32 + (size_t)r.tab[i] * NM, a.shf32,
-                                              a.lat, lane, acc, rk, &as, &se);
+            v = tk_lattice_mom_f32<K, false, 1>(bt, a.F + r.fac[i], a.chi32 + (size_t)r.tab[i] * NM, a.shf32,
+                                                a.lat, lane, acc, rk, &as, &se, nullptr);
         if (lane == 0) {
             r.res[i] = v;
             if (r.res0) r.res0[i] = as;

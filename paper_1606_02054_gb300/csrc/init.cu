@@ -20,6 +20,52 @@ __global__ void random_partition_kernel(long long n, int g, uint64_t seed, int s
     }
 }
 
+// k-means assignment (Lloyd): label_j = argmin_h ||y_j - c_h||^2, the first centre on ties;
+// every product and sum rounded on its own (no fused multiply-add), in coordinate order.
+// *changes counts the labels that changed (one atomic per warp).
+__global__ void kmeans_assign_kernel(Dims D, const double* __restrict__ y, const double* __restrict__ centres,
+                                     int* __restrict__ labels, int* __restrict__ changes)
+{
+    extern __shared__ double cs[];  // g x p centres
+    const int p = D.p, g = D.g;
+    for (int t = threadIdx.x; t < g * p; t += blockDim.x) cs[t] = centres[t];
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    // the loop runs the same number of times on every lane of a warp (j past n does no work)
+    const long long n_pad = (D.n + 31) / 32 * 32;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n_pad; j += stride) {
+        bool changed = false;
+        if (j < D.n) {
+            double best = INFINITY;
+            int hb = 0;
+            for (int h = 0; h < g; ++h) {
+                double dist = 0.0;
+                for (int d = 0; d < p; ++d) {
+                    const double t = __dsub_rn(y[(size_t)j * p + d], cs[h * p + d]);
+                    dist = __dadd_rn(dist, __dmul_rn(t, t));
+                }
+                if (dist < best) {
+                    best = dist;
+                    hb = h;
+                }
+            }
+            changed = labels[j] != hb;
+            labels[j] = hb;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, changed);
+        if ((threadIdx.x & 31) == 0 && m) atomicAdd(changes, __popc(m));
+    }
+}
+
+cudaError_t launch_kmeans_assign(const Dims& D, const double* y, const double* centres, int* labels,
+                                 int* changes, int nsm, cudaStream_t st)
+{
+    const long long blocks = (D.n + 255) / 256;
+    const int b = (int)(blocks < 8LL * nsm ? blocks : 8LL * nsm);
+    kmeans_assign_kernel<<<b, 256, sizeof(double) * D.g * D.p, st>>>(D, y, centres, labels, changes);
+    return cudaGetLastError();
+}
+
 // Per-cluster sums, one block partial per block (FP64, fixed order).
 //   pass 0: [count, sum y (p)]                      W = 1 + p
 //   pass 1: [sum r r^T (lower, packed), sum r^3 (p)] W = p(p+1)/2 + p, r = y - mean_h

@@ -178,6 +178,9 @@ struct IntegArgs {
     // T_2 records only (may be null): quadrature nodes evaluated, added once per warp
     // (the profiler's algorithmic work count)
     unsigned long long* nodes;
+    // FP32 T_2 records of finite dof may share a warp (several records per warp, each on
+    // a group of lanes); 0: one warp per record (the CFUSN model's Phi_2 records)
+    int t2_grouped;
 };
 
 constexpr int T1TAB_N = 4096;
@@ -258,6 +261,8 @@ void cf_set_global_error(const std::string& msg);
 size_t cluster_moments_smem(int pass, int p, int g, int chunk);
 cudaError_t launch_random_partition(long long n, int g, uint64_t seed, int start, int* labels,
                                     cudaStream_t st);
+cudaError_t launch_kmeans_assign(const Dims& D, const double* y, const double* centres, int* labels,
+                                 int* changes, int nsm, cudaStream_t st);
 cudaError_t launch_cluster_moments(int pass, const Dims& D, const double* y, const int* labels,
                                    const double* mean, int chunk, int blocks, double* partial,
                                    cudaStream_t st);

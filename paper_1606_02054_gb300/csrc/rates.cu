@@ -12,11 +12,12 @@
 //   - the single-pass integrand mix of dimension K: per lattice point K normal
 //     CDFs, K inverse normal CDFs (this library's FP32 forms, cf_ncdf_f32 and
 //     cf_ncdfinv_f32), the K(K-1)/2 + 3K FMAs of the chain and the
-//     2 + K + K(K+1)/2 FMAs of the weighted moment sums, with two independent
-//     points in flight per thread and no memory traffic: the rate an
-//     implementation of the same algorithm could reach if it did nothing else;
+//     2 + K + K(K+1)/2 FMAs of the weighted moment sums, with 1, 2 or 4
+//     independent points in flight per thread (the best of the three) and no
+//     memory traffic: the rate an implementation of the same algorithm could
+//     reach if it did nothing else;
 //   - one node of the FP32 T_2 quadrature (two sines, the sin^(nu-1) weight, the
-//     inner T_1 from its table), two independent nodes per thread.
+//     inner T_1 from its table), 1, 2 or 4 independent nodes per thread (the best).
 // Every kernel runs a full grid (8 blocks of 256 threads per SM) for a fixed
 // number of iterations; rates are operations (or points) per second of
 // CUDA-event time after one warm-up launch, and the SM clock is read with
@@ -70,7 +71,8 @@ __global__ void __launch_bounds__(kThreads) fma64_rate_kernel(double* out, int i
 }
 
 // fn 0: x = ex2(-x) (stays in [0.5, 1]); 1: x = lg2(x) + 1.5 (stays in [0.5, 3]);
-// 2: x = rcp(x) (alternates between x and 1/x)
+// 2: x = rcp(x) + 0.5 (stays near 1.28; the added constant keeps the compiler from
+// cancelling two reciprocals)
 template <int FN>
 __global__ void __launch_bounds__(kThreads) mufu_rate_kernel(float* out, int iters)
 {
@@ -84,7 +86,7 @@ __global__ void __launch_bounds__(kThreads) mufu_rate_kernel(float* out, int ite
             for (int k = 0; k < 8; ++k) {
                 if constexpr (FN == 0) a[k] = ptx_ex2_approx(-a[k]);
                 else if constexpr (FN == 1) a[k] = ptx_lg2_approx(a[k]) + 1.5f;
-                else a[k] = ptx_rcp_approx(a[k]);
+                else a[k] = ptx_rcp_approx(a[k]) + 0.5f;
             }
     }
     float s = 0.f;
@@ -96,10 +98,9 @@ __global__ void __launch_bounds__(kThreads) mufu_rate_kernel(float* out, int ite
 // The single-pass integrand of dimension K for two independent points per thread.
 // Coordinates w advance by a fixed irrational-like step (one add and one select per
 // coordinate, kept in [0, 1)); the chi variate s is taken from the first coordinate.
-template <int K>
+template <int K, int P>
 __global__ void __launch_bounds__(kThreads) mix_rate_kernel(float* out, int iters)
 {
-    constexpr int P = 2;
     constexpr int K2 = K * (K + 1) / 2;
     const float t0 = threadIdx.x * (1.0f / 4096.0f);
     float b[K], invd[K], L[K][K];
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(kThreads) mix_rate_kernel(float* out, int iter
     for (int d = 0; d <= K; ++d) {
         dw[d] = 0.6180339f * (d + 1) - (int)(0.6180339f * (d + 1));
 #pragma unroll
-        for (int p = 0; p < P; ++p) w[p][d] = 0.5f * dw[d] + 0.25f * p + t0 * 0.1f;
+        for (int p = 0; p < P; ++p) w[p][d] = 0.5f * dw[d] + 0.125f * p + t0 * 0.1f;
     }
     float af[P], aw[P], a1[P][K], a2[P][K2];
 #pragma unroll
@@ -174,14 +175,14 @@ __global__ void __launch_bounds__(kThreads) mix_rate_kernel(float* out, int iter
 // (cf_sin_pi), the weight sin^(nu-1) (lg2, ex2), the inner T_1 from a per-dof table
 // (t1cdf_table: asinh by lg2 and sqrt, cubic Hermite, ex2) and the weighted sum; two
 // independent nodes per thread, angles advancing by a fixed step, the table L1-resident.
+template <int P>
 __global__ void __launch_bounds__(kThreads) t2node_rate_kernel(float* out, const float2* __restrict__ tab, int iters)
 {
-    constexpr int P = 2;
     const float t0 = threadIdx.x * (1.0f / 8192.0f);
     float th[P], acc[P];
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        th[p] = 0.1f + 0.7f * p + t0;
+        th[p] = 0.1f + 0.7f * (p & 3) + 0.05f * (p >> 2) + t0;
         acc[p] = 0.f;
     }
     const float dth = 0.00613f, zs = -2.3f, d0 = 0.4f, num1 = 7.5f, wgt = 0.01f;
@@ -196,7 +197,10 @@ __global__ void __launch_bounds__(kThreads) t2node_rate_kernel(float* out, const
             th[p] = t >= 3.0f ? t - 2.9f : t;
         }
     }
-    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = acc[0] + acc[1];
+    float sum = 0.f;
+#pragma unroll
+    for (int p = 0; p < P; ++p) sum += acc[p];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = sum;
 }
 
 __global__ void fill_t1tab_kernel(float2* tab)
@@ -257,13 +261,39 @@ cudaError_t calibrate(Timer& t, F launch_iters, int probe, double target, int* i
     return timed(t, [&] { launch_iters(*iters); }, secs);
 }
 
-template <int K>
-cudaError_t mix_rate(Timer& t, float* out, int blocks, double target, double* rate)
+// the best of 1, 2 and 4 independent points per thread (the rate of the arithmetic alone)
+template <int K, int P>
+cudaError_t mix_rate_p(Timer& t, float* out, int blocks, double target, double* rate)
 {
     int it = 0;
     double s = 0.0;
-    cudaError_t e = calibrate(t, [&](int n) { mix_rate_kernel<K><<<blocks, kThreads>>>(out, n); }, 64, target, &it, &s);
-    if (e == cudaSuccess) *rate = 2.0 * (double)blocks * kThreads * it / s;
+    cudaError_t e = calibrate(t, [&](int n) { mix_rate_kernel<K, P><<<blocks, kThreads>>>(out, n); }, 64, target, &it, &s);
+    if (e == cudaSuccess) {
+        const double r = (double)P * blocks * kThreads * it / s;
+        if (r > *rate) *rate = r;
+    }
+    return e;
+}
+
+template <int K>
+cudaError_t mix_rate(Timer& t, float* out, int blocks, double target, double* rate)
+{
+    cudaError_t e = mix_rate_p<K, 1>(t, out, blocks, target / 3, rate);
+    if (e == cudaSuccess) e = mix_rate_p<K, 2>(t, out, blocks, target / 3, rate);
+    if (e == cudaSuccess) e = mix_rate_p<K, 4>(t, out, blocks, target / 3, rate);
+    return e;
+}
+
+template <int P>
+cudaError_t t2node_rate(Timer& t, float* out, const float2* tab, int blocks, double target, double* rate)
+{
+    int it = 0;
+    double s = 0.0;
+    cudaError_t e = calibrate(t, [&](int n) { t2node_rate_kernel<P><<<blocks, kThreads>>>(out, tab, n); }, 64, target, &it, &s);
+    if (e == cudaSuccess) {
+        const double r = (double)P * blocks * kThreads * it / s;
+        if (r > *rate) *rate = r;
+    }
     return e;
 }
 
@@ -331,9 +361,9 @@ extern "C" cfust_status cfust_measure_rates(int device, double seconds, cfust_ra
         if ((e = mix_rate<7>(t, f32, blocks, tgt, &out->mix_points[7])) != cudaSuccess) break;
         if ((e = mix_rate<8>(t, f32, blocks, tgt, &out->mix_points[8])) != cudaSuccess) break;
         fill_t1tab_kernel<<<(T1TAB_N + 255) / 256, 256>>>(t1tab);
-        e = calibrate(t, [&](int n) { t2node_rate_kernel<<<blocks, kThreads>>>(f32, t1tab, n); }, 64, tgt, &it, &s);
-        if (e != cudaSuccess) break;
-        out->t2_nodes = 2.0 * nthr * it / s;
+        if ((e = t2node_rate<1>(t, f32, t1tab, blocks, tgt / 3, &out->t2_nodes)) != cudaSuccess) break;
+        if ((e = t2node_rate<2>(t, f32, t1tab, blocks, tgt / 3, &out->t2_nodes)) != cudaSuccess) break;
+        if ((e = t2node_rate<4>(t, f32, t1tab, blocks, tgt / 3, &out->t2_nodes)) != cudaSuccess) break;
     } while (0);
     cudaFree(buf);
     if (e != cudaSuccess) {

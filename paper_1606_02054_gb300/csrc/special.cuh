@@ -409,6 +409,69 @@ __device__ double t2cdf_warp(R h, R k, R rho, R nu, R omr2, R cr, R lgb, R lgb1,
     return (double)(C2 * acc);
 }
 
+// Sum over aligned groups of L lanes (L a power of two <= 32); every lane of a group
+// gets the group's total, bitwise identical (the group's first lane's value).  All 32
+// lanes must execute it.
+template <int L>
+__device__ __forceinline__ float group_sum(float v)
+{
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(CF_FULL, v, o);
+    return __shfl_sync(CF_FULL, v, (threadIdx.x & (CF_WARP - 1)) & ~(L - 1));
+}
+
+// ---------------------------------------------------------------------------
+// FP32 T_2(h, k; rho, nu) by the quadrature of t2cdf_warp, on an aligned group of L
+// lanes (sub = the lane's index in its group): the nodes of the record's pieces are
+// spread over the group's lanes, so a warp evaluates 32/L records at once and the
+// per-record set-up (the angles of the split, the pieces' lengths) is paid once per
+// group instead of once per warp.  Every lane of the warp must call it (the group
+// reductions are warp-wide shuffles); the |rho| = 1 limits take no early return so
+// that every group reaches them.  nodes_out: nodes evaluated (0 at |rho| = 1).
+// ---------------------------------------------------------------------------
+template <int L>
+__device__ double t2cdf_group_f32(float h, float k, float rho, float nu, float omr2, float cr, float lgb,
+                                  float lgb1, float C2, int n, const float* __restrict__ glx,
+                                  const float* __restrict__ glw, int nh, const float* __restrict__ glxh,
+                                  const float* __restrict__ glwh, int sub, const float2* __restrict__ t1tab,
+                                  int* nodes_out)
+{
+    const bool lim = rho >= 1.0f || rho <= -1.0f;
+    float acc = 0.0f;
+    int nodes = 0;
+    if (!lim) {
+        const bool graded = fabsf(rho) > 0.99f;
+        const T2Setup<float> S = t2_setup<float>(h, k, rho, nu, omr2, cr);
+        const int nn = graded ? nh : n;
+        const float* __restrict__ gx = graded ? glxh : glx;
+        const float* __restrict__ gw = graded ? glwh : glw;
+        nodes = (S.split ? 2 : 1) * nn;
+        const float nu1 = nu + 1.0f, num1 = nu - 1.0f;
+        for (int t = sub; t < nodes; t += L) {
+            const bool p1 = t >= nn;
+            const int i = p1 ? t - nn : t;
+            const float anc = p1 ? S.phis : S.anc0;
+            const float Lp = p1 ? S.L1 : S.L0;
+            const float u = gx[i];
+            const float um = graded ? u * u * u : u;
+            const float jac = graded ? 3.0f * u * u : 1.0f;
+            const float off = Lp * um;
+            const float sp = cf_sin_pi(anc + off);  // both arguments lie in [-pi, pi]
+            const float sd = cf_sin_pi((p1 ? 0.0f : S.d0) + off);
+            const float z = S.zs * sd;
+            const float f = ptx_ex2_approx(num1 * ptx_lg2_approx(sp)) *
+                            (t1tab ? t1cdf_table(z, t1tab) : t1cdf_dev<float>(z, nu1, lgb1));
+            acc += gw[i] * jac * f * fabsf(Lp);
+        }
+    }
+    acc = group_sum<L>(acc);
+    if (nodes_out) *nodes_out = nodes;
+    if (!lim) return (double)(C2 * acc);
+    if (rho >= 1.0f) return (double)t1cdf_dev<float>(h < k ? h : k, nu, lgb);
+    const float v = t1cdf_dev<float>(h, nu, lgb) + t1cdf_dev<float>(k, nu, lgb) - 1.0f;
+    return v > 0.0f ? (double)v : 0.0;
+}
+
 // ---------------------------------------------------------------------------
 // Phi_2(h, k; rho), the nu -> infinity limit of T_2 (the CFUSN model of eq 5),
 // warp-cooperative.  With e(theta) = exp(-(h^2 - 2 h k sin theta + k^2) / (2 cos^2 theta)),
@@ -965,4 +1028,187 @@ __device__ double tk_lattice_mom_tab_warp(const double* bt, const double* Lc, co
     *alpha_s = acc_sm[1 + K + K2];
     *se = acc_sm[2 + K + K2];
     return Sf / ((double)N * M);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 single-pass lattice pass of T_K with the truncated moments: the estimator of
+// tk_lattice_mom_warp / tk_lattice_mom_tab_warp (same points, same weights), arranged
+// for a GPU whose FP64 rate is a small fraction of its FP32 rate:
+//   - every sum except the per-shift sums of f (alpha_s's standard error needs those)
+//     stays in per-lane FP32 registers over all shifts, and the warp reduces each one
+//     once per record instead of once per shift;
+//   - the epilogue (the L-mapping of the moments, the mean and standard error of
+//     alpha_s over the shifts) runs in FP32 on every lane; only the record's outputs
+//     are widened to FP64;
+//   - TAB: the baker-transformed coordinates of each point come from wtab (K <= 4);
+//     P points per lane are in flight at once (independent chains of the separation
+//     of variables), P = 1 without the table.
+// Output protocol as tk_lattice_mom_warp: returns alpha (all lanes), *alpha_s, *se,
+// and acc_sm[1 .. K + K(K+1)/2] the standardised moments (FP64, visible to the warp).
+// acc_sm is this warp's slot of K + K(K+1)/2 + 3 + CF_MAXSHIFT doubles; its tail holds
+// the per-shift sums as floats.
+// ---------------------------------------------------------------------------
+template <int K, bool TAB, int P>
+__device__ double tk_lattice_mom_f32(const double* bt, const double* Lc, const float* __restrict__ chi,
+                                     const float* __restrict__ shf, const Lattice& lat, int lane,
+                                     double* acc_sm, float rk, double* alpha_s, double* se,
+                                     const float4* __restrict__ wtab)
+{
+    static_assert(TAB || P == 1, "P > 1 needs the coordinate table");
+    static_assert(!TAB || K <= 4, "the coordinate table holds 4 coordinates");
+    constexpr int K2 = K * (K + 1) / 2;
+    constexpr int W = K + K2;
+    float b[K], invd[K], Lf[K][K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        b[r] = (float)bt[r];
+        invd[r] = 1.0f / (float)Lc[r * K + r];
+#pragma unroll
+        for (int l = 0; l < K; ++l) Lf[r][l] = l <= r ? (float)Lc[r * K + l] : 0.0f;
+    }
+    const int N = lat.N, M = lat.M;
+    float* fshift = (float*)(acc_sm + W + 3);  // M per-shift sums of f
+    float x0[K + 1], dx[K + 1], omdx[K + 1];   // coordinates advanced in floating point (!TAB)
+    if constexpr (!TAB) {
+        const float invN = 1.0f / (float)N;
+#pragma unroll
+        for (int d = 1; d <= K; ++d) {
+            dx[d] = (float)(((long long)CF_WARP * lat.z[d]) % N) * invN;
+            omdx[d] = 1.0f - dx[d];
+            x0[d] = (float)(((long long)lane * lat.z[d]) % N) * invN;
+        }
+    }
+    float aw = 0.0f, a1[K], a2[K2];
+#pragma unroll
+    for (int r = 0; r < K; ++r) a1[r] = 0.0f;
+#pragma unroll
+    for (int r = 0; r < K2; ++r) a2[r] = 0.0f;
+    const float rk2 = rk * rk;
+    for (int m = 0; m < M; ++m) {
+        const float* __restrict__ crow = chi + (size_t)m * N;
+        float af = 0.0f;
+        float xs[K + 1];
+        if constexpr (!TAB) {
+#pragma unroll
+            for (int d = 1; d <= K; ++d) {
+                xs[d] = x0[d] + shf[m * CF_MAXDIM + d];
+                if (xs[d] >= 1.0f) xs[d] -= 1.0f;
+            }
+        }
+        const float4* __restrict__ wrow = TAB ? wtab + (size_t)m * N : nullptr;
+        for (int i0 = lane; i0 < N; i0 += CF_WARP * P) {
+            float s[P], wc[P][4];
+            bool ok[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const int i = i0 + CF_WARP * p;
+                ok[p] = i < N;
+                s[p] = ok[p] ? crow[i] : 0.0f;
+                if constexpr (TAB) {
+                    const float4 t = ok[p] ? wrow[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    wc[p][0] = t.x; wc[p][1] = t.y; wc[p][2] = t.z; wc[p][3] = t.w;
+                }
+            }
+            float y[P][K], f[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) f[p] = 1.0f;
+#pragma unroll
+            for (int r = 0; r < K; ++r) {
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    float a = b[r] * s[p];
+#pragma unroll
+                    for (int l = 0; l < r; ++l) a -= Lf[r][l] * y[p][l];
+                    const float e = cf_ncdf_f32(a * invd[r]);
+                    f[p] *= e;
+                    float w;
+                    if constexpr (TAB) w = wc[p][r];
+                    else w = 1.0f - fabsf(2.0f * xs[r + 1] - 1.0f);
+                    float v = w * e;
+                    v = v < Lim<float>::vmin() ? Lim<float>::vmin() : v;
+                    v = v > Lim<float>::one_minus_ulp() ? Lim<float>::one_minus_ulp() : v;
+                    y[p][r] = cf_ncdfinv_f32(v);
+                }
+            }
+            // weight f s^2 (alpha at k2 dof); X = L y / s2 is linear in y: accumulate
+            // f s rk y and f rk^2 y y^T and map through L once per record
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const float fp = ok[p] ? f[p] : 0.0f;
+                const float fs = fp * s[p];
+                const float w1 = fs * rk, w2 = fp * rk2;
+                af += fp;
+                aw = fmaf(fs, s[p], aw);
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    a1[r] = fmaf(w1, y[p][r], a1[r]);
+                    const float t = w2 * y[p][r];
+#pragma unroll
+                    for (int c = 0; c <= r; ++c) a2[r * (r + 1) / 2 + c] = fmaf(t, y[p][c], a2[r * (r + 1) / 2 + c]);
+                }
+            }
+            if constexpr (!TAB) {
+#pragma unroll
+                for (int d = 1; d <= K; ++d) {
+                    const float t = xs[d] - omdx[d];
+                    xs[d] = t >= 0.0f ? t : xs[d] + dx[d];
+                }
+            }
+        }
+        af = warp_sum(af);
+        if (lane == 0) fshift[m] = af;
+    }
+    aw = warp_sum(aw);
+#pragma unroll
+    for (int r = 0; r < K; ++r) a1[r] = warp_sum(a1[r]);
+#pragma unroll
+    for (int r = 0; r < K2; ++r) a2[r] = warp_sum(a2[r]);
+    __syncwarp();
+    // alpha_s: mean of the shift means and its standard error, shifts over lanes
+    const float invN = 1.0f / (float)N;
+    float sm0 = lane < M ? fshift[lane] * invN : 0.0f;
+    float sm1 = lane + CF_WARP < M ? fshift[lane + CF_WARP] * invN : 0.0f;
+    const float mean = warp_sum(sm0 + sm1) / (float)M;
+    const float d0 = lane < M ? sm0 - mean : 0.0f, d1 = lane + CF_WARP < M ? sm1 - mean : 0.0f;
+    const float ss = warp_sum(d0 * d0 + d1 * d1);
+    // the moments: m1 = L a1 / aw, m2 = L A L^T / aw (A the symmetric matrix of a2), on every
+    // lane; lane t keeps output t
+    const float inv = aw > 0.0f ? 1.0f / aw : 0.0f;
+    float mine[2] = {0.0f, 0.0f};
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+        float v = 0.0f;
+#pragma unroll
+        for (int l = 0; l <= t; ++l) v = fmaf(Lf[t][l], a1[l], v);
+        if (lane == t) mine[0] = v * inv;
+        if (lane + CF_WARP == t) mine[1] = v * inv;
+    }
+    float B[K][K];  // B = A L^T
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            float v = 0.0f;
+#pragma unroll
+            for (int j = 0; j <= c; ++j) v = fmaf(a2[i >= j ? i * (i + 1) / 2 + j : j * (j + 1) / 2 + i], Lf[c][j], v);
+            B[i][c] = v;
+        }
+#pragma unroll
+    for (int r = 0; r < K; ++r)
+#pragma unroll
+        for (int c = 0; c <= r; ++c) {
+            float v = 0.0f;
+#pragma unroll
+            for (int i = 0; i <= r; ++i) v = fmaf(Lf[r][i], B[i][c], v);
+            const int t = K + r * (r + 1) / 2 + c;
+            if (lane == t) mine[0] = v * inv;
+            if (lane + CF_WARP == t) mine[1] = v * inv;
+        }
+    __syncwarp();  // every lane has read the per-shift sums before the slot is overwritten
+    if (lane < W) acc_sm[1 + lane] = (double)mine[0];
+    if (lane + CF_WARP < W) acc_sm[1 + lane + CF_WARP] = (double)mine[1];
+    __syncwarp();
+    *alpha_s = (double)mean;
+    *se = M > 1 ? (double)sqrtf(ss / (float)(M - 1) / (float)M) : 0.0;
+    return (double)aw / ((double)N * M);
 }

@@ -83,10 +83,10 @@ class CudaShard:
     """One shard of the observations on this process's GPU: a library context
     over rows [lo, hi) and its padded segment buffer."""
 
-    def __init__(self, cf, p, q, g, lo, hi, opts, y_rows, params, seg_per_rank):
+    def __init__(self, cf, p, q, g, lo, hi, opts, y_rows, params, seg_per_rank, n_total):
         import torch
 
-        self.cf, self.lo, self.hi = cf, lo, hi
+        self.cf, self.lo, self.hi, self.n_total = cf, lo, hi, n_total
         self.ctx = cf.cfust_create(p, q, g, hi - lo, opts)
         cf.cfust_set_data(self.ctx, y_rows)
         cf.cfust_set_params(self.ctx, params)
@@ -100,7 +100,7 @@ class CudaShard:
         return self.local
 
     def reduce_segments(self, allseg):
-        return self.cf.cfust_reduce_segments(self.ctx, allseg)
+        return self.cf.cfust_reduce_segments(self.ctx, allseg, self.n_total)
 
     def mstep(self):
         self.cf.cfust_mstep(self.ctx)
@@ -165,7 +165,7 @@ class TorchGroup:
 
     def make_fit(self, cf, w, opts, y_rows):
         lo, hi = self.rows(w["n"], cf, w, opts)
-        eng = CudaShard(cf, w["p"], w["q"], w["g"], lo, hi, opts, y_rows, w["init"], self.seg_per_rank)
+        eng = CudaShard(cf, w["p"], w["q"], w["g"], lo, hi, opts, y_rows, w["init"], self.seg_per_rank, w["n"])
         group = self
 
         class Step:

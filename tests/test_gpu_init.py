@@ -97,3 +97,56 @@ def test_init_errors(cf):
     with pytest.raises(cf.CfustError) as e:
         cf.cfust_init(c, nstarts=1, labels=one)
     assert e.value.status == cf.CFUST_ENOTPD
+
+
+# ---- k-means partitions on the device (Algorithm 1's clusterings) ------------------
+def _near_ties(y, centres, rel=1e-9):
+    """Observations whose two nearest centres are within rel in squared distance: there
+    the assignment may differ by the order of the cluster sums' rounding."""
+    d = np.sort(((y[:, None, :] - centres[None]) ** 2).sum(-1), axis=1)
+    return d[:, 1] - d[:, 0] <= rel * d[:, 0]
+
+
+@pytest.mark.parametrize("name,n,starts", [("flow_p4", 20000, 3), ("wide_p16", 20000, 2), ("two_comp_p2", 5000, 2)])
+def test_kmeans_matches_oracle(cf, oracle, name, n, starts):
+    """Same starting centres, same Lloyd iteration: labels identical (but for near-ties,
+    which rounding may decide either way), centres within 1e-9 relative, same count of
+    assignments when no label differs."""
+    w = synth.make_workload(name, n=n, with_init=False)
+    c = _ctx(cf, w, w["y"])
+    lab, its, cen = cf.cfust_kmeans(c, nstarts=starts, seed=2024, max_iter=300)
+    rlab, rits, rcen = oracle.kmeans(w["y"], w["g"], nstarts=starts, seed=2024, max_iter=300)
+    for s in range(starts):
+        diff = lab[s] != rlab[s]
+        tie = _near_ties(w["y"], rcen[s])
+        assert np.all(tie[diff]), f"start {s}: {diff.sum()} labels differ, {np.sum(diff & ~tie)} not at ties"
+        np.testing.assert_allclose(cen[s], rcen[s], rtol=1e-9, atol=1e-12)
+        if not diff.any():
+            assert its[s] == rits[s]
+        assert its[s] < 300
+
+
+def test_kmeans_partitions_for_init(cf, oracle):
+    """Algorithm 1 on device k-means partitions: the candidates and the chosen start
+    match the oracle's Algorithm 1 on the oracle's k-means partitions."""
+    w = synth.make_workload("flow_p4", n=3000, with_init=False)
+    c = _ctx(cf, w, w["y"])
+    lab, _, _ = cf.cfust_kmeans(c, nstarts=2, seed=5, max_iter=200)
+    rlab, _, _ = oracle.kmeans(w["y"], w["g"], nstarts=2, seed=5, max_iter=200)
+    assert np.array_equal(lab, rlab)
+    ll, ib = cf.cfust_init(c, nstarts=2, labels=lab)
+    ref = oracle.init(w["y"], w["g"], w["q"], oracle.qmc(**dict(w["qmc"], moments=1)), nstarts=2, labels=rlab)
+    _compare(cf, c, ll, ib, ref)
+
+
+def test_kmeans_errors(cf):
+    w = synth.make_workload("two_comp_p2", n=200, with_init=False)
+    c = _ctx(cf, w, w["y"])
+    with pytest.raises(cf.CfustError) as e:
+        cf.cfust_kmeans(c, nstarts=0)
+    assert e.value.status == cf.CFUST_EINVAL
+    c1 = cf.cfust_create(2, 2, 2, 1, cf.cfust_default_opts())
+    cf.cfust_set_data(c1, w["y"][:1])
+    with pytest.raises(cf.CfustError) as e:
+        cf.cfust_kmeans(c1)
+    assert e.value.status == cf.CFUST_EINVAL

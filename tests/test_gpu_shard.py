@@ -49,7 +49,7 @@ def test_sharded_fit_reproduces_cfust_fit(cf, name, n, precision, moments, world
     bounds, per = shard.shard_bounds(n, world, rps)
     assert all(lo % rps == 0 for lo, _ in bounds)
     engines = [shard.CudaShard(cf, w["p"], w["q"], w["g"], lo, hi, opts, np.ascontiguousarray(y[lo:hi]),
-                               w["init"], per) for lo, hi in bounds]
+                               w["init"], per, n) for lo, hi in bounds]
     it, hist = shard.sharded_fit(engines, torch.cat, iters)
     assert it == it_ref == iters
     assert np.array_equal(hist[:-1], hist_ref[:-1])
@@ -72,7 +72,7 @@ def test_sharded_statistics_equal_whole(cf):
     S = cf.cfust_get_stats(whole)
     rps = cf.cfust_rows_per_segment(w["p"], w["q"], w["g"], 1)
     bounds, per = shard.shard_bounds(w["n"], 3, rps)
-    engines = [shard.CudaShard(cf, w["p"], w["q"], w["g"], lo, hi, opts, w["y"][lo:hi], w["init"], per)
+    engines = [shard.CudaShard(cf, w["p"], w["q"], w["g"], lo, hi, opts, w["y"][lo:hi], w["init"], per, w["n"])
                for lo, hi in bounds]
     allseg = torch.cat([e.estep_segments() for e in engines])
     for e in engines:

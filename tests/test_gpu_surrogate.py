@@ -176,7 +176,7 @@ def _ctx(cf, w, n, precision=1):
 
 def test_surrogate_estep_and_em(cf):
     """learned_p6 subsample (p = q = g = 6), FP32: after training at Psi^(0) the
-    surrogate E-step reproduces the lattice l within 5e-3 relative with under 5 %
+    surrogate E-step reproduces the lattice l within 1e-3 relative with under 5 %
     fallbacks; every M-step after a surrogate E-step succeeds (the predicted
     covariances are positive definite by construction); 20 surrogate iterations
     followed by 20 lattice iterations keep at least half the l gain of 40 lattice
@@ -191,7 +191,8 @@ def test_surrogate_estep_and_em(cf):
     L_sur = cf.cfust_estep(b)
     recs, fb = cf.cfust_surrogate_info(b)
     assert recs == 2 * n * w["g"] and fb < 0.05 * recs
-    assert abs(L_sur - ll0) <= 5e-3 * abs(ll0)  # measured 1.3e-4 .. 2e-3 across training settings
+    print(f"surrogate E-step l relative error {abs(L_sur - ll0) / abs(ll0):.2e}, fallbacks {fb / recs:.2e}")
+    assert abs(L_sur - ll0) <= 1e-3 * abs(ll0)
     for _ in range(20):
         cf.cfust_mstep(b)
         cf.cfust_estep(b)
