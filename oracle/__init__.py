@@ -43,7 +43,7 @@ def build(force: bool = False) -> str:
 
 class Qmc(C.Structure):
     _fields_ = [("npoints", C.c_int), ("nshifts", C.c_int), ("korobov_a", C.c_int),
-                ("seed", C.c_uint64), ("moments", C.c_int)]
+                ("seed", C.c_uint64), ("moments", C.c_int), ("elogw", C.c_int)]
 
 
 _dp = C.POINTER(C.c_double)
@@ -122,11 +122,12 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def qmc(npoints=1024, nshifts=8, korobov_a=119, seed=0, moments=0):
+def qmc(npoints=1024, nshifts=8, korobov_a=119, seed=0, moments=0, elogw=0):
     """Lattice settings (both sides receive the same values as inputs);
     moments = 1 selects the single-pass ratio estimators of the truncated-t
-    moments (q >= 3)."""
-    return Qmc(int(npoints), int(nshifts), int(korobov_a), int(seed), int(moments))
+    moments (q >= 3); elogw = 1 (with moments = 1) the exact E[log W | y] from
+    the same pass instead of the one-step-late eq (15)."""
+    return Qmc(int(npoints), int(nshifts), int(korobov_a), int(seed), int(moments), int(elogw))
 
 
 # ---- scalar special functions -------------------------------------------------

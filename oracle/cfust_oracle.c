@@ -578,7 +578,7 @@ static double tk_moments_qmc(int k, const double* b, const double* V, double nu,
  * The unweighted mean of the same points is alpha_s (eq 4).  Returns alpha; m1 (k) and
  * m2 (k x k) in the units of X.  stab: chi table at k1 dof (optional). */
 static double tk_joint_qmc(int k, const double* c, const double* Lam, double nud, double k1,
-                           const ora_qmc* qmc, const double* stab, double* m1, double* m2)
+                           const ora_qmc* qmc, const double* stab, double* m1, double* m2, double* elogw)
 {
     const double k2 = k1 + 2.0;
     double R[ORA_MAXQ * ORA_MAXQ], L[ORA_MAXQ * ORA_MAXQ], bt[ORA_MAXQ], dl[ORA_MAXQ];
@@ -590,6 +590,7 @@ static double tk_joint_qmc(int k, const double* c, const double* Lam, double nud
     const double ratio = sqrt(k1 / k2);
     const int N = qmc->npoints, M = qmc->nshifts;
     double sw = 0.0, sx[ORA_MAXQ], sxx[ORA_MAXQ * ORA_MAXQ];
+    double sf = 0.0, sfl = 0.0;  /* sum f and sum f log(s^2) over the points (elogw) */
     memset(sx, 0, sizeof(sx));
     memset(sxx, 0, sizeof(sxx));
     for (int m = 0; m < M; ++m) {
@@ -611,6 +612,11 @@ static double tk_joint_qmc(int k, const double* c, const double* Lam, double nud
                 y[r] = ora_phi_inv(v);
             }
             if (f == 0.0) continue;
+            if (elogw) {
+                /* W = k1 s^2 / nud, so log W = log(s^2) + log(k1/nud) */
+                sf += f;
+                sfl += f * log(s * s);
+            }
             const double fw = f * s * s, s2 = s * ratio;
             double x[ORA_MAXQ];
             for (int r = 0; r < k; ++r) {
@@ -626,6 +632,7 @@ static double tk_joint_qmc(int k, const double* c, const double* Lam, double nud
         }
     }
     const double alpha = sw / ((double)N * M);
+    if (elogw) *elogw = sf > 0.0 ? sfl / sf + log(k1 / nud) : NAN;
     for (int a = 0; a < k; ++a) {
         const double sa = sqrt(nud / k2) * dl[a];
         m1[a] = sw > 0.0 ? sx[a] / sw * sa : 0.0;
@@ -639,7 +646,7 @@ double ora_tk_joint(int k, const double* c, const double* Lam, double nud, doubl
                     double* m1, double* m2)
 {
     if (k < 1 || k > ORA_MAXQ || !(k1 > 0.0) || !(nud > 0.0)) return NAN;
-    return tk_joint_qmc(k, c, Lam, nud, k1, qmc, NULL, m1, m2);
+    return tk_joint_qmc(k, c, Lam, nud, k1, qmc, NULL, m1, m2, NULL);
 }
 
 double ora_tk_moments(int k, const double* b, const double* V, double nu, const ora_qmc* qmc,
@@ -926,11 +933,13 @@ static int pair_core(const comp_t* C, const ora_qmc* qmc, const double* y, int d
     if (qmc->moments && q >= 3) {
         /* eqs (13), (16), (17) from the lattice pass of alpha_s (points weighted by W/(nu+p)):
          * X ~ t_q(0, S2, nu+p+2), S2 = ((nu+d)/(nu+p+2)) Lambda, truncated to X <= c; U = c - X. */
-        double m1[ORA_MAXQ], m2[ORA_MAXQ * ORA_MAXQ];
-        double alpha = tk_joint_qmc(q, c, C->Lambda, nu + d, nu + p, qmc, C->stab[0], m1, m2);
+        double m1[ORA_MAXQ], m2[ORA_MAXQ * ORA_MAXQ], ew = NAN;
+        const int exact = qmc->elogw && !isinf(nu);
+        double alpha = tk_joint_qmc(q, c, C->Lambda, nu + d, nu + p, qmc, C->stab[0], m1, m2, exact ? &ew : NULL);
         double u = (nu + p) / (nu + d) * alpha / alpha_s;
         *u_out = u;
-        *elogu_out = u - log(0.5 * (nu + d)) - (nu + p) / (nu + d) + ora_digamma(0.5 * (nu + p));
+        /* eq (15) (one-step-late), or the exact E[log W | y] of the same pass */
+        *elogu_out = exact ? ew : u - log(0.5 * (nu + d)) - (nu + p) / (nu + d) + ora_digamma(0.5 * (nu + p));
         for (int a = 0; a < q; ++a) eu[a] = u * (c[a] - m1[a]);
         for (int a = 0; a < q; ++a)
             for (int bb = 0; bb < q; ++bb) {

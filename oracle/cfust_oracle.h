@@ -45,6 +45,10 @@ typedef struct {
     uint64_t seed;      /* SplitMix64 key for the random shifts */
     int moments;        /* 0: truncated-t moments by the T_{q-1}/T_{q-2} recursion;
                            1 (q >= 3): ratio estimators from the lattice pass of alpha */
+    int elogw;          /* E[log W | y] of the nu update: 0: the one-step-late form of eq (15);
+                           1 (moments = 1, q >= 3): exact, the ratio estimator of log W over the
+                           points of the pass of alpha_s (the posterior of W given y is the
+                           Gamma((nu+p)/2, (nu+d)/2) law tilted by Phi_q(sqrt(W) c; 0, Lambda)) */
 } ora_qmc;
 
 /* ---- special functions (exposed for the pin tests) ---- */

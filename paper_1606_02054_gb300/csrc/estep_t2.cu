@@ -88,9 +88,9 @@ __global__ void __launch_bounds__(256) t2_records_group_kernel(RecSet r, IntegAr
 
 // Lanes per FP32 T_2 record (finite dof); 32 = the warp-per-record kernel.  Measured at
 // p = 16, q = 2, g = 8, n = 2e6 (3.2e7 records, ~45 nodes each): 14.3 ms with 32 lanes,
-// 9.6 with 16, 7.9 with 8, 7.1 with 4.
+// 9.6 with 16, 7.9 with 8, 7.1 with 4, 6.8 with 2.
 #ifndef CF_T2_GROUP
-#define CF_T2_GROUP 4
+#define CF_T2_GROUP 2
 #endif
 
 cudaError_t launch_t2(const RecSet& r, const IntegArgs& a, int fp32, int blocks, cudaStream_t st)

@@ -415,3 +415,72 @@ def test_joint_pass_change_of_measure(oracle):
         R = np.full((q, q), 0.5) + 0.5 * np.eye(q)
         a0, _, _ = oracle.tk_joint(np.zeros(q), R, 7.0, 5.0, big)
         assert abs(a0 - 1.0 / (q + 1)) <= 2e-4, (q, a0)
+
+
+# ---------------------------------------------------------------------------
+# Exact E[log W | y] from the single pass (elogw = 1) in place of the OSL eq (15)
+# ---------------------------------------------------------------------------
+def _elogw_reference(y, mu, Sigma, Delta, nu):
+    """E[log W | y] for one component by a 1-D integral over t = log W: the posterior of W
+    is the Gamma((nu+p)/2, rate (nu+d)/2) law tilted by Phi_q(sqrt(W) c; 0, Lambda) (the
+    hierarchy of eq 6 with U0 integrated out), so in t its density is proportional to
+    exp(a t - b e^t) Phi_q(e^(t/2) c), a = (nu+p)/2, b = (nu+d)/2; trapezoid rule on a
+    wide uniform grid (exponentially accurate for this smooth, fast-decaying integrand),
+    Phi_q by scipy's multivariate normal CDF."""
+    p, q = Delta.shape
+    Om = Sigma + Delta @ Delta.T
+    r = y - mu
+    Oir = np.linalg.solve(Om, r)
+    d = float(r @ Oir)
+    c = Delta.T @ Oir
+    Lam = np.eye(q) - Delta.T @ np.linalg.solve(Om, Delta)
+    a, b = (nu + p) / 2, (nu + d) / 2
+    t0 = math.log(a / b)
+    t = np.linspace(t0 - 30.0 / math.sqrt(a) - 8.0, t0 + 20.0 / math.sqrt(a), 120)
+    mvn = st.multivariate_normal(mean=np.zeros(q), cov=Lam, abseps=1e-13, releps=1e-6, maxpts=400_000)
+    phi = np.array([mvn.cdf(math.exp(0.5 * ti) * c) for ti in t])
+    lg = a * t - b * np.exp(t)
+    wgt = np.exp(lg - lg.max()) * phi
+    return float(np.sum(t * wgt) / np.sum(wgt)), d
+
+
+def test_exact_elogw_delta_zero(oracle):
+    """Delta = 0: the tilt is a constant, the posterior of W is Gamma((nu+p)/2, (nu+d)/2)
+    and E[log W | y] = psi((nu+p)/2) - log((nu+d)/2) -- which the OSL form of eq (15)
+    also gives here, exactly but for the lattice error of its u.  The lattice mean of
+    log W is within its QMC error."""
+    p = q = 3
+    rng = np.random.default_rng(61)
+    S = _rand_spd(rng, p)
+    nu = 6.3
+    y = rng.normal(0, 1.5, p)
+    spec = oracle.qmc(4096, 16, 1517, 3, 1, 1)
+    r = oracle.pair(y, np.zeros(p), S, np.zeros((p, q)), nu, spec)
+    d = float(y @ np.linalg.solve(S, y))
+    ref = sp.digamma((nu + p) / 2) - math.log((nu + d) / 2)
+    assert abs(r["elogu"] - ref) <= 2e-4 * max(1.0, abs(ref))
+    osl = oracle.pair(y, np.zeros(p), S, np.zeros((p, q)), nu, oracle.qmc(4096, 16, 1517, 3, 1, 0))
+    assert abs(osl["elogu"] - ref) <= 1e-5 * max(1.0, abs(ref))
+
+
+@pytest.mark.parametrize("case", [0, 1, 2])
+def test_exact_elogw_matches_tilted_gamma_integral(oracle, case):
+    """Skewed components (q = 3, 4): the single-pass E[log W | y] equals the integral of
+    log W against the tilted Gamma posterior to the lattice's error (1.5e-3; case 1 puts y
+    on the unskewed side, where the tilt is steep and the 4096 x 16 lattice's mean is
+    9e-4 off), where the OSL form of eq (15) is off by 7e-3 to 0.43."""
+    rng = np.random.default_rng(700 + case)
+    p, q = (3, 3) if case < 2 else (4, 4)
+    S = _rand_spd(rng, p)
+    Delta = rng.normal(0, 1.2, (p, q))
+    nu = [4.5, 9.0, 6.0][case]
+    mu = np.zeros(p)
+    y = rng.normal(0, 1.0, p) + (Delta @ np.abs(rng.normal(0, 1, q))) * (1 if case != 1 else -1)
+    ref, d = _elogw_reference(y, mu, S, Delta, nu)
+    ex = oracle.pair(y, mu, S, Delta, nu, oracle.qmc(4096, 16, 1517, 9, 1, 1))
+    osl = oracle.pair(y, mu, S, Delta, nu, oracle.qmc(4096, 16, 1517, 9, 1, 0))
+    assert abs(ex["elogu"] - ref) <= 1.5e-3 * max(1.0, abs(ref)), (ex["elogu"], ref)
+    assert abs(osl["elogu"] - ref) > 3 * abs(ex["elogu"] - ref)
+    # the same pass's u = E[W | y] (eq 13) is unchanged by the elogw reading
+    assert ex["u"] == osl["u"] and np.array_equal(ex["eu"], osl["eu"])
+    print(f"case {case}: exact {ex['elogu']:.6f}, integral {ref:.6f}, OSL {osl['elogu']:.6f}")
