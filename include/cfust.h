@@ -99,7 +99,18 @@ typedef struct {
                             CFUST_MODEL_CFUSN: its nu -> infinity limit, the CFUSN mixture
                             of eq (5) (density 2^q phi_p(y; mu, Omega) Phi_q(c; 0, Lambda),
                             u = 1, no nu step: nu is held and stored as +infinity) */
+    int elogw;           /* E[log W | y] of the nu update (eq 22): CFUST_ELOGW_OSL (0,
+                            default): the one-step-late form of eq (15);
+                            CFUST_ELOGW_EXACT: the exact conditional expectation -- the
+                            posterior of W given y is the Gamma((nu+p)/2, (nu+d)/2) law
+                            tilted by Phi_q(sqrt(W) c; 0, Lambda), which the points of the
+                            lattice pass of alpha_s sample with weight f, so E[log W | y] is
+                            the f-weighted mean of log W over them (needs moments = 1,
+                            q >= 3, the CFUST model; not with the learned surrogate) */
 } cfust_opts;
+
+#define CFUST_ELOGW_OSL 0
+#define CFUST_ELOGW_EXACT 1
 
 #define CFUST_MODEL_CFUST 0
 #define CFUST_MODEL_CFUSN 1
@@ -247,7 +258,23 @@ cfust_status cfust_init(cfust_ctx* ctx, int nstarts, const int32_t* labels, uint
 cfust_status cfust_kmeans(cfust_ctx* ctx, int nstarts, uint64_t seed, int max_iter, int32_t* labels_out,
                           int* iters_out, double* centres_out);
 
-/* Flags of cfust_fit_batch. *//* Flags of cfust_fit_batch. */
+/* Autotuner of the integrators' launch shapes (not part of the paper).  Runs one
+ * E-step at the current Psi, then times (CUDA events, best of reps runs after one
+ * warm-up) each candidate shape of the context's integral records:
+ *   - FP32 T_2 records of finite dof: 2, 4, 8, 16 or 32 lanes per record
+ *     (ms[0..4]; -1 where the context has no such records);
+ *   - the FP32 single-pass moment pass at q <= 4: 1 or 2 lattice points in flight
+ *     per lane (ms[5..6]; -1 where not applicable);
+ * and keeps the fastest (choices[0]: lanes per T_2 record, choices[1]: points per
+ * lane; 0 where not applicable).  The choice holds for this context and, for the rest
+ * of the process, for every context (one not tuned itself) whose records fall in the
+ * same (kernel, dimension, precision, floor(log2 records)) bucket, from its next
+ * E-step on (a fit graph of cfust_fit_batch keeps the shapes it was captured with).  Leaves no E-step
+ * results (run cfust_estep before cfust_mstep).  Without tuning the shapes are 2 lanes
+ * per T_2 record and 2 points per lane.  choices (2) and ms (7) may be NULL. */
+cfust_status cfust_autotune(cfust_ctx* ctx, int reps, int* choices, double* ms);
+
+/* Flags of cfust_fit_batch. *//* Flags of cfust_fit_batch. *//* Flags of cfust_fit_batch. */
 #define CFUST_FIT_NO_FINAL 1 /* skip the density pass that gives l(Psi^(max_iter)) */
 
 /* Batched form of cfust_fit: nfits independent fits (different contexts,

@@ -54,7 +54,7 @@ class cfust_opts(C.Structure):
                 ("qmc_korobov_a", C.c_int), ("seed", C.c_uint64), ("nu_min", C.c_double),
                 ("nu_max", C.c_double), ("device", C.c_int), ("cuda_stream", C.c_void_p),
                 ("t2_nodes", C.c_int), ("profile", C.c_int), ("moments", C.c_int),
-                ("hold", C.c_int), ("model", C.c_int)]
+                ("hold", C.c_int), ("model", C.c_int), ("elogw", C.c_int)]
 
 
 class cfust_rates(C.Structure):
@@ -103,6 +103,8 @@ def lib():
             L.cfust_init.restype = i
             L.cfust_kmeans.argtypes = [vp, i, C.c_uint64, i, vp, C.POINTER(i), _dp]
             L.cfust_kmeans.restype = i
+            L.cfust_autotune.argtypes = [vp, i, C.POINTER(i), _dp]
+            L.cfust_autotune.restype = i
             L.cfust_special_f32.argtypes = [i, i64, vp, vp, i]
             L.cfust_special_f32.restype = i
             L.cfust_tk_eval.argtypes = [vp, i, i, _dp, _dp, _dp, _dp, _dp]
@@ -320,6 +322,18 @@ def cfust_kmeans(ctx: Context, nstarts=1, seed=0, max_iter=100):
                               lab.ctypes.data_as(C.c_void_p), its.ctypes.data_as(C.POINTER(C.c_int)),
                               _ptr(cen)), ctx)
     return lab, its, cen
+
+
+def cfust_autotune(ctx: Context, reps=3):
+    """Times the integrators' candidate launch shapes on this context's records and keeps
+    the fastest (see include/cfust.h): returns (choices {t2_lanes, mom_points}, timings
+    {name: ms or None})."""
+    ch = (C.c_int * 2)()
+    ms = np.zeros(7)
+    _check(lib().cfust_autotune(ctx.handle, int(reps), ch, _ptr(ms)), ctx)
+    names = ["t2_lanes_2", "t2_lanes_4", "t2_lanes_8", "t2_lanes_16", "t2_lanes_32", "mom_points_1", "mom_points_2"]
+    return ({"t2_lanes": int(ch[0]), "mom_points": int(ch[1])},
+            {k: (float(v) if v >= 0 else None) for k, v in zip(names, ms)})
 
 
 def cfust_init(ctx: Context, nstarts=4, labels=None, seed=0, alphas=None, nu0=10.0):

@@ -6,7 +6,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "cfust.h"
@@ -16,7 +19,7 @@
 __global__ void setup_components_kernel(Dims, Layout, const double*, const double*, const double*,
                                         const double*, double*, int*);
 __global__ void chi_table_kernel(int, int, const double*, const double*, Lattice, const double*, double, double*,
-                                 float*);
+                                 float*, double*, float*);
 __global__ void dof_consts_kernel(Dims, Layout, const double*, int, double*, double*, float*);
 __global__ void t1_table_kernel(int, const double*, float2*);
 __global__ void widen_kernel(const float*, long long, Dims, double*);
@@ -53,6 +56,8 @@ struct cfust_ctx {
     float* cst32 = nullptr;
     double* chi64 = nullptr;
     float* chi32 = nullptr;
+    double* lchi64 = nullptr;  // exact E[log W]: log(s^2) beside the chi tables
+    float* lchi32 = nullptr;
     double* shf64 = nullptr;
     float* shf32 = nullptr;
     float4* wtab = nullptr;  // FP32 single pass: lattice coordinates of every (shift, point)
@@ -62,6 +67,8 @@ struct cfust_ctx {
     double *logf = nullptr, *u = nullptr, *elogu = nullptr, *eu = nullptr, *euu = nullptr,
            *se = nullptr, *tau = nullptr;
     double *partial = nullptr, *stats = nullptr;
+    int tune_t2_group = 0;  // launch shapes of the integrators chosen by cfust_autotune on this
+    int tune_mom_p = 0;     // context (0: the process-wide choice for its bucket, else the default)
     double* seg = nullptr;  // segment sums of the block partials (nseg x width)
     long long nseg = 0;
     long long n_stats = 0;  // observations behind the current statistics (all shards'), the n of eq (18)
@@ -106,6 +113,10 @@ struct cfust_ctx {
     FitState* h_fstate = nullptr;
     double* h_fhist = nullptr;
 };
+
+namespace {
+void tune_lookup(const cfust_ctx* c, int* t2_group, int* mom_p);  // shapes in force (below)
+}
 
 static thread_local std::string g_create_err;
 
@@ -345,11 +356,11 @@ static void free_all(cfust_ctx* c)
                     c->glx64, c->glw64, c->glx32, c->glw32, c->glx32h, c->glw32h, c->logf, c->u, c->elogu, c->eu,
                     c->euu, c->se, c->tau, c->partial, c->stats, c->flags, c->comp_status,
                     c->stage32, c->pd, c->pc, c->fix_count, c->fix_list, c->y32, c->F32, c->t1tab,
-                    c->work_dev, c->seg};
+                    c->work_dev, c->seg, c->lchi64, c->lchi32};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (RecSet& r : c->rec) {
-        void* rb[] = {r.bt, r.fac, r.tab, r.dof, r.res, r.se, r.mom, r.t2f};
+        void* rb[] = {r.bt, r.fac, r.tab, r.dof, r.res, r.se, r.mom, r.t2f, r.lw};
         for (void* b : rb)
             if (b) cudaFree(b);
     }
@@ -407,6 +418,10 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
         return fail(nullptr, CFUST_EINVAL, "cfust_create: hold must combine CFUST_HOLD_DELTA and CFUST_HOLD_NU");
     if (o.model != CFUST_MODEL_CFUST && o.model != CFUST_MODEL_CFUSN)
         return fail(nullptr, CFUST_EINVAL, "cfust_create: model must be CFUST_MODEL_CFUST or CFUST_MODEL_CFUSN");
+    if (o.elogw != CFUST_ELOGW_OSL && o.elogw != CFUST_ELOGW_EXACT)
+        return fail(nullptr, CFUST_EINVAL, "cfust_create: elogw must be CFUST_ELOGW_OSL or CFUST_ELOGW_EXACT");
+    if (o.elogw == CFUST_ELOGW_EXACT && (o.moments != 1 || q < 3 || o.model != CFUST_MODEL_CFUST))
+        return fail(nullptr, CFUST_EINVAL, "cfust_create: exact E[log W] needs moments = 1, q >= 3 and the CFUST model");
     if (o.model == CFUST_MODEL_CFUSN) o.hold |= CFUST_HOLD_NU;  // no nu step in the normal limit
     cudaError_t e = cudaSetDevice(o.device);
     if (e != cudaSuccess)
@@ -470,6 +485,10 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     ALLOC(cst32, 3 * g * CST_STRIDE);
     ALLOC(chi64, ntab * NM);
     ALLOC(chi32, ntab * NM);
+    if (o.elogw == CFUST_ELOGW_EXACT) {
+        ALLOC(lchi64, ntab * NM);
+        ALLOC(lchi32, ntab * NM);
+    }
     ALLOC(shf64, (size_t)o.qmc_shifts * CF_MAXDIM);
     ALLOC(shf32, (size_t)o.qmc_shifts * CF_MAXDIM);
     ALLOC(glx64, c->t2n); ALLOC(glw64, c->t2n); ALLOC(glx32, c->t2n); ALLOC(glw32, c->t2n);
@@ -506,6 +525,7 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
             if (l == 0) { ALLOC(rec[l].se, nr); }
             if (r.k == 2 && o.precision != CFUST_PREC_FP64) { ALLOC(rec[l].t2f, 2 * nr); }
             if (l == 3) { ALLOC(rec[l].mom, nr * (q + q * (q + 1) / 2)); }
+            if (l == 3 && o.elogw == CFUST_ELOGW_EXACT) { ALLOC(rec[l].lw, nr); }
         }
     }
 #undef ALLOC
@@ -710,7 +730,7 @@ static cfust_status launch_setup(cfust_ctx* c)
         // fix-up reads it, and 1e-9 is far inside what a pair sent there needs
         const double rtol = c->opts.precision == CFUST_PREC_FP64 ? 1e-15 : 1e-9;
         chi_table_kernel<<<blocks, 128, 0, c->st>>>(3 * c->g, every, c->dofs, c->cst64, c->lat, c->shf64, rtol,
-                                                     c->chi64, c->chi32);
+                                                     c->chi64, c->chi32, c->lchi64, c->lchi32);
         LAUNCHED();
         prof_end(c, CFUST_PROF_CHI, 1);
     }
@@ -729,7 +749,12 @@ static IntegArgs integ_args(const cfust_ctx* c)
     ia.t1tab = c->t1tab;
     ia.wtab = c->wtab;
     ia.nodes = nullptr;
-    ia.t2_grouped = c->opts.model == CFUST_MODEL_CFUSN ? 0 : 1;
+    int t2g = 0, mp = 0;
+    tune_lookup(c, &t2g, &mp);
+    ia.t2_group = c->opts.model == CFUST_MODEL_CFUSN ? CF_WARP : t2g;
+    ia.mom_p = mp;
+    ia.lchi64 = c->lchi64;
+    ia.lchi32 = c->lchi32;
     return ia;
 }
 
@@ -840,6 +865,7 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
         a.t2n = c->t2n;
         a.density_only = density_only;
         a.single_pass = sp;
+        a.lchi64 = c->lchi64;
         a.logf = c->logf; a.u = c->u; a.elogu = c->elogu; a.eu = c->eu; a.euu = c->euu; a.se = c->se;
         a.flags = c->flags;
         n0 = c->launches;
@@ -1071,6 +1097,133 @@ extern "C" cfust_status cfust_fit(cfust_ctx* c, int max_iter, double tol, int* i
     if (iters_out) *iters_out = it;
     if (loglik_hist) std::memcpy(loglik_hist, hist.data(), sizeof(double) * ((size_t)it + 1));
     return s;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the integrators' launch shapes.  Choices are kept per (kernel, record
+// dimension, precision, record-count bucket = floor(log2 records)) for the process, so
+// every context of a bucket that is created after a tuning run uses them (a CUDA graph
+// captures the shape in force when it is built).
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tune;  // (kind, k, precision, bucket) -> choice
+enum { TUNE_T2 = 0, TUNE_MOM = 1 };
+int bucket_of(long long nrec)
+{
+    int b = 0;
+    while (nrec > 1) { nrec >>= 1; ++b; }
+    return b;
+}
+// the level of the context's T_2 records (FP32, finite dof), or -1
+int t2_level(const cfust_ctx* c)
+{
+    if (c->opts.precision == CFUST_PREC_FP64 || c->opts.model == CFUST_MODEL_CFUSN) return -1;
+    for (int l = 0; l < 3; ++l)
+        if (c->rec[l].k == 2 && c->rec[l].nrec > 0) return l;
+    return -1;
+}
+bool mom_tunable(const cfust_ctx* c)
+{
+    return c->single_pass && c->opts.precision != CFUST_PREC_FP64 && c->q <= 4 && c->rec[3].nrec > 0;
+}
+// The shapes in force: this context's tuning, else the process-wide choice for its
+// bucket, else the defaults (2 lanes per T_2 record, 2 points per lane)
+void tune_lookup(const cfust_ctx* c, int* t2_group, int* mom_p)
+{
+    *t2_group = c->tune_t2_group ? c->tune_t2_group : 2;
+    *mom_p = c->tune_mom_p ? c->tune_mom_p : 2;
+    if (c->tune_t2_group && c->tune_mom_p) return;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const int l = t2_level(c);
+    if (!c->tune_t2_group && l >= 0) {
+        auto it = g_tune.find({TUNE_T2, 2, c->opts.precision, bucket_of(c->rec[l].nrec)});
+        if (it != g_tune.end()) *t2_group = it->second;
+    }
+    if (!c->tune_mom_p && mom_tunable(c)) {
+        auto it = g_tune.find({TUNE_MOM, c->q, c->opts.precision, bucket_of(c->rec[3].nrec)});
+        if (it != g_tune.end()) *mom_p = it->second;
+    }
+}
+}  // namespace
+
+extern "C" cfust_status cfust_autotune(cfust_ctx* c, int reps, int* choices, double* ms)
+{
+    if (!c) return fail(nullptr, CFUST_EINVAL, "cfust_autotune: ctx is NULL");
+    if (reps < 1 || reps > 100) return fail(c, CFUST_EINVAL, "cfust_autotune: reps must lie in [1, 100]");
+    if (!c->have_data || !c->have_params)
+        return fail(c, CFUST_ESTATE, "cfust_autotune: set_data and set_params must come first");
+    CU(cudaSetDevice(c->opts.device));
+    static const int t2c[5] = {2, 4, 8, 16, 32};
+    static const int mpc[2] = {1, 2};
+    double t[7];
+    for (int i = 0; i < 7; ++i) t[i] = -1.0;
+    // one E-step leaves the records of the current Psi on the device
+    cfust_status s;
+    if ((s = enqueue_estep(c)) != CFUST_OK) return s;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CU(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(c, CFUST_ECUDA, "cfust_autotune: cudaEventCreate failed");
+    }
+    auto timeit = [&](auto launch, double* best) -> cudaError_t {
+        cudaError_t e = launch();  // warm-up
+        *best = 1e30;
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+            if ((e = cudaEventRecord(e0, c->st)) != cudaSuccess) break;
+            if ((e = launch()) != cudaSuccess) break;
+            if ((e = cudaEventRecord(e1, c->st)) != cudaSuccess) break;
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+            float f = 0.f;
+            if ((e = cudaEventElapsedTime(&f, e0, e1)) != cudaSuccess) break;
+            *best = std::min(*best, (double)f);
+        }
+        return e;
+    };
+    cudaError_t e = cudaSuccess;
+    IntegArgs ia = integ_args(c);
+    long long dummy = 0;
+    const int l = t2_level(c);
+    if (l >= 0) {
+        int bi = 0;
+        for (int i = 0; i < 5 && e == cudaSuccess; ++i) {
+            ia.t2_group = t2c[i];
+            e = timeit([&] { return launch_integrals(c->rec[l], ia, 1, c->nsm, c->st, &dummy); }, &t[i]);
+            if (t[i] < t[bi]) bi = i;
+        }
+        if (e == cudaSuccess) c->tune_t2_group = t2c[bi];
+    }
+    if (e == cudaSuccess && mom_tunable(c)) {
+        RecSet rm = c->rec[3];
+        rm.res0 = c->rec[0].res;
+        rm.se0 = c->rec[0].se;
+        int bi = 0;
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+            ia = integ_args(c);
+            ia.mom_p = mpc[i];
+            e = timeit([&] { return launch_moments(rm, ia, 1, c->nsm, c->st, &dummy); }, &t[5 + i]);
+            if (t[5 + i] < t[5 + bi]) bi = i;
+        }
+        if (e == cudaSuccess) c->tune_mom_p = mpc[bi];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return fail(c, CFUST_ECUDA, std::string("cfust_autotune: ") + cudaGetErrorString(e));
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (l >= 0) g_tune[{TUNE_T2, 2, c->opts.precision, bucket_of(c->rec[l].nrec)}] = c->tune_t2_group;
+        if (mom_tunable(c)) g_tune[{TUNE_MOM, c->q, c->opts.precision, bucket_of(c->rec[3].nrec)}] = c->tune_mom_p;
+    }
+    c->launches += dummy;
+    c->have_stats = false;  // the timing runs overwrote the integral records
+    if (choices) {
+        choices[0] = l >= 0 ? c->tune_t2_group : 0;
+        choices[1] = mom_tunable(c) ? c->tune_mom_p : 0;
+    }
+    if (ms)
+        for (int i = 0; i < 7; ++i) ms[i] = t[i];
+    return CFUST_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1700,7 +1853,7 @@ extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const doub
             const int blocks = (int)std::min<long long>((total + 127) / 128, 64LL * c->nsm);
             chi_table_kernel<<<blocks, 128, 0, c->st>>>(count, 1, r.dof, k64, c->lat, c->shf64,
                                                          c->opts.precision == CFUST_PREC_FP64 ? 1e-15 : 1e-9,
-                                                         t64, t32);
+                                                         t64, t32, nullptr, nullptr);
             c->launches++;
             if ((e = cudaGetLastError())) break;
         }
@@ -1750,6 +1903,8 @@ extern "C" cfust_status cfust_surrogate_train(cfust_ctx* c, const cfust_surrogat
     if (!opts) return fail(c, CFUST_EINVAL, "cfust_surrogate_train: opts is NULL");
     if (!c->single_pass)
         return fail(c, CFUST_EINVAL, "cfust_surrogate_train: needs single-pass moments (moments = 1, q >= 3)");
+    if (c->opts.elogw == CFUST_ELOGW_EXACT)
+        return fail(c, CFUST_EINVAL, "cfust_surrogate_train: the network predicts no E[log W]; use elogw = OSL");
     if (opts->epochs < 0 || opts->batch < 64 || opts->batch > (1 << 20) || opts->batch % 64 ||
         !(opts->lr > 0.f) || !(opts->margin >= 0.f))
         return fail(c, CFUST_EINVAL, "cfust_surrogate_train: epochs >= 0, batch a multiple of 64 in [64, 2^20], "

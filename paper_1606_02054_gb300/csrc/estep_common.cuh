@@ -240,9 +240,11 @@ __device__ inline void pair_assemble(const double* F, const Layout& Ly, int p, i
 // moments m = (E[X~], lower triangle of E[X~ X~^T]) of the truncated
 // X ~ t_q(0, S2, nu+p+2), S2 = ((nu+d)/(nu+p+2)) Lambda, X <= c, come from one
 // lattice pass; X = sigma * X~ with sigma_i = sqrt(S2_ii); U = c - X.
+// lw: the f-weighted mean of log(s^2) over the pass (exact E[log W]), or NaN for the
+// one-step-late form of eq (15)
 __device__ inline void pair_assemble_sp(const double* F, const Layout& Ly, int p, int q,
                                         const double* c, double d, double logtp, double alpha_s,
-                                        double alpha, const double* m, PairOut& o)
+                                        double alpha, const double* m, PairOut& o, double lw = NAN)
 {
     const double nu = F[Ly.scal + SC_NU], nu1 = nu + p;
     const bool nrm = isinf(nu);  // the normal limit (eq 5): u = 1, X ~ N(0, Lambda)
@@ -250,7 +252,9 @@ __device__ inline void pair_assemble_sp(const double* F, const Layout& Ly, int p
     o.logf = q * 0.6931471805599453 + logtp + log(alpha_s);  // eq (4)
     const double u = nrm ? 1.0 : nu1 / (nu + d) * alpha / alpha_s;  // eq (13)
     o.u = u;
-    o.elogu = nrm ? 0.0 : u - log(0.5 * (nu + d)) - nu1 / (nu + d) + F[Ly.scal + SC_PSI];  // eq (15)
+    // eq (15), or the exact E[log W | y]: W = s^2 (nu+p)/(nu+d) at every point of the pass
+    o.elogu = nrm ? 0.0 : !isnan(lw) ? lw + log(nu1 / (nu + d))
+                                     : u - log(0.5 * (nu + d)) - nu1 / (nu + d) + F[Ly.scal + SC_PSI];
     const double sc = nrm ? 1.0 : sqrt((nu + d) / (nu1 + 2.0));
     double sig[CF_MAXQ], m1[CF_MAXQ];
     for (int a = 0; a < q; ++a) {

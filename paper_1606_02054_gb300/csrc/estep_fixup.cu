@@ -60,19 +60,21 @@ __global__ void __launch_bounds__(128) fixup_kernel(EstepArgs a, const int* coun
             // the pass of alpha_s (bt still holds its limits) weighted to dof nu+p+2
             const double* Lq = F + fac_l0(a.Ly);
             const double rk = isinf(nu1) ? 1.0 : sqrt((nu1 + 2.0) / nu1);
-            double as = 0.0, sej = 0.0;
+            double as = 0.0, sej = 0.0, lw = NAN;
+            const double* lchi = a.lchi64 ? a.lchi64 + (size_t)(3 * h) * NM : nullptr;
+            double* lwp = lchi ? &lw : nullptr;
             switch (q) {
-            case 3: alpha = tk_lattice_mom_warp<double, 3>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej); break;
-            case 4: alpha = tk_lattice_mom_warp<double, 4>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej); break;
-            case 5: alpha = tk_lattice_mom_warp<double, 5>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej); break;
-            case 6: alpha = tk_lattice_mom_warp<double, 6>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej); break;
-            case 7: alpha = tk_lattice_mom_warp<double, 7>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej); break;
-            default: alpha = tk_lattice_mom_warp<double, 8>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej); break;
+            case 3: alpha = tk_lattice_mom_warp<double, 3>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej, lchi, lwp); break;
+            case 4: alpha = tk_lattice_mom_warp<double, 4>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej, lchi, lwp); break;
+            case 5: alpha = tk_lattice_mom_warp<double, 5>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej, lchi, lwp); break;
+            case 6: alpha = tk_lattice_mom_warp<double, 6>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej, lchi, lwp); break;
+            case 7: alpha = tk_lattice_mom_warp<double, 7>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej, lchi, lwp); break;
+            default: alpha = tk_lattice_mom_warp<double, 8>(bt, Lq, chi, a.shf64, a.lat, lane, acc, rk, &as, &sej, lchi, lwp); break;
             }
             for (int k = 0; k < q + q * (q + 1) / 2; ++k) m[k] = acc[1 + k];
             __syncwarp();
             PairOut o;
-            pair_assemble_sp(F, a.Ly, p, q, c, d, logtp, alpha_s, alpha, m, o);
+            pair_assemble_sp(F, a.Ly, p, q, c, d, logtp, alpha_s, alpha, m, o, lw);
             if (lane == 0) {
                 a.logf[pid] = o.logf;
                 if (a.se) a.se[pid] = se;

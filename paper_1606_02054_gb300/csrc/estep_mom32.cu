@@ -4,25 +4,19 @@
 #include "internal.cuh"
 #include "special.cuh"
 
-// Lattice points in flight per lane (with the coordinate table, K <= 4).
-#ifndef CF_MOM_P
-#define CF_MOM_P 2
-#endif
 // Blocks of 4 warps.  K = 7, 8 need 147-168 registers: 3 such blocks (12 warps) share an
 // SM where one block of 8 would leave it at 8.
 template <int K>
 __host__ __device__ constexpr int mom32_block() { return K >= 7 || K <= 4 ? 128 : 256; }
-// minimum resident blocks (an explicit 1 would let ptxas take up to 255 registers: K = 6
-// went from 128 to 154, halving its resident warps): K <= 4: CF_MOM_MINB4; K = 5, 6: 2
-// (128); K = 7, 8: 3 (170)
-#ifndef CF_MOM_MINB4
-#define CF_MOM_MINB4 5
-#endif
-template <int K>
-__host__ __device__ constexpr int mom32_minb() { return K <= 4 ? CF_MOM_MINB4 : (K <= 6 ? 2 : 3); }
+// Minimum resident blocks (an explicit 1 would let ptxas take up to 255 registers: K = 6
+// went from 128 to 154, halving its resident warps).  K <= 4 with P lattice points in flight
+// per lane: P = 1: 7 blocks (72 registers), P = 2: 5 (92); K = 5, 6: 2 (128); K = 7, 8: 3
+// (170).  Measured at flow_p4 (K = 4, 8e5 records): P = 1 40.4 ms, P = 2 39.1 ms.
+template <int K, int P>
+__host__ __device__ constexpr int mom32_minb() { return K <= 4 ? (P == 1 ? 7 : 5) : (K <= 6 ? 2 : 3); }
 
-template <int K, bool SEL>
-__global__ void __launch_bounds__(mom32_block<K>(), mom32_minb<K>()) lattice_mom_kernel_32(RecSet r, IntegArgs a)
+template <int K, bool SEL, bool LW, int P>
+__global__ void __launch_bounds__(mom32_block<K>(), mom32_minb<K, P>()) lattice_mom_kernel_32(RecSet r, IntegArgs a)
 {
     constexpr int W = K + K * (K + 1) / 2;
     const int lane = threadIdx.x & (CF_WARP - 1);
@@ -40,20 +34,22 @@ __global__ void __launch_bounds__(mom32_block<K>(), mom32_minb<K>()) lattice_mom
         // the pass of alpha_s (chi table at dof k1 = dof - 2) weighted to dof k2 = r.dof
         const float k2 = (float)r.dof[i];
         const float rk = isinf(k2) ? 1.0f : sqrtf(k2 / (k2 - 2.0f));
-        double as = 0.0, se = 0.0;
+        double as = 0.0, se = 0.0, lw = 0.0;
+        const float* lchi = LW ? a.lchi32 + (size_t)r.tab[i] * NM : nullptr;
         // the coordinate table only at K <= 4 (one float4 per point); at K = 6 it measured
         // 1.6x slower than advancing the coordinates
         double v;
         if constexpr (K <= 4)
-            v = tk_lattice_mom_f32<K, true, CF_MOM_P>(bt, a.F + r.fac[i], a.chi32 + (size_t)r.tab[i] * NM, a.shf32,
-                                                      a.lat, lane, acc, rk, &as, &se, a.wtab);
+            v = tk_lattice_mom_f32<K, true, P, LW>(bt, a.F + r.fac[i], a.chi32 + (size_t)r.tab[i] * NM,
+                                                          a.shf32, a.lat, lane, acc, rk, &as, &se, a.wtab, lchi, &lw);
         else
-            v = tk_lattice_mom_f32<K, false, 1>(bt, a.F + r.fac[i], a.chi32 + (size_t)r.tab[i] * NM, a.shf32,
-                                                a.lat, lane, acc, rk, &as, &se, nullptr);
+            v = tk_lattice_mom_f32<K, false, 1, LW>(bt, a.F + r.fac[i], a.chi32 + (size_t)r.tab[i] * NM, a.shf32,
+                                                    a.lat, lane, acc, rk, &as, &se, nullptr, lchi, &lw);
         if (lane == 0) {
             r.res[i] = v;
             if (r.res0) r.res0[i] = as;
             if (r.se0) r.se0[i] = se;
+            if (LW) r.lw[i] = lw;
         }
         for (int k = lane; k < W; k += CF_WARP) r.mom[i * W + k] = acc[1 + k];
         __syncwarp();  // the slot is reset by the next record
@@ -61,11 +57,25 @@ __global__ void __launch_bounds__(mom32_block<K>(), mom32_minb<K>()) lattice_mom
 }
 
 // the selection-list instantiation only where a list is given
+template <int K, int P>
+static void go_p(const RecSet& r, const IntegArgs& a, int blocks, int threads, cudaStream_t st)
+{
+    // exact E[log W] (r.lw) only without a selection list (the surrogate excludes it)
+    if (r.sel) lattice_mom_kernel_32<K, true, false, P><<<blocks, threads, 0, st>>>(r, a);
+    else if (r.lw) lattice_mom_kernel_32<K, false, true, P><<<blocks, threads, 0, st>>>(r, a);
+    else lattice_mom_kernel_32<K, false, false, P><<<blocks, threads, 0, st>>>(r, a);
+}
+
+// points in flight per lane: a.mom_p (1 or 2) with the coordinate table (K <= 4), else 1
 template <int K>
 static void go(const RecSet& r, const IntegArgs& a, int blocks, int threads, cudaStream_t st)
 {
-    if (r.sel) lattice_mom_kernel_32<K, true><<<blocks, threads, 0, st>>>(r, a);
-    else lattice_mom_kernel_32<K, false><<<blocks, threads, 0, st>>>(r, a);
+    if constexpr (K <= 4) {
+        if (a.mom_p == 1) go_p<K, 1>(r, a, blocks, threads, st);
+        else go_p<K, 2>(r, a, blocks, threads, st);
+    } else {
+        go_p<K, 1>(r, a, blocks, threads, st);
+    }
 }
 
 cudaError_t launch_mom32(int k, const RecSet& r, const IntegArgs& a, int blocks, cudaStream_t st)

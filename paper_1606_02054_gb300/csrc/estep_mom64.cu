@@ -23,13 +23,16 @@ __global__ void __launch_bounds__(256) lattice_mom_kernel_64(RecSet r, IntegArgs
         // the pass of alpha_s (chi table at dof k1 = dof - 2) weighted to dof k2 = r.dof
         const double k2 = r.dof[i];
         const double rk = isinf(k2) ? double(1) : (double)sqrt(k2 / (k2 - 2.0));
-        double as = 0.0, se = 0.0;
+        double as = 0.0, se = 0.0, lw = 0.0;
+        const double* lchi = r.lw ? a.lchi64 + (size_t)r.tab[i] * NM : nullptr;
         const double v = tk_lattice_mom_warp<double, K>(bt, a.F + r.fac[i], a.chi64 + (size_t)r.tab[i] * NM,
-                                                      a.shf64, a.lat, lane, acc, rk, &as, &se);
+                                                      a.shf64, a.lat, lane, acc, rk, &as, &se, lchi,
+                                                      r.lw ? &lw : nullptr);
         if (lane == 0) {
             r.res[i] = v;
             if (r.res0) r.res0[i] = as;
             if (r.se0) r.se0[i] = se;
+            if (r.lw) r.lw[i] = lw;
         }
         for (int k = lane; k < W; k += CF_WARP) r.mom[i * W + k] = acc[1 + k];
         __syncwarp();  // the slot is reset by the next record

@@ -178,7 +178,8 @@ __global__ void __launch_bounds__(128) combine_kernel(CombineArgs a)
         }
         PairOut o;
         if (a.single_pass && !a.density_only) {
-            pair_assemble_sp(F, a.Ly, p, q, c, d, logtp, alpha_s, a.LM.res[pid], a.LM.mom + pid * W, o);
+            pair_assemble_sp(F, a.Ly, p, q, c, d, logtp, alpha_s, a.LM.res[pid], a.LM.mom + pid * W, o,
+                             a.LM.lw ? a.LM.lw[pid] : NAN);
         } else {
             const double alpha = a.density_only ? 0.0 : a.L0.res[pid * m0 + 1];
             double tq1[CF_MAXQ], tq2[CF_MAXQ * CF_MAXQ];

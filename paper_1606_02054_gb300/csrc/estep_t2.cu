@@ -86,21 +86,27 @@ __global__ void __launch_bounds__(256) t2_records_group_kernel(RecSet r, IntegAr
     if (a.nodes && sub == 0 && nodes) atomicAdd(a.nodes, nodes);
 }
 
-// Lanes per FP32 T_2 record (finite dof); 32 = the warp-per-record kernel.  Measured at
-// p = 16, q = 2, g = 8, n = 2e6 (3.2e7 records, ~45 nodes each): 14.3 ms with 32 lanes,
-// 9.6 with 16, 7.9 with 8, 7.1 with 4, 6.8 with 2.
-#ifndef CF_T2_GROUP
-#define CF_T2_GROUP 2
-#endif
+// Lanes per FP32 T_2 record (finite dof), a.t2_group in {2, 4, 8, 16}; 32 (or 0: the CFUSN
+// model's records) = the warp-per-record kernel.  Measured at p = 16, q = 2, g = 8,
+// n = 2e6 (3.2e7 records, ~45 nodes each): 14.3 ms with 32 lanes, 9.6 with 16, 7.9 with 8,
+// 7.1 with 4, 6.8 with 2.
+template <int L>
+static void go_group(const RecSet& r, const IntegArgs& a, int blocks, cudaStream_t st)
+{
+    // the same warps, each on 32/L records at a time
+    const long long need = (r.nrec + 8LL * (CF_WARP / L) - 1) / (8LL * (CF_WARP / L));
+    const int gb = (int)(need < blocks ? need : blocks);
+    t2_records_group_kernel<L><<<gb > 0 ? gb : 1, 256, 0, st>>>(r, a);
+}
 
 cudaError_t launch_t2(const RecSet& r, const IntegArgs& a, int fp32, int blocks, cudaStream_t st)
 {
-    if (fp32 && a.t2_grouped && CF_T2_GROUP < CF_WARP) {
-        // the same warps, each on 32/L records at a time
-        const long long need = (r.nrec + 8LL * (CF_WARP / CF_T2_GROUP) - 1) / (8LL * (CF_WARP / CF_T2_GROUP));
-        const int gb = (int)(need < blocks ? need : blocks);
-        t2_records_group_kernel<CF_T2_GROUP><<<gb > 0 ? gb : 1, 256, 0, st>>>(r, a);
-    } else if (fp32) {
+    const int L = a.t2_group;
+    if (fp32 && L == 2) go_group<2>(r, a, blocks, st);
+    else if (fp32 && L == 4) go_group<4>(r, a, blocks, st);
+    else if (fp32 && L == 8) go_group<8>(r, a, blocks, st);
+    else if (fp32 && L == 16) go_group<16>(r, a, blocks, st);
+    else if (fp32) {
         t2_records_kernel<float><<<blocks, 256, 0, st>>>(r, a);
     } else {
         t2_records_kernel<double><<<blocks, 256, 0, st>>>(r, a);

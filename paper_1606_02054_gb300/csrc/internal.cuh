@@ -109,6 +109,8 @@ struct RecSet {
     double* se0;       //   results and standard error; may be null)
     const int* sel;    // lattice kernels (k >= 3): if set, only records sel[0 .. *nsel)
     const int* nsel;   //   (the learned surrogate's fallback list; device count)
+    double* lw;        // moment records, exact E[log W] only (else null): the f-weighted mean of
+                       // log(s^2) over the points of the pass (s the chi variate of alpha_s)
 };
 
 // Record index t of a set: every record, or (SEL: a kernel instantiated for
@@ -178,9 +180,15 @@ struct IntegArgs {
     // T_2 records only (may be null): quadrature nodes evaluated, added once per warp
     // (the profiler's algorithmic work count)
     unsigned long long* nodes;
-    // FP32 T_2 records of finite dof may share a warp (several records per warp, each on
-    // a group of lanes); 0: one warp per record (the CFUSN model's Phi_2 records)
-    int t2_grouped;
+    // lanes per FP32 T_2 record of finite dof: 2, 4, 8, 16 (32/L records share a warp) or
+    // 32 (a warp per record; always for the CFUSN model's Phi_2 records)
+    int t2_group;
+    // lattice points in flight per lane in the FP32 moment pass with the coordinate table
+    // (K <= 4): 1 or 2
+    int mom_p;
+    // exact E[log W] (else null): log(s^2) at every point of the chi tables, same layout
+    const double* lchi64;
+    const float* lchi32;
 };
 
 constexpr int T1TAB_N = 4096;
@@ -230,6 +238,7 @@ struct EstepArgs {
     int t2n;
     int density_only;
     int single_pass;
+    const double* lchi64;   // exact E[log W]: log(s^2) beside chi64 (else null)
     double* logf;           // g*n
     double* u;
     double* elogu;

@@ -169,7 +169,8 @@ __global__ void setup_components_kernel(Dims D, Layout Ly, const double* mu, con
 // all that the single-pass E-step reads).
 __global__ void chi_table_kernel(int ndof, int every, const double* __restrict__ dofs, const double* __restrict__ cst,
                                  Lattice lat, const double* __restrict__ shf, double rtol,
-                                 double* __restrict__ t64, float* __restrict__ t32)
+                                 double* __restrict__ t64, float* __restrict__ t32,
+                                 double* __restrict__ l64, float* __restrict__ l32)
 {
     const long long NM = (long long)lat.M * lat.N;
     const long long total = (long long)((ndof + every - 1) / every) * NM;
@@ -185,9 +186,15 @@ __global__ void chi_table_kernel(int ndof, int every, const double* __restrict__
         const double wc = fabs(2.0 * x - 1.0);
         const double w = 1.0 - wc;
         // dof = infinity (the normal limit): no chi variable, s = 1
-        const double s = isinf(dof) ? 1.0 : sqrt(cf_chi2_quantile(w, wc, dof, cst[k * CST_STRIDE + CST_LGA], rtol) / dof);
+        const double x2 = isinf(dof) ? 1.0 : cf_chi2_quantile(w, wc, dof, cst[k * CST_STRIDE + CST_LGA], rtol) / dof;
+        const double s = sqrt(x2);
         t64[t] = s;
         t32[t] = (float)s;
+        if (l64) {  // log(s^2) (exact E[log W])
+            const double ls = log(x2);
+            l64[t] = ls;
+            l32[t] = (float)ls;
+        }
     }
 }
 

@@ -708,8 +708,12 @@ __device__ double tk_lattice_warp(const double* bt, const double* Lc, const R* _
 template <typename R, int K>
 __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const R* __restrict__ chi,
                                       const R* __restrict__ shf, const Lattice& lat, int lane,
-                                      double* acc_sm, R rk, double* alpha_s, double* se)
+                                      double* acc_sm, R rk, double* alpha_s, double* se,
+                                      const R* __restrict__ lchi = nullptr, double* lw_out = nullptr)
 {
+    // lchi (exact E[log W], may be null): log(s^2) at every point; *lw_out receives the
+    // f-weighted mean of it over the points (all lanes)
+    double lw_acc = 0.0;
     // acc_sm: this warp's shared-memory slot of K + K(K+1)/2 + 3 + CF_MAXSHIFT doubles
     // that lane 0 uses for the running totals and the per-shift sums of f
     constexpr int K2 = K * (K + 1) / 2;
@@ -739,7 +743,7 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
             xs[d] = x0[d] + shf[m * CF_MAXDIM + d];
             if (xs[d] >= R(1)) xs[d] -= R(1);
         }
-        R af = R(0), aw = R(0), a1[K], a2[K2];
+        R af = R(0), aw = R(0), al = R(0), a1[K], a2[K2];
 #pragma unroll
         for (int r = 0; r < K; ++r) a1[r] = R(0);
 #pragma unroll
@@ -771,6 +775,7 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
             const R w1 = fs * rk, w2 = f * (rk * rk);
             af += f;
             aw += fs * s;
+            if (lchi) al += f * lchi[(size_t)m * N + i];
 #pragma unroll
             for (int r = 0; r < K; ++r) {
                 a1[r] += w1 * y[r];
@@ -786,6 +791,7 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
         }
         af = warp_sum(af);
         aw = warp_sum(aw);
+        if (lchi) lw_acc += (double)warp_sum(al);
 #pragma unroll
         for (int r = 0; r < K; ++r) a1[r] = warp_sum(a1[r]);
 #pragma unroll
@@ -800,6 +806,11 @@ __device__ double tk_lattice_mom_warp(const double* bt, const double* Lc, const 
         }
     }
     __syncwarp();
+    if (lw_out) {  // sum f over all shifts (every lane reads the per-shift sums)
+        double sf = 0.0;
+        for (int m = 0; m < M; ++m) sf += acc_sm[3 + K + K2 + m];
+        *lw_out = sf > 0.0 ? lw_acc / sf : NAN;
+    }
     const double Sf = acc_sm[0];
     const double inv = Sf > 0.0 ? 1.0 / Sf : 0.0;
     // m1 = L E[y/s], m2 = L E[y y^T / s^2] L^T in FP64 (Lc is the full lower
@@ -1048,12 +1059,15 @@ __device__ double tk_lattice_mom_tab_warp(const double* bt, const double* Lc, co
 // acc_sm is this warp's slot of K + K(K+1)/2 + 3 + CF_MAXSHIFT doubles; its tail holds
 // the per-shift sums as floats.
 // ---------------------------------------------------------------------------
-template <int K, bool TAB, int P>
+template <int K, bool TAB, int P, bool LW = false>
 __device__ double tk_lattice_mom_f32(const double* bt, const double* Lc, const float* __restrict__ chi,
                                      const float* __restrict__ shf, const Lattice& lat, int lane,
                                      double* acc_sm, float rk, double* alpha_s, double* se,
-                                     const float4* __restrict__ wtab)
+                                     const float4* __restrict__ wtab, const float* __restrict__ lchi = nullptr,
+                                     double* lw_out = nullptr)
 {
+    // LW (exact E[log W]): lchi holds log(s^2) at every point; *lw_out receives its
+    // f-weighted mean over the points
     static_assert(TAB || P == 1, "P > 1 needs the coordinate table");
     static_assert(!TAB || K <= 4, "the coordinate table holds 4 coordinates");
     constexpr int K2 = K * (K + 1) / 2;
@@ -1078,7 +1092,7 @@ __device__ double tk_lattice_mom_f32(const double* bt, const double* Lc, const f
             x0[d] = (float)(((long long)lane * lat.z[d]) % N) * invN;
         }
     }
-    float aw = 0.0f, a1[K], a2[K2];
+    float aw = 0.0f, al = 0.0f, a1[K], a2[K2];
 #pragma unroll
     for (int r = 0; r < K; ++r) a1[r] = 0.0f;
 #pragma unroll
@@ -1086,6 +1100,7 @@ __device__ double tk_lattice_mom_f32(const double* bt, const double* Lc, const f
     const float rk2 = rk * rk;
     for (int m = 0; m < M; ++m) {
         const float* __restrict__ crow = chi + (size_t)m * N;
+        const float* __restrict__ lrow = LW ? lchi + (size_t)m * N : nullptr;
         float af = 0.0f;
         float xs[K + 1];
         if constexpr (!TAB) {
@@ -1097,13 +1112,14 @@ __device__ double tk_lattice_mom_f32(const double* bt, const double* Lc, const f
         }
         const float4* __restrict__ wrow = TAB ? wtab + (size_t)m * N : nullptr;
         for (int i0 = lane; i0 < N; i0 += CF_WARP * P) {
-            float s[P], wc[P][4];
+            float s[P], wc[P][4], ls[P];
             bool ok[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) {
                 const int i = i0 + CF_WARP * p;
                 ok[p] = i < N;
                 s[p] = ok[p] ? crow[i] : 0.0f;
+                if constexpr (LW) ls[p] = ok[p] ? lrow[i] : 0.0f;
                 if constexpr (TAB) {
                     const float4 t = ok[p] ? wrow[i] : make_float4(0.f, 0.f, 0.f, 0.f);
                     wc[p][0] = t.x; wc[p][1] = t.y; wc[p][2] = t.z; wc[p][3] = t.w;
@@ -1139,6 +1155,7 @@ __device__ double tk_lattice_mom_f32(const double* bt, const double* Lc, const f
                 const float w1 = fs * rk, w2 = fp * rk2;
                 af += fp;
                 aw = fmaf(fs, s[p], aw);
+                if constexpr (LW) al = fmaf(fp, ls[p], al);
 #pragma unroll
                 for (int r = 0; r < K; ++r) {
                     a1[r] = fmaf(w1, y[p][r], a1[r]);
@@ -1159,6 +1176,7 @@ __device__ double tk_lattice_mom_f32(const double* bt, const double* Lc, const f
         if (lane == 0) fshift[m] = af;
     }
     aw = warp_sum(aw);
+    if constexpr (LW) al = warp_sum(al);
 #pragma unroll
     for (int r = 0; r < K; ++r) a1[r] = warp_sum(a1[r]);
 #pragma unroll
@@ -1169,6 +1187,10 @@ __device__ double tk_lattice_mom_f32(const double* bt, const double* Lc, const f
     float sm0 = lane < M ? fshift[lane] * invN : 0.0f;
     float sm1 = lane + CF_WARP < M ? fshift[lane + CF_WARP] * invN : 0.0f;
     const float mean = warp_sum(sm0 + sm1) / (float)M;
+    if constexpr (LW) {  // sum f = mean x N x M
+        const float sf = mean * (float)N * (float)M;
+        *lw_out = sf > 0.0f ? (double)(al / sf) : NAN;
+    }
     const float d0 = lane < M ? sm0 - mean : 0.0f, d1 = lane + CF_WARP < M ? sm1 - mean : 0.0f;
     const float ss = warp_sum(d0 * d0 + d1 * d1);
     // the moments: m1 = L a1 / aw, m2 = L A L^T / aw (A the symmetric matrix of a2), on every
