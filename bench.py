@@ -115,6 +115,11 @@ class Clocks:
             self.t.start()
         except OSError:
             self.proc = None
+            return
+        # the sampler's start-up (driver queries) stays out of the timed region
+        t0 = time.time()
+        while not self.lines and self.proc.poll() is None and time.time() - t0 < 5.0:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -263,7 +268,7 @@ def measure(cf, torch, w, form, y_dev, flush, stream, steps, warmup, with_clocks
     if shard is not None:
         shard.barrier()
     torch.cuda.synchronize()
-    total_ms, lls = 0.0, []
+    total_ms, lls, each = 0.0, [], []
     for _ in range(steps):
         flush.fill_(1.0)  # evict L2 before each timed step
         e0 = torch.cuda.Event(enable_timing=True)
@@ -272,7 +277,8 @@ def measure(cf, torch, w, form, y_dev, flush, stream, steps, warmup, with_clocks
         lls.append(step())
         e1.record(stream)
         e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
+        each.append(e0.elapsed_time(e1))
+        total_ms += each[-1]
     torch.cuda.synchronize()
     if shard is not None:
         shard.barrier()
@@ -283,7 +289,9 @@ def measure(cf, torch, w, form, y_dev, flush, stream, steps, warmup, with_clocks
     prof = cf.cfust_profile(ctx)
     work = cf.cfust_profile_work(ctx)
     estep_ms = sum(v[0] for k, v in prof.items() if k != "mstep") / steps
-    return dict(ms=ms, estep_ms=estep_ms, prof=prof, work=work, ll=lls[-1], clk=clk,
+    each.sort()
+    spread = {"min": each[0], "median": each[len(each) // 2], "max": each[-1]}
+    return dict(ms=ms, estep_ms=estep_ms, prof=prof, work=work, ll=lls[-1], clk=clk, spread=spread,
                 launches=cf.cfust_launch_count(ctx) - n0, ctx=ctx, tuned=tuned)
 
 
@@ -325,7 +333,7 @@ def roofline(w, run, rates):
 def form_summary(w, run, pairs, world):
     return {"value": pairs / (run["ms"] / 1e3), "unit": UNIT, "ms_per_step": run["ms"],
             "steps": run["steps"], "warmup": run["warmup"], "launch_shapes": run["tuned"],
-            "em_iter_per_s": 1e3 / run["ms"],
+            "em_iter_per_s": 1e3 / run["ms"], "step_ms_spread": run["spread"],
             "estep_obs_comp_per_s": pairs / (run["estep_ms"] / 1e3),
             "loglik_last": run["ll"], "gpu_launches": int(run["launches"]),
             "kernel_ms_per_step": {k: v[0] / max(1, run["steps"]) for k, v in run["prof"].items()}}
@@ -649,7 +657,7 @@ def main():
                            "l2": "flushed (256 MB write) before every timed step; inputs > L2",
                            "parallelism": (f"rows sharded over {world} ranks, one all-gather of the "
                                            f"segment statistics per iteration" if world > 1 else "1 GPU")},
-                "em_iter_per_s": 1e3 / ms,
+                "em_iter_per_s": 1e3 / ms, "step_ms_spread": ch["step_ms_spread"],
                 "estep_obs_comp_per_s": ch["estep_obs_comp_per_s"],
                 "loglik_last": ch["loglik_last"],
                 "gpu_launches": ch["gpu_launches"],

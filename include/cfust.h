@@ -107,6 +107,13 @@ typedef struct {
                             lattice pass of alpha_s sample with weight f, so E[log W | y] is
                             the f-weighted mean of log W over them (needs moments = 1,
                             q >= 3, the CFUST model; not with the learned surrogate) */
+    int tensor_stats;    /* CFUST_PREC_MIXED: 1: the cross statistics Srr = sum tau u r r^T,
+                            Sre = sum tau r e2^T and Sr = sum tau u r of eqs (18)-(21) as one
+                            tcgen05 tensor-core contraction per block of observations (TF32
+                            hi/lo split, FP32 accumulation per block, FP64 across blocks)
+                            where g p <= 128 and g (p + q + 1) <= 256; 0 (default):
+                            compensated FP32 sums on the CUDA cores.  Ignored by the other
+                            precisions. */
 } cfust_opts;
 
 #define CFUST_ELOGW_OSL 0
@@ -267,9 +274,11 @@ cfust_status cfust_kmeans(cfust_ctx* ctx, int nstarts, uint64_t seed, int max_it
  *     per lane (ms[5..6]; -1 where not applicable);
  * and keeps the fastest (choices[0]: lanes per T_2 record, choices[1]: points per
  * lane; 0 where not applicable).  The choice holds for this context and, for the rest
- * of the process, for every context (one not tuned itself) whose records fall in the
- * same (kernel, dimension, precision, floor(log2 records)) bucket, from its next
- * E-step on (a fit graph of cfust_fit_batch keeps the shapes it was captured with).  Leaves no E-step
+ * of the process, for every context (one not tuned itself) with records of the same
+ * (kernel, dimension, precision), from its next E-step on (a fit graph of
+ * cfust_fit_batch keeps the shapes it was captured with).  The lanes per T_2 record
+ * decide the order in which a record's nodes are added, so the choice is one per shape,
+ * not per problem size: the shards of one problem stay bitwise equal to it.  Leaves no E-step
  * results (run cfust_estep before cfust_mstep).  Without tuning the shapes are 2 lanes
  * per T_2 record and 2 points per lane.  choices (2) and ms (7) may be NULL. */
 cfust_status cfust_autotune(cfust_ctx* ctx, int reps, int* choices, double* ms);

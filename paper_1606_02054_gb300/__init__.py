@@ -54,7 +54,7 @@ class cfust_opts(C.Structure):
                 ("qmc_korobov_a", C.c_int), ("seed", C.c_uint64), ("nu_min", C.c_double),
                 ("nu_max", C.c_double), ("device", C.c_int), ("cuda_stream", C.c_void_p),
                 ("t2_nodes", C.c_int), ("profile", C.c_int), ("moments", C.c_int),
-                ("hold", C.c_int), ("model", C.c_int), ("elogw", C.c_int)]
+                ("hold", C.c_int), ("model", C.c_int), ("elogw", C.c_int), ("tensor_stats", C.c_int)]
 
 
 class cfust_rates(C.Structure):

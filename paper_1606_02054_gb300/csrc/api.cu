@@ -21,7 +21,7 @@ __global__ void setup_components_kernel(Dims, Layout, const double*, const doubl
 __global__ void chi_table_kernel(int, int, const double*, const double*, Lattice, const double*, double, double*,
                                  float*, double*, float*);
 __global__ void dof_consts_kernel(Dims, Layout, const double*, int, double*, double*, float*);
-__global__ void t1_table_kernel(int, const double*, float2*);
+__global__ void t1_table_kernel(int, const double*, float2*, int);
 __global__ void widen_kernel(const float*, long long, Dims, double*);
 __global__ void narrow_kernel(const double*, Dims, float*);
 
@@ -64,6 +64,8 @@ struct cfust_ctx {
     double *glx64 = nullptr, *glw64 = nullptr;
     float *glx32 = nullptr, *glw32 = nullptr;
     float *glx32h = nullptr, *glw32h = nullptr;  // T2_NH nodes for graded T_2 pieces
+    float *glx32l = nullptr, *glw32l = nullptr;  // t2n_lo nodes for smooth FP32 T_2 pieces
+    int t2n_lo = 0;
     double *logf = nullptr, *u = nullptr, *elogu = nullptr, *eu = nullptr, *euu = nullptr,
            *se = nullptr, *tau = nullptr;
     double *partial = nullptr, *stats = nullptr;
@@ -77,6 +79,7 @@ struct cfust_ctx {
     float2* t1tab = nullptr;  // FP32 T_2: per-dof tables of T_1 at dof + 1
     // mixed precision: FP32 copies of the observations and factor blocks
     bool mixed = false;
+    bool tc_stats = false;  // mixed form: cross statistics on the tensor cores (reduce_tc.cu)
     float* y32 = nullptr;
     float* F32 = nullptr;
     // E-step pipeline: per-pair (d, log t_p) and c, integral records per level
@@ -206,6 +209,7 @@ static cfust_status check_flags(cfust_ctx* c, int f, const char* where)
     if (f & (KF_NOTPD_OMEGA | KF_NOTPD_LAMBDA))
         return fail(c, CFUST_ENOTPD, std::string(where) + ": Sigma, Omega or Lambda not positive definite");
     if (f & KF_NAN) return fail(c, CFUST_ENAN, std::string(where) + ": non-finite density or statistic");
+    if (f & KF_TIMEOUT) return fail(c, CFUST_ETIMEOUT, std::string(where) + ": a bounded device wait gave up");
     return CFUST_OK;
 }
 
@@ -278,6 +282,7 @@ extern "C" void cfust_default_opts(cfust_opts* o)
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
     o->precision = CFUST_PREC_FP64;
+    o->tensor_stats = 0;
     o->qmc_points = 1024;
     o->qmc_shifts = 8;
     o->qmc_korobov_a = 119;
@@ -353,7 +358,8 @@ static void free_all(cfust_ctx* c)
     sur_free(c->sur);
     void* bufs[] = {c->y, c->pi, c->mu, c->Sigma, c->Delta, c->nu, c->pi_n, c->mu_n, c->Sigma_n,
                     c->Delta_n, c->nu_n, c->F, c->dofs, c->cst64, c->cst32, c->chi64, c->chi32, c->shf64, c->shf32, c->wtab,
-                    c->glx64, c->glw64, c->glx32, c->glw32, c->glx32h, c->glw32h, c->logf, c->u, c->elogu, c->eu,
+                    c->glx64, c->glw64, c->glx32, c->glw32, c->glx32h, c->glw32h, c->glx32l, c->glw32l,
+                    c->logf, c->u, c->elogu, c->eu,
                     c->euu, c->se, c->tau, c->partial, c->stats, c->flags, c->comp_status,
                     c->stage32, c->pd, c->pc, c->fix_count, c->fix_list, c->y32, c->F32, c->t1tab,
                     c->work_dev, c->seg, c->lchi64, c->lchi32};
@@ -418,6 +424,8 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
         return fail(nullptr, CFUST_EINVAL, "cfust_create: hold must combine CFUST_HOLD_DELTA and CFUST_HOLD_NU");
     if (o.model != CFUST_MODEL_CFUST && o.model != CFUST_MODEL_CFUSN)
         return fail(nullptr, CFUST_EINVAL, "cfust_create: model must be CFUST_MODEL_CFUST or CFUST_MODEL_CFUSN");
+    if (o.tensor_stats != 0 && o.tensor_stats != 1)
+        return fail(nullptr, CFUST_EINVAL, "cfust_create: tensor_stats must be 0 or 1");
     if (o.elogw != CFUST_ELOGW_OSL && o.elogw != CFUST_ELOGW_EXACT)
         return fail(nullptr, CFUST_EINVAL, "cfust_create: elogw must be CFUST_ELOGW_OSL or CFUST_ELOGW_EXACT");
     if (o.elogw == CFUST_ELOGW_EXACT && (o.moments != 1 || q < 3 || o.model != CFUST_MODEL_CFUST))
@@ -444,8 +452,12 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
         }
     }
     c->mixed = o.precision == CFUST_PREC_MIXED;
+    c->tc_stats = c->mixed && o.tensor_stats && reduce_tc_fits(p, q, g);
     // a warp evaluates 32 nodes at a time: fewer than 32 per piece saves nothing
     c->t2n = o.t2_nodes ? o.t2_nodes : (o.precision == CFUST_PREC_FP64 ? 64 : 32);
+    // FP32 modes by default: T2_LO nodes where the integrand is smooth enough (a node count set
+    // in the options holds for every piece)
+    c->t2n_lo = (o.precision != CFUST_PREC_FP64 && o.t2_nodes == 0) ? T2_LO : 0;
     cudaDeviceProp prop;
     if ((e = cudaGetDeviceProperties(&prop, o.device)) != cudaSuccess) {
         cfust_status s = fail(nullptr, CFUST_ECUDA, std::string("cfust_create: ") + cudaGetErrorString(e));
@@ -493,6 +505,7 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     ALLOC(shf32, (size_t)o.qmc_shifts * CF_MAXDIM);
     ALLOC(glx64, c->t2n); ALLOC(glw64, c->t2n); ALLOC(glx32, c->t2n); ALLOC(glw32, c->t2n);
     ALLOC(glx32h, T2_NH); ALLOC(glw32h, T2_NH);
+    ALLOC(glx32l, T2_LO); ALLOC(glw32l, T2_LO);
     ALLOC(logf, ng); ALLOC(u, ng); ALLOC(elogu, ng); ALLOC(se, ng); ALLOC(tau, ng);
     ALLOC(eu, ng * q); ALLOC(euu, ng * q * q);
     ALLOC(partial, part);
@@ -552,6 +565,9 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     std::vector<double> gxh, gwh;
     gauss_legendre01(T2_NH, gxh, gwh);
     std::vector<float> gxh32(gxh.begin(), gxh.end()), gwh32(gwh.begin(), gwh.end());
+    std::vector<double> gxl, gwl;
+    gauss_legendre01(T2_LO, gxl, gwl);
+    std::vector<float> gxl32(gxl.begin(), gxl.end()), gwl32(gwl.begin(), gwl.end());
     cfust_status s = CFUST_OK;
     auto cp = [&](void* dst, const void* src, size_t bytes) {
         cudaError_t ee = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
@@ -585,6 +601,8 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     cp(c->glw32, gw32.data(), sizeof(float) * gw32.size());
     cp(c->glx32h, gxh32.data(), sizeof(float) * gxh32.size());
     cp(c->glw32h, gwh32.data(), sizeof(float) * gwh32.size());
+    cp(c->glx32l, gxl32.data(), sizeof(float) * gxl32.size());
+    cp(c->glw32l, gwl32.data(), sizeof(float) * gwl32.size());
     if (s != CFUST_OK) {
         free_all(c);
         delete c;
@@ -711,8 +729,17 @@ static cfust_status launch_setup(cfust_ctx* c)
     dof_consts_kernel<<<1, 64, 0, c->st>>>(c->D, c->Ly, c->F, 3 * c->g, c->dofs, c->cst64, c->cst32);
     LAUNCHED();
     if (c->t1tab) {
+        // tables t = 3h + j hold T_1 at dof nu_h + p + j + 1: the FP32 T_2 records read those of
+        // their own dof, the q = 2 level-1 T_1 records (dof nu + p + 1) the j = 0 table
+        int jmask = 0;
+        for (int l = 0; l < 3; ++l) {
+            const RecSet& r = c->rec[l];
+            if (r.nrec == 0) continue;
+            if (r.k == 2) jmask |= l == 0 ? 5 : l == 1 ? 2 : 1;  // dofs nu+p (+2), nu+p+1, nu+p
+            if (r.k == 1 && l == 1) jmask |= 1;
+        }
         const int total = 3 * c->g * T1TAB_N;
-        t1_table_kernel<<<(total + 255) / 256, 256, 0, c->st>>>(3 * c->g, c->dofs, c->t1tab);
+        t1_table_kernel<<<(total + 255) / 256, 256, 0, c->st>>>(3 * c->g, c->dofs, c->t1tab, jmask);
         LAUNCHED();
     }
     if (c->mixed) {
@@ -746,6 +773,7 @@ static IntegArgs integ_args(const cfust_ctx* c)
     ia.glx64 = c->glx64; ia.glw64 = c->glw64; ia.glx32 = c->glx32; ia.glw32 = c->glw32;
     ia.t2n = c->t2n;
     ia.glx32h = c->glx32h; ia.glw32h = c->glw32h;
+    ia.t2n_lo = c->t2n_lo; ia.glx32l = c->glx32l; ia.glw32l = c->glw32l;
     ia.t1tab = c->t1tab;
     ia.wtab = c->wtab;
     ia.nodes = nullptr;
@@ -844,7 +872,8 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
     }
     if (fp32) CU(cudaMemsetAsync(c->fix_count, 0, sizeof(int), c->st));
     CombineArgs ca;
-    ca.D = c->D; ca.Ly = c->Ly; ca.cst64 = c->cst64; ca.F = c->F; ca.pd = c->pd; ca.pc = c->pc;
+    ca.D = c->D; ca.Ly = c->Ly; ca.cst64 = c->cst64; ca.cst32 = c->cst32; ca.F = c->F; ca.pd = c->pd; ca.pc = c->pc;
+    ca.F32 = c->mixed ? c->F32 : nullptr;
     ca.L0 = pa.L0; ca.L1 = c->rec[1]; ca.L2 = c->rec[2]; ca.LM = c->rec[3];
     ca.density_only = density_only; ca.single_pass = sp; ca.fp32 = fp32;
     ca.mixed = c->mixed ? 1 : 0;
@@ -891,18 +920,24 @@ static cfust_status enqueue_estep_segments(cfust_ctx* c, double* seg, long long 
     r.elogu = c->elogu; r.eu = c->eu; r.euu = c->euu; r.tau = c->tau; r.partial = c->partial;
     r.chunk = c->chunk; r.row = c->row;
     r.y32 = c->y32;
+    r.small_only = c->tc_stats ? 1 : 0;
     const size_t smem = (c->mixed ? sizeof(float) : sizeof(double)) * ((size_t)c->chunk * c->row + (size_t)c->g * c->chunk) +
                         sizeof(double) * ((size_t)c->chunk + CF_MAXG);
     prof_begin(c, CFUST_PROF_REDUCE);
     if (c->mixed) estep_reduce_kernel_f32<<<c->nblocks_red, 256, smem, c->st>>>(r);
     else estep_reduce_kernel<<<c->nblocks_red, 256, smem, c->st>>>(r);
     LAUNCHED();
+    if (c->tc_stats) {  // Sr, Sre, Srr of the same blocks (reads the tau just written)
+        cudaError_t e = launch_reduce_tc(r, c->flags, c->nsm, c->st);
+        if (e != cudaSuccess) return fail(c, CFUST_ECUDA, std::string("tensor-core statistics: ") + cudaGetErrorString(e));
+        c->launches++;
+    }
     const int width = c->g * stats_per_comp(c->p, c->q) + 1;
     const long long tot = nseg_out * width;
     segment_partials_kernel<<<(int)std::min<long long>((tot + 255) / 256, 8LL * c->nsm), 256, 0, c->st>>>(
         c->partial, c->nblocks_red, SEG_BLOCKS, width, seg, nseg_out);
     LAUNCHED();
-    prof_end(c, CFUST_PROF_REDUCE, 2);
+    prof_end(c, CFUST_PROF_REDUCE, c->tc_stats ? 3 : 2);
     return CFUST_OK;
 }
 
@@ -1101,20 +1136,16 @@ extern "C" cfust_status cfust_fit(cfust_ctx* c, int max_iter, double tol, int* i
 
 // ---------------------------------------------------------------------------
 // Autotuner of the integrators' launch shapes.  Choices are kept per (kernel, record
-// dimension, precision, record-count bucket = floor(log2 records)) for the process, so
-// every context of a bucket that is created after a tuning run uses them (a CUDA graph
-// captures the shape in force when it is built).
+// dimension, precision) for the process, and every context of that shape without a tuning
+// of its own uses them from its next E-step on (a CUDA graph keeps the shape in force when
+// it was built).  The lanes per T_2 record set the order in which a record's nodes are
+// added, so one choice per shape -- not per problem size -- keeps the shards of one
+// problem (which differ in size) bitwise equal to the whole problem.
 // ---------------------------------------------------------------------------
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, int> g_tune;  // (kind, k, precision, bucket) -> choice
+std::map<std::tuple<int, int, int>, int> g_tune;  // (kind, k, precision) -> choice
 enum { TUNE_T2 = 0, TUNE_MOM = 1 };
-int bucket_of(long long nrec)
-{
-    int b = 0;
-    while (nrec > 1) { nrec >>= 1; ++b; }
-    return b;
-}
 // the level of the context's T_2 records (FP32, finite dof), or -1
 int t2_level(const cfust_ctx* c)
 {
@@ -1137,11 +1168,11 @@ void tune_lookup(const cfust_ctx* c, int* t2_group, int* mom_p)
     std::lock_guard<std::mutex> lk(g_tune_mu);
     const int l = t2_level(c);
     if (!c->tune_t2_group && l >= 0) {
-        auto it = g_tune.find({TUNE_T2, 2, c->opts.precision, bucket_of(c->rec[l].nrec)});
+        auto it = g_tune.find({TUNE_T2, 2, c->opts.precision});
         if (it != g_tune.end()) *t2_group = it->second;
     }
     if (!c->tune_mom_p && mom_tunable(c)) {
-        auto it = g_tune.find({TUNE_MOM, c->q, c->opts.precision, bucket_of(c->rec[3].nrec)});
+        auto it = g_tune.find({TUNE_MOM, c->q, c->opts.precision});
         if (it != g_tune.end()) *mom_p = it->second;
     }
 }
@@ -1212,8 +1243,8 @@ extern "C" cfust_status cfust_autotune(cfust_ctx* c, int reps, int* choices, dou
     if (e != cudaSuccess) return fail(c, CFUST_ECUDA, std::string("cfust_autotune: ") + cudaGetErrorString(e));
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        if (l >= 0) g_tune[{TUNE_T2, 2, c->opts.precision, bucket_of(c->rec[l].nrec)}] = c->tune_t2_group;
-        if (mom_tunable(c)) g_tune[{TUNE_MOM, c->q, c->opts.precision, bucket_of(c->rec[3].nrec)}] = c->tune_mom_p;
+        if (l >= 0) g_tune[{TUNE_T2, 2, c->opts.precision}] = c->tune_t2_group;
+        if (mom_tunable(c)) g_tune[{TUNE_MOM, c->q, c->opts.precision}] = c->tune_mom_p;
     }
     c->launches += dummy;
     c->have_stats = false;  // the timing runs overwrote the integral records
@@ -1859,7 +1890,7 @@ extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const doub
         }
         if (use_t1tab) {
             const int total = count * T1TAB_N;
-            t1_table_kernel<<<(total + 255) / 256, 256, 0, c->st>>>(count, r.dof, t1t);
+            t1_table_kernel<<<(total + 255) / 256, 256, 0, c->st>>>(count, r.dof, t1t, 7);
             c->launches++;
             if ((e = cudaGetLastError())) break;
         }

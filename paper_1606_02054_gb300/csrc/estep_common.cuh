@@ -273,26 +273,29 @@ __device__ inline void pair_assemble_sp(const double* F, const Layout& Ly, int p
 
 // Mixed precision: the assembly of pair_assemble in FP32 (log f keeps the
 // FP64 log t_p and adds log alpha_s computed in FP32).
-__device__ inline void pair_assemble_f32(const double* F, const Layout& Ly, int p, int q,
+// F: the component's FP32 factor block, cst its FP32 per-dof constants (conversions from
+// FP64 run on GB300's FP64 pipe, 1/64 of the FP32 rate: the per-component values are read
+// from their FP32 copies).
+__device__ inline void pair_assemble_f32(const float* F, const Layout& Ly, int p, int q,
                                          const double* cd, double dd, double logtp, double alpha_s_d,
                                          double alpha_d, const double* tq1, const double* tq2,
-                                         int density_only, const double* cst, PairOut& o)
+                                         int density_only, const float* cst, PairOut& o)
 {
     const float alpha_s = (float)alpha_s_d;
     if (!(alpha_s > 0.0f)) return pair_null(q, density_only, o);
     o.logf = q * 0.6931471805599453 + logtp + (double)logf(alpha_s);  // eq (4)
     if (density_only) return;
-    const float nu = (float)F[Ly.scal + SC_NU], nu1 = nu + (float)p, d = (float)dd;
+    const float nu = F[Ly.scal + SC_NU], nu1 = nu + (float)p, d = (float)dd;
     float c[CF_MAXQ];
     for (int k = 0; k < q; ++k) c[k] = (float)cd[k];
     const bool nrm = isinf(nu);  // the normal limit (eq 5): u = 1, every t scaling is 1
     const float u = nrm ? 1.0f : nu1 / (nu + d) * (float)alpha_d / alpha_s;  // eq (13)
     o.u = u;
-    o.elogu = nrm ? 0.0f : u - logf(0.5f * (nu + d)) - nu1 / (nu + d) + (float)F[Ly.scal + SC_PSI];  // eq (15)
+    o.elogu = nrm ? 0.0f : u - logf(0.5f * (nu + d)) - nu1 / (nu + d) + F[Ly.scal + SC_PSI];  // eq (15)
     float Lam[CF_MAXQ * CF_MAXQ];
-    for (int i = 0; i < q * q; ++i) Lam[i] = (float)F[Ly.Lam + i];
+    for (int i = 0; i < q * q; ++i) Lam[i] = F[Ly.Lam + i];
     const float k0 = nrm ? 1.0f : (nu + d) / nu1;
-    const float lt1 = (float)cst[CST_LT1], lt1m = (float)cst[CST_LT1M];
+    const float lt1 = cst[CST_LT1], lt1m = cst[CST_LT1M];
     const int q1 = q - 1;
     float xi[CF_MAXQ], H[CF_MAXQ * CF_MAXQ];
     for (int i = 0; i < q * q; ++i) H[i] = 0.0f;
@@ -303,10 +306,10 @@ __device__ inline void pair_assemble_f32(const double* F, const Layout& Ly, int 
                          : lt1 - 0.5f * logf(Srr) - 0.5f * (nu1 + 1.0f) * log1pf(c[r] * c[r] / (nu1 * Srr))) * t1q;
         H[r * q + r] = c[r] * xi[r];
         if (q1 == 0 || xi[r] == 0.0f) continue;
-        const double* blk = F + Ly.l1 + r * Ly.l1s;
+        const float* blk = F + Ly.l1 + r * Ly.l1s;
         float mvec[CF_MAXQ], sch[CF_MAXQ * CF_MAXQ], cp[CF_MAXQ];
-        for (int i = 0; i < q1; ++i) mvec[i] = (float)blk[i];
-        for (int i = 0; i < q1 * q1; ++i) sch[i] = (float)blk[q1 + i];
+        for (int i = 0; i < q1; ++i) mvec[i] = blk[i];
+        for (int i = 0; i < q1 * q1; ++i) sch[i] = blk[q1 + i];
         for (int i = 0; i < q1; ++i) {
             const int b = i < r ? i : i + 1;
             cp[i] = c[b] - mvec[i] * c[r];

@@ -90,6 +90,18 @@ __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, long long
     }
 }
 
+// Mixed form: FP32 pairs in a kernel of their own, so the FP64 path's registers do not
+// limit its occupancy (one kernel for both took 118 registers, 24 % warps active).
+__global__ void __launch_bounds__(128) plan_kernel_f32(PlanArgs a)
+{
+    const long long np = a.D.n * a.D.g;
+    for (long long pid = blockIdx.x * (long long)blockDim.x + threadIdx.x; pid < np;
+         pid += (long long)gridDim.x * blockDim.x) {
+        const int h = (int)(pid / a.D.n);
+        plan_pair_f32(a, pid, h, pid - (long long)h * a.D.n);
+    }
+}
+
 __global__ void __launch_bounds__(128) plan_kernel(PlanArgs a)
 {
     const int p = a.D.p, q = a.D.q;
@@ -99,10 +111,6 @@ __global__ void __launch_bounds__(128) plan_kernel(PlanArgs a)
          pid += (long long)gridDim.x * blockDim.x) {
         const int h = (int)(pid / a.D.n);
         const long long j = pid - (long long)h * a.D.n;
-        if (a.F32) {
-            plan_pair_f32(a, pid, h, j);
-            continue;
-        }
         const double* F = a.F + (size_t)h * a.Ly.stride;
         const int foff = h * a.Ly.stride;
         const double nu1 = F[a.Ly.scal + SC_NU] + p;
@@ -154,6 +162,8 @@ __global__ void __launch_bounds__(128) plan_kernel(PlanArgs a)
     }
 }
 
+// MIXED: the FP32 assembly of the mixed form (its own instantiation, for its registers)
+template <bool MIXED>
 __global__ void __launch_bounds__(128) combine_kernel(CombineArgs a)
 {
     const int p = a.D.p, q = a.D.q;
@@ -188,9 +198,9 @@ __global__ void __launch_bounds__(128) combine_kernel(CombineArgs a)
                 if (q1 > 1)
                     for (int i = 0; i < q * q1; ++i) tq2[i] = a.L2.res[pid * q * q1 + i];
             }
-            if (a.mixed)
-                pair_assemble_f32(F, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1, tq2, a.density_only,
-                                  a.cst64 + (size_t)(3 * h) * CST_STRIDE, o);
+            if constexpr (MIXED)
+                pair_assemble_f32(a.F32 + (size_t)h * a.Ly.stride, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1,
+                                  tq2, a.density_only, a.cst32 + (size_t)(3 * h) * CST_STRIDE, o);
             else
                 pair_assemble(F, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1, tq2, a.density_only,
                               a.cst64 + (size_t)(3 * h) * CST_STRIDE, o);
@@ -206,6 +216,9 @@ __global__ void __launch_bounds__(128) combine_kernel(CombineArgs a)
     }
 }
 
+// FP32 with the T_1 tables (a.t1tab) and a record of table index 3h + 1 (dof nu + p + 1,
+// the q = 2 moments' level 1): T_1 by interpolation in the table 3h, which holds T_1 at
+// that dof (see t1cdf_table), instead of the continued fraction.
 template <typename R>
 __global__ void __launch_bounds__(128) t1_records_kernel(RecSet r, IntegArgs a)
 {
@@ -213,8 +226,12 @@ __global__ void __launch_bounds__(128) t1_records_kernel(RecSet r, IntegArgs a)
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < r.nrec;
          i += (long long)gridDim.x * blockDim.x) {
         const R dof = (R)r.dof[i];  // infinite: the normal limit, Phi
-        r.res[i] = isinf(dof) ? (double)m_ncdf((R)r.bt[i])
-                              : (double)t1cdf_dev<R>((R)r.bt[i], dof, cst[r.tab[i] * CST_STRIDE + CST_LGB]);
+        const int tab = r.tab[i];
+        if (sizeof(R) == sizeof(float) && a.t1tab && tab % 3 == 1 && !isinf(dof))
+            r.res[i] = (double)t1cdf_table((float)r.bt[i], a.t1tab + (size_t)(tab - 1) * T1TAB_N);
+        else
+            r.res[i] = isinf(dof) ? (double)m_ncdf((R)r.bt[i])
+                                  : (double)t1cdf_dev<R>((R)r.bt[i], dof, cst[tab * CST_STRIDE + CST_LGB]);
         if (r.se) r.se[i] = 0.0;
     }
 }
@@ -229,7 +246,8 @@ static int grid_for(long long work, int threads, int cap)
 cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st, long long* launches)
 {
     const long long np = a.D.n * a.D.g;
-    plan_kernel<<<grid_for(np, 128, 1 << 20), 128, 0, st>>>(a);
+    if (a.F32) plan_kernel_f32<<<grid_for(np, 128, 1 << 20), 128, 0, st>>>(a);
+    else plan_kernel<<<grid_for(np, 128, 1 << 20), 128, 0, st>>>(a);
     ++*launches;
     return cudaGetLastError();
 }
@@ -237,7 +255,8 @@ cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st, long long* launches)
 cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st, long long* launches)
 {
     const long long np = a.D.n * a.D.g;
-    combine_kernel<<<grid_for(np, 128, 1 << 20), 128, 0, st>>>(a);
+    if (a.mixed) combine_kernel<true><<<grid_for(np, 128, 1 << 20), 128, 0, st>>>(a);
+    else combine_kernel<false><<<grid_for(np, 128, 1 << 20), 128, 0, st>>>(a);
     ++*launches;
     return cudaGetLastError();
 }

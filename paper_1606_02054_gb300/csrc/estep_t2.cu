@@ -33,7 +33,8 @@ __global__ void __launch_bounds__(256) t2_records_kernel(RecSet r, IntegArgs a)
                                    : t2cdf_warp<R>(h, k, rho, nu, omr2, cr, c[CST_LGB], c[CST_LGB1], c[CST_C2], a.t2n,
                                        glx, glw, f32 ? T2_NH : a.t2n,
                                        f32 ? (const R*)a.glx32h : glx, f32 ? (const R*)a.glw32h : glw,
-                                       lane, tab, &nn);
+                                       lane, tab, &nn, f32 ? a.t2n_lo : 0, f32 ? (const R*)a.glx32l : nullptr,
+                                       f32 ? (const R*)a.glw32l : nullptr);
         nodes += (unsigned long long)nn;
         if (lane == 0) {
             r.res[i] = v;
@@ -74,7 +75,8 @@ __global__ void __launch_bounds__(256) t2_records_group_kernel(RecSet r, IntegAr
         const float2* tab = a.t1tab ? a.t1tab + (size_t)r.tab[i] * T1TAB_N : nullptr;
         int nn = 0;
         const double v = t2cdf_group_f32<L>(h, k, rho, nu, omr2, cr, c[CST_LGB], c[CST_LGB1], c[CST_C2], a.t2n,
-                                            a.glx32, a.glw32, T2_NH, a.glx32h, a.glw32h, sub, tab, &nn);
+                                            a.glx32, a.glw32, T2_NH, a.glx32h, a.glw32h, sub, tab, &nn,
+                                            a.t2n_lo, a.glx32l, a.glw32l);
         if (own) {
             nodes += (unsigned long long)nn;
             if (sub == 0) {

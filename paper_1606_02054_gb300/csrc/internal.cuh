@@ -74,6 +74,7 @@ enum {
     KF_EMPTY = 1 << 4,
     KF_NUROOT = 1 << 5,
     KF_NAN = 1 << 6,
+    KF_TIMEOUT = 1 << 7,  // a bounded device wait gave up
 };
 
 // Number of statistics per component (see cfust_get_stats).
@@ -169,6 +170,10 @@ struct IntegArgs {
     // nodes of the graded T_2 pieces (|rho| > 0.99): T2_NH per piece
     const float* glx32h;
     const float* glw32h;
+    // FP32: t2n_lo nodes per piece where 4 <= dof <= 64 and |rho| < 0.9 (T2_LO_* below)
+    int t2n_lo;
+    const float* glx32l;
+    const float* glw32l;
     // FP32 T_2: per tab, log2 T_1(-|z|; dof + 1) on the grid of T1TAB_N points
     // uniform in v = asinh(|z|)/ln 2 over [0, T1TAB_V], with d/dv (float2 each);
     // NULL: the continued fraction is used instead
@@ -193,13 +198,22 @@ struct IntegArgs {
 
 constexpr int T1TAB_N = 4096;
 constexpr int T2_NH = 64;
+// FP32 T_2: the node count of a piece whose integrand is smooth enough for fewer nodes.
+// Emulated on the host against the oracle's adaptive quadrature: 24 nodes stay within
+// 1.8e-6 relative over 2,231 cases with 4 <= dof <= 64 and |rho| < 0.9 (32 nodes are needed
+// beyond: sin^(dof-1) peaks more sharply at large dof, the boundary layer narrows as |rho|
+// -> 1); the FP32 integrators' error floor is 5e-5.
+constexpr int T2_LO = 24;
+constexpr float T2_LO_DOF_MIN = 4.0f, T2_LO_DOF_MAX = 64.0f, T2_LO_RHO = 0.9f;
 constexpr float T1TAB_V = 48.0f;
 
 struct CombineArgs {
     Dims D;
     Layout Ly;
     const double* cst64;   // per-dof constants, [3h + j][CST_STRIDE]
+    const float* cst32;    //   (FP32 copies, read by the mixed form's assembly)
     const double* F;
+    const float* F32;      // mixed form: FP32 copies of the factor blocks (else null)
     const double* pd;
     const double* pc;
     RecSet L0, L1, L2, LM;
@@ -312,7 +326,12 @@ struct ReduceArgs {
     int chunk;         // observations per block (<= blockDim.x)
     int row;           // values per staged observation row
     const float* y32;  // FP32 observations (FP32 statistics kernel only)
+    int small_only;    // 1: N, U, Snu, Se, See only (Sr, Sre, Srr from the tensor-core kernel)
 };
+
+size_t reduce_tc_smem(int p, int q, int g);
+bool reduce_tc_fits(int p, int q, int g);
+cudaError_t launch_reduce_tc(const ReduceArgs& a, int* flags, int nsm, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // Learned surrogate (not part of the paper): a 3 x 256 tanh MLP mapping a

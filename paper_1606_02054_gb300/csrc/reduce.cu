@@ -132,7 +132,9 @@ __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
                 rw[1] = (T)(tv * uv);
                 rw[2] = (T)(a.elogu[pid] - uv);
                 rw[3] = T(1);
-                if (sizeof(T) == sizeof(float)) {
+                if (a.small_only) {
+                    // r is not read
+                } else if (sizeof(T) == sizeof(float)) {
                     const float* yj = a.y32 + (size_t)(j0 + t) * p;
                     for (int i = 0; i < p; ++i) rw[4 + i] = (T)(yj[i] - (float)a.mu[(size_t)h * p + i]);
                 } else {
@@ -146,8 +148,10 @@ __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
             }
         }
         __syncthreads();
-        const int Sred = stats_reduced(p, q);
-        for (int e = t; e < Sred; e += blockDim.x) {
+        // small_only: N, U, Snu, Se and See (the tensor-core kernel writes Sr, Sre, Srr)
+        const int Sred = a.small_only ? 3 + q + q * (q + 1) / 2 : stats_reduced(p, q);
+        for (int es = t; es < Sred; es += blockDim.x) {
+            const int e = !a.small_only || es < 3 ? es : es < 3 + q ? 3 + p + (es - 3) : 3 + p + q + p * q + (es - 3 - q);
             int ia, ib, ic, o1, o2;
             stat_operands(e, p, q, ia, ib, ic, o1, o2);
             T acc = T(0), comp = T(0);

@@ -270,13 +270,16 @@ static __device__ double log_t1_lower(double w, double nu)
 }
 
 // Tables of log2 T_1(-|z|; dofs[t] + 1) and d/dv on the asinh grid (see IntegArgs::t1tab).
-__global__ void t1_table_kernel(int ndof, const double* __restrict__ dofs, float2* __restrict__ tab)
+// jmask: the tables t with bit (t mod 3) set are built (E-step tables t = 3h + j; the
+// others are left as they are: no record reads them); 7 builds every table.
+__global__ void t1_table_kernel(int ndof, const double* __restrict__ dofs, float2* __restrict__ tab, int jmask)
 {
     const long long total = (long long)ndof * T1TAB_N;
     const double hv = (double)T1TAB_V / (T1TAB_N - 1);
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
         const int t = (int)(e / T1TAB_N), i = (int)(e % T1TAB_N);
+        if (!((jmask >> (t % 3)) & 1)) continue;
         const double nu = dofs[t] + 1.0;
         if (isinf(nu)) {  // the normal limit evaluates Phi_2 directly, not through this table
             tab[e] = make_float2(0.0f, 0.0f);

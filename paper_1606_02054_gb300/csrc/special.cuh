@@ -357,7 +357,8 @@ template <typename R>
 __device__ double t2cdf_warp(R h, R k, R rho, R nu, R omr2, R cr, R lgb, R lgb1, R C2, int n,
                              const R* __restrict__ glx, const R* __restrict__ glw, int nh,
                              const R* __restrict__ glxh, const R* __restrict__ glwh, int lane,
-                             const float2* __restrict__ t1tab = nullptr, int* nodes_out = nullptr)
+                             const float2* __restrict__ t1tab = nullptr, int* nodes_out = nullptr,
+                             int nlo = 0, const R* __restrict__ glxl = nullptr, const R* __restrict__ glwl = nullptr)
 {
     if (nodes_out) *nodes_out = 0;
     if (rho >= R(1)) {
@@ -369,10 +370,13 @@ __device__ double t2cdf_warp(R h, R k, R rho, R nu, R omr2, R cr, R lgb, R lgb1,
         return v > R(0) ? (double)v : 0.0;
     }
     const bool graded = m_abs(rho) > R(0.99);
+    // fewer nodes where the integrand is smooth enough (nlo > 0: the FP32 rule of T2_LO)
+    const bool lo = nlo > 0 && !graded && m_abs(rho) < R(T2_LO_RHO) && nu >= R(T2_LO_DOF_MIN) &&
+                    nu <= R(T2_LO_DOF_MAX);
     const T2Setup<R> S = t2_setup<R>(h, k, rho, nu, omr2, cr);
-    const int nn = graded ? nh : n;
-    const R* __restrict__ gx = graded ? glxh : glx;
-    const R* __restrict__ gw = graded ? glwh : glw;
+    const int nn = graded ? nh : lo ? nlo : n;
+    const R* __restrict__ gx = graded ? glxh : lo ? glxl : glx;
+    const R* __restrict__ gw = graded ? glwh : lo ? glwl : glw;
     const int npieces = S.split ? 2 : 1;
     if (nodes_out) *nodes_out = npieces * nn;
     const R nu1 = nu + R(1), num1 = nu - R(1);
@@ -425,26 +429,31 @@ __device__ __forceinline__ float group_sum(float v)
 // lanes (sub = the lane's index in its group): the nodes of the record's pieces are
 // spread over the group's lanes, so a warp evaluates 32/L records at once and the
 // per-record set-up (the angles of the split, the pieces' lengths) is paid once per
-// group instead of once per warp.  Every lane of the warp must call it (the group
-// reductions are warp-wide shuffles); the |rho| = 1 limits take no early return so
-// that every group reaches them.  nodes_out: nodes evaluated (0 at |rho| = 1).
+// group instead of once per warp.  Lane sub adds the nodes t = sub, sub + L, ... and the
+// group sums its lanes, so the rounding of the sum depends on L (the same L gives the same
+// bits).  Every lane of the warp must call it (the group reductions are warp-wide
+// shuffles); the |rho| = 1 limits take no early return so that every group reaches them.
+// nodes_out: nodes evaluated (0 at |rho| = 1).
 // ---------------------------------------------------------------------------
 template <int L>
 __device__ double t2cdf_group_f32(float h, float k, float rho, float nu, float omr2, float cr, float lgb,
                                   float lgb1, float C2, int n, const float* __restrict__ glx,
                                   const float* __restrict__ glw, int nh, const float* __restrict__ glxh,
                                   const float* __restrict__ glwh, int sub, const float2* __restrict__ t1tab,
-                                  int* nodes_out)
+                                  int* nodes_out, int nlo, const float* __restrict__ glxl,
+                                  const float* __restrict__ glwl)
 {
     const bool lim = rho >= 1.0f || rho <= -1.0f;
     float acc = 0.0f;
     int nodes = 0;
     if (!lim) {
         const bool graded = fabsf(rho) > 0.99f;
+        // fewer nodes where the integrand is smooth enough (the rule of T2_LO)
+        const bool lo = nlo > 0 && !graded && fabsf(rho) < T2_LO_RHO && nu >= T2_LO_DOF_MIN && nu <= T2_LO_DOF_MAX;
         const T2Setup<float> S = t2_setup<float>(h, k, rho, nu, omr2, cr);
-        const int nn = graded ? nh : n;
-        const float* __restrict__ gx = graded ? glxh : glx;
-        const float* __restrict__ gw = graded ? glwh : glw;
+        const int nn = graded ? nh : lo ? nlo : n;
+        const float* __restrict__ gx = graded ? glxh : lo ? glxl : glx;
+        const float* __restrict__ gw = graded ? glwh : lo ? glwl : glw;
         nodes = (S.split ? 2 : 1) * nn;
         const float nu1 = nu + 1.0f, num1 = nu - 1.0f;
         for (int t = sub; t < nodes; t += L) {

@@ -89,17 +89,21 @@ def test_mixed_fit_error(cf, oracle):
     assert max(perr.values()) <= 1e-4
 
 
-@pytest.mark.parametrize("p,q,g,n", [(32, 8, 2, 300), (17, 3, 3, 257), (5, 1, 2, 1000)])
-def test_mixed_cross_statistics(cf, p, q, g, n):
-    """Sre = sum tau r eu^T and Srr = sum tau u r r^T of the mixed form (compensated
-    FP32 sums per block of at most 256 rows, FP64 across blocks) at the largest
-    shape (p = 32, q = 8) and ragged n, against FP64 sums of the same FP32 row values
-    built from the context's own tau, u and eu: 1e-5 of each block's largest entry;
-    Srr exactly symmetric."""
+@pytest.mark.parametrize("tensor", [0, 1])
+@pytest.mark.parametrize("p,q,g,n", [(32, 8, 2, 300), (17, 3, 3, 257), (5, 1, 2, 1000), (16, 2, 8, 3001)])
+def test_mixed_cross_statistics(cf, p, q, g, n, tensor):
+    """Sr = sum tau u r, Sre = sum tau r eu^T and Srr = sum tau u r r^T of the mixed form
+    -- compensated FP32 sums per block of at most 256 rows on the CUDA cores
+    (tensor = 0), or the tcgen05 contraction with a TF32 hi/lo split and FP32
+    accumulation per block (tensor = 1) -- FP64 across blocks, at the largest shape
+    (p = 32, q = 8), the benchmark's p = 16, g = 8 and ragged n, against FP64 sums of the
+    same FP32 row values built from the context's own tau, u and eu: 1e-5 of each
+    block's largest entry; Srr exactly symmetric."""
     rng = np.random.default_rng(100 * p + q)
     P = synth.draw_params(rng, p, q, g, wishart_df=p + 8)
     y32 = np.ascontiguousarray(synth.sample(rng, n, P)[0], dtype=np.float32)
-    ctx = cf.cfust_create(p, q, g, n, cf.cfust_default_opts(precision=cf.CFUST_PREC_MIXED, moments=1))
+    ctx = cf.cfust_create(p, q, g, n, cf.cfust_default_opts(precision=cf.CFUST_PREC_MIXED, moments=1,
+                                                             tensor_stats=tensor))
     cf.cfust_set_data(ctx, y32)
     cf.cfust_set_params(ctx, P)
     cf.cfust_estep(ctx)
@@ -108,15 +112,21 @@ def test_mixed_cross_statistics(cf, p, q, g, n):
     f64 = np.float64
     off = 3 + p + q
     fSrr = off + p * q + q * q
+    worst = 0.0
     for h in range(g):
         t = pr["tau"][h].astype(np.float32).astype(f64)
         tu = (pr["tau"][h] * pr["u"][h]).astype(np.float32).astype(f64)
         r = (y32 - P["mu"][h].astype(np.float32)).astype(f64)
         e = pr["eu"][h].astype(np.float32).astype(f64)
+        Sr = tu @ r
         Sre = np.einsum("j,ja,jb->ab", t, r, e)
         Srr = np.einsum("j,ja,jb->ab", tu, r, r)
+        got_r = S[h][3:3 + p]
         got_re = S[h][off:off + p * q].reshape(p, q)
         got_rr = S[h][fSrr:fSrr + p * p].reshape(p, p)
-        assert np.max(np.abs(got_re - Sre)) <= 1e-5 * np.abs(Sre).max(), h
-        assert np.max(np.abs(got_rr - Srr)) <= 1e-5 * np.abs(Srr).max(), h
+        for got, ref in ((got_r, Sr), (got_re, Sre), (got_rr, Srr)):
+            err = np.max(np.abs(got - ref)) / np.abs(ref).max()
+            worst = max(worst, err)
+            assert err <= 1e-5, (h, err)
         assert np.array_equal(got_rr, got_rr.T)
+    print(f"p={p} q={q} g={g} tensor={tensor}: worst cross-statistic error {worst:.2e}")
