@@ -268,19 +268,20 @@ cfust_status cfust_kmeans(cfust_ctx* ctx, int nstarts, uint64_t seed, int max_it
 /* Autotuner of the integrators' launch shapes (not part of the paper).  Runs one
  * E-step at the current Psi, then times (CUDA events, best of reps runs after one
  * warm-up) each candidate shape of the context's integral records:
- *   - FP32 T_2 records of finite dof: 2, 4, 8, 16 or 32 lanes per record
+ *   - FP32 T_2 records of finite dof: 2, 4, 8 or 16 lanes per quadrature piece (a
+ *     warp's pieces dealt to groups of that many lanes) or 32 (a warp per record)
  *     (ms[0..4]; -1 where the context has no such records);
  *   - the FP32 single-pass moment pass at q <= 4: 1 or 2 lattice points in flight
  *     per lane (ms[5..6]; -1 where not applicable);
- * and keeps the fastest (choices[0]: lanes per T_2 record, choices[1]: points per
+ * and keeps the fastest (choices[0]: lanes per T_2 piece, choices[1]: points per
  * lane; 0 where not applicable).  The choice holds for this context and, for the rest
  * of the process, for every context (one not tuned itself) with records of the same
  * (kernel, dimension, precision), from its next E-step on (a fit graph of
- * cfust_fit_batch keeps the shapes it was captured with).  The lanes per T_2 record
+ * cfust_fit_batch keeps the shapes it was captured with).  The lanes per T_2 piece
  * decide the order in which a record's nodes are added, so the choice is one per shape,
  * not per problem size: the shards of one problem stay bitwise equal to it.  Leaves no E-step
  * results (run cfust_estep before cfust_mstep).  Without tuning the shapes are 2 lanes
- * per T_2 record and 2 points per lane.  choices (2) and ms (7) may be NULL. */
+ * per T_2 piece and 2 points per lane.  choices (2) and ms (7) may be NULL. */
 cfust_status cfust_autotune(cfust_ctx* ctx, int reps, int* choices, double* ms);
 
 /* Flags of cfust_fit_batch. *//* Flags of cfust_fit_batch. *//* Flags of cfust_fit_batch. */

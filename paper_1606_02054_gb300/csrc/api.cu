@@ -23,6 +23,7 @@ __global__ void chi_table_kernel(int, int, const double*, const double*, Lattice
 __global__ void dof_consts_kernel(Dims, Layout, const double*, int, double*, double*, float*);
 __global__ void t1_table_kernel(int, const double*, float2*, int);
 __global__ void widen_kernel(const float*, long long, Dims, double*);
+__global__ void widen_pairs_kernel(const float*, long long, int, double*, double*, double*, double*);
 __global__ void narrow_kernel(const double*, Dims, float*);
 
 
@@ -70,7 +71,7 @@ struct cfust_ctx {
            *se = nullptr, *tau = nullptr;
     double *partial = nullptr, *stats = nullptr;
     int tune_t2_group = 0;  // launch shapes of the integrators chosen by cfust_autotune on this
-    int tune_mom_p = 0;     // context (0: the process-wide choice for its bucket, else the default)
+    int tune_mom_p = 0;     // context (0: the process-wide choice for its shape, else the default)
     double* seg = nullptr;  // segment sums of the block partials (nseg x width)
     long long nseg = 0;
     long long n_stats = 0;  // observations behind the current statistics (all shards'), the n of eq (18)
@@ -82,6 +83,7 @@ struct cfust_ctx {
     bool tc_stats = false;  // mixed form: cross statistics on the tensor cores (reduce_tc.cu)
     float* y32 = nullptr;
     float* F32 = nullptr;
+    float* pr32 = nullptr;  // FP32 pair rows (u, E log w, eu, euu) written by the mixed E-step
     // E-step pipeline: per-pair (d, log t_p) and c, integral records per level
     double *pd = nullptr, *pc = nullptr;
     RecSet rec[4]{};  // levels 0, 1, 2 and the single-pass moment records
@@ -216,9 +218,18 @@ static cfust_status check_flags(cfust_ctx* c, int f, const char* where)
 // Observations per block of the statistics reduction: rows of 4 + p + q + q^2 values
 // (FP32 in the mixed form) plus g posterior weights staged in at most ~64 KB of
 // shared memory, chunk <= 256.  Depends on the sizes and the precision only, not on n.
-static int reduce_chunk(int p, int q, int g, bool mixed)
+// values per staged row of the statistics kernel; odd in the mixed form, whose register
+// tiles read rows rg, rg + RG, ... in the lanes of a warp (an odd stride keeps them in
+// distinct shared-memory banks)
+static int reduce_row(int p, int q, bool mixed)
 {
     const int row = 4 + p + q + q * q;
+    return mixed ? (row | 1) : row;
+}
+
+static int reduce_chunk(int p, int q, int g, bool mixed)
+{
+    const int row = reduce_row(p, q, mixed);
     const size_t rowbytes = mixed ? sizeof(float) : sizeof(double);
     int chunk = 256;
     while (chunk > 32 && (size_t)chunk * ((row + g) * rowbytes + sizeof(double)) + CF_MAXG * sizeof(double) > 64 * 1024)
@@ -361,7 +372,7 @@ static void free_all(cfust_ctx* c)
                     c->glx64, c->glw64, c->glx32, c->glw32, c->glx32h, c->glw32h, c->glx32l, c->glw32l,
                     c->logf, c->u, c->elogu, c->eu,
                     c->euu, c->se, c->tau, c->partial, c->stats, c->flags, c->comp_status,
-                    c->stage32, c->pd, c->pc, c->fix_count, c->fix_list, c->y32, c->F32, c->t1tab,
+                    c->stage32, c->pd, c->pc, c->fix_count, c->fix_list, c->y32, c->F32, c->pr32, c->t1tab,
                     c->work_dev, c->seg, c->lchi64, c->lchi32};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -469,7 +480,7 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     const int S = stats_per_comp(p, q);
     // reduction staging: rows of 4 + p + q + q^2 doubles, chunk <= 256 observations,
     // at most ~64 KB of shared memory
-    c->row = 4 + p + q + q * q;
+    c->row = reduce_row(p, q, c->mixed);
     const int chunk = reduce_chunk(p, q, g, c->mixed);
     c->chunk = chunk;
     c->nblocks_red = (int)((n + chunk - 1) / chunk);
@@ -516,6 +527,7 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     if (c->mixed) {
         ALLOC(y32, (size_t)n * p);
         ALLOC(F32, (size_t)g * c->Ly.stride);
+        ALLOC(pr32, ng * pr32_width(q));
     }
     ALLOC(fix_count, 1); ALLOC(fix_list, ng);
     // T_2 records exist at q = 2 (level 0) and, in the recursion form, at q = 3, 4 (levels 1, 2)
@@ -723,7 +735,7 @@ extern "C" cfust_status cfust_get_params(cfust_ctx* c, cfust_params* P)
 static cfust_status launch_setup(cfust_ctx* c)
 {
     prof_begin(c, CFUST_PROF_SETUP);
-    setup_components_kernel<<<1, 32, 0, c->st>>>(c->D, c->Ly, c->mu, c->Sigma, c->Delta, c->nu,
+    setup_components_kernel<<<c->g, 32, 0, c->st>>>(c->D, c->Ly, c->mu, c->Sigma, c->Delta, c->nu,
                                                  c->F, c->flags);
     LAUNCHED();
     dof_consts_kernel<<<1, 64, 0, c->st>>>(c->D, c->Ly, c->F, 3 * c->g, c->dofs, c->cst64, c->cst32);
@@ -878,6 +890,7 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
     ca.density_only = density_only; ca.single_pass = sp; ca.fp32 = fp32;
     ca.mixed = c->mixed ? 1 : 0;
     ca.logf = c->logf; ca.u = c->u; ca.elogu = c->elogu; ca.eu = c->eu; ca.euu = c->euu; ca.se = c->se;
+    ca.pr32 = c->mixed ? c->pr32 : nullptr;
     ca.fix_count = c->fix_count; ca.fix_list = c->fix_list; ca.flags = c->flags;
     n0 = c->launches;
     prof_begin(c, CFUST_PROF_COMBINE);
@@ -896,6 +909,7 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
         a.single_pass = sp;
         a.lchi64 = c->lchi64;
         a.logf = c->logf; a.u = c->u; a.elogu = c->elogu; a.eu = c->eu; a.euu = c->euu; a.se = c->se;
+        a.pr32 = c->mixed ? c->pr32 : nullptr;
         a.flags = c->flags;
         n0 = c->launches;
         prof_begin(c, CFUST_PROF_FIXUP);
@@ -918,6 +932,7 @@ static cfust_status enqueue_estep_segments(cfust_ctx* c, double* seg, long long 
     ReduceArgs r;
     r.D = c->D; r.y = c->y; r.pi = c->pi; r.mu = c->mu; r.logf = c->logf; r.u = c->u;
     r.elogu = c->elogu; r.eu = c->eu; r.euu = c->euu; r.tau = c->tau; r.partial = c->partial;
+    r.pr32 = c->mixed ? c->pr32 : nullptr;
     r.chunk = c->chunk; r.row = c->row;
     r.y32 = c->y32;
     r.small_only = c->tc_stats ? 1 : 0;
@@ -990,6 +1005,12 @@ extern "C" cfust_status cfust_get_pairs(cfust_ctx* c, double* logf, double* tau,
     if (!c->have_stats) return fail(c, CFUST_ESTATE, "cfust_get_pairs: no E-step results");
     const size_t ng = (size_t)c->n * c->g;
     CU(cudaSetDevice(c->opts.device));
+    if (c->mixed && (u || elogu || eu || euu)) {  // the mixed E-step keeps these in its FP32 rows
+        widen_pairs_kernel<<<(int)std::min<size_t>((ng + 255) / 256, 64 * (size_t)c->nsm), 256, 0, c->st>>>(
+            c->pr32, (long long)ng, c->q, c->u, c->elogu, c->eu, c->euu);
+        c->launches++;
+        CU(cudaGetLastError());
+    }
     if (logf) CU(cudaMemcpyAsync(logf, c->logf, sizeof(double) * ng, cudaMemcpyDeviceToHost, c->st));
     if (tau) CU(cudaMemcpyAsync(tau, c->tau, sizeof(double) * ng, cudaMemcpyDeviceToHost, c->st));
     if (u) CU(cudaMemcpyAsync(u, c->u, sizeof(double) * ng, cudaMemcpyDeviceToHost, c->st));
@@ -1020,7 +1041,7 @@ static cfust_status enqueue_mstep(cfust_ctx* c, const int* gate)
     prof_begin(c, CFUST_PROF_MSTEP);
     Dims Dm = c->D;
     Dm.n = c->n_stats;  // pi_h = N_h / n over every observation the statistics cover
-    mstep_kernel<<<1, 32, 0, c->st>>>(Dm, c->stats, c->opts.nu_min, c->opts.nu_max, c->mu, c->Delta,
+    mstep_kernel<<<c->g, 32, 0, c->st>>>(Dm, c->stats, c->opts.nu_min, c->opts.nu_max, c->mu, c->Delta,
                                       c->nu, c->pi_n, c->mu_n, c->Sigma_n, c->Delta_n, c->nu_n,
                                       c->flags, c->comp_status, gate, c->opts.hold);
     LAUNCHED();
@@ -1138,7 +1159,7 @@ extern "C" cfust_status cfust_fit(cfust_ctx* c, int max_iter, double tol, int* i
 // Autotuner of the integrators' launch shapes.  Choices are kept per (kernel, record
 // dimension, precision) for the process, and every context of that shape without a tuning
 // of its own uses them from its next E-step on (a CUDA graph keeps the shape in force when
-// it was built).  The lanes per T_2 record set the order in which a record's nodes are
+// it was built).  The lanes per T_2 piece set the order in which a record's nodes are
 // added, so one choice per shape -- not per problem size -- keeps the shards of one
 // problem (which differ in size) bitwise equal to the whole problem.
 // ---------------------------------------------------------------------------
@@ -1159,7 +1180,7 @@ bool mom_tunable(const cfust_ctx* c)
     return c->single_pass && c->opts.precision != CFUST_PREC_FP64 && c->q <= 4 && c->rec[3].nrec > 0;
 }
 // The shapes in force: this context's tuning, else the process-wide choice for its
-// bucket, else the defaults (2 lanes per T_2 record, 2 points per lane)
+// shape, else the defaults (2 lanes per T_2 piece, 2 points per lane)
 void tune_lookup(const cfust_ctx* c, int* t2_group, int* mom_p)
 {
     *t2_group = c->tune_t2_group ? c->tune_t2_group : 2;

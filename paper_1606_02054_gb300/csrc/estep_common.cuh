@@ -22,6 +22,33 @@ struct PairOut {
     double euu[CF_MAXQ * CF_MAXQ];
 };
 
+// The mixed form's pair: log f in FP64, the conditional expectations in FP32 as assembled.
+struct PairOutF {
+    double logf;
+    float u, elogu;
+    float eu[CF_MAXQ];
+    float euu[CF_MAXQ * CF_MAXQ];
+};
+
+// Mixed form: one FP32 row per pair, [u, E log w, eu (q), euu (q x q)], the layout the
+// statistics kernel stages (widened to the FP64 pair buffers only when read back).
+
+__device__ inline void store_pr32(float* row, int q, const PairOutF& o)
+{
+    row[0] = o.u;
+    row[1] = o.elogu;
+    for (int k = 0; k < q; ++k) row[2 + k] = o.eu[k];
+    for (int k = 0; k < q * q; ++k) row[2 + q + k] = o.euu[k];
+}
+
+__device__ inline void store_pr32(float* row, int q, const PairOut& o)
+{
+    row[0] = (float)o.u;
+    row[1] = (float)o.elogu;
+    for (int k = 0; k < q; ++k) row[2 + k] = (float)o.eu[k];
+    for (int k = 0; k < q * q; ++k) row[2 + q + k] = (float)o.euu[k];
+}
+
 __device__ inline void pair_whiten(const double* F, const Layout& Ly, int p, int q,
                                    const double* yj, double* d_out, double* c, double* logtp)
 {
@@ -151,14 +178,15 @@ __device__ inline int fac_l2(const Layout& Ly, int q, int r, int s)
 // arithmetic on this component's skewing side): log f = -inf, so tau = 0 (eq 12),
 // and the conditional expectations, which enter eqs (18)-(22) only multiplied by
 // tau, are set to u = 1, E[log w] = 0, e2 = 0, e3 = 0 instead of a 0/0.
-__device__ inline void pair_null(int q, int density_only, PairOut& o)
+template <typename O>
+__device__ inline void pair_null(int q, int density_only, O& o)
 {
     o.logf = -INFINITY;
     if (density_only) return;
-    o.u = 1.0;
-    o.elogu = 0.0;
-    for (int a = 0; a < q; ++a) o.eu[a] = 0.0;
-    for (int a = 0; a < q * q; ++a) o.euu[a] = 0.0;
+    o.u = 1;
+    o.elogu = 0;
+    for (int a = 0; a < q; ++a) o.eu[a] = 0;
+    for (int a = 0; a < q * q; ++a) o.euu[a] = 0;
 }
 
 // tq1[r] = T_{q-1} of level 1 (1 when q = 1); tq2[r*(q-1)+s] = T_{q-2} of
@@ -279,7 +307,7 @@ __device__ inline void pair_assemble_sp(const double* F, const Layout& Ly, int p
 __device__ inline void pair_assemble_f32(const float* F, const Layout& Ly, int p, int q,
                                          const double* cd, double dd, double logtp, double alpha_s_d,
                                          double alpha_d, const double* tq1, const double* tq2,
-                                         int density_only, const float* cst, PairOut& o)
+                                         int density_only, const float* cst, PairOutF& o)
 {
     const float alpha_s = (float)alpha_s_d;
     if (!(alpha_s > 0.0f)) return pair_null(q, density_only, o);

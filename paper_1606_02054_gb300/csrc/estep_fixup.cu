@@ -79,10 +79,14 @@ __global__ void __launch_bounds__(128) fixup_kernel(EstepArgs a, const int* coun
                 a.logf[pid] = o.logf;
                 if (a.se) a.se[pid] = se;
                 if (!(o.logf < INFINITY)) atomicOr(a.flags, KF_NAN);  // NaN or +inf; -inf is a null pair
-                a.u[pid] = o.u;
-                a.elogu[pid] = o.elogu;
-                for (int k = 0; k < q; ++k) a.eu[pid * q + k] = o.eu[k];
-                for (int k = 0; k < q * q; ++k) a.euu[pid * q * q + k] = o.euu[k];
+                if (a.pr32) {
+                    store_pr32(a.pr32 + pid * pr32_width(q), q, o);
+                } else {
+                    a.u[pid] = o.u;
+                    a.elogu[pid] = o.elogu;
+                    for (int k = 0; k < q; ++k) a.eu[pid * q + k] = o.eu[k];
+                    for (int k = 0; k < q * q; ++k) a.euu[pid * q * q + k] = o.euu[k];
+                }
             }
             continue;
         }
@@ -105,7 +109,9 @@ __global__ void __launch_bounds__(128) fixup_kernel(EstepArgs a, const int* coun
             a.logf[pid] = o.logf;
             if (a.se) a.se[pid] = se;
             if (!(o.logf < INFINITY)) atomicOr(a.flags, KF_NAN);  // NaN or +inf; -inf is a null pair
-            if (!a.density_only) {
+            if (!a.density_only && a.pr32) {
+                store_pr32(a.pr32 + pid * pr32_width(q), q, o);
+            } else if (!a.density_only) {
                 a.u[pid] = o.u;
                 a.elogu[pid] = o.elogu;
                 for (int k = 0; k < q; ++k) a.eu[pid * q + k] = o.eu[k];

@@ -28,7 +28,7 @@ __device__ __forceinline__ void put_t2f32(const RecSet& L, long long rec, const 
 
 // Mixed form: one pair in FP32 (whitening, log t_p, limits, FP32 T_2 inputs);
 // T_2 records of the FP32 modes need no FP64 fields, the others get them.
-__device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, long long j)
+__device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const float* yj)
 {
     const int p = a.D.p, q = a.D.q;
     const int m0 = (a.density_only || a.single_pass) ? 1 : 2;
@@ -37,7 +37,7 @@ __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, long long
     const double nu1d = a.F[(size_t)h * a.Ly.stride + a.Ly.scal + SC_NU] + p;
     const float nu1 = F[a.Ly.scal + SC_NU] + p;
     float c[CF_MAXQ], d, logtp, bt[CF_MAXQ];
-    pair_whiten_f32(F, a.Ly, p, q, a.y32 + (size_t)j * p, &d, c, &logtp);
+    pair_whiten_f32(F, a.Ly, p, q, yj, &d, c, &logtp);
     a.pd[2 * pid] = d;
     a.pd[2 * pid + 1] = logtp;
     for (int k = 0; k < q; ++k) a.pc[pid * q + k] = c[k];
@@ -92,13 +92,30 @@ __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, long long
 
 // Mixed form: FP32 pairs in a kernel of their own, so the FP64 path's registers do not
 // limit its occupancy (one kernel for both took 118 registers, 24 % warps active).
-__global__ void __launch_bounds__(128) plan_kernel_f32(PlanArgs a)
+// The block's observation rows are staged in shared memory by coalesced loads (a block's
+// pairs are consecutive observations of one or two components), at an odd row stride so
+// the threads' row reads fall in distinct banks.
+constexpr int PLAN_THREADS = 128;
+__global__ void __launch_bounds__(PLAN_THREADS) plan_kernel_f32(PlanArgs a)
 {
-    const long long np = a.D.n * a.D.g;
-    for (long long pid = blockIdx.x * (long long)blockDim.x + threadIdx.x; pid < np;
-         pid += (long long)gridDim.x * blockDim.x) {
-        const int h = (int)(pid / a.D.n);
-        plan_pair_f32(a, pid, h, pid - (long long)h * a.D.n);
+    __shared__ float ys[PLAN_THREADS * (CF_MAXP + 1)];
+    const int p = a.D.p, ps = p | 1, t = threadIdx.x;
+    const long long n = a.D.n, np = n * a.D.g;
+    for (long long base = blockIdx.x * (long long)PLAN_THREADS; base < np;
+         base += (long long)gridDim.x * PLAN_THREADS) {
+        const int rows = np - base < PLAN_THREADS ? (int)(np - base) : PLAN_THREADS;
+        __syncthreads();  // the previous rows are read
+        for (int e = t; e < rows * p; e += PLAN_THREADS) {
+            const int r = e / p, i = e - r * p;
+            const long long pid = base + r;
+            const long long j = pid - (pid / n) * n;
+            ys[r * ps + i] = a.y32[(size_t)j * p + i];
+        }
+        __syncthreads();
+        if (t < rows) {
+            const long long pid = base + t;
+            plan_pair_f32(a, pid, (int)(pid / n), ys + t * ps);
+        }
     }
 }
 
@@ -186,6 +203,26 @@ __global__ void __launch_bounds__(128) combine_kernel(CombineArgs a)
             a.fix_list[slot] = (int)pid;
             continue;
         }
+        if constexpr (MIXED) {
+            if (!(a.single_pass && !a.density_only)) {
+                // FP32 assembly straight into the FP32 pair row
+                const double alpha = a.density_only ? 0.0 : a.L0.res[pid * m0 + 1];
+                double tq1[CF_MAXQ], tq2[CF_MAXQ * CF_MAXQ];
+                if (!a.density_only) {
+                    for (int r = 0; r < q && q1 > 0; ++r) tq1[r] = a.L1.res[pid * q + r];
+                    if (q1 > 1)
+                        for (int i = 0; i < q * q1; ++i) tq2[i] = a.L2.res[pid * q * q1 + i];
+                }
+                PairOutF of;
+                pair_assemble_f32(a.F32 + (size_t)h * a.Ly.stride, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1,
+                                  tq2, a.density_only, a.cst32 + (size_t)(3 * h) * CST_STRIDE, of);
+                a.logf[pid] = of.logf;
+                if (a.se) a.se[pid] = se;
+                if (!(of.logf < INFINITY)) atomicOr(a.flags, KF_NAN);  // NaN or +inf; -inf is a null pair
+                if (!a.density_only) store_pr32(a.pr32 + pid * pr32_width(q), q, of);
+                continue;
+            }
+        }
         PairOut o;
         if (a.single_pass && !a.density_only) {
             pair_assemble_sp(F, a.Ly, p, q, c, d, logtp, alpha_s, a.LM.res[pid], a.LM.mom + pid * W, o,
@@ -198,17 +235,17 @@ __global__ void __launch_bounds__(128) combine_kernel(CombineArgs a)
                 if (q1 > 1)
                     for (int i = 0; i < q * q1; ++i) tq2[i] = a.L2.res[pid * q * q1 + i];
             }
-            if constexpr (MIXED)
-                pair_assemble_f32(a.F32 + (size_t)h * a.Ly.stride, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1,
-                                  tq2, a.density_only, a.cst32 + (size_t)(3 * h) * CST_STRIDE, o);
-            else
-                pair_assemble(F, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1, tq2, a.density_only,
-                              a.cst64 + (size_t)(3 * h) * CST_STRIDE, o);
+            pair_assemble(F, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1, tq2, a.density_only,
+                          a.cst64 + (size_t)(3 * h) * CST_STRIDE, o);
         }
         a.logf[pid] = o.logf;
         if (a.se) a.se[pid] = se;
         if (!(o.logf < INFINITY)) atomicOr(a.flags, KF_NAN);  // NaN or +inf; -inf is a null pair
         if (a.density_only) continue;
+        if (a.pr32) {  // mixed form, single pass: FP64 assembly, FP32 row
+            store_pr32(a.pr32 + pid * pr32_width(q), q, o);
+            continue;
+        }
         a.u[pid] = o.u;
         a.elogu[pid] = o.elogu;
         for (int k = 0; k < q; ++k) a.eu[pid * q + k] = o.eu[k];
@@ -246,7 +283,7 @@ static int grid_for(long long work, int threads, int cap)
 cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st, long long* launches)
 {
     const long long np = a.D.n * a.D.g;
-    if (a.F32) plan_kernel_f32<<<grid_for(np, 128, 1 << 20), 128, 0, st>>>(a);
+    if (a.F32) plan_kernel_f32<<<grid_for(np, PLAN_THREADS, 1 << 20), PLAN_THREADS, 0, st>>>(a);
     else plan_kernel<<<grid_for(np, 128, 1 << 20), 128, 0, st>>>(a);
     ++*launches;
     return cudaGetLastError();
@@ -293,6 +330,21 @@ cudaError_t launch_integrals(const RecSet& r, const IntegArgs& a, int fp32, int 
     }
     ++*launches;
     return e;
+}
+
+// The mixed form's FP32 pair rows widened into the FP64 pair buffers (read-back only).
+__global__ void widen_pairs_kernel(const float* __restrict__ pr32, long long ng, int q, double* __restrict__ u,
+                                   double* __restrict__ elogu, double* __restrict__ eu, double* __restrict__ euu)
+{
+    const int w = pr32_width(q);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ng;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float* r = pr32 + i * w;
+        u[i] = r[0];
+        elogu[i] = r[1];
+        for (int k = 0; k < q; ++k) eu[i * q + k] = r[2 + k];
+        for (int k = 0; k < q * q; ++k) euu[i * q * q + k] = r[2 + q + k];
+    }
 }
 
 // FP32 copies of the factor blocks (mixed precision)

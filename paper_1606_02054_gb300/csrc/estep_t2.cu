@@ -1,4 +1,5 @@
-// estep_t2.cu -- T_2 records (warp per record, quadrature nodes over lanes).
+// estep_t2.cu -- T_2 records: a warp per record (quadrature nodes over lanes), or in FP32
+// the records' quadrature pieces dealt to groups of lanes.
 #include "internal.cuh"
 #include "special.cuh"
 
@@ -44,61 +45,167 @@ __global__ void __launch_bounds__(256) t2_records_kernel(RecSet r, IntegArgs a)
     if (a.nodes && lane == 0 && nodes) atomicAdd(a.nodes, nodes);
 }
 
-// FP32 T_2 records (finite dof) on groups of L lanes: 32/L records per warp at a time.
-// The record loop is uniform over the warp (a group past the last record evaluates the
-// last record again and writes nothing), so the group reductions see all 32 lanes.
+// FP32 T_2 records (finite dof), scheduled by quadrature piece.  A warp takes a chunk of
+// 64 records; lane l sets up records l and l + 32 (the angles of the split and the pieces'
+// lengths, once per record), the chunk's pieces (one or two per record, 24, 32 or 64
+// nodes each) are ordered by node count and dealt to the warp's 32/L groups of L lanes,
+// a group sums its piece's nodes (lane sub takes nodes sub, sub + L, ...), and the record's
+// value is C_nu (piece 0 + piece 1).  Dealing pieces rather than records keeps the groups
+// of a round on equal node counts: a record with one piece no longer idles its lanes
+// while a neighbour's second piece runs.  The same L gives the same bits.
+namespace {
+constexpr int T2P_WARPS = 8;
+constexpr int T2P_CH = 2 * CF_WARP;  // records per warp chunk
+struct T2PieceRec {
+    float anc0, phis, L0, L1, d0, zs, nu, lgb1;
+    int tab, kind;  // kind: 0 = t2n_lo nodes, 1 = t2n nodes, 2 = graded (T2_NH nodes)
+};
+}  // namespace
+
 template <int L>
-__global__ void __launch_bounds__(256) t2_records_group_kernel(RecSet r, IntegArgs a)
+__global__ void __launch_bounds__(T2P_WARPS * CF_WARP, 4) t2_pieces_kernel(RecSet r, IntegArgs a)
 {
     constexpr int G = CF_WARP / L;
-    const int lane = threadIdx.x & (CF_WARP - 1);
+    __shared__ T2PieceRec srec[T2P_WARPS][T2P_CH];
+    __shared__ float spsum[T2P_WARPS][T2P_CH][2];
+    __shared__ unsigned char sitem[T2P_WARPS][2 * T2P_CH];  // (record << 1) | piece
+    const int lane = threadIdx.x & (CF_WARP - 1), wib = threadIdx.x >> 5;
     const int sub = lane & (L - 1), grp = lane / L;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    unsigned long long nodes = 0;  // this group's quadrature nodes (profiler count)
-    for (long long base = warp * G; base < r.nrec; base += nwarps * G) {
-        const long long want = base + grp;
-        const bool own = want < r.nrec;
-        const long long i = own ? want : r.nrec - 1;
-        const float* c = a.cst32 + r.tab[i] * CST_STRIDE;
-        float h, k, rho, nu, omr2, cr;
-        if (r.t2f) {
-            const float4 u0 = r.t2f[2 * i], u1 = r.t2f[2 * i + 1];
-            h = u0.x; k = u0.y; rho = u0.z; nu = u0.w; omr2 = u1.x; cr = u1.y;
-        } else {
-            const double h64 = r.bt[2 * i], k64 = r.bt[2 * i + 1];
-            const double rho64 = a.F[r.fac[i] + 2];  // L[1][0] of the 2 x 2 correlation factor
-            h = (float)h64; k = (float)k64; rho = (float)rho64; nu = (float)r.dof[i];
-            omr2 = (float)((1.0 - rho64) * (1.0 + rho64));
-            cr = (float)(h64 * (rho64 > 0.0 ? rho64 : -rho64) - (rho64 > 0.0 ? k64 : -k64));
-        }
-        const float2* tab = a.t1tab ? a.t1tab + (size_t)r.tab[i] * T1TAB_N : nullptr;
-        int nn = 0;
-        const double v = t2cdf_group_f32<L>(h, k, rho, nu, omr2, cr, c[CST_LGB], c[CST_LGB1], c[CST_C2], a.t2n,
-                                            a.glx32, a.glw32, T2_NH, a.glx32h, a.glw32h, sub, tab, &nn,
-                                            a.t2n_lo, a.glx32l, a.glw32l);
-        if (own) {
-            nodes += (unsigned long long)nn;
-            if (sub == 0) {
-                r.res[i] = v;
-                if (r.se) r.se[i] = 0.0;
+    T2PieceRec* R = srec[wib];
+    float (*P)[2] = spsum[wib];
+    unsigned char* items = sitem[wib];
+    const int nlo = a.t2n_lo > 0 ? a.t2n_lo : a.t2n;
+    unsigned long long nodes = 0;  // this lane's records' quadrature nodes (profiler count)
+    for (long long base = warp * T2P_CH; base < r.nrec; base += nwarps * T2P_CH) {
+        // phase 1: set-up of records lane and lane + 32
+        int np[2], kind[2];
+        float C2[2], lim[2];
+        bool limit[2];
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int rr = lane + m * CF_WARP;
+            const long long i = base + rr;
+            np[m] = 0; kind[m] = 1; C2[m] = 0.0f; lim[m] = 0.0f; limit[m] = false;
+            if (i >= r.nrec) continue;
+            const float* c = a.cst32 + r.tab[i] * CST_STRIDE;
+            float h, k, rho, nu, omr2, cr;
+            if (r.t2f) {  // FP32 record fields written by the plan
+                const float4 u0 = r.t2f[2 * i], u1 = r.t2f[2 * i + 1];
+                h = u0.x; k = u0.y; rho = u0.z; nu = u0.w; omr2 = u1.x; cr = u1.y;
+            } else {
+                const double h64 = r.bt[2 * i], k64 = r.bt[2 * i + 1];
+                const double rho64 = a.F[r.fac[i] + 2];  // L[1][0] of the 2 x 2 correlation factor
+                h = (float)h64; k = (float)k64; rho = (float)rho64; nu = (float)r.dof[i];
+                omr2 = (float)((1.0 - rho64) * (1.0 + rho64));
+                cr = (float)(h64 * (rho64 > 0.0 ? rho64 : -rho64) - (rho64 > 0.0 ? k64 : -k64));
             }
+            C2[m] = c[CST_C2];
+            if (rho >= 1.0f || rho <= -1.0f) {  // the |rho| = 1 limits: no pieces
+                limit[m] = true;
+                if (rho >= 1.0f) {
+                    lim[m] = t1cdf_dev<float>(h < k ? h : k, nu, c[CST_LGB]);
+                } else {
+                    const float v = t1cdf_dev<float>(h, nu, c[CST_LGB]) + t1cdf_dev<float>(k, nu, c[CST_LGB]) - 1.0f;
+                    lim[m] = v > 0.0f ? v : 0.0f;
+                }
+                continue;
+            }
+            const bool graded = fabsf(rho) > 0.99f;
+            // fewer nodes where the integrand is smooth enough (the rule of T2_LO)
+            const bool lo = a.t2n_lo > 0 && !graded && fabsf(rho) < T2_LO_RHO && nu >= T2_LO_DOF_MIN &&
+                            nu <= T2_LO_DOF_MAX;
+            const T2Setup<float> S = t2_setup<float>(h, k, rho, nu, omr2, cr);
+            kind[m] = graded ? 2 : lo ? 0 : 1;
+            np[m] = S.split ? 2 : 1;
+            nodes += (unsigned long long)(np[m] * (kind[m] == 0 ? nlo : kind[m] == 1 ? a.t2n : T2_NH));
+            R[rr] = T2PieceRec{S.anc0, S.phis, S.L0, S.L1, S.d0, S.zs, nu, c[CST_LGB1], r.tab[i], kind[m]};
         }
+        // the chunk's pieces, grouped by node count (kind 0, then 1, then 2)
+        int M = 0;
+#pragma unroll
+        for (int kd = 0; kd < 3; ++kd) {
+            const int cnt = (kind[0] == kd ? np[0] : 0) + (kind[1] == kd ? np[1] : 0);
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < CF_WARP; o <<= 1) {
+                const int v = __shfl_up_sync(CF_FULL, incl, o);
+                if (lane >= o) incl += v;
+            }
+            int pos = M + incl - cnt;
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+                if (kind[m] == kd)
+                    for (int pc = 0; pc < np[m]; ++pc) items[pos++] = (unsigned char)(((lane + m * CF_WARP) << 1) | pc);
+            M += __shfl_sync(CF_FULL, incl, CF_WARP - 1);
+        }
+        __syncwarp();
+        // phase 2: rounds of G pieces, one per group
+        for (int it0 = 0; it0 < M; it0 += G) {
+            const int it = it0 + grp;
+            float acc = 0.0f;
+            int rr = 0, pc = 0;
+            if (it < M) {
+                rr = items[it] >> 1;
+                pc = items[it] & 1;
+                const T2PieceRec& q = R[rr];
+                const int nn = q.kind == 0 ? nlo : q.kind == 1 ? a.t2n : T2_NH;
+                const float* __restrict__ gx = q.kind == 2 ? a.glx32h : q.kind == 0 ? a.glx32l : a.glx32;
+                const float* __restrict__ gw = q.kind == 2 ? a.glw32h : q.kind == 0 ? a.glw32l : a.glw32;
+                const bool graded = q.kind == 2;
+                const float anc = pc ? q.phis : q.anc0;
+                const float Lp = pc ? q.L1 : q.L0;
+                const float d0 = pc ? 0.0f : q.d0;
+                const float num1 = q.nu - 1.0f, nu1 = q.nu + 1.0f;
+                const float2* tab = a.t1tab ? a.t1tab + (size_t)q.tab * T1TAB_N : nullptr;
+                for (int t = sub; t < nn; t += L) {
+                    const float u = gx[t];
+                    const float um = graded ? u * u * u : u;
+                    const float jac = graded ? 3.0f * u * u : 1.0f;
+                    const float off = Lp * um;
+                    const float sp = cf_sin_pi(anc + off);  // both arguments lie in [-pi, pi]
+                    const float sd = cf_sin_pi(d0 + off);
+                    const float z = q.zs * sd;
+                    const float f = ptx_ex2_approx(num1 * ptx_lg2_approx(sp)) *
+                                    (tab ? t1cdf_table(z, tab) : t1cdf_dev<float>(z, nu1, q.lgb1));
+                    acc += gw[t] * jac * f * fabsf(Lp);
+                }
+            }
+            acc = group_sum<L>(acc);
+            if (it < M && sub == 0) P[rr][pc] = acc;
+        }
+        __syncwarp();
+        // phase 3: records lane and lane + 32
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+            const int rr = lane + m * CF_WARP;
+            const long long i = base + rr;
+            if (i >= r.nrec) continue;
+            float v;
+            if (limit[m]) v = lim[m];
+            else v = C2[m] * (np[m] == 2 ? P[rr][0] + P[rr][1] : P[rr][0]);
+            r.res[i] = (double)v;
+            if (r.se) r.se[i] = 0.0;
+        }
+        __syncwarp();
     }
-    if (a.nodes && sub == 0 && nodes) atomicAdd(a.nodes, nodes);
+    if (a.nodes) {
+#pragma unroll
+        for (int o = CF_WARP / 2; o > 0; o >>= 1) nodes += __shfl_xor_sync(CF_FULL, nodes, o);
+        if (lane == 0 && nodes) atomicAdd(a.nodes, nodes);
+    }
 }
 
-// Lanes per FP32 T_2 record (finite dof), a.t2_group in {2, 4, 8, 16}; 32 (or 0: the CFUSN
-// model's records) = the warp-per-record kernel.  Measured at p = 16, q = 2, g = 8,
-// n = 2e6 (3.2e7 records, ~45 nodes each): 14.3 ms with 32 lanes, 9.6 with 16, 7.9 with 8,
-// 7.1 with 4, 6.8 with 2.
+// Lanes per FP32 T_2 piece (finite dof), a.t2_group in {2, 4, 8, 16}; 32 (or 0: the CFUSN
+// model's records) = the warp-per-record kernel.
 template <int L>
 static void go_group(const RecSet& r, const IntegArgs& a, int blocks, cudaStream_t st)
 {
-    // the same warps, each on 32/L records at a time
-    const long long need = (r.nrec + 8LL * (CF_WARP / L) - 1) / (8LL * (CF_WARP / L));
+    const long long per_block = (long long)T2P_WARPS * T2P_CH;
+    const long long need = (r.nrec + per_block - 1) / per_block;
     const int gb = (int)(need < blocks ? need : blocks);
-    t2_records_group_kernel<L><<<gb > 0 ? gb : 1, 256, 0, st>>>(r, a);
+    t2_pieces_kernel<L><<<gb > 0 ? gb : 1, T2P_WARPS * CF_WARP, 0, st>>>(r, a);
 }
 
 cudaError_t launch_t2(const RecSet& r, const IntegArgs& a, int fp32, int blocks, cudaStream_t st)

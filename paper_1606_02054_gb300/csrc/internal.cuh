@@ -185,8 +185,8 @@ struct IntegArgs {
     // T_2 records only (may be null): quadrature nodes evaluated, added once per warp
     // (the profiler's algorithmic work count)
     unsigned long long* nodes;
-    // lanes per FP32 T_2 record of finite dof: 2, 4, 8, 16 (32/L records share a warp) or
-    // 32 (a warp per record; always for the CFUSN model's Phi_2 records)
+    // lanes per FP32 T_2 quadrature piece of finite dof: 2, 4, 8, 16 (a warp's pieces dealt
+    // to its 32/L groups) or 32 (a warp per record; always for the CFUSN model's Phi_2 records)
     int t2_group;
     // lattice points in flight per lane in the FP32 moment pass with the coordinate table
     // (K <= 4): 1 or 2
@@ -226,6 +226,7 @@ struct CombineArgs {
     double* elogu;
     double* eu;
     double* euu;
+    float* pr32;           // mixed form: FP32 pair rows (pr32_width(q) floats) instead of u..euu
     double* se;
     int* fix_count;
     int* fix_list;
@@ -258,6 +259,7 @@ struct EstepArgs {
     double* elogu;
     double* eu;             // g*n*q
     double* euu;            // g*n*q*q
+    float* pr32;            // mixed form: FP32 pair rows in place of u..euu (else null)
     double* se;
     int* flags;
 };
@@ -321,6 +323,7 @@ struct ReduceArgs {
     const double* elogu;
     const double* eu;
     const double* euu;
+    const float* pr32;  // mixed form: FP32 pair rows (read in place of u..euu when set)
     double* tau;       // g*n
     double* partial;   // nblocks x (g*S + 1)
     int chunk;         // observations per block (<= blockDim.x)
@@ -328,6 +331,9 @@ struct ReduceArgs {
     const float* y32;  // FP32 observations (FP32 statistics kernel only)
     int small_only;    // 1: N, U, Snu, Se, See only (Sr, Sre, Srr from the tensor-core kernel)
 };
+
+// floats per pair in the mixed form's FP32 pair rows: u, E log w, eu (q), euu (q x q)
+__host__ __device__ inline int pr32_width(int q) { return 2 + q + q * q; }
 
 size_t reduce_tc_smem(int p, int q, int g);
 bool reduce_tc_fits(int p, int q, int g);

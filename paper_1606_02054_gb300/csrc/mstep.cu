@@ -1,4 +1,4 @@
-// mstep.cu -- M-step solve (S11), one thread per component, FP64.
+// mstep.cu -- M-step solve (S11), one warp per component, FP64.
 //
 // From the statistics of estep_reduce (centred at mu^(k), r = y - mu^(k)):
 //   eq (18)  pi = N / n
@@ -39,13 +39,20 @@ __device__ double nu_eq(double v, double N, double Snu)
 }
 }  // namespace
 
-__global__ void mstep_kernel(Dims D, const double* __restrict__ stats, double nu_min, double nu_max,
-                             const double* __restrict__ mu, const double* __restrict__ Delta,
-                             const double* __restrict__ nu, double* pi_o, double* mu_o,
-                             double* Sigma_o, double* Delta_o, double* nu_o, int* flags,
-                             int* comp_status, const int* gate, int hold)
+__global__ void __launch_bounds__(32) mstep_kernel(Dims D, const double* __restrict__ stats, double nu_min,
+                                                   double nu_max, const double* __restrict__ mu,
+                                                   const double* __restrict__ Delta, const double* __restrict__ nu,
+                                                   double* pi_o, double* mu_o, double* Sigma_o, double* Delta_o,
+                                                   double* nu_o, int* flags, int* comp_status, const int* gate,
+                                                   int hold)
 {
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per component (blockIdx.x); rows and matrix entries over the lanes, each
+    // entry summed in the order of the serial definition
+    __shared__ double delta[CF_MAXP], A[CF_MAXP * CF_MAXQ], Dn[CF_MAXP * CF_MAXQ];
+    __shared__ double Bs[CF_MAXQ * CF_MAXQ], LB[CF_MAXQ * CF_MAXQ];
+    __shared__ double Sn[CF_MAXP * CF_MAXP];
+    __shared__ int fail;
+    const int h = blockIdx.x, lane = threadIdx.x;
     if (h >= D.g) return;
     if (gate && *gate) return;  // a fit captured in a graph has already stopped
     const int p = D.p, q = D.q;
@@ -59,34 +66,43 @@ __global__ void mstep_kernel(Dims D, const double* __restrict__ stats, double nu
     const double* Srr = See + q * q;
     const double* muh = mu + (size_t)h * p;
     const double* Dh = Delta + (size_t)h * p * q;
-    comp_status[h] = 0;
+    if (lane == 0) comp_status[h] = 0;
     if (!(N > 1e-12 * (double)D.n) || !(U > 0.0)) {
-        atomicOr(flags, KF_EMPTY);
-        comp_status[h] = KF_EMPTY;
+        if (lane == 0) {
+            atomicOr(flags, KF_EMPTY);
+            comp_status[h] = KF_EMPTY;
+        }
         return;
     }
-    double delta[CF_MAXP], A[CF_MAXP * CF_MAXQ], Dn[CF_MAXP * CF_MAXQ];
-    for (int i = 0; i < p; ++i) {
+    for (int i = lane; i < p; i += 32) {
         double s = Sr[i];
         for (int k = 0; k < q; ++k) s -= Dh[i * q + k] * Se[k];
         delta[i] = s / U;
     }
-    for (int i = 0; i < p; ++i)
-        for (int k = 0; k < q; ++k) A[i * q + k] = Sre[i * q + k] - delta[i] * Se[k];
-    double Bs[CF_MAXQ * CF_MAXQ], LB[CF_MAXQ * CF_MAXQ];
-    for (int a = 0; a < q; ++a)
-        for (int b = 0; b < q; ++b) Bs[a * q + b] = 0.5 * (See[a * q + b] + See[b * q + a]);
+    __syncwarp();
+    for (int e = lane; e < p * q; e += 32) A[e] = Sre[e] - delta[e / q] * Se[e % q];
+    for (int e = lane; e < q * q; e += 32) {
+        const int a = e / q, b = e % q;
+        Bs[e] = 0.5 * (See[a * q + b] + See[b * q + a]);
+    }
+    __syncwarp();
     const bool hold_delta = hold & CFUST_HOLD_DELTA;
-    if (hold_delta) {
-        // Delta held at Delta^(k): eq (21) below uses it in place of Delta^(k+1)
-        for (int i = 0; i < p * q; ++i) Dn[i] = Dh[i];
-    } else if (!chol_small(q, Bs, LB)) {
-        atomicOr(flags, KF_NOTPD_SEE);
-        comp_status[h] = KF_NOTPD_SEE;
+    if (lane == 0) fail = (!hold_delta && !chol_small(q, Bs, LB)) ? 1 : 0;
+    __syncwarp();
+    if (fail) {
+        if (lane == 0) {
+            atomicOr(flags, KF_NOTPD_SEE);
+            comp_status[h] = KF_NOTPD_SEE;
+        }
         return;
     }
-    // Delta = A See^{-1}: each row solves See x = A_i^T
-    for (int i = 0; i < p && !hold_delta; ++i) {
+    // Delta = A See^{-1}: row i (lane i) solves See x = A_i^T; held: Delta^(k), which
+    // eq (21) below then uses in place of Delta^(k+1)
+    for (int i = lane; i < p; i += 32) {
+        if (hold_delta) {
+            for (int k = 0; k < q; ++k) Dn[i * q + k] = Dh[i * q + k];
+            continue;
+        }
         double zz[CF_MAXQ];
         for (int k = 0; k < q; ++k) {
             double s = A[i * q + k];
@@ -99,50 +115,73 @@ __global__ void mstep_kernel(Dims D, const double* __restrict__ stats, double nu
             Dn[i * q + k] = s / LB[k * q + k];
         }
     }
-    // Sigma (eq 21)
-    double Sn[CF_MAXP * CF_MAXP];
-    for (int i = 0; i < p; ++i)
-        for (int l = 0; l <= i; ++l) {
-            double s = Srr[i * p + l] - Sr[i] * delta[l] - delta[i] * Sr[l] + U * delta[i] * delta[l];
-            for (int k = 0; k < q; ++k) s -= Dn[i * q + k] * A[l * q + k] + A[i * q + k] * Dn[l * q + k];
-            for (int a = 0; a < q; ++a) {
-                double t = 0.0;
-                for (int b = 0; b < q; ++b) t += Bs[a * q + b] * Dn[l * q + b];
-                s += Dn[i * q + a] * t;
-            }
-            Sn[i * p + l] = s / N;
-            Sn[l * p + i] = s / N;
+    __syncwarp();
+    // Sigma (eq 21), lower-triangle entries over the lanes
+    for (int e = lane; e < p * p; e += 32) {
+        const int i = e / p, l = e % p;
+        if (l > i) continue;
+        double s = Srr[i * p + l] - Sr[i] * delta[l] - delta[i] * Sr[l] + U * delta[i] * delta[l];
+        for (int k = 0; k < q; ++k) s -= Dn[i * q + k] * A[l * q + k] + A[i * q + k] * Dn[l * q + k];
+        for (int a = 0; a < q; ++a) {
+            double t = 0.0;
+            for (int b = 0; b < q; ++b) t += Bs[a * q + b] * Dn[l * q + b];
+            s += Dn[i * q + a] * t;
         }
-    double LS[CF_MAXP * CF_MAXP];
-    if (!chol_small(p, Sn, LS)) {
-        atomicOr(flags, KF_NOTPD_SIGMA);
-        comp_status[h] = KF_NOTPD_SIGMA;
-        return;
+        Sn[i * p + l] = s / N;
+        Sn[l * p + i] = s / N;
+    }
+    __syncwarp();
+    // positive definiteness of Sigma: Cholesky, column j at step j, lane i >= j on row i
+    // (the factor itself is not kept: L overwrites a copy in registers' place, W below)
+    __shared__ double W[CF_MAXP * CF_MAXP];
+    for (int e = lane; e < p * p; e += 32) W[e] = Sn[e];
+    __syncwarp();
+    for (int j = 0; j < p; ++j) {
+        double t = 0.0;
+        if (lane >= j && lane < p) {
+            t = W[lane * p + j];
+            for (int k = 0; k < j; ++k) t -= W[lane * p + k] * W[j * p + k];
+        }
+        const double sjj = __shfl_sync(0xffffffffu, t, j);
+        if (!(sjj > 0.0)) {
+            if (lane == 0) {
+                atomicOr(flags, KF_NOTPD_SIGMA);
+                comp_status[h] = KF_NOTPD_SIGMA;
+            }
+            return;
+        }
+        const double dj = sqrt(sjj);
+        __syncwarp();
+        if (lane == j) W[j * p + j] = dj;
+        else if (lane > j && lane < p) W[lane * p + j] = t / dj;
+        __syncwarp();
     }
     // nu (eq 22): F decreasing in nu
-    double vnew;
-    const double flo = nu_eq(nu_min, N, Snu), fhi = nu_eq(nu_max, N, Snu);
-    if (hold & CFUST_HOLD_NU) vnew = nu[h];
-    else if (!(flo > 0.0)) { vnew = nu_min; atomicOr(flags, KF_NUROOT); comp_status[h] = KF_NUROOT; }
-    else if (!(fhi < 0.0)) { vnew = nu_max; atomicOr(flags, KF_NUROOT); comp_status[h] = KF_NUROOT; }
-    else {
-        double lo = nu_min, hi = nu_max;
-        double v = nu[h] > lo && nu[h] < hi ? nu[h] : 0.5 * (lo + hi);
-        for (int it = 0; it < 200; ++it) {
-            const double f = nu_eq(v, N, Snu);
-            if (f > 0.0) lo = v; else hi = v;
-            const double fp = N * (1.0 / v - 0.5 * cf_trigamma(0.5 * v));
-            double vn = v - f / fp;
-            if (!(vn > lo && vn < hi)) vn = 0.5 * (lo + hi);
-            const bool done = fabs(vn - v) <= 1e-14 * v || hi - lo <= 1e-14 * hi;
-            v = vn;
-            if (done) break;
+    if (lane == 0) {
+        double vnew;
+        const double flo = nu_eq(nu_min, N, Snu), fhi = nu_eq(nu_max, N, Snu);
+        if (hold & CFUST_HOLD_NU) vnew = nu[h];
+        else if (!(flo > 0.0)) { vnew = nu_min; atomicOr(flags, KF_NUROOT); comp_status[h] = KF_NUROOT; }
+        else if (!(fhi < 0.0)) { vnew = nu_max; atomicOr(flags, KF_NUROOT); comp_status[h] = KF_NUROOT; }
+        else {
+            double lo = nu_min, hi = nu_max;
+            double v = nu[h] > lo && nu[h] < hi ? nu[h] : 0.5 * (lo + hi);
+            for (int it = 0; it < 200; ++it) {
+                const double f = nu_eq(v, N, Snu);
+                if (f > 0.0) lo = v; else hi = v;
+                const double fp = N * (1.0 / v - 0.5 * cf_trigamma(0.5 * v));
+                double vn = v - f / fp;
+                if (!(vn > lo && vn < hi)) vn = 0.5 * (lo + hi);
+                const bool done = fabs(vn - v) <= 1e-14 * v || hi - lo <= 1e-14 * hi;
+                v = vn;
+                if (done) break;
+            }
+            vnew = v;
         }
-        vnew = v;
+        pi_o[h] = N / (double)D.n;
+        nu_o[h] = vnew;
     }
-    pi_o[h] = N / (double)D.n;
-    for (int i = 0; i < p; ++i) mu_o[(size_t)h * p + i] = muh[i] + delta[i];
-    for (int i = 0; i < p * q; ++i) Delta_o[(size_t)h * p * q + i] = Dn[i];
-    for (int i = 0; i < p * p; ++i) Sigma_o[(size_t)h * p * p + i] = Sn[i];
-    nu_o[h] = vnew;
+    for (int i = lane; i < p; i += 32) mu_o[(size_t)h * p + i] = muh[i] + delta[i];
+    for (int i = lane; i < p * q; i += 32) Delta_o[(size_t)h * p * q + i] = Dn[i];
+    for (int i = lane; i < p * p; i += 32) Sigma_o[(size_t)h * p * p + i] = Sn[i];
 }

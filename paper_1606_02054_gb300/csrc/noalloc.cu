@@ -84,6 +84,7 @@ extern "C" cfust_status cfust_reduce_stats_noalloc(int p, int q, int g, int64_t 
     r.chunk = chunk;
     r.row = row;
     r.y32 = nullptr;
+    r.pr32 = nullptr;
     r.small_only = 0;
     const size_t smem = sizeof(double) * ((size_t)chunk * row + (size_t)g * chunk + chunk + CF_MAXG);
     estep_reduce_kernel<<<nblocks, 256, smem, st>>>(r);

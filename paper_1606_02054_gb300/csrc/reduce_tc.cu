@@ -178,14 +178,16 @@ __global__ void __launch_bounds__(TC_THREADS) estep_reduce_tc_kernel(ReduceArgs 
             const long long j = js + (t % TC_SUB);
             const bool live = t < g * TC_SUB && j < jend;
             pf_tau = live ? (float)a.tau[(size_t)h * n + j] : 0.0f;
-            pf_u = live ? (float)a.u[(size_t)h * n + j] : 0.0f;
+            pf_u = !live ? 0.0f : a.pr32 ? a.pr32[((size_t)h * n + j) * pr32_width(q)] : (float)a.u[(size_t)h * n + j];
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int i = t + u * TC_THREADS;  // (h, jj, k) with k fastest
             const int h = i / (TC_SUB * q), jj = (i / q) % TC_SUB, k = i % q;
             const long long j = js + jj;
-            pf_eu[u] = (i < g * TC_SUB * q && j < jend) ? (float)a.eu[((size_t)h * n + j) * q + k] : 0.0f;
+            pf_eu[u] = !(i < g * TC_SUB * q && j < jend) ? 0.0f
+                     : a.pr32 ? a.pr32[((size_t)h * n + j) * pr32_width(q) + 2 + k]
+                              : (float)a.eu[((size_t)h * n + j) * q + k];
         }
     };
     auto stage = [&]() {

@@ -1,6 +1,6 @@
 // setup.cu -- per-component factors (S0) and the chi table (S1).
 //
-// S0, one thread per component, FP64 (definitions under eq (4)):
+// S0, one warp per component, FP64 (definitions under eq (4)):
 //   Omega = Sigma + Delta Delta^T, L = chol(Omega), Linv = L^{-1},
 //   log|Omega|, A = Linv Delta (so c = A^T Linv (y - mu), d = |Linv (y-mu)|^2),
 //   Lambda = I - Delta^T Omega^{-1} Delta = I - A^T A,
@@ -68,91 +68,113 @@ __device__ void schur_dev(int n, const double* S, int r, double* out, double* mv
 
 }  // namespace
 
-__global__ void setup_components_kernel(Dims D, Layout Ly, const double* mu, const double* Sigma,
-                                        const double* Delta, const double* nu, double* F, int* flags)
+__global__ void __launch_bounds__(32) setup_components_kernel(Dims D, Layout Ly, const double* mu,
+                                                              const double* Sigma, const double* Delta,
+                                                              const double* nu, double* F, int* flags)
 {
-    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per component (blockIdx.x); lane i owns row i (Cholesky, A) or column i
+    // (L^{-1}); every element is summed in the same order as a serial loop would
+    __shared__ double W[CF_MAXP * CF_MAXP];
+    __shared__ double Li[CF_MAXP * CF_MAXP];
+    const int h = blockIdx.x, lane = threadIdx.x;
     if (h >= D.g) return;
     const int p = D.p, q = D.q;
     const double* Sg = Sigma + (size_t)h * p * p;
     const double* Dl = Delta + (size_t)h * p * q;
     double* Fh = F + (size_t)h * Ly.stride;
-    double W[CF_MAXP * CF_MAXP];
 
-    for (int i = 0; i < p; ++i) Fh[Ly.mu + i] = mu[(size_t)h * p + i];
-    // Omega = Sigma + Delta Delta^T, factorised in place (lower triangle of W)
-    for (int i = 0; i < p; ++i)
-        for (int j = 0; j <= i; ++j) {
-            double s = Sg[i * p + j];
-            for (int k = 0; k < q; ++k) s += Dl[i * q + k] * Dl[j * q + k];
-            W[i * p + j] = s;
-        }
+    for (int i = lane; i < p; i += 32) Fh[Ly.mu + i] = mu[(size_t)h * p + i];
+    // Omega = Sigma + Delta Delta^T (lower triangle of W)
+    for (int e = lane; e < p * p; e += 32) {
+        const int i = e / p, j = e % p;
+        if (j > i) continue;
+        double s = Sg[i * p + j];
+        for (int k = 0; k < q; ++k) s += Dl[i * q + k] * Dl[j * q + k];
+        W[i * p + j] = s;
+    }
+    __syncwarp();
+    // L = chol(Omega) in place, column j at step j: lane i >= j forms its row's entry
     double logdet = 0.0;
     for (int j = 0; j < p; ++j) {
-        double s = W[j * p + j];
-        for (int k = 0; k < j; ++k) s -= W[j * p + k] * W[j * p + k];
-        if (!(s > 0.0)) { atomicOr(flags, KF_NOTPD_OMEGA); return; }
-        const double dj = sqrt(s);
-        W[j * p + j] = dj;
-        logdet += 2.0 * log(dj);
-        for (int i = j + 1; i < p; ++i) {
-            double t = W[i * p + j];
-            for (int k = 0; k < j; ++k) t -= W[i * p + k] * W[j * p + k];
-            W[i * p + j] = t / dj;
+        double t = 0.0;
+        if (lane >= j && lane < p) {
+            t = W[lane * p + j];
+            for (int k = 0; k < j; ++k) t -= W[lane * p + k] * W[j * p + k];
         }
+        const double sjj = __shfl_sync(0xffffffffu, t, j);
+        if (!(sjj > 0.0)) {
+            if (lane == 0) atomicOr(flags, KF_NOTPD_OMEGA);
+            return;
+        }
+        const double dj = sqrt(sjj);
+        logdet += 2.0 * log(dj);
+        __syncwarp();
+        if (lane == j) W[j * p + j] = dj;
+        else if (lane > j && lane < p) W[lane * p + j] = t / dj;
+        __syncwarp();
     }
-    // Linv = L^{-1} (forward substitution per column), written to the block
-    double* Li = Fh + Ly.Linv;
-    for (int c = 0; c < p; ++c)
+    // Linv = L^{-1}: lane c forward-substitutes column c
+    for (int c = lane; c < p; c += 32)
         for (int i = 0; i < p; ++i) {
             if (i < c) { Li[i * p + c] = 0.0; continue; }
             double s = (i == c) ? 1.0 : 0.0;
             for (int k = c; k < i; ++k) s -= W[i * p + k] * Li[k * p + c];
             Li[i * p + c] = s / W[i * p + i];
         }
-    // A = Linv Delta
-    double* A = Fh + Ly.A;
-    for (int i = 0; i < p; ++i)
+    __syncwarp();
+    for (int e = lane; e < p * p; e += 32) Fh[Ly.Linv + e] = Li[e];
+    // A = Linv Delta (lane i: row i), into W's upper part is not needed: A goes to Fh and smem
+    __shared__ double As[CF_MAXP * CF_MAXQ];
+    __shared__ double Lam[CF_MAXQ * CF_MAXQ];
+    for (int i = lane; i < p; i += 32)
         for (int k = 0; k < q; ++k) {
             double s = 0.0;
             for (int l = 0; l <= i; ++l) s += Li[i * p + l] * Dl[l * q + k];
-            A[i * q + k] = s;
+            As[i * q + k] = s;
+            Fh[Ly.A + i * q + k] = s;
         }
+    __syncwarp();
     // Lambda = I - A^T A
-    double* Lam = Fh + Ly.Lam;
-    for (int a = 0; a < q; ++a)
-        for (int b = 0; b < q; ++b) {
-            double s = (a == b) ? 1.0 : 0.0;
-            for (int i = 0; i < p; ++i) s -= A[i * q + a] * A[i * q + b];
-            Lam[a * q + b] = s;
-        }
-    const double v = nu[h];
-    Fh[Ly.scal + SC_NU] = v;
-    if (isinf(v)) {  // nu = infinity: the normal density of eq (2) (CFUSN, eq 5); no eq (15)
-        Fh[Ly.scal + SC_LOGTP] = -0.5 * p * log(2.0 * CF_PI) - 0.5 * logdet;
-        Fh[Ly.scal + SC_PSI] = 0.0;
-    } else {
-        Fh[Ly.scal + SC_LOGTP] = lgamma(0.5 * (v + p)) - lgamma(0.5 * v) - 0.5 * p * log(v * CF_PI)
-                               - 0.5 * logdet;
-        Fh[Ly.scal + SC_PSI] = cf_digamma(0.5 * (v + p));
+    for (int e = lane; e < q * q; e += 32) {
+        const int a = e / q, b = e % q;
+        double s = (a == b) ? 1.0 : 0.0;
+        for (int i = 0; i < p; ++i) s -= As[i * q + a] * As[i * q + b];
+        Lam[e] = s;
+        Fh[Ly.Lam + e] = s;
     }
-    Fh[Ly.scal + 3] = 0.0;
-    if (!corr_chol_dev(q, Lam, Fh + Ly.dq, Fh + Ly.Lq)) { atomicOr(flags, KF_NOTPD_LAMBDA); return; }
-    // level 1: Schur complement of Lambda at each r
+    __syncwarp();
+    const double v = nu[h];
+    if (lane == 0) {
+        Fh[Ly.scal + SC_NU] = v;
+        if (isinf(v)) {  // nu = infinity: the normal density of eq (2) (CFUSN, eq 5); no eq (15)
+            Fh[Ly.scal + SC_LOGTP] = -0.5 * p * log(2.0 * CF_PI) - 0.5 * logdet;
+            Fh[Ly.scal + SC_PSI] = 0.0;
+        } else {
+            Fh[Ly.scal + SC_LOGTP] = lgamma(0.5 * (v + p)) - lgamma(0.5 * v) - 0.5 * p * log(v * CF_PI)
+                                   - 0.5 * logdet;
+            Fh[Ly.scal + SC_PSI] = cf_digamma(0.5 * (v + p));
+        }
+        Fh[Ly.scal + 3] = 0.0;
+        if (!corr_chol_dev(q, Lam, Fh + Ly.dq, Fh + Ly.Lq)) atomicOr(flags, KF_NOTPD_LAMBDA);
+    }
+    // level 1: Schur complement of Lambda at each r (lane r), level 2 inside
     const int q1 = q - 1, q2 = q - 2;
-    for (int r = 0; r < q && q1 > 0; ++r) {
+    if (lane < q && q1 > 0) {
+        const int r = lane;
         double* blk = Fh + Ly.l1 + r * Ly.l1s;
         double* mvec = blk;
         double* sch = blk + q1;
         double* dsc = sch + q1 * q1;
         double* Lc = dsc + q1;
         schur_dev(q, Lam, r, sch, mvec);
-        if (!corr_chol_dev(q1, sch, dsc, Lc)) { atomicOr(flags, KF_NOTPD_LAMBDA); return; }
-        // level 2: Schur complement of sch at each s
-        for (int s = 0; s < q1 && q2 > 0; ++s) {
-            double* b2 = Fh + Ly.l2 + (r * q1 + s) * Ly.l2s;
+        if (!corr_chol_dev(q1, sch, dsc, Lc)) {
+            atomicOr(flags, KF_NOTPD_LAMBDA);
+            return;
+        }
+        for (int s2 = 0; s2 < q1 && q2 > 0; ++s2) {
+            double* b2 = Fh + Ly.l2 + (r * q1 + s2) * Ly.l2s;
             double sch2[CF_MAXQ * CF_MAXQ];
-            schur_dev(q1, sch, s, sch2, b2);
+            schur_dev(q1, sch, s2, sch2, b2);
             if (!corr_chol_dev(q2, sch2, b2 + q2, b2 + 2 * q2)) {
                 atomicOr(flags, KF_NOTPD_LAMBDA);
                 return;
