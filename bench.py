@@ -91,10 +91,10 @@ SUB_PLAIN_STEPS = {"learned_p6": 1}
 # build (dram__bytes_read.sum + dram__bytes_write.sum of one launch / its units); None
 # where no capture of the current kernel exists
 TRAFFIC_PER_UNIT = {
-    # t2_records_group_kernel<2>, wide_p16 shape at n = 200,000 (mixed form, 24/32/64 nodes
-    # per piece): 115.28 MB read + 25.81 MB written for 113.49 M nodes; the records (40 B
-    # each: FP32 fields in, FP64 result out) scale with the nodes at any n
-    ("level0_Tq", 2): (115.277824e6 + 25.810176e6) / 113494704,
+    # t2_pieces_kernel<2>, wide_p16 shape at n = 200,000 (mixed form, 24/32/64 nodes per
+    # piece): 115.32 MB read + 22.65 MB written for 113.49 M nodes; the records (FP32 fields
+    # in, FP64 result out) scale with the nodes at any n
+    ("level0_Tq", 2): (115.318272e6 + 22.646016e6) / 113494656,
 }
 
 

@@ -218,18 +218,9 @@ static cfust_status check_flags(cfust_ctx* c, int f, const char* where)
 // Observations per block of the statistics reduction: rows of 4 + p + q + q^2 values
 // (FP32 in the mixed form) plus g posterior weights staged in at most ~64 KB of
 // shared memory, chunk <= 256.  Depends on the sizes and the precision only, not on n.
-// values per staged row of the statistics kernel; odd in the mixed form, whose register
-// tiles read rows rg, rg + RG, ... in the lanes of a warp (an odd stride keeps them in
-// distinct shared-memory banks)
-static int reduce_row(int p, int q, bool mixed)
-{
-    const int row = 4 + p + q + q * q;
-    return mixed ? (row | 1) : row;
-}
-
 static int reduce_chunk(int p, int q, int g, bool mixed)
 {
-    const int row = reduce_row(p, q, mixed);
+    const int row = 4 + p + q + q * q;
     const size_t rowbytes = mixed ? sizeof(float) : sizeof(double);
     int chunk = 256;
     while (chunk > 32 && (size_t)chunk * ((row + g) * rowbytes + sizeof(double)) + CF_MAXG * sizeof(double) > 64 * 1024)
@@ -480,7 +471,7 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     const int S = stats_per_comp(p, q);
     // reduction staging: rows of 4 + p + q + q^2 doubles, chunk <= 256 observations,
     // at most ~64 KB of shared memory
-    c->row = reduce_row(p, q, c->mixed);
+    c->row = 4 + p + q + q * q;
     const int chunk = reduce_chunk(p, q, g, c->mixed);
     c->chunk = chunk;
     c->nblocks_red = (int)((n + chunk - 1) / chunk);
@@ -827,17 +818,17 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
         n0 = c->launches;
         prof_begin(c, CFUST_PROF_SURROGATE);
         if (density_only) {
-            if ((e = sur_infer(c->sur, pa.L0, c->F, 0, c->sur.fall0, c->sur.nfall, c->st)) != cudaSuccess)
+            if ((e = sur_infer(c->sur, pa.L0, c->F, 0, c->sur.fall0, c->sur.nfall, c->flags, c->st)) != cudaSuccess)
                 return fail(c, CFUST_ECUDA, std::string("surrogate kernel: ") + cudaGetErrorString(e));
             ++c->launches;
         } else {
             // moment records first (marking the pairs they leave to the lattice); a level-0
             // record out of range sends its pair to the same list, since the shared lattice
             // pass gives alpha_s as well
-            if ((e = sur_infer(c->sur, c->rec[3], c->F, 1, c->sur.fallM, c->sur.nfall + 1, c->st,
+            if ((e = sur_infer(c->sur, c->rec[3], c->F, 1, c->sur.fallM, c->sur.nfall + 1, c->flags, c->st,
                                c->sur.mark)) != cudaSuccess ||
-                (e = sur_infer(c->sur, pa.L0, c->F, 0, c->sur.fallM, c->sur.nfall + 1, c->st, c->sur.mark)) !=
-                    cudaSuccess)
+                (e = sur_infer(c->sur, pa.L0, c->F, 0, c->sur.fallM, c->sur.nfall + 1, c->flags, c->st,
+                               c->sur.mark)) != cudaSuccess)
                 return fail(c, CFUST_ECUDA, std::string("surrogate kernel: ") + cudaGetErrorString(e));
             c->launches += 2;
         }

@@ -75,21 +75,33 @@ __device__ inline void pair_whiten(const double* F, const Layout& Ly, int p, int
 
 // Mixed precision: the same whitening and log t_p in FP32 from FP32 copies of y
 // and of the factor block.
-__device__ inline void pair_whiten_f32(const float* F32, const Layout& Ly, int p, int q, const float* yj,
+// P > 0: p known at compile time (= P), the loops unrolled and the vectors in registers;
+// P = 0: any p.  The same operations in the same order either way.
+template <int P = 0>
+__device__ inline void pair_whiten_f32(const float* F32, const Layout& Ly, int p_rt, int q, const float* yj,
                                        float* d_out, float* c, float* logtp)
 {
-    float rr[CF_MAXP], z[CF_MAXP];
-    for (int i = 0; i < p; ++i) rr[i] = yj[i] - F32[Ly.mu + i];
+    constexpr int NA = P > 0 ? P : CF_MAXP;
+    const int p = P > 0 ? P : p_rt;
+    float rr[NA], z[NA];
+#pragma unroll
+    for (int i = 0; i < NA; ++i)
+        if (i < p) rr[i] = yj[i] - F32[Ly.mu + i];
     float d = 0.0f;
-    for (int i = 0; i < p; ++i) {
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+        if (i >= p) break;
         float s = 0.0f;
+#pragma unroll
         for (int l = 0; l <= i; ++l) s = fmaf(F32[Ly.Linv + i * p + l], rr[l], s);
         z[i] = s;
         d = fmaf(s, s, d);
     }
     for (int k = 0; k < q; ++k) {
         float s = 0.0f;
-        for (int i = 0; i < p; ++i) s = fmaf(F32[Ly.A + i * q + k], z[i], s);
+#pragma unroll
+        for (int i = 0; i < NA; ++i)
+            if (i < p) s = fmaf(F32[Ly.A + i * q + k], z[i], s);
         c[k] = s;
     }
     const float nu = F32[Ly.scal + SC_NU];

@@ -28,6 +28,7 @@ __device__ __forceinline__ void put_t2f32(const RecSet& L, long long rec, const 
 
 // Mixed form: one pair in FP32 (whitening, log t_p, limits, FP32 T_2 inputs);
 // T_2 records of the FP32 modes need no FP64 fields, the others get them.
+template <int P>
 __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const float* yj)
 {
     const int p = a.D.p, q = a.D.q;
@@ -37,7 +38,7 @@ __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const flo
     const double nu1d = a.F[(size_t)h * a.Ly.stride + a.Ly.scal + SC_NU] + p;
     const float nu1 = F[a.Ly.scal + SC_NU] + p;
     float c[CF_MAXQ], d, logtp, bt[CF_MAXQ];
-    pair_whiten_f32(F, a.Ly, p, q, yj, &d, c, &logtp);
+    pair_whiten_f32<P>(F, a.Ly, p, q, yj, &d, c, &logtp);
     a.pd[2 * pid] = d;
     a.pd[2 * pid + 1] = logtp;
     for (int k = 0; k < q; ++k) a.pc[pid * q + k] = c[k];
@@ -92,30 +93,16 @@ __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const flo
 
 // Mixed form: FP32 pairs in a kernel of their own, so the FP64 path's registers do not
 // limit its occupancy (one kernel for both took 118 registers, 24 % warps active).
-// The block's observation rows are staged in shared memory by coalesced loads (a block's
-// pairs are consecutive observations of one or two components), at an odd row stride so
-// the threads' row reads fall in distinct banks.
-constexpr int PLAN_THREADS = 128;
-__global__ void __launch_bounds__(PLAN_THREADS) plan_kernel_f32(PlanArgs a)
+// P: the dimension p at compile time for common sizes (whitening in registers), 0 for any p
+template <int P>
+__global__ void __launch_bounds__(128) plan_kernel_f32(PlanArgs a)
 {
-    __shared__ float ys[PLAN_THREADS * (CF_MAXP + 1)];
-    const int p = a.D.p, ps = p | 1, t = threadIdx.x;
-    const long long n = a.D.n, np = n * a.D.g;
-    for (long long base = blockIdx.x * (long long)PLAN_THREADS; base < np;
-         base += (long long)gridDim.x * PLAN_THREADS) {
-        const int rows = np - base < PLAN_THREADS ? (int)(np - base) : PLAN_THREADS;
-        __syncthreads();  // the previous rows are read
-        for (int e = t; e < rows * p; e += PLAN_THREADS) {
-            const int r = e / p, i = e - r * p;
-            const long long pid = base + r;
-            const long long j = pid - (pid / n) * n;
-            ys[r * ps + i] = a.y32[(size_t)j * p + i];
-        }
-        __syncthreads();
-        if (t < rows) {
-            const long long pid = base + t;
-            plan_pair_f32(a, pid, (int)(pid / n), ys + t * ps);
-        }
+    const int p = a.D.p;
+    const long long np = a.D.n * a.D.g;
+    for (long long pid = blockIdx.x * (long long)blockDim.x + threadIdx.x; pid < np;
+         pid += (long long)gridDim.x * blockDim.x) {
+        const int h = (int)(pid / a.D.n);
+        plan_pair_f32<P>(a, pid, h, a.y32 + (size_t)(pid - (long long)h * a.D.n) * p);
     }
 }
 
@@ -283,7 +270,17 @@ static int grid_for(long long work, int threads, int cap)
 cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st, long long* launches)
 {
     const long long np = a.D.n * a.D.g;
-    if (a.F32) plan_kernel_f32<<<grid_for(np, PLAN_THREADS, 1 << 20), PLAN_THREADS, 0, st>>>(a);
+    const int gb = grid_for(np, 128, 1 << 20);
+    if (a.F32) {
+        switch (a.D.p) {
+        case 4: plan_kernel_f32<4><<<gb, 128, 0, st>>>(a); break;
+        case 6: plan_kernel_f32<6><<<gb, 128, 0, st>>>(a); break;
+        case 8: plan_kernel_f32<8><<<gb, 128, 0, st>>>(a); break;
+        case 16: plan_kernel_f32<16><<<gb, 128, 0, st>>>(a); break;
+        case 32: plan_kernel_f32<32><<<gb, 128, 0, st>>>(a); break;
+        default: plan_kernel_f32<0><<<gb, 128, 0, st>>>(a); break;
+        }
+    }
     else plan_kernel<<<grid_for(np, 128, 1 << 20), 128, 0, st>>>(a);
     ++*launches;
     return cudaGetLastError();

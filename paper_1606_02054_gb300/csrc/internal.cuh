@@ -368,7 +368,8 @@ struct Surrogate {
     float margin = 0.25f;
     float *theta = nullptr, *grad = nullptr, *am = nullptr, *av = nullptr, *stats = nullptr;
     void* wb = nullptr;          // BF16 row-major copy of theta
-    void* wf = nullptr;          // BF16 weights in mma fragment order (inference)
+    void* wf = nullptr;          // BF16 weights in mma fragment order
+    void* wtc = nullptr;         // BF16 W^T per layer in the tensor-core operand layout (inference)
     // training set
     long long ns = 0, ns_cap = 0;
     float *X = nullptr, *T = nullptr;
@@ -393,5 +394,6 @@ cudaError_t sur_collect(Surrogate& s, const RecSet& L0, const RecSet& LM, const 
 cudaError_t sur_train(Surrogate& s, const SurOpts& o, cudaStream_t st, double* losses);
 // mark (optional): with moments = 1 records which pairs went to the fallback list;
 // with moments = 0 a level-0 record whose pair is marked is not appended again
+// err: device flags, KF_TIMEOUT set if a barrier wait of the kernel ran out
 cudaError_t sur_infer(const Surrogate& s, const RecSet& r, const double* F, int moments, int* fall, int* nfall,
-                      cudaStream_t st, unsigned char* mark = nullptr);
+                      int* err, cudaStream_t st, unsigned char* mark = nullptr);

@@ -9,6 +9,7 @@
 // shared memory in fragment order.
 #include "internal.cuh"
 #include "cfust.h"
+#include "tc_ptx.cuh"
 
 #include <cuda_bf16.h>
 
@@ -620,6 +621,8 @@ __global__ void __launch_bounds__(INF_WARPS * 32, 1) mlp_infer_kernel(InferArgs 
     }
 }
 
+#include "mlp_tc.cuh"
+
 int grid_of(long long work, int threads, int cap)
 {
     long long b = (work + threads - 1) / threads;
@@ -715,6 +718,7 @@ cudaError_t mlp_fwd_bwd(Surrogate& s, int B, int nout, double* loss, cudaStream_
 cudaError_t convert(Surrogate& s, cudaStream_t st)
 {
     mlp_convert_kernel<<<grid_of(MLP_NPARAM, 256, 1024), 256, 0, st>>>(s.theta, (bf16_t*)s.wb, (uint2*)s.wf);
+    mlp_tc_pack_kernel<<<grid_of((long long)(TCI_WTC / 2), 256, 1024), 256, 0, st>>>(s.theta, (bf16_t*)s.wtc);
     return cudaGetLastError();
 }
 
@@ -738,6 +742,7 @@ cudaError_t alloc_params(Surrogate& s)
     if ((e = dalloc(&s.theta, MLP_NPARAM)) || (e = dalloc(&s.grad, MLP_NPARAM)) || (e = dalloc(&s.am, MLP_NPARAM)) ||
         (e = dalloc(&s.av, MLP_NPARAM)) || (e = dalloc(&s.stats, MLP_NSTAT)) ||
         (e = dalloc((bf16_t**)&s.wb, MLP_NPARAM)) || (e = dalloc((bf16_t**)&s.wf, MLP_NPARAM)) ||
+        (e = dalloc((bf16_t**)&s.wtc, TCI_WTC / 2)) ||
         (e = dalloc(&s.nfall, 2)) || (e = dalloc(&s.count, 1)))
         return e;
     return cudaSuccess;
@@ -776,7 +781,8 @@ cudaError_t sur_reserve(Surrogate& s, int q, long long records, cudaStream_t)
     cudaError_t e;
     if ((e = alloc_params(s))) return e;
     // the inference kernel's shared memory (set here, outside any stream capture)
-    if ((e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INFER_SMEM)))
+    if ((e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)INFER_SMEM)) ||
+        (e = cudaFuncSetAttribute(mlp_infer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TCI_SMEM)))
         return e;
     s.q = q;
     s.nin = q + q * (q - 1) / 2 + 1;
@@ -795,7 +801,7 @@ cudaError_t sur_reserve(Surrogate& s, int q, long long records, cudaStream_t)
 
 void sur_free(Surrogate& s)
 {
-    void* ps[] = {s.theta, s.grad, s.am, s.av, s.stats, s.wb, s.wf, s.X, s.T, s.type, s.count, s.xb, s.h1,
+    void* ps[] = {s.theta, s.grad, s.am, s.av, s.stats, s.wb, s.wf, s.wtc, s.X, s.T, s.type, s.count, s.xb, s.h1,
                   s.h2, s.h3, s.dz, s.dz2, s.one, s.y, s.tb, s.mb, s.part, s.lpart, s.fall0, s.fallM, s.nfall,
                   s.mark};
     for (void* p : ps) cudaFree(p);
@@ -937,17 +943,18 @@ cudaError_t sur_train(Surrogate& s, const SurOpts& o, cudaStream_t st, double* l
 }
 
 cudaError_t sur_infer(const Surrogate& s, const RecSet& r, const double* F, int moments, int* fall, int* nfall,
-                      cudaStream_t st, unsigned char* mark)
+                      int* err, cudaStream_t st, unsigned char* mark)
 {
     if (r.nrec == 0) return cudaSuccess;
     InferArgs a;
     a.wf = (const uint2*)s.wf; a.theta = s.theta; a.stats = s.stats; a.margin = s.margin;
     a.q = s.q; a.nin = s.nin; a.nout = s.nout; a.moments = moments;
     a.r = r; a.F = F; a.fall = fall; a.nfall = nfall; a.mark = mark;
-    const long long groups = (r.nrec + INF_WARPS * INF_ROWS - 1) / (INF_WARPS * INF_ROWS);
+    // the tensor-core kernel: one CTA per SM at most, tiles of 128 records
+    const long long tiles = (r.nrec + TCI_M - 1) / TCI_M;
     const int nsm = sm_count();
-    const int blocks = (int)(groups < nsm ? groups : nsm);
-    mlp_infer_kernel<<<blocks, INF_WARPS * 32, INFER_SMEM, st>>>(a);
+    const int blocks = (int)(tiles < nsm ? tiles : nsm);
+    mlp_infer_tc_kernel<<<blocks, TCI_THREADS, TCI_SMEM, st>>>(a, (const bf16_t*)s.wtc, err);
     return cudaGetLastError();
 }
 
@@ -1046,7 +1053,7 @@ extern "C" cfust_status cfust_mlp_records(const float* theta, const float* stats
     cudaStream_t st = nullptr;
     const int W = q + q * (q + 1) / 2;
     double *dbt = nullptr, *dF = nullptr, *ddof = nullptr, *dres = nullptr, *dmom = nullptr;
-    int *dfac = nullptr, *dfall = nullptr;
+    int *dfac = nullptr, *dfall = nullptr, *derr = nullptr;
     cudaError_t e = cudaStreamCreate(&st);
     if (!e) e = alloc_params(s);
     if (!e) e = sur_reserve(s, q, rows, st);
@@ -1057,6 +1064,8 @@ extern "C" cfust_status cfust_mlp_records(const float* theta, const float* stats
     if (!e) e = dalloc(&dmom, (size_t)rows * W);
     if (!e) e = dalloc(&dfac, (size_t)rows);
     if (!e) e = dalloc(&dfall, (size_t)rows);
+    if (!e) e = dalloc(&derr, 1);
+    if (!e) e = cudaMemsetAsync(derr, 0, sizeof(int), st);
     std::vector<int> fac((size_t)rows);
     for (int64_t i = 0; i < rows; ++i) fac[i] = (int)(i * q * q);
     if (!e) e = cudaMemcpyAsync(s.theta, theta, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice, st);
@@ -1071,13 +1080,21 @@ extern "C" cfust_status cfust_mlp_records(const float* theta, const float* stats
     s.margin = margin;
     RecSet r{};
     r.k = q; r.nrec = rows; r.bt = dbt; r.fac = dfac; r.dof = ddof; r.res = dres; r.mom = dmom;
-    if (!e) e = sur_infer(s, r, dF, 1, dfall, s.nfall, st);
+    if (!e) e = sur_infer(s, r, dF, 1, dfall, s.nfall, derr, st);
     std::vector<double> res((size_t)rows);
-    int nf = 0;
+    int nf = 0, herr = 0;
     if (!e) e = cudaMemcpyAsync(res.data(), dres, sizeof(double) * rows, cudaMemcpyDeviceToHost, st);
     if (!e && mom) e = cudaMemcpyAsync(mom, dmom, sizeof(double) * rows * W, cudaMemcpyDeviceToHost, st);
     if (!e) e = cudaMemcpyAsync(&nf, s.nfall, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (!e) e = cudaStreamSynchronize(st);
+    if (!e && herr) {
+        cudaFree(dbt); cudaFree(dF); cudaFree(ddof); cudaFree(dres); cudaFree(dmom); cudaFree(dfac); cudaFree(dfall);
+        cudaFree(derr);
+        sur_free(s);
+        if (st) cudaStreamDestroy(st);
+        return CFUST_ETIMEOUT;
+    }
     std::vector<int> fl;
     if (!e && nf > 0) {
         fl.resize((size_t)nf);
@@ -1094,6 +1111,7 @@ extern "C" cfust_status cfust_mlp_records(const float* theta, const float* stats
         }
     }
     cudaFree(dbt); cudaFree(dF); cudaFree(ddof); cudaFree(dres); cudaFree(dmom); cudaFree(dfac); cudaFree(dfall);
+    cudaFree(derr);
     sur_free(s);
     if (st) cudaStreamDestroy(st);
     return mlp_fail(e);

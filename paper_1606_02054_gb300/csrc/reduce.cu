@@ -58,181 +58,9 @@ __device__ inline void stat_operands(int e, int p, int q, int& ia, int& ib, int&
     if (a != b) o2 = fSrr + b * p + a;
 }
 
-// Mixed form, S9 on the staged FP32 rows by register tiles.  With x = [r (p), 1] every
-// statistic but See, N and Snu is an entry of one of two weighted Gram matrices:
-//   A = sum tau u x x^T (lower triangle): Srr, Sr (row p) and U (entry (p, p));
-//   B = sum tau x eu^T: Sre and Se (row p);
-// and C = sum tau [1, elogu - u, euu (lower)] gives N, Snu and See.  A thread owns a 4 x 4
-// tile of A or B (or 16 entries of C) over the rows rg, rg + RG, ... of the chunk; it adds
-// blocks of 8 rows in plain FP32 into a compensated FP32 sum, the RG row groups' partials
-// are then combined in increasing rg order (compensated) through shared memory, so the
-// result is fixed by (p, q, chunk) alone.
-struct TiledJobs {
-    int n1, nb1, nbq, nC, tA, tB, tC, J;
-};
-
-__host__ __device__ inline TiledJobs tiled_jobs(int p, int q)
-{
-    TiledJobs t;
-    t.n1 = p + 1;
-    t.nb1 = (t.n1 + 3) / 4;
-    t.nbq = (q + 3) / 4;
-    t.nC = 2 + q * (q + 1) / 2;
-    t.tA = t.nb1 * (t.nb1 + 1) / 2;
-    t.tB = t.nb1 * t.nbq;
-    t.tC = (t.nC + 15) / 16;
-    t.J = t.tA + t.tB + t.tC;
-    return t;
-}
-
-// row offset of x_i (r_i for i < p, the constant 1 at i = p), -1 beyond
-__device__ __forceinline__ int tiled_xoff(int i, int p) { return i < p ? 4 + i : i == p ? 3 : -1; }
-
-// (I, J) of lower-triangle tile number t (row-major over I >= J)
-__device__ __forceinline__ void tiled_tri(int t, int& I, int& Jb)
-{
-    I = 0;
-    while ((I + 1) * (I + 2) / 2 <= t) ++I;
-    Jb = t - I * (I + 1) / 2;
-}
-
-// the lower-triangle entry (a, b) of number e in row-major order
-__device__ __forceinline__ void tiled_lower(int e, int& a, int& b)
-{
-    a = 0;
-    while ((a + 1) * (a + 2) / 2 <= e) ++a;
-    b = e - a * (a + 1) / 2;
-}
-
-__device__ void stats_tiled_f32(float* __restrict__ rows, int row, int cap, int cnt, int p, int q,
-                                double* __restrict__ out)
-{
-    const TiledJobs T = tiled_jobs(p, q);
-    const int fSee = 3 + p + q + p * q, fSrr = fSee + q * q;
-    int RG = (int)blockDim.x / T.J;
-    RG = min(RG, cap / (16 * T.J));
-    RG = max(1, min(RG, cnt));
-    const int t = threadIdx.x;
-    const int job = t / RG, rg = t % RG;
-    const bool active = job < T.J && cnt > 0;
-    // operand offsets: outer-product jobs use off[0..3] (a) and off[4..7] (b), the C jobs off[0..15]
-    int off[16];
-    int woff = 0;
-    bool outer = true;
-    if (job < T.tA) {
-        int I, Jb;
-        tiled_tri(job, I, Jb);
-        for (int m = 0; m < 4; ++m) { off[m] = tiled_xoff(4 * I + m, p); off[4 + m] = tiled_xoff(4 * Jb + m, p); }
-        woff = 1;
-    } else if (job < T.tA + T.tB) {
-        const int jb = job - T.tA, I = jb / T.nbq, K = jb % T.nbq;
-        for (int m = 0; m < 4; ++m) {
-            off[m] = tiled_xoff(4 * I + m, p);
-            off[4 + m] = 4 * K + m < q ? 4 + p + 4 * K + m : -1;
-        }
-    } else {
-        outer = false;
-        const int e0 = 16 * (job - T.tA - T.tB);
-        for (int m = 0; m < 16; ++m) {
-            const int e = e0 + m;
-            int a2, b2;
-            tiled_lower(e - 2 > 0 ? e - 2 : 0, a2, b2);
-            off[m] = e == 0 ? 3 : e == 1 ? 2 : e < T.nC ? 4 + p + q + a2 * q + b2 : -1;
-        }
-    }
-    if (outer)
-        for (int m = 8; m < 16; ++m) off[m] = -1;
-    float acc[16], comp[16], tmp[16];
-#pragma unroll
-    for (int m = 0; m < 16; ++m) { acc[m] = 0.0f; comp[m] = 0.0f; tmp[m] = 0.0f; }
-    auto flush = [&]() {
-#pragma unroll
-        for (int m = 0; m < 16; ++m) {
-            const float y = tmp[m] - comp[m];
-            const float tt = acc[m] + y;
-            comp[m] = (tt - acc[m]) - y;
-            acc[m] = tt;
-            tmp[m] = 0.0f;
-        }
-    };
-    if (active) {
-        int k8 = 0;
-        for (int rr = rg; rr < cnt; rr += RG) {
-            const float* rw = rows + (size_t)rr * row;
-            if (outer) {
-                const float w = rw[woff];
-                float av[4], bv[4];
-#pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    av[m] = off[m] >= 0 ? w * rw[off[m]] : 0.0f;
-                    bv[m] = off[4 + m] >= 0 ? rw[off[4 + m]] : 0.0f;
-                }
-#pragma unroll
-                for (int m = 0; m < 4; ++m)
-#pragma unroll
-                    for (int n2 = 0; n2 < 4; ++n2) tmp[4 * m + n2] = fmaf(av[m], bv[n2], tmp[4 * m + n2]);
-            } else {
-                const float w = rw[0];
-#pragma unroll
-                for (int m = 0; m < 16; ++m)
-                    if (off[m] >= 0) tmp[m] = fmaf(w, rw[off[m]], tmp[m]);
-            }
-            if (++k8 == 8) {
-                flush();
-                k8 = 0;
-            }
-        }
-        flush();
-    }
-    __syncthreads();  // the rows are read: their space takes the partials
-    float* part = rows;  // [16 J][RG]
-    if (active)
-#pragma unroll
-        for (int m = 0; m < 16; ++m) part[(job * 16 + m) * RG + rg] = acc[m] - comp[m];
-    __syncthreads();
-    for (int x = t; x < 16 * T.J; x += blockDim.x) {
-        float sacc = 0.0f, scomp = 0.0f;
-        if (cnt > 0)
-            for (int g2 = 0; g2 < RG; ++g2) {
-                const float y = part[x * RG + g2] - scomp;
-                const float tt = sacc + y;
-                scomp = (tt - sacc) - y;
-                sacc = tt;
-            }
-        const double v = (double)sacc;
-        const int jx = x / 16, m = x % 16;
-        int o1 = -1, o2 = -1;
-        if (jx < T.tA) {
-            int I, Jb;
-            tiled_tri(jx, I, Jb);
-            const int i = 4 * I + m / 4, j = 4 * Jb + m % 4;
-            if (i <= p && j <= i) {
-                if (i < p) { o1 = fSrr + i * p + j; if (i != j) o2 = fSrr + j * p + i; }
-                else if (j < p) o1 = 3 + j;
-                else o1 = 1;
-            }
-        } else if (jx < T.tA + T.tB) {
-            const int jb = jx - T.tA, i = 4 * (jb / T.nbq) + m / 4, k = 4 * (jb % T.nbq) + m % 4;
-            if (i <= p && k < q) o1 = i < p ? 3 + p + q + i * q + k : 3 + p + k;
-        } else {
-            const int e = 16 * (jx - T.tA - T.tB) + m;
-            if (e == 0) o1 = 0;
-            else if (e == 1) o1 = 2;
-            else if (e < T.nC) {
-                int a2, b2;
-                tiled_lower(e - 2, a2, b2);
-                o1 = fSee + a2 * q + b2;
-                if (a2 != b2) o2 = fSee + b2 * q + a2;
-            }
-        }
-        if (o1 >= 0) out[o1] = v;
-        if (o2 >= 0) out[o2] = v;
-    }
-}
-
 // T = double: FP64 rows and sums.  T = float (mixed precision): FP32 rows
 // (centred observations from the FP32 copy of y) and compensated FP32 sums
-// per block by register tiles (stats_tiled_f32); tau, l_j and the block partials stay FP64.
+// per block; tau, l_j and the block partials stay FP64.
 template <typename T>
 __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
 {
@@ -342,11 +170,6 @@ __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
             }
         }
         __syncthreads();
-        if (sizeof(T) == sizeof(float) && !a.small_only) {
-            stats_tiled_f32((float*)rows, a.row, a.chunk * a.row, cnt, p, q, out + h * S);
-            __syncthreads();
-            continue;
-        }
         // small_only: N, U, Snu, Se and See (the tensor-core kernel writes Sr, Sre, Srr)
         const int Sred = a.small_only ? 3 + q + q * (q + 1) / 2 : stats_reduced(p, q);
         for (int es = t; es < Sred; es += blockDim.x) {
