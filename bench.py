@@ -95,6 +95,9 @@ TRAFFIC_PER_UNIT = {
     # piece): 115.32 MB read + 22.65 MB written for 113.49 M nodes; the records (FP32 fields
     # in, FP64 result out) scale with the nodes at any n
     ("level0_Tq", 2): (115.318272e6 + 22.646016e6) / 113494656,
+    # lattice_mom_kernel_32<4, 0, 0, 2>, flow_p4 shape at n = 4,000: 1.07 MB read, nothing
+    # written to DRAM, for 131.07 M lattice points (the records, 67 B each, scale with them)
+    ("moments_Tq", 4): 1.070080e6 / 131072000,
 }
 
 
