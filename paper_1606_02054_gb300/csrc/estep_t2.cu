@@ -56,27 +56,40 @@ __global__ void __launch_bounds__(256) t2_records_kernel(RecSet r, IntegArgs a)
 namespace {
 constexpr int T2P_WARPS = 8;
 constexpr int T2P_CH = 2 * CF_WARP;  // records per warp chunk
-struct T2PieceRec {
-    float anc0, phis, L0, L1, d0, zs, nu, lgb1;
-    int tab, kind;  // kind: 0 = t2n_lo nodes, 1 = t2n nodes, 2 = graded (T2_NH nodes)
-};
+// a record's set-up fields, one array per field (consecutive records in distinct banks)
+enum { T2F_ANC0, T2F_PHIS, T2F_L0, T2F_L1, T2F_D0, T2F_ZS, T2F_NU, T2F_LGB1, T2F_N };
+constexpr int T2P_NMAX = 64;  // nodes per piece at most (t2_nodes <= 64, T2_NH = 64)
 }  // namespace
 
 template <int L>
 __global__ void __launch_bounds__(T2P_WARPS * CF_WARP, 4) t2_pieces_kernel(RecSet r, IntegArgs a)
 {
     constexpr int G = CF_WARP / L;
-    __shared__ T2PieceRec srec[T2P_WARPS][T2P_CH];
+    __shared__ float srf[T2P_WARPS][T2F_N][T2P_CH];
+    __shared__ int srt[T2P_WARPS][T2P_CH], srk[T2P_WARPS][T2P_CH];  // table index, kind (0: t2n_lo
+                                                                    // nodes, 1: t2n, 2: graded)
+    __shared__ float sgx[3][T2P_NMAX], sgw[3][T2P_NMAX];            // the node sets by kind
     __shared__ float spsum[T2P_WARPS][T2P_CH][2];
     __shared__ unsigned char sitem[T2P_WARPS][2 * T2P_CH];  // (record << 1) | piece
     const int lane = threadIdx.x & (CF_WARP - 1), wib = threadIdx.x >> 5;
     const int sub = lane & (L - 1), grp = lane / L;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    T2PieceRec* R = srec[wib];
+    float (*Rf)[T2P_CH] = srf[wib];
+    int* Rt = srt[wib];
+    int* Rk = srk[wib];
     float (*P)[2] = spsum[wib];
     unsigned char* items = sitem[wib];
     const int nlo = a.t2n_lo > 0 ? a.t2n_lo : a.t2n;
+    for (int e = threadIdx.x; e < T2P_NMAX; e += blockDim.x) {
+        sgx[0][e] = e < nlo && a.t2n_lo > 0 ? a.glx32l[e] : 0.0f;
+        sgw[0][e] = e < nlo && a.t2n_lo > 0 ? a.glw32l[e] : 0.0f;
+        sgx[1][e] = e < a.t2n ? a.glx32[e] : 0.0f;
+        sgw[1][e] = e < a.t2n ? a.glw32[e] : 0.0f;
+        sgx[2][e] = e < T2_NH ? a.glx32h[e] : 0.0f;
+        sgw[2][e] = e < T2_NH ? a.glw32h[e] : 0.0f;
+    }
+    __syncthreads();
     unsigned long long nodes = 0;  // this lane's records' quadrature nodes (profiler count)
     for (long long base = warp * T2P_CH; base < r.nrec; base += nwarps * T2P_CH) {
         // phase 1: set-up of records lane and lane + 32
@@ -120,7 +133,11 @@ __global__ void __launch_bounds__(T2P_WARPS * CF_WARP, 4) t2_pieces_kernel(RecSe
             kind[m] = graded ? 2 : lo ? 0 : 1;
             np[m] = S.split ? 2 : 1;
             nodes += (unsigned long long)(np[m] * (kind[m] == 0 ? nlo : kind[m] == 1 ? a.t2n : T2_NH));
-            R[rr] = T2PieceRec{S.anc0, S.phis, S.L0, S.L1, S.d0, S.zs, nu, c[CST_LGB1], r.tab[i], kind[m]};
+            Rf[T2F_ANC0][rr] = S.anc0; Rf[T2F_PHIS][rr] = S.phis;
+            Rf[T2F_L0][rr] = S.L0; Rf[T2F_L1][rr] = S.L1;
+            Rf[T2F_D0][rr] = S.d0; Rf[T2F_ZS][rr] = S.zs;
+            Rf[T2F_NU][rr] = nu; Rf[T2F_LGB1][rr] = c[CST_LGB1];
+            Rt[rr] = r.tab[i]; Rk[rr] = kind[m];
         }
         // the chunk's pieces, grouped by node count (kind 0, then 1, then 2)
         int M = 0;
@@ -149,16 +166,17 @@ __global__ void __launch_bounds__(T2P_WARPS * CF_WARP, 4) t2_pieces_kernel(RecSe
             if (it < M) {
                 rr = items[it] >> 1;
                 pc = items[it] & 1;
-                const T2PieceRec& q = R[rr];
-                const int nn = q.kind == 0 ? nlo : q.kind == 1 ? a.t2n : T2_NH;
-                const float* __restrict__ gx = q.kind == 2 ? a.glx32h : q.kind == 0 ? a.glx32l : a.glx32;
-                const float* __restrict__ gw = q.kind == 2 ? a.glw32h : q.kind == 0 ? a.glw32l : a.glw32;
-                const bool graded = q.kind == 2;
-                const float anc = pc ? q.phis : q.anc0;
-                const float Lp = pc ? q.L1 : q.L0;
-                const float d0 = pc ? 0.0f : q.d0;
-                const float num1 = q.nu - 1.0f, nu1 = q.nu + 1.0f;
-                const float2* tab = a.t1tab ? a.t1tab + (size_t)q.tab * T1TAB_N : nullptr;
+                const int kd = Rk[rr];
+                const int nn = kd == 0 ? nlo : kd == 1 ? a.t2n : T2_NH;
+                const float* gx = sgx[kd];
+                const float* gw = sgw[kd];
+                const bool graded = kd == 2;
+                const float anc = pc ? Rf[T2F_PHIS][rr] : Rf[T2F_ANC0][rr];
+                const float Lp = pc ? Rf[T2F_L1][rr] : Rf[T2F_L0][rr];
+                const float d0 = pc ? 0.0f : Rf[T2F_D0][rr];
+                const float zs = Rf[T2F_ZS][rr], nu = Rf[T2F_NU][rr], lgb1 = Rf[T2F_LGB1][rr];
+                const float num1 = nu - 1.0f, nu1 = nu + 1.0f;
+                const float2* tab = a.t1tab ? a.t1tab + (size_t)Rt[rr] * T1TAB_N : nullptr;
                 for (int t = sub; t < nn; t += L) {
                     const float u = gx[t];
                     const float um = graded ? u * u * u : u;
@@ -166,9 +184,9 @@ __global__ void __launch_bounds__(T2P_WARPS * CF_WARP, 4) t2_pieces_kernel(RecSe
                     const float off = Lp * um;
                     const float sp = cf_sin_pi(anc + off);  // both arguments lie in [-pi, pi]
                     const float sd = cf_sin_pi(d0 + off);
-                    const float z = q.zs * sd;
+                    const float z = zs * sd;
                     const float f = ptx_ex2_approx(num1 * ptx_lg2_approx(sp)) *
-                                    (tab ? t1cdf_table(z, tab) : t1cdf_dev<float>(z, nu1, q.lgb1));
+                                    (tab ? t1cdf_table(z, tab) : t1cdf_dev<float>(z, nu1, lgb1));
                     acc += gw[t] * jac * f * fabsf(Lp);
                 }
             }
