@@ -639,29 +639,29 @@ extern "C" cfust_status cfust_set_data(cfust_ctx* c, const void* y, int dtype, i
         return fail(c, CFUST_EINVAL, "cfust_set_data: need y != NULL, ld >= p, dtype F32 or F64");
     CU(cudaSetDevice(c->opts.device));
     const size_t rows = (size_t)c->n, pitch = (size_t)c->p;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    // contiguous rows: one linear copy (a pitched copy of n short rows is far slower)
+    auto copy_rows = [&](void* dst, size_t elem) -> cudaError_t {
+        if ((size_t)ld == pitch) return cudaMemcpyAsync(dst, y, rows * pitch * elem, kind, c->st);
+        return cudaMemcpy2DAsync(dst, pitch * elem, y, (size_t)ld * elem, pitch * elem, rows, kind, c->st);
+    };
+    const long long total = (long long)rows * pitch;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 4LL * c->nsm * 8);
     if (dtype == CFUST_F64) {
-        CU(cudaMemcpy2DAsync(c->y, pitch * sizeof(double), y, (size_t)ld * sizeof(double),
-                             pitch * sizeof(double), rows,
-                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
-    } else {
-        const float* src = (const float*)y;
-        if (!on_device) {
-            if (!c->stage32) CU(dalloc(&c->stage32, rows * pitch));
-            CU(cudaMemcpy2DAsync(c->stage32, pitch * sizeof(float), y, (size_t)ld * sizeof(float),
-                                 pitch * sizeof(float), rows, cudaMemcpyHostToDevice, c->st));
-            src = c->stage32;
-            ld = c->p;
+        CU(copy_rows(c->y, sizeof(double)));
+        if (c->mixed) {  // the FP32 copy, narrowed from the FP64 rows
+            narrow_kernel<<<blocks, 256, 0, c->st>>>(c->y, c->D, c->y32);
+            LAUNCHED();
         }
-        const long long total = (long long)rows * pitch;
-        const int blocks = (int)std::min<long long>((total + 255) / 256, 4LL * c->nsm * 8);
-        widen_kernel<<<blocks, 256, 0, c->st>>>(src, ld, c->D, c->y);
-        LAUNCHED();
-    }
-    if (c->mixed) {
-        // the FP32 copy: narrowed from the FP64 rows (exact for FP32 input)
-        const long long total = (long long)rows * pitch;
-        const int blocks = (int)std::min<long long>((total + 255) / 256, 4LL * c->nsm * 8);
-        narrow_kernel<<<blocks, 256, 0, c->st>>>(c->y, c->D, c->y32);
+    } else {
+        // FP32 rows: into the mixed form's FP32 copy (exact) or a staging buffer, then widened
+        float* dst = c->mixed ? c->y32 : nullptr;
+        if (!dst) {
+            if (!c->stage32) CU(dalloc(&c->stage32, rows * pitch));
+            dst = c->stage32;
+        }
+        CU(copy_rows(dst, sizeof(float)));
+        widen_kernel<<<blocks, 256, 0, c->st>>>(dst, c->p, c->D, c->y);
         LAUNCHED();
     }
     c->have_data = true;
