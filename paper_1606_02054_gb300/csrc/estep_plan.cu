@@ -28,10 +28,10 @@ __device__ __forceinline__ void put_t2f32(const RecSet& L, long long rec, const 
 
 // Mixed form: one pair in FP32 (whitening, log t_p, limits, FP32 T_2 inputs);
 // T_2 records of the FP32 modes need no FP64 fields, the others get them.
-template <int P>
+template <int P, int Q>
 __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const float* yj)
 {
-    const int p = a.D.p, q = a.D.q;
+    const int p = a.D.p, q = Q > 0 ? Q : a.D.q;
     const int m0 = (a.density_only || a.single_pass) ? 1 : 2;
     const float* F = a.F32 + (size_t)h * a.Ly.stride;
     const int foff = h * a.Ly.stride;
@@ -93,8 +93,9 @@ __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const flo
 
 // Mixed form: FP32 pairs in a kernel of their own, so the FP64 path's registers do not
 // limit its occupancy (one kernel for both took 118 registers, 24 % warps active).
-// P: the dimension p at compile time for common sizes (whitening in registers), 0 for any p
-template <int P>
+// P, Q: the dimensions p and q at compile time for common sizes (whitening and limits in
+// registers), 0 for any
+template <int P, int Q>
 __global__ void __launch_bounds__(128) plan_kernel_f32(PlanArgs a)
 {
     const int p = a.D.p;
@@ -102,8 +103,15 @@ __global__ void __launch_bounds__(128) plan_kernel_f32(PlanArgs a)
     for (long long pid = blockIdx.x * (long long)blockDim.x + threadIdx.x; pid < np;
          pid += (long long)gridDim.x * blockDim.x) {
         const int h = (int)(pid / a.D.n);
-        plan_pair_f32<P>(a, pid, h, a.y32 + (size_t)(pid - (long long)h * a.D.n) * p);
+        plan_pair_f32<P, Q>(a, pid, h, a.y32 + (size_t)(pid - (long long)h * a.D.n) * p);
     }
+}
+
+template <int P>
+static void launch_plan_f32(const PlanArgs& a, int gb, cudaStream_t st)
+{
+    if (a.D.q == 2) plan_kernel_f32<P, 2><<<gb, 128, 0, st>>>(a);
+    else plan_kernel_f32<P, 0><<<gb, 128, 0, st>>>(a);
 }
 
 __global__ void __launch_bounds__(128) plan_kernel(PlanArgs a)
@@ -166,7 +174,48 @@ __global__ void __launch_bounds__(128) plan_kernel(PlanArgs a)
     }
 }
 
-// MIXED: the FP32 assembly of the mixed form (its own instantiation, for its registers)
+// The mixed form's recursion-moment pairs (and its density passes): FP32 assembly into the
+// FP32 pair rows, in a kernel of its own (its code and registers only; Q = q at compile time
+// for q = 2, where the moment arrays stay in registers, 0 for any q).
+template <int Q>
+__global__ void __launch_bounds__(128) combine_mixed_kernel(CombineArgs a)
+{
+    const int p = a.D.p, q = Q > 0 ? Q : a.D.q;
+    const long long np = a.D.n * a.D.g;
+    const int m0 = a.density_only ? 1 : 2;
+    const int q1 = q - 1;
+    for (long long pid = blockIdx.x * (long long)blockDim.x + threadIdx.x; pid < np;
+         pid += (long long)gridDim.x * blockDim.x) {
+        const int h = (int)(pid / a.D.n);
+        const double d = a.pd[2 * pid], logtp = a.pd[2 * pid + 1];
+        double c[CF_MAXQ];
+        for (int k = 0; k < q; ++k) c[k] = a.pc[pid * q + k];
+        const double alpha_s = a.L0.res[pid * m0];
+        const double se = a.L0.se ? a.L0.se[pid * m0] : 0.0;
+        if (!(alpha_s >= 1e-35)) {
+            // outside the FP32 range of the lattice products: redo in FP64
+            const int slot = atomicAdd(a.fix_count, 1);
+            a.fix_list[slot] = (int)pid;
+            continue;
+        }
+        const double alpha = a.density_only ? 0.0 : a.L0.res[pid * m0 + 1];
+        double tq1[CF_MAXQ], tq2[Q == 2 ? 1 : CF_MAXQ * CF_MAXQ];
+        if (!a.density_only) {
+            for (int r = 0; r < q && q1 > 0; ++r) tq1[r] = a.L1.res[pid * q + r];
+            if (Q != 2 && q1 > 1)
+                for (int i = 0; i < q * q1; ++i) tq2[i] = a.L2.res[pid * q * q1 + i];
+        }
+        PairOutF of;
+        pair_assemble_f32(a.F32 + (size_t)h * a.Ly.stride, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1, tq2,
+                          a.density_only, a.cst32 + (size_t)(3 * h) * CST_STRIDE, of);
+        a.logf[pid] = of.logf;
+        if (a.se) a.se[pid] = se;
+        if (!(of.logf < INFINITY)) atomicOr(a.flags, KF_NAN);  // NaN or +inf; -inf is a null pair
+        if (!a.density_only) store_pr32(a.pr32 + pid * pr32_width(q), q, of);
+    }
+}
+
+// MIXED: the mixed form's single-pass pairs (FP64 assembly, FP32 rows)
 template <bool MIXED>
 __global__ void __launch_bounds__(128) combine_kernel(CombineArgs a)
 {
@@ -273,12 +322,12 @@ cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st, long long* launches)
     const int gb = grid_for(np, 128, 1 << 20);
     if (a.F32) {
         switch (a.D.p) {
-        case 4: plan_kernel_f32<4><<<gb, 128, 0, st>>>(a); break;
-        case 6: plan_kernel_f32<6><<<gb, 128, 0, st>>>(a); break;
-        case 8: plan_kernel_f32<8><<<gb, 128, 0, st>>>(a); break;
-        case 16: plan_kernel_f32<16><<<gb, 128, 0, st>>>(a); break;
-        case 32: plan_kernel_f32<32><<<gb, 128, 0, st>>>(a); break;
-        default: plan_kernel_f32<0><<<gb, 128, 0, st>>>(a); break;
+        case 4: launch_plan_f32<4>(a, gb, st); break;
+        case 6: launch_plan_f32<6>(a, gb, st); break;
+        case 8: launch_plan_f32<8>(a, gb, st); break;
+        case 16: launch_plan_f32<16>(a, gb, st); break;
+        case 32: launch_plan_f32<32>(a, gb, st); break;
+        default: launch_plan_f32<0>(a, gb, st); break;
         }
     }
     else plan_kernel<<<grid_for(np, 128, 1 << 20), 128, 0, st>>>(a);
@@ -289,8 +338,15 @@ cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st, long long* launches)
 cudaError_t launch_combine(const CombineArgs& a, cudaStream_t st, long long* launches)
 {
     const long long np = a.D.n * a.D.g;
-    if (a.mixed) combine_kernel<true><<<grid_for(np, 128, 1 << 20), 128, 0, st>>>(a);
-    else combine_kernel<false><<<grid_for(np, 128, 1 << 20), 128, 0, st>>>(a);
+    const int gb = grid_for(np, 128, 1 << 20);
+    if (a.mixed && !(a.single_pass && !a.density_only)) {
+        if (a.D.q == 2) combine_mixed_kernel<2><<<gb, 128, 0, st>>>(a);
+        else combine_mixed_kernel<0><<<gb, 128, 0, st>>>(a);
+    } else if (a.mixed) {
+        combine_kernel<true><<<gb, 128, 0, st>>>(a);
+    } else {
+        combine_kernel<false><<<gb, 128, 0, st>>>(a);
+    }
     ++*launches;
     return cudaGetLastError();
 }
