@@ -177,18 +177,23 @@ __global__ void __launch_bounds__(T2P_WARPS * CF_WARP, 4) t2_pieces_kernel(RecSe
                 const float zs = Rf[T2F_ZS][rr], nu = Rf[T2F_NU][rr], lgb1 = Rf[T2F_LGB1][rr];
                 const float num1 = nu - 1.0f, nu1 = nu + 1.0f;
                 const float2* tab = a.t1tab ? a.t1tab + (size_t)Rt[rr] * T1TAB_N : nullptr;
-                for (int t = sub; t < nn; t += L) {
-                    const float u = gx[t];
-                    const float um = graded ? u * u * u : u;
-                    const float jac = graded ? 3.0f * u * u : 1.0f;
-                    const float off = Lp * um;
+                // the node's integrand; the piece's sum is scaled by |L| once, below
+                auto node = [&](float off) {
                     const float sp = cf_sin_pi(anc + off);  // both arguments lie in [-pi, pi]
                     const float sd = cf_sin_pi(d0 + off);
                     const float z = zs * sd;
-                    const float f = ptx_ex2_approx(num1 * ptx_lg2_approx(sp)) *
-                                    (tab ? t1cdf_table(z, tab) : t1cdf_dev<float>(z, nu1, lgb1));
-                    acc += gw[t] * jac * f * fabsf(Lp);
+                    return ptx_ex2_approx(num1 * ptx_lg2_approx(sp)) *
+                           (tab ? t1cdf_table(z, tab) : t1cdf_dev<float>(z, nu1, lgb1));
+                };
+                if (graded) {  // nodes anchor + L u^3, weights 3 u^2
+                    for (int t = sub; t < nn; t += L) {
+                        const float u = gx[t];
+                        acc = fmaf(gw[t] * (3.0f * u * u), node(Lp * (u * u * u)), acc);
+                    }
+                } else {
+                    for (int t = sub; t < nn; t += L) acc = fmaf(gw[t], node(Lp * gx[t]), acc);
                 }
+                acc *= fabsf(Lp);
             }
             acc = group_sum<L>(acc);
             if (it < M && sub == 0) P[rr][pc] = acc;
