@@ -61,7 +61,8 @@ enum { T2F_ANC0, T2F_PHIS, T2F_L0, T2F_L1, T2F_D0, T2F_ZS, T2F_NU, T2F_LGB1, T2F
 constexpr int T2P_NMAX = 64;  // nodes per piece at most (t2_nodes <= 64, T2_NH = 64)
 }  // namespace
 
-template <int L>
+// TAB: the inner T_1 from the per-dof tables (a.t1tab), else by its continued fraction
+template <int L, bool TAB>
 __global__ void __launch_bounds__(T2P_WARPS * CF_WARP, 4) t2_pieces_kernel(RecSet r, IntegArgs a)
 {
     constexpr int G = CF_WARP / L;
@@ -176,14 +177,16 @@ __global__ void __launch_bounds__(T2P_WARPS * CF_WARP, 4) t2_pieces_kernel(RecSe
                 const float d0 = pc ? 0.0f : Rf[T2F_D0][rr];
                 const float zs = Rf[T2F_ZS][rr], nu = Rf[T2F_NU][rr], lgb1 = Rf[T2F_LGB1][rr];
                 const float num1 = nu - 1.0f, nu1 = nu + 1.0f;
-                const float2* tab = a.t1tab ? a.t1tab + (size_t)Rt[rr] * T1TAB_N : nullptr;
+                const float2* tab = TAB ? a.t1tab + (size_t)Rt[rr] * T1TAB_N : nullptr;
                 // the node's integrand; the piece's sum is scaled by |L| once, below
                 auto node = [&](float off) {
                     const float sp = cf_sin_pi(anc + off);  // both arguments lie in [-pi, pi]
                     const float sd = cf_sin_pi(d0 + off);
                     const float z = zs * sd;
-                    return ptx_ex2_approx(num1 * ptx_lg2_approx(sp)) *
-                           (tab ? t1cdf_table(z, tab) : t1cdf_dev<float>(z, nu1, lgb1));
+                    float t1;
+                    if constexpr (TAB) t1 = t1cdf_table(z, tab);
+                    else t1 = t1cdf_dev<float>(z, nu1, lgb1);
+                    return ptx_ex2_approx(num1 * ptx_lg2_approx(sp)) * t1;
                 };
                 if (graded) {  // nodes anchor + L u^3, weights 3 u^2
                     for (int t = sub; t < nn; t += L) {
@@ -228,7 +231,8 @@ static void go_group(const RecSet& r, const IntegArgs& a, int blocks, cudaStream
     const long long per_block = (long long)T2P_WARPS * T2P_CH;
     const long long need = (r.nrec + per_block - 1) / per_block;
     const int gb = (int)(need < blocks ? need : blocks);
-    t2_pieces_kernel<L><<<gb > 0 ? gb : 1, T2P_WARPS * CF_WARP, 0, st>>>(r, a);
+    if (a.t1tab) t2_pieces_kernel<L, true><<<gb > 0 ? gb : 1, T2P_WARPS * CF_WARP, 0, st>>>(r, a);
+    else t2_pieces_kernel<L, false><<<gb > 0 ? gb : 1, T2P_WARPS * CF_WARP, 0, st>>>(r, a);
 }
 
 cudaError_t launch_t2(const RecSet& r, const IntegArgs& a, int fp32, int blocks, cudaStream_t st)
