@@ -84,6 +84,7 @@ struct cfust_ctx {
     float* y32 = nullptr;
     float* F32 = nullptr;
     float* pr32 = nullptr;  // FP32 pair rows (u, E log w, eu, euu) written by the mixed E-step
+    float *pd32 = nullptr, *pc32 = nullptr;  // mixed form: d, log t_p and c in FP32
     // E-step pipeline: per-pair (d, log t_p) and c, integral records per level
     double *pd = nullptr, *pc = nullptr;
     RecSet rec[4]{};  // levels 0, 1, 2 and the single-pass moment records
@@ -363,7 +364,7 @@ static void free_all(cfust_ctx* c)
                     c->glx64, c->glw64, c->glx32, c->glw32, c->glx32h, c->glw32h, c->glx32l, c->glw32l,
                     c->logf, c->u, c->elogu, c->eu,
                     c->euu, c->se, c->tau, c->partial, c->stats, c->flags, c->comp_status,
-                    c->stage32, c->pd, c->pc, c->fix_count, c->fix_list, c->y32, c->F32, c->pr32, c->t1tab,
+                    c->stage32, c->pd, c->pc, c->fix_count, c->fix_list, c->y32, c->F32, c->pr32, c->pd32, c->pc32, c->t1tab,
                     c->work_dev, c->seg, c->lchi64, c->lchi32};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -519,6 +520,7 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
         ALLOC(y32, (size_t)n * p);
         ALLOC(F32, (size_t)g * c->Ly.stride);
         ALLOC(pr32, ng * pr32_width(q));
+        ALLOC(pd32, 2 * ng); ALLOC(pc32, ng * q);
     }
     ALLOC(fix_count, 1); ALLOC(fix_list, ng);
     // T_2 records exist at q = 2 (level 0) and, in the recursion form, at q = 3, 4 (levels 1, 2)
@@ -800,6 +802,7 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
     pa.F32 = c->mixed ? c->F32 : nullptr;
     pa.single_pass = sp;
     pa.pd = c->pd; pa.pc = c->pc;
+    pa.pd32 = c->mixed ? c->pd32 : nullptr; pa.pc32 = c->mixed ? c->pc32 : nullptr;
     pa.L0 = c->rec[0]; pa.L1 = c->rec[1]; pa.L2 = c->rec[2]; pa.LM = c->rec[3];
     if (density_only || sp) pa.L0.nrec = c->n * c->g;
     cudaError_t e;
@@ -876,6 +879,7 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
     if (fp32) CU(cudaMemsetAsync(c->fix_count, 0, sizeof(int), c->st));
     CombineArgs ca;
     ca.D = c->D; ca.Ly = c->Ly; ca.cst64 = c->cst64; ca.cst32 = c->cst32; ca.F = c->F; ca.pd = c->pd; ca.pc = c->pc;
+    ca.pd32 = c->mixed ? c->pd32 : nullptr; ca.pc32 = c->mixed ? c->pc32 : nullptr;
     ca.F32 = c->mixed ? c->F32 : nullptr;
     ca.L0 = pa.L0; ca.L1 = c->rec[1]; ca.L2 = c->rec[2]; ca.LM = c->rec[3];
     ca.density_only = density_only; ca.single_pass = sp; ca.fp32 = fp32;

@@ -317,17 +317,17 @@ __device__ inline void pair_assemble_sp(const double* F, const Layout& Ly, int p
 // FP64 run on GB300's FP64 pipe, 1/64 of the FP32 rate: the per-component values are read
 // from their FP32 copies).
 __device__ inline void pair_assemble_f32(const float* F, const Layout& Ly, int p, int q,
-                                         const double* cd, double dd, double logtp, double alpha_s_d,
+                                         const float* cf, float d, float logtp, double alpha_s_d,
                                          double alpha_d, const double* tq1, const double* tq2,
                                          int density_only, const float* cst, PairOutF& o)
 {
     const float alpha_s = (float)alpha_s_d;
     if (!(alpha_s > 0.0f)) return pair_null(q, density_only, o);
-    o.logf = q * 0.6931471805599453 + logtp + (double)logf(alpha_s);  // eq (4)
+    o.logf = q * 0.6931471805599453 + (double)logtp + (double)logf(alpha_s);  // eq (4)
     if (density_only) return;
-    const float nu = F[Ly.scal + SC_NU], nu1 = nu + (float)p, d = (float)dd;
+    const float nu = F[Ly.scal + SC_NU], nu1 = nu + (float)p;
     float c[CF_MAXQ];
-    for (int k = 0; k < q; ++k) c[k] = (float)cd[k];
+    for (int k = 0; k < q; ++k) c[k] = cf[k];
     const bool nrm = isinf(nu);  // the normal limit (eq 5): u = 1, every t scaling is 1
     const float u = nrm ? 1.0f : nu1 / (nu + d) * (float)alpha_d / alpha_s;  // eq (13)
     o.u = u;

@@ -39,9 +39,9 @@ __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const flo
     const float nu1 = F[a.Ly.scal + SC_NU] + p;
     float c[CF_MAXQ], d, logtp, bt[CF_MAXQ];
     pair_whiten_f32<P>(F, a.Ly, p, q, yj, &d, c, &logtp);
-    a.pd[2 * pid] = d;
-    a.pd[2 * pid + 1] = logtp;
-    for (int k = 0; k < q; ++k) a.pc[pid * q + k] = c[k];
+    a.pd32[2 * pid] = d;
+    a.pd32[2 * pid + 1] = logtp;
+    for (int k = 0; k < q; ++k) a.pc32[pid * q + k] = c[k];
     for (int w = 0; w < m0; ++w) {
         const long long rec = pid * m0 + w;
         limits_l0<float>(F, a.Ly, p, q, c, d, w, bt);
@@ -187,9 +187,9 @@ __global__ void __launch_bounds__(128) combine_mixed_kernel(CombineArgs a)
     for (long long pid = blockIdx.x * (long long)blockDim.x + threadIdx.x; pid < np;
          pid += (long long)gridDim.x * blockDim.x) {
         const int h = (int)(pid / a.D.n);
-        const double d = a.pd[2 * pid], logtp = a.pd[2 * pid + 1];
-        double c[CF_MAXQ];
-        for (int k = 0; k < q; ++k) c[k] = a.pc[pid * q + k];
+        const float d = a.pd32[2 * pid], logtp = a.pd32[2 * pid + 1];
+        float c[CF_MAXQ];
+        for (int k = 0; k < q; ++k) c[k] = a.pc32[pid * q + k];
         const double alpha_s = a.L0.res[pid * m0];
         const double se = a.L0.se ? a.L0.se[pid * m0] : 0.0;
         if (!(alpha_s >= 1e-35)) {
@@ -228,9 +228,16 @@ __global__ void __launch_bounds__(128) combine_kernel(CombineArgs a)
          pid += (long long)gridDim.x * blockDim.x) {
         const int h = (int)(pid / a.D.n);
         const double* F = a.F + (size_t)h * a.Ly.stride;
-        const double d = a.pd[2 * pid], logtp = a.pd[2 * pid + 1];
-        double c[CF_MAXQ];
-        for (int k = 0; k < q; ++k) c[k] = a.pc[pid * q + k];
+        double d, logtp, c[CF_MAXQ];
+        if (MIXED) {
+            d = a.pd32[2 * pid];
+            logtp = a.pd32[2 * pid + 1];
+            for (int k = 0; k < q; ++k) c[k] = a.pc32[pid * q + k];
+        } else {
+            d = a.pd[2 * pid];
+            logtp = a.pd[2 * pid + 1];
+            for (int k = 0; k < q; ++k) c[k] = a.pc[pid * q + k];
+        }
         const double alpha_s = a.L0.res[pid * m0];
         const double se = a.L0.se ? a.L0.se[pid * m0] : 0.0;
         if (a.fp32 && !(alpha_s >= 1e-35)) {
@@ -238,26 +245,6 @@ __global__ void __launch_bounds__(128) combine_kernel(CombineArgs a)
             const int slot = atomicAdd(a.fix_count, 1);
             a.fix_list[slot] = (int)pid;
             continue;
-        }
-        if constexpr (MIXED) {
-            if (!(a.single_pass && !a.density_only)) {
-                // FP32 assembly straight into the FP32 pair row
-                const double alpha = a.density_only ? 0.0 : a.L0.res[pid * m0 + 1];
-                double tq1[CF_MAXQ], tq2[CF_MAXQ * CF_MAXQ];
-                if (!a.density_only) {
-                    for (int r = 0; r < q && q1 > 0; ++r) tq1[r] = a.L1.res[pid * q + r];
-                    if (q1 > 1)
-                        for (int i = 0; i < q * q1; ++i) tq2[i] = a.L2.res[pid * q * q1 + i];
-                }
-                PairOutF of;
-                pair_assemble_f32(a.F32 + (size_t)h * a.Ly.stride, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1,
-                                  tq2, a.density_only, a.cst32 + (size_t)(3 * h) * CST_STRIDE, of);
-                a.logf[pid] = of.logf;
-                if (a.se) a.se[pid] = se;
-                if (!(of.logf < INFINITY)) atomicOr(a.flags, KF_NAN);  // NaN or +inf; -inf is a null pair
-                if (!a.density_only) store_pr32(a.pr32 + pid * pr32_width(q), q, of);
-                continue;
-            }
         }
         PairOut o;
         if (a.single_pass && !a.density_only) {

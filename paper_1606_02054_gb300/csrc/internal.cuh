@@ -140,6 +140,8 @@ struct PlanArgs {
     int single_pass;       // moments by ratio estimators (q >= 3): records LM instead of alpha/L1/L2
     double* pd;        // per pair: d, log t_p
     double* pc;        // per pair: c (q)
+    float* pd32;       // mixed form: the same in FP32 (written instead of pd, pc)
+    float* pc32;
     RecSet L0, L1, L2, LM;
 };
 
@@ -216,6 +218,8 @@ struct CombineArgs {
     const float* F32;      // mixed form: FP32 copies of the factor blocks (else null)
     const double* pd;
     const double* pc;
+    const float* pd32;     // mixed form: d, log t_p and c in FP32 (read instead of pd, pc)
+    const float* pc32;
     RecSet L0, L1, L2, LM;
     int density_only;
     int single_pass;
