@@ -39,17 +39,19 @@ __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const flo
     const float nu1 = F[a.Ly.scal + SC_NU] + p;
     float c[CF_MAXQ], d, logtp, bt[CF_MAXQ];
     pair_whiten_f32<P>(F, a.Ly, p, q, yj, &d, c, &logtp);
-    a.pd32[2 * pid] = d;
-    a.pd32[2 * pid + 1] = logtp;
-    for (int k = 0; k < q; ++k) a.pc32[pid * q + k] = c[k];
+    reinterpret_cast<float2*>(a.pd32)[pid] = make_float2(d, logtp);
+    if (Q == 2) reinterpret_cast<float2*>(a.pc32)[pid] = make_float2(c[0], c[1]);
+    else for (int k = 0; k < q; ++k) a.pc32[pid * q + k] = c[k];
+    // a record gets the fields its integrator reads: FP32 T_2 records their FP32 fields and
+    // table index, T_1 records no factor
     for (int w = 0; w < m0; ++w) {
         const long long rec = pid * m0 + w;
         limits_l0<float>(F, a.Ly, p, q, c, d, w, bt);
-        a.L0.fac[rec] = foff + fac_l0(a.Ly);
         a.L0.tab[rec] = 3 * h + 2 * w;
         if (q == 2 && a.L0.t2f) {
             put_t2f32(a.L0, rec, bt, F + fac_l0(a.Ly), nu1 + 2.0f * w);
         } else {
+            a.L0.fac[rec] = foff + fac_l0(a.Ly);
             for (int k = 0; k < q; ++k) a.L0.bt[rec * q + k] = bt[k];
             a.L0.dof[rec] = nu1d + 2.0 * w;
         }
@@ -68,22 +70,22 @@ __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const flo
     for (int r = 0; r < q && q1 > 0; ++r) {
         const long long rec = pid * q + r;
         limits_l1<float>(F, a.Ly, p, q, c, d, r, bt);
-        a.L1.fac[rec] = foff + fac_l1(a.Ly, q, r);
         a.L1.tab[rec] = 3 * h + 1;
         if (q1 == 2 && a.L1.t2f) {
             put_t2f32(a.L1, rec, bt, F + fac_l1(a.Ly, q, r), nu1 + 1.0f);
         } else {
+            if (q1 >= 2) a.L1.fac[rec] = foff + fac_l1(a.Ly, q, r);
             for (int k = 0; k < q1; ++k) a.L1.bt[rec * q1 + k] = bt[k];
             a.L1.dof[rec] = nu1d + 1.0;
         }
         for (int s = 0; s < q1 && q2 > 0; ++s) {
             const long long r2 = pid * q * q1 + r * q1 + s;
             limits_l2<float>(F, a.Ly, p, q, c, d, r, s, bt);
-            a.L2.fac[r2] = foff + fac_l2(a.Ly, q, r, s);
             a.L2.tab[r2] = 3 * h;
             if (q2 == 2 && a.L2.t2f) {
                 put_t2f32(a.L2, r2, bt, F + fac_l2(a.Ly, q, r, s), nu1);
             } else {
+                if (q2 >= 2) a.L2.fac[r2] = foff + fac_l2(a.Ly, q, r, s);
                 for (int k = 0; k < q2; ++k) a.L2.bt[r2 * q2 + k] = bt[k];
                 a.L2.dof[r2] = nu1d;
             }
@@ -187,9 +189,16 @@ __global__ void __launch_bounds__(128) combine_mixed_kernel(CombineArgs a)
     for (long long pid = blockIdx.x * (long long)blockDim.x + threadIdx.x; pid < np;
          pid += (long long)gridDim.x * blockDim.x) {
         const int h = (int)(pid / a.D.n);
-        const float d = a.pd32[2 * pid], logtp = a.pd32[2 * pid + 1];
+        const float2 dl = reinterpret_cast<const float2*>(a.pd32)[pid];
+        const float d = dl.x, logtp = dl.y;
         float c[CF_MAXQ];
-        for (int k = 0; k < q; ++k) c[k] = a.pc32[pid * q + k];
+        if (Q == 2) {
+            const float2 c2 = reinterpret_cast<const float2*>(a.pc32)[pid];
+            c[0] = c2.x;
+            c[1] = c2.y;
+        } else {
+            for (int k = 0; k < q; ++k) c[k] = a.pc32[pid * q + k];
+        }
         const double alpha_s = a.L0.res[pid * m0];
         const double se = a.L0.se ? a.L0.se[pid * m0] : 0.0;
         if (!(alpha_s >= 1e-35)) {
