@@ -219,9 +219,12 @@ static cfust_status check_flags(cfust_ctx* c, int f, const char* where)
 // Observations per block of the statistics reduction: rows of 4 + p + q + q^2 values
 // (FP32 in the mixed form) plus g posterior weights staged in at most ~64 KB of
 // shared memory, chunk <= 256.  Depends on the sizes and the precision only, not on n.
+// values per staged row of the statistics kernel (FP32 rows also hold tau u r: p more)
+static int reduce_row(int p, int q, bool mixed) { return 4 + p + q + q * q + (mixed ? p : 0); }
+
 static int reduce_chunk(int p, int q, int g, bool mixed)
 {
-    const int row = 4 + p + q + q * q;
+    const int row = reduce_row(p, q, mixed);
     const size_t rowbytes = mixed ? sizeof(float) : sizeof(double);
     int chunk = 256;
     while (chunk > 32 && (size_t)chunk * ((row + g) * rowbytes + sizeof(double)) + CF_MAXG * sizeof(double) > 64 * 1024)
@@ -472,7 +475,7 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     const int S = stats_per_comp(p, q);
     // reduction staging: rows of 4 + p + q + q^2 doubles, chunk <= 256 observations,
     // at most ~64 KB of shared memory
-    c->row = 4 + p + q + q * q;
+    c->row = reduce_row(p, q, c->mixed);
     const int chunk = reduce_chunk(p, q, g, c->mixed);
     c->chunk = chunk;
     c->nblocks_red = (int)((n + chunk - 1) / chunk);

@@ -14,9 +14,10 @@
 
 
 
-// Staged row of one observation for component h:
+// Staged FP64 row of one observation for component h:
 //   [0] tau, [1] tau*u, [2] elogu - u, [3] 1, [4..4+p) r, then eu (q), euu (q*q).
-// Each statistic is the sum over the chunk of row[ia]*row[ib]*row[ic].  The
+// Each statistic is the sum over the chunk of row[ia]*row[ib]*row[ic] (the FP32 rows:
+// stat_operands_w below).  The
 // symmetric See and Srr are computed for their lower triangles only
 // (stats_reduced(p, q) statistics) and written to both positions o1, o2 of the
 // full layout (o2 = -1 when there is one).
@@ -54,6 +55,41 @@ __device__ inline void stat_operands(int e, int p, int q, int& ia, int& ib, int&
     while ((a + 1) * (a + 2) / 2 <= e) ++a;                                   // Srr (lower)
     const int b = e - a * (a + 1) / 2;
     ia = 1; ib = R0 + a; ic = R0 + b;
+    o1 = fSrr + a * p + b;
+    if (a != b) o2 = fSrr + b * p + a;
+}
+
+// The FP32 rows hold the weighted vectors too: [0] tau, [1] tau u, [2] tau (elogu - u),
+// [3] 1, then r (p), tau u r (p), tau eu (q), tau euu (q*q), so that every statistic is the
+// sum over the chunk of row[ia] * row[ib] (two operands instead of three).
+__device__ inline void stat_operands_w(int e, int p, int q, int& ia, int& ib, int& o1, int& o2)
+{
+    const int R0 = 4, WR0 = 4 + p, E0 = 4 + 2 * p, EE0 = 4 + 2 * p + q;
+    const int fSee = 3 + p + q + p * q, fSrr = fSee + q * q;
+    o2 = -1;
+    ib = 3;
+    if (e < 3) { ia = e; o1 = e; return; }                                       // N, U, Snu
+    o1 = e;
+    e -= 3;
+    if (e < p) { ia = WR0 + e; return; }                                         // Sr
+    e -= p;
+    if (e < q) { ia = E0 + e; return; }                                          // Se
+    e -= q;
+    if (e < p * q) { ia = R0 + e / q; ib = E0 + e % q; return; }                 // Sre
+    e -= p * q;
+    int a = 0;
+    if (e < q * (q + 1) / 2) {                                                   // See (lower)
+        while ((a + 1) * (a + 2) / 2 <= e) ++a;
+        const int b = e - a * (a + 1) / 2;
+        ia = EE0 + a * q + b;
+        o1 = fSee + a * q + b;
+        if (a != b) o2 = fSee + b * q + a;
+        return;
+    }
+    e -= q * (q + 1) / 2;
+    while ((a + 1) * (a + 2) / 2 <= e) ++a;                                      // Srr (lower)
+    const int b = e - a * (a + 1) / 2;
+    ia = WR0 + a; ib = R0 + b;
     o1 = fSrr + a * p + b;
     if (a != b) o2 = fSrr + b * p + a;
 }
@@ -141,7 +177,7 @@ __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
                     const T tv = taus[h * a.chunk + t];
                     rw[0] = tv;
                     rw[1] = tv * (T)pr[0];
-                    rw[2] = (T)pr[1] - (T)pr[0];
+                    rw[2] = tv * ((T)pr[1] - (T)pr[0]);
                 } else {
                     const double tv = (double)taus[h * a.chunk + t];
                     const double uv = a.u[pid];
@@ -154,13 +190,17 @@ __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
                     // r is not read
                 } else if (sizeof(T) == sizeof(float)) {
                     const float* yj = a.y32 + (size_t)(j0 + t) * p;
-                    for (int i = 0; i < p; ++i) rw[4 + i] = (T)(yj[i] - mu32[h * p + i]);
+                    for (int i = 0; i < p; ++i) {
+                        const T ri = (T)(yj[i] - mu32[h * p + i]);
+                        rw[4 + i] = ri;
+                        rw[4 + p + i] = rw[1] * ri;
+                    }
                 } else {
                     const double* yj = a.y + (size_t)(j0 + t) * p;
                     for (int i = 0; i < p; ++i) rw[4 + i] = (T)(yj[i] - a.mu[(size_t)h * p + i]);
                 }
                 if (pr) {
-                    for (int k = 0; k < q + q * q; ++k) rw[4 + p + k] = (T)pr[2 + k];
+                    for (int k = 0; k < q + q * q; ++k) rw[4 + 2 * p + k] = rw[0] * (T)pr[2 + k];
                 } else {
                     for (int k = 0; k < q; ++k) rw[4 + p + k] = (T)a.eu[pid * q + k];
                     for (int k = 0; k < q * q; ++k) rw[4 + p + q + k] = (T)a.euu[pid * q * q + k];
@@ -175,17 +215,18 @@ __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
         for (int es = t; es < Sred; es += blockDim.x) {
             const int e = !a.small_only || es < 3 ? es : es < 3 + q ? 3 + p + (es - 3) : 3 + p + q + p * q + (es - 3 - q);
             int ia, ib, ic, o1, o2;
-            stat_operands(e, p, q, ia, ib, ic, o1, o2);
             T acc = T(0), comp = T(0);
             if (sizeof(T) == sizeof(float)) {
+                stat_operands_w(e, p, q, ia, ib, o1, o2);
                 for (int jj = 0; jj < cnt; ++jj) {
                     const T* rw = rows + (size_t)jj * a.row;
-                    const T v = rw[ia] * rw[ib] * rw[ic] - comp;  // compensated FP32 sum
+                    const T v = fmaf(rw[ia], rw[ib], -comp);  // compensated FP32 sum
                     const T tt = acc + v;
                     comp = (tt - acc) - v;
                     acc = tt;
                 }
             } else {
+                stat_operands(e, p, q, ia, ib, ic, o1, o2);
                 for (int jj = 0; jj < cnt; ++jj) {
                     const T* rw = rows + (size_t)jj * a.row;
                     acc += rw[ia] * rw[ib] * rw[ic];
