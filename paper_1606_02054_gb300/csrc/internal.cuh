@@ -177,7 +177,7 @@ struct IntegArgs {
     const float* glx32l;
     const float* glw32l;
     // FP32 T_2: per tab, log2 T_1(-|z|; dof + 1) on the grid of T1TAB_N points
-    // uniform in v = asinh(|z|)/ln 2 over [0, T1TAB_V], with d/dv (float2 each);
+    // uniform in v = log2(1 + |z|) over [0, T1TAB_V], with d/dv (float2 each);
     // NULL: the continued fraction is used instead
     const float2* t1tab;
     // FP32 single-pass moments at q <= 4 (else null): per shift m and lattice point i, the

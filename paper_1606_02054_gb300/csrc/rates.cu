@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kThreads) mix_rate_kernel(float* out, int iter
 
 // One node of the FP32 T_2 quadrature, per node: the two sines of the angle
 // (cf_sin_pi), the weight sin^(nu-1) (lg2, ex2), the inner T_1 from a per-dof table
-// (t1cdf_table: asinh by lg2 and sqrt, cubic Hermite, ex2) and the weighted sum; two
+// (t1cdf_table: log2(1 + |z|) by lg2, cubic Hermite, ex2) and the weighted sum; two
 // independent nodes per thread, angles advancing by a fixed step, the table L1-resident.
 template <int P>
 __global__ void __launch_bounds__(kThreads) t2node_rate_kernel(float* out, const float2* __restrict__ tab, int iters)

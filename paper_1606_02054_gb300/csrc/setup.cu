@@ -291,7 +291,8 @@ static __device__ double log_t1_lower(double w, double nu)
     return log1p(-exp(lbt) * betacf_dev<double>(b, a, y) / b) - CF_LN2;
 }
 
-// Tables of log2 T_1(-|z|; dofs[t] + 1) and d/dv on the asinh grid (see IntegArgs::t1tab).
+// Tables of log2 T_1(-|z|; dofs[t] + 1) and d/dv on the grid uniform in v = log2(1 + |z|)
+// (see IntegArgs::t1tab).
 // jmask: the tables t with bit (t mod 3) set are built (E-step tables t = 3h + j; the
 // others are left as they are: no record reads them); 7 builds every table.
 __global__ void t1_table_kernel(int ndof, const double* __restrict__ dofs, float2* __restrict__ tab, int jmask)
@@ -308,12 +309,12 @@ __global__ void t1_table_kernel(int ndof, const double* __restrict__ dofs, float
             continue;
         }
         const double v = i * hv;
-        const double w = sinh(v * CF_LN2);
+        const double w = expm1(v * CF_LN2);
         const double lT = log_t1_lower(w, nu);
-        // d/dv log2 T_1(-w(v)) = -t_nu(w) cosh(v ln 2) / T_1(-w)
+        // d/dv log2 T_1(-w(v)) = -t_nu(w) (1 + w) / T_1(-w)   (dw/dv = (1 + w) ln 2)
         const double lt = lgamma(0.5 * (nu + 1.0)) - lgamma(0.5 * nu) - 0.5 * log(nu * CF_PI) -
                           0.5 * (nu + 1.0) * log1p(w * w / nu);
-        const double d = -exp(lt - lT) * cosh(v * CF_LN2);
+        const double d = -exp(lt - lT) * (1.0 + w);
         tab[e] = make_float2((float)(lT / CF_LN2), (float)d);
     }
 }

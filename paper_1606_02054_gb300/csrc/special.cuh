@@ -279,7 +279,7 @@ __device__ __forceinline__ double t1_lgb(double nu)
 
 // ---------------------------------------------------------------------------
 // T_1(z; nu + 1) inside an FP32 T_2 from its per-dof table (IntegArgs::t1tab):
-// cubic Hermite interpolation of log2 T_1(-|z|) in v = asinh(|z|)/ln 2 (values
+// cubic Hermite interpolation of log2 T_1(-|z|) in v = log2(1 + |z|) (values
 // and derivatives tabulated in FP64, see t1_table_kernel), continued linearly
 // beyond the grid, where log2 T_1 approaches its asymptote -(nu+1) v + const.
 // T_1(z) = 1 - T_1(-z) for z > 0.  Interpolation error ~1e-8 in log2 T_1;
@@ -289,7 +289,7 @@ __device__ __forceinline__ float t1cdf_table(float z, const float2* __restrict__
 {
     constexpr float hv = T1TAB_V / (T1TAB_N - 1);
     const float w = fabsf(z);
-    const float v = ptx_lg2_approx(w + sqrtf(fmaf(w, w, 1.0f)));
+    const float v = ptx_lg2_approx(1.0f + w);
     const float pos = fminf(v * (1.0f / hv), (float)(T1TAB_N - 1));
     const int i = min((int)pos, T1TAB_N - 2);
     const float t = pos - (float)i;
