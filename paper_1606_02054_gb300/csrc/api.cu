@@ -21,7 +21,7 @@ __global__ void setup_components_kernel(Dims, Layout, const double*, const doubl
 __global__ void chi_table_kernel(int, int, const double*, const double*, Lattice, const double*, double, double*,
                                  float*, double*, float*);
 __global__ void dof_consts_kernel(Dims, Layout, const double*, int, double*, double*, float*);
-__global__ void t1_table_kernel(int, const double*, float2*, int);
+__global__ void t1_table_kernel(int, const double*, const double*, float2*, int);
 __global__ void widen_kernel(const float*, long long, Dims, double*);
 __global__ void widen_pairs_kernel(const float*, long long, int, double*, double*, double*, double*);
 __global__ void narrow_kernel(const double*, Dims, float*);
@@ -747,7 +747,7 @@ static cfust_status launch_setup(cfust_ctx* c)
             if (r.k == 1 && l == 1) jmask |= 1;
         }
         const int total = 3 * c->g * T1TAB_N;
-        t1_table_kernel<<<(total + 255) / 256, 256, 0, c->st>>>(3 * c->g, c->dofs, c->t1tab, jmask);
+        t1_table_kernel<<<(total + 255) / 256, 256, 0, c->st>>>(3 * c->g, c->dofs, c->cst64, c->t1tab, jmask);
         LAUNCHED();
     }
     if (c->mixed) {
@@ -1909,7 +1909,7 @@ extern "C" cfust_status cfust_tk_eval(cfust_ctx* c, int k, int count, const doub
         }
         if (use_t1tab) {
             const int total = count * T1TAB_N;
-            t1_table_kernel<<<(total + 255) / 256, 256, 0, c->st>>>(count, r.dof, t1t, 7);
+            t1_table_kernel<<<(total + 255) / 256, 256, 0, c->st>>>(count, r.dof, k64, t1t, 7);
             c->launches++;
             if ((e = cudaGetLastError())) break;
         }

@@ -278,14 +278,15 @@ __global__ void narrow_kernel(const double* __restrict__ src, Dims D, float* __r
 }
 
 // log T_1(-w; nu) for w >= 0 in FP64, without underflow: with x = nu/(nu+w^2),
-// T_1(-w) = I_x(nu/2, 1/2)/2 from the continued fraction in log form.
-static __device__ double log_t1_lower(double w, double nu)
+// T_1(-w) = I_x(nu/2, 1/2)/2 from the continued fraction in log form; lbeta =
+// lgamma((nu+1)/2) - lgamma(nu/2) - lgamma(1/2), the table's constant.
+static __device__ double log_t1_lower(double w, double nu, double lbeta)
 {
     if (w == 0.0) return -CF_LN2;
     const double w2 = w * w, den = nu + w2;
     const double x = nu / den, y = w2 / den;
     const double a = 0.5 * nu, b = 0.5;
-    const double lbt = lgamma(a + b) - lgamma(a) - lgamma(b) + a * log(x) + b * log(y);
+    const double lbt = lbeta + a * log(x) + b * log(y);
     if (x < (a + 1.0) / (a + b + 2.0))
         return lbt + log(betacf_dev<double>(a, b, x)) - log(a) - CF_LN2;
     return log1p(-exp(lbt) * betacf_dev<double>(b, a, y) / b) - CF_LN2;
@@ -295,7 +296,9 @@ static __device__ double log_t1_lower(double w, double nu)
 // (see IntegArgs::t1tab).
 // jmask: the tables t with bit (t mod 3) set are built (E-step tables t = 3h + j; the
 // others are left as they are: no record reads them); 7 builds every table.
-__global__ void t1_table_kernel(int ndof, const double* __restrict__ dofs, float2* __restrict__ tab, int jmask)
+// cst: the per-dof constants of dof_consts_kernel (CST_LGB1: lbeta at dofs[t] + 1).
+__global__ void t1_table_kernel(int ndof, const double* __restrict__ dofs, const double* __restrict__ cst,
+                                float2* __restrict__ tab, int jmask)
 {
     const long long total = (long long)ndof * T1TAB_N;
     const double hv = (double)T1TAB_V / (T1TAB_N - 1);
@@ -310,10 +313,11 @@ __global__ void t1_table_kernel(int ndof, const double* __restrict__ dofs, float
         }
         const double v = i * hv;
         const double w = expm1(v * CF_LN2);
-        const double lT = log_t1_lower(w, nu);
-        // d/dv log2 T_1(-w(v)) = -t_nu(w) (1 + w) / T_1(-w)   (dw/dv = (1 + w) ln 2)
-        const double lt = lgamma(0.5 * (nu + 1.0)) - lgamma(0.5 * nu) - 0.5 * log(nu * CF_PI) -
-                          0.5 * (nu + 1.0) * log1p(w * w / nu);
+        const double lbeta = cst[t * CST_STRIDE + CST_LGB1];
+        const double lT = log_t1_lower(w, nu, lbeta);
+        // d/dv log2 T_1(-w(v)) = -t_nu(w) (1 + w) / T_1(-w)   (dw/dv = (1 + w) ln 2); the
+        // density's constant lgamma((nu+1)/2) - lgamma(nu/2) - log(nu pi)/2 is lbeta - log(nu)/2
+        const double lt = lbeta - 0.5 * log(nu) - 0.5 * (nu + 1.0) * log1p(w * w / nu);
         const double d = -exp(lt - lT) * (1.0 + w);
         tab[e] = make_float2((float)(lT / CF_LN2), (float)d);
     }
