@@ -806,6 +806,9 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
     pa.single_pass = sp;
     pa.pd = c->pd; pa.pc = c->pc;
     pa.pd32 = c->mixed ? c->pd32 : nullptr; pa.pc32 = c->mixed ? c->pc32 : nullptr;
+    // mixed form at q = 2: the level-1 T_1s are table lookups done by combine, not records
+    const int fuse_l1 = c->mixed && c->q == 2 && !c->single_pass && c->t1tab != nullptr;
+    pa.fuse_l1 = fuse_l1;
     pa.L0 = c->rec[0]; pa.L1 = c->rec[1]; pa.L2 = c->rec[2]; pa.LM = c->rec[3];
     if (density_only || sp) pa.L0.nrec = c->n * c->g;
     cudaError_t e;
@@ -844,6 +847,7 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
         // single-pass E-step: alpha_s comes from the moment pass (the same lattice points),
         // also for the surrogate's out-of-range pairs; level 0 runs only in density passes
         if (l == 0 && sp && !density_only) continue;
+        if (l == 1 && fuse_l1) continue;  // evaluated inside combine
         RecSet r = l == 0 ? pa.L0 : c->rec[l];
         n0 = c->launches;
         prof_begin(c, CFUST_PROF_LEVEL0 + l);
@@ -883,6 +887,7 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
     CombineArgs ca;
     ca.D = c->D; ca.Ly = c->Ly; ca.cst64 = c->cst64; ca.cst32 = c->cst32; ca.F = c->F; ca.pd = c->pd; ca.pc = c->pc;
     ca.pd32 = c->mixed ? c->pd32 : nullptr; ca.pc32 = c->mixed ? c->pc32 : nullptr;
+    ca.t1tab = c->t1tab; ca.fuse_l1 = fuse_l1;
     ca.F32 = c->mixed ? c->F32 : nullptr;
     ca.L0 = pa.L0; ca.L1 = c->rec[1]; ca.L2 = c->rec[2]; ca.LM = c->rec[3];
     ca.density_only = density_only; ca.single_pass = sp; ca.fp32 = fp32;

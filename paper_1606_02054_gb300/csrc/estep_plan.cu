@@ -66,6 +66,7 @@ __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const flo
         a.LM.dof[pid] = nu1d + 2.0;
         return;
     }
+    if (Q == 2 && a.fuse_l1) return;  // combine evaluates the level-1 T_1s itself
     const int q1 = q - 1, q2 = q - 2;
     for (int r = 0; r < q && q1 > 0; ++r) {
         const long long rec = pid * q + r;
@@ -208,14 +209,26 @@ __global__ void __launch_bounds__(128) combine_mixed_kernel(CombineArgs a)
             continue;
         }
         const double alpha = a.density_only ? 0.0 : a.L0.res[pid * m0 + 1];
+        const float* F32 = a.F32 + (size_t)h * a.Ly.stride;
         double tq1[CF_MAXQ], tq2[Q == 2 ? 1 : CF_MAXQ * CF_MAXQ];
         if (!a.density_only) {
-            for (int r = 0; r < q && q1 > 0; ++r) tq1[r] = a.L1.res[pid * q + r];
+            if (Q == 2 && a.fuse_l1) {
+                // the level-1 T_1 at dof nu+p+1 (table 3h holds T_1 at that dof; the normal
+                // limit takes Phi), from the same FP32 limits the records would carry
+                const bool nrm = isinf(F32[a.Ly.scal + SC_NU]);
+                for (int r = 0; r < 2; ++r) {
+                    float bt1[CF_MAXQ];
+                    limits_l1<float>(F32, a.Ly, p, 2, c, d, r, bt1);
+                    tq1[r] = (double)(nrm ? m_ncdf(bt1[0]) : t1cdf_table(bt1[0], a.t1tab + (size_t)(3 * h) * T1TAB_N));
+                }
+            } else {
+                for (int r = 0; r < q && q1 > 0; ++r) tq1[r] = a.L1.res[pid * q + r];
+            }
             if (Q != 2 && q1 > 1)
                 for (int i = 0; i < q * q1; ++i) tq2[i] = a.L2.res[pid * q * q1 + i];
         }
         PairOutF of;
-        pair_assemble_f32(a.F32 + (size_t)h * a.Ly.stride, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1, tq2,
+        pair_assemble_f32(F32, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1, tq2,
                           a.density_only, a.cst32 + (size_t)(3 * h) * CST_STRIDE, of);
         a.logf[pid] = of.logf;
         if (a.se) a.se[pid] = se;

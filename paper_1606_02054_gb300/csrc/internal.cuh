@@ -142,6 +142,7 @@ struct PlanArgs {
     double* pc;        // per pair: c (q)
     float* pd32;       // mixed form: the same in FP32 (written instead of pd, pc)
     float* pc32;
+    int fuse_l1;       // mixed form at q = 2: no level-1 records (combine evaluates the T_1s)
     RecSet L0, L1, L2, LM;
 };
 
@@ -220,6 +221,8 @@ struct CombineArgs {
     const double* pc;
     const float* pd32;     // mixed form: d, log t_p and c in FP32 (read instead of pd, pc)
     const float* pc32;
+    const float2* t1tab;   // mixed form at q = 2 with fuse_l1: the level-1 T_1 from the tables
+    int fuse_l1;
     RecSet L0, L1, L2, LM;
     int density_only;
     int single_pass;
