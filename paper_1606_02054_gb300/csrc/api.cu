@@ -219,8 +219,10 @@ static cfust_status check_flags(cfust_ctx* c, int f, const char* where)
 // Observations per block of the statistics reduction: rows of 4 + p + q + q^2 values
 // (FP32 in the mixed form) plus g posterior weights staged in at most ~64 KB of
 // shared memory, chunk <= 256.  Depends on the sizes and the precision only, not on n.
-// values per staged row of the statistics kernel (FP32 rows also hold tau u r: p more)
-static int reduce_row(int p, int q, bool mixed) { return 4 + p + q + q * q + (mixed ? p : 0); }
+// values per staged row of the statistics kernel (FP32 rows also hold tau u r: p more, and
+// an odd length, so that the threads of a warp staging consecutive rows write to distinct
+// shared-memory banks)
+static int reduce_row(int p, int q, bool mixed) { return mixed ? (4 + 2 * p + q + q * q) | 1 : 4 + p + q + q * q; }
 
 static int reduce_chunk(int p, int q, int g, bool mixed)
 {
