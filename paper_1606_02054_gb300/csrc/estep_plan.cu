@@ -43,9 +43,12 @@ __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const flo
     if (Q == 2) reinterpret_cast<float2*>(a.pc32)[pid] = make_float2(c[0], c[1]);
     else for (int k = 0; k < q; ++k) a.pc32[pid * q + k] = c[k];
     // a record gets the fields its integrator reads: FP32 T_2 records their FP32 fields and
-    // table index, T_1 records no factor
+    // table index, T_1 records no factor.  With the level-1 T_1s fused into combine (q = 2),
+    // the level-0 records are stored record-major (alpha_s of every pair, then alpha), so the
+    // threads of a warp write consecutive records.
+    const long long np = a.D.n * a.D.g;
     for (int w = 0; w < m0; ++w) {
-        const long long rec = pid * m0 + w;
+        const long long rec = (Q == 2 && a.fuse_l1) ? w * np + pid : pid * m0 + w;
         limits_l0<float>(F, a.Ly, p, q, c, d, w, bt);
         a.L0.tab[rec] = 3 * h + 2 * w;
         if (q == 2 && a.L0.t2f) {
@@ -200,15 +203,18 @@ __global__ void __launch_bounds__(128) combine_mixed_kernel(CombineArgs a)
         } else {
             for (int k = 0; k < q; ++k) c[k] = a.pc32[pid * q + k];
         }
-        const double alpha_s = a.L0.res[pid * m0];
-        const double se = a.L0.se ? a.L0.se[pid * m0] : 0.0;
+        // level-0 records: record-major with the fused level 1 (see plan_pair_f32)
+        const bool rmaj = Q == 2 && a.fuse_l1;
+        const long long r0 = rmaj ? pid : pid * m0;
+        const double alpha_s = a.L0.res[r0];
+        const double se = a.L0.se ? a.L0.se[r0] : 0.0;
         if (!(alpha_s >= 1e-35)) {
             // outside the FP32 range of the lattice products: redo in FP64
             const int slot = atomicAdd(a.fix_count, 1);
             a.fix_list[slot] = (int)pid;
             continue;
         }
-        const double alpha = a.density_only ? 0.0 : a.L0.res[pid * m0 + 1];
+        const double alpha = a.density_only ? 0.0 : a.L0.res[rmaj ? np + pid : pid * m0 + 1];
         const float* F32 = a.F32 + (size_t)h * a.Ly.stride;
         double tq1[CF_MAXQ], tq2[Q == 2 ? 1 : CF_MAXQ * CF_MAXQ];
         if (!a.density_only) {
