@@ -85,6 +85,7 @@ struct cfust_ctx {
     float* F32 = nullptr;
     float* pr32 = nullptr;  // FP32 pair rows (u, E log w, eu, euu) written by the mixed E-step
     float *pd32 = nullptr, *pc32 = nullptr;  // mixed form: d, log t_p and c in FP32
+    float* res32_l0 = nullptr;  // mixed form at q = 2: the level-0 T_2 results in FP32
     // E-step pipeline: per-pair (d, log t_p) and c, integral records per level
     double *pd = nullptr, *pc = nullptr;
     RecSet rec[4]{};  // levels 0, 1, 2 and the single-pass moment records
@@ -369,7 +370,7 @@ static void free_all(cfust_ctx* c)
                     c->glx64, c->glw64, c->glx32, c->glw32, c->glx32h, c->glw32h, c->glx32l, c->glw32l,
                     c->logf, c->u, c->elogu, c->eu,
                     c->euu, c->se, c->tau, c->partial, c->stats, c->flags, c->comp_status,
-                    c->stage32, c->pd, c->pc, c->fix_count, c->fix_list, c->y32, c->F32, c->pr32, c->pd32, c->pc32, c->t1tab,
+                    c->stage32, c->pd, c->pc, c->fix_count, c->fix_list, c->y32, c->F32, c->pr32, c->pd32, c->pc32, c->res32_l0, c->t1tab,
                     c->work_dev, c->seg, c->lchi64, c->lchi32};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -526,6 +527,7 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
         ALLOC(F32, (size_t)g * c->Ly.stride);
         ALLOC(pr32, ng * pr32_width(q));
         ALLOC(pd32, 2 * ng); ALLOC(pc32, ng * q);
+        if (q == 2) ALLOC(res32_l0, 2 * ng);
     }
     ALLOC(fix_count, 1); ALLOC(fix_list, ng);
     // T_2 records exist at q = 2 (level 0) and, in the recursion form, at q = 3, 4 (levels 1, 2)
@@ -812,6 +814,11 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
     const int fuse_l1 = c->mixed && c->q == 2 && !c->single_pass && c->t1tab != nullptr;
     pa.fuse_l1 = fuse_l1;
     pa.L0 = c->rec[0]; pa.L1 = c->rec[1]; pa.L2 = c->rec[2]; pa.LM = c->rec[3];
+    if (fuse_l1 && c->res32_l0) {
+        // the level-0 T_2 results in FP32 for combine; no standard errors (quadrature: 0)
+        pa.L0.res32 = c->res32_l0;
+        pa.L0.se = nullptr;
+    }
     if (density_only || sp) pa.L0.nrec = c->n * c->g;
     cudaError_t e;
     long long n0 = c->launches;

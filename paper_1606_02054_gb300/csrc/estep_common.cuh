@@ -317,19 +317,19 @@ __device__ inline void pair_assemble_sp(const double* F, const Layout& Ly, int p
 // FP64 run on GB300's FP64 pipe, 1/64 of the FP32 rate: the per-component values are read
 // from their FP32 copies).
 __device__ inline void pair_assemble_f32(const float* F, const Layout& Ly, int p, int q,
-                                         const float* cf, float d, float logtp, double alpha_s_d,
-                                         double alpha_d, const double* tq1, const double* tq2,
+                                         const float* cf, float d, float logtp, float alpha_s,
+                                         float alpha, const float* tq1, const float* tq2,
                                          int density_only, const float* cst, PairOutF& o)
 {
-    const float alpha_s = (float)alpha_s_d;
     if (!(alpha_s > 0.0f)) return pair_null(q, density_only, o);
-    o.logf = q * 0.6931471805599453 + (double)logtp + (double)logf(alpha_s);  // eq (4)
+    // eq (4): log t_p + log alpha_s in FP32 (both FP32 quantities), q log 2 added in FP64
+    o.logf = q * 0.6931471805599453 + (double)(logtp + logf(alpha_s));
     if (density_only) return;
     const float nu = F[Ly.scal + SC_NU], nu1 = nu + (float)p;
     float c[CF_MAXQ];
     for (int k = 0; k < q; ++k) c[k] = cf[k];
     const bool nrm = isinf(nu);  // the normal limit (eq 5): u = 1, every t scaling is 1
-    const float u = nrm ? 1.0f : nu1 / (nu + d) * (float)alpha_d / alpha_s;  // eq (13)
+    const float u = nrm ? 1.0f : nu1 / (nu + d) * alpha / alpha_s;  // eq (13)
     o.u = u;
     o.elogu = nrm ? 0.0f : u - logf(0.5f * (nu + d)) - nu1 / (nu + d) + F[Ly.scal + SC_PSI];  // eq (15)
     float Lam[CF_MAXQ * CF_MAXQ];
@@ -341,7 +341,7 @@ __device__ inline void pair_assemble_f32(const float* F, const Layout& Ly, int p
     for (int i = 0; i < q * q; ++i) H[i] = 0.0f;
     for (int r = 0; r < q; ++r) {
         const float Srr = k0 * Lam[r * q + r];
-        const float t1q = q1 > 0 ? (float)tq1[r] : 1.0f;
+        const float t1q = q1 > 0 ? tq1[r] : 1.0f;
         xi[r] = expf(nrm ? -0.5f * logf(2.0f * (float)CF_PI * Srr) - 0.5f * c[r] * c[r] / Srr
                          : lt1 - 0.5f * logf(Srr) - 0.5f * (nu1 + 1.0f) * log1pf(c[r] * c[r] / (nu1 * Srr))) * t1q;
         H[r * q + r] = c[r] * xi[r];
@@ -360,7 +360,7 @@ __device__ inline void pair_assemble_f32(const float* F, const Layout& Ly, int p
         float xip[CF_MAXQ];
         for (int s = 0; s < q1; ++s) {
             const float Vss = kp * sch[s * q1 + s];
-            const float t2q = q1 > 1 ? (float)tq2[r * q1 + s] : 1.0f;
+            const float t2q = q1 > 1 ? tq2[r * q1 + s] : 1.0f;
             const float nuv = nu2 - 2.0f;
             xip[s] = expf(nrm ? -0.5f * logf(2.0f * (float)CF_PI * Vss) - 0.5f * cp[s] * cp[s] / Vss
                               : lt1m - 0.5f * logf(Vss) - 0.5f * (nuv + 1.0f) * log1pf(cp[s] * cp[s] / (nuv * Vss))) * t2q;

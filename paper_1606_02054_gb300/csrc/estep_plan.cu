@@ -206,17 +206,19 @@ __global__ void __launch_bounds__(128) combine_mixed_kernel(CombineArgs a)
         // level-0 records: record-major with the fused level 1 (see plan_pair_f32)
         const bool rmaj = Q == 2 && a.fuse_l1;
         const long long r0 = rmaj ? pid : pid * m0;
-        const double alpha_s = a.L0.res[r0];
+        // FP32 results where the T_2 kernel wrote them (res32), else the FP64 ones
+        const float alpha_s = a.L0.res32 ? a.L0.res32[r0] : (float)a.L0.res[r0];
         const double se = a.L0.se ? a.L0.se[r0] : 0.0;
-        if (!(alpha_s >= 1e-35)) {
+        if (!(alpha_s >= 1e-35f)) {
             // outside the FP32 range of the lattice products: redo in FP64
             const int slot = atomicAdd(a.fix_count, 1);
             a.fix_list[slot] = (int)pid;
             continue;
         }
-        const double alpha = a.density_only ? 0.0 : a.L0.res[rmaj ? np + pid : pid * m0 + 1];
+        const long long r1 = rmaj ? np + pid : pid * m0 + 1;
+        const float alpha = a.density_only ? 0.0f : a.L0.res32 ? a.L0.res32[r1] : (float)a.L0.res[r1];
         const float* F32 = a.F32 + (size_t)h * a.Ly.stride;
-        double tq1[CF_MAXQ], tq2[Q == 2 ? 1 : CF_MAXQ * CF_MAXQ];
+        float tq1[CF_MAXQ], tq2[Q == 2 ? 1 : CF_MAXQ * CF_MAXQ];
         if (!a.density_only) {
             if (Q == 2 && a.fuse_l1) {
                 // the level-1 T_1 at dof nu+p+1 (table 3h holds T_1 at that dof; the normal
@@ -225,13 +227,13 @@ __global__ void __launch_bounds__(128) combine_mixed_kernel(CombineArgs a)
                 for (int r = 0; r < 2; ++r) {
                     float bt1[CF_MAXQ];
                     limits_l1<float>(F32, a.Ly, p, 2, c, d, r, bt1);
-                    tq1[r] = (double)(nrm ? m_ncdf(bt1[0]) : t1cdf_table(bt1[0], a.t1tab + (size_t)(3 * h) * T1TAB_N));
+                    tq1[r] = nrm ? m_ncdf(bt1[0]) : t1cdf_table(bt1[0], a.t1tab + (size_t)(3 * h) * T1TAB_N);
                 }
             } else {
-                for (int r = 0; r < q && q1 > 0; ++r) tq1[r] = a.L1.res[pid * q + r];
+                for (int r = 0; r < q && q1 > 0; ++r) tq1[r] = (float)a.L1.res[pid * q + r];
             }
             if (Q != 2 && q1 > 1)
-                for (int i = 0; i < q * q1; ++i) tq2[i] = a.L2.res[pid * q * q1 + i];
+                for (int i = 0; i < q * q1; ++i) tq2[i] = (float)a.L2.res[pid * q * q1 + i];
         }
         PairOutF of;
         pair_assemble_f32(F32, a.Ly, p, q, c, d, logtp, alpha_s, alpha, tq1, tq2,

@@ -38,7 +38,8 @@ __global__ void __launch_bounds__(256) t2_records_kernel(RecSet r, IntegArgs a)
                                        f32 ? (const R*)a.glw32l : nullptr);
         nodes += (unsigned long long)nn;
         if (lane == 0) {
-            r.res[i] = v;
+            if (r.res32) r.res32[i] = (float)v;
+            else r.res[i] = v;
             if (r.se) r.se[i] = 0.0;
         }
     }
@@ -211,7 +212,8 @@ __global__ void __launch_bounds__(T2P_WARPS * CF_WARP, 4) t2_pieces_kernel(RecSe
             float v;
             if (limit[m]) v = lim[m];
             else v = C2[m] * (np[m] == 2 ? P[rr][0] + P[rr][1] : P[rr][0]);
-            r.res[i] = (double)v;
+            if (r.res32) r.res32[i] = v;
+            else r.res[i] = (double)v;
             if (r.se) r.se[i] = 0.0;
         }
         __syncwarp();

@@ -112,6 +112,8 @@ struct RecSet {
     const int* nsel;   //   (the learned surrogate's fallback list; device count)
     double* lw;        // moment records, exact E[log W] only (else null): the f-weighted mean of
                        // log(s^2) over the points of the pass (s the chi variate of alpha_s)
+    float* res32 = nullptr;  // FP32 T_2 records of the mixed form at q = 2 (else null): the
+                             // results in FP32, written instead of res
 };
 
 // Record index t of a set: every record, or (SEL: a kernel instantiated for
