@@ -813,6 +813,7 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
     // mixed form at q = 2: the level-1 T_1s are table lookups done by combine, not records
     const int fuse_l1 = c->mixed && c->q == 2 && !c->single_pass && c->t1tab != nullptr;
     pa.fuse_l1 = fuse_l1;
+    pa.blocks = 16 * c->nsm;
     pa.L0 = c->rec[0]; pa.L1 = c->rec[1]; pa.L2 = c->rec[2]; pa.LM = c->rec[3];
     if (fuse_l1 && c->res32_l0) {
         // the level-0 T_2 results in FP32 for combine; no standard errors (quadrature: 0)

@@ -76,7 +76,9 @@ __device__ inline void pair_whiten(const double* F, const Layout& Ly, int p, int
 // Mixed precision: the same whitening and log t_p in FP32 from FP32 copies of y
 // and of the factor block.
 // P > 0: p known at compile time (= P), the loops unrolled and the vectors in registers;
-// P = 0: any p.  The same operations in the same order either way.
+// P = 0: any p.  P a multiple of 4: y_j, mu and the rows of Linv read four values per
+// load (F32 and yj 16-byte aligned; mu, Linv and A then start on 16-byte boundaries).
+// The same operations in the same order in every case.
 template <int P = 0>
 __device__ inline void pair_whiten_f32(const float* F32, const Layout& Ly, int p_rt, int q, const float* yj,
                                        float* d_out, float* c, float* logtp)
@@ -84,16 +86,36 @@ __device__ inline void pair_whiten_f32(const float* F32, const Layout& Ly, int p
     constexpr int NA = P > 0 ? P : CF_MAXP;
     const int p = P > 0 ? P : p_rt;
     float rr[NA], z[NA];
+    if constexpr (P > 0 && P % 4 == 0) {
 #pragma unroll
-    for (int i = 0; i < NA; ++i)
-        if (i < p) rr[i] = yj[i] - F32[Ly.mu + i];
+        for (int i = 0; i < P; i += 4) {
+            const float4 y4 = *reinterpret_cast<const float4*>(yj + i);
+            const float4 m4 = *reinterpret_cast<const float4*>(F32 + Ly.mu + i);
+            rr[i] = y4.x - m4.x; rr[i + 1] = y4.y - m4.y; rr[i + 2] = y4.z - m4.z; rr[i + 3] = y4.w - m4.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NA; ++i)
+            if (i < p) rr[i] = yj[i] - F32[Ly.mu + i];
+    }
     float d = 0.0f;
 #pragma unroll
     for (int i = 0; i < NA; ++i) {
         if (i >= p) break;
         float s = 0.0f;
+        if constexpr (P > 0 && P % 4 == 0) {
 #pragma unroll
-        for (int l = 0; l <= i; ++l) s = fmaf(F32[Ly.Linv + i * p + l], rr[l], s);
+            for (int l4 = 0; l4 <= i; l4 += 4) {
+                const float4 w = *reinterpret_cast<const float4*>(F32 + Ly.Linv + i * P + l4);
+                s = fmaf(w.x, rr[l4], s);
+                if (l4 + 1 <= i) s = fmaf(w.y, rr[l4 + 1], s);
+                if (l4 + 2 <= i) s = fmaf(w.z, rr[l4 + 2], s);
+                if (l4 + 3 <= i) s = fmaf(w.w, rr[l4 + 3], s);
+            }
+        } else {
+#pragma unroll
+            for (int l = 0; l <= i; ++l) s = fmaf(F32[Ly.Linv + i * p + l], rr[l], s);
+        }
         z[i] = s;
         d = fmaf(s, s, d);
     }

@@ -28,14 +28,15 @@ __device__ __forceinline__ void put_t2f32(const RecSet& L, long long rec, const 
 
 // Mixed form: one pair in FP32 (whitening, log t_p, limits, FP32 T_2 inputs);
 // T_2 records of the FP32 modes need no FP64 fields, the others get them.
+// F: the component's FP32 factor block (staged in shared memory by the kernel)
 template <int P, int Q>
-__device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const float* yj)
+__device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const float* yj, const float* F)
 {
     const int p = a.D.p, q = Q > 0 ? Q : a.D.q;
     const int m0 = (a.density_only || a.single_pass) ? 1 : 2;
-    const float* F = a.F32 + (size_t)h * a.Ly.stride;
     const int foff = h * a.Ly.stride;
-    const double nu1d = a.F[(size_t)h * a.Ly.stride + a.Ly.scal + SC_NU] + p;
+    // dof nu + p in FP64 for the records with FP64 fields (read only where used)
+    auto nu1d = [&]() { return a.F[(size_t)h * a.Ly.stride + a.Ly.scal + SC_NU] + p; };
     const float nu1 = F[a.Ly.scal + SC_NU] + p;
     float c[CF_MAXQ], d, logtp, bt[CF_MAXQ];
     pair_whiten_f32<P>(F, a.Ly, p, q, yj, &d, c, &logtp);
@@ -56,7 +57,7 @@ __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const flo
         } else {
             a.L0.fac[rec] = foff + fac_l0(a.Ly);
             for (int k = 0; k < q; ++k) a.L0.bt[rec * q + k] = bt[k];
-            a.L0.dof[rec] = nu1d + 2.0 * w;
+            a.L0.dof[rec] = nu1d() + 2.0 * w;
         }
     }
     if (a.density_only) return;
@@ -66,7 +67,7 @@ __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const flo
         for (int k = 0; k < q; ++k) a.LM.bt[pid * q + k] = bt[k];
         a.LM.fac[pid] = foff + fac_l0(a.Ly);
         a.LM.tab[pid] = 3 * h;
-        a.LM.dof[pid] = nu1d + 2.0;
+        a.LM.dof[pid] = nu1d() + 2.0;
         return;
     }
     if (Q == 2 && a.fuse_l1) return;  // combine evaluates the level-1 T_1s itself
@@ -80,7 +81,7 @@ __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const flo
         } else {
             if (q1 >= 2) a.L1.fac[rec] = foff + fac_l1(a.Ly, q, r);
             for (int k = 0; k < q1; ++k) a.L1.bt[rec * q1 + k] = bt[k];
-            a.L1.dof[rec] = nu1d + 1.0;
+            a.L1.dof[rec] = nu1d() + 1.0;
         }
         for (int s = 0; s < q1 && q2 > 0; ++s) {
             const long long r2 = pid * q * q1 + r * q1 + s;
@@ -91,7 +92,7 @@ __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const flo
             } else {
                 if (q2 >= 2) a.L2.fac[r2] = foff + fac_l2(a.Ly, q, r, s);
                 for (int k = 0; k < q2; ++k) a.L2.bt[r2 * q2 + k] = bt[k];
-                a.L2.dof[r2] = nu1d;
+                a.L2.dof[r2] = nu1d();
             }
         }
     }
@@ -101,23 +102,39 @@ __device__ void plan_pair_f32(const PlanArgs& a, long long pid, int h, const flo
 // limit its occupancy (one kernel for both took 118 registers, 24 % warps active).
 // P, Q: the dimensions p and q at compile time for common sizes (whitening and limits in
 // registers), 0 for any
+// The pairs in tiles of 128 observations of one component (pid = h n + j as before): a
+// block stages its component's FP32 factor block in shared memory (when the component
+// changes), so the whitening reads it there, four values per load, rather than as
+// warp-uniform global loads that filled the load/store queue.
 template <int P, int Q>
 __global__ void __launch_bounds__(128) plan_kernel_f32(PlanArgs a)
 {
+    extern __shared__ float4 plan_sF4[];
+    float* sF = reinterpret_cast<float*>(plan_sF4);
     const int p = a.D.p;
-    const long long np = a.D.n * a.D.g;
-    for (long long pid = blockIdx.x * (long long)blockDim.x + threadIdx.x; pid < np;
-         pid += (long long)gridDim.x * blockDim.x) {
-        const int h = (int)(pid / a.D.n);
-        plan_pair_f32<P, Q>(a, pid, h, a.y32 + (size_t)(pid - (long long)h * a.D.n) * p);
+    const long long n = a.D.n;
+    const long long tpc = (n + 127) / 128;  // tiles per component
+    const long long ntiles = tpc * a.D.g;
+    int hs = -1;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int h = (int)(tile / tpc);
+        if (h != hs) {  // the same for the whole block
+            __syncthreads();
+            for (int e = threadIdx.x; e < a.Ly.stride; e += blockDim.x) sF[e] = a.F32[(size_t)h * a.Ly.stride + e];
+            __syncthreads();
+            hs = h;
+        }
+        const long long j = (tile - (long long)h * tpc) * 128 + threadIdx.x;
+        if (j < n) plan_pair_f32<P, Q>(a, (long long)h * n + j, h, a.y32 + (size_t)j * p, sF);
     }
 }
 
 template <int P>
 static void launch_plan_f32(const PlanArgs& a, int gb, cudaStream_t st)
 {
-    if (a.D.q == 2) plan_kernel_f32<P, 2><<<gb, 128, 0, st>>>(a);
-    else plan_kernel_f32<P, 0><<<gb, 128, 0, st>>>(a);
+    const size_t sh = sizeof(float) * (size_t)a.Ly.stride;
+    if (a.D.q == 2) plan_kernel_f32<P, 2><<<gb, 128, sh, st>>>(a);
+    else plan_kernel_f32<P, 0><<<gb, 128, sh, st>>>(a);
 }
 
 __global__ void __launch_bounds__(128) plan_kernel(PlanArgs a)
@@ -338,16 +355,18 @@ cudaError_t launch_plan(const PlanArgs& a, cudaStream_t st, long long* launches)
     const long long np = a.D.n * a.D.g;
     const int gb = grid_for(np, 128, 1 << 20);
     if (a.F32) {
+        const long long ntiles = (a.D.n + 127) / 128 * a.D.g;
+        const int gf = a.blocks > 0 && a.blocks < ntiles ? a.blocks : (int)(ntiles < (1 << 20) ? ntiles : (1 << 20));
         switch (a.D.p) {
-        case 4: launch_plan_f32<4>(a, gb, st); break;
-        case 6: launch_plan_f32<6>(a, gb, st); break;
-        case 8: launch_plan_f32<8>(a, gb, st); break;
-        case 16: launch_plan_f32<16>(a, gb, st); break;
-        case 32: launch_plan_f32<32>(a, gb, st); break;
-        default: launch_plan_f32<0>(a, gb, st); break;
+        case 4: launch_plan_f32<4>(a, gf, st); break;
+        case 6: launch_plan_f32<6>(a, gf, st); break;
+        case 8: launch_plan_f32<8>(a, gf, st); break;
+        case 16: launch_plan_f32<16>(a, gf, st); break;
+        case 32: launch_plan_f32<32>(a, gf, st); break;
+        default: launch_plan_f32<0>(a, gf, st); break;
         }
     }
-    else plan_kernel<<<grid_for(np, 128, 1 << 20), 128, 0, st>>>(a);
+    else plan_kernel<<<gb, 128, 0, st>>>(a);
     ++*launches;
     return cudaGetLastError();
 }

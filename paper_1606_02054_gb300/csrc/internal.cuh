@@ -145,6 +145,8 @@ struct PlanArgs {
     float* pd32;       // mixed form: the same in FP32 (written instead of pd, pc)
     float* pc32;
     int fuse_l1;       // mixed form at q = 2: no level-1 records (combine evaluates the T_1s)
+    int blocks = 0;    // mixed form: blocks of the plan (resident on the device; each takes
+                       // tiles of 128 observations of one component), 0: one per tile
     RecSet L0, L1, L2, LM;
 };
 

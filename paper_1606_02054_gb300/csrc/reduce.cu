@@ -95,8 +95,9 @@ __device__ inline void stat_operands_w(int e, int p, int q, int& ia, int& ib, in
 }
 
 // T = double: FP64 rows and sums.  T = float (mixed precision): FP32 rows
-// (centred observations from the FP32 copy of y) and compensated FP32 sums
-// per block; tau, l_j and the block partials stay FP64.
+// (centred observations from the FP32 copy of y), compensated FP32 sums per
+// block, FP32 exponentials of the log-sum-exp; the log-sum-exp's terms, l_j and
+// the block partials stay FP64.
 template <typename T>
 __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
 {
@@ -117,7 +118,7 @@ __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
     if (sizeof(T) == sizeof(float))
         for (int e = t; e < g * p; e += blockDim.x) mu32[e] = (float)a.mu[e];
 
-    // S8: tau and l_j for this chunk (FP64 log-sum-exp: one exp per component)
+    // S8: tau and l_j for this chunk (log-sum-exp about the largest term, one exp per component)
     if (t < g) lpi[t] = log(a.pi[t]);
     __syncthreads();
     if (t < cnt) {
@@ -131,27 +132,48 @@ __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
                 mx = v[h] > mx ? v[h] : mx;
             }
         }
-        double s = 0.0;
+        if (sizeof(T) == sizeof(float)) {
+            // FP32 rows: each term's distance from the largest one is formed in FP64 and
+            // rounded once, the exponentials, their sum (between 1 and g), its logarithm and
+            // the quotients are FP32: tau to a few ulp of FP32, l_j = max + log s to ~1e-7
+            // absolute, the largest term itself exact
+            float e[CF_MAXG];
+            float s = 0.0f;
 #pragma unroll
-        for (int h = 0; h < CF_MAXG; ++h) {
-            if (h < g) {
-                const double x = v[h] - mx;
-                // FP32 rows: a term below e^-37 (< 1e-16 of the sum, whose largest term is 1)
-                // takes the FP32 exp, whose relative error (below 1e-5 with the rounding of x)
-                // is then below 1e-21 of the sum; the terms that decide l_j stay FP64
-                if (sizeof(T) == sizeof(float) && x < -37.0) v[h] = (double)expf((float)x);
-                else v[h] = exp(x);
-                s += v[h];
+            for (int h = 0; h < CF_MAXG; ++h) {
+                if (h < g) {
+                    e[h] = expf((float)(v[h] - mx));
+                    s += e[h];
+                }
             }
-        }
-        lj[t] = mx + log(s);
-        const double rs = 1.0 / s;
+            lj[t] = mx + (double)logf(s);
+            const float rs = 1.0f / s;
 #pragma unroll
-        for (int h = 0; h < CF_MAXG; ++h) {
-            if (h < g) {
-                const double tv = v[h] * rs;
-                taus[h * a.chunk + t] = (T)tv;
-                if (a.tau) a.tau[(size_t)h * n + j] = tv;
+            for (int h = 0; h < CF_MAXG; ++h) {
+                if (h < g) {
+                    const float tv = e[h] * rs;
+                    taus[h * a.chunk + t] = (T)tv;
+                    if (a.tau) a.tau[(size_t)h * n + j] = (double)tv;
+                }
+            }
+        } else {
+            double s = 0.0;
+#pragma unroll
+            for (int h = 0; h < CF_MAXG; ++h) {
+                if (h < g) {
+                    v[h] = exp(v[h] - mx);
+                    s += v[h];
+                }
+            }
+            lj[t] = mx + log(s);
+            const double rs = 1.0 / s;
+#pragma unroll
+            for (int h = 0; h < CF_MAXG; ++h) {
+                if (h < g) {
+                    const double tv = v[h] * rs;
+                    taus[h * a.chunk + t] = (T)tv;
+                    if (a.tau) a.tau[(size_t)h * n + j] = tv;
+                }
             }
         }
     } else if (t < a.chunk) {
