@@ -65,7 +65,7 @@ struct cfust_ctx {
     double *glx64 = nullptr, *glw64 = nullptr;
     float *glx32 = nullptr, *glw32 = nullptr;
     float *glx32h = nullptr, *glw32h = nullptr;  // T2_NH nodes for graded T_2 pieces
-    float *glx32l = nullptr, *glw32l = nullptr;  // t2n_lo nodes for smooth FP32 T_2 pieces
+    float *glx32l = nullptr, *glw32l = nullptr;  // node sets of the FP32 T_2 piece classes (t2_lo_class)
     int t2n_lo = 0;
     double *logf = nullptr, *u = nullptr, *elogu = nullptr, *eu = nullptr, *euu = nullptr,
            *se = nullptr, *tau = nullptr;
@@ -464,9 +464,9 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     c->tc_stats = c->mixed && o.tensor_stats && reduce_tc_fits(p, q, g);
     // a warp evaluates 32 nodes at a time: fewer than 32 per piece saves nothing
     c->t2n = o.t2_nodes ? o.t2_nodes : (o.precision == CFUST_PREC_FP64 ? 64 : 32);
-    // FP32 modes by default: T2_LO nodes where the integrand is smooth enough (a node count set
-    // in the options holds for every piece)
-    c->t2n_lo = (o.precision != CFUST_PREC_FP64 && o.t2_nodes == 0) ? T2_LO : 0;
+    // FP32 modes by default: 8-24 nodes by t2_lo_class where the integrand is smooth enough
+    // (a node count set in the options holds for every piece)
+    c->t2n_lo = (o.precision != CFUST_PREC_FP64 && o.t2_nodes == 0) ? 1 : 0;
     cudaDeviceProp prop;
     if ((e = cudaGetDeviceProperties(&prop, o.device)) != cudaSuccess) {
         cfust_status s = fail(nullptr, CFUST_ECUDA, std::string("cfust_create: ") + cudaGetErrorString(e));
@@ -514,7 +514,7 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     ALLOC(shf32, (size_t)o.qmc_shifts * CF_MAXDIM);
     ALLOC(glx64, c->t2n); ALLOC(glw64, c->t2n); ALLOC(glx32, c->t2n); ALLOC(glw32, c->t2n);
     ALLOC(glx32h, T2_NH); ALLOC(glw32h, T2_NH);
-    ALLOC(glx32l, T2_LO); ALLOC(glw32l, T2_LO);
+    ALLOC(glx32l, T2_LO_TOTAL); ALLOC(glw32l, T2_LO_TOTAL);
     ALLOC(logf, ng); ALLOC(u, ng); ALLOC(elogu, ng); ALLOC(se, ng); ALLOC(tau, ng);
     ALLOC(eu, ng * q); ALLOC(euu, ng * q * q);
     ALLOC(partial, part);
@@ -577,9 +577,13 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
     std::vector<double> gxh, gwh;
     gauss_legendre01(T2_NH, gxh, gwh);
     std::vector<float> gxh32(gxh.begin(), gxh.end()), gwh32(gwh.begin(), gwh.end());
-    std::vector<double> gxl, gwl;
-    gauss_legendre01(T2_LO, gxl, gwl);
-    std::vector<float> gxl32(gxl.begin(), gxl.end()), gwl32(gwl.begin(), gwl.end());
+    std::vector<float> gxl32, gwl32;  // the node sets of the classes of t2_lo_class, packed
+    for (int cl = 0; cl < T2_LO_NCLS; ++cl) {
+        std::vector<double> gxl, gwl;
+        gauss_legendre01(t2_lo_nodes(cl), gxl, gwl);
+        gxl32.insert(gxl32.end(), gxl.begin(), gxl.end());
+        gwl32.insert(gwl32.end(), gwl.begin(), gwl.end());
+    }
     cfust_status s = CFUST_OK;
     auto cp = [&](void* dst, const void* src, size_t bytes) {
         cudaError_t ee = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);

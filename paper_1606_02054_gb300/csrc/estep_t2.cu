@@ -47,19 +47,21 @@ __global__ void __launch_bounds__(256) t2_records_kernel(RecSet r, IntegArgs a)
 }
 
 // FP32 T_2 records (finite dof), scheduled by quadrature piece.  A warp takes a chunk of
-// 64 records; lane l sets up records l and l + 32 (the angles of the split and the pieces'
-// lengths, once per record), the chunk's pieces (one or two per record, 24, 32 or 64
-// nodes each) are ordered by node count and dealt to the warp's 32/L groups of L lanes,
-// a group sums its piece's nodes (lane sub takes nodes sub, sub + L, ...), and the record's
-// value is C_nu (piece 0 + piece 1).  Dealing pieces rather than records keeps the groups
-// of a round on equal node counts: a record with one piece no longer idles its lanes
-// while a neighbour's second piece runs.  The same L gives the same bits.
+// 64 records; lane l sets up records l and l + 32 (the angles of the split, the pieces'
+// lengths and node counts, once per record), the chunk's pieces (one or two per record,
+// 8 to 64 nodes each) are ordered by node set and dealt to the warp's 32/L groups of L
+// lanes, a group sums its piece's nodes (lane sub takes nodes sub, sub + L, ...), and the
+// record's value is C_nu (piece 0 + piece 1).  Dealing pieces rather than records keeps
+// the groups of a round on equal node counts: a record with one piece no longer idles its
+// lanes while a neighbour's second piece runs.  The same L gives the same bits.
 namespace {
 constexpr int T2P_WARPS = 8;
 constexpr int T2P_CH = 2 * CF_WARP;  // records per warp chunk
 // a record's set-up fields, one array per field (consecutive records in distinct banks)
 enum { T2F_ANC0, T2F_PHIS, T2F_L0, T2F_L1, T2F_D0, T2F_ZS, T2F_NU, T2F_LGB1, T2F_N };
 constexpr int T2P_NMAX = 64;  // nodes per piece at most (t2_nodes <= 64, T2_NH = 64)
+// node sets: the classes 0-4 of t2_lo_class, then t2n nodes, then the graded pieces' T2_NH
+constexpr int T2P_NK = T2_LO_NCLS + 2, T2P_KN = T2_LO_NCLS, T2P_KG = T2_LO_NCLS + 1;
 }  // namespace
 
 // TAB: the inner T_1 from the per-dof tables (a.t1tab), else by its continued fraction
@@ -68,9 +70,9 @@ __global__ void __launch_bounds__(T2P_WARPS * CF_WARP, 4) t2_pieces_kernel(RecSe
 {
     constexpr int G = CF_WARP / L;
     __shared__ float srf[T2P_WARPS][T2F_N][T2P_CH];
-    __shared__ int srt[T2P_WARPS][T2P_CH], srk[T2P_WARPS][T2P_CH];  // table index, kind (0: t2n_lo
-                                                                    // nodes, 1: t2n, 2: graded)
-    __shared__ float sgx[3][T2P_NMAX], sgw[3][T2P_NMAX];            // the node sets by kind
+    __shared__ int srt[T2P_WARPS][T2P_CH];                     // table index
+    __shared__ unsigned char srk[T2P_WARPS][2 * T2P_CH];       // node set of piece (record << 1) | pc
+    __shared__ float sgx[T2P_NK][T2P_NMAX], sgw[T2P_NK][T2P_NMAX];  // the node sets
     __shared__ float spsum[T2P_WARPS][T2P_CH][2];
     __shared__ unsigned char sitem[T2P_WARPS][2 * T2P_CH];  // (record << 1) | piece
     const int lane = threadIdx.x & (CF_WARP - 1), wib = threadIdx.x >> 5;
@@ -79,30 +81,35 @@ __global__ void __launch_bounds__(T2P_WARPS * CF_WARP, 4) t2_pieces_kernel(RecSe
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     float (*Rf)[T2P_CH] = srf[wib];
     int* Rt = srt[wib];
-    int* Rk = srk[wib];
+    unsigned char* Rk = srk[wib];
     float (*P)[2] = spsum[wib];
     unsigned char* items = sitem[wib];
-    const int nlo = a.t2n_lo > 0 ? a.t2n_lo : a.t2n;
-    for (int e = threadIdx.x; e < T2P_NMAX; e += blockDim.x) {
-        sgx[0][e] = e < nlo && a.t2n_lo > 0 ? a.glx32l[e] : 0.0f;
-        sgw[0][e] = e < nlo && a.t2n_lo > 0 ? a.glw32l[e] : 0.0f;
-        sgx[1][e] = e < a.t2n ? a.glx32[e] : 0.0f;
-        sgw[1][e] = e < a.t2n ? a.glw32[e] : 0.0f;
-        sgx[2][e] = e < T2_NH ? a.glx32h[e] : 0.0f;
-        sgw[2][e] = e < T2_NH ? a.glw32h[e] : 0.0f;
+    auto count = [&](int kd) { return kd < T2P_KN ? t2_lo_nodes(kd) : kd == T2P_KN ? a.t2n : T2_NH; };
+    for (int e = threadIdx.x; e < T2P_NK * T2P_NMAX; e += blockDim.x) {
+        const int kd = e / T2P_NMAX, i = e % T2P_NMAX;
+        float x = 0.0f, w = 0.0f;
+        if (kd < T2P_KN) {
+            if (a.t2n_lo > 0 && i < t2_lo_nodes(kd)) { x = a.glx32l[t2_lo_off(kd) + i]; w = a.glw32l[t2_lo_off(kd) + i]; }
+        } else if (kd == T2P_KN) {
+            if (i < a.t2n) { x = a.glx32[i]; w = a.glw32[i]; }
+        } else if (i < T2_NH) {
+            x = a.glx32h[i]; w = a.glw32h[i];
+        }
+        sgx[kd][i] = x;
+        sgw[kd][i] = w;
     }
     __syncthreads();
     unsigned long long nodes = 0;  // this lane's records' quadrature nodes (profiler count)
     for (long long base = warp * T2P_CH; base < r.nrec; base += nwarps * T2P_CH) {
         // phase 1: set-up of records lane and lane + 32
-        int np[2], kind[2];
+        int np[2], kind[2][2];
         float C2[2], lim[2];
         bool limit[2];
 #pragma unroll
         for (int m = 0; m < 2; ++m) {
             const int rr = lane + m * CF_WARP;
             const long long i = base + rr;
-            np[m] = 0; kind[m] = 1; C2[m] = 0.0f; lim[m] = 0.0f; limit[m] = false;
+            np[m] = 0; kind[m][0] = kind[m][1] = T2P_KN; C2[m] = 0.0f; lim[m] = 0.0f; limit[m] = false;
             if (i >= r.nrec) continue;
             const float* c = a.cst32 + r.tab[i] * CST_STRIDE;
             float h, k, rho, nu, omr2, cr;
@@ -128,24 +135,39 @@ __global__ void __launch_bounds__(T2P_WARPS * CF_WARP, 4) t2_pieces_kernel(RecSe
                 continue;
             }
             const bool graded = fabsf(rho) > 0.99f;
-            // fewer nodes where the integrand is smooth enough (the rule of T2_LO)
+            // fewer nodes where the integrand is smooth enough (t2_lo_class, per piece)
             const bool lo = a.t2n_lo > 0 && !graded && fabsf(rho) < T2_LO_RHO && nu >= T2_LO_DOF_MIN &&
                             nu <= T2_LO_DOF_MAX;
             const T2Setup<float> S = t2_setup<float>(h, k, rho, nu, omr2, cr);
-            kind[m] = graded ? 2 : lo ? 0 : 1;
             np[m] = S.split ? 2 : 1;
-            nodes += (unsigned long long)(np[m] * (kind[m] == 0 ? nlo : kind[m] == 1 ? a.t2n : T2_NH));
+            kind[m][0] = graded ? T2P_KG : lo ? t2_lo_class(S.L0, nu, S.zs) : T2P_KN;
+            kind[m][1] = graded ? T2P_KG : lo ? t2_lo_class(S.L1, nu, S.zs) : T2P_KN;
+            nodes += (unsigned long long)(count(kind[m][0]) + (S.split ? count(kind[m][1]) : 0));
             Rf[T2F_ANC0][rr] = S.anc0; Rf[T2F_PHIS][rr] = S.phis;
             Rf[T2F_L0][rr] = S.L0; Rf[T2F_L1][rr] = S.L1;
             Rf[T2F_D0][rr] = S.d0; Rf[T2F_ZS][rr] = S.zs;
             Rf[T2F_NU][rr] = nu; Rf[T2F_LGB1][rr] = c[CST_LGB1];
-            Rt[rr] = r.tab[i]; Rk[rr] = kind[m];
+            Rt[rr] = r.tab[i];
+            Rk[2 * rr] = (unsigned char)kind[m][0];
+            Rk[2 * rr + 1] = (unsigned char)kind[m][1];
         }
-        // the chunk's pieces, grouped by node count (kind 0, then 1, then 2)
+        // the chunk's pieces, grouped by node set (the sets present in the chunk, in order)
         int M = 0;
+        unsigned present = 0;
 #pragma unroll
-        for (int kd = 0; kd < 3; ++kd) {
-            const int cnt = (kind[0] == kd ? np[0] : 0) + (kind[1] == kd ? np[1] : 0);
+        for (int m = 0; m < 2; ++m)
+#pragma unroll
+            for (int pc = 0; pc < 2; ++pc)
+                if (pc < np[m]) present |= 1u << kind[m][pc];
+        present = __reduce_or_sync(CF_FULL, present);
+        while (present) {
+            const int kd = __ffs(present) - 1;
+            present &= present - 1;
+            int cnt = 0;
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+#pragma unroll
+                for (int pc = 0; pc < 2; ++pc) cnt += pc < np[m] && kind[m][pc] == kd;
             int incl = cnt;
 #pragma unroll
             for (int o = 1; o < CF_WARP; o <<= 1) {
@@ -155,8 +177,9 @@ __global__ void __launch_bounds__(T2P_WARPS * CF_WARP, 4) t2_pieces_kernel(RecSe
             int pos = M + incl - cnt;
 #pragma unroll
             for (int m = 0; m < 2; ++m)
-                if (kind[m] == kd)
-                    for (int pc = 0; pc < np[m]; ++pc) items[pos++] = (unsigned char)(((lane + m * CF_WARP) << 1) | pc);
+#pragma unroll
+                for (int pc = 0; pc < 2; ++pc)
+                    if (pc < np[m] && kind[m][pc] == kd) items[pos++] = (unsigned char)(((lane + m * CF_WARP) << 1) | pc);
             M += __shfl_sync(CF_FULL, incl, CF_WARP - 1);
         }
         __syncwarp();
@@ -168,11 +191,11 @@ __global__ void __launch_bounds__(T2P_WARPS * CF_WARP, 4) t2_pieces_kernel(RecSe
             if (it < M) {
                 rr = items[it] >> 1;
                 pc = items[it] & 1;
-                const int kd = Rk[rr];
-                const int nn = kd == 0 ? nlo : kd == 1 ? a.t2n : T2_NH;
+                const int kd = Rk[items[it]];
+                const int nn = count(kd);
                 const float* gx = sgx[kd];
                 const float* gw = sgw[kd];
-                const bool graded = kd == 2;
+                const bool graded = kd == T2P_KG;
                 const float anc = pc ? Rf[T2F_PHIS][rr] : Rf[T2F_ANC0][rr];
                 const float Lp = pc ? Rf[T2F_L1][rr] : Rf[T2F_L0][rr];
                 const float d0 = pc ? 0.0f : Rf[T2F_D0][rr];

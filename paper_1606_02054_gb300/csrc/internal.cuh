@@ -177,7 +177,8 @@ struct IntegArgs {
     // nodes of the graded T_2 pieces (|rho| > 0.99): T2_NH per piece
     const float* glx32h;
     const float* glw32h;
-    // FP32: t2n_lo nodes per piece where 4 <= dof <= 64 and |rho| < 0.9 (T2_LO_* below)
+    // FP32: > 0 where pieces with 4 <= dof <= 64 and |rho| < 0.9 take 8-32 nodes by
+    // t2_lo_class (T2_LO_* below), glx32l / glw32l the node sets of classes 0-4 packed
     int t2n_lo;
     const float* glx32l;
     const float* glw32l;
@@ -205,13 +206,43 @@ struct IntegArgs {
 
 constexpr int T1TAB_N = 4096;
 constexpr int T2_NH = 64;
-// FP32 T_2: the node count of a piece whose integrand is smooth enough for fewer nodes.
-// Emulated on the host against the oracle's adaptive quadrature: 24 nodes stay within
-// 1.8e-6 relative over 2,231 cases with 4 <= dof <= 64 and |rho| < 0.9 (32 nodes are needed
-// beyond: sin^(dof-1) peaks more sharply at large dof, the boundary layer narrows as |rho|
-// -> 1); the FP32 integrators' error floor is 5e-5.
-constexpr int T2_LO = 24;
+// FP32 T_2 pieces where 4 <= dof <= 64 and |rho| < 0.9: Gauss-Legendre with 8, 12, 16, 20,
+// 24 or t2n (32) nodes by the piece's length L in units of the integrand's two widths: the
+// peak of sin^(dof-1) (~ 1/sqrt(dof - 1)) and the rise of the inner T_1 at the split point
+// (~ 1/|zs|, zs the slope of its argument there).  Class c <= 4 serves a piece with
+//   s^2 = L^2 (dof - 1 + 0.2 zs^2) <= T2_LO_S2_c  (and dof <= T2_LO_DMAX_c for c = 0, 1:
+// a piece that ends at phi = 0 carries the factor phi^(dof-1), integrated exactly only by
+// enough nodes), class 5 (the t2n set) the rest.  The bounds were fitted on the host
+// against 1024-node graded quadrature over 1.3e5 pieces (dof log-uniform, tails of h and k
+// down to T_1 = 1e-12, h up to 40) with the largest admissible error 5e-6 relative to T_2,
+// and 0.85 of each fitted bound is kept; on held-out samples of two other distributions
+// (4.4e5 pieces) the pieces of classes 0-4 stay within 1.9e-6, and whole records with
+// |k| <= 8 within 2.5e-6 (one 24-node set for every piece reached 2.9e-4 there, at large h
+// and dof).  The FP32 integrators' error floor is 5e-5.
+constexpr int T2_LO_NCLS = 5;            // classes with a node set of their own (0-4)
+constexpr int T2_LO_TOTAL = 80;            // 8 + 12 + 16 + 20 + 24 nodes, packed by class
+__host__ __device__ constexpr int t2_lo_nodes(int c) { return 8 + 4 * c; }
+__host__ __device__ constexpr int t2_lo_off(int c) { return 2 * c * c + 6 * c; }  // sum of the counts below c
+// bounds on s^2 = L^2 (dof - 1 + T2_LO_ZW zs^2) of the classes 0-4, and the dof caps
+constexpr float T2_LO_S2_0 = 1.54f * 1.54f, T2_LO_S2_1 = 4.12f * 4.12f, T2_LO_S2_2 = 7.58f * 7.58f,
+                T2_LO_S2_3 = 11.32f * 11.32f, T2_LO_S2_4 = 15.5f * 15.5f;
+constexpr float T2_LO_DMAX_0 = 20.0f, T2_LO_DMAX_1 = 40.0f;
+constexpr float T2_LO_ZW = 0.2f;
 constexpr float T2_LO_DOF_MIN = 4.0f, T2_LO_DOF_MAX = 64.0f, T2_LO_RHO = 0.9f;
+
+// class of an FP32 T_2 piece of length L (either sign) in the region above: 0-4, or 5 for
+// the t2n nodes
+__device__ __forceinline__ int t2_lo_class(float L, float nu, float zs)
+{
+    const float s2 = L * L * fmaf(T2_LO_ZW * zs, zs, nu - 1.0f);
+    return (s2 <= T2_LO_S2_0 && nu <= T2_LO_DMAX_0)   ? 0
+           : (s2 <= T2_LO_S2_1 && nu <= T2_LO_DMAX_1) ? 1
+           : s2 <= T2_LO_S2_2                         ? 2
+           : s2 <= T2_LO_S2_3                         ? 3
+           : s2 <= T2_LO_S2_4                         ? 4
+                                                      : T2_LO_NCLS;
+}
+
 constexpr float T1TAB_V = 48.0f;
 
 struct CombineArgs {

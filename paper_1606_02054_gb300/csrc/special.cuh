@@ -315,7 +315,9 @@ __device__ __forceinline__ float t1cdf_table(float z, const float2* __restrict__
 // cancels near phi*.  The interval is split at phi*.  For |rho| > 0.99 the
 // nodes are graded (phi = anchor + L t^3) toward the split point (or toward
 // phi_h when there is no split) to resolve the boundary layer of width
-// ~ sqrt(1 - rho^2), and glxh/glwh (nh nodes) replace glx/glw (n nodes).
+// ~ sqrt(1 - rho^2), and glxh/glwh (nh nodes) replace glx/glw (n nodes).  With nlo > 0
+// (FP32), a piece with 4 <= nu <= 64 and |rho| < 0.9 takes the node set of its
+// t2_lo_class from glxl/glwl (the classes' sets packed in order).
 // The second piece's length phi_h - phi* is computed directly (not as a
 // difference of the two angles, which can be far shorter than FP32 resolves
 // them), and it also places the upper end, so the split point and the upper
@@ -370,23 +372,33 @@ __device__ double t2cdf_warp(R h, R k, R rho, R nu, R omr2, R cr, R lgb, R lgb1,
         return v > R(0) ? (double)v : 0.0;
     }
     const bool graded = m_abs(rho) > R(0.99);
-    // fewer nodes where the integrand is smooth enough (nlo > 0: the FP32 rule of T2_LO)
+    // fewer nodes where the integrand is smooth enough (nlo > 0: FP32, t2_lo_class per piece)
     const bool lo = nlo > 0 && !graded && m_abs(rho) < R(T2_LO_RHO) && nu >= R(T2_LO_DOF_MIN) &&
                     nu <= R(T2_LO_DOF_MAX);
     const T2Setup<R> S = t2_setup<R>(h, k, rho, nu, omr2, cr);
-    const int nn = graded ? nh : lo ? nlo : n;
-    const R* __restrict__ gx = graded ? glxh : lo ? glxl : glx;
-    const R* __restrict__ gw = graded ? glwh : lo ? glwl : glw;
     const int npieces = S.split ? 2 : 1;
-    if (nodes_out) *nodes_out = npieces * nn;
+    // node set of each piece: its class's Gauss-Legendre set, else n nodes, else nh graded
+    const R* __restrict__ gx0 = graded ? glxh : glx;
+    const R* __restrict__ gw0 = graded ? glwh : glw;
+    const R* __restrict__ gx1 = gx0;
+    const R* __restrict__ gw1 = gw0;
+    int n0 = graded ? nh : n, n1 = n0;
+    if (lo) {
+        const int c0 = t2_lo_class((float)S.L0, (float)nu, (float)S.zs);
+        const int c1 = t2_lo_class((float)S.L1, (float)nu, (float)S.zs);
+        if (c0 < T2_LO_NCLS) { n0 = t2_lo_nodes(c0); gx0 = glxl + t2_lo_off(c0); gw0 = glwl + t2_lo_off(c0); }
+        if (c1 < T2_LO_NCLS) { n1 = t2_lo_nodes(c1); gx1 = glxl + t2_lo_off(c1); gw1 = glwl + t2_lo_off(c1); }
+    }
+    if (npieces == 1) n1 = 0;
+    if (nodes_out) *nodes_out = n0 + n1;
     const R nu1 = nu + R(1), num1 = nu - R(1);
     R acc = R(0);
-    for (int t = lane; t < npieces * nn; t += CF_WARP) {
-        const bool p1 = t >= nn;
-        const int i = p1 ? t - nn : t;
+    for (int t = lane; t < n0 + n1; t += CF_WARP) {
+        const bool p1 = t >= n0;
+        const int i = p1 ? t - n0 : t;
         const R anc = p1 ? S.phis : S.anc0;
         const R L = p1 ? S.L1 : S.L0;
-        const R u = gx[i];
+        const R u = p1 ? gx1[i] : gx0[i];
         const R um = graded ? u * u * u : u;
         const R jac = graded ? R(3) * u * u : R(1);
         const R off = L * um;
@@ -407,7 +419,7 @@ __device__ double t2cdf_warp(R h, R k, R rho, R nu, R omr2, R cr, R lgb, R lgb1,
         } else {
             f = m_exp(num1 * m_log(sp)) * t1cdf_dev<R>(z, nu1, lgb1);
         }
-        acc += gw[i] * jac * f * m_abs(L);
+        acc += (p1 ? gw1[i] : gw0[i]) * jac * f * m_abs(L);
     }
     acc = warp_sum(acc);
     return (double)(C2 * acc);
@@ -422,63 +434,6 @@ __device__ __forceinline__ float group_sum(float v)
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(CF_FULL, v, o);
     return __shfl_sync(CF_FULL, v, (threadIdx.x & (CF_WARP - 1)) & ~(L - 1));
-}
-
-// ---------------------------------------------------------------------------
-// FP32 T_2(h, k; rho, nu) by the quadrature of t2cdf_warp, on an aligned group of L
-// lanes (sub = the lane's index in its group): the nodes of the record's pieces are
-// spread over the group's lanes, so a warp evaluates 32/L records at once and the
-// per-record set-up (the angles of the split, the pieces' lengths) is paid once per
-// group instead of once per warp.  Lane sub adds the nodes t = sub, sub + L, ... and the
-// group sums its lanes, so the rounding of the sum depends on L (the same L gives the same
-// bits).  Every lane of the warp must call it (the group reductions are warp-wide
-// shuffles); the |rho| = 1 limits take no early return so that every group reaches them.
-// nodes_out: nodes evaluated (0 at |rho| = 1).
-// ---------------------------------------------------------------------------
-template <int L>
-__device__ double t2cdf_group_f32(float h, float k, float rho, float nu, float omr2, float cr, float lgb,
-                                  float lgb1, float C2, int n, const float* __restrict__ glx,
-                                  const float* __restrict__ glw, int nh, const float* __restrict__ glxh,
-                                  const float* __restrict__ glwh, int sub, const float2* __restrict__ t1tab,
-                                  int* nodes_out, int nlo, const float* __restrict__ glxl,
-                                  const float* __restrict__ glwl)
-{
-    const bool lim = rho >= 1.0f || rho <= -1.0f;
-    float acc = 0.0f;
-    int nodes = 0;
-    if (!lim) {
-        const bool graded = fabsf(rho) > 0.99f;
-        // fewer nodes where the integrand is smooth enough (the rule of T2_LO)
-        const bool lo = nlo > 0 && !graded && fabsf(rho) < T2_LO_RHO && nu >= T2_LO_DOF_MIN && nu <= T2_LO_DOF_MAX;
-        const T2Setup<float> S = t2_setup<float>(h, k, rho, nu, omr2, cr);
-        const int nn = graded ? nh : lo ? nlo : n;
-        const float* __restrict__ gx = graded ? glxh : lo ? glxl : glx;
-        const float* __restrict__ gw = graded ? glwh : lo ? glwl : glw;
-        nodes = (S.split ? 2 : 1) * nn;
-        const float nu1 = nu + 1.0f, num1 = nu - 1.0f;
-        for (int t = sub; t < nodes; t += L) {
-            const bool p1 = t >= nn;
-            const int i = p1 ? t - nn : t;
-            const float anc = p1 ? S.phis : S.anc0;
-            const float Lp = p1 ? S.L1 : S.L0;
-            const float u = gx[i];
-            const float um = graded ? u * u * u : u;
-            const float jac = graded ? 3.0f * u * u : 1.0f;
-            const float off = Lp * um;
-            const float sp = cf_sin_pi(anc + off);  // both arguments lie in [-pi, pi]
-            const float sd = cf_sin_pi((p1 ? 0.0f : S.d0) + off);
-            const float z = S.zs * sd;
-            const float f = ptx_ex2_approx(num1 * ptx_lg2_approx(sp)) *
-                            (t1tab ? t1cdf_table(z, t1tab) : t1cdf_dev<float>(z, nu1, lgb1));
-            acc += gw[i] * jac * f * fabsf(Lp);
-        }
-    }
-    acc = group_sum<L>(acc);
-    if (nodes_out) *nodes_out = nodes;
-    if (!lim) return (double)(C2 * acc);
-    if (rho >= 1.0f) return (double)t1cdf_dev<float>(h < k ? h : k, nu, lgb);
-    const float v = t1cdf_dev<float>(h, nu, lgb) + t1cdf_dev<float>(k, nu, lgb) - 1.0f;
-    return v > 0.0f ? (double)v : 0.0;
 }
 
 // ---------------------------------------------------------------------------
