@@ -91,10 +91,10 @@ SUB_PLAIN_STEPS = {"learned_p6": 1}
 # build (dram__bytes_read.sum + dram__bytes_write.sum of one launch / its units); None
 # where no capture of the current kernel exists
 TRAFFIC_PER_UNIT = {
-    # t2_pieces_kernel<2, 1>, wide_p16 shape at n = 200,000 (mixed form, 24/32/64 nodes per
-    # piece): 115.30 MB read + 6.07 MB written for 113.49 M nodes; the records (FP32 fields
-    # in, FP32 result out) scale with the nodes at any n
-    ("level0_Tq", 2): (115.298048e6 + 6.067456e6) / 113494656,
+    # t2_pieces_kernel<2, 1>, wide_p16 shape at n = 200,000 (mixed form, 8-32 nodes per piece
+    # by its class, 64 graded): 115.28 MB read + 5.56 MB written for 83.24 M nodes; the
+    # records (FP32 fields in, FP32 result out) scale with the nodes at any n
+    ("level0_Tq", 2): (115.277056e6 + 5.564672e6) / 83239548,
     # lattice_mom_kernel_32<4, 0, 0, 2>, flow_p4 shape at n = 4,000: 1.07 MB read, nothing
     # written to DRAM, for 131.07 M lattice points (the records, 67 B each, scale with them)
     ("moments_Tq", 4): 1.070080e6 / 131072000,

@@ -76,10 +76,12 @@ typedef struct {
     double nu_max;       /* (default 200) */
     int device;          /* CUDA device ordinal (default 0) */
     void* cuda_stream;   /* cudaStream_t to issue work on (default NULL) */
-    int t2_nodes;        /* Gauss-Legendre nodes per piece of the T_2 quadrature, 8..64
-                            (0: 64 in FP64 mode, 32 in the FP32 and mixed modes, where
-                            the T_1 inside each node is interpolated from a per-dof
-                            table built once per E-step) */
+    int t2_nodes;        /* Gauss-Legendre nodes per piece of the T_2 quadrature, 8..64,
+                            for every piece (0: 64 in FP64 mode; in the FP32 and mixed
+                            modes 8 to 32 by the piece's length in units of the
+                            integrand's widths where 4 <= dof <= 64 and |rho| < 0.9, 32
+                            elsewhere; the T_1 inside each node is interpolated there from
+                            a per-dof table built once per E-step) */
     int profile;         /* 1: time every kernel class with CUDA events on the context
                             stream (read with cfust_profile); 0 (default): off */
     int moments;         /* truncated-t moments of eqs (16)-(17) for q >= 3:

@@ -204,7 +204,7 @@ struct IntegArgs {
     const float* lchi32;
 };
 
-constexpr int T1TAB_N = 4096;
+constexpr int T1TAB_N = 2048;
 constexpr int T2_NH = 64;
 // FP32 T_2 pieces where 4 <= dof <= 64 and |rho| < 0.9: Gauss-Legendre with 8, 12, 16, 20,
 // 24 or t2n (32) nodes by the piece's length L in units of the integrand's two widths: the

@@ -240,11 +240,31 @@ __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
             T acc = T(0), comp = T(0);
             if (sizeof(T) == sizeof(float)) {
                 stat_operands_w(e, p, q, ia, ib, o1, o2);
-                for (int jj = 0; jj < cnt; ++jj) {
-                    const T* rw = rows + (size_t)jj * a.row;
-                    const T v = fmaf(rw[ia], rw[ib], -comp);  // compensated FP32 sum
+                // two compensated sums, even and odd rows (independent chains), added at the end
+                T acc1 = T(0), comp1 = T(0);
+                const T* ra = rows + ia;
+                const T* rb = rows + ib;
+                int jj = 0;
+                for (; jj + 1 < cnt; jj += 2) {
+                    const T x0 = ra[(size_t)jj * a.row], y0 = rb[(size_t)jj * a.row];
+                    const T x1 = ra[(size_t)(jj + 1) * a.row], y1 = rb[(size_t)(jj + 1) * a.row];
+                    const T v0 = fmaf(x0, y0, -comp);
+                    const T v1 = fmaf(x1, y1, -comp1);
+                    const T t0 = acc + v0, t1 = acc1 + v1;
+                    comp = (t0 - acc) - v0;
+                    comp1 = (t1 - acc1) - v1;
+                    acc = t0;
+                    acc1 = t1;
+                }
+                if (jj < cnt) {
+                    const T v0 = fmaf(ra[(size_t)jj * a.row], rb[(size_t)jj * a.row], -comp);
+                    const T t0 = acc + v0;
+                    comp = (t0 - acc) - v0;
+                    acc = t0;
+                }
+                {   // the odd rows' sum into the even rows' one
+                    const T v = acc1 - comp1 - comp;
                     const T tt = acc + v;
-                    comp = (tt - acc) - v;
                     acc = tt;
                 }
             } else {
