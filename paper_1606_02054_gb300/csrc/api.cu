@@ -28,7 +28,6 @@ __global__ void narrow_kernel(const double*, Dims, float*);
 
 
 __global__ void estep_reduce_kernel(ReduceArgs);
-__global__ void estep_reduce_kernel_f32(ReduceArgs);
 __global__ void reduce_partials_kernel(const double*, int, int, double*, int*);
 __global__ void segment_partials_kernel(const double*, int, int, int, double*, long long);
 __global__ void loglik_partial_kernel(Dims, const double*, const double*, double*);
@@ -624,8 +623,7 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
         delete c;
         return s;
     }
-    cudaFuncSetAttribute(estep_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    cudaFuncSetAttribute(estep_reduce_kernel_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    reduce_set_smem_limits(96 * 1024);
     if (o.profile &&
         (cudaMalloc((void**)&c->work_dev, sizeof(unsigned long long) * CFUST_NPROF) != cudaSuccess ||
          cudaMemset(c->work_dev, 0, sizeof(unsigned long long) * CFUST_NPROF) != cudaSuccess)) {
@@ -956,7 +954,7 @@ static cfust_status enqueue_estep_segments(cfust_ctx* c, double* seg, long long 
     const size_t smem = (c->mixed ? sizeof(float) : sizeof(double)) * ((size_t)c->chunk * c->row + (size_t)c->g * c->chunk) +
                         sizeof(double) * ((size_t)c->chunk + CF_MAXG);
     prof_begin(c, CFUST_PROF_REDUCE);
-    if (c->mixed) estep_reduce_kernel_f32<<<c->nblocks_red, 256, smem, c->st>>>(r);
+    if (c->mixed) launch_reduce_f32(r, c->nblocks_red, smem, c->st);
     else estep_reduce_kernel<<<c->nblocks_red, 256, smem, c->st>>>(r);
     LAUNCHED();
     if (c->tc_stats) {  // Sr, Sre, Srr of the same blocks (reads the tau just written)

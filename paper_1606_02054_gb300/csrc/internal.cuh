@@ -380,6 +380,8 @@ __host__ __device__ inline int pr32_width(int q) { return 2 + q + q * q; }
 size_t reduce_tc_smem(int p, int q, int g);
 bool reduce_tc_fits(int p, int q, int g);
 cudaError_t launch_reduce_tc(const ReduceArgs& a, int* flags, int nsm, cudaStream_t st);
+cudaError_t launch_reduce_f32(const ReduceArgs& a, int nblocks, size_t smem, cudaStream_t st);
+void reduce_set_smem_limits(int bytes);
 
 // ---------------------------------------------------------------------------
 // Learned surrogate (not part of the paper): a 3 x 256 tanh MLP mapping a

@@ -98,10 +98,16 @@ __device__ inline void stat_operands_w(int e, int p, int q, int& ia, int& ib, in
 // (centred observations from the FP32 copy of y), compensated FP32 sums per
 // block, FP32 exponentials of the log-sum-exp; the log-sum-exp's terms, l_j and
 // the block partials stay FP64.
-template <typename T>
+// PF (mixed form, p = P a multiple of 4 and q = Q = 2 known at compile time, pair rows
+// present, full statistics): the observation's FP32 row is read once into registers for all
+// components, and the next component's pair row is loaded while the current one's sums run.
+// The staged values are the same operations in the same order either way.
+template <typename T, int P = 0, int Q = 0>
 __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
 {
-    const int p = a.D.p, q = a.D.q, g = a.D.g;
+    constexpr bool PF = sizeof(T) == sizeof(float) && P > 0 && P % 4 == 0 && Q == 2;
+    constexpr int PW = 2 + Q + Q * Q;  // FP32 pair-row width at q = Q
+    const int p = P > 0 ? P : a.D.p, q = Q > 0 ? Q : a.D.q, g = a.D.g;
     const long long n = a.D.n;
     const int S = stats_per_comp(p, q);
     const long long j0 = (long long)blockIdx.x * a.chunk;
@@ -188,11 +194,42 @@ __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
     if (t == 0) out[g * S] = lj[0];
     __syncthreads();
 
+    float yr[PF ? P : 1], pc[PF ? PW : 1];
+    if constexpr (PF) {
+        if (t < cnt) {
+#pragma unroll
+            for (int i = 0; i < P; i += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(a.y32 + (size_t)(j0 + t) * P + i);
+                yr[i] = v.x; yr[i + 1] = v.y; yr[i + 2] = v.z; yr[i + 3] = v.w;
+            }
+            const float4* src = reinterpret_cast<const float4*>(a.pr32 + (size_t)(j0 + t) * PW);
+#pragma unroll
+            for (int k = 0; k < PW / 4; ++k) {
+                const float4 v = src[k];
+                pc[4 * k] = v.x; pc[4 * k + 1] = v.y; pc[4 * k + 2] = v.z; pc[4 * k + 3] = v.w;
+            }
+        }
+    }
+
     // S9: statistics, one component at a time
     for (int h = 0; h < g; ++h) {
         if (t < a.chunk) {
             T* rw = rows + (size_t)t * a.row;
-            if (t < cnt) {
+            if (PF && t < cnt) {
+                const T tv = taus[h * a.chunk + t];
+                rw[0] = tv;
+                rw[1] = tv * pc[0];
+                rw[2] = tv * (pc[1] - pc[0]);
+                rw[3] = T(1);
+#pragma unroll
+                for (int i = 0; i < (PF ? P : 1); ++i) {
+                    const T ri = yr[i] - mu32[h * p + i];
+                    rw[4 + i] = ri;
+                    rw[4 + p + i] = rw[1] * ri;
+                }
+#pragma unroll
+                for (int k = 0; k < (PF ? Q + Q * Q : 1); ++k) rw[4 + 2 * p + k] = rw[0] * pc[2 + k];
+            } else if (t < cnt) {
                 const size_t pid = (size_t)h * n + j0 + t;
                 const float* pr = a.pr32 ? a.pr32 + pid * pr32_width(q) : nullptr;
                 if (pr) {  // mixed form: the FP32 pair row, no conversions
@@ -232,6 +269,16 @@ __device__ void estep_reduce_body(const ReduceArgs& a, T* rows)
             }
         }
         __syncthreads();
+        if constexpr (PF) {  // the next component's pair row, consumed at its staging
+            if (h + 1 < g && t < cnt) {
+                const float4* src = reinterpret_cast<const float4*>(a.pr32 + ((size_t)(h + 1) * n + j0 + t) * PW);
+#pragma unroll
+                for (int k = 0; k < PW / 4; ++k) {
+                    const float4 v = src[k];
+                    pc[4 * k] = v.x; pc[4 * k + 1] = v.y; pc[4 * k + 2] = v.z; pc[4 * k + 3] = v.w;
+                }
+            }
+        }
         // small_only: N, U, Snu, Se and See (the tensor-core kernel writes Sr, Sre, Srr)
         const int Sred = a.small_only ? 3 + q + q * (q + 1) / 2 : stats_reduced(p, q);
         for (int es = t; es < Sred; es += blockDim.x) {
@@ -291,6 +338,38 @@ __global__ void estep_reduce_kernel_f32(ReduceArgs a)
 {
     extern __shared__ double sm[];
     estep_reduce_body<float>(a, (float*)sm);
+}
+
+template <int P>
+__global__ void __launch_bounds__(256, 4) estep_reduce_kernel_f32_pq(ReduceArgs a)
+{
+    extern __shared__ double sm[];
+    estep_reduce_body<float, P, 2>(a, (float*)sm);
+}
+
+// The mixed form's statistics kernel: compile-time p and q = 2 where they apply (pair rows
+// present, all statistics on the CUDA cores), else the general one.
+cudaError_t launch_reduce_f32(const ReduceArgs& a, int nblocks, size_t smem, cudaStream_t st)
+{
+    const bool pf = a.pr32 != nullptr && !a.small_only && a.D.q == 2;
+    if (pf && a.D.p == 16) estep_reduce_kernel_f32_pq<16><<<nblocks, 256, smem, st>>>(a);
+    else if (pf && a.D.p == 8) estep_reduce_kernel_f32_pq<8><<<nblocks, 256, smem, st>>>(a);
+    else if (pf && a.D.p == 4) estep_reduce_kernel_f32_pq<4><<<nblocks, 256, smem, st>>>(a);
+    else if (pf && a.D.p == 32) estep_reduce_kernel_f32_pq<32><<<nblocks, 256, smem, st>>>(a);
+    else estep_reduce_kernel_f32<<<nblocks, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// dynamic shared memory above the default 48 KB for every statistics kernel (set once per
+// context, before any launch or capture)
+void reduce_set_smem_limits(int bytes)
+{
+    cudaFuncSetAttribute(estep_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(estep_reduce_kernel_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(estep_reduce_kernel_f32_pq<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(estep_reduce_kernel_f32_pq<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(estep_reduce_kernel_f32_pq<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(estep_reduce_kernel_f32_pq<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 // S10, first level: seg[s][e] = sum of partial[b][e] over the blocks b of segment s
