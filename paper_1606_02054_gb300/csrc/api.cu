@@ -108,6 +108,11 @@ struct cfust_ctx {
     // whole-fit CUDA graph (cfust_fit_batch): captured on gst, cached per (max_iter, tol, flags)
     bool capturing = false;
     cudaStream_t gst = nullptr;
+    // the T_1 tables are built on a side stream while the plan runs: forked after the dof
+    // constants, joined before the first kernel that reads them (t1_pending in between)
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool t1_pending = false;
     cudaGraph_t fgraph = nullptr;
     cudaGraphExec_t fexec = nullptr;
     int fg_max_iter = -1, fg_flags = -1;
@@ -387,6 +392,9 @@ static void free_all(cfust_ctx* c)
     if (c->fexec) cudaGraphExecDestroy(c->fexec);
     if (c->fgraph) cudaGraphDestroy(c->fgraph);
     if (c->gst) cudaStreamDestroy(c->gst);
+    if (c->st2) cudaStreamDestroy(c->st2);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->fstate) cudaFree(c->fstate);
     if (c->fhist) cudaFree(c->fhist);
     if (c->h_fstate) cudaFreeHost(c->h_fstate);
@@ -399,6 +407,7 @@ extern "C" cfust_status cfust_destroy(cfust_ctx* c)
     cudaSetDevice(c->opts.device);
     if (c->st) cudaStreamSynchronize(c->st);
     if (c->gst) cudaStreamSynchronize(c->gst);
+    if (c->st2) cudaStreamSynchronize(c->st2);
     free_all(c);
     delete c;
     return CFUST_OK;
@@ -639,6 +648,13 @@ extern "C" cfust_status cfust_create(cfust_ctx** out, int p, int q, int g, int64
                     delete c;
                     return fail(nullptr, CFUST_ECUDA, "cfust_create: cudaEventCreate failed");
                 }
+    if (c->t1tab && (cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) != cudaSuccess ||
+                     cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                     cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)) {
+        free_all(c);
+        delete c;
+        return fail(nullptr, CFUST_ECUDA, "cfust_create: side stream or events");
+    }
     *out = c;
     return CFUST_OK;
 }
@@ -753,8 +769,12 @@ static cfust_status launch_setup(cfust_ctx* c)
             if (r.k == 1 && l == 1) jmask |= 1;
         }
         const int total = 3 * c->g * T1TAB_N;
-        t1_table_kernel<<<(total + 255) / 256, 256, 0, c->st>>>(3 * c->g, c->dofs, c->cst64, c->t1tab, jmask);
+        CU(cudaEventRecord(c->ev_fork, c->st));
+        CU(cudaStreamWaitEvent(c->st2, c->ev_fork, 0));
+        t1_table_kernel<<<(total + 255) / 256, 256, 0, c->st2>>>(3 * c->g, c->dofs, c->cst64, c->t1tab, jmask);
         LAUNCHED();
+        CU(cudaEventRecord(c->ev_join, c->st2));
+        c->t1_pending = true;
     }
     if (c->mixed) {
         cudaError_t e = launch_factors_f32(c->F, c->F32, (long long)c->g * c->Ly.stride, c->st, &c->launches);
@@ -828,6 +848,10 @@ static cfust_status launch_pairs(cfust_ctx* c, int density_only)
     prof_begin(c, CFUST_PROF_PLAN);
     if ((e = launch_plan(pa, c->st, &c->launches)) != cudaSuccess)
         return fail(c, CFUST_ECUDA, std::string("plan kernel: ") + cudaGetErrorString(e));
+    if (c->t1_pending) {  // the T_1 tables of this E-step, built beside the plan
+        CU(cudaStreamWaitEvent(c->st, c->ev_join, 0));
+        c->t1_pending = false;
+    }
     prof_end(c, CFUST_PROF_PLAN, c->launches - n0);
     const IntegArgs ia = integ_args(c);
     // learned surrogate: the network evaluates the level-0 and moment records, the
