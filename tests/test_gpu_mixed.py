@@ -91,16 +91,17 @@ def test_mixed_fit_error(cf, oracle):
 
 @pytest.mark.parametrize("tensor", [0, 1])
 @pytest.mark.parametrize("p,q,g,n", [(32, 8, 2, 300), (17, 3, 3, 257), (5, 1, 2, 1000), (16, 2, 8, 3001),
-                                     (4, 2, 3, 700), (8, 2, 2, 513), (32, 2, 2, 300)])
+                                     (4, 2, 3, 700), (8, 2, 2, 513), (32, 2, 2, 300), (6, 2, 3, 400)])
 def test_mixed_cross_statistics(cf, p, q, g, n, tensor):
     """Sr = sum tau u r, Sre = sum tau r eu^T and Srr = sum tau u r r^T of the mixed form
     -- compensated FP32 sums per block of at most 256 rows on the CUDA cores
     (tensor = 0), or the tcgen05 contraction with a TF32 hi/lo split and FP32
     accumulation per block (tensor = 1) -- FP64 across blocks, at the largest shape
     (p = 32, q = 8), the benchmark's p = 16, g = 8, the kernels at compile-time p for
-    q = 2 (p = 4, 8, 16, 32) and ragged n, against FP64 sums of the same FP32 row values
-    built from the context's own tau, u and eu: 1e-5 of each block's largest entry; Srr
-    exactly symmetric; N = sum tau, U = sum tau u and Se = sum tau eu likewise."""
+    q = 2 (p = 4, 8, 16, 32; p = 6 has a compile-time plan, not statistics) and ragged
+    n, against FP64 sums of the same FP32 row values built from the context's own tau,
+    u and eu: 1e-5 of each block's largest entry; Srr exactly symmetric; N = sum tau,
+    U = sum tau u and Se = sum tau eu likewise."""
     rng = np.random.default_rng(100 * p + q)
     P = synth.draw_params(rng, p, q, g, wishart_df=p + 8)
     y32 = np.ascontiguousarray(synth.sample(rng, n, P)[0], dtype=np.float32)
