@@ -33,9 +33,37 @@ __device__ bool chol_small(int n, const double* A, double* L)
     return true;
 }
 
-__device__ double nu_eq(double v, double N, double Snu)
+// digamma and trigamma at x > 0 together, by all 32 lanes of a warp: the recurrence terms
+// 1/(x + i), i < k (k the steps that bring x + k to at least 12), one per lane and added by a
+// butterfly (every lane ends with the same bits), then the asymptotic series at x + k (the
+// expansions of cf_digamma and cf_trigamma)
+__device__ void psi_pair_warp(double x, int lane, double& psi, double& tri)
 {
-    return N * (log(0.5 * v) - cf_digamma(0.5 * v) + 1.0) + Snu;
+    const int k = x < 12.0 ? (int)ceil(12.0 - x) : 0;
+    double a = 0.0, b = 0.0;
+    if (lane < k) {
+        const double r = 1.0 / (x + lane);
+        a = r;
+        b = r * r;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const double y = x + k, r = 1.0 / y, r2 = r * r;
+    psi = -a + log(y) - 0.5 * r - r2 * (1.0 / 12 + r2 * (-1.0 / 120 + r2 * (1.0 / 252 + r2 * (-1.0 / 240
+                 + r2 * (1.0 / 132 + r2 * (-691.0 / 32760))))));
+    tri = b + r * (1.0 + r * (0.5 + r * (1.0 / 6 + r2 * (-1.0 / 30 + r2 * (1.0 / 42
+                 + r2 * (-1.0 / 30 + r2 * (5.0 / 66)))))));
+}
+
+// eq (22) at v and its derivative in v, by all lanes
+__device__ double nu_eq_warp(double v, double N, double Snu, int lane, double* fp)
+{
+    double psi, tri;
+    psi_pair_warp(0.5 * v, lane, psi, tri);
+    if (fp) *fp = N * (1.0 / v - 0.5 * tri);
+    return N * (log(0.5 * v) - psi + 1.0) + Snu;
 }
 }  // namespace
 
@@ -156,30 +184,39 @@ __global__ void __launch_bounds__(32) mstep_kernel(Dims D, const double* __restr
         else if (lane > j && lane < p) W[lane * p + j] = t / dj;
         __syncwarp();
     }
-    // nu (eq 22): F decreasing in nu
-    if (lane == 0) {
+    // nu (eq 22): F decreasing in nu; every lane runs the same safeguarded Newton (the values,
+    // hence the branches, are the same in all lanes), lane 0 writes
+    {
         double vnew;
-        const double flo = nu_eq(nu_min, N, Snu), fhi = nu_eq(nu_max, N, Snu);
-        if (hold & CFUST_HOLD_NU) vnew = nu[h];
-        else if (!(flo > 0.0)) { vnew = nu_min; atomicOr(flags, KF_NUROOT); comp_status[h] = KF_NUROOT; }
-        else if (!(fhi < 0.0)) { vnew = nu_max; atomicOr(flags, KF_NUROOT); comp_status[h] = KF_NUROOT; }
-        else {
-            double lo = nu_min, hi = nu_max;
-            double v = nu[h] > lo && nu[h] < hi ? nu[h] : 0.5 * (lo + hi);
-            for (int it = 0; it < 200; ++it) {
-                const double f = nu_eq(v, N, Snu);
-                if (f > 0.0) lo = v; else hi = v;
-                const double fp = N * (1.0 / v - 0.5 * cf_trigamma(0.5 * v));
-                double vn = v - f / fp;
-                if (!(vn > lo && vn < hi)) vn = 0.5 * (lo + hi);
-                const bool done = fabs(vn - v) <= 1e-14 * v || hi - lo <= 1e-14 * hi;
-                v = vn;
-                if (done) break;
+        int st = 0;
+        if (hold & CFUST_HOLD_NU) {
+            vnew = nu[h];
+        } else {
+            const double flo = nu_eq_warp(nu_min, N, Snu, lane, nullptr);
+            const double fhi = nu_eq_warp(nu_max, N, Snu, lane, nullptr);
+            if (!(flo > 0.0)) { vnew = nu_min; st = KF_NUROOT; }
+            else if (!(fhi < 0.0)) { vnew = nu_max; st = KF_NUROOT; }
+            else {
+                double lo = nu_min, hi = nu_max;
+                double v = nu[h] > lo && nu[h] < hi ? nu[h] : 0.5 * (lo + hi);
+                for (int it = 0; it < 200; ++it) {
+                    double fp;
+                    const double f = nu_eq_warp(v, N, Snu, lane, &fp);
+                    if (f > 0.0) lo = v; else hi = v;
+                    double vn = v - f / fp;
+                    if (!(vn > lo && vn < hi)) vn = 0.5 * (lo + hi);
+                    const bool done = fabs(vn - v) <= 1e-14 * v || hi - lo <= 1e-14 * hi;
+                    v = vn;
+                    if (done) break;
+                }
+                vnew = v;
             }
-            vnew = v;
         }
-        pi_o[h] = N / (double)D.n;
-        nu_o[h] = vnew;
+        if (lane == 0) {
+            if (st) { atomicOr(flags, st); comp_status[h] = st; }
+            pi_o[h] = N / (double)D.n;
+            nu_o[h] = vnew;
+        }
     }
     for (int i = lane; i < p; i += 32) mu_o[(size_t)h * p + i] = muh[i] + delta[i];
     for (int i = lane; i < p * q; i += 32) Delta_o[(size_t)h * p * q + i] = Dn[i];

@@ -389,6 +389,7 @@ __global__ void segment_partials_kernel(const double* __restrict__ partial, int 
         const long long b0 = s * per;
         const long long b1 = b0 + per < nblocks ? b0 + per : nblocks;
         double v = 0.0;
+#pragma unroll 8  // loads in flight; the sum's order is unchanged
         for (long long b = b0; b < b1; ++b) v += partial[b * width + e];
         seg[t] = v;
     }
@@ -400,6 +401,7 @@ __global__ void reduce_partials_kernel(const double* __restrict__ partial, int n
 {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < width; e += gridDim.x * blockDim.x) {
         double s = 0.0;
+#pragma unroll 8  // loads in flight; the sum's order is unchanged
         for (int b = 0; b < nblocks; ++b) s += partial[(size_t)b * width + e];
         stats[e] = s;
         if (!isfinite(s)) atomicOr(flags, KF_NAN);
