@@ -1,9 +1,9 @@
 """The mixed-precision form (CFUST_PREC_MIXED): FP32 whitening, FP32
-integrals and FP32 compensated statistics, FP64 factorisations, tau,
-log-likelihood, M-step and nu.  Its error against the FP64 oracle is
+integrals and FP32 compensated statistics, FP64 factorisations, log-sum-exp
+terms (the exponentials FP32), log-likelihood sums, M-step and nu.  Its error against the FP64 oracle is
 reported (printed) and bounded:
   per-pair log f: 5e-5 max(1, |ref|)   (FP32 whitening: d and c to ~1e-6 relative;
-                                        24-node FP32 T_2: ~1e-5 relative)
+                                        FP32 T_2 pieces of 8-32 nodes: ~1e-5 relative)
   statistics: 2e-5 of each component's largest statistic
   log-likelihood: 1e-6 relative;  10-iteration fit: l 1e-6, each parameter block
   1e-4 in norm-wise relative error."""
