@@ -213,6 +213,7 @@ constexpr int T2_NH = 64;
 //   s^2 = L^2 (dof - 1 + 0.2 zs^2) <= T2_LO_S2_c  (and dof <= T2_LO_DMAX_c for c = 0, 1:
 // a piece that ends at phi = 0 carries the factor phi^(dof-1), integrated exactly only by
 // enough nodes), class 5 (the t2n set) the rest.  The bounds were fitted on the host
+// (fit_t2_classes.py, which derives them and checks them on held-out records)
 // against 1024-node graded quadrature over 1.3e5 pieces (dof log-uniform, tails of h and k
 // down to T_1 = 1e-12, h up to 40) with the largest admissible error 5e-6 relative to T_2,
 // and 0.85 of each fitted bound is kept; on held-out samples of two other distributions
