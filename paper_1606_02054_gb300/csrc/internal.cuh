@@ -214,7 +214,7 @@ constexpr int T2_NH = 64;
 // a piece that ends at phi = 0 carries the factor phi^(dof-1), integrated exactly only by
 // enough nodes), class 5 (the t2n set) the rest.  The bounds were fitted on the host
 // (fit_t2_classes.py, which derives them and checks them on held-out records)
-// against 1024-node graded quadrature over 1.3e5 pieces (dof log-uniform, tails of h and k
+// against 1024-node graded quadrature over 2.2e5 pieces (dof log-uniform, tails of h and k
 // down to T_1 = 1e-12, h up to 40) with the largest admissible error 5e-6 relative to T_2,
 // and 0.85 of each fitted bound is kept; on held-out samples of two other distributions
 // (4.4e5 pieces) the pieces of classes 0-4 stay within 1.9e-6, and whole records with
