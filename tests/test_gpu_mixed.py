@@ -143,8 +143,8 @@ def test_mixed_ill_conditioned_sigma(cf):
     """The mixed form at p = 32 with badly conditioned Sigma (condition number 1e4): the
     FP32 whitening's error grows with sqrt(kappa); per-pair log f against the FP64 path on
     the same FP32 data is bounded by C p 2^-24 sqrt(kappa) (nu + p) with C = 0.1 (measured
-    1.3e-4, C = 0.014: the bound leaves a factor of 7); at kappa ~ 10 the same comparison
-    stays within the 5e-5 of test_mixed_estep_error."""
+    1.3e-4, C = 0.014: the bound leaves a factor of 7); with the well-conditioned Sigma of
+    test_mixed_estep_error the per-pair bound is 5e-5."""
     p, q, g, n = 32, 2, 2, 400
     rng = np.random.default_rng(3232)
     P = synth.draw_params(rng, p, q, g, wishart_df=p + 8)
